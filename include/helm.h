@@ -1,0 +1,187 @@
+/*
+ * helm.h -- C ABI of the GB300 semi matrix-free twogrid-preconditioned FGMRES
+ * solver for the Helmholtz problem with an impedance boundary.
+ *
+ * The method (arXiv 2104.01439):
+ *   -Lap u - k^2 u = f in (0,1)^d,  du/dn - i k u = g on the boundary (Sec. 2,
+ *   eq. Helmholtz). Lagrange FE discretisation gives A(k,eps) u = F with
+ *   A(k,eps) = K - (k^2 + i eps) M - i k B  (Sec. 2, eq. sys_matrix).
+ *   FGMRES (Saad 1993) solves A0 P_eps^{-1} (P_eps u) = F with A0 = A(k,0);
+ *   P_eps^{-1} is one twogrid V(nu,nu)-cycle on A_eps = A(k,eps): damped
+ *   Jacobi smoothing, restriction P^T, a direct coarse solve on the 2h mesh,
+ *   prolongation P (Sec. 4, Algorithm 1). Fine-level operators are applied
+ *   matrix-free; the coarse matrix is factored once per (k, h, order, shift)
+ *   (Sec. 6: "semi matrix-free").
+ *
+ * Discretisation of this library: P1 or P2 Lagrange elements on the uniform
+ * right-triangle mesh of the unit square (each cell split along its main
+ * diagonal), or P1 on Kuhn's six-tetrahedra subdivision of the unit cube.
+ * DoFs are numbered lexicographically, x fastest: (order*n + 1)^dim of them.
+ *
+ * Conventions for every entry point:
+ *   - complex vectors are interleaved (re, im) pairs of double (complex128);
+ *   - "device" pointers are CUDA device memory owned by the caller, used on
+ *     the handle's stream and never retained after the call returns;
+ *   - "host" pointers are host memory owned by the caller;
+ *   - return value: HELM_OK (0) or a negative HELM_E* code; nothing calls
+ *     exit(), prints, or traps on the device. After an error the handle stays
+ *     valid unless the code is HELM_ECUDA (the CUDA context may be lost).
+ */
+#ifndef HELM_H
+#define HELM_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- return codes ---------------------------------------------------- */
+#define HELM_OK 0
+#define HELM_EINVAL (-1)     /* bad argument (sizes, order, dim, null pointer) */
+#define HELM_ENOMEM (-2)     /* device allocation failed */
+#define HELM_ECUDA (-3)      /* a CUDA runtime call failed */
+#define HELM_EZEROPIVOT (-4) /* coarse factorisation met a zero/non-finite pivot (eps = 0 can) */
+#define HELM_ETIMEOUT (-5)   /* a bounded device-side wait ran out */
+#define HELM_ENOTSUP (-6)    /* configuration not supported by this build/device */
+
+/* ---- helm_result.status (non-fatal outcome of a solve) --------------- */
+#define HELM_CONVERGED 0     /* true relative residual <= tol */
+#define HELM_MAXIT 1         /* iteration cap reached; x holds the last iterate */
+#define HELM_BREAKDOWN 2     /* h_{j+1,j} = 0 (happy breakdown); x is the Krylov solution */
+#define HELM_NONFINITE 3     /* NaN/Inf met in the residual; x is not meaningful */
+
+/* ---- precision of the preconditioner (opts.precision) ---------------- */
+#define HELM_FP64 0          /* everything in complex128 */
+#define HELM_MIXED 1         /* V-cycle (smoother, transfers, coarse triangular
+                                solves) in complex64; outer apply, Arnoldi,
+                                Givens, true residual and the coarse
+                                factorisation in complex128 */
+
+typedef struct helm_ctx* helm_t;
+
+typedef struct {
+  int dim;          /* 2 or 3 (3 only with order 1)                      */
+  double omega;     /* Jacobi damping (paper: 2/3, Sec. 4; default 0.6)   */
+  int nu;           /* pre- and post-smoothing steps of V(nu,nu), 1..8    */
+  int restart;      /* FGMRES restart length m, 1..512                    */
+  int maxit;        /* cap on total Arnoldi steps (paper: 500, Sec. 6)    */
+  double tol;       /* on the TRUE relative residual ||F - A0 x||/||F||   */
+  int precision;    /* HELM_FP64 or HELM_MIXED                            */
+  void* stream;     /* cudaStream_t for all work of this handle (NULL = legacy default) */
+} helm_opts;
+
+typedef struct {
+  int iters;            /* total Arnoldi steps = preconditioner applications */
+  int cycles;           /* FGMRES cycles (restarts + 1)                      */
+  int status;           /* HELM_CONVERGED / HELM_MAXIT / HELM_BREAKDOWN / HELM_NONFINITE */
+  double relres_true;   /* ||F - A0 x|| / ||F|| recomputed in FP64 at the end */
+  double relres_est;    /* last Givens residual estimate |g_{j+1}| / ||F||    */
+  float solve_ms;       /* device time of the solve (CUDA events)            */
+} helm_result;
+
+/* Defaults: dim 2, omega 0.6, nu 2, restart 50, maxit 500, tol 1e-8, FP64, stream NULL. */
+void helm_default_opts(helm_opts* opts);
+
+/*
+ * Set up a solver for A(k, shift) on the mesh with h = 1/n (1/h must be an
+ * even integer >= 4) and Lagrange order 1 or 2 (Sec. 2; Sec. 4 two levels).
+ * Builds the per-DoF-class stencil coefficients of A0 and A_eps, the Jacobi
+ * diagonal, the transfer weights, and factors the coarse matrix A_eps^(2h)
+ * (block tridiagonal over grid lines / planes; the explicit inverses of the
+ * diagonal Schur blocks are formed by Gauss-Jordan without pivoting, in
+ * complex128; for shift > 0 every leading principal minor is non-zero because
+ * Im(x^H A x) < 0). Allocates all device state on the opts' stream.
+ * shift >= 0 is the paper's epsilon (Sec. 2, eq. Helmholtz_shift).
+ * Returns HELM_EZEROPIVOT if a pivot is zero or not finite (possible for shift = 0).
+ */
+int helm_setup(double k, double h, int order, double shift, const helm_opts* opts, helm_t* out);
+
+/* Number of complex DoFs N = (order/h + 1)^dim of the fine space. */
+int helm_num_dofs(helm_t h, int64_t* n);
+
+/* Number of complex DoFs of the 2h (coarse) space. */
+int helm_num_coarse_dofs(helm_t h, int64_t* n);
+
+/* Milliseconds the last helm_setup spent (device events around the coarse factorisation and tables). */
+int helm_setup_ms(helm_t h, float* ms);
+
+/*
+ * Solve A0 x = F (Sec. 4: FGMRES right-preconditioned by the twogrid
+ * V-cycle on A_eps). F, x: device complex128[N], caller-owned; x is
+ * overwritten (x0 = 0 is used, any input content is ignored).
+ * The call is synchronous with respect to the host (it reads the convergence
+ * state). res may be NULL.
+ */
+int helm_solve(helm_t h, const void* F, void* x, helm_result* res);
+
+/*
+ * Same as helm_solve with HOST buffers: copies F host->device, solves, copies
+ * x device->host, all on the handle's stream. F_host, x_host: complex128[N].
+ */
+int helm_solve_host(helm_t h, const void* F_host, void* x_host, helm_result* res);
+
+/*
+ * Solve `count` independent problems concurrently (each handle keeps its own
+ * stream; their iterations are interleaved by one host loop so that the
+ * device overlaps them). F[i], x[i]: device complex128 of handle i's size.
+ * res: array of count results (may be NULL). Handles must be distinct.
+ */
+int helm_batch_solve(int count, const helm_t* hs, const void* const* F, void* const* x,
+                     helm_result* res);
+
+/* Free every device resource of the handle. NULL is ignored. */
+void helm_destroy(helm_t h);
+
+/* Static string for a return code. */
+const char* helm_strerror(int code);
+
+/* Name of the last CUDA runtime error this thread met inside the library
+ * ("none" if there was none); the detail behind a HELM_ECUDA / HELM_ENOMEM. */
+const char* helm_last_cuda_error(void);
+
+/* ---- right-hand sides (host output, complex128[N]) --------------------- */
+
+/*
+ * Load vector of the plane wave u = exp(i k d.x), d = (cos theta, sin theta[, 0]):
+ * f = 0 and impedance data g = i k (d.n - 1) u on each boundary facet with
+ * that facet's outward normal (Sec. 2, F(v) = int f v + int_dOmega g v).
+ */
+int helm_rhs_planewave(helm_t h, double theta, void* F_host);
+
+/* Load vector of f = exp(-|x - c|^2 / (2 sigma^2)) with g = 0: F = M (I_h f). */
+int helm_rhs_gaussian(helm_t h, double sigma, double cx, double cy, double cz, void* F_host);
+
+/* ---- individual hot-path steps (device complex128 buffers) ------------- */
+
+/* y = A x with A = A0 (which = 0) or A_eps (which = 1), matrix-free, FP64 (Sec. 6). */
+int helm_apply(helm_t h, int which, const void* x, void* y);
+
+/*
+ * u = one twogrid V(nu,nu)-cycle on A_eps applied to f with u^0 = 0
+ * (Algorithm 1), in the handle's precision. f, u: device complex128[N].
+ */
+int helm_vcycle(helm_t h, const void* f, void* u);
+
+/*
+ * uc = A_eps^(2h)^{-1} rc with the stored coarse factor (Algorithm 1, direct
+ * coarse solve), in the handle's precision. rc, uc: device complex128[Nc],
+ * lexicographic order of the 2h mesh's DoFs.
+ */
+int helm_coarse_solve(helm_t h, const void* rc, void* uc);
+
+/*
+ * Runtime statistics of the last solve's kernels: fills up to `cap` entries
+ * of names/ms (device time per phase, summed over the solve) and returns the
+ * count through *n. Used by the benchmark for the roofline of each kernel.
+ */
+int helm_last_profile(helm_t h, int cap, const char** names, double* ms, int* calls, int* n);
+
+/* Enable (1) / disable (0) per-phase CUDA-event timing inside helm_solve (default off). */
+int helm_set_profiling(helm_t h, int on);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* HELM_H */

@@ -1,0 +1,223 @@
+"""Thin ctypes binding of include/helm.h (argument marshalling only).
+
+Every computation happens in libhelm.so's CUDA kernels. Device buffers are
+PyTorch complex128 CUDA tensors (interleaved re/im doubles); the library runs
+on the CUDA stream given at setup (default: PyTorch's current stream).
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from dataclasses import dataclass
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libhelm.so")
+
+HELM_OK = 0
+HELM_FP64 = 0
+HELM_MIXED = 1
+STATUS = {0: "converged", 1: "maxit", 2: "breakdown", 3: "nonfinite"}
+
+EXPORTS = [
+    "helm_default_opts", "helm_setup", "helm_last_cuda_error", "helm_num_dofs", "helm_num_coarse_dofs", "helm_setup_ms",
+    "helm_solve", "helm_solve_host", "helm_batch_solve", "helm_destroy", "helm_strerror",
+    "helm_rhs_planewave", "helm_rhs_gaussian", "helm_apply", "helm_vcycle", "helm_coarse_solve",
+    "helm_last_profile", "helm_set_profiling",
+]
+
+
+class HelmOpts(ctypes.Structure):
+    _fields_ = [("dim", ctypes.c_int), ("omega", ctypes.c_double), ("nu", ctypes.c_int),
+                ("restart", ctypes.c_int), ("maxit", ctypes.c_int), ("tol", ctypes.c_double),
+                ("precision", ctypes.c_int), ("stream", ctypes.c_void_p)]
+
+
+class HelmResult(ctypes.Structure):
+    _fields_ = [("iters", ctypes.c_int), ("cycles", ctypes.c_int), ("status", ctypes.c_int),
+                ("relres_true", ctypes.c_double), ("relres_est", ctypes.c_double),
+                ("solve_ms", ctypes.c_float)]
+
+
+class HelmError(RuntimeError):
+    pass
+
+
+_lib = None
+
+
+def load(path: str = LIB_PATH):
+    """Load libhelm.so (raises if it has not been built: there is no fallback path)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise HelmError(f"{path} not found: build it with paper_2104_01439_gb300.build.build()")
+    lib = ctypes.CDLL(path)
+    vp, i, d, i64p = ctypes.c_void_p, ctypes.c_int, ctypes.c_double, ctypes.POINTER(ctypes.c_int64)
+    lib.helm_default_opts.argtypes = [ctypes.POINTER(HelmOpts)]
+    lib.helm_default_opts.restype = None
+    lib.helm_setup.argtypes = [d, d, i, d, ctypes.POINTER(HelmOpts), ctypes.POINTER(vp)]
+    lib.helm_num_dofs.argtypes = [vp, i64p]
+    lib.helm_num_coarse_dofs.argtypes = [vp, i64p]
+    lib.helm_setup_ms.argtypes = [vp, ctypes.POINTER(ctypes.c_float)]
+    lib.helm_solve.argtypes = [vp, vp, vp, ctypes.POINTER(HelmResult)]
+    lib.helm_solve_host.argtypes = [vp, vp, vp, ctypes.POINTER(HelmResult)]
+    lib.helm_batch_solve.argtypes = [i, ctypes.POINTER(vp), ctypes.POINTER(vp), ctypes.POINTER(vp),
+                                     ctypes.POINTER(HelmResult)]
+    lib.helm_destroy.argtypes = [vp]
+    lib.helm_destroy.restype = None
+    lib.helm_strerror.argtypes = [i]
+    lib.helm_strerror.restype = ctypes.c_char_p
+    lib.helm_last_cuda_error.argtypes = []
+    lib.helm_last_cuda_error.restype = ctypes.c_char_p
+    lib.helm_rhs_planewave.argtypes = [vp, d, vp]
+    lib.helm_rhs_gaussian.argtypes = [vp, d, d, d, d, vp]
+    lib.helm_apply.argtypes = [vp, i, vp, vp]
+    lib.helm_vcycle.argtypes = [vp, vp, vp]
+    lib.helm_coarse_solve.argtypes = [vp, vp, vp]
+    lib.helm_last_profile.argtypes = [vp, i, ctypes.POINTER(ctypes.c_char_p), ctypes.POINTER(d),
+                                      ctypes.POINTER(i), ctypes.POINTER(i)]
+    lib.helm_set_profiling.argtypes = [vp, i]
+    for name in EXPORTS:
+        if name not in ("helm_default_opts", "helm_destroy", "helm_strerror", "helm_last_cuda_error"):
+            getattr(lib, name).restype = i
+    _lib = lib
+    return lib
+
+
+def _check(rc: int):
+    if rc != HELM_OK:
+        lib = load()
+        raise HelmError(f"helm error {rc}: {lib.helm_strerror(rc).decode()} "
+                        f"(last CUDA error: {lib.helm_last_cuda_error().decode()})")
+
+
+@dataclass
+class SolveResult:
+    iters: int
+    cycles: int
+    status: str
+    relres_true: float
+    relres_est: float
+    solve_ms: float
+
+
+def _res(r: HelmResult) -> SolveResult:
+    return SolveResult(r.iters, r.cycles, STATUS.get(r.status, str(r.status)), r.relres_true,
+                       r.relres_est, r.solve_ms)
+
+
+def _ptr(t):
+    import torch
+    if not isinstance(t, torch.Tensor) or t.dtype != torch.complex128 or not t.is_contiguous():
+        raise TypeError("expected a contiguous complex128 tensor")
+    return ctypes.c_void_p(t.data_ptr())
+
+
+class Solver:
+    """A set-up solver for A(k, shift) on the h = 1/n mesh (wraps helm_setup)."""
+
+    def __init__(self, k: float, n: int, order: int = 1, shift: float = 0.0, dim: int = 2,
+                 omega: float = 0.6, nu: int = 2, restart: int = 50, maxit: int = 500,
+                 tol: float = 1e-8, precision: int = HELM_FP64, stream=None):
+        import torch
+        lib = load()
+        o = HelmOpts()
+        lib.helm_default_opts(ctypes.byref(o))
+        o.dim, o.omega, o.nu, o.restart, o.maxit, o.tol, o.precision = dim, omega, nu, restart, maxit, tol, precision
+        if stream is None:
+            stream = torch.cuda.current_stream()
+        self.stream = stream
+        o.stream = ctypes.c_void_p(stream.cuda_stream)
+        self._h = ctypes.c_void_p()
+        self.k, self.n, self.order, self.shift, self.dim, self.precision = k, n, order, shift, dim, precision
+        _check(lib.helm_setup(float(k), 1.0 / n, order, float(shift), ctypes.byref(o), ctypes.byref(self._h)))
+        nd = ctypes.c_int64()
+        _check(lib.helm_num_dofs(self._h, ctypes.byref(nd)))
+        self.num_dofs = nd.value
+        _check(lib.helm_num_coarse_dofs(self._h, ctypes.byref(nd)))
+        self.num_coarse_dofs = nd.value
+        ms = ctypes.c_float()
+        _check(lib.helm_setup_ms(self._h, ctypes.byref(ms)))
+        self.setup_ms = ms.value
+
+    @property
+    def handle(self):
+        return self._h
+
+    def close(self):
+        if self._h:
+            load().helm_destroy(self._h)
+            self._h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def _dev(self, n=None):
+        import torch
+        return torch.empty(self.num_dofs if n is None else n, dtype=torch.complex128, device="cuda")
+
+    def solve(self, F, x=None) -> tuple:
+        x = self._dev() if x is None else x
+        r = HelmResult()
+        _check(load().helm_solve(self._h, _ptr(F), _ptr(x), ctypes.byref(r)))
+        return x, _res(r)
+
+    def solve_host(self, F_host, x_host) -> SolveResult:
+        r = HelmResult()
+        _check(load().helm_solve_host(self._h, _ptr(F_host), _ptr(x_host), ctypes.byref(r)))
+        return _res(r)
+
+    def apply(self, x, which: int = 0):
+        y = self._dev()
+        _check(load().helm_apply(self._h, which, _ptr(x), _ptr(y)))
+        return y
+
+    def vcycle(self, f):
+        u = self._dev()
+        _check(load().helm_vcycle(self._h, _ptr(f), _ptr(u)))
+        return u
+
+    def coarse_solve(self, rc):
+        uc = self._dev(self.num_coarse_dofs)
+        _check(load().helm_coarse_solve(self._h, _ptr(rc), _ptr(uc)))
+        return uc
+
+    def rhs_planewave(self, theta: float = 0.3):
+        import torch
+        F = torch.empty(self.num_dofs, dtype=torch.complex128)
+        _check(load().helm_rhs_planewave(self._h, theta, ctypes.c_void_p(F.data_ptr())))
+        return F
+
+    def rhs_gaussian(self, sigma: float, center=(0.5, 0.5, 0.5)):
+        import torch
+        F = torch.empty(self.num_dofs, dtype=torch.complex128)
+        c = list(center) + [0.5] * (3 - len(center))
+        _check(load().helm_rhs_gaussian(self._h, sigma, c[0], c[1], c[2], ctypes.c_void_p(F.data_ptr())))
+        return F
+
+    def set_profiling(self, on: bool):
+        _check(load().helm_set_profiling(self._h, 1 if on else 0))
+
+    def profile(self) -> dict:
+        n = ctypes.c_int()
+        names = (ctypes.c_char_p * 16)()
+        ms = (ctypes.c_double * 16)()
+        calls = (ctypes.c_int * 16)()
+        _check(load().helm_last_profile(self._h, 16, names, ms, calls, ctypes.byref(n)))
+        return {names[i].decode(): (ms[i], calls[i]) for i in range(n.value)}
+
+
+def batch_solve(solvers, Fs, xs=None):
+    """helm_batch_solve over distinct solvers; returns (xs, results)."""
+    n = len(solvers)
+    xs = [s._dev() for s in solvers] if xs is None else xs
+    hs = (ctypes.c_void_p * n)(*[s.handle.value for s in solvers])
+    fp = (ctypes.c_void_p * n)(*[F.data_ptr() for F in Fs])
+    xp = (ctypes.c_void_p * n)(*[x.data_ptr() for x in xs])
+    res = (HelmResult * n)()
+    _check(load().helm_batch_solve(n, hs, fp, xp, res))
+    return xs, [_res(r) for r in res]

@@ -1,0 +1,766 @@
+// C ABI (include/helm.h): setup of the operators and the coarse factor, the
+// V-cycle and FGMRES iteration as a captured CUDA graph, the host loop that
+// launches iterations and reads the device's convergence state, batched
+// solves over several streams, and the single-step entry points.
+#include <algorithm>
+#include <chrono>
+#include <cmath>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include "kernels.cuh"
+
+using namespace helm;
+
+namespace {
+
+struct Profile {
+  bool on = false;
+  static constexpr int kPhases = 6;
+  double ms[kPhases] = {0};
+  int calls[kPhases] = {0};
+  std::vector<cudaEvent_t> ev;   // kPhases + 1 per iteration
+};
+const char* kPhaseNames[Profile::kPhases] = {"vcycle_pre_restrict", "coarse_solve", "vcycle_prolong_post",
+                                             "apply_A0", "arnoldi_cgs", "givens"};
+
+template <typename T> struct Prec {
+  c2<T>* coefAe = nullptr;   // fine A_eps
+  c2<T>* wdinv = nullptr;    // fine omega/diag(A_eps)
+  c2<T>* coefAc = nullptr;   // coarse A_eps
+  T* pw = nullptr;           // prolongation weights
+  c2<T>* Dinv = nullptr;     // coarse factor
+  CoarsePlan plan{};
+  // V-cycle workspaces
+  c2<T>* ua = nullptr;
+  c2<T>* ub = nullptr;
+  c2<T>* r = nullptr;
+  c2<T>* fT = nullptr;
+  c2<T>* rc = nullptr;
+  c2<T>* uc = nullptr;
+};
+
+}  // namespace
+
+struct helm_ctx {
+  int dim = 2, order = 1, n = 0;
+  double k = 0, h = 0, shift = 0;
+  helm_opts opts{};
+  cudaStream_t s = nullptr;
+  int nsm = 0;
+  HostTables tab;
+  GridDesc gf{}, gc{};
+  CoarseLayout L{};
+  int ncls_f = 0, ncls_c = 0;
+  double2* coefA0 = nullptr;   // fine A0 (FP64)
+  int* cpl = nullptr;          // coarse coupling lists
+  Prec<double> p64;
+  Prec<float> p32;
+  // Krylov
+  KrylovBufs kb{};
+  KState* st_h = nullptr;   // pinned mirror
+  int* err = nullptr;
+  double2* rres = nullptr;  // true residual buffer
+  double2* Fdev = nullptr;  // staging for host solves
+  double2* xdev = nullptr;
+  cudaGraphExec_t iter = nullptr;
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  float setup_ms = 0.f;
+  Profile prof;
+  std::vector<void*> allocs;
+
+  template <typename P> cudaError_t alloc(P** p, size_t bytes) {
+    cudaError_t e = cudaMalloc((void**)p, std::max<size_t>(bytes, 16));
+    if (e == cudaSuccess) allocs.push_back(*p);
+    return e;
+  }
+  template <typename T> Prec<T>& prec();
+};
+template <> Prec<double>& helm_ctx::prec<double>() { return p64; }
+template <> Prec<float>& helm_ctx::prec<float>() { return p32; }
+
+namespace {
+
+thread_local const char* g_last_cuda_error = "none";
+
+int cuda_fail(cudaError_t e) {
+  g_last_cuda_error = cudaGetErrorName(e);
+  return e == cudaErrorMemoryAllocation ? HELM_ENOMEM : HELM_ECUDA;
+}
+
+#define CK(x)                                 \
+  do {                                        \
+    cudaError_t e_ = (x);                     \
+    if (e_ != cudaSuccess) return cuda_fail(e_); \
+  } while (0)
+
+template <typename T>
+StencilView<T> make_view(const GridDesc& g, const c2<T>* coef, const c2<T>* wdinv) {
+  StencilView<T> v{};
+  v.coef = coef;
+  v.wdinv = wdinv;
+  v.g = g;
+  int side = 2 * g.R + 1;
+  for (int o = 0; o < g.noff; ++o) {
+    int t = o, lin = 0, mul = 1;
+    for (int ax = 0; ax < 3; ++ax) {
+      int d = 0;
+      if (ax < g.dim) {
+        d = t % side - g.R;
+        t /= side;
+      }
+      v.dx[o][ax] = d;
+      if (ax < g.dim) {
+        lin += d * mul;
+        mul *= g.W;
+      }
+    }
+    v.off[o] = lin;
+  }
+  return v;
+}
+
+template <typename T>
+TransferView<T> make_transfer(const helm_ctx* h, const T* w) {
+  TransferView<T> P{};
+  P.w = w;
+  P.fine = h->gf;
+  P.coarse = h->gc;
+  P.pf = h->tab.pf;
+  P.npc = h->tab.npc;
+  P.npo = h->tab.npo;
+  int q = h->order;
+  for (int o = 0; o < P.npo; ++o) {
+    int t = o;
+    for (int ax = 0; ax < 3; ++ax) {
+      P.po[o][ax] = ax < h->dim ? t % (q + 1) : 0;
+      if (ax < h->dim) t /= (q + 1);
+    }
+  }
+  return P;
+}
+
+// complex coefficient table K - lam M - i k B for one level
+std::vector<double2> complex_table(const std::vector<double>& K, const std::vector<double>& M,
+                                   const std::vector<double>& B, double k, double eps) {
+  std::vector<double2> c(K.size());
+  for (size_t i = 0; i < K.size(); ++i) {
+    // (K - k^2 M) + i (-eps M - k B)
+    c[i] = make_double2(K[i] - k * k * M[i], -eps * M[i] - k * B[i]);
+  }
+  return c;
+}
+
+std::vector<double2> wdinv_table(const std::vector<double2>& coef, int ncls, int noff, double omega) {
+  std::vector<double2> d(ncls);
+  int center = noff / 2;   // box centre (all offsets zero)
+  for (int c = 0; c < ncls; ++c) {
+    double2 a = coef[(size_t)c * noff + center];
+    double m2 = a.x * a.x + a.y * a.y;
+    d[c] = m2 > 0 ? make_double2(omega * a.x / m2, -omega * a.y / m2) : make_double2(0, 0);
+  }
+  return d;
+}
+
+template <typename T>
+int upload(helm_ctx* h, c2<T>** dst, const std::vector<double2>& src) {
+  std::vector<c2<T>> tmp(src.size());
+  for (size_t i = 0; i < src.size(); ++i) tmp[i] = mk((T)src[i].x, (T)src[i].y);
+  CK(h->alloc(dst, sizeof(c2<T>) * tmp.size()));
+  CK(cudaMemcpy(*dst, tmp.data(), sizeof(c2<T>) * tmp.size(), cudaMemcpyHostToDevice));
+  return HELM_OK;
+}
+template <typename T>
+int upload_real(helm_ctx* h, T** dst, const std::vector<double>& src) {
+  std::vector<T> tmp(src.begin(), src.end());
+  CK(h->alloc(dst, sizeof(T) * tmp.size()));
+  CK(cudaMemcpy(*dst, tmp.data(), sizeof(T) * tmp.size(), cudaMemcpyHostToDevice));
+  return HELM_OK;
+}
+
+template <typename T>
+int setup_prec(helm_ctx* h, const std::vector<double2>& Ae, const std::vector<double2>& wd,
+               const std::vector<double2>& Ac, bool solves) {
+  Prec<T>& p = h->prec<T>();
+  int rc;
+  if ((rc = upload<T>(h, &p.coefAe, Ae))) return rc;
+  if ((rc = upload<T>(h, &p.wdinv, wd))) return rc;
+  if ((rc = upload<T>(h, &p.coefAc, Ac))) return rc;
+  if ((rc = upload_real<T>(h, &p.pw, h->tab.pw))) return rc;
+  if (!solves) return HELM_OK;   // tables only (the FP64 coarse table feeds the factorisation)
+  size_t Nf = (size_t)h->gf.N, Nc = (size_t)h->L.nb * h->L.ldb;
+  CK(h->alloc(&p.ua, sizeof(c2<T>) * Nf));
+  CK(h->alloc(&p.ub, sizeof(c2<T>) * Nf));
+  CK(h->alloc(&p.r, sizeof(c2<T>) * Nf));
+  CK(h->alloc(&p.fT, sizeof(c2<T>) * Nf));
+  CK(h->alloc(&p.rc, sizeof(c2<T>) * Nc));
+  CK(h->alloc(&p.uc, sizeof(c2<T>) * Nc));
+  return plan_coarse_solve<T>(h->L, h->gc, &p.plan);
+}
+
+// One V(nu,nu)-cycle on A_eps (Algorithm 1, two levels): z = Vcycle(f), u^0 = 0.
+template <typename T>
+void enqueue_vcycle(helm_ctx* h, VecSel<const double2> f, VecSel<double2> z, const int* active,
+                    cudaStream_t s, Profile* prof, int ev0) {
+  using V = c2<T>;
+  Prec<T>& p = h->prec<T>();
+  StencilView<T> Ae = make_view<T>(h->gf, p.coefAe, p.wdinv);
+  StencilView<T> Ac = make_view<T>(h->gc, p.coefAc, nullptr);
+  TransferView<T> P = make_transfer<T>(h, p.pw);
+  const int nu = h->opts.nu;
+  V* cur = p.ua;
+  V* oth = p.ub;
+  VecSel<const V> fT;
+  if constexpr (sizeof(V) == sizeof(double2)) {
+    launch_jacobi_from_zero<T, double2>(Ae, f, cur, nullptr, nu >= 2, active, s);
+    fT = VecSel<const V>{reinterpret_cast<const V*>(f.base), f.stride, f.jsel, f.jadd};
+  } else {
+    launch_jacobi_from_zero<T, double2>(Ae, f, cur, p.fT, nu >= 2, active, s);
+    fT = vsel<const V>(p.fT);
+  }
+  for (int it = 2; it < nu; ++it) {   // presmoothing steps 3..nu
+    launch_jacobi<T, V, V>(Ae, fT, cur, vsel<V>(oth), active, s);
+    std::swap(cur, oth);
+  }
+  launch_residual<T, V, V>(Ae, fT, cur, p.r, active, s);
+  launch_restrict<T>(P, h->L, p.r, p.rc, active, s);
+  if (prof) cudaEventRecord(prof->ev[ev0 + 1], s);
+  launch_coarse_solve<T>(p.plan, p.Dinv, Ac, h->L, h->cpl, p.rc, p.uc, h->err, active, s);
+  if (prof) cudaEventRecord(prof->ev[ev0 + 2], s);
+  launch_prolong_add<T>(P, h->L, p.uc, cur, active, s);
+  for (int it = 0; it < nu; ++it) {   // postsmoothing
+    if (it == nu - 1) {
+      launch_jacobi<T, V, double2>(Ae, fT, cur, z, active, s);
+    } else {
+      launch_jacobi<T, V, V>(Ae, fT, cur, vsel<V>(oth), active, s);
+      std::swap(cur, oth);
+    }
+  }
+}
+
+void enqueue_vcycle_any(helm_ctx* h, VecSel<const double2> f, VecSel<double2> z, const int* active,
+                        cudaStream_t s, Profile* prof = nullptr, int ev0 = 0) {
+  if (h->opts.precision == HELM_MIXED)
+    enqueue_vcycle<float>(h, f, z, active, s, prof, ev0);
+  else
+    enqueue_vcycle<double>(h, f, z, active, s, prof, ev0);
+}
+
+// One FGMRES/Arnoldi step j (device index): z_j = Vcycle(v_j), w = A0 z_j,
+// CGS(+DGKS) against V[0..j], v_{j+1} = w/||w||, Givens + convergence test.
+void enqueue_iteration(helm_ctx* h, cudaStream_t s, Profile* prof = nullptr, int ev0 = 0) {
+  const KrylovBufs& kb = h->kb;
+  const int* act = &kb.st->active;
+  const int* jsel = &kb.st->j;
+  if (prof) cudaEventRecord(prof->ev[ev0 + 0], s);
+  enqueue_vcycle_any(h, VecSel<const double2>{kb.V, kb.ldN, jsel, 0}, VecSel<double2>{kb.Z, kb.ldN, jsel, 0},
+                     act, s, prof, ev0);
+  if (prof) cudaEventRecord(prof->ev[ev0 + 3], s);
+  StencilView<double> A0 = make_view<double>(h->gf, h->coefA0, nullptr);
+  launch_apply<double, double2, double2>(A0, VecSel<const double2>{kb.Z, kb.ldN, jsel, 0},
+                                         VecSel<double2>{kb.V, kb.ldN, jsel, 1}, act, s);
+  if (prof) cudaEventRecord(prof->ev[ev0 + 4], s);
+  launch_cgs_pass(kb, false, s);
+  launch_cgs_pass(kb, true, s);
+  launch_normalize(kb, s);
+  if (prof) cudaEventRecord(prof->ev[ev0 + 5], s);
+  launch_givens(kb, s);
+  if (prof) cudaEventRecord(prof->ev[ev0 + 6], s);
+}
+
+int capture_iteration(helm_ctx* h) {
+  cudaStream_t cs;
+  CK(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
+  cudaGraph_t g = nullptr;
+  cudaError_t e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
+  if (e == cudaSuccess) {
+    enqueue_iteration(h, cs);
+    e = cudaStreamEndCapture(cs, &g);
+  }
+  if (e == cudaSuccess) e = cudaGraphInstantiate(&h->iter, g, 0);
+  if (g) cudaGraphDestroy(g);
+  cudaStreamDestroy(cs);
+  if (e == cudaSuccess) e = cudaGetLastError();   // nothing may be left pending from the capture
+  return e == cudaSuccess ? HELM_OK : cuda_fail(e);
+}
+
+int check_err(helm_ctx* h) {
+  int e = 0;
+  cudaError_t ce = cudaMemcpy(&e, h->err, sizeof(int), cudaMemcpyDeviceToHost);
+  if (ce != cudaSuccess) return HELM_ECUDA;
+  return e;
+}
+
+// ---- solve driver: one FGMRES solve as a resumable state machine ----------
+struct SolveTask {
+  helm_ctx* h;
+  const double2* F;
+  double2* x;
+  helm_result* res;
+  enum Phase { ITER, WAIT_ITER, WAIT_END, DONE } phase = ITER;
+  int launched_in_cycle = 0;
+  int launched_total = 0;
+  int cycles = 0;
+  int rc = HELM_OK;
+  cudaEvent_t ready = nullptr;
+};
+
+int solve_begin(SolveTask& t) {
+  helm_ctx* h = t.h;
+  cudaStream_t s = h->s;
+  const KrylovBufs& kb = h->kb;
+  KState st{};
+  st.m = h->opts.restart;
+  st.maxit = h->opts.maxit;
+  st.tol = h->opts.tol;
+  CK(cudaMemcpyAsync(kb.st, &st, sizeof(KState), cudaMemcpyHostToDevice, s));
+  CK(cudaMemsetAsync(h->err, 0, sizeof(int), s));
+  CK(cudaMemsetAsync(t.x, 0, sizeof(double2) * kb.N, s));
+  CK(cudaEventRecord(h->e0, s));
+  launch_norm(kb, t.F, 0, s);          // ||F||, beta = ||F||  (x0 = 0: r0 = F)
+  launch_cycle_start(kb, t.F, s);      // v1 = F / beta
+  CK(cudaEventCreateWithFlags(&t.ready, cudaEventDisableTiming));
+  t.phase = SolveTask::ITER;
+  return HELM_OK;
+}
+
+// Advance the task without blocking when possible. Returns true when done.
+bool solve_step(SolveTask& t, bool blocking) {
+  helm_ctx* h = t.h;
+  cudaStream_t s = h->s;
+  const KrylovBufs& kb = h->kb;
+  const int m = h->opts.restart, maxit = h->opts.maxit;
+  switch (t.phase) {
+    case SolveTask::ITER: {
+      int chunk = std::min({4, m - t.launched_in_cycle, maxit - t.launched_total});
+      if (chunk < 1) chunk = 1;
+      for (int c = 0; c < chunk; ++c) {
+        if (h->prof.on) {
+          KState cur;
+          cudaMemcpyAsync(&cur, kb.st, sizeof(KState), cudaMemcpyDeviceToHost, s);
+          cudaStreamSynchronize(s);
+          if (!cur.active) break;
+          int need = (Profile::kPhases + 1);
+          if ((int)h->prof.ev.size() < need) {
+            h->prof.ev.resize(need);
+            for (auto& e : h->prof.ev) cudaEventCreate(&e);
+          }
+          enqueue_iteration(h, s, &h->prof, 0);
+          cudaEventSynchronize(h->prof.ev[Profile::kPhases]);
+          for (int ph = 0; ph < Profile::kPhases; ++ph) {
+            float ms = 0.f;
+            cudaEventElapsedTime(&ms, h->prof.ev[ph], h->prof.ev[ph + 1]);
+            h->prof.ms[ph] += ms;
+            h->prof.calls[ph] += 1;
+          }
+        } else {
+          cudaGraphLaunch(h->iter, s);
+        }
+      }
+      t.launched_in_cycle += chunk;
+      t.launched_total += chunk;
+      cudaMemcpyAsync(h->st_h, kb.st, sizeof(KState), cudaMemcpyDeviceToHost, s);
+      cudaEventRecord(t.ready, s);
+      t.phase = SolveTask::WAIT_ITER;
+      return false;
+    }
+    case SolveTask::WAIT_ITER: {
+      if (blocking) cudaEventSynchronize(t.ready);
+      else if (cudaEventQuery(t.ready) == cudaErrorNotReady) return false;
+      if (h->st_h->active && t.launched_in_cycle < m && t.launched_total < maxit) {
+        t.phase = SolveTask::ITER;
+        return false;
+      }
+      // cycle end: y = R^{-1} g, x += Z y, true residual
+      launch_backsolve(kb, s);
+      launch_update_x(kb, t.x, s);
+      StencilView<double> A0 = make_view<double>(h->gf, h->coefA0, nullptr);
+      launch_residual<double, double2, double2>(A0, vsel<const double2>(t.F), t.x, h->rres, nullptr, s);
+      launch_norm(kb, h->rres, 1, s);
+      cudaMemcpyAsync(h->st_h, kb.st, sizeof(KState), cudaMemcpyDeviceToHost, s);
+      cudaEventRecord(t.ready, s);
+      t.cycles += 1;
+      t.phase = SolveTask::WAIT_END;
+      return false;
+    }
+    case SolveTask::WAIT_END: {
+      if (blocking) cudaEventSynchronize(t.ready);
+      else if (cudaEventQuery(t.ready) == cudaErrorNotReady) return false;
+      KState* st = h->st_h;
+      bool done = st->relres <= h->opts.tol || st->total >= maxit || st->breakdown || st->nonfinite ||
+                  !(st->relres == st->relres);
+      if (!done) {
+        launch_cycle_start(kb, h->rres, s);   // restart from r = F - A0 x
+        t.launched_in_cycle = 0;
+        t.phase = SolveTask::ITER;
+        return false;
+      }
+      cudaEventRecord(h->e1, s);
+      cudaEventSynchronize(h->e1);
+      int e = 0;
+      cudaMemcpy(&e, h->err, sizeof(int), cudaMemcpyDeviceToHost);
+      cudaError_t ce = cudaGetLastError();
+      if (ce != cudaSuccess) t.rc = cuda_fail(ce);
+      else if (e != 0) t.rc = e;
+      if (t.res) {
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, h->e0, h->e1);
+        t.res->iters = st->total;
+        t.res->cycles = t.cycles;
+        t.res->relres_true = st->relres;
+        t.res->relres_est = st->est;
+        t.res->solve_ms = ms;
+        t.res->status = st->nonfinite || !(st->relres == st->relres) ? HELM_NONFINITE
+                        : st->relres <= h->opts.tol                  ? HELM_CONVERGED
+                        : st->breakdown                             ? HELM_BREAKDOWN
+                                                                    : HELM_MAXIT;
+      }
+      cudaEventDestroy(t.ready);
+      t.ready = nullptr;
+      t.phase = SolveTask::DONE;
+      return true;
+    }
+    case SolveTask::DONE:
+      return true;
+  }
+  return true;
+}
+
+}  // namespace
+
+// ============================================================================
+extern "C" {
+
+void helm_default_opts(helm_opts* o) {
+  if (!o) return;
+  o->dim = 2;
+  o->omega = 0.6;
+  o->nu = 2;
+  o->restart = 50;
+  o->maxit = 500;
+  o->tol = 1e-8;
+  o->precision = HELM_FP64;
+  o->stream = nullptr;
+}
+
+const char* helm_last_cuda_error(void) { return g_last_cuda_error; }
+
+const char* helm_strerror(int code) {
+  switch (code) {
+    case HELM_OK: return "ok";
+    case HELM_EINVAL: return "invalid argument";
+    case HELM_ENOMEM: return "device out of memory";
+    case HELM_ECUDA: return "CUDA runtime error";
+    case HELM_EZEROPIVOT: return "zero or non-finite pivot in the coarse factorisation";
+    case HELM_ETIMEOUT: return "bounded device wait timed out";
+    case HELM_ENOTSUP: return "configuration not supported on this device";
+    default: return "unknown error";
+  }
+}
+
+void helm_destroy(helm_t h) {
+  if (!h) return;
+  if (h->s) cudaStreamSynchronize(h->s);
+  if (h->iter) cudaGraphExecDestroy(h->iter);
+  for (void* p : h->allocs) cudaFree(p);
+  if (h->st_h) cudaFreeHost(h->st_h);
+  if (h->e0) cudaEventDestroy(h->e0);
+  if (h->e1) cudaEventDestroy(h->e1);
+  for (auto& e : h->prof.ev) cudaEventDestroy(e);
+  delete h;
+}
+
+static int setup_impl(helm_ctx* h) {
+  const helm_opts& o = h->opts;
+  int rc = build_tables(o.dim, h->order, h->n, &h->tab);
+  if (rc) return rc;
+  h->gf = h->tab.fine;
+  h->gc = h->tab.coarse;
+  h->ncls_f = h->tab.ncls_f;
+  h->ncls_c = h->tab.ncls_c;
+  if (h->gf.N >= (1ll << 31) / 2) return HELM_ENOTSUP;
+  int dev = 0;
+  CK(cudaGetDevice(&dev));
+  CK(cudaDeviceGetAttribute(&h->nsm, cudaDevAttrMultiProcessorCount, dev));
+  CK(cudaEventCreate(&h->e0));
+  CK(cudaEventCreate(&h->e1));
+  cudaStream_t s = h->s;
+
+  // coefficient tables (Sec. 2, eq. sys_matrix): A0 = A(k, 0), A_eps = A(k, eps)
+  auto A0 = complex_table(h->tab.Kf, h->tab.Mf, h->tab.Bf, h->k, 0.0);
+  auto Ae = complex_table(h->tab.Kf, h->tab.Mf, h->tab.Bf, h->k, h->shift);
+  auto Ac = complex_table(h->tab.Kc, h->tab.Mc, h->tab.Bc, h->k, h->shift);
+  auto wd = wdinv_table(Ae, h->ncls_f, h->gf.noff, o.omega);
+  if ((rc = upload<double>(h, &h->coefA0, A0))) return rc;
+
+  // coarse block layout
+  CoarseLayout& L = h->L;
+  L.rows = h->order;
+  L.plane = 1;
+  for (int ax = 0; ax < o.dim - 1; ++ax) L.plane *= h->gc.W;
+  L.nb = (h->gc.W + L.rows - 1) / L.rows;
+  L.B = L.rows * L.plane;
+  L.ldb = (L.B + 1) & ~1;
+  {
+    std::vector<int> lists;
+    coupling_lists(h->gc, L, lists);
+    CK(h->alloc(&h->cpl, sizeof(int) * lists.size()));
+    CK(cudaMemcpy(h->cpl, lists.data(), sizeof(int) * lists.size(), cudaMemcpyHostToDevice));
+  }
+  if (o.precision == HELM_MIXED) {
+    if ((rc = setup_prec<float>(h, Ae, wd, Ac, true))) return rc;
+  }
+  if ((rc = setup_prec<double>(h, Ae, wd, Ac, o.precision == HELM_FP64))) return rc;
+
+  // coarse factorisation in FP64 (Sec. 6: factor once, reuse)
+  size_t blk = (size_t)L.B * L.ldb;
+  double2* D64 = nullptr;
+  double2 *tmp = nullptr, *piv = nullptr;
+  unsigned* bar = nullptr;
+  CK(cudaMalloc(&D64, sizeof(double2) * blk * L.nb));
+  CK(cudaMalloc(&tmp, sizeof(double2) * blk));
+  CK(cudaMalloc(&piv, sizeof(double2) * 2 * L.ldb));
+  CK(cudaMalloc(&bar, 2 * sizeof(unsigned)));
+  CK(h->alloc(&h->err, sizeof(int)));
+  CK(cudaMemsetAsync(h->err, 0, sizeof(int), s));
+  CK(cudaEventRecord(h->e0, s));
+  StencilView<double> Acv = make_view<double>(h->gc, h->p64.coefAc, nullptr);
+  rc = launch_coarse_factor<double>(D64, tmp, piv, bar, h->err, Acv, L, h->nsm, s);
+  if (rc == HELM_OK && o.precision == HELM_MIXED) {
+    if (cudaMalloc(&h->p32.Dinv, sizeof(float2) * blk * L.nb) != cudaSuccess) rc = HELM_ENOMEM;
+    else {
+      h->allocs.push_back(h->p32.Dinv);
+      launch_convert_factor(D64, h->p32.Dinv, blk * L.nb, s);
+    }
+  }
+  cudaEventRecord(h->e1, s);
+  cudaEventSynchronize(h->e1);
+  cudaEventElapsedTime(&h->setup_ms, h->e0, h->e1);
+  cudaFree(tmp);
+  cudaFree(piv);
+  cudaFree(bar);
+  if (rc == HELM_OK) {
+    cudaError_t le = cudaGetLastError();
+    if (le != cudaSuccess) rc = cuda_fail(le);
+  }
+  if (rc == HELM_OK) {
+    int e = check_err(h);
+    if (e) rc = e;
+  }
+  if (rc != HELM_OK) {
+    cudaFree(D64);
+    return rc;
+  }
+  if (o.precision == HELM_MIXED) {
+    cudaFree(D64);
+  } else {
+    h->p64.Dinv = D64;
+    h->allocs.push_back(D64);
+  }
+
+  // Krylov storage
+  KrylovBufs& kb = h->kb;
+  const int m = o.restart;
+  kb.N = h->gf.N;
+  kb.ldN = (kb.N + 31) & ~int64_t(31);
+  kb.nblk = std::max(1, std::min<int>((int)((kb.N + 255) / 256), 2 * h->nsm));
+  CK(h->alloc(&kb.V, sizeof(double2) * kb.ldN * (m + 1)));
+  CK(h->alloc(&kb.Z, sizeof(double2) * kb.ldN * m));
+  CK(h->alloc(&kb.H, sizeof(double2) * (m + 1) * m));
+  CK(h->alloc(&kb.cs, sizeof(double) * m));
+  CK(h->alloc(&kb.sn, sizeof(double2) * m));
+  CK(h->alloc(&kb.g, sizeof(double2) * (m + 1)));
+  CK(h->alloc(&kb.y, sizeof(double2) * m));
+  CK(h->alloc(&kb.hcol, sizeof(double2) * (m + 2)));
+  CK(h->alloc(&kb.hp, sizeof(double2) * (m + 2)));
+  CK(h->alloc(&kb.part, sizeof(double2) * (size_t)kb.nblk * (m + 2)));
+  CK(h->alloc(&kb.st, sizeof(KState)));
+  CK(h->alloc(&h->rres, sizeof(double2) * kb.ldN));
+  CK(cudaMallocHost(&h->st_h, sizeof(KState)));
+  CK(cudaMemsetAsync(kb.V, 0, sizeof(double2) * kb.ldN * (m + 1), s));
+  CK(cudaMemsetAsync(kb.Z, 0, sizeof(double2) * kb.ldN * m, s));
+  CK(cudaStreamSynchronize(s));
+  return capture_iteration(h);
+}
+
+int helm_setup(double k, double h, int order, double shift, const helm_opts* opts, helm_t* out) {
+  if (!out) return HELM_EINVAL;
+  *out = nullptr;
+  helm_opts o;
+  helm_default_opts(&o);
+  if (opts) o = *opts;
+  if (!(h > 0) || !(k > 0) || !(shift >= 0) || !std::isfinite(k) || !std::isfinite(shift)) return HELM_EINVAL;
+  double nn = 1.0 / h;
+  int n = (int)std::lround(nn);
+  if (std::fabs(nn - n) > 1e-9 * nn || n < 4 || n % 2) return HELM_EINVAL;
+  if (!(o.dim == 2 || o.dim == 3) || !(order == 1 || order == 2) || (o.dim == 3 && order != 1)) return HELM_EINVAL;
+  if (o.nu < 1 || o.nu > 8 || o.restart < 1 || o.restart > 512 || o.maxit < 1 || !(o.tol > 0) ||
+      !(o.omega > 0) || !(o.precision == HELM_FP64 || o.precision == HELM_MIXED))
+    return HELM_EINVAL;
+  helm_ctx* c = new (std::nothrow) helm_ctx();
+  if (!c) return HELM_ENOMEM;
+  c->dim = o.dim;
+  c->order = order;
+  c->n = n;
+  c->k = k;
+  c->h = h;
+  c->shift = shift;
+  c->opts = o;
+  c->s = (cudaStream_t)o.stream;
+  int rc = setup_impl(c);
+  if (rc != HELM_OK) {
+    helm_destroy(c);
+    return rc;
+  }
+  *out = c;
+  return HELM_OK;
+}
+
+int helm_num_dofs(helm_t h, int64_t* n) {
+  if (!h || !n) return HELM_EINVAL;
+  *n = h->gf.N;
+  return HELM_OK;
+}
+
+int helm_num_coarse_dofs(helm_t h, int64_t* n) {
+  if (!h || !n) return HELM_EINVAL;
+  *n = h->gc.N;
+  return HELM_OK;
+}
+
+int helm_setup_ms(helm_t h, float* ms) {
+  if (!h || !ms) return HELM_EINVAL;
+  *ms = h->setup_ms;
+  return HELM_OK;
+}
+
+int helm_solve(helm_t h, const void* F, void* x, helm_result* res) {
+  if (!h || !F || !x) return HELM_EINVAL;
+  SolveTask t{h, (const double2*)F, (double2*)x, res};
+  int rc = solve_begin(t);
+  if (rc) return rc;
+  while (!solve_step(t, true)) {
+  }
+  return t.rc;
+}
+
+int helm_solve_host(helm_t h, const void* F_host, void* x_host, helm_result* res) {
+  if (!h || !F_host || !x_host) return HELM_EINVAL;
+  size_t bytes = sizeof(double2) * h->gf.N;
+  if (!h->Fdev) {
+    CK(h->alloc(&h->Fdev, bytes));
+    CK(h->alloc(&h->xdev, bytes));
+  }
+  CK(cudaMemcpyAsync(h->Fdev, F_host, bytes, cudaMemcpyHostToDevice, h->s));
+  int rc = helm_solve(h, h->Fdev, h->xdev, res);
+  if (rc) return rc;
+  CK(cudaMemcpyAsync(x_host, h->xdev, bytes, cudaMemcpyDeviceToHost, h->s));
+  CK(cudaStreamSynchronize(h->s));
+  return HELM_OK;
+}
+
+int helm_batch_solve(int count, const helm_t* hs, const void* const* F, void* const* x, helm_result* res) {
+  if (count < 0 || (count > 0 && (!hs || !F || !x))) return HELM_EINVAL;
+  for (int i = 0; i < count; ++i) {
+    if (!hs[i] || !F[i] || !x[i]) return HELM_EINVAL;
+    for (int j = 0; j < i; ++j)
+      if (hs[j] == hs[i]) return HELM_EINVAL;
+  }
+  std::vector<SolveTask> tasks(count);
+  int rc = HELM_OK;
+  for (int i = 0; i < count; ++i) {
+    tasks[i] = SolveTask{hs[i], (const double2*)F[i], (double2*)x[i], res ? &res[i] : nullptr};
+    int r = solve_begin(tasks[i]);
+    if (r) return r;
+  }
+  int left = count;
+  while (left > 0) {
+    left = 0;
+    for (auto& t : tasks) {
+      if (t.phase == SolveTask::DONE) continue;
+      if (!solve_step(t, false)) ++left;
+    }
+  }
+  for (auto& t : tasks)
+    if (t.rc && !rc) rc = t.rc;
+  return rc;
+}
+
+int helm_rhs_planewave(helm_t h, double theta, void* F_host) {
+  if (!h || !F_host) return HELM_EINVAL;
+  rhs_planewave(h->dim, h->order, h->n, h->k, theta, (double2*)F_host);
+  return HELM_OK;
+}
+
+int helm_rhs_gaussian(helm_t h, double sigma, double cx, double cy, double cz, void* F_host) {
+  if (!h || !F_host || !(sigma > 0)) return HELM_EINVAL;
+  double c[3] = {cx, cy, cz};
+  rhs_gaussian(h->dim, h->order, h->n, sigma, c, (double2*)F_host);
+  return HELM_OK;
+}
+
+int helm_apply(helm_t h, int which, const void* x, void* y) {
+  if (!h || !x || !y || (which != 0 && which != 1)) return HELM_EINVAL;
+  StencilView<double> A = which == 0 ? make_view<double>(h->gf, h->coefA0, nullptr)
+                                     : make_view<double>(h->gf, h->p64.coefAe, nullptr);
+  launch_apply<double, double2, double2>(A, vsel<const double2>((const double2*)x), vsel<double2>((double2*)y),
+                                         nullptr, h->s);
+  CK(cudaGetLastError());
+  CK(cudaStreamSynchronize(h->s));
+  return HELM_OK;
+}
+
+int helm_vcycle(helm_t h, const void* f, void* u) {
+  if (!h || !f || !u) return HELM_EINVAL;
+  CK(cudaMemsetAsync(h->err, 0, sizeof(int), h->s));
+  enqueue_vcycle_any(h, vsel<const double2>((const double2*)f), vsel<double2>((double2*)u), nullptr, h->s);
+  CK(cudaGetLastError());
+  CK(cudaStreamSynchronize(h->s));
+  return check_err(h);
+}
+
+int helm_coarse_solve(helm_t h, const void* rc_nat, void* uc_nat) {
+  if (!h || !rc_nat || !uc_nat) return HELM_EINVAL;
+  CK(cudaMemsetAsync(h->err, 0, sizeof(int), h->s));
+  if (h->opts.precision == HELM_MIXED) {
+    Prec<float>& p = h->p32;
+    launch_coarse_pack<double2, float2>(h->gc, h->L, (const double2*)rc_nat, p.rc, h->s);
+    launch_coarse_solve<float>(p.plan, p.Dinv, make_view<float>(h->gc, p.coefAc, nullptr), h->L, h->cpl, p.rc,
+                               p.uc, h->err, nullptr, h->s);
+    launch_coarse_unpack<float2, double2>(h->gc, h->L, p.uc, (double2*)uc_nat, h->s);
+  } else {
+    Prec<double>& p = h->p64;
+    launch_coarse_pack<double2, double2>(h->gc, h->L, (const double2*)rc_nat, p.rc, h->s);
+    launch_coarse_solve<double>(p.plan, p.Dinv, make_view<double>(h->gc, p.coefAc, nullptr), h->L,
+                                h->cpl, p.rc, p.uc, h->err, nullptr, h->s);
+    launch_coarse_unpack<double2, double2>(h->gc, h->L, p.uc, (double2*)uc_nat, h->s);
+  }
+  CK(cudaGetLastError());
+  CK(cudaStreamSynchronize(h->s));
+  return check_err(h);
+}
+
+int helm_set_profiling(helm_t h, int on) {
+  if (!h) return HELM_EINVAL;
+  h->prof.on = on != 0;
+  for (int i = 0; i < Profile::kPhases; ++i) {
+    h->prof.ms[i] = 0;
+    h->prof.calls[i] = 0;
+  }
+  return HELM_OK;
+}
+
+int helm_last_profile(helm_t h, int cap, const char** names, double* ms, int* calls, int* n) {
+  if (!h || !n) return HELM_EINVAL;
+  int k = std::min(cap, Profile::kPhases);
+  for (int i = 0; i < k; ++i) {
+    if (names) names[i] = kPhaseNames[i];
+    if (ms) ms[i] = h->prof.ms[i];
+    if (calls) calls[i] = h->prof.calls[i];
+  }
+  *n = Profile::kPhases;
+  return HELM_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,174 @@
+// Shared device/host definitions of the GB300 Helmholtz twogrid-FGMRES library.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <cstddef>
+#include <vector>
+
+#include "helm.h"
+
+namespace helm {
+
+// ----------------------------------------------------------------------------
+// Complex arithmetic on float2 / double2 (interleaved re, im).
+// ----------------------------------------------------------------------------
+template <typename T> struct C2;
+template <> struct C2<float> { using type = float2; };
+template <> struct C2<double> { using type = double2; };
+template <typename T> using c2 = typename C2<T>::type;
+
+__host__ __device__ inline float2 mk(float a, float b) { return make_float2(a, b); }
+__host__ __device__ inline double2 mk(double a, double b) { return make_double2(a, b); }
+
+template <typename V> __host__ __device__ inline V cadd(V a, V b) { return mk(a.x + b.x, a.y + b.y); }
+template <typename V> __host__ __device__ inline V csub(V a, V b) { return mk(a.x - b.x, a.y - b.y); }
+template <typename V> __host__ __device__ inline V cmul(V a, V b) {
+  return mk(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
+}
+// acc += a * b
+template <typename V> __host__ __device__ inline V cfma(V a, V b, V acc) {
+  acc.x = fma(a.x, b.x, acc.x);
+  acc.x = fma(-a.y, b.y, acc.x);
+  acc.y = fma(a.x, b.y, acc.y);
+  acc.y = fma(a.y, b.x, acc.y);
+  return acc;
+}
+// acc += conj(a) * b
+template <typename V> __host__ __device__ inline V cfma_conj(V a, V b, V acc) {
+  acc.x = fma(a.x, b.x, acc.x);
+  acc.x = fma(a.y, b.y, acc.x);
+  acc.y = fma(a.x, b.y, acc.y);
+  acc.y = fma(-a.y, b.x, acc.y);
+  return acc;
+}
+template <typename V> __host__ __device__ inline V cinv(V a) {
+  auto d = a.x * a.x + a.y * a.y;
+  return mk(a.x / d, -a.y / d);
+}
+
+#if defined(__CUDACC__)
+// conversions between precisions
+__device__ inline float2 cvt(double2 v, float2*) { return make_float2((float)v.x, (float)v.y); }
+__device__ inline double2 cvt(float2 v, double2*) { return make_double2(v.x, v.y); }
+__device__ inline float2 cvt(float2 v, float2*) { return v; }
+__device__ inline double2 cvt(double2 v, double2*) { return v; }
+template <typename To, typename From> __device__ inline To to(From v) { return cvt(v, (To*)nullptr); }
+#endif
+
+// ----------------------------------------------------------------------------
+// DoF grids and per-class stencils.
+//
+// A level's DoFs form a W^dim lattice (W = order*n + 1). Along each axis an
+// index a belongs to one of C1 = 2R + q classes: the R positions nearest each
+// boundary are their own classes, interior positions are classed by a mod q
+// (R = reach of the stencil in lattice units = order, q = lattice period =
+// order). The d-dimensional class is the mixed-radix number of the per-axis
+// classes. Every DoF of a class has the same stencil (constant k, uniform
+// mesh), with noff = (2R+1)^dim offsets in lexicographic box order.
+// ----------------------------------------------------------------------------
+constexpr int kMaxOff = 27;   // (2*1+1)^3 or (2*2+1)^2 = 25
+constexpr int kMaxCls = 36;   // (2*2+2)^2 = 36 or (2+1)^3 = 27
+constexpr int kMaxPW = 16;    // prolongation classes: (2q)^dim <= 16
+constexpr int kMaxPO = 9;     // prolongation offsets: (q+1)^dim <= 9
+
+struct GridDesc {
+  int dim;      // 2 or 3
+  int W;        // lattice points per side
+  int R;        // stencil reach (lattice units)
+  int q;        // lattice period
+  int C1;       // per-axis classes = 2R + q
+  int noff;     // (2R+1)^dim
+  int64_t N;    // W^dim
+};
+
+__host__ __device__ inline int axis_class(int a, int W, int R, int q) {
+  if (a < R) return a;
+  if (a >= W - R) return R + q + (a - (W - R));
+  return R + (a % q);
+}
+
+// Device view of one operator's stencil table: coef[cls * noff + o].
+template <typename T> struct StencilView {
+  const c2<T>* coef;   // [ncls * noff]
+  const c2<T>* wdinv;  // [ncls] omega / diag (only for smoothing operators), may be null
+  GridDesc g;
+  int off[kMaxOff];    // linear index offset of box point o
+  int dx[kMaxOff][3];  // per-axis offset of box point o
+};
+
+// Prolongation (canonical interpolation V_2h -> V_h) as per-class weights.
+// Fine index a on an axis: class a mod pf (pf = 2q), coarse anchor (a / pf) * q;
+// weights w[cls][o] to coarse points anchor + box offset o in {0..q}^dim.
+template <typename T> struct TransferView {
+  const T* w;          // [npc * npo]
+  GridDesc fine, coarse;
+  int pf;              // 2q
+  int npc, npo;        // (2q)^dim classes, (q+1)^dim offsets
+  int po[kMaxPO][3];   // per-axis offsets of box point o
+};
+
+// Coarse vectors are stored block-padded: block J (grid line / line pair /
+// plane) occupies [J*ldb, J*ldb + B), in-block index = lexicographic within
+// the block. nb blocks; fake padding rows of the last block are identity rows.
+struct CoarseLayout {
+  int nb;       // number of blocks
+  int B;        // DoFs per block (rows per block * W^(dim-1))
+  int ldb;      // padded row length / block stride of vectors (even, >= B)
+  int rows;     // lattice rows (or planes) per block = q
+  int plane;    // W^(dim-1)
+};
+
+#if defined(__CUDACC__)
+// ----------------------------------------------------------------------------
+// Bounded software grid barrier for cooperative launches.
+// state[0] = arrival counter, state[1] = generation. On timeout the kernel's
+// error word gets HELM_ETIMEOUT and the barrier returns false.
+// ----------------------------------------------------------------------------
+__device__ inline bool grid_barrier(unsigned* state, int* err, unsigned nblocks) {
+  __syncthreads();
+  __shared__ int ok_s;
+  if (threadIdx.x == 0) {
+    int ok = 1;
+    volatile unsigned* vgen = state + 1;
+    unsigned gen = *vgen;
+    __threadfence();
+    unsigned arrived = atomicAdd(state, 1u);
+    if (arrived == nblocks - 1) {
+      atomicExch(state, 0u);
+      __threadfence();
+      atomicAdd(state + 1, 1u);
+    } else {
+      long long spins = 0;
+      while (*vgen == gen) {
+        if (++spins > (1ll << 24)) { atomicExch(err, HELM_ETIMEOUT); ok = 0; break; }
+        if (*(volatile int*)err != 0) { ok = 0; break; }
+      }
+    }
+    __threadfence();
+    ok_s = ok;
+  }
+  __syncthreads();
+  return ok_s != 0;
+}
+#endif
+
+// ----------------------------------------------------------------------------
+// Host-side tables (computed in tables.cpp from element matrices).
+// ----------------------------------------------------------------------------
+struct HostTables {
+  GridDesc fine, coarse;
+  int ncls_f, ncls_c;
+  // real stencils (K, M, B) per class, unit coefficients, for the fine and coarse level
+  std::vector<double> Kf, Mf, Bf, Kc, Mc, Bc;   // [ncls * noff]
+  // prolongation weights
+  int pf, npc, npo;
+  std::vector<double> pw;                         // [npc * npo]
+};
+
+int build_tables(int dim, int order, int n, HostTables* t);
+void rhs_planewave(int dim, int order, int n, double k, double theta, double2* F);
+void rhs_gaussian(int dim, int order, int n, double sigma, const double* c, double2* F);
+
+}  // namespace helm

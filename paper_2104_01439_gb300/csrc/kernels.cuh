@@ -1,0 +1,127 @@
+// Launchers of the hot-path kernels (internal to the library).
+#pragma once
+
+#include "common.cuh"
+
+namespace helm {
+
+// Index selection from device state: a pointer into a strided array of vectors,
+// base + (*jsel + jadd) * stride, so that a captured graph can address the
+// current Krylov column without being re-captured.
+template <typename V> struct VecSel {
+  V* base;
+  int64_t stride;
+  const int* jsel;   // null -> index jadd
+  int jadd;
+  __device__ __forceinline__ V* ptr() const {
+    return base + (int64_t)((jsel ? *jsel : 0) + jadd) * stride;
+  }
+};
+template <typename V> inline VecSel<V> vsel(V* p) { return VecSel<V>{p, 0, nullptr, 0}; }
+
+// ---- fine level (stencil.cu) -----------------------------------------------
+// y = A x
+template <typename T, typename Vin, typename Vout>
+void launch_apply(const StencilView<T>& A, VecSel<const Vin> x, VecSel<Vout> y, const int* active,
+                  cudaStream_t s);
+// r = f - A u
+template <typename T, typename Vf, typename Vr>
+void launch_residual(const StencilView<T>& A, VecSel<const Vf> f, const c2<T>* u, Vr* r,
+                     const int* active, cudaStream_t s);
+// u_out = omega D^-1 f (+ one more sweep if two_steps): the first nu <= 2 sweeps from u = 0.
+// If fcopy != null, f is also stored in precision T there.
+template <typename T, typename Vf>
+void launch_jacobi_from_zero(const StencilView<T>& A, VecSel<const Vf> f, c2<T>* u_out,
+                             c2<T>* fcopy, bool two_steps, const int* active, cudaStream_t s);
+// out = u + omega D^-1 (f - A u)
+template <typename T, typename Vf, typename Vout>
+void launch_jacobi(const StencilView<T>& A, VecSel<const Vf> f, const c2<T>* u, VecSel<Vout> out,
+                   const int* active, cudaStream_t s);
+// u += P uc  (uc in block-padded coarse layout)
+template <typename T>
+void launch_prolong_add(const TransferView<T>& P, const CoarseLayout& L, const c2<T>* uc, c2<T>* u,
+                        const int* active, cudaStream_t s);
+// rc = P^T r (rc in block-padded coarse layout, padding zeroed)
+template <typename T>
+void launch_restrict(const TransferView<T>& P, const CoarseLayout& L, const c2<T>* r, c2<T>* rc,
+                     const int* active, cudaStream_t s);
+// padded <-> natural coarse ordering (with precision conversion)
+template <typename Vin, typename Vout>
+void launch_coarse_pack(const GridDesc& gc, const CoarseLayout& L, const Vin* nat, Vout* pad,
+                        cudaStream_t s);
+template <typename Vin, typename Vout>
+void launch_coarse_unpack(const GridDesc& gc, const CoarseLayout& L, const Vin* pad, Vout* nat,
+                          cudaStream_t s);
+
+// ---- coarse level (coarse.cu) ----------------------------------------------
+struct CoarsePlan {
+  int CS;       // cluster size
+  int R;        // rows per CTA
+  int CW;       // columns per pipeline chunk (even)
+  int nchunk;   // chunks per step
+  int S;        // pipeline stages
+  size_t smem;  // dynamic shared memory bytes
+  int threads;
+};
+template <typename T>
+int plan_coarse_solve(const CoarseLayout& L, const GridDesc& gc, CoarsePlan* plan);
+template <typename T>
+void launch_coarse_solve(const CoarsePlan& plan, const c2<T>* Dinv, const StencilView<T>& Ac,
+                         const CoarseLayout& L, const int* cpl, const c2<T>* rc, c2<T>* uc, int* err,
+                         const int* active, cudaStream_t s);
+// host-built coupling lists of the coarse blocks (uploaded once per handle)
+int coupling_max(const GridDesc& g);
+void coupling_lists(const GridDesc& g, const CoarseLayout& L, std::vector<int>& out);
+// Block-Thomas factorisation: Dinv[J] = (A_JJ - A_J,J-1 Dinv[J-1] A_J-1,J)^{-1}
+template <typename T>
+int launch_coarse_factor(c2<T>* Dinv, c2<T>* tmp, c2<T>* piv, unsigned* bar, int* err,
+                         const StencilView<T>& Ac, const CoarseLayout& L, int nsm, cudaStream_t s);
+void launch_convert_factor(const double2* src, float2* dst, size_t n, cudaStream_t s);
+
+// ---- Krylov (krylov.cu) ----------------------------------------------------
+struct KState {
+  int j;           // Arnoldi column being built in this cycle
+  int active;      // 1 while the cycle runs
+  int total;       // total Arnoldi steps
+  int converged;   // Givens estimate <= tol
+  int breakdown;   // h_{j+1,j} == 0
+  int reorth;      // DGKS: second CGS pass needed
+  int m, maxit;
+  int nonfinite;
+  int pad_;
+  double nF;       // ||F||
+  double beta;     // cycle's initial residual norm
+  double tol;
+  double est;      // |g_{j+1}| / ||F||
+  double wn0;      // ||w|| before orthogonalisation
+  double wn;       // ||w|| after
+  double relres;   // true relative residual at cycle end
+};
+
+struct KrylovBufs {
+  double2* V;      // (m+1) x ldN
+  double2* Z;      // m x ldN
+  int64_t ldN;
+  int64_t N;
+  double2* H;      // (m+1) x m column-major, rotated (upper triangular R)
+  double* cs;      // m
+  double2* sn;     // m
+  double2* g;      // m+1
+  double2* y;      // m
+  double2* hcol;   // m+2 : accumulated h of the current column
+  double2* hp;     // m+1 : projection coefficients of the current CGS pass
+  double2* part;   // nblk x (m+2) partial sums
+  int nblk;
+  KState* st;
+};
+
+void launch_cgs_pass(const KrylovBufs& kb, bool second, cudaStream_t s);   // dots+reduce+update+norm
+void launch_normalize(const KrylovBufs& kb, cudaStream_t s);
+void launch_givens(const KrylovBufs& kb, cudaStream_t s);
+void launch_cycle_start(const KrylovBufs& kb, const double2* r, cudaStream_t s);   // V0 = r / ||r||
+void launch_backsolve(const KrylovBufs& kb, cudaStream_t s);
+void launch_update_x(const KrylovBufs& kb, double2* x, cudaStream_t s);
+// ||v||^2 into st field (which: 0 = nF (and beta), 1 = relres using nF)
+void launch_norm(const KrylovBufs& kb, const double2* v, int which, cudaStream_t s);
+
+}  // namespace helm

@@ -1,0 +1,367 @@
+// Flexible GMRES (Saad 1993; Sec. 4: A0 P^{-1} (P u) = F) in complex128.
+//
+// Arnoldi orthogonalisation is classical Gram-Schmidt with one conditional
+// second pass (DGKS criterion ||w_after|| < ||w_before|| / sqrt(2)); inner
+// products are Hermitian, <a, b> = sum conj(a_i) b_i. Each pass is a
+// grid-wide dot-product kernel (8 basis vectors per sweep over w, warp-shuffle
+// + shared-memory block reductions into per-block partials), a one-block
+// deterministic reduction, and an update kernel that also accumulates ||w||^2.
+// Complex Givens rotations (c real, s complex), the residual estimate
+// |g_{j+1}| and the convergence test run on the device in one thread, so a
+// captured iteration never returns to the host. All kernels read the Arnoldi
+// index j and the 'active' flag from device state.
+#include "kernels.cuh"
+
+namespace helm {
+namespace {
+
+constexpr int kT = 256;
+constexpr int kG = 8;   // basis vectors per sweep
+
+__device__ __forceinline__ double2 wsum(double2 v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    v.x += __shfl_xor_sync(0xffffffffu, v.x, o);
+    v.y += __shfl_xor_sync(0xffffffffu, v.y, o);
+  }
+  return v;
+}
+__device__ __forceinline__ double wsum(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+// partial dots of w = V[j+1] against V[0..j] (and ||w||^2 in the first pass)
+__global__ void __launch_bounds__(kT) k_dots(KrylovBufs kb, int second) {
+  KState* st = kb.st;
+  if (!st->active || (second && !st->reorth)) return;
+  const int j = st->j, m = st->m;
+  const int64_t N = kb.N, ld = kb.ldN;
+  const double2* w = kb.V + (int64_t)(j + 1) * ld;
+  __shared__ double2 red[kT / 32][kG];
+  __shared__ double rn[kT / 32];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  double2* part = kb.part + (int64_t)blockIdx.x * (m + 2);
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  if (!second) {
+    double s = 0.0;
+    for (int64_t n = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; n < N; n += stride) {
+      double2 v = w[n];
+      s = fma(v.x, v.x, fma(v.y, v.y, s));
+    }
+    s = wsum(s);
+    if (lane == 0) rn[warp] = s;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      double t = 0.0;
+      for (int i = 0; i < kT / 32; ++i) t += rn[i];
+      part[m + 1] = make_double2(t, 0.0);
+    }
+  }
+  for (int i0 = 0; i0 <= j; i0 += kG) {
+    const int ng = min(kG, j + 1 - i0);
+    double2 acc[kG];
+#pragma unroll
+    for (int t = 0; t < kG; ++t) acc[t] = make_double2(0.0, 0.0);
+    for (int64_t n = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; n < N; n += stride) {
+      double2 wn = w[n];
+#pragma unroll
+      for (int t = 0; t < kG; ++t)
+        if (t < ng) acc[t] = cfma_conj(kb.V[(int64_t)(i0 + t) * ld + n], wn, acc[t]);
+    }
+#pragma unroll
+    for (int t = 0; t < kG; ++t) {
+      double2 v = wsum(acc[t]);
+      if (lane == 0) red[warp][t] = v;
+    }
+    __syncthreads();
+    if (threadIdx.x < ng) {
+      double2 t2 = make_double2(0.0, 0.0);
+      for (int wi = 0; wi < kT / 32; ++wi) t2 = cadd(t2, red[wi][threadIdx.x]);
+      part[i0 + threadIdx.x] = t2;
+    }
+    __syncthreads();
+  }
+}
+
+// Deterministic block reduction of the per-block partials: warp w sums entry
+// i (lanes stride over the blocks, then a fixed shuffle tree).
+__device__ __forceinline__ double2 sum_partials(const KrylovBufs& kb, int m, int i, int lane) {
+  double2 s = make_double2(0.0, 0.0);
+  for (int b = lane; b < kb.nblk; b += 32) s = cadd(s, kb.part[(int64_t)b * (m + 2) + i]);
+  return wsum(s);
+}
+
+// h = sum of partials; hp = this pass's h, hcol accumulates over the passes.
+__global__ void __launch_bounds__(kT) k_reduce_h(KrylovBufs kb, double2* hp, int second) {
+  KState* st = kb.st;
+  if (!st->active || (second && !st->reorth)) return;
+  const int j = st->j, m = st->m;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  for (int i = warp; i <= j + 1; i += nw) {
+    int idx = i <= j ? i : m + 1;                 // last slot: ||w||^2 (first pass)
+    if (i == j + 1 && second) break;
+    double2 s2 = sum_partials(kb, m, idx, lane);
+    if (lane == 0) {
+      if (i <= j) {
+        hp[i] = s2;
+        kb.hcol[i] = second ? cadd(kb.hcol[i], s2) : s2;
+      } else {
+        st->wn0 = sqrt(s2.x);
+      }
+    }
+  }
+}
+
+// w -= sum_i hp[i] V[i];  partial ||w||^2
+__global__ void __launch_bounds__(kT) k_update(KrylovBufs kb, const double2* hp, int second) {
+  KState* st = kb.st;
+  if (!st->active || (second && !st->reorth)) return;
+  const int j = st->j, m = st->m;
+  const int64_t N = kb.N, ld = kb.ldN;
+  double2* w = kb.V + (int64_t)(j + 1) * ld;
+  extern __shared__ double2 hs[];
+  for (int i = threadIdx.x; i <= j; i += blockDim.x) hs[i] = hp[i];
+  __syncthreads();
+  double s = 0.0;
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t n = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; n < N; n += stride) {
+    double2 a = w[n];
+    for (int i = 0; i <= j; ++i) {
+      double2 v = kb.V[(int64_t)i * ld + n];
+      double2 h = hs[i];
+      a.x = fma(-h.x, v.x, a.x);
+      a.x = fma(h.y, v.y, a.x);
+      a.y = fma(-h.x, v.y, a.y);
+      a.y = fma(-h.y, v.x, a.y);
+    }
+    w[n] = a;
+    s = fma(a.x, a.x, fma(a.y, a.y, s));
+  }
+  __shared__ double rn[kT / 32];
+  s = wsum(s);
+  if ((threadIdx.x & 31) == 0) rn[threadIdx.x >> 5] = s;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double t = 0.0;
+    for (int i = 0; i < kT / 32; ++i) t += rn[i];
+    kb.part[(int64_t)blockIdx.x * (m + 2) + m + 1] = make_double2(t, 0.0);
+  }
+}
+
+__global__ void k_reduce_norm(KrylovBufs kb, int second) {
+  KState* st = kb.st;
+  if (!st->active || (second && !st->reorth)) return;
+  const int m = st->m;
+  double2 s2 = sum_partials(kb, m, m + 1, threadIdx.x & 31);
+  if (threadIdx.x != 0) return;
+  double wn = sqrt(s2.x);
+  st->wn = wn;
+  if (!second) st->reorth = (wn < 0.70710678118654752 * st->wn0) ? 1 : 0;
+}
+
+__global__ void __launch_bounds__(kT) k_normalize(KrylovBufs kb) {
+  KState* st = kb.st;
+  if (!st->active) return;
+  const double wn = st->wn;
+  if (!(wn > 1e-14 * st->beta) || !isfinite(wn)) return;   // breakdown: handled by k_givens
+  const double inv = 1.0 / wn;
+  double2* w = kb.V + (int64_t)(st->j + 1) * kb.ldN;
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t n = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; n < kb.N; n += stride) {
+    double2 a = w[n];
+    w[n] = make_double2(a.x * inv, a.y * inv);
+  }
+}
+
+__global__ void __launch_bounds__(kT) k_givens(KrylovBufs kb) {
+  KState* st = kb.st;
+  if (!st->active) return;
+  const int j = st->j, m = st->m;
+  __shared__ double2 col[513];
+  __shared__ double2 sn[512];
+  __shared__ double cs[512];
+  for (int i = threadIdx.x; i <= j; i += blockDim.x) {
+    col[i] = kb.hcol[i];
+    if (i < j) {
+      cs[i] = kb.cs[i];
+      sn[i] = kb.sn[i];
+    }
+  }
+  __syncthreads();
+  const double wn = st->wn;
+  if (threadIdx.x == 0) {
+    col[j + 1] = make_double2(wn, 0.0);
+    for (int i = 0; i < j; ++i) {   // previous rotations
+      double c = cs[i];
+      double2 sv = sn[i], a = col[i], b = col[i + 1];
+      double2 sb = cmul(sv, b);
+      double2 nsa = cmul(make_double2(-sv.x, sv.y), a);   // -conj(s) a
+      col[i] = make_double2(c * a.x + sb.x, c * a.y + sb.y);
+      col[i + 1] = make_double2(nsa.x + c * b.x, nsa.y + c * b.y);
+    }
+    // new rotation zeroing col[j+1]: [c s; -conj(s) c] [a; b] = [r; 0]
+    double2 a = col[j], b = col[j + 1];
+    double aa = hypot(a.x, a.y), bb = hypot(b.x, b.y);
+    double c;
+    double2 sv, r;
+    if (bb == 0.0) {
+      c = 1.0; sv = make_double2(0.0, 0.0); r = a;
+    } else if (aa == 0.0) {
+      c = 0.0; sv = make_double2(1.0, 0.0); r = b;
+    } else {
+      double nu = hypot(aa, bb);
+      double2 ph = make_double2(a.x / aa, a.y / aa);
+      c = aa / nu;
+      sv = cmul(ph, make_double2(b.x / nu, -b.y / nu));
+      r = make_double2(ph.x * nu, ph.y * nu);
+    }
+    kb.cs[j] = c;
+    kb.sn[j] = sv;
+    col[j] = r;
+    col[j + 1] = make_double2(0.0, 0.0);
+    double2 gj = kb.g[j];
+    double2 gj1 = cmul(make_double2(-sv.x, sv.y), gj);
+    kb.g[j + 1] = gj1;
+    kb.g[j] = make_double2(c * gj.x, c * gj.y);
+    double est = hypot(gj1.x, gj1.y) / st->nF;
+    st->est = est;
+    st->j = j + 1;
+    st->total += 1;
+    if (!isfinite(est) || !isfinite(wn)) st->nonfinite = 1;
+    if (!(wn > 1e-14 * st->beta)) st->breakdown = 1;
+    if (est <= st->tol) st->converged = 1;
+    if (st->converged || st->breakdown || st->nonfinite || st->j >= m || st->total >= st->maxit) st->active = 0;
+  }
+  __syncthreads();
+  double2* Hc = kb.H + (int64_t)j * (m + 1);
+  for (int i = threadIdx.x; i <= j + 1; i += blockDim.x) Hc[i] = col[i];
+}
+
+// ||v||^2 partials / final
+__global__ void __launch_bounds__(kT) k_norm_part(KrylovBufs kb, const double2* v) {
+  double s = 0.0;
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t n = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; n < kb.N; n += stride) {
+    double2 a = v[n];
+    s = fma(a.x, a.x, fma(a.y, a.y, s));
+  }
+  __shared__ double rn[kT / 32];
+  s = wsum(s);
+  if ((threadIdx.x & 31) == 0) rn[threadIdx.x >> 5] = s;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double t = 0.0;
+    for (int i = 0; i < kT / 32; ++i) t += rn[i];
+    kb.part[(int64_t)blockIdx.x * (kb.st->m + 2) + kb.st->m + 1] = make_double2(t, 0.0);
+  }
+}
+__global__ void k_norm_fin(KrylovBufs kb, int which) {
+  KState* st = kb.st;
+  const int m = st->m;
+  double2 s2 = sum_partials(kb, m, m + 1, threadIdx.x & 31);
+  if (threadIdx.x != 0) return;
+  double nrm = sqrt(s2.x);
+  if (which == 0) {
+    st->nF = nrm;
+    st->beta = nrm;
+  } else {
+    st->beta = nrm;
+    st->relres = st->nF > 0.0 ? nrm / st->nF : 0.0;
+    if (!isfinite(nrm)) st->nonfinite = 1;
+  }
+}
+
+// V0 = r / beta, g = (beta, 0, ...), new cycle
+__global__ void __launch_bounds__(kT) k_cycle_start(KrylovBufs kb, const double2* r) {
+  KState* st = kb.st;
+  const double beta = st->beta;
+  const bool ok = beta > 0.0 && isfinite(beta);
+  const double inv = ok ? 1.0 / beta : 0.0;
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t n = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; n < kb.N; n += stride) {
+    double2 a = r[n];
+    kb.V[n] = make_double2(a.x * inv, a.y * inv);
+  }
+  if (blockIdx.x == 0) {
+    for (int i = threadIdx.x; i <= st->m; i += blockDim.x) kb.g[i] = make_double2(i == 0 ? beta : 0.0, 0.0);
+    if (threadIdx.x == 0) {
+      st->j = 0;
+      st->active = ok ? 1 : 0;
+      st->converged = 0;
+      st->breakdown = 0;
+      st->reorth = 0;
+      if (!isfinite(beta)) st->nonfinite = 1;
+    }
+  }
+}
+
+// y = R^{-1} g over the cycle's j columns (R = rotated H, upper triangular),
+// column-oriented: after y_i is known, every thread updates the rows above it.
+__global__ void __launch_bounds__(kT) k_backsolve(KrylovBufs kb) {
+  KState* st = kb.st;
+  const int jj = st->j, m = st->m;
+  __shared__ double2 rhs[512];
+  __shared__ double2 yi_s;
+  for (int i = threadIdx.x; i < jj; i += blockDim.x) rhs[i] = kb.g[i];
+  __syncthreads();
+  for (int i = jj - 1; i >= 0; --i) {
+    const double2* Ri = kb.H + (int64_t)i * (m + 1);   // column i
+    if (threadIdx.x == 0) {
+      double2 yi = cmul(rhs[i], cinv(Ri[i]));
+      kb.y[i] = yi;
+      yi_s = yi;
+    }
+    __syncthreads();
+    double2 yi = yi_s;
+    for (int l = threadIdx.x; l < i; l += blockDim.x) rhs[l] = csub(rhs[l], cmul(Ri[l], yi));
+    __syncthreads();
+  }
+}
+
+// x += sum_i y_i Z[i]
+__global__ void __launch_bounds__(kT) k_update_x(KrylovBufs kb, double2* x) {
+  KState* st = kb.st;
+  const int jj = st->j;
+  extern __shared__ double2 ys[];
+  for (int i = threadIdx.x; i < jj; i += blockDim.x) ys[i] = kb.y[i];
+  __syncthreads();
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t n = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; n < kb.N; n += stride) {
+    double2 a = x[n];
+    for (int i = 0; i < jj; ++i) a = cfma(ys[i], kb.Z[(int64_t)i * kb.ldN + n], a);
+    x[n] = a;
+  }
+}
+
+}  // namespace
+
+void launch_cgs_pass(const KrylovBufs& kb, bool second, cudaStream_t s) {
+  int sec = second ? 1 : 0;
+  k_dots<<<kb.nblk, kT, 0, s>>>(kb, sec);
+  k_reduce_h<<<1, kT, 0, s>>>(kb, kb.hp, sec);
+  k_update<<<kb.nblk, kT, sizeof(double2) * 513, s>>>(kb, kb.hp, sec);
+  k_reduce_norm<<<1, 32, 0, s>>>(kb, sec);
+}
+
+void launch_normalize(const KrylovBufs& kb, cudaStream_t s) { k_normalize<<<kb.nblk, kT, 0, s>>>(kb); }
+
+void launch_givens(const KrylovBufs& kb, cudaStream_t s) { k_givens<<<1, kT, 0, s>>>(kb); }
+
+void launch_cycle_start(const KrylovBufs& kb, const double2* r, cudaStream_t s) {
+  k_cycle_start<<<kb.nblk, kT, 0, s>>>(kb, r);
+}
+
+void launch_backsolve(const KrylovBufs& kb, cudaStream_t s) { k_backsolve<<<1, kT, 0, s>>>(kb); }
+
+void launch_update_x(const KrylovBufs& kb, double2* x, cudaStream_t s) {
+  k_update_x<<<kb.nblk, kT, sizeof(double2) * 512, s>>>(kb, x);
+}
+
+void launch_norm(const KrylovBufs& kb, const double2* v, int which, cudaStream_t s) {
+  k_norm_part<<<kb.nblk, kT, 0, s>>>(kb, v);
+  k_norm_fin<<<1, 32, 0, s>>>(kb, which);
+}
+
+}  // namespace helm

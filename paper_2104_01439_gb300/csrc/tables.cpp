@@ -1,0 +1,575 @@
+// Host-side setup of the matrix-free operators: per-class stencil
+// coefficients of K, M, B (Sec. 2, eq. discreteproblem), prolongation weights
+// of the canonical interpolation V_2h -> V_h (Sec. 4), and load vectors.
+//
+// Element integrals use Gauss-Legendre quadrature in collapsed (Duffy)
+// coordinates on the reference simplex, exact for the polynomial degrees met
+// here (<= 4 for the P2 mass matrix). The stencil of each DoF class is read
+// off a small reference mesh that contains every class at least once.
+#include <algorithm>
+#include <array>
+#include <cmath>
+#include <cstring>
+#include <map>
+#include <vector>
+
+#include "common.cuh"
+
+namespace helm {
+namespace {
+
+// Gauss-Legendre nodes/weights on [0,1] by Newton's method on P_n.
+void gauss_legendre01(int n, std::vector<double>& x, std::vector<double>& w) {
+  x.assign(n, 0.0);
+  w.assign(n, 0.0);
+  for (int i = 0; i < n; ++i) {
+    double t = std::cos(M_PI * (i + 0.75) / (n + 0.5));
+    for (int it = 0; it < 100; ++it) {
+      double p0 = 1.0, p1 = t;
+      for (int k = 2; k <= n; ++k) {
+        double p2 = ((2.0 * k - 1.0) * t * p1 - (k - 1.0) * p0) / k;
+        p0 = p1;
+        p1 = p2;
+      }
+      double dp = n * (t * p1 - p0) / (t * t - 1.0);
+      double dt = p1 / dp;
+      t -= dt;
+      if (std::fabs(dt) < 1e-16) break;
+    }
+    double p0 = 1.0, p1 = t;
+    for (int k = 2; k <= n; ++k) {
+      double p2 = ((2.0 * k - 1.0) * t * p1 - (k - 1.0) * p0) / k;
+      p0 = p1;
+      p1 = p2;
+    }
+    double dp = n * (t * p1 - p0) / (t * t - 1.0);
+    x[i] = 0.5 * (t + 1.0);
+    w[i] = 1.0 / ((1.0 - t * t) * dp * dp);   // = 2/((1-t^2)P'^2) scaled by 1/2
+  }
+}
+
+// Quadrature on the reference d-simplex: barycentric points, weights summing to 1.
+struct Quad {
+  std::vector<std::array<double, 4>> lam;
+  std::vector<double> w;
+};
+
+Quad simplex_quadrature(int d) {
+  std::vector<double> x, w;
+  gauss_legendre01(4, x, w);
+  Quad q;
+  if (d == 1) {
+    for (int i = 0; i < 4; ++i) {
+      q.lam.push_back({1.0 - x[i], x[i], 0.0, 0.0});
+      q.w.push_back(w[i]);
+    }
+  } else if (d == 2) {
+    for (int i = 0; i < 4; ++i)
+      for (int j = 0; j < 4; ++j) {
+        double xi = x[i], eta = x[j] * (1.0 - x[i]);
+        q.lam.push_back({1.0 - xi - eta, xi, eta, 0.0});
+        q.w.push_back(2.0 * w[i] * w[j] * (1.0 - x[i]));
+      }
+  } else {
+    for (int i = 0; i < 4; ++i)
+      for (int j = 0; j < 4; ++j)
+        for (int k = 0; k < 4; ++k) {
+          double xi = x[i], eta = x[j] * (1.0 - x[i]), zeta = x[k] * (1.0 - x[i]) * (1.0 - x[j]);
+          q.lam.push_back({1.0 - xi - eta - zeta, xi, eta, zeta});
+          q.w.push_back(6.0 * w[i] * w[j] * w[k] * (1.0 - x[i]) * (1.0 - x[i]) * (1.0 - x[j]));
+        }
+  }
+  return q;
+}
+
+// Lagrange basis on a d-simplex: P1 = lam_i; P2 = vertices lam_i(2lam_i-1) then
+// edge midpoints 4 lam_a lam_b over pairs (a<b) in lexicographic pair order.
+int nbasis(int d, int order) { return order == 1 ? d + 1 : (d + 1) * (d + 2) / 2; }
+
+void edge_pairs(int d, std::vector<std::pair<int, int>>& e) {
+  e.clear();
+  for (int a = 0; a <= d; ++a)
+    for (int b = a + 1; b <= d; ++b) e.push_back({a, b});
+}
+
+double basis_val(int d, int order, int i, const double* lam) {
+  if (order == 1) return lam[i];
+  if (i <= d) return lam[i] * (2.0 * lam[i] - 1.0);
+  std::vector<std::pair<int, int>> e;
+  edge_pairs(d, e);
+  auto ab = e[i - d - 1];
+  return 4.0 * lam[ab.first] * lam[ab.second];
+}
+
+// d phi_i / d lam_a
+double basis_dlam(int d, int order, int i, int a, const double* lam) {
+  if (order == 1) return i == a ? 1.0 : 0.0;
+  if (i <= d) return i == a ? 4.0 * lam[i] - 1.0 : 0.0;
+  std::vector<std::pair<int, int>> e;
+  edge_pairs(d, e);
+  auto ab = e[i - d - 1];
+  if (a == ab.first) return 4.0 * lam[ab.second];
+  if (a == ab.second) return 4.0 * lam[ab.first];
+  return 0.0;
+}
+
+// Barycentric node coordinates of local DoF i (vertex or edge midpoint).
+std::array<double, 4> basis_node(int d, int order, int i) {
+  std::array<double, 4> l = {0, 0, 0, 0};
+  if (order == 1 || i <= d) {
+    l[i] = 1.0;
+    return l;
+  }
+  std::vector<std::pair<int, int>> e;
+  edge_pairs(d, e);
+  auto ab = e[i - d - 1];
+  l[ab.first] = 0.5;
+  l[ab.second] = 0.5;
+  return l;
+}
+
+double det3(const double m[3][3]) {
+  return m[0][0] * (m[1][1] * m[2][2] - m[1][2] * m[2][1]) -
+         m[0][1] * (m[1][0] * m[2][2] - m[1][2] * m[2][0]) +
+         m[0][2] * (m[1][0] * m[2][1] - m[1][1] * m[2][0]);
+}
+
+// Element stiffness/mass on a full-dimensional simplex with vertices v[d+1][d].
+void element_km(int d, int order, const double v[4][3], std::vector<double>& K,
+                std::vector<double>& M) {
+  int nb = nbasis(d, order);
+  // Jacobian J = [v1-v0, ..., vd-v0] (columns); grad lam_a for a >= 1 are rows of J^{-1}
+  double J[3][3] = {{1, 0, 0}, {0, 1, 0}, {0, 0, 1}};
+  for (int c = 0; c < d; ++c)
+    for (int r = 0; r < d; ++r) J[r][c] = v[c + 1][r] - v[0][r];
+  double det = d == 2 ? J[0][0] * J[1][1] - J[0][1] * J[1][0] : det3(J);
+  double meas = std::fabs(det) / (d == 2 ? 2.0 : 6.0);
+  double Ji[3][3] = {{0}};
+  if (d == 2) {
+    Ji[0][0] = J[1][1] / det; Ji[0][1] = -J[0][1] / det;
+    Ji[1][0] = -J[1][0] / det; Ji[1][1] = J[0][0] / det;
+  } else {
+    for (int r = 0; r < 3; ++r)
+      for (int c = 0; c < 3; ++c) {
+        int r1 = (c + 1) % 3, r2 = (c + 2) % 3, c1 = (r + 1) % 3, c2 = (r + 2) % 3;
+        Ji[r][c] = (J[r1][c1] * J[r2][c2] - J[r1][c2] * J[r2][c1]) / det;
+      }
+  }
+  double G[4][3] = {{0}};   // grad lam_a
+  for (int a = 1; a <= d; ++a)
+    for (int x = 0; x < d; ++x) G[a][x] = Ji[a - 1][x];
+  for (int x = 0; x < d; ++x) {
+    double s = 0;
+    for (int a = 1; a <= d; ++a) s += G[a][x];
+    G[0][x] = -s;
+  }
+  Quad q = simplex_quadrature(d);
+  K.assign(nb * nb, 0.0);
+  M.assign(nb * nb, 0.0);
+  std::vector<double> phi(nb), grad(nb * 3);
+  for (size_t p = 0; p < q.w.size(); ++p) {
+    const double* lam = q.lam[p].data();
+    for (int i = 0; i < nb; ++i) {
+      phi[i] = basis_val(d, order, i, lam);
+      for (int x = 0; x < 3; ++x) grad[i * 3 + x] = 0.0;
+      for (int a = 0; a <= d; ++a) {
+        double da = basis_dlam(d, order, i, a, lam);
+        for (int x = 0; x < d; ++x) grad[i * 3 + x] += da * G[a][x];
+      }
+    }
+    double wq = q.w[p] * meas;
+    for (int i = 0; i < nb; ++i)
+      for (int j = 0; j < nb; ++j) {
+        double gg = 0;
+        for (int x = 0; x < d; ++x) gg += grad[i * 3 + x] * grad[j * 3 + x];
+        K[i * nb + j] += wq * gg;
+        M[i * nb + j] += wq * phi[i] * phi[j];
+      }
+  }
+}
+
+// Mass matrix of a (d-1)-facet with vertices v[d][3] embedded in R^d.
+void facet_mass(int d, int order, const double v[4][3], std::vector<double>& B) {
+  int fd = d - 1;
+  int nb = nbasis(fd, order);
+  double meas;
+  if (fd == 1) {
+    double dx = v[1][0] - v[0][0], dy = v[1][1] - v[0][1];
+    meas = std::sqrt(dx * dx + dy * dy);
+  } else {
+    double a[3], b[3];
+    for (int x = 0; x < 3; ++x) { a[x] = v[1][x] - v[0][x]; b[x] = v[2][x] - v[0][x]; }
+    double c0 = a[1] * b[2] - a[2] * b[1], c1 = a[2] * b[0] - a[0] * b[2], c2 = a[0] * b[1] - a[1] * b[0];
+    meas = 0.5 * std::sqrt(c0 * c0 + c1 * c1 + c2 * c2);
+  }
+  Quad q = simplex_quadrature(fd);
+  B.assign(nb * nb, 0.0);
+  for (size_t p = 0; p < q.w.size(); ++p) {
+    const double* lam = q.lam[p].data();
+    for (int i = 0; i < nb; ++i)
+      for (int j = 0; j < nb; ++j)
+        B[i * nb + j] += q.w[p] * meas * basis_val(fd, order, i, lam) * basis_val(fd, order, j, lam);
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Structured mesh enumeration: cells of n^d, split into simplices.
+// 2D: {(0,0),(1,0),(1,1)} and {(0,0),(1,1),(0,1)}; 3D: Kuhn, one tetrahedron
+// per axis permutation along the path (0,0,0) -> ... -> (1,1,1).
+// ---------------------------------------------------------------------------
+void cell_simplices(int d, std::vector<std::array<std::array<int, 3>, 4>>& out) {
+  out.clear();
+  if (d == 2) {
+    out.push_back({{{0, 0, 0}, {1, 0, 0}, {1, 1, 0}, {0, 0, 0}}});
+    out.push_back({{{0, 0, 0}, {1, 1, 0}, {0, 1, 0}, {0, 0, 0}}});
+    return;
+  }
+  int perm[3] = {0, 1, 2};
+  std::sort(perm, perm + 3);
+  do {
+    std::array<std::array<int, 3>, 4> s;
+    std::array<int, 3> p = {0, 0, 0};
+    s[0] = p;
+    for (int k = 0; k < 3; ++k) {
+      p[perm[k]] += 1;
+      s[k + 1] = p;
+    }
+    out.push_back(s);
+  } while (std::next_permutation(perm, perm + 3));
+}
+
+struct SMesh {
+  int d, order, n, W;
+  double h;
+  int64_t idx(const int* c) const {
+    int64_t s = 0;
+    for (int ax = d - 1; ax >= 0; --ax) s = s * W + c[ax];
+    return s;
+  }
+};
+
+// Calls fn(local DoF lattice coords [nb][3], vertex coords [d+1][3]) per element.
+template <typename Fn> void for_each_element(const SMesh& m, Fn fn) {
+  std::vector<std::array<std::array<int, 3>, 4>> simp;
+  cell_simplices(m.d, simp);
+  int nb = nbasis(m.d, m.order);
+  int nc3 = m.d == 3 ? m.n : 1;
+  std::vector<std::array<int, 3>> loc(nb);
+  double vx[4][3];
+  for (int cz = 0; cz < nc3; ++cz)
+    for (int cy = 0; cy < m.n; ++cy)
+      for (int cx = 0; cx < m.n; ++cx)
+        for (auto& s : simp) {
+          int cell[3] = {cx, cy, cz};
+          for (int i = 0; i < nb; ++i) {
+            auto l = basis_node(m.d, m.order, i);
+            for (int ax = 0; ax < 3; ++ax) {
+              double p = 0;
+              for (int a = 0; a <= m.d; ++a) p += l[a] * (cell[ax] + s[a][ax]) * m.order;
+              loc[i][ax] = (int)std::lround(p);
+            }
+          }
+          for (int a = 0; a <= m.d; ++a)
+            for (int ax = 0; ax < 3; ++ax) vx[a][ax] = (cell[ax] + s[a][ax]) * m.h;
+          fn(loc, vx);
+        }
+}
+
+// Calls fn(facet DoF lattice coords, facet vertex coords [d][3], outward normal[3]) per boundary facet.
+template <typename Fn> void for_each_boundary_facet(const SMesh& m, Fn fn) {
+  std::vector<std::array<std::array<int, 3>, 4>> simp;
+  cell_simplices(m.d, simp);
+  int fd = m.d - 1;
+  int nfb = nbasis(fd, m.order);
+  int nc3 = m.d == 3 ? m.n : 1;
+  std::vector<std::array<int, 3>> loc(nfb);
+  double vx[4][3];
+  for (int cz = 0; cz < nc3; ++cz)
+    for (int cy = 0; cy < m.n; ++cy)
+      for (int cx = 0; cx < m.n; ++cx) {
+        int cell[3] = {cx, cy, cz};
+        bool bnd = false;
+        for (int ax = 0; ax < m.d; ++ax) bnd |= (cell[ax] == 0 || cell[ax] == m.n - 1);
+        if (!bnd) continue;
+        for (auto& s : simp) {
+          // faces: drop one vertex
+          for (int drop = 0; drop <= m.d; ++drop) {
+            int fv[3][3];
+            int c = 0;
+            for (int a = 0; a <= m.d; ++a)
+              if (a != drop) {
+                for (int ax = 0; ax < 3; ++ax) fv[c][ax] = cell[ax] + s[a][ax];
+                ++c;
+              }
+            for (int ax = 0; ax < m.d; ++ax)
+              for (int side = 0; side < 2; ++side) {
+                int val = side == 0 ? 0 : m.n;
+                bool on = true;
+                for (int v = 0; v < m.d; ++v) on &= (fv[v][ax] == val);
+                if (!on) continue;
+                for (int i = 0; i < nfb; ++i) {
+                  auto l = basis_node(fd, m.order, i);
+                  for (int x = 0; x < 3; ++x) {
+                    double p = 0;
+                    for (int a = 0; a < m.d; ++a) p += l[a] * fv[a][x] * m.order;
+                    loc[i][x] = (int)std::lround(p);
+                  }
+                }
+                for (int a = 0; a < m.d; ++a)
+                  for (int x = 0; x < 3; ++x) vx[a][x] = fv[a][x] * m.h;
+                double nrm[3] = {0, 0, 0};
+                nrm[ax] = side == 0 ? -1.0 : 1.0;
+                fn(loc, vx, nrm);
+              }
+          }
+        }
+      }
+}
+
+// Dense assembly of K, M, B on a small mesh.
+void assemble_dense(const SMesh& m, std::vector<double>& K, std::vector<double>& M,
+                    std::vector<double>& B) {
+  int64_t N = 1;
+  for (int ax = 0; ax < m.d; ++ax) N *= m.W;
+  K.assign(N * N, 0.0);
+  M.assign(N * N, 0.0);
+  B.assign(N * N, 0.0);
+  std::vector<double> Ke, Me, Be;
+  for_each_element(m, [&](const std::vector<std::array<int, 3>>& loc, const double (*vx)[3]) {
+    element_km(m.d, m.order, vx, Ke, Me);
+    int nb = (int)loc.size();
+    for (int i = 0; i < nb; ++i)
+      for (int j = 0; j < nb; ++j) {
+        int64_t r = m.idx(loc[i].data()), c = m.idx(loc[j].data());
+        K[r * N + c] += Ke[i * nb + j];
+        M[r * N + c] += Me[i * nb + j];
+      }
+  });
+  for_each_boundary_facet(m, [&](const std::vector<std::array<int, 3>>& loc, const double (*vx)[3],
+                                 const double*) {
+    facet_mass(m.d, m.order, vx, Be);
+    int nb = (int)loc.size();
+    for (int i = 0; i < nb; ++i)
+      for (int j = 0; j < nb; ++j) {
+        int64_t r = m.idx(loc[i].data()), c = m.idx(loc[j].data());
+        B[r * N + c] += Be[i * nb + j];
+      }
+  });
+}
+
+// Representative lattice index (on a reference lattice of Wr points) of axis class c.
+int class_rep(int c, int Wr, int R, int q) {
+  if (c < R) return c;
+  if (c >= R + q) return Wr - R + (c - R - q);
+  int p = c - R;
+  for (int a = R; a < Wr - R; ++a)
+    if (a % q == p) return a;
+  return -1;
+}
+
+void level_stencils(int d, int order, int n, GridDesc& g, std::vector<double>& Ks,
+                    std::vector<double>& Ms, std::vector<double>& Bs, int& ncls) {
+  g.dim = d;
+  g.R = order;
+  g.q = order;
+  g.W = order * n + 1;
+  g.C1 = 2 * g.R + g.q;
+  g.noff = 1;
+  g.N = 1;
+  for (int ax = 0; ax < d; ++ax) {
+    g.noff *= 2 * g.R + 1;
+    g.N *= g.W;
+  }
+  ncls = 1;
+  for (int ax = 0; ax < d; ++ax) ncls *= g.C1;
+  // reference mesh: smallest n_ref with a full interior period
+  int nref = order == 1 ? 2 : 4;
+  nref = std::min(nref, n);
+  SMesh rm{d, order, nref, order * nref + 1, 1.0 / n};   // same h as the target level
+  std::vector<double> K, M, B;
+  assemble_dense(rm, K, M, B);
+  int64_t Nr = 1;
+  for (int ax = 0; ax < d; ++ax) Nr *= rm.W;
+  Ks.assign((size_t)ncls * g.noff, 0.0);
+  Ms.assign((size_t)ncls * g.noff, 0.0);
+  Bs.assign((size_t)ncls * g.noff, 0.0);
+  int side = 2 * g.R + 1;
+  for (int cls = 0; cls < ncls; ++cls) {
+    int cc[3] = {0, 0, 0}, rep[3] = {0, 0, 0};
+    int t = cls;
+    bool ok = true;
+    for (int ax = 0; ax < d; ++ax) {
+      cc[ax] = t % g.C1;
+      t /= g.C1;
+      // a class only exists on the target lattice if it has a member there
+      rep[ax] = class_rep(cc[ax], rm.W, g.R, g.q);
+      if (rep[ax] < 0) ok = false;
+    }
+    if (!ok) continue;
+    int64_t r = rm.idx(rep);
+    for (int o = 0; o < g.noff; ++o) {
+      int oo = o, nb[3] = {0, 0, 0};
+      bool in = true;
+      for (int ax = 0; ax < d; ++ax) {
+        int dxx = oo % side - g.R;
+        oo /= side;
+        nb[ax] = rep[ax] + dxx;
+        if (nb[ax] < 0 || nb[ax] >= rm.W) in = false;
+      }
+      if (!in) continue;
+      int64_t c = rm.idx(nb);
+      Ks[(size_t)cls * g.noff + o] = K[r * Nr + c];
+      Ms[(size_t)cls * g.noff + o] = M[r * Nr + c];
+      Bs[(size_t)cls * g.noff + o] = B[r * Nr + c];
+    }
+  }
+}
+
+}  // namespace
+
+int build_tables(int d, int order, int n, HostTables* t) {
+  if (!(d == 2 || d == 3) || !(order == 1 || order == 2) || (d == 3 && order != 1)) return HELM_EINVAL;
+  if (n < 4 || n % 2) return HELM_EINVAL;
+  level_stencils(d, order, n, t->fine, t->Kf, t->Mf, t->Bf, t->ncls_f);
+  level_stencils(d, order, n / 2, t->coarse, t->Kc, t->Mc, t->Bc, t->ncls_c);
+  // prolongation weights: evaluate coarse basis functions at fine positions
+  int q = order;
+  t->pf = 2 * q;
+  t->npc = 1;
+  t->npo = 1;
+  for (int ax = 0; ax < d; ++ax) {
+    t->npc *= t->pf;
+    t->npo *= q + 1;
+  }
+  t->pw.assign((size_t)t->npc * t->npo, 0.0);
+  std::vector<std::array<std::array<int, 3>, 4>> simp;
+  cell_simplices(d, simp);
+  int nb = nbasis(d, order);
+  for (int c = 0; c < t->npc; ++c) {
+    double xi[3] = {0, 0, 0};   // position in the coarse cell, [0,1)
+    int tt = c;
+    for (int ax = 0; ax < d; ++ax) {
+      xi[ax] = (double)(tt % t->pf) / t->pf;
+      tt /= t->pf;
+    }
+    bool found = false;
+    for (auto& s : simp) {
+      // barycentric coords of xi in simplex s (unit cell coords)
+      double J[3][3] = {{1, 0, 0}, {0, 1, 0}, {0, 0, 1}}, rhs[3] = {0, 0, 0};
+      for (int col = 0; col < d; ++col)
+        for (int r = 0; r < d; ++r) J[r][col] = s[col + 1][r] - s[0][r];
+      for (int r = 0; r < d; ++r) rhs[r] = xi[r] - s[0][r];
+      double lam[4] = {0, 0, 0, 0};
+      if (d == 2) {
+        double det = J[0][0] * J[1][1] - J[0][1] * J[1][0];
+        lam[1] = (rhs[0] * J[1][1] - J[0][1] * rhs[1]) / det;
+        lam[2] = (J[0][0] * rhs[1] - rhs[0] * J[1][0]) / det;
+      } else {
+        double det = det3(J);
+        for (int col = 0; col < 3; ++col) {
+          double Jc[3][3];
+          for (int r = 0; r < 3; ++r)
+            for (int cc = 0; cc < 3; ++cc) Jc[r][cc] = cc == col ? rhs[r] : J[r][cc];
+          lam[col + 1] = det3(Jc) / det;
+        }
+      }
+      double s0 = 1.0;
+      for (int a = 1; a <= d; ++a) s0 -= lam[a];
+      lam[0] = s0;
+      bool inside = true;
+      for (int a = 0; a <= d; ++a) inside &= lam[a] >= -1e-12;
+      if (!inside) continue;
+      for (int i = 0; i < nb; ++i) {
+        double wv = basis_val(d, order, i, lam);
+        if (std::fabs(wv) < 1e-15) continue;
+        auto l = basis_node(d, order, i);
+        int o = 0, mul = 1;
+        for (int ax = 0; ax < d; ++ax) {
+          double p = 0;
+          for (int a = 0; a <= d; ++a) p += l[a] * s[a][ax] * q;
+          o += (int)std::lround(p) * mul;
+          mul *= q + 1;
+        }
+        t->pw[(size_t)c * t->npo + o] = wv;
+      }
+      found = true;
+      break;
+    }
+    if (!found) return HELM_EINVAL;
+  }
+  return HELM_OK;
+}
+
+void rhs_planewave(int d, int order, int n, double k, double theta, double2* F) {
+  SMesh m{d, order, n, order * n + 1, 1.0 / n};
+  int64_t N = 1;
+  for (int ax = 0; ax < d; ++ax) N *= m.W;
+  std::memset(F, 0, sizeof(double2) * N);
+  double dir[3] = {std::cos(theta), std::sin(theta), 0.0};
+  std::vector<double> Be;
+  for_each_boundary_facet(m, [&](const std::vector<std::array<int, 3>>& loc, const double (*vx)[3],
+                                 const double* nrm) {
+    facet_mass(d, order, vx, Be);
+    int nb = (int)loc.size();
+    double dn = dir[0] * nrm[0] + dir[1] * nrm[1] + dir[2] * nrm[2];
+    for (int j = 0; j < nb; ++j) {
+      double ph = 0;
+      for (int ax = 0; ax < d; ++ax) ph += dir[ax] * loc[j][ax] * m.h / order;
+      // g = i k (d.n - 1) exp(i k d.x)
+      double gr = -k * (dn - 1.0) * std::sin(k * ph), gi = k * (dn - 1.0) * std::cos(k * ph);
+      for (int i = 0; i < nb; ++i) {
+        int64_t r = m.idx(loc[i].data());
+        F[r].x += Be[i * nb + j] * gr;
+        F[r].y += Be[i * nb + j] * gi;
+      }
+    }
+  });
+}
+
+void rhs_gaussian(int d, int order, int n, double sigma, const double* c, double2* F) {
+  GridDesc g;
+  std::vector<double> Ks, Ms, Bs;
+  int ncls;
+  level_stencils(d, order, n, g, Ks, Ms, Bs, ncls);
+  double h = 1.0 / n / order;
+  int W = g.W, side = 2 * g.R + 1;
+  std::vector<double> f(g.N);
+  for (int64_t p = 0; p < g.N; ++p) {
+    int64_t t = p;
+    double r2 = 0;
+    for (int ax = 0; ax < d; ++ax) {
+      double x = (double)(t % W) * h - c[ax];
+      t /= W;
+      r2 += x * x;
+    }
+    f[p] = std::exp(-r2 / (2.0 * sigma * sigma));
+  }
+  for (int64_t p = 0; p < g.N; ++p) {
+    int a[3] = {0, 0, 0};
+    int64_t t = p;
+    int cls = 0, mul = 1;
+    for (int ax = 0; ax < d; ++ax) {
+      a[ax] = (int)(t % W);
+      t /= W;
+      cls += axis_class(a[ax], W, g.R, g.q) * mul;
+      mul *= g.C1;
+    }
+    double s = 0;
+    for (int o = 0; o < g.noff; ++o) {
+      double coef = Ms[(size_t)cls * g.noff + o];
+      if (coef == 0.0) continue;
+      int oo = o;
+      int64_t idx = 0, st = 1;
+      for (int ax = 0; ax < d; ++ax) {
+        int b = a[ax] + oo % side - g.R;
+        oo /= side;
+        idx += (int64_t)b * st;
+        st *= W;
+      }
+      s += coef * f[idx];
+    }
+    F[p] = make_double2(s, 0.0);
+  }
+}
+
+}  // namespace helm

@@ -1,0 +1,122 @@
+"""GPU parity of every hot-path step against the FP64 CPU oracle (through the C ABI).
+
+Tolerances (derived from the arithmetic):
+  * FP64 operator applies: <= 1e-12 relative (a 9..27-term stencil sum in
+    complex128 vs CSR SpMV, both ~1e-16 per term).
+  * FP64 coarse solve / V-cycle: <= 1e-9 relative (explicit inverses of the
+    Schur blocks amplify rounding by the block condition number, ~1e4..1e6).
+  * complex64 V-cycle: <= 2e-5 relative (float32 unit roundoff 6e-8 times the
+    same conditioning).
+  * Solves: true relative residual <= 1e-8 (recomputed here by the oracle's CSR
+    A0), FGMRES iterations within +-1 of the oracle (FP64) and within +-3
+    (complex64 preconditioner), solution within cond-scaled tolerance.
+"""
+import numpy as np
+import pytest
+
+import helm_inputs as hi
+from oracle import fem, solver as osolver
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+if not torch.cuda.is_available():
+    pytest.skip("no CUDA device", allow_module_level=True)
+
+import paper_2104_01439_gb300 as pkg  # noqa: E402
+
+_PB = {}
+
+
+def problem(wl):
+    key = (wl.dim, wl.order, wl.n, wl.k, wl.shift, wl.rhs, wl.seed)
+    if key not in _PB:
+        _PB[key] = osolver.build_problem(wl)
+    return _PB[key]
+
+
+def rel(a, b):
+    return np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300)
+
+
+def crand(n, seed):
+    g = np.random.default_rng(seed)
+    return g.standard_normal(n) + 1j * g.standard_normal(n)
+
+
+def dev(a):
+    return torch.from_numpy(np.ascontiguousarray(a, dtype=np.complex128)).cuda()
+
+
+CASES = [
+    hi.Workload("p1_n8", 2, 1, 8, 6.0, 18.0, "random", seed=1),
+    hi.Workload("p1_n36_ragged", 2, 1, 36, 12.0, 72.0, "random", seed=2),
+    hi.Workload("p1_n64", 2, 1, 64, 20.0, 200.0, "planewave"),
+    hi.Workload("p2_n8", 2, 2, 8, 6.0, 18.0, "random", seed=3),
+    hi.Workload("p2_n22_ragged", 2, 2, 22, 10.0, 50.0, "random", seed=4),
+    hi.Workload("p1_3d_n6", 3, 1, 6, 4.0, 8.0, "random", seed=5),
+]
+
+
+@pytest.mark.parametrize("wl", CASES, ids=lambda w: w.name)
+def test_apply_fp64(wl):
+    pb = problem(wl)
+    s = pkg.Solver(wl.k, wl.n, wl.order, wl.shift, dim=wl.dim)
+    x = crand(pb.mesh.num_dofs, 7)
+    for which, A in ((0, pb.A0), (1, pb.Aeps)):
+        y = s.apply(dev(x), which).cpu().numpy()
+        assert rel(y, A @ x) <= 1e-12
+    s.close()
+
+
+@pytest.mark.parametrize("prec,tol", [(pkg.HELM_FP64, 1e-9), (pkg.HELM_MIXED, 2e-5)])
+@pytest.mark.parametrize("wl", CASES, ids=lambda w: w.name)
+def test_coarse_solve(wl, prec, tol):
+    pb = problem(wl)
+    s = pkg.Solver(wl.k, wl.n, wl.order, wl.shift, dim=wl.dim, precision=prec)
+    r = crand(pb.cmesh.num_dofs, 11)
+    uc = s.coarse_solve(dev(r)).cpu().numpy()
+    ref = pb.twogrid().coarse_solve(r)
+    assert rel(uc, ref) <= tol
+    s.close()
+
+
+@pytest.mark.parametrize("prec,tol", [(pkg.HELM_FP64, 1e-9), (pkg.HELM_MIXED, 2e-5)])
+@pytest.mark.parametrize("wl", CASES, ids=lambda w: w.name)
+def test_vcycle(wl, prec, tol):
+    pb = problem(wl)
+    s = pkg.Solver(wl.k, wl.n, wl.order, wl.shift, dim=wl.dim, precision=prec)
+    f = crand(pb.mesh.num_dofs, 13)
+    u = s.vcycle(dev(f)).cpu().numpy()
+    ref = pb.twogrid().apply(f)
+    assert rel(u, ref) <= tol
+    s.close()
+
+
+@pytest.mark.parametrize("wl", [CASES[1], CASES[2], CASES[4], CASES[5]], ids=lambda w: w.name)
+def test_rhs_builders(wl):
+    pb = problem(wl)
+    s = pkg.Solver(wl.k, wl.n, wl.order, wl.shift, dim=wl.dim)
+    Fp = s.rhs_planewave(0.3).numpy()
+    assert rel(Fp, fem.load_planewave(pb.mesh, pb.M, wl.k, 0.3)) <= 1e-12
+    Fg = s.rhs_gaussian(2.0 / wl.n).numpy()
+    assert rel(Fg, fem.load_gaussian(pb.mesh, pb.M, 2.0 / wl.n)) <= 1e-12
+    s.close()
+
+
+@pytest.mark.parametrize("prec", [pkg.HELM_FP64, pkg.HELM_MIXED])
+@pytest.mark.parametrize("wl", [CASES[1], CASES[2], CASES[4], CASES[5]], ids=lambda w: w.name)
+def test_solve_parity(wl, prec):
+    pb = problem(wl)
+    ref = pb.solve()
+    s = pkg.Solver(wl.k, wl.n, wl.order, wl.shift, dim=wl.dim, restart=wl.restart, maxit=wl.maxit,
+                   tol=wl.tol, precision=prec)
+    x, res = s.solve(dev(pb.F))
+    xh = x.cpu().numpy()
+    relres = np.linalg.norm(pb.F - pb.A0 @ xh) / np.linalg.norm(pb.F)
+    assert res.status == "converged"
+    assert relres <= 1e-8 and abs(relres - res.relres_true) <= 1e-10
+    slack = 1 if prec == pkg.HELM_FP64 else 3
+    assert abs(res.iters - ref.iters) <= slack, (res.iters, ref.iters)
+    assert rel(xh, ref.x) <= 1e-5
+    s.close()
