@@ -78,6 +78,7 @@ typedef struct {
   double relres_true;   /* ||F - A0 x|| / ||F|| recomputed in FP64 at the end */
   double relres_est;    /* last Givens residual estimate |g_{j+1}| / ||F||    */
   float solve_ms;       /* device time of the solve (CUDA events)            */
+  int kernels;          /* kernel launches issued by the solve (graph nodes included) */
 } helm_result;
 
 /* Defaults: dim 2, omega 0.6, nu 2, restart 50, maxit 500, tol 1e-8, FP64, stream NULL. */
@@ -103,8 +104,9 @@ int helm_num_dofs(helm_t h, int64_t* n);
 /* Number of complex DoFs of the 2h (coarse) space. */
 int helm_num_coarse_dofs(helm_t h, int64_t* n);
 
-/* Milliseconds the last helm_setup spent (device events around the coarse factorisation and tables). */
-int helm_setup_ms(helm_t h, float* ms);
+/* Device milliseconds helm_setup spent in the coarse factorisation (CUDA
+ * events) and the number of kernels it launched. Either pointer may be NULL. */
+int helm_setup_info(helm_t h, float* ms, int* kernels);
 
 /*
  * Solve A0 x = F (Sec. 4: FGMRES right-preconditioned by the twogrid

@@ -19,7 +19,7 @@ HELM_MIXED = 1
 STATUS = {0: "converged", 1: "maxit", 2: "breakdown", 3: "nonfinite"}
 
 EXPORTS = [
-    "helm_default_opts", "helm_setup", "helm_last_cuda_error", "helm_num_dofs", "helm_num_coarse_dofs", "helm_setup_ms",
+    "helm_default_opts", "helm_setup", "helm_last_cuda_error", "helm_num_dofs", "helm_num_coarse_dofs", "helm_setup_info",
     "helm_solve", "helm_solve_host", "helm_batch_solve", "helm_destroy", "helm_strerror",
     "helm_rhs_planewave", "helm_rhs_gaussian", "helm_apply", "helm_vcycle", "helm_coarse_solve",
     "helm_last_profile", "helm_set_profiling",
@@ -35,7 +35,7 @@ class HelmOpts(ctypes.Structure):
 class HelmResult(ctypes.Structure):
     _fields_ = [("iters", ctypes.c_int), ("cycles", ctypes.c_int), ("status", ctypes.c_int),
                 ("relres_true", ctypes.c_double), ("relres_est", ctypes.c_double),
-                ("solve_ms", ctypes.c_float)]
+                ("solve_ms", ctypes.c_float), ("kernels", ctypes.c_int)]
 
 
 class HelmError(RuntimeError):
@@ -59,7 +59,7 @@ def load(path: str = LIB_PATH):
     lib.helm_setup.argtypes = [d, d, i, d, ctypes.POINTER(HelmOpts), ctypes.POINTER(vp)]
     lib.helm_num_dofs.argtypes = [vp, i64p]
     lib.helm_num_coarse_dofs.argtypes = [vp, i64p]
-    lib.helm_setup_ms.argtypes = [vp, ctypes.POINTER(ctypes.c_float)]
+    lib.helm_setup_info.argtypes = [vp, ctypes.POINTER(ctypes.c_float), ctypes.POINTER(ctypes.c_int)]
     lib.helm_solve.argtypes = [vp, vp, vp, ctypes.POINTER(HelmResult)]
     lib.helm_solve_host.argtypes = [vp, vp, vp, ctypes.POINTER(HelmResult)]
     lib.helm_batch_solve.argtypes = [i, ctypes.POINTER(vp), ctypes.POINTER(vp), ctypes.POINTER(vp),
@@ -100,11 +100,12 @@ class SolveResult:
     relres_true: float
     relres_est: float
     solve_ms: float
+    kernels: int
 
 
 def _res(r: HelmResult) -> SolveResult:
     return SolveResult(r.iters, r.cycles, STATUS.get(r.status, str(r.status)), r.relres_true,
-                       r.relres_est, r.solve_ms)
+                       r.relres_est, r.solve_ms, r.kernels)
 
 
 def _ptr(t):
@@ -137,9 +138,10 @@ class Solver:
         self.num_dofs = nd.value
         _check(lib.helm_num_coarse_dofs(self._h, ctypes.byref(nd)))
         self.num_coarse_dofs = nd.value
-        ms = ctypes.c_float()
-        _check(lib.helm_setup_ms(self._h, ctypes.byref(ms)))
+        ms, nk = ctypes.c_float(), ctypes.c_int()
+        _check(lib.helm_setup_info(self._h, ctypes.byref(ms), ctypes.byref(nk)))
         self.setup_ms = ms.value
+        self.setup_kernels = nk.value
 
     @property
     def handle(self):

@@ -67,6 +67,8 @@ struct helm_ctx {
   cudaGraphExec_t iter = nullptr;
   cudaEvent_t e0 = nullptr, e1 = nullptr;
   float setup_ms = 0.f;
+  int setup_kernels = 0;
+  int iter_nodes = 0;          // kernel nodes in the captured iteration graph
   Profile prof;
   std::vector<void*> allocs;
 
@@ -278,6 +280,11 @@ int capture_iteration(helm_ctx* h) {
     enqueue_iteration(h, cs);
     e = cudaStreamEndCapture(cs, &g);
   }
+  if (e == cudaSuccess) {
+    size_t nn = 0;
+    cudaGraphGetNodes(g, nullptr, &nn);
+    h->iter_nodes = (int)nn;
+  }
   if (e == cudaSuccess) e = cudaGraphInstantiate(&h->iter, g, 0);
   if (g) cudaGraphDestroy(g);
   cudaStreamDestroy(cs);
@@ -302,6 +309,7 @@ struct SolveTask {
   int launched_in_cycle = 0;
   int launched_total = 0;
   int cycles = 0;
+  int kernels = 0;
   int rc = HELM_OK;
   cudaEvent_t ready = nullptr;
 };
@@ -320,6 +328,7 @@ int solve_begin(SolveTask& t) {
   CK(cudaEventRecord(h->e0, s));
   launch_norm(kb, t.F, 0, s);          // ||F||, beta = ||F||  (x0 = 0: r0 = F)
   launch_cycle_start(kb, t.F, s);      // v1 = F / beta
+  t.kernels = 3;
   CK(cudaEventCreateWithFlags(&t.ready, cudaEventDisableTiming));
   t.phase = SolveTask::ITER;
   return HELM_OK;
@@ -357,6 +366,7 @@ bool solve_step(SolveTask& t, bool blocking) {
         } else {
           cudaGraphLaunch(h->iter, s);
         }
+        t.kernels += h->iter_nodes;
       }
       t.launched_in_cycle += chunk;
       t.launched_total += chunk;
@@ -378,6 +388,7 @@ bool solve_step(SolveTask& t, bool blocking) {
       StencilView<double> A0 = make_view<double>(h->gf, h->coefA0, nullptr);
       launch_residual<double, double2, double2>(A0, vsel<const double2>(t.F), t.x, h->rres, nullptr, s);
       launch_norm(kb, h->rres, 1, s);
+      t.kernels += 5;
       cudaMemcpyAsync(h->st_h, kb.st, sizeof(KState), cudaMemcpyDeviceToHost, s);
       cudaEventRecord(t.ready, s);
       t.cycles += 1;
@@ -392,6 +403,7 @@ bool solve_step(SolveTask& t, bool blocking) {
                   !(st->relres == st->relres);
       if (!done) {
         launch_cycle_start(kb, h->rres, s);   // restart from r = F - A0 x
+        t.kernels += 1;
         t.launched_in_cycle = 0;
         t.phase = SolveTask::ITER;
         return false;
@@ -411,6 +423,7 @@ bool solve_step(SolveTask& t, bool blocking) {
         t.res->relres_true = st->relres;
         t.res->relres_est = st->est;
         t.res->solve_ms = ms;
+        t.res->kernels = t.kernels;
         t.res->status = st->nonfinite || !(st->relres == st->relres) ? HELM_NONFINITE
                         : st->relres <= h->opts.tol                  ? HELM_CONVERGED
                         : st->breakdown                             ? HELM_BREAKDOWN
@@ -527,6 +540,7 @@ static int setup_impl(helm_ctx* h) {
   CK(cudaEventRecord(h->e0, s));
   StencilView<double> Acv = make_view<double>(h->gc, h->p64.coefAc, nullptr);
   rc = launch_coarse_factor<double>(D64, tmp, piv, bar, h->err, Acv, L, h->nsm, s);
+  h->setup_kernels = L.nb + (o.precision == HELM_MIXED ? 1 : 0);
   if (rc == HELM_OK && o.precision == HELM_MIXED) {
     if (cudaMalloc(&h->p32.Dinv, sizeof(float2) * blk * L.nb) != cudaSuccess) rc = HELM_ENOMEM;
     else {
@@ -629,9 +643,10 @@ int helm_num_coarse_dofs(helm_t h, int64_t* n) {
   return HELM_OK;
 }
 
-int helm_setup_ms(helm_t h, float* ms) {
-  if (!h || !ms) return HELM_EINVAL;
-  *ms = h->setup_ms;
+int helm_setup_info(helm_t h, float* ms, int* kernels) {
+  if (!h) return HELM_EINVAL;
+  if (ms) *ms = h->setup_ms;
+  if (kernels) *kernels = h->setup_kernels;
   return HELM_OK;
 }
 
