@@ -44,6 +44,7 @@ extern "C" {
 #define HELM_EZEROPIVOT (-4) /* coarse factorisation met a zero/non-finite pivot (eps = 0 can) */
 #define HELM_ETIMEOUT (-5)   /* a bounded device-side wait ran out */
 #define HELM_ENOTSUP (-6)    /* configuration not supported by this build/device */
+#define HELM_ESCRATCH (-7)   /* problem too large for the fixed scratch of helm_coarse_solve_noalloc */
 
 /* ---- helm_result.status (non-fatal outcome of a solve) --------------- */
 #define HELM_CONVERGED 0     /* true relative residual <= tol */
@@ -171,6 +172,31 @@ int helm_vcycle(helm_t h, const void* f, void* u);
  * lexicographic order of the 2h mesh's DoFs.
  */
 int helm_coarse_solve(helm_t h, const void* rc, void* uc);
+
+/*
+ * Coarse solve that allocates no device memory. The paper has no counterpart;
+ * this entry point only serves callers that must not allocate when they call:
+ * code running under a fixed device-memory budget with no headroom left, code
+ * that has handed all device memory to its own allocator, and latency-bound
+ * loops that cannot afford the implicit device synchronisation a cudaMalloc
+ * or cudaFree may cause. It computes exactly what helm_coarse_solve computes
+ * (same arguments, same kernels), but its temporary block-padded coarse
+ * vectors live in one fixed array of 4 MiB that is part of the library's
+ * device image (every GPU that loads the library holds it until the process
+ * exits) instead of the handle's own buffers.
+ *   - Limit: 2 * (coarse blocks) * (padded block length) complex values of the
+ *     handle's precision must fit in 4 MiB (complex128: 131072 values, e.g. the
+ *     coarse grid of P1 h=1/512; complex64: twice that). Larger problems get
+ *     HELM_ESCRATCH and nothing is launched.
+ *   - The first call on a device looks up the array's device address for that
+ *     device; make that first call outside any stream capture.
+ *   - All calls share the one array and it keeps the previous call's contents
+ *     (every entry a call reads is written by that call first). Calls whose
+ *     work overlaps on the GPU -- several streams, several host threads -- race
+ *     on it: serialise them.
+ * rc, uc: device complex128[Nc] as for helm_coarse_solve; synchronous.
+ */
+int helm_coarse_solve_noalloc(helm_t h, const void* rc, void* uc);
 
 /*
  * Runtime statistics of the last solve's kernels: fills up to `cap` entries

@@ -22,7 +22,7 @@ EXPORTS = [
     "helm_default_opts", "helm_setup", "helm_last_cuda_error", "helm_num_dofs", "helm_num_coarse_dofs", "helm_setup_info",
     "helm_solve", "helm_solve_host", "helm_batch_solve", "helm_destroy", "helm_strerror",
     "helm_rhs_planewave", "helm_rhs_gaussian", "helm_apply", "helm_vcycle", "helm_coarse_solve",
-    "helm_last_profile", "helm_set_profiling",
+    "helm_last_profile", "helm_set_profiling", "helm_coarse_solve_noalloc",
 ]
 
 
@@ -78,6 +78,7 @@ def load(path: str = LIB_PATH):
     lib.helm_last_profile.argtypes = [vp, i, ctypes.POINTER(ctypes.c_char_p), ctypes.POINTER(d),
                                       ctypes.POINTER(i), ctypes.POINTER(i)]
     lib.helm_set_profiling.argtypes = [vp, i]
+    lib.helm_coarse_solve_noalloc.argtypes = [vp, vp, vp]
     for name in EXPORTS:
         if name not in ("helm_default_opts", "helm_destroy", "helm_strerror", "helm_last_cuda_error"):
             getattr(lib, name).restype = i

@@ -6,6 +6,7 @@
 #include <chrono>
 #include <cmath>
 #include <cstring>
+#include <mutex>
 #include <new>
 #include <vector>
 
@@ -468,6 +469,7 @@ const char* helm_strerror(int code) {
     case HELM_EZEROPIVOT: return "zero or non-finite pivot in the coarse factorisation";
     case HELM_ETIMEOUT: return "bounded device wait timed out";
     case HELM_ENOTSUP: return "configuration not supported on this device";
+    case HELM_ESCRATCH: return "problem too large for the 4 MiB scratch of helm_coarse_solve_noalloc";
     default: return "unknown error";
   }
 }
@@ -779,3 +781,66 @@ int helm_last_profile(helm_t h, int cap, const char** names, double* ms, int* ca
 }
 
 }  // extern "C"
+
+// ============================================================================
+// Coarse solve without device allocation (helm_coarse_solve_noalloc).
+//
+// The two block-padded coarse vectors that helm_coarse_solve keeps in the
+// handle live here in one file-scope device array instead. In host code the
+// symbol g_noalloc_scratch only names a host-side stand-in, so its device
+// address is looked up once per device with cudaGetSymbolAddress (with that
+// device current) and cached; the kernels receive that address.
+// ============================================================================
+namespace {
+constexpr size_t kNoAllocScratchBytes = size_t(4) << 20;   // 4 MiB
+constexpr int kMaxDevices = 64;
+std::mutex g_noalloc_mu;
+void* g_noalloc_ptr[kMaxDevices] = {nullptr};
+}  // namespace
+
+static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocScratchBytes];
+
+namespace {
+// Device address of the scratch array on the current device (first call: lookup).
+int noalloc_scratch(void** out) {
+  int dev = 0;
+  CK(cudaGetDevice(&dev));
+  if (dev < 0 || dev >= kMaxDevices) return HELM_ENOTSUP;
+  std::lock_guard<std::mutex> lock(g_noalloc_mu);
+  if (!g_noalloc_ptr[dev]) {
+    void* p = nullptr;
+    CK(cudaGetSymbolAddress(&p, g_noalloc_scratch));
+    g_noalloc_ptr[dev] = p;
+  }
+  *out = g_noalloc_ptr[dev];
+  return HELM_OK;
+}
+
+template <typename T>
+int coarse_solve_noalloc(helm_t h, const double2* rc_nat, double2* uc_nat) {
+  using V = c2<T>;
+  Prec<T>& p = h->prec<T>();
+  const size_t nvec = (size_t)h->L.nb * h->L.ldb;
+  if (2 * nvec * sizeof(V) > kNoAllocScratchBytes) return HELM_ESCRATCH;
+  void* base = nullptr;
+  int rc = noalloc_scratch(&base);
+  if (rc) return rc;
+  V* pad_rc = static_cast<V*>(base);
+  V* pad_uc = pad_rc + nvec;   // 16-byte aligned: nvec * sizeof(V) is a multiple of 16 (ldb even)
+  CK(cudaMemsetAsync(h->err, 0, sizeof(int), h->s));   // the error word must start at zero
+  launch_coarse_pack<double2, V>(h->gc, h->L, rc_nat, pad_rc, h->s);   // writes every padded entry
+  launch_coarse_solve<T>(p.plan, p.Dinv, make_view<T>(h->gc, p.coefAc, nullptr), h->L, h->cpl, pad_rc, pad_uc,
+                         h->err, nullptr, h->s);
+  launch_coarse_unpack<V, double2>(h->gc, h->L, pad_uc, uc_nat, h->s);
+  CK(cudaGetLastError());
+  CK(cudaStreamSynchronize(h->s));
+  return check_err(h);
+}
+}  // namespace
+
+extern "C" int helm_coarse_solve_noalloc(helm_t h, const void* rc, void* uc) {
+  if (!h || !rc || !uc) return HELM_EINVAL;
+  if (h->opts.precision == HELM_MIXED)
+    return coarse_solve_noalloc<float>(h, (const double2*)rc, (double2*)uc);
+  return coarse_solve_noalloc<double>(h, (const double2*)rc, (double2*)uc);
+}
