@@ -535,7 +535,7 @@ static int setup_impl(helm_ctx* h) {
   unsigned* bar = nullptr;
   CK(cudaMalloc(&D64, sizeof(double2) * blk * L.nb));
   CK(cudaMalloc(&tmp, sizeof(double2) * blk));
-  CK(cudaMalloc(&piv, sizeof(double2) * 2 * L.ldb));
+  CK(cudaMalloc(&piv, sizeof(double2) * factor_workspace(L)));
   CK(cudaMalloc(&bar, 2 * sizeof(unsigned)));
   CK(h->alloc(&h->err, sizeof(int)));
   CK(cudaMemsetAsync(h->err, 0, sizeof(int), s));

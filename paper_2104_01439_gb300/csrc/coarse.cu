@@ -98,6 +98,45 @@ __device__ __forceinline__ void st_cluster(const void* local, unsigned rank, dou
   asm volatile("st.shared::cluster.v2.f64 [%0], {%1, %2};" ::"r"(ra), "d"(v.x), "d"(v.y) : "memory");
 }
 
+__device__ __forceinline__ unsigned mapa(unsigned local, unsigned rank) {
+  unsigned ra;
+  asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(ra) : "r"(local), "r"(rank));
+  return ra;
+}
+// Asynchronous store into CTA `rank`'s shared memory that completes its bytes
+// on that CTA's mbarrier (the receiver waits on its own barrier; no cluster barrier).
+__device__ __forceinline__ void st_async(const void* dst, unsigned rank, float2 v, const uint64_t* bar) {
+  unsigned d = mapa(smem_u32(dst), rank), b = mapa(smem_u32(bar), rank);
+  asm volatile("st.async.shared::cluster.mbarrier::complete_tx::bytes.v2.f32 [%0], {%1, %2}, [%3];" ::"r"(d),
+               "f"(v.x), "f"(v.y), "r"(b)
+               : "memory");
+}
+__device__ __forceinline__ void st_async(const void* dst, unsigned rank, double2 v, const uint64_t* bar) {
+  unsigned d = mapa(smem_u32(dst), rank), b = mapa(smem_u32(bar), rank);
+  asm volatile("st.async.shared::cluster.mbarrier::complete_tx::bytes.v2.f64 [%0], {%1, %2}, [%3];" ::"r"(d),
+               "d"(v.x), "d"(v.y), "r"(b)
+               : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait_cluster(uint64_t* bar, unsigned parity) {
+  unsigned ok;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "mbarrier.try_wait.parity.acquire.cluster.shared::cta.b64 p, [%1], %2;\n\t"
+      "selp.u32 %0, 1, 0, p;\n\t}"
+      : "=r"(ok)
+      : "r"(smem_u32(bar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+// Bounded wait for data pushed by the other CTAs of the cluster (acquire at cluster scope).
+__device__ __forceinline__ void mbar_wait_cluster(uint64_t* bar, unsigned parity, int* s_err, int* err) {
+  if (*(volatile int*)s_err) return;
+  for (int i = 0; i < (1 << 20); ++i)
+    if (mbar_try_wait_cluster(bar, parity)) return;
+  *(volatile int*)s_err = 1;
+  atomicExch(err, HELM_ETIMEOUT);
+}
+
 template <typename V> __device__ __forceinline__ V warp_sum(V v) {
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) {
@@ -148,10 +187,12 @@ __device__ __forceinline__ bool neighbour(const GridDesc& g, const CoarseLayout&
 // ---------------------------------------------------------------------------
 // Factorisation kernel: Schur update + in-place Gauss-Jordan of block J.
 // ---------------------------------------------------------------------------
+constexpr int kGJP = 8;   // pivots per Gauss-Jordan panel (factor_workspace assumes 8)
+
 template <typename T>
 __global__ void __launch_bounds__(256) k_factor_block(c2<T>* D, c2<T>* Tmp, c2<T>* piv,
                                                       unsigned* bar, int* err, StencilView<T> Ac,
-                                                      CoarseLayout L, int J) {
+                                                      CoarseLayout L, int J, int stageR) {
   using V = c2<T>;
   extern __shared__ __align__(128) unsigned char sm[];
   const GridDesc g = Ac.g;
@@ -217,49 +258,132 @@ __global__ void __launch_bounds__(256) k_factor_block(c2<T>* D, c2<T>* Tmp, c2<T
       }
     }
     S[idx] = v;
+    if (l < B && i < kGJP) piv[(int64_t)i * ldb + l] = v;                          // pivot rows of panel 0
+    if (l < kGJP && l < B) piv[2 * kGJP * (int64_t)ldb + (int64_t)i * kGJP + l] = v;   // its columns
   }
   if (!grid_barrier(bar, err, gridDim.x)) return;
 
-  // In-place Gauss-Jordan inversion of S (no pivoting).
-  const int rpb = (B + gridDim.x - 1) / gridDim.x;
-  const int r0 = blockIdx.x * rpb, r1 = min(B, r0 + rpb), nr = max(0, r1 - r0);
-  V* fs = coef + ncls * g.noff;   // per-row multipliers, rpb entries
-  if (r0 <= 0 && 0 < r1)
-    for (int j = threadIdx.x; j < B; j += blockDim.x) piv[j] = S[j];
-  if (!grid_barrier(bar, err, gridDim.x)) return;
-  for (int k = 0; k < B; ++k) {
-    const V* pk = piv + (k & 1) * ldb;
-    V pkk = pk[k];
-    T mag = pkk.x * pkk.x + pkk.y * pkk.y;
-    if (!(mag > T(0)) || !isfinite(mag)) {
-      if (threadIdx.x == 0) atomicCAS(err, 0, HELM_EZEROPIVOT);
-      return;
-    }
-    V p = cinv(pkk);
-    for (int r = threadIdx.x; r < nr; r += blockDim.x) fs[r] = cmul(S[(int64_t)(r0 + r) * ldb + k], p);
+  // In-place blocked Gauss-Jordan inversion of S (no pivoting), kGJP pivots per
+  // panel. For the panel block P = S[k0:k1, k0:k1] with pivot rows R = S[k0:k1, :]
+  // and the panel columns C = S[:, k0:k1]:
+  //   pivot rows:  R <- P^{-1} R,          panel block <- P^{-1}
+  //   other rows:  S[i,:] <- S[i,:] - (C_i P^{-1}) R,   C_i <- -C_i P^{-1}
+  // which equals kGJP consecutive scalar Gauss-Jordan steps. Every CTA inverts P
+  // itself; R and C are read from snapshots written while the previous panel was
+  // updated, so each panel needs a single grid barrier. The B x B elements are
+  // split into contiguous row-major ranges, one per CTA (FP64 work is balanced).
+  const int G = gridDim.x;
+  const int64_t BB = (int64_t)B * B;
+  const int64_t epb = (BB + G - 1) / G;
+  const int64_t e0 = (int64_t)blockIdx.x * epb, e1 = min(BB, e0 + epb);
+  const int i0 = (int)(e0 / B), i1 = e1 > e0 ? (int)((e1 - 1) / B) : i0 - 1;   // rows touched
+  V* Pm = coef + ncls * g.noff;                 // kGJP x kGJP panel block -> its inverse
+  V* cP = Pm + kGJP * kGJP;                     // (rows touched) x kGJP : C_i P^{-1}
+  V* Rsm = cP + (epb / B + 3) * kGJP;            // kGJP x ldb staged pivot rows (when stageR); the
+                                                // host sizes cP for epb / B + 3 rows (>= rows touched)
+  __shared__ int gj_bad_s;
+  int* gj_bad = &gj_bad_s;
+  if (threadIdx.x == 0) gj_bad_s = 0;
+  V* pbuf = piv;                                // 2 x [kGJP x ldb]  pivot-row snapshots
+  V* cbuf = piv + 2 * kGJP * (int64_t)ldb;      // 2 x [B x kGJP]    panel-column snapshots
+  for (int k0 = 0, q = 0; k0 < B; k0 += kGJP, ++q) {
+    const int p = min(kGJP, B - k0), k1 = k0 + p, k2 = min(B, k1 + kGJP);
+    const V* R = pbuf + (int64_t)(q & 1) * kGJP * ldb;
+    const V* C = cbuf + (int64_t)(q & 1) * B * kGJP;
+    V* Rn = pbuf + (int64_t)((q + 1) & 1) * kGJP * ldb;
+    V* Cn = cbuf + (int64_t)((q + 1) & 1) * B * kGJP;
+    // (1) P^{-1}: warp 0 runs Gauss-Jordan on the p x p block in shared memory
+    // (one reciprocal per pivot, warp-synchronous; the other warps wait below)
+    for (int t = threadIdx.x; t < p * p; t += blockDim.x) Pm[(t / p) * kGJP + t % p] = R[(int64_t)(t / p) * ldb + k0 + t % p];
     __syncthreads();
-    for (int t = threadIdx.x; t < nr * B; t += blockDim.x) {
-      int r = t / B, j = t - r * B, i = r0 + r;
-      int64_t at = (int64_t)i * ldb + j;
-      if (i == k) {
-        S[at] = j == k ? p : cmul(p, pk[j]);
-      } else if (j == k) {
-        S[at] = mk(-fs[r].x, -fs[r].y);
-      } else {
-        V s = S[at];
-        V f = fs[r];
-        V pj = pk[j];
-        s.x = fma(-f.x, pj.x, s.x);
-        s.x = fma(f.y, pj.y, s.x);
-        s.y = fma(-f.x, pj.y, s.y);
-        s.y = fma(-f.y, pj.x, s.y);
-        S[at] = s;
+    if (threadIdx.x < 32) {
+      const int lane = threadIdx.x;
+      for (int kk = 0; kk < p; ++kk) {
+        const V d = Pm[kk * kGJP + kk];
+        const T mag = d.x * d.x + d.y * d.y;
+        if (!(mag > T(0)) || !isfinite(mag)) {
+          if (lane == 0) *gj_bad = 1;
+          break;
+        }
+        const T rm = T(1) / mag;
+        const V pinv = mk(d.x * rm, -d.y * rm);
+        V nv[2];
+        for (int h = 0; h < 2; ++h) {
+          const int e = lane + 32 * h, a = e / p, bc = e % p;
+          nv[h] = zero;
+          if (e < p * p) {
+            if (a == kk) {
+              nv[h] = bc == kk ? pinv : cmul(pinv, Pm[kk * kGJP + bc]);
+            } else {
+              const V f = cmul(Pm[a * kGJP + kk], pinv);
+              nv[h] = bc == kk ? mk(-f.x, -f.y) : csub(Pm[a * kGJP + bc], cmul(f, Pm[kk * kGJP + bc]));
+            }
+          }
+        }
+        __syncwarp();
+        for (int h = 0; h < 2; ++h) {
+          const int e = lane + 32 * h;
+          if (e < p * p) Pm[(e / p) * kGJP + e % p] = nv[h];
+        }
+        __syncwarp();
       }
     }
     __syncthreads();
-    if (k + 1 < B && r0 <= k + 1 && k + 1 < r1) {
-      V* nxt = piv + ((k + 1) & 1) * ldb;
-      for (int j = threadIdx.x; j < B; j += blockDim.x) nxt[j] = S[(int64_t)(k + 1) * ldb + j];
+    if (*gj_bad) {
+      if (threadIdx.x == 0) atomicCAS(err, 0, HELM_EZEROPIVOT);
+      return;   // every CTA sees the same pivot block and returns
+    }
+    // (2) C_i P^{-1} for the rows this CTA touches (non-pivot rows)
+    for (int t = threadIdx.x; t < (i1 - i0 + 1) * p; t += blockDim.x) {
+      int r = t / p, c = t % p, i = i0 + r;
+      V acc = zero;
+      if (i < k0 || i >= k1)
+        for (int s2 = 0; s2 < p; ++s2) acc = cfma(C[(int64_t)i * kGJP + s2], Pm[s2 * kGJP + c], acc);
+      cP[r * kGJP + c] = acc;
+    }
+    __syncthreads();
+    // (3) element update over the CTA's row-major range, row by row (no per-element
+    // division); the pivot rows are staged in shared memory when they fit.
+    const V* Rs = R;
+    if (stageR) {
+      for (int t = threadIdx.x; t < p * B; t += blockDim.x) Rsm[(t / B) * ldb + t % B] = R[(int64_t)(t / B) * ldb + t % B];
+      __syncthreads();
+      Rs = Rsm;
+    }
+    for (int i = i0; i <= i1; ++i) {
+      const int jb = i == i0 ? (int)(e0 - (int64_t)i0 * B) : 0;
+      const int je = i == i1 ? (int)(e1 - (int64_t)i1 * B) : B;
+      V* Si = S + (int64_t)i * ldb;
+      const bool pivrow = i >= k0 && i < k1;
+      const V* pr = Pm + (i - k0) * kGJP;       // row of P^{-1} (pivot rows)
+      const V* ci = cP + (i - i0) * kGJP;       // C_i P^{-1} (other rows)
+      V* rn = (i >= k1 && i < k2) ? Rn + (int64_t)(i - k1) * ldb : nullptr;
+      for (int j = jb + threadIdx.x; j < je; j += blockDim.x) {
+        V nv;
+        const bool pcol = j >= k0 && j < k1;
+        if (pivrow) {
+          if (pcol) {
+            nv = pr[j - k0];
+          } else {
+            nv = zero;
+            for (int s2 = 0; s2 < p; ++s2) nv = cfma(pr[s2], Rs[s2 * ldb + j], nv);
+          }
+        } else if (pcol) {
+          nv = mk(-ci[j - k0].x, -ci[j - k0].y);
+        } else {
+          nv = Si[j];
+          for (int s2 = 0; s2 < p; ++s2) {
+            const V c = ci[s2], rr = Rs[s2 * ldb + j];
+            nv.x = fma(-c.x, rr.x, nv.x);
+            nv.x = fma(c.y, rr.y, nv.x);
+            nv.y = fma(-c.x, rr.y, nv.y);
+            nv.y = fma(-c.y, rr.x, nv.y);
+          }
+        }
+        Si[j] = nv;
+        if (rn) rn[j] = nv;
+        if (j >= k1 && j < k2) Cn[(int64_t)i * kGJP + (j - k1)] = nv;
+      }
     }
     if (!grid_barrier(bar, err, gridDim.x)) return;
   }
@@ -295,7 +419,7 @@ SolveGeom solve_geometry(const CoarseLayout& L, const GridDesc& gc, int CS, int 
   auto al = [](size_t x) { return (x + 127) & ~size_t(127); };
   size_t o = 0;
   G.off_mbar = o; o = al(o + 8 * S);
-  G.off_rbar = o; o = al(o + 16 + 16);   // two mbarriers, then the CTA's error word
+  G.off_rbar = o; o = al(o + 48);   // rhs mbarriers [2], error word, receive mbarriers [2] at +24
   G.off_coef = o; o = al(o + sizeof(V) * ncls * noff);
   G.off_z = o; o = al(o + sizeof(V) * L.ldb);
   G.off_gath = o; o = al(o + sizeof(V) * 2 * L.ldb);
@@ -313,8 +437,11 @@ SolveGeom solve_geometry(const CoarseLayout& L, const GridDesc& gc, int CS, int 
   return G;
 }
 
+constexpr int kRPW = 4;          // rows of the CTA slice per warp (registers)
+constexpr int kSolveMaxWarps = 18;
+
 template <typename T>
-__global__ void __launch_bounds__(512, 1) k_coarse_solve(const c2<T>* __restrict__ Dinv, StencilView<T> Ac,
+__global__ void __launch_bounds__(kSolveMaxWarps * 32, 1) k_coarse_solve(const c2<T>* __restrict__ Dinv, StencilView<T> Ac,
                                                         CoarseLayout L, SolveGeom G,
                                                         const int* __restrict__ cpl,
                                                         const c2<T>* __restrict__ rc, c2<T>* __restrict__ uc,
@@ -335,6 +462,7 @@ __global__ void __launch_bounds__(512, 1) k_coarse_solve(const c2<T>* __restrict
   int* dn = reinterpret_cast<int*>(sm + G.off_dn);     // [B][maxc] (o | in << 8), -1 terminated
   int* up = reinterpret_cast<int*>(sm + G.off_up);
   int* s_err = reinterpret_cast<int*>(sm + G.off_rbar + 16);
+  uint64_t* gbar = reinterpret_cast<uint64_t*>(sm + G.off_rbar + 24);   // receive barriers of gath[0/1]
 
   const GridDesc g = Ac.g;
   const unsigned rank = cluster_rank(), CS = cluster_size();
@@ -360,6 +488,8 @@ __global__ void __launch_bounds__(512, 1) k_coarse_solve(const c2<T>* __restrict
     for (int s = 0; s < S; ++s) mbar_init(&mbar[s], 1);
     mbar_init(&rbar[0], 1);
     mbar_init(&rbar[1], 1);
+    mbar_init(&gbar[0], 1);
+    mbar_init(&gbar[1], 1);
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
   __syncthreads();
@@ -396,48 +526,63 @@ __global__ void __launch_bounds__(512, 1) k_coarse_solve(const c2<T>* __restrict
     for (int u = 0; u < min(S, U); ++u) issue(u);
     if (nb > 1) issue_r(1);
   }
-  cluster_sync();   // every CTA initialised before any remote store
+  cluster_sync();   // every CTA's barriers initialised before any remote store
+  const unsigned rx_bytes = (unsigned)(sizeof(V) * B);   // one value per row, from its owner
 
   int u = 0;
   for (int s = 0; s < nsteps; ++s) {
     const bool fwd = s < nb;
     const int blk = fwd ? s : 2 * nb - 2 - s;
-    if (fwd && tid == 0 && blk + 2 < nb) issue_r(blk + 2);
-    // ---- GEMV over the CTA's rows: acc[r] = Dinv[blk][r0+r][:] . zbuf
+    if (tid == 0) {
+      mbar_expect_tx(&gbar[s & 1], rx_bytes);   // arm this step's receive phase (arrival + bytes)
+      if (fwd && blk + 2 < nb) issue_r(blk + 2);
+    }
+    // ---- GEMV: warp w owns rows w, w + nwarps, ... (at most kRPW) of the CTA's
+    // slice of Dinv[blk]; partial sums stay in registers across column chunks.
+    V accr[kRPW];
+#pragma unroll
+    for (int q = 0; q < kRPW; ++q) accr[q] = zero;
     for (int c = 0; c < nchunk; ++c, ++u) {
       int slot = u % S;
       mbar_wait(&mbar[slot], (unsigned)((u / S) & 1), s_err, err);
       const V* st = stage + (size_t)slot * R * CW;
-      int c0 = c * CW, nc = min(CW, B - c0);
-      for (int r = warp; r < nr; r += nwarps) {
-        V sacc = zero;
-        for (int col = lane; col < nc; col += 32) sacc = cfma(st[(size_t)r * CW + col], zbuf[c0 + col], sacc);
-        sacc = warp_sum(sacc);
-        if (lane == 0) acc[r] = c == 0 ? sacc : cadd(acc[r], sacc);
+      const int c0 = c * CW, nc = min(CW, B - c0);
+#pragma unroll
+      for (int q = 0; q < kRPW; ++q) {
+        const int r = warp + q * nwarps;
+        if (r < nr) {
+          V a0 = zero, a1 = zero;   // two chains for ILP
+          int col = lane;
+          for (; col + 32 < nc; col += 64) {
+            a0 = cfma(st[(size_t)r * CW + col], zbuf[c0 + col], a0);
+            a1 = cfma(st[(size_t)r * CW + col + 32], zbuf[c0 + col + 32], a1);
+          }
+          if (col < nc) a0 = cfma(st[(size_t)r * CW + col], zbuf[c0 + col], a0);
+          accr[q] = cadd(accr[q], cadd(a0, a1));
+        }
       }
-      __syncthreads();
+      __syncthreads();   // every warp is done with this stage before it is refilled
       if (tid == 0 && u + S < U) {
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
         issue(u + S);
       }
     }
-    // ---- results of my rows, broadcast to every CTA
+    // ---- row results: lanes 0..CS-1 of the owning warp broadcast to every CTA
     V* gdst = gath + (size_t)(s & 1) * ldb;
-    for (int t = tid; t < nr * (int)CS; t += blockDim.x) {
-      int r = t / CS, dst_rank = t - r * CS;
-      V val;
-      if (fwd) {
-        val = acc[r];
-      } else {
-        val = csub(wrows[(size_t)blk * R + r], acc[r]);
+#pragma unroll
+    for (int q = 0; q < kRPW; ++q) {
+      const int r = warp + q * nwarps;
+      if (r < nr) {
+        V val = warp_sum(accr[q]);
+        if (!fwd) val = csub(wrows[(size_t)blk * R + r], val);
+        if (lane == 0) {
+          if (fwd) wrows[(size_t)blk * R + r] = val;
+          if (!fwd || blk == nb - 1) uc[(size_t)blk * ldb + r0 + r] = val;
+        }
+        if (lane < (int)CS) st_async(gdst + r0 + r, (unsigned)lane, val, &gbar[s & 1]);
       }
-      if (dst_rank == 0) {
-        if (fwd) wrows[(size_t)blk * R + r] = val;
-        if (!fwd || blk == nb - 1) uc[(size_t)blk * ldb + r0 + r] = val;
-      }
-      st_cluster(gdst + r0 + r, (unsigned)dst_rank, val);
     }
-    cluster_sync();
+    mbar_wait_cluster(&gbar[s & 1], (unsigned)((s >> 1) & 1), s_err, err);   // all B values arrived
     // ---- next GEMV input, computed locally from the gathered block
     if (s + 1 < nsteps) {
       const bool down = fwd && blk + 1 < nb;   // z_{blk+1} = r_{blk+1} - A_{blk+1,blk} w_blk
@@ -477,6 +622,10 @@ int plan_coarse_solve(const CoarseLayout& L, const GridDesc& gc, CoarsePlan* pla
   size_t budget = (size_t)optin - 1024;
   cudaFuncSetAttribute(k_coarse_solve<T>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
   for (int CS : {16, 8, 4, 2, 1}) {
+    const int R = (L.B + CS - 1) / CS;
+    // one warp per row of the CTA's slice (up to kRPW rows per warp)
+    const int nwarps = std::min(kSolveMaxWarps, std::max(4, R));
+    if ((R + nwarps - 1) / nwarps > kRPW) continue;
     // widest chunk (even, <= ldb) that leaves room for >= 2 stages
     for (int CW = L.ldb; CW >= 2; CW = ((CW / 2) + 1) & ~1) {
       for (int S = 4; S >= 2; --S) {
@@ -485,7 +634,7 @@ int plan_coarse_solve(const CoarseLayout& L, const GridDesc& gc, CoarsePlan* pla
         cudaFuncSetAttribute(k_coarse_solve<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)budget);
         cudaLaunchConfig_t cfg = {};
         cfg.gridDim = dim3(CS);
-        cfg.blockDim = dim3(512);
+        cfg.blockDim = dim3(32 * nwarps);
         cfg.dynamicSmemBytes = G.total;
         cudaLaunchAttribute at[1];
         at[0].id = cudaLaunchAttributeClusterDimension;
@@ -505,7 +654,7 @@ int plan_coarse_solve(const CoarseLayout& L, const GridDesc& gc, CoarsePlan* pla
         plan->nchunk = G.nchunk;
         plan->S = S;
         plan->smem = G.total;
-        plan->threads = 512;
+        plan->threads = 32 * nwarps;
         return HELM_OK;
       }
       if (CW == 2) break;
@@ -541,22 +690,25 @@ int launch_coarse_factor(c2<T>* Dinv, c2<T>* tmp, c2<T>* piv, unsigned* bar, int
                          const StencilView<T>& Ac, const CoarseLayout& L, int nsm, cudaStream_t s) {
   int ncls = 1;
   for (int ax = 0; ax < Ac.g.dim; ++ax) ncls *= Ac.g.C1;
-  int nblk = nsm;
-  int rpb = (L.B + nblk - 1) / nblk;
+  // one CTA per SM: the update is FP64-bound and every SM must take an equal share
+  const int nblk = std::max(1, std::min(nsm, L.B * L.B));
+  const int64_t epb = ((int64_t)L.B * L.B + nblk - 1) / nblk;
+  const int rows = (int)(epb / L.B) + 3;
   // +256: the grid barrier's static shared flag precedes the 128-byte aligned dynamic window
-  size_t smem = sizeof(c2<T>) * ((size_t)ncls * Ac.g.noff + rpb) + 256;
+  size_t smem = sizeof(c2<T>) * ((size_t)ncls * Ac.g.noff + kGJP * kGJP + (size_t)rows * kGJP) + 256;
+  const size_t rstage = sizeof(c2<T>) * (size_t)kGJP * L.ldb;
+  int stageR = smem + rstage <= 200 * 1024 ? 1 : 0;   // pivot rows in shared memory when they fit
+  if (stageR) smem += rstage;
   int per_sm = 0;
+  cudaFuncSetAttribute(k_factor_block<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_factor_block<T>, 256, smem);
   if (per_sm < 1) return HELM_ENOTSUP;
-  nblk = std::min(nsm * std::min(per_sm, 2), std::max(1, L.B));
-  rpb = (L.B + nblk - 1) / nblk;
-  smem = sizeof(c2<T>) * ((size_t)ncls * Ac.g.noff + rpb) + 256;
   for (int J = 0; J < L.nb; ++J) {
     cudaMemsetAsync(bar, 0, 2 * sizeof(unsigned), s);
     StencilView<T> acv = Ac;
     CoarseLayout lv = L;
     int Jv = J;
-    void* args[] = {&Dinv, &tmp, &piv, &bar, &err, &acv, &lv, &Jv};
+    void* args[] = {&Dinv, &tmp, &piv, &bar, &err, &acv, &lv, &Jv, &stageR};
     cudaError_t e = cudaLaunchCooperativeKernel((void*)k_factor_block<T>, dim3(nblk), dim3(256), args, smem, s);
     if (e != cudaSuccess) return HELM_ECUDA;
   }

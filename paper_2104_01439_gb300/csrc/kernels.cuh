@@ -72,7 +72,9 @@ void launch_coarse_solve(const CoarsePlan& plan, const c2<T>* Dinv, const Stenci
 // host-built coupling lists of the coarse blocks (uploaded once per handle)
 int coupling_max(const GridDesc& g);
 void coupling_lists(const GridDesc& g, const CoarseLayout& L, std::vector<int>& out);
-// Block-Thomas factorisation: Dinv[J] = (A_JJ - A_J,J-1 Dinv[J-1] A_J-1,J)^{-1}
+// Block-Thomas factorisation: Dinv[J] = (A_JJ - A_J,J-1 Dinv[J-1] A_J-1,J)^{-1}.
+// tmp: B x ldb; piv: factor_workspace(L) elements.
+inline size_t factor_workspace(const CoarseLayout& L) { return 2 * 8 * (size_t)L.ldb + 2 * 8 * (size_t)L.B; }
 template <typename T>
 int launch_coarse_factor(c2<T>* Dinv, c2<T>* tmp, c2<T>* piv, unsigned* bar, int* err,
                          const StencilView<T>& Ac, const CoarseLayout& L, int nsm, cudaStream_t s);
