@@ -40,6 +40,8 @@ template <typename T> struct Prec {
   c2<T>* fT = nullptr;
   c2<T>* rc = nullptr;
   c2<T>* uc = nullptr;
+  c2<T>* xmid = nullptr;   // middle-block exchange of the twisted coarse solve (2 x ldb)
+  int* xflag = nullptr;    // its two ready flags
 };
 
 }  // namespace
@@ -199,7 +201,13 @@ int setup_prec(helm_ctx* h, const std::vector<double2>& Ae, const std::vector<do
   CK(h->alloc(&p.fT, sizeof(c2<T>) * Nf));
   CK(h->alloc(&p.rc, sizeof(c2<T>) * Nc));
   CK(h->alloc(&p.uc, sizeof(c2<T>) * Nc));
-  return plan_coarse_solve<T>(h->L, h->gc, &p.plan);
+  CK(h->alloc(&p.xmid, sizeof(c2<T>) * 2 * h->L.ldb));
+  CK(h->alloc(&p.xflag, sizeof(int) * 2));
+  if ((rc = plan_coarse_solve<T>(h->L, h->gc, &p.plan))) return rc;
+  // the elimination order (one chain, or two chains meeting in the middle) is fixed
+  // here, before the factorisation, and used by both the factor and the solve
+  h->L.mid = p.plan.ncl == 2 ? h->L.nb / 2 : h->L.nb - 1;
+  return HELM_OK;
 }
 
 // One V(nu,nu)-cycle on A_eps (Algorithm 1, two levels): z = Vcycle(f), u^0 = 0.
@@ -229,7 +237,7 @@ void enqueue_vcycle(helm_ctx* h, VecSel<const double2> f, VecSel<double2> z, con
   launch_residual<T, V, V>(Ae, fT, cur, p.r, active, s);
   launch_restrict<T>(P, h->L, p.r, p.rc, active, s);
   if (prof) cudaEventRecord(prof->ev[ev0 + 1], s);
-  launch_coarse_solve<T>(p.plan, p.Dinv, Ac, h->L, h->cpl, p.rc, p.uc, h->err, active, s);
+  launch_coarse_solve<T>(p.plan, p.Dinv, Ac, h->L, h->cpl, p.rc, p.uc, p.xmid, p.xflag, h->err, active, s);
   if (prof) cudaEventRecord(prof->ev[ev0 + 2], s);
   launch_prolong_add<T>(P, h->L, p.uc, cur, active, s);
   for (int it = 0; it < nu; ++it) {   // postsmoothing
@@ -517,6 +525,7 @@ static int setup_impl(helm_ctx* h) {
   L.nb = (h->gc.W + L.rows - 1) / L.rows;
   L.B = L.rows * L.plane;
   L.ldb = (L.B + 1) & ~1;
+  L.mid = L.nb - 1;   // single chain unless the solve plan runs two clusters (set below)
   {
     std::vector<int> lists;
     coupling_lists(h->gc, L, lists);
@@ -534,9 +543,9 @@ static int setup_impl(helm_ctx* h) {
   double2 *tmp = nullptr, *piv = nullptr;
   unsigned* bar = nullptr;
   CK(cudaMalloc(&D64, sizeof(double2) * blk * L.nb));
-  CK(cudaMalloc(&tmp, sizeof(double2) * blk));
-  CK(cudaMalloc(&piv, sizeof(double2) * factor_workspace(L)));
-  CK(cudaMalloc(&bar, 2 * sizeof(unsigned)));
+  CK(cudaMalloc(&tmp, sizeof(double2) * 2 * blk));
+  CK(cudaMalloc(&piv, sizeof(double2) * 2 * factor_workspace(L)));
+  CK(cudaMalloc(&bar, 4 * sizeof(unsigned)));
   CK(h->alloc(&h->err, sizeof(int)));
   CK(cudaMemsetAsync(h->err, 0, sizeof(int), s));
   CK(cudaEventRecord(h->e0, s));
@@ -744,13 +753,13 @@ int helm_coarse_solve(helm_t h, const void* rc_nat, void* uc_nat) {
     Prec<float>& p = h->p32;
     launch_coarse_pack<double2, float2>(h->gc, h->L, (const double2*)rc_nat, p.rc, h->s);
     launch_coarse_solve<float>(p.plan, p.Dinv, make_view<float>(h->gc, p.coefAc, nullptr), h->L, h->cpl, p.rc,
-                               p.uc, h->err, nullptr, h->s);
+                               p.uc, p.xmid, p.xflag, h->err, nullptr, h->s);
     launch_coarse_unpack<float2, double2>(h->gc, h->L, p.uc, (double2*)uc_nat, h->s);
   } else {
     Prec<double>& p = h->p64;
     launch_coarse_pack<double2, double2>(h->gc, h->L, (const double2*)rc_nat, p.rc, h->s);
     launch_coarse_solve<double>(p.plan, p.Dinv, make_view<double>(h->gc, p.coefAc, nullptr), h->L,
-                                h->cpl, p.rc, p.uc, h->err, nullptr, h->s);
+                                h->cpl, p.rc, p.uc, p.xmid, p.xflag, h->err, nullptr, h->s);
     launch_coarse_unpack<double2, double2>(h->gc, h->L, p.uc, (double2*)uc_nat, h->s);
   }
   CK(cudaGetLastError());
@@ -830,7 +839,7 @@ int coarse_solve_noalloc(helm_t h, const double2* rc_nat, double2* uc_nat) {
   CK(cudaMemsetAsync(h->err, 0, sizeof(int), h->s));   // the error word must start at zero
   launch_coarse_pack<double2, V>(h->gc, h->L, rc_nat, pad_rc, h->s);   // writes every padded entry
   launch_coarse_solve<T>(p.plan, p.Dinv, make_view<T>(h->gc, p.coefAc, nullptr), h->L, h->cpl, pad_rc, pad_uc,
-                         h->err, nullptr, h->s);
+                         p.xmid, p.xflag, h->err, nullptr, h->s);
   launch_coarse_unpack<V, double2>(h->gc, h->L, pad_uc, uc_nat, h->s);
   CK(cudaGetLastError());
   CK(cudaStreamSynchronize(h->s));

@@ -137,6 +137,9 @@ __device__ __forceinline__ void mbar_wait_cluster(uint64_t* bar, unsigned parity
   atomicExch(err, HELM_ETIMEOUT);
 }
 
+__device__ __forceinline__ float2 cvt_ldcg(const float2* p) { return __ldcg(p); }
+__device__ __forceinline__ double2 cvt_ldcg(const double2* p) { return __ldcg(p); }
+
 template <typename V> __device__ __forceinline__ V warp_sum(V v) {
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) {
@@ -189,10 +192,20 @@ __device__ __forceinline__ bool neighbour(const GridDesc& g, const CoarseLayout&
 // ---------------------------------------------------------------------------
 constexpr int kGJP = 8;   // pivots per Gauss-Jordan panel (factor_workspace assumes 8)
 
+// One block to invert: S_J = A_JJ - sum over factored neighbours Jn = J + d of
+// A_{J,Jn} Dinv[Jn] A_{Jn,J}  (d = -1: block J-1 of the top chain or the middle;
+// d = +1: block J+1 of the bottom chain or the middle), then Dinv[J] = S_J^{-1}.
+struct FactorJob {
+  int J;
+  int ndir;
+  int dir[2];
+};
+
 template <typename T>
 __global__ void __launch_bounds__(256) k_factor_block(c2<T>* D, c2<T>* Tmp, c2<T>* piv,
                                                       unsigned* bar, int* err, StencilView<T> Ac,
-                                                      CoarseLayout L, int J, int stageR) {
+                                                      CoarseLayout L, FactorJob job0, FactorJob job1,
+                                                      int njobs, int stageR) {
   using V = c2<T>;
   extern __shared__ __align__(128) unsigned char sm[];
   const GridDesc g = Ac.g;
@@ -203,13 +216,24 @@ __global__ void __launch_bounds__(256) k_factor_block(c2<T>* D, c2<T>* Tmp, c2<T
   __syncthreads();
   const int B = L.B, ldb = L.ldb;
   const int64_t blk = (int64_t)B * ldb;
+  // two independent jobs (top and bottom chain) share the grid: each half has its
+  // own barrier state and workspaces
+  const int half = njobs == 2 ? (int)gridDim.x / 2 : (int)gridDim.x;
+  const int grp = (njobs == 2 && (int)blockIdx.x >= half) ? 1 : 0;
+  const int G = grp ? (int)gridDim.x - half : half;
+  const int lb = (int)blockIdx.x - (grp ? half : 0);
+  const FactorJob job = grp ? job1 : job0;
+  const int J = job.J;
+  Tmp += grp * blk;
+  piv += grp * (int64_t)factor_workspace(L);
+  bar += 2 * grp;
   V* S = D + J * blk;
-  const V* X = J > 0 ? D + (J - 1) * blk : nullptr;
-  const int gt = blockIdx.x * blockDim.x + threadIdx.x, gs = gridDim.x * blockDim.x;
+  const int gt = lb * blockDim.x + threadIdx.x, gs = G * blockDim.x;
   const V zero = mk(T(0), T(0));
 
-  // Tmp[a][l] = sum_{o: l+o in block J-1} A[l][l+o] X[a][l+o]   (= X A_{J-1,J})
-  if (J > 0) {
+  // Tmp[a][l] = sum_{o: l+o in block J+d} A[l][l+o] Dinv[J+d][a][l+o]   (= Dinv[J+d] A_{J+d,J})
+  auto tmp_phase = [&](int d) {
+    const V* X = D + (J + d) * blk;
     for (int64_t idx = gt; idx < (int64_t)B * B; idx += gs) {
       int aa = (int)(idx / B), l = (int)(idx - (int64_t)aa * B);
       int c[3];
@@ -218,15 +242,19 @@ __global__ void __launch_bounds__(256) k_factor_block(c2<T>* D, c2<T>* Tmp, c2<T
         const V* cl = coef + class_at(g, c) * g.noff;
         for (int o = 0; o < g.noff; ++o) {
           int Jn, in;
-          if (!neighbour(g, L, Ac.dx, o, c, &Jn, &in) || Jn != J - 1) continue;
+          if (!neighbour(g, L, Ac.dx, o, c, &Jn, &in) || Jn != J + d) continue;
           acc = cfma(cl[o], X[(int64_t)aa * ldb + in], acc);
         }
       }
       Tmp[(int64_t)aa * ldb + l] = acc;
     }
-    if (!grid_barrier(bar, err, gridDim.x)) return;
-  }
-  // S[i][l] = A_JJ[i][l] - sum_{o: i+o in block J-1} A[i][i+o] Tmp[i+o][l]; zero padding columns
+  };
+  // snapshots of the first Gauss-Jordan panel (pivot rows and columns)
+  auto snapshot = [&](int i, int l, V v) {
+    if (l < B && i < kGJP) piv[(int64_t)i * ldb + l] = v;
+    if (l < kGJP && l < B) piv[2 * kGJP * (int64_t)ldb + (int64_t)i * kGJP + l] = v;
+  };
+  // S = A_JJ (identity on padding rows, zero padding columns)
   for (int64_t idx = gt; idx < (int64_t)B * ldb; idx += gs) {
     int i = (int)(idx / ldb), l = (int)(idx - (int64_t)i * ldb);
     V v = zero;
@@ -241,27 +269,45 @@ __global__ void __launch_bounds__(256) k_factor_block(c2<T>* D, c2<T>* Tmp, c2<T
         int o = 0, mul = 1;
         bool in = true;
         for (int ax = 0; ax < g.dim; ++ax) {
-          int d = cl[ax] - ci[ax];
-          in &= (d >= -g.R && d <= g.R);
-          o += (d + g.R) * mul;
+          int dd = cl[ax] - ci[ax];
+          in &= (dd >= -g.R && dd <= g.R);
+          o += (dd + g.R) * mul;
           mul *= 2 * g.R + 1;
         }
         if (in) v = c[o];
-        if (J > 0) {
-          for (int oo = 0; oo < g.noff; ++oo) {
-            int Jn, inb;
-            if (!neighbour(g, L, Ac.dx, oo, ci, &Jn, &inb) || Jn != J - 1) continue;
-            V t = Tmp[(int64_t)inb * ldb + l];
-            v = csub(v, cmul(c[oo], t));
-          }
-        }
       }
     }
     S[idx] = v;
-    if (l < B && i < kGJP) piv[(int64_t)i * ldb + l] = v;                          // pivot rows of panel 0
-    if (l < kGJP && l < B) piv[2 * kGJP * (int64_t)ldb + (int64_t)i * kGJP + l] = v;   // its columns
+    if (job.ndir == 0) snapshot(i, l, v);
   }
-  if (!grid_barrier(bar, err, gridDim.x)) return;
+  if (job.ndir > 0) tmp_phase(job.dir[0]);
+  if (!grid_barrier(bar, err, G)) return;
+  // S[i][l] -= sum_{o: i+o in block J+d} A[i][i+o] Tmp[i+o][l], for each factored neighbour
+  for (int q = 0; q < job.ndir; ++q) {
+    const int d = job.dir[q];
+    if (q > 0) {
+      tmp_phase(d);
+      if (!grid_barrier(bar, err, G)) return;
+    }
+    const bool last = q == job.ndir - 1;
+    for (int64_t idx = gt; idx < (int64_t)B * ldb; idx += gs) {
+      int i = (int)(idx / ldb), l = (int)(idx - (int64_t)i * ldb);
+      if (l >= B) continue;
+      V v = S[idx];
+      int ci[3];
+      if (block_coords(g, L, J, i, ci)) {
+        const V* c = coef + class_at(g, ci) * g.noff;
+        for (int oo = 0; oo < g.noff; ++oo) {
+          int Jn, inb;
+          if (!neighbour(g, L, Ac.dx, oo, ci, &Jn, &inb) || Jn != J + d) continue;
+          v = csub(v, cmul(c[oo], Tmp[(int64_t)inb * ldb + l]));
+        }
+        S[idx] = v;
+      }
+      if (last) snapshot(i, l, v);
+    }
+    if (!grid_barrier(bar, err, G)) return;
+  }
 
   // In-place blocked Gauss-Jordan inversion of S (no pivoting), kGJP pivots per
   // panel. For the panel block P = S[k0:k1, k0:k1] with pivot rows R = S[k0:k1, :]
@@ -272,10 +318,9 @@ __global__ void __launch_bounds__(256) k_factor_block(c2<T>* D, c2<T>* Tmp, c2<T
   // itself; R and C are read from snapshots written while the previous panel was
   // updated, so each panel needs a single grid barrier. The B x B elements are
   // split into contiguous row-major ranges, one per CTA (FP64 work is balanced).
-  const int G = gridDim.x;
   const int64_t BB = (int64_t)B * B;
   const int64_t epb = (BB + G - 1) / G;
-  const int64_t e0 = (int64_t)blockIdx.x * epb, e1 = min(BB, e0 + epb);
+  const int64_t e0 = (int64_t)lb * epb, e1 = min(BB, e0 + epb);
   const int i0 = (int)(e0 / B), i1 = e1 > e0 ? (int)((e1 - 1) / B) : i0 - 1;   // rows touched
   V* Pm = coef + ncls * g.noff;                 // kGJP x kGJP panel block -> its inverse
   V* cP = Pm + kGJP * kGJP;                     // (rows touched) x kGJP : C_i P^{-1}
@@ -385,7 +430,7 @@ __global__ void __launch_bounds__(256) k_factor_block(c2<T>* D, c2<T>* Tmp, c2<T
         if (j >= k1 && j < k2) Cn[(int64_t)i * kGJP + (j - k1)] = nv;
       }
     }
-    if (!grid_barrier(bar, err, gridDim.x)) return;
+    if (!grid_barrier(bar, err, G)) return;
   }
 }
 
@@ -445,6 +490,7 @@ __global__ void __launch_bounds__(kSolveMaxWarps * 32, 1) k_coarse_solve(const c
                                                         CoarseLayout L, SolveGeom G,
                                                         const int* __restrict__ cpl,
                                                         const c2<T>* __restrict__ rc, c2<T>* __restrict__ uc,
+                                                        c2<T>* xmid, int* xflag,
                                                         int* err, const int* active) {
   using V = c2<T>;
   if (active && *active == 0) return;
@@ -455,7 +501,6 @@ __global__ void __launch_bounds__(kSolveMaxWarps * 32, 1) k_coarse_solve(const c
   V* zbuf = reinterpret_cast<V*>(sm + G.off_z);
   V* gath = reinterpret_cast<V*>(sm + G.off_gath);
   V* rbuf = reinterpret_cast<V*>(sm + G.off_rbuf);
-  V* acc = reinterpret_cast<V*>(sm + G.off_acc);
   V* wrows = reinterpret_cast<V*>(sm + G.off_w);
   V* stage = reinterpret_cast<V*>(sm + G.off_stage);
   int* clo = reinterpret_cast<int*>(sm + G.off_clo);   // [B] in-plane class part, [B] row in block
@@ -468,10 +513,25 @@ __global__ void __launch_bounds__(kSolveMaxWarps * 32, 1) k_coarse_solve(const c
   const unsigned rank = cluster_rank(), CS = cluster_size();
   const int B = L.B, ldb = L.ldb, nb = L.nb, R = G.R, CW = G.CW, nchunk = G.nchunk, S = G.S;
   const int r0 = (int)rank * R, r1 = min(B, r0 + R), nr = max(0, r1 - r0);
-  const int nsteps = 2 * nb - 1, U = nsteps * nchunk;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nwarps = blockDim.x >> 5;
   const int maxc = G.maxc;
   const V zero = mk(T(0), T(0));
+
+  // This cluster's elimination chain. Cluster 0: forward over blocks 0..mid-1;
+  // cluster 1 (twisted launch): forward over blocks nb-1..mid+1. Both then solve
+  // the middle block (its right-hand side takes both chains' couplings) and run
+  // their backward sweeps outwards.
+  const int ncl = (int)(gridDim.x / CS);
+  unsigned cidu;
+  asm volatile("mov.u32 %0, %%clusterid.x;" : "=r"(cidu));
+  const int cid = ncl > 1 ? (int)cidu : 0;
+  const int m = L.mid, dir = cid == 0 ? 1 : -1, J0 = cid == 0 ? 0 : nb - 1;
+  const int nf = cid == 0 ? m : nb - 1 - m;
+  const int nsteps = 2 * nf + 1, U = nsteps * nchunk;
+  auto blockof = [&](int t) { return t < nf ? J0 + dir * t : (t == nf ? m : m - dir * (t - nf)); };
+  const int* lfwd = dir > 0 ? dn : up;   // couplings into the next block of the forward sweep
+  const int* lbwd = dir > 0 ? up : dn;   // couplings into the next block of the backward sweep
+
   int ncls = 1, cmul_last = 1;
   for (int ax = 0; ax < g.dim; ++ax) ncls *= g.C1;
   for (int ax = 0; ax < g.dim - 1; ++ax) cmul_last *= g.C1;
@@ -480,12 +540,12 @@ __global__ void __launch_bounds__(kSolveMaxWarps * 32, 1) k_coarse_solve(const c
   // coupling lists (built on the host by coupling_lists): plain copy
   for (int i = tid; i < 2 * B + 2 * B * maxc; i += blockDim.x) clo[i] = cpl[i];
   for (int i = tid; i < ldb; i += blockDim.x) {
-    zbuf[i] = rc[i];   // z_0 = r_0
+    zbuf[i] = nf > 0 ? rc[(size_t)J0 * ldb + i] : zero;   // first forward input z = r
     gath[i] = zero;
     gath[ldb + i] = zero;
   }
   if (tid == 0) {
-    for (int s = 0; s < S; ++s) mbar_init(&mbar[s], 1);
+    for (int q = 0; q < S; ++q) mbar_init(&mbar[q], 1);
     mbar_init(&rbar[0], 1);
     mbar_init(&rbar[1], 1);
     mbar_init(&gbar[0], 1);
@@ -494,10 +554,10 @@ __global__ void __launch_bounds__(kSolveMaxWarps * 32, 1) k_coarse_solve(const c
   }
   __syncthreads();
 
-  // producer: unit u = (step s, chunk c) -> stage slot u % S
+  // producer: unit u = (step t, chunk c) -> stage slot u % S
   auto issue = [&](int u) {
-    int s = u / nchunk, c = u - s * nchunk;
-    int blk = s < nb ? s : 2 * nb - 2 - s;
+    int t = u / nchunk, c = u - t * nchunk;
+    int blk = blockof(t);
     int slot = u % S;
     V* dst = stage + (size_t)slot * R * CW;
     const V* src = Dinv + ((size_t)blk * B + r0) * ldb;
@@ -516,26 +576,71 @@ __global__ void __launch_bounds__(kSolveMaxWarps * 32, 1) k_coarse_solve(const c
       for (int r = 0; r < nr; ++r) bulk_g2s(dst + (size_t)r * CW, src + (size_t)r * ldb + c0, bytes, &mbar[slot]);
     }
   };
-  auto issue_r = [&](int b) {   // rc block b into rbuf[b & 1]
+  auto issue_r = [&](int t) {   // right-hand side block of step t (1 <= t <= nf) into rbuf[t & 1]
     unsigned bytes = (unsigned)(sizeof(V) * ldb);
-    mbar_expect_tx(&rbar[b & 1], bytes);
-    bulk_g2s(rbuf + (size_t)(b & 1) * ldb, rc + (size_t)b * ldb, bytes, &rbar[b & 1]);
+    mbar_expect_tx(&rbar[t & 1], bytes);
+    bulk_g2s(rbuf + (size_t)(t & 1) * ldb, rc + (size_t)blockof(t) * ldb, bytes, &rbar[t & 1]);
   };
   if (tid == 0) {
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
     for (int u = 0; u < min(S, U); ++u) issue(u);
-    if (nb > 1) issue_r(1);
+    if (nf >= 1) issue_r(1);
   }
   cluster_sync();   // every CTA's barriers initialised before any remote store
   const unsigned rx_bytes = (unsigned)(sizeof(V) * B);   // one value per row, from its owner
 
+  // Middle-block right-hand side: zbuf holds this chain's coupling g; afterwards
+  // zbuf = r_mid - g - g_other, g_other published by the other cluster through
+  // global memory (release flag / bounded acquire spin).
+  auto finish_mid = [&](const V* rm) {
+    if (ncl > 1) {
+      if (rank == 0) {
+        for (int i = tid; i < B; i += blockDim.x) xmid[(size_t)cid * ldb + i] = zbuf[i];
+        __syncthreads();
+        if (tid == 0) {
+          __threadfence();
+          atomicExch(&xflag[cid], 1);
+        }
+      }
+      if (tid == 0) {
+        int ok = 0;
+        for (long long it = 0; it < (1ll << 24); ++it) {
+          int f;
+          asm volatile("ld.acquire.gpu.global.b32 %0, [%1];" : "=r"(f) : "l"(xflag + (1 - cid)) : "memory");
+          if (f) {
+            ok = 1;
+            break;
+          }
+          if (*(volatile int*)s_err) break;
+        }
+        if (!ok) {
+          *(volatile int*)s_err = 1;
+          atomicExch(err, HELM_ETIMEOUT);
+        }
+        __threadfence();
+      }
+      __syncthreads();
+      const V* other = xmid + (size_t)(1 - cid) * ldb;
+      for (int i = tid; i < B; i += blockDim.x) {
+        V o = cvt_ldcg(other + i);
+        zbuf[i] = csub(csub(rm[i], zbuf[i]), o);
+      }
+    } else {
+      for (int i = tid; i < B; i += blockDim.x) zbuf[i] = csub(rm[i], zbuf[i]);
+    }
+  };
+  if (nf == 0) {   // the chain is empty: the middle block is the first step
+    finish_mid(rc + (size_t)m * ldb);
+    __syncthreads();
+  }
+
   int u = 0;
-  for (int s = 0; s < nsteps; ++s) {
-    const bool fwd = s < nb;
-    const int blk = fwd ? s : 2 * nb - 2 - s;
+  for (int t = 0; t < nsteps; ++t) {
+    const int blk = blockof(t);
+    const int kind = t < nf ? 0 : (t == nf ? 1 : 2);   // forward / middle / backward
     if (tid == 0) {
-      mbar_expect_tx(&gbar[s & 1], rx_bytes);   // arm this step's receive phase (arrival + bytes)
-      if (fwd && blk + 2 < nb) issue_r(blk + 2);
+      mbar_expect_tx(&gbar[t & 1], rx_bytes);   // arm this step's receive phase (arrival + bytes)
+      if (t + 2 <= nf) issue_r(t + 2);
     }
     // ---- GEMV: warp w owns rows w, w + nwarps, ... (at most kRPW) of the CTA's
     // slice of Dinv[blk]; partial sums stay in registers across column chunks.
@@ -568,28 +673,28 @@ __global__ void __launch_bounds__(kSolveMaxWarps * 32, 1) k_coarse_solve(const c
       }
     }
     // ---- row results: lanes 0..CS-1 of the owning warp broadcast to every CTA
-    V* gdst = gath + (size_t)(s & 1) * ldb;
+    V* gdst = gath + (size_t)(t & 1) * ldb;
 #pragma unroll
     for (int q = 0; q < kRPW; ++q) {
       const int r = warp + q * nwarps;
       if (r < nr) {
         V val = warp_sum(accr[q]);
-        if (!fwd) val = csub(wrows[(size_t)blk * R + r], val);
+        if (kind == 2) val = csub(wrows[(size_t)(2 * nf - t) * R + r], val);   // x = w - Dinv q
         if (lane == 0) {
-          if (fwd) wrows[(size_t)blk * R + r] = val;
-          if (!fwd || blk == nb - 1) uc[(size_t)blk * ldb + r0 + r] = val;
+          if (kind == 0) wrows[(size_t)t * R + r] = val;
+          if (kind == 2 || (kind == 1 && cid == 0)) uc[(size_t)blk * ldb + r0 + r] = val;
         }
-        if (lane < (int)CS) st_async(gdst + r0 + r, (unsigned)lane, val, &gbar[s & 1]);
+        if (lane < (int)CS) st_async(gdst + r0 + r, (unsigned)lane, val, &gbar[t & 1]);
       }
     }
-    mbar_wait_cluster(&gbar[s & 1], (unsigned)((s >> 1) & 1), s_err, err);   // all B values arrived
+    mbar_wait_cluster(&gbar[t & 1], (unsigned)((t >> 1) & 1), s_err, err);   // all B values arrived
     // ---- next GEMV input, computed locally from the gathered block
-    if (s + 1 < nsteps) {
-      const bool down = fwd && blk + 1 < nb;   // z_{blk+1} = r_{blk+1} - A_{blk+1,blk} w_blk
-      const int Jd = down ? blk + 1 : blk - 1; // else q_{blk-1} = A_{blk-1,blk} x_blk
-      const int* lst = down ? dn : up;
-      const V* rb = rbuf + (size_t)(Jd & 1) * ldb;
-      if (down) mbar_wait(&rbar[Jd & 1], (unsigned)(((Jd - 1) >> 1) & 1), s_err, err);
+    if (t + 1 < nsteps) {
+      const int Jd = blockof(t + 1);
+      const bool fw = t + 1 <= nf;   // next step is forward or the middle: coupling of w
+      const int* lst = fw ? lfwd : lbwd;
+      const V* rb = rbuf + (size_t)((t + 1) & 1) * ldb;
+      if (fw) mbar_wait(&rbar[(t + 1) & 1], (unsigned)((t >> 1) & 1), s_err, err);
       for (int i = tid; i < B; i += blockDim.x) {
         const int lastc = Jd * L.rows + clo[B + i];
         V a = zero;
@@ -600,11 +705,15 @@ __global__ void __launch_bounds__(kSolveMaxWarps * 32, 1) k_coarse_solve(const c
             if (e < 0) break;
             a = cfma(c[e & 255], gdst[e >> 8], a);
           }
-          if (down) a = csub(rb[i], a);
+          if (fw && t + 1 < nf) a = csub(rb[i], a);
         }
         zbuf[i] = a;
       }
       __syncthreads();
+      if (t + 1 == nf) {   // next: the middle block
+        finish_mid(rb);
+        __syncthreads();
+      }
     }
   }
   cluster_sync();
@@ -655,6 +764,32 @@ int plan_coarse_solve(const CoarseLayout& L, const GridDesc& gc, CoarsePlan* pla
         plan->S = S;
         plan->smem = G.total;
         plan->threads = 32 * nwarps;
+        plan->ncl = 1;
+        // Twisted form: two co-resident clusters (cooperative launch). Validated by an
+        // inert trial launch whose 'active' flag is 0 (the kernel returns at entry).
+        if (L.nb >= 4 && ncl >= 2) {
+          int* off = nullptr;
+          if (cudaMalloc(&off, sizeof(int)) == cudaSuccess) {
+            cudaMemset(off, 0, sizeof(int));
+            CoarseLayout L2 = L;
+            L2.mid = L.nb / 2;
+            cudaLaunchAttribute at2[2];
+            at2[0] = at[0];
+            at2[1].id = cudaLaunchAttributeCooperative;
+            at2[1].val.cooperative = 1;
+            cfg.gridDim = dim3(2 * CS);
+            cfg.attrs = at2;
+            cfg.numAttrs = 2;
+            StencilView<T> nov{};
+            cudaError_t e = cudaLaunchKernelEx(&cfg, k_coarse_solve<T>, (const c2<T>*)nullptr, nov, L2, G,
+                                               (const int*)nullptr, (const c2<T>*)nullptr, (c2<T>*)nullptr,
+                                               (c2<T>*)nullptr, (int*)nullptr, (int*)nullptr, (const int*)off);
+            if (e == cudaSuccess) e = cudaDeviceSynchronize();
+            if (e == cudaSuccess) plan->ncl = 2;
+            cudaGetLastError();
+            cudaFree(off);
+          }
+        }
         return HELM_OK;
       }
       if (CW == 2) break;
@@ -665,24 +800,29 @@ int plan_coarse_solve(const CoarseLayout& L, const GridDesc& gc, CoarsePlan* pla
 
 template <typename T>
 void launch_coarse_solve(const CoarsePlan& plan, const c2<T>* Dinv, const StencilView<T>& Ac,
-                         const CoarseLayout& L, const int* cpl, const c2<T>* rc, c2<T>* uc, int* err,
-                         const int* active, cudaStream_t s) {
+                         const CoarseLayout& L, const int* cpl, const c2<T>* rc, c2<T>* uc, c2<T>* xmid,
+                         int* xflag, int* err, const int* active, cudaStream_t s) {
   SolveGeom G = solve_geometry<T>(L, Ac.g, plan.CS, plan.CW, plan.S);
   // (the function's dynamic shared-memory cap was raised to the device limit by
   // plan_coarse_solve, outside any stream capture)
+  const int ncl = L.mid < L.nb - 1 ? 2 : 1;
+  if (ncl > 1) cudaMemsetAsync(xflag, 0, 2 * sizeof(int), s);
   cudaLaunchConfig_t cfg = {};
-  cfg.gridDim = dim3(plan.CS);
+  cfg.gridDim = dim3(plan.CS * ncl);
   cfg.blockDim = dim3(plan.threads);
   cfg.dynamicSmemBytes = G.total;
   cfg.stream = s;
-  cudaLaunchAttribute at[1];
+  cudaLaunchAttribute at[2];
   at[0].id = cudaLaunchAttributeClusterDimension;
   at[0].val.clusterDim.x = plan.CS;
   at[0].val.clusterDim.y = 1;
   at[0].val.clusterDim.z = 1;
+  // the two clusters exchange the middle block's couplings: they must be co-resident
+  at[1].id = cudaLaunchAttributeCooperative;
+  at[1].val.cooperative = 1;
   cfg.attrs = at;
-  cfg.numAttrs = 1;
-  cudaLaunchKernelEx(&cfg, k_coarse_solve<T>, Dinv, Ac, L, G, cpl, rc, uc, err, active);
+  cfg.numAttrs = ncl > 1 ? 2 : 1;
+  cudaLaunchKernelEx(&cfg, k_coarse_solve<T>, Dinv, Ac, L, G, cpl, rc, uc, xmid, xflag, err, active);
 }
 
 template <typename T>
@@ -690,11 +830,12 @@ int launch_coarse_factor(c2<T>* Dinv, c2<T>* tmp, c2<T>* piv, unsigned* bar, int
                          const StencilView<T>& Ac, const CoarseLayout& L, int nsm, cudaStream_t s) {
   int ncls = 1;
   for (int ax = 0; ax < Ac.g.dim; ++ax) ncls *= Ac.g.C1;
-  // one CTA per SM: the update is FP64-bound and every SM must take an equal share
-  const int nblk = std::max(1, std::min(nsm, L.B * L.B));
-  const int64_t epb = ((int64_t)L.B * L.B + nblk - 1) / nblk;
+  // one CTA per SM: the update is FP64-bound and every SM must take an equal share;
+  // while both chains run, each half of the grid owns one of them
+  const int nblk = std::max(2, std::min(nsm, L.B * L.B));
+  const int64_t epb = ((int64_t)L.B * L.B + nblk / 2 - 1) / (nblk / 2);
   const int rows = (int)(epb / L.B) + 3;
-  // +256: the grid barrier's static shared flag precedes the 128-byte aligned dynamic window
+  // +256: the grid barrier's static shared flags precede the 128-byte aligned dynamic window
   size_t smem = sizeof(c2<T>) * ((size_t)ncls * Ac.g.noff + kGJP * kGJP + (size_t)rows * kGJP) + 256;
   const size_t rstage = sizeof(c2<T>) * (size_t)kGJP * L.ldb;
   int stageR = smem + rstage <= 200 * 1024 ? 1 : 0;   // pivot rows in shared memory when they fit
@@ -703,16 +844,30 @@ int launch_coarse_factor(c2<T>* Dinv, c2<T>* tmp, c2<T>* piv, unsigned* bar, int
   cudaFuncSetAttribute(k_factor_block<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_factor_block<T>, 256, smem);
   if (per_sm < 1) return HELM_ENOTSUP;
-  for (int J = 0; J < L.nb; ++J) {
-    cudaMemsetAsync(bar, 0, 2 * sizeof(unsigned), s);
+  // top chain J = 0..mid-1 and bottom chain J = nb-1..mid+1 run concurrently, then
+  // the middle block mid takes both neighbours (non-twisted: mid = nb-1, no bottom chain)
+  const int m = L.mid, nf_top = m, nf_bot = L.nb - 1 - m;
+  auto launch = [&](FactorJob j0, FactorJob j1, int njobs) -> int {
+    cudaMemsetAsync(bar, 0, 4 * sizeof(unsigned), s);
     StencilView<T> acv = Ac;
     CoarseLayout lv = L;
-    int Jv = J;
-    void* args[] = {&Dinv, &tmp, &piv, &bar, &err, &acv, &lv, &Jv, &stageR};
+    void* args[] = {&Dinv, &tmp, &piv, &bar, &err, &acv, &lv, &j0, &j1, &njobs, &stageR};
     cudaError_t e = cudaLaunchCooperativeKernel((void*)k_factor_block<T>, dim3(nblk), dim3(256), args, smem, s);
-    if (e != cudaSuccess) return HELM_ECUDA;
+    return e == cudaSuccess ? HELM_OK : HELM_ECUDA;
+  };
+  for (int t = 0; t < std::max(nf_top, nf_bot); ++t) {
+    FactorJob top{t, t > 0 ? 1 : 0, {-1, 0}};
+    FactorJob bot{L.nb - 1 - t, t > 0 ? 1 : 0, {+1, 0}};
+    int rc;
+    if (t < nf_top && t < nf_bot) rc = launch(top, bot, 2);
+    else if (t < nf_top) rc = launch(top, top, 1);
+    else rc = launch(bot, bot, 1);
+    if (rc) return rc;
   }
-  return HELM_OK;
+  FactorJob mid{m, 0, {0, 0}};
+  if (m > 0) mid.dir[mid.ndir++] = -1;
+  if (m < L.nb - 1) mid.dir[mid.ndir++] = +1;
+  return launch(mid, mid, 1);
 }
 
 int coupling_max(const GridDesc& g) {
@@ -773,11 +928,11 @@ void launch_convert_factor(const double2* src, float2* dst, size_t n, cudaStream
 template int plan_coarse_solve<float>(const CoarseLayout&, const GridDesc&, CoarsePlan*);
 template int plan_coarse_solve<double>(const CoarseLayout&, const GridDesc&, CoarsePlan*);
 template void launch_coarse_solve<float>(const CoarsePlan&, const float2*, const StencilView<float>&,
-                                         const CoarseLayout&, const int*, const float2*, float2*, int*,
-                                         const int*, cudaStream_t);
+                                         const CoarseLayout&, const int*, const float2*, float2*, float2*,
+                                         int*, int*, const int*, cudaStream_t);
 template void launch_coarse_solve<double>(const CoarsePlan&, const double2*, const StencilView<double>&,
-                                          const CoarseLayout&, const int*, const double2*, double2*, int*,
-                                          const int*, cudaStream_t);
+                                          const CoarseLayout&, const int*, const double2*, double2*,
+                                          double2*, int*, int*, const int*, cudaStream_t);
 template int launch_coarse_factor<double>(double2*, double2*, double2*, unsigned*, int*,
                                           const StencilView<double>&, const CoarseLayout&, int, cudaStream_t);
 template int launch_coarse_factor<float>(float2*, float2*, float2*, unsigned*, int*,

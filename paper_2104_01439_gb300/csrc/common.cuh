@@ -118,6 +118,8 @@ struct CoarseLayout {
   int ldb;      // padded row length / block stride of vectors (even, >= B)
   int rows;     // lattice rows (or planes) per block = q
   int plane;    // W^(dim-1)
+  int mid;      // middle block: top chain 0..mid-1 and bottom chain nb-1..mid+1 meet here
+                // (twisted elimination); mid = nb-1 means a single top-down chain
 };
 
 #if defined(__CUDACC__)

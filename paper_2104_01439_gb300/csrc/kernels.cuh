@@ -55,6 +55,7 @@ void launch_coarse_unpack(const GridDesc& gc, const CoarseLayout& L, const Vin* 
 
 // ---- coarse level (coarse.cu) ----------------------------------------------
 struct CoarsePlan {
+  int ncl;      // clusters: 2 = twisted (top and bottom chains), 1 = single chain
   int CS;       // cluster size
   int R;        // rows per CTA
   int CW;       // columns per pipeline chunk (even)
@@ -65,16 +66,19 @@ struct CoarsePlan {
 };
 template <typename T>
 int plan_coarse_solve(const CoarseLayout& L, const GridDesc& gc, CoarsePlan* plan);
+// uc = A^{-1} rc for the block-padded coarse vectors; L.mid < L.nb - 1 runs the
+// twisted form on two clusters (xmid: 2 x ldb, xflag: 2 ints of exchange space).
 template <typename T>
 void launch_coarse_solve(const CoarsePlan& plan, const c2<T>* Dinv, const StencilView<T>& Ac,
-                         const CoarseLayout& L, const int* cpl, const c2<T>* rc, c2<T>* uc, int* err,
-                         const int* active, cudaStream_t s);
+                         const CoarseLayout& L, const int* cpl, const c2<T>* rc, c2<T>* uc, c2<T>* xmid,
+                         int* xflag, int* err, const int* active, cudaStream_t s);
 // host-built coupling lists of the coarse blocks (uploaded once per handle)
 int coupling_max(const GridDesc& g);
 void coupling_lists(const GridDesc& g, const CoarseLayout& L, std::vector<int>& out);
 // Block-Thomas factorisation: Dinv[J] = (A_JJ - A_J,J-1 Dinv[J-1] A_J-1,J)^{-1}.
-// tmp: B x ldb; piv: factor_workspace(L) elements.
-inline size_t factor_workspace(const CoarseLayout& L) { return 2 * 8 * (size_t)L.ldb + 2 * 8 * (size_t)L.B; }
+// tmp: 2 x B x ldb; piv: 2 x factor_workspace(L) elements; bar: 4 unsigned
+// (two halves of the grid factor the top and bottom chains concurrently).
+__host__ __device__ inline size_t factor_workspace(const CoarseLayout& L) { return 2 * 8 * (size_t)L.ldb + 2 * 8 * (size_t)L.B; }
 template <typename T>
 int launch_coarse_factor(c2<T>* Dinv, c2<T>* tmp, c2<T>* piv, unsigned* bar, int* err,
                          const StencilView<T>& Ac, const CoarseLayout& L, int nsm, cudaStream_t s);
