@@ -265,12 +265,12 @@ void enqueue_iteration(helm_ctx* h, cudaStream_t s, Profile* prof = nullptr, int
   const int* act = &kb.st->active;
   const int* jsel = &kb.st->j;
   if (prof) cudaEventRecord(prof->ev[ev0 + 0], s);
-  enqueue_vcycle_any(h, VecSel<const double2>{kb.V, kb.ldN, jsel, 0}, VecSel<double2>{kb.Z, kb.ldN, jsel, 0},
+  enqueue_vcycle_any(h, VecSel<const double2>{kb.vj, 0, nullptr, 0}, VecSel<double2>{kb.Z, kb.ldN, jsel, 0},
                      act, s, prof, ev0);
   if (prof) cudaEventRecord(prof->ev[ev0 + 3], s);
   StencilView<double> A0 = make_view<double>(h->gf, h->coefA0, nullptr);
   launch_apply<double, double2, double2>(A0, VecSel<const double2>{kb.Z, kb.ldN, jsel, 0},
-                                         VecSel<double2>{kb.V, kb.ldN, jsel, 1}, act, s);
+                                         VecSel<double2>{kb.W, 0, nullptr, 0}, act, s);
   if (prof) cudaEventRecord(prof->ev[ev0 + 4], s);
   launch_cgs_pass(kb, false, s);
   launch_cgs_pass(kb, true, s);
@@ -589,8 +589,15 @@ static int setup_impl(helm_ctx* h) {
   const int m = o.restart;
   kb.N = h->gf.N;
   kb.ldN = (kb.N + 31) & ~int64_t(31);
-  kb.nblk = std::max(1, std::min<int>((int)((kb.N + 255) / 256), 2 * h->nsm));
-  CK(h->alloc(&kb.V, sizeof(double2) * kb.ldN * (m + 1)));
+  // element-wise Krylov kernels: one entry per thread; inner products: <= 4 per thread
+  kb.nblk = (int)std::max<int64_t>(1, (kb.N + 255) / 256);
+  kb.nblk_dots = (int)std::max<int64_t>(1, (kb.N + 1023) / 1024);
+  CK(h->alloc(&kb.Vh, sizeof(float2) * kb.ldN * (m + 1)));
+  CK(h->alloc(&kb.Vl, sizeof(float2) * kb.ldN * (m + 1)));
+  CK(h->alloc(&kb.vj, sizeof(double2) * kb.ldN));
+  CK(h->alloc(&kb.W, sizeof(double2) * kb.ldN));
+  CK(h->alloc(&kb.Wh, sizeof(float2) * kb.ldN));
+  CK(h->alloc(&kb.Wl, sizeof(float2) * kb.ldN));
   CK(h->alloc(&kb.Z, sizeof(double2) * kb.ldN * m));
   CK(h->alloc(&kb.H, sizeof(double2) * (m + 1) * m));
   CK(h->alloc(&kb.cs, sizeof(double) * m));
@@ -603,7 +610,10 @@ static int setup_impl(helm_ctx* h) {
   CK(h->alloc(&kb.st, sizeof(KState)));
   CK(h->alloc(&h->rres, sizeof(double2) * kb.ldN));
   CK(cudaMallocHost(&h->st_h, sizeof(KState)));
-  CK(cudaMemsetAsync(kb.V, 0, sizeof(double2) * kb.ldN * (m + 1), s));
+  CK(cudaMemsetAsync(kb.Vh, 0, sizeof(float2) * kb.ldN * (m + 1), s));
+  CK(cudaMemsetAsync(kb.Vl, 0, sizeof(float2) * kb.ldN * (m + 1), s));
+  CK(cudaMemsetAsync(kb.vj, 0, sizeof(double2) * kb.ldN, s));
+  CK(cudaMemsetAsync(kb.W, 0, sizeof(double2) * kb.ldN, s));
   CK(cudaMemsetAsync(kb.Z, 0, sizeof(double2) * kb.ldN * m, s));
   CK(cudaStreamSynchronize(s));
   return capture_iteration(h);

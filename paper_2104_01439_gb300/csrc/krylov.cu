@@ -3,9 +3,15 @@
 // Arnoldi orthogonalisation is classical Gram-Schmidt with one conditional
 // second pass (DGKS criterion ||w_after|| < ||w_before|| / sqrt(2)); inner
 // products are Hermitian, <a, b> = sum conj(a_i) b_i. Each pass is a
-// grid-wide dot-product kernel (8 basis vectors per sweep over w, warp-shuffle
-// + shared-memory block reductions into per-block partials), a one-block
+// grid-wide dot-product kernel (8 basis vectors per sweep over w), a one-block
 // deterministic reduction, and an update kernel that also accumulates ||w||^2.
+//
+// GB300 issues FP64 at 1/58 of its FP32 rate, so the Gram-Schmidt arithmetic
+// is done in double-float: every basis entry is stored as hi + lo float pairs,
+// every product is formed exactly with an FMA (TwoProduct) and accumulated with
+// Knuth's TwoSum; warp reductions stay in double-float and only the per-block
+// partials are converted to double. Inner products carry ~48 significant bits
+// (relative error ~1e-15 of sum |a_i b_i|), the vector w itself stays complex128.
 // Complex Givens rotations (c real, s complex), the residual estimate
 // |g_{j+1}| and the convergence test run on the device in one thread, so a
 // captured iteration never returns to the host. All kernels read the Arnoldi
@@ -32,26 +38,82 @@ __device__ __forceinline__ double wsum(double v) {
   return v;
 }
 
-// partial dots of w = V[j+1] against V[0..j] (and ||w||^2 in the first pass)
-__global__ void __launch_bounds__(kT) k_dots(KrylovBufs kb, int second) {
+// ---- double-float (hi + lo float) arithmetic --------------------------------
+struct DF {
+  float h, l;
+};
+__device__ __forceinline__ DF df_split(double d) {
+  float h = (float)d;
+  return DF{h, (float)(d - (double)h)};
+}
+// s += a * b  (TwoProduct by FMA, TwoSum on the high parts)
+__device__ __forceinline__ void df_mac(float ah, float al, float bh, float bl, DF& s) {
+  float p = ah * bh;
+  float e = fmaf(ah, bh, -p);
+  e = fmaf(ah, bl, e);
+  e = fmaf(al, bh, e);
+  float t = s.h + p;
+  float bp = t - s.h;
+  float err = (s.h - (t - bp)) + (p - bp);
+  s.h = t;
+  s.l += err + e;
+}
+__device__ __forceinline__ DF df_add(DF a, DF b) {
+  float s = a.h + b.h;
+  float bp = s - a.h;
+  float e = (a.h - (s - bp)) + (b.h - bp);
+  e += a.l + b.l;
+  float h = s + e;
+  return DF{h, e - (h - s)};
+}
+__device__ __forceinline__ DF df_wsum(DF v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    DF w{__shfl_xor_sync(0xffffffffu, v.h, o), __shfl_xor_sync(0xffffffffu, v.l, o)};
+    v = df_add(v, w);
+  }
+  return v;
+}
+__device__ __forceinline__ double df_val(DF v) { return (double)v.h + (double)v.l; }
+
+constexpr int kE = 4;    // basis entries per thread in the inner-product kernel
+constexpr int kGD = 4;   // basis vectors per sweep of the inner-product kernel
+
+// w -> (hi, lo) once per pass, so the inner products run on FP32 pipes only
+__global__ void __launch_bounds__(kT) k_split_w(KrylovBufs kb) {
+  KState* st = kb.st;
+  if (!st->active) return;
+  for (int64_t n = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; n < kb.N; n += (int64_t)gridDim.x * blockDim.x) {
+    double2 v = kb.W[n];
+    DF r = df_split(v.x), q = df_split(v.y);
+    kb.Wh[n] = make_float2(r.h, q.h);
+    kb.Wl[n] = make_float2(r.l, q.l);
+  }
+}
+
+// partial dots of w against the double-float basis V[0..j] (and ||w||^2 in the first pass)
+__global__ void __launch_bounds__(kT, 2) k_dots(KrylovBufs kb, int second) {
   KState* st = kb.st;
   if (!st->active || (second && !st->reorth)) return;
   const int j = st->j, m = st->m;
   const int64_t N = kb.N, ld = kb.ldN;
-  const double2* w = kb.V + (int64_t)(j + 1) * ld;
-  __shared__ double2 red[kT / 32][kG];
+  __shared__ double2 red[kT / 32][kGD];
   __shared__ double rn[kT / 32];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   double2* part = kb.part + (int64_t)blockIdx.x * (m + 2);
-  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x, base = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (!second) {
-    double s = 0.0;
-    for (int64_t n = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; n < N; n += stride) {
-      double2 v = w[n];
-      s = fma(v.x, v.x, fma(v.y, v.y, s));
+    double s2 = 0.0;
+#pragma unroll
+    for (int k = 0; k < kE; ++k) {
+      const int64_t n = base + k * stride;
+      if (n < N) {
+        double2 v = kb.W[n];
+        s2 = fma(v.x, v.x, fma(v.y, v.y, s2));
+      }
     }
-    s = wsum(s);
-    if (lane == 0) rn[warp] = s;
+    s2 = wsum(s2);
+    if (lane == 0) rn[warp] = s2;
     __syncthreads();
     if (threadIdx.x == 0) {
       double t = 0.0;
@@ -59,26 +121,37 @@ __global__ void __launch_bounds__(kT) k_dots(KrylovBufs kb, int second) {
       part[m + 1] = make_double2(t, 0.0);
     }
   }
-  for (int i0 = 0; i0 <= j; i0 += kG) {
-    const int ng = min(kG, j + 1 - i0);
-    double2 acc[kG];
+  for (int i0 = 0; i0 <= j; i0 += kGD) {
+    const int ng = min(kGD, j + 1 - i0);
+    DF ar[kGD], ai[kGD];
 #pragma unroll
-    for (int t = 0; t < kG; ++t) acc[t] = make_double2(0.0, 0.0);
-    for (int64_t n = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; n < N; n += stride) {
-      double2 wn = w[n];
+    for (int t = 0; t < kGD; ++t) ar[t] = ai[t] = DF{0.f, 0.f};
 #pragma unroll
-      for (int t = 0; t < kG; ++t)
-        if (t < ng) acc[t] = cfma_conj(kb.V[(int64_t)(i0 + t) * ld + n], wn, acc[t]);
+    for (int k = 0; k < kE; ++k) {
+      const int64_t n = base + k * stride;
+      if (n >= N) break;
+      const float2 wh = kb.Wh[n], wl = kb.Wl[n];
+#pragma unroll
+      for (int t = 0; t < kGD; ++t) {
+        if (t < ng) {
+          const float2 vh = kb.Vh[(int64_t)(i0 + t) * ld + n], vl = kb.Vl[(int64_t)(i0 + t) * ld + n];
+          // conj(v) w = (vr wr + vi wi) + i (vr wi - vi wr)
+          df_mac(vh.x, vl.x, wh.x, wl.x, ar[t]);
+          df_mac(vh.y, vl.y, wh.y, wl.y, ar[t]);
+          df_mac(vh.x, vl.x, wh.y, wl.y, ai[t]);
+          df_mac(-vh.y, -vl.y, wh.x, wl.x, ai[t]);
+        }
+      }
     }
 #pragma unroll
-    for (int t = 0; t < kG; ++t) {
-      double2 v = wsum(acc[t]);
-      if (lane == 0) red[warp][t] = v;
+    for (int t = 0; t < kGD; ++t) {
+      DF r = df_wsum(ar[t]), q = df_wsum(ai[t]);
+      if (lane == 0) red[warp][t] = make_double2(df_val(r), df_val(q));
     }
     __syncthreads();
     if (threadIdx.x < ng) {
       double2 t2 = make_double2(0.0, 0.0);
-      for (int wi = 0; wi < kT / 32; ++wi) t2 = cadd(t2, red[wi][threadIdx.x]);
+      for (int wi2 = 0; wi2 < kT / 32; ++wi2) t2 = cadd(t2, red[wi2][threadIdx.x]);
       part[i0 + threadIdx.x] = t2;
     }
     __syncthreads();
@@ -87,9 +160,9 @@ __global__ void __launch_bounds__(kT) k_dots(KrylovBufs kb, int second) {
 
 // Deterministic block reduction of the per-block partials: warp w sums entry
 // i (lanes stride over the blocks, then a fixed shuffle tree).
-__device__ __forceinline__ double2 sum_partials(const KrylovBufs& kb, int m, int i, int lane) {
+__device__ __forceinline__ double2 sum_partials(const KrylovBufs& kb, int m, int i, int lane, int nrows) {
   double2 s = make_double2(0.0, 0.0);
-  for (int b = lane; b < kb.nblk; b += 32) s = cadd(s, kb.part[(int64_t)b * (m + 2) + i]);
+  for (int b = lane; b < nrows; b += 32) s = cadd(s, kb.part[(int64_t)b * (m + 2) + i]);
   return wsum(s);
 }
 
@@ -102,7 +175,7 @@ __global__ void __launch_bounds__(kT) k_reduce_h(KrylovBufs kb, double2* hp, int
   for (int i = warp; i <= j + 1; i += nw) {
     int idx = i <= j ? i : m + 1;                 // last slot: ||w||^2 (first pass)
     if (i == j + 1 && second) break;
-    double2 s2 = sum_partials(kb, m, idx, lane);
+    double2 s2 = sum_partials(kb, m, idx, lane, kb.nblk_dots);
     if (lane == 0) {
       if (i <= j) {
         hp[i] = s2;
@@ -114,34 +187,47 @@ __global__ void __launch_bounds__(kT) k_reduce_h(KrylovBufs kb, double2* hp, int
   }
 }
 
-// w -= sum_i hp[i] V[i];  partial ||w||^2
+// w -= sum_i hp[i] V[i] (sum in double-float, subtraction in FP64);  partial ||w||^2.
+// One entry per thread; the basis loop is unrolled so that several loads are in flight.
 __global__ void __launch_bounds__(kT) k_update(KrylovBufs kb, const double2* hp, int second) {
   KState* st = kb.st;
   if (!st->active || (second && !st->reorth)) return;
   const int j = st->j, m = st->m;
   const int64_t N = kb.N, ld = kb.ldN;
-  double2* w = kb.V + (int64_t)(j + 1) * ld;
-  extern __shared__ double2 hs[];
-  for (int i = threadIdx.x; i <= j; i += blockDim.x) hs[i] = hp[i];
+  extern __shared__ float4 hs4[];   // per coefficient: (re.h, re.l, im.h, im.l)
+  for (int i = threadIdx.x; i <= j; i += blockDim.x) {
+    DF r = df_split(hp[i].x), q = df_split(hp[i].y);
+    hs4[i] = make_float4(r.h, r.l, q.h, q.l);
+  }
   __syncthreads();
-  double s = 0.0;
+  double s2 = 0.0;
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
   for (int64_t n = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; n < N; n += stride) {
-    double2 a = w[n];
+    DF cr{0.f, 0.f}, ci{0.f, 0.f};
+    const float2* vh = kb.Vh + n;
+    const float2* vl = kb.Vl + n;
+#pragma unroll 4
     for (int i = 0; i <= j; ++i) {
-      double2 v = kb.V[(int64_t)i * ld + n];
-      double2 h = hs[i];
-      a.x = fma(-h.x, v.x, a.x);
-      a.x = fma(h.y, v.y, a.x);
-      a.y = fma(-h.x, v.y, a.y);
-      a.y = fma(-h.y, v.x, a.y);
+      const float2 a = vh[(int64_t)i * ld], b = vl[(int64_t)i * ld];
+      const float4 h = hs4[i];
+      // h v = (hr vr - hi vi) + i (hr vi + hi vr)
+      df_mac(h.x, h.y, a.x, b.x, cr);
+      df_mac(-h.z, -h.w, a.y, b.y, cr);
+      df_mac(h.x, h.y, a.y, b.y, ci);
+      df_mac(h.z, h.w, a.x, b.x, ci);
     }
-    w[n] = a;
-    s = fma(a.x, a.x, fma(a.y, a.y, s));
+    double2 w = kb.W[n];
+    w.x -= df_val(cr);
+    w.y -= df_val(ci);
+    kb.W[n] = w;
+    DF r = df_split(w.x), q = df_split(w.y);
+    kb.Wh[n] = make_float2(r.h, q.h);
+    kb.Wl[n] = make_float2(r.l, q.l);
+    s2 = fma(w.x, w.x, fma(w.y, w.y, s2));
   }
   __shared__ double rn[kT / 32];
-  s = wsum(s);
-  if ((threadIdx.x & 31) == 0) rn[threadIdx.x >> 5] = s;
+  s2 = wsum(s2);
+  if ((threadIdx.x & 31) == 0) rn[threadIdx.x >> 5] = s2;
   __syncthreads();
   if (threadIdx.x == 0) {
     double t = 0.0;
@@ -154,11 +240,19 @@ __global__ void k_reduce_norm(KrylovBufs kb, int second) {
   KState* st = kb.st;
   if (!st->active || (second && !st->reorth)) return;
   const int m = st->m;
-  double2 s2 = sum_partials(kb, m, m + 1, threadIdx.x & 31);
+  double2 s2 = sum_partials(kb, m, m + 1, threadIdx.x & 31, kb.nblk);
   if (threadIdx.x != 0) return;
   double wn = sqrt(s2.x);
   st->wn = wn;
   if (!second) st->reorth = (wn < 0.70710678118654752 * st->wn0) ? 1 : 0;
+}
+
+// v_{j+1} = w / ||w||: stored split (hi + lo) in the basis and in complex128 for the preconditioner
+__device__ __forceinline__ void store_basis(const KrylovBufs& kb, int col, int64_t n, double2 v) {
+  DF r = df_split(v.x), q = df_split(v.y);
+  kb.Vh[(int64_t)col * kb.ldN + n] = make_float2(r.h, q.h);
+  kb.Vl[(int64_t)col * kb.ldN + n] = make_float2(r.l, q.l);
+  kb.vj[n] = v;
 }
 
 __global__ void __launch_bounds__(kT) k_normalize(KrylovBufs kb) {
@@ -167,11 +261,11 @@ __global__ void __launch_bounds__(kT) k_normalize(KrylovBufs kb) {
   const double wn = st->wn;
   if (!(wn > 1e-14 * st->beta) || !isfinite(wn)) return;   // breakdown: handled by k_givens
   const double inv = 1.0 / wn;
-  double2* w = kb.V + (int64_t)(st->j + 1) * kb.ldN;
+  const int col = st->j + 1;
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
   for (int64_t n = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; n < kb.N; n += stride) {
-    double2 a = w[n];
-    w[n] = make_double2(a.x * inv, a.y * inv);
+    double2 a = kb.W[n];
+    store_basis(kb, col, n, make_double2(a.x * inv, a.y * inv));
   }
 }
 
@@ -260,7 +354,7 @@ __global__ void __launch_bounds__(kT) k_norm_part(KrylovBufs kb, const double2* 
 __global__ void k_norm_fin(KrylovBufs kb, int which) {
   KState* st = kb.st;
   const int m = st->m;
-  double2 s2 = sum_partials(kb, m, m + 1, threadIdx.x & 31);
+  double2 s2 = sum_partials(kb, m, m + 1, threadIdx.x & 31, kb.nblk);
   if (threadIdx.x != 0) return;
   double nrm = sqrt(s2.x);
   if (which == 0) {
@@ -282,7 +376,7 @@ __global__ void __launch_bounds__(kT) k_cycle_start(KrylovBufs kb, const double2
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
   for (int64_t n = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; n < kb.N; n += stride) {
     double2 a = r[n];
-    kb.V[n] = make_double2(a.x * inv, a.y * inv);
+    store_basis(kb, 0, n, make_double2(a.x * inv, a.y * inv));
   }
   if (blockIdx.x == 0) {
     for (int i = threadIdx.x; i <= st->m; i += blockDim.x) kb.g[i] = make_double2(i == 0 ? beta : 0.0, 0.0);
@@ -339,9 +433,10 @@ __global__ void __launch_bounds__(kT) k_update_x(KrylovBufs kb, double2* x) {
 
 void launch_cgs_pass(const KrylovBufs& kb, bool second, cudaStream_t s) {
   int sec = second ? 1 : 0;
-  k_dots<<<kb.nblk, kT, 0, s>>>(kb, sec);
+  if (!second) k_split_w<<<kb.nblk, kT, 0, s>>>(kb);
+  k_dots<<<kb.nblk_dots, kT, 0, s>>>(kb, sec);
   k_reduce_h<<<1, kT, 0, s>>>(kb, kb.hp, sec);
-  k_update<<<kb.nblk, kT, sizeof(double2) * 513, s>>>(kb, kb.hp, sec);
+  k_update<<<kb.nblk, kT, sizeof(float4) * 513, s>>>(kb, kb.hp, sec);
   k_reduce_norm<<<1, 32, 0, s>>>(kb, sec);
 }
 
