@@ -592,12 +592,10 @@ static int setup_impl(helm_ctx* h) {
   // element-wise Krylov kernels: one entry per thread; inner products: <= 4 per thread
   kb.nblk = (int)std::max<int64_t>(1, (kb.N + 255) / 256);
   kb.nblk_dots = (int)std::max<int64_t>(1, (kb.N + 1023) / 1024);
-  CK(h->alloc(&kb.Vh, sizeof(float2) * kb.ldN * (m + 1)));
-  CK(h->alloc(&kb.Vl, sizeof(float2) * kb.ldN * (m + 1)));
+  CK(h->alloc(&kb.Vs, sizeof(float4) * kb.ldN * (m + 1)));
   CK(h->alloc(&kb.vj, sizeof(double2) * kb.ldN));
   CK(h->alloc(&kb.W, sizeof(double2) * kb.ldN));
-  CK(h->alloc(&kb.Wh, sizeof(float2) * kb.ldN));
-  CK(h->alloc(&kb.Wl, sizeof(float2) * kb.ldN));
+  CK(h->alloc(&kb.Ws, sizeof(float4) * kb.ldN));
   CK(h->alloc(&kb.Z, sizeof(double2) * kb.ldN * m));
   CK(h->alloc(&kb.H, sizeof(double2) * (m + 1) * m));
   CK(h->alloc(&kb.cs, sizeof(double) * m));
@@ -610,8 +608,7 @@ static int setup_impl(helm_ctx* h) {
   CK(h->alloc(&kb.st, sizeof(KState)));
   CK(h->alloc(&h->rres, sizeof(double2) * kb.ldN));
   CK(cudaMallocHost(&h->st_h, sizeof(KState)));
-  CK(cudaMemsetAsync(kb.Vh, 0, sizeof(float2) * kb.ldN * (m + 1), s));
-  CK(cudaMemsetAsync(kb.Vl, 0, sizeof(float2) * kb.ldN * (m + 1), s));
+  CK(cudaMemsetAsync(kb.Vs, 0, sizeof(float4) * kb.ldN * (m + 1), s));
   CK(cudaMemsetAsync(kb.vj, 0, sizeof(double2) * kb.ldN, s));
   CK(cudaMemsetAsync(kb.W, 0, sizeof(double2) * kb.ldN, s));
   CK(cudaMemsetAsync(kb.Z, 0, sizeof(double2) * kb.ldN * m, s));

@@ -108,12 +108,10 @@ struct KrylovBufs {
   // Krylov basis V in double-float form: each complex128 entry as a pair of
   // complex64 (hi + lo), 16 bytes like complex128, used by the Gram-Schmidt
   // kernels at FP32 throughput with ~48-bit accurate inner products.
-  float2* Vh;      // (m+1) x ldN
-  float2* Vl;      // (m+1) x ldN
+  float4* Vs;      // (m+1) x ldN: (hi.re, hi.im, lo.re, lo.im) per entry
   double2* vj;     // current basis vector v_j in complex128 (preconditioner input)
   double2* W;      // w = A0 z_j being orthogonalised (complex128)
-  float2* Wh;      // w split into hi + lo (read by the inner-product kernel)
-  float2* Wl;
+  float4* Ws;      // w split into hi + lo (read by the inner-product kernel)
   double2* Z;      // m x ldN preconditioned vectors
   int64_t ldN;
   int64_t N;
@@ -124,7 +122,7 @@ struct KrylovBufs {
   double2* y;      // m
   double2* hcol;   // m+2 : accumulated h of the current column
   double2* hp;     // m+1 : projection coefficients of the current CGS pass
-  double2* part;   // nblk x (m+2) partial sums
+  double2* part;   // nblk x (m+2) partial sums (inner products: double-float as float4)
   int nblk;        // blocks of the element-wise Krylov kernels (256 threads, one entry per thread)
   int nblk_dots;   // blocks of the inner-product kernel (256 threads, <= 4 entries per thread)
   KState* st;

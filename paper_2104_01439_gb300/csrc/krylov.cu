@@ -86,8 +86,7 @@ __global__ void __launch_bounds__(kT) k_split_w(KrylovBufs kb) {
   for (int64_t n = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; n < kb.N; n += (int64_t)gridDim.x * blockDim.x) {
     double2 v = kb.W[n];
     DF r = df_split(v.x), q = df_split(v.y);
-    kb.Wh[n] = make_float2(r.h, q.h);
-    kb.Wl[n] = make_float2(r.l, q.l);
+    kb.Ws[n] = make_float4(r.h, q.h, r.l, q.l);
   }
 }
 
@@ -97,7 +96,7 @@ __global__ void __launch_bounds__(kT, 2) k_dots(KrylovBufs kb, int second) {
   if (!st->active || (second && !st->reorth)) return;
   const int j = st->j, m = st->m;
   const int64_t N = kb.N, ld = kb.ldN;
-  __shared__ double2 red[kT / 32][kGD];
+  __shared__ float4 red[kT / 32][kGD];
   __shared__ double rn[kT / 32];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   double2* part = kb.part + (int64_t)blockIdx.x * (m + 2);
@@ -121,6 +120,7 @@ __global__ void __launch_bounds__(kT, 2) k_dots(KrylovBufs kb, int second) {
       part[m + 1] = make_double2(t, 0.0);
     }
   }
+  float4* part4 = reinterpret_cast<float4*>(part);
   for (int i0 = 0; i0 <= j; i0 += kGD) {
     const int ng = min(kGD, j + 1 - i0);
     DF ar[kGD], ai[kGD];
@@ -130,29 +130,33 @@ __global__ void __launch_bounds__(kT, 2) k_dots(KrylovBufs kb, int second) {
     for (int k = 0; k < kE; ++k) {
       const int64_t n = base + k * stride;
       if (n >= N) break;
-      const float2 wh = kb.Wh[n], wl = kb.Wl[n];
+      const float4 w = kb.Ws[n];   // (hr, hi, lr, li)
 #pragma unroll
       for (int t = 0; t < kGD; ++t) {
         if (t < ng) {
-          const float2 vh = kb.Vh[(int64_t)(i0 + t) * ld + n], vl = kb.Vl[(int64_t)(i0 + t) * ld + n];
+          const float4 v = kb.Vs[(int64_t)(i0 + t) * ld + n];
           // conj(v) w = (vr wr + vi wi) + i (vr wi - vi wr)
-          df_mac(vh.x, vl.x, wh.x, wl.x, ar[t]);
-          df_mac(vh.y, vl.y, wh.y, wl.y, ar[t]);
-          df_mac(vh.x, vl.x, wh.y, wl.y, ai[t]);
-          df_mac(-vh.y, -vl.y, wh.x, wl.x, ai[t]);
+          df_mac(v.x, v.z, w.x, w.z, ar[t]);
+          df_mac(v.y, v.w, w.y, w.w, ar[t]);
+          df_mac(v.x, v.z, w.y, w.w, ai[t]);
+          df_mac(-v.y, -v.w, w.x, w.z, ai[t]);
         }
       }
     }
 #pragma unroll
     for (int t = 0; t < kGD; ++t) {
       DF r = df_wsum(ar[t]), q = df_wsum(ai[t]);
-      if (lane == 0) red[warp][t] = make_double2(df_val(r), df_val(q));
+      if (lane == 0) red[warp][t] = make_float4(r.h, r.l, q.h, q.l);
     }
     __syncthreads();
-    if (threadIdx.x < ng) {
-      double2 t2 = make_double2(0.0, 0.0);
-      for (int wi2 = 0; wi2 < kT / 32; ++wi2) t2 = cadd(t2, red[wi2][threadIdx.x]);
-      part[i0 + threadIdx.x] = t2;
+    if (threadIdx.x < ng) {   // block partial, still double-float (converted by k_reduce_h)
+      DF r{0.f, 0.f}, q{0.f, 0.f};
+      for (int wi2 = 0; wi2 < kT / 32; ++wi2) {
+        const float4 x = red[wi2][threadIdx.x];
+        r = df_add(r, DF{x.x, x.y});
+        q = df_add(q, DF{x.z, x.w});
+      }
+      part4[i0 + threadIdx.x] = make_float4(r.h, r.l, q.h, q.l);
     }
     __syncthreads();
   }
@@ -166,24 +170,32 @@ __device__ __forceinline__ double2 sum_partials(const KrylovBufs& kb, int m, int
   return wsum(s);
 }
 
-// h = sum of partials; hp = this pass's h, hcol accumulates over the passes.
+// h = sum of the inner-product partials (double-float, reduced in double-float and
+// converted once); hp = this pass's h, hcol accumulates over the passes.
 __global__ void __launch_bounds__(kT) k_reduce_h(KrylovBufs kb, double2* hp, int second) {
   KState* st = kb.st;
   if (!st->active || (second && !st->reorth)) return;
   const int j = st->j, m = st->m;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
-  for (int i = warp; i <= j + 1; i += nw) {
-    int idx = i <= j ? i : m + 1;                 // last slot: ||w||^2 (first pass)
-    if (i == j + 1 && second) break;
-    double2 s2 = sum_partials(kb, m, idx, lane, kb.nblk_dots);
-    if (lane == 0) {
-      if (i <= j) {
-        hp[i] = s2;
-        kb.hcol[i] = second ? cadd(kb.hcol[i], s2) : s2;
-      } else {
-        st->wn0 = sqrt(s2.x);
-      }
+  const float4* p4 = reinterpret_cast<const float4*>(kb.part);
+  for (int i = warp; i <= j; i += nw) {
+    DF r{0.f, 0.f}, q{0.f, 0.f};
+    for (int b = lane; b < kb.nblk_dots; b += 32) {
+      const float4 x = p4[(int64_t)b * (m + 2) + i];
+      r = df_add(r, DF{x.x, x.y});
+      q = df_add(q, DF{x.z, x.w});
     }
+    r = df_wsum(r);
+    q = df_wsum(q);
+    if (lane == 0) {
+      double2 s2 = make_double2(df_val(r), df_val(q));
+      hp[i] = s2;
+      kb.hcol[i] = second ? cadd(kb.hcol[i], s2) : s2;
+    }
+  }
+  if (!second && warp == 0) {
+    double2 s2 = sum_partials(kb, m, m + 1, lane, kb.nblk_dots);   // ||w||^2 (FP64)
+    if (lane == 0) st->wn0 = sqrt(s2.x);
   }
 }
 
@@ -204,25 +216,23 @@ __global__ void __launch_bounds__(kT) k_update(KrylovBufs kb, const double2* hp,
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
   for (int64_t n = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; n < N; n += stride) {
     DF cr{0.f, 0.f}, ci{0.f, 0.f};
-    const float2* vh = kb.Vh + n;
-    const float2* vl = kb.Vl + n;
-#pragma unroll 4
+    const float4* vs = kb.Vs + n;
+#pragma unroll 8
     for (int i = 0; i <= j; ++i) {
-      const float2 a = vh[(int64_t)i * ld], b = vl[(int64_t)i * ld];
-      const float4 h = hs4[i];
+      const float4 v = vs[(int64_t)i * ld];   // (hr, hi, lr, li)
+      const float4 h = hs4[i];                // (re.h, re.l, im.h, im.l)
       // h v = (hr vr - hi vi) + i (hr vi + hi vr)
-      df_mac(h.x, h.y, a.x, b.x, cr);
-      df_mac(-h.z, -h.w, a.y, b.y, cr);
-      df_mac(h.x, h.y, a.y, b.y, ci);
-      df_mac(h.z, h.w, a.x, b.x, ci);
+      df_mac(h.x, h.y, v.x, v.z, cr);
+      df_mac(-h.z, -h.w, v.y, v.w, cr);
+      df_mac(h.x, h.y, v.y, v.w, ci);
+      df_mac(h.z, h.w, v.x, v.z, ci);
     }
     double2 w = kb.W[n];
     w.x -= df_val(cr);
     w.y -= df_val(ci);
     kb.W[n] = w;
     DF r = df_split(w.x), q = df_split(w.y);
-    kb.Wh[n] = make_float2(r.h, q.h);
-    kb.Wl[n] = make_float2(r.l, q.l);
+    kb.Ws[n] = make_float4(r.h, q.h, r.l, q.l);
     s2 = fma(w.x, w.x, fma(w.y, w.y, s2));
   }
   __shared__ double rn[kT / 32];
@@ -250,8 +260,7 @@ __global__ void k_reduce_norm(KrylovBufs kb, int second) {
 // v_{j+1} = w / ||w||: stored split (hi + lo) in the basis and in complex128 for the preconditioner
 __device__ __forceinline__ void store_basis(const KrylovBufs& kb, int col, int64_t n, double2 v) {
   DF r = df_split(v.x), q = df_split(v.y);
-  kb.Vh[(int64_t)col * kb.ldN + n] = make_float2(r.h, q.h);
-  kb.Vl[(int64_t)col * kb.ldN + n] = make_float2(r.l, q.l);
+  kb.Vs[(int64_t)col * kb.ldN + n] = make_float4(r.h, q.h, r.l, q.l);
   kb.vj[n] = v;
 }
 
