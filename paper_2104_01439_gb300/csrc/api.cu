@@ -31,7 +31,9 @@ template <typename T> struct Prec {
   c2<T>* wdinv = nullptr;    // fine omega/diag(A_eps)
   c2<T>* coefAc = nullptr;   // coarse A_eps
   T* pw = nullptr;           // prolongation weights
-  c2<T>* Dinv = nullptr;     // coarse factor
+  c2<T>* Dinv = nullptr;     // coarse factor: inverses of the Schur blocks
+  c2<T>* Lm = nullptr;       // Dinv[J] A_J,J-1 (couplings folded into the inverses)
+  c2<T>* Up = nullptr;       // Dinv[J] A_J,J+1
   CoarsePlan plan{};
   // V-cycle workspaces
   c2<T>* ua = nullptr;
@@ -41,7 +43,8 @@ template <typename T> struct Prec {
   c2<T>* rc = nullptr;
   c2<T>* uc = nullptr;
   c2<T>* xmid = nullptr;   // middle-block exchange of the twisted coarse solve (2 x ldb)
-  int* xflag = nullptr;    // its two ready flags
+  int* xflag = nullptr;    // its ready flags (one per row of each chain)
+  unsigned* gbar = nullptr;   // grid barrier of the whole-grid coarse solve
 };
 
 }  // namespace
@@ -57,7 +60,6 @@ struct helm_ctx {
   CoarseLayout L{};
   int ncls_f = 0, ncls_c = 0;
   double2* coefA0 = nullptr;   // fine A0 (FP64)
-  int* cpl = nullptr;          // coarse coupling lists
   Prec<double> p64;
   Prec<float> p32;
   // Krylov
@@ -202,8 +204,9 @@ int setup_prec(helm_ctx* h, const std::vector<double2>& Ae, const std::vector<do
   CK(h->alloc(&p.rc, sizeof(c2<T>) * Nc));
   CK(h->alloc(&p.uc, sizeof(c2<T>) * Nc));
   CK(h->alloc(&p.xmid, sizeof(c2<T>) * 2 * h->L.ldb));
-  CK(h->alloc(&p.xflag, sizeof(int) * 2));
-  if ((rc = plan_coarse_solve<T>(h->L, h->gc, &p.plan))) return rc;
+  CK(h->alloc(&p.xflag, sizeof(int) * 2 * h->L.ldb));
+  CK(h->alloc(&p.gbar, sizeof(unsigned) * 2));
+  if ((rc = plan_coarse_solve<T>(h->L, &p.plan))) return rc;
   // the elimination order (one chain, or two chains meeting in the middle) is fixed
   // here, before the factorisation, and used by both the factor and the solve
   h->L.mid = p.plan.ncl == 2 ? h->L.nb / 2 : h->L.nb - 1;
@@ -237,7 +240,8 @@ void enqueue_vcycle(helm_ctx* h, VecSel<const double2> f, VecSel<double2> z, con
   launch_residual<T, V, V>(Ae, fT, cur, p.r, active, s);
   launch_restrict<T>(P, h->L, p.r, p.rc, active, s);
   if (prof) cudaEventRecord(prof->ev[ev0 + 1], s);
-  launch_coarse_solve<T>(p.plan, p.Dinv, Ac, h->L, h->cpl, p.rc, p.uc, p.xmid, p.xflag, h->err, active, s);
+  launch_coarse_solve<T>(p.plan, p.Dinv, p.Lm, p.Up, h->L, p.rc, p.uc, p.xmid, p.xflag, p.gbar, h->err, active,
+                         h->nsm, s);
   if (prof) cudaEventRecord(prof->ev[ev0 + 2], s);
   launch_prolong_add<T>(P, h->L, p.uc, cur, active, s);
   for (int it = 0; it < nu; ++it) {   // postsmoothing
@@ -526,12 +530,6 @@ static int setup_impl(helm_ctx* h) {
   L.B = L.rows * L.plane;
   L.ldb = (L.B + 1) & ~1;
   L.mid = L.nb - 1;   // single chain unless the solve plan runs two clusters (set below)
-  {
-    std::vector<int> lists;
-    coupling_lists(h->gc, L, lists);
-    CK(h->alloc(&h->cpl, sizeof(int) * lists.size()));
-    CK(cudaMemcpy(h->cpl, lists.data(), sizeof(int) * lists.size(), cudaMemcpyHostToDevice));
-  }
   if (o.precision == HELM_MIXED) {
     if ((rc = setup_prec<float>(h, Ae, wd, Ac, true))) return rc;
   }
@@ -551,12 +549,25 @@ static int setup_impl(helm_ctx* h) {
   CK(cudaEventRecord(h->e0, s));
   StencilView<double> Acv = make_view<double>(h->gc, h->p64.coefAc, nullptr);
   rc = launch_coarse_factor<double>(D64, tmp, piv, bar, h->err, Acv, L, h->nsm, s);
-  h->setup_kernels = L.nb + (o.precision == HELM_MIXED ? 1 : 0);
+  h->setup_kernels = std::max(L.mid, L.nb - 1 - L.mid) + 1 + 1 + (o.precision == HELM_MIXED ? 1 : 0);
+  // couplings folded into the inverses: Lm[J] = Dinv[J] A_J,J-1, Up[J] = Dinv[J] A_J,J+1
   if (rc == HELM_OK && o.precision == HELM_MIXED) {
-    if (cudaMalloc(&h->p32.Dinv, sizeof(float2) * blk * L.nb) != cudaSuccess) rc = HELM_ENOMEM;
-    else {
-      h->allocs.push_back(h->p32.Dinv);
-      launch_convert_factor(D64, h->p32.Dinv, blk * L.nb, s);
+    Prec<float>& p = h->p32;
+    if (h->alloc(&p.Dinv, sizeof(float2) * blk * L.nb) != cudaSuccess ||
+        h->alloc(&p.Lm, sizeof(float2) * blk * L.nb) != cudaSuccess ||
+        h->alloc(&p.Up, sizeof(float2) * blk * L.nb) != cudaSuccess) {
+      rc = HELM_ENOMEM;
+    } else {
+      launch_convert_factor(D64, p.Dinv, blk * L.nb, s);
+      launch_coarse_couple<float2>(D64, p.Lm, p.Up, Acv, L, h->nsm, s);
+    }
+  } else if (rc == HELM_OK) {
+    Prec<double>& p = h->p64;
+    if (h->alloc(&p.Lm, sizeof(double2) * blk * L.nb) != cudaSuccess ||
+        h->alloc(&p.Up, sizeof(double2) * blk * L.nb) != cudaSuccess) {
+      rc = HELM_ENOMEM;
+    } else {
+      launch_coarse_couple<double2>(D64, p.Lm, p.Up, Acv, L, h->nsm, s);
     }
   }
   cudaEventRecord(h->e1, s);
@@ -759,14 +770,14 @@ int helm_coarse_solve(helm_t h, const void* rc_nat, void* uc_nat) {
   if (h->opts.precision == HELM_MIXED) {
     Prec<float>& p = h->p32;
     launch_coarse_pack<double2, float2>(h->gc, h->L, (const double2*)rc_nat, p.rc, h->s);
-    launch_coarse_solve<float>(p.plan, p.Dinv, make_view<float>(h->gc, p.coefAc, nullptr), h->L, h->cpl, p.rc,
-                               p.uc, p.xmid, p.xflag, h->err, nullptr, h->s);
+    launch_coarse_solve<float>(p.plan, p.Dinv, p.Lm, p.Up, h->L, p.rc, p.uc, p.xmid, p.xflag, p.gbar, h->err,
+                               nullptr, h->nsm, h->s);
     launch_coarse_unpack<float2, double2>(h->gc, h->L, p.uc, (double2*)uc_nat, h->s);
   } else {
     Prec<double>& p = h->p64;
     launch_coarse_pack<double2, double2>(h->gc, h->L, (const double2*)rc_nat, p.rc, h->s);
-    launch_coarse_solve<double>(p.plan, p.Dinv, make_view<double>(h->gc, p.coefAc, nullptr), h->L,
-                                h->cpl, p.rc, p.uc, p.xmid, p.xflag, h->err, nullptr, h->s);
+    launch_coarse_solve<double>(p.plan, p.Dinv, p.Lm, p.Up, h->L, p.rc, p.uc, p.xmid, p.xflag, p.gbar, h->err,
+                                nullptr, h->nsm, h->s);
     launch_coarse_unpack<double2, double2>(h->gc, h->L, p.uc, (double2*)uc_nat, h->s);
   }
   CK(cudaGetLastError());
@@ -845,8 +856,8 @@ int coarse_solve_noalloc(helm_t h, const double2* rc_nat, double2* uc_nat) {
   V* pad_uc = pad_rc + nvec;   // 16-byte aligned: nvec * sizeof(V) is a multiple of 16 (ldb even)
   CK(cudaMemsetAsync(h->err, 0, sizeof(int), h->s));   // the error word must start at zero
   launch_coarse_pack<double2, V>(h->gc, h->L, rc_nat, pad_rc, h->s);   // writes every padded entry
-  launch_coarse_solve<T>(p.plan, p.Dinv, make_view<T>(h->gc, p.coefAc, nullptr), h->L, h->cpl, pad_rc, pad_uc,
-                         p.xmid, p.xflag, h->err, nullptr, h->s);
+  launch_coarse_solve<T>(p.plan, p.Dinv, p.Lm, p.Up, h->L, pad_rc, pad_uc, p.xmid, p.xflag, p.gbar, h->err,
+                         nullptr, h->nsm, h->s);
   launch_coarse_unpack<V, double2>(h->gc, h->L, pad_uc, uc_nat, h->s);
   CK(cudaGetLastError());
   CK(cudaStreamSynchronize(h->s));

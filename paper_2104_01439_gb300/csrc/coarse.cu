@@ -54,10 +54,22 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, unsigned parity) {
       : "memory");
   return ok != 0;
 }
+__device__ __forceinline__ bool mbar_test_wait(uint64_t* bar, unsigned parity) {
+  unsigned ok;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "mbarrier.test_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+      "selp.u32 %0, 1, 0, p;\n\t}"
+      : "=r"(ok)
+      : "r"(smem_u32(bar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
 // Bounded wait: gives up after 2^20 polls, flags HELM_ETIMEOUT in the CTA's
 // shared error word and in global memory; once flagged, later waits return at
 // once so that a failed solve ends quickly instead of waiting out every step.
 __device__ __forceinline__ void mbar_wait(uint64_t* bar, unsigned parity, int* s_err, int* err) {
+  if (mbar_test_wait(bar, parity)) return;   // usually complete already: no suspend
   if (*(volatile int*)s_err) return;
   for (int i = 0; i < (1 << 20); ++i)
     if (mbar_try_wait(bar, parity)) return;
@@ -440,21 +452,124 @@ __global__ void k_convert(const double2* __restrict__ s, float2* __restrict__ d,
 }
 
 // ---------------------------------------------------------------------------
-// Cluster solve kernel.
+// Couplings folded into the inverses (setup):
+//   Lm[J] = Dinv[J] A_J,J-1   (B x B, columns = DoFs of block J-1)
+//   Up[J] = Dinv[J] A_J,J+1   (B x B, columns = DoFs of block J+1)
+// A is complex symmetric, so A_J,J-1[i][l] = A[l][i] is read from the stencil
+// row of DoF l (block J-1): Lm[J][a][l] = sum over l's neighbours i in block J
+// of A[l][i] Dinv[J][a][i]. Padding rows and columns are zero.
+// ---------------------------------------------------------------------------
+template <typename TO>
+__global__ void __launch_bounds__(256) k_couple(const double2* __restrict__ D, TO* __restrict__ Lm,
+                                                TO* __restrict__ Up, StencilView<double> Ac, CoarseLayout L) {
+  extern __shared__ __align__(16) double2 coef[];
+  const GridDesc g = Ac.g;
+  int ncls = 1;
+  for (int ax = 0; ax < g.dim; ++ax) ncls *= g.C1;
+  for (int i = threadIdx.x; i < ncls * g.noff; i += blockDim.x) coef[i] = Ac.coef[i];
+  __syncthreads();
+  const int B = L.B, ldb = L.ldb;
+  const int64_t blk = (int64_t)B * ldb, total = 2 * (int64_t)L.nb * blk;
+  for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; idx < total;
+       idx += (int64_t)gridDim.x * blockDim.x) {
+    const int which = (int)(idx / ((int64_t)L.nb * blk));   // 0: Lm, 1: Up
+    const int64_t rem = idx - which * (int64_t)L.nb * blk;
+    const int J = (int)(rem / blk);
+    const int a = (int)((rem - (int64_t)J * blk) / ldb), l = (int)(rem - (int64_t)J * blk - (int64_t)a * ldb);
+    const int Jl = which == 0 ? J - 1 : J + 1;   // block of column l
+    double2 acc = make_double2(0.0, 0.0);
+    int c[3];
+    if (l < B && Jl >= 0 && Jl < L.nb && block_coords(g, L, Jl, l, c)) {
+      const double2* cl = coef + class_at(g, c) * g.noff;
+      const double2* Drow = D + (int64_t)J * blk + (int64_t)a * ldb;
+      for (int o = 0; o < g.noff; ++o) {
+        int Jn, in;
+        if (!neighbour(g, L, Ac.dx, o, c, &Jn, &in) || Jn != J) continue;
+        acc = cfma(cl[o], Drow[in], acc);
+      }
+    }
+    TO* out = (which == 0 ? Lm : Up) + rem;
+    *out = to<TO>(acc);
+  }
+}
+
+// ---- dense row x vector products (row and vector padded to an even length) ----
+// complex64: two complex values per 16-byte load
+__device__ __forceinline__ float2 row_dot(const float2* a, const float2* x, int nc, int lane) {
+  const float4* a4 = reinterpret_cast<const float4*>(a);
+  const float4* x4 = reinterpret_cast<const float4*>(x);
+  const int np = nc >> 1;
+  float2 s0 = make_float2(0.f, 0.f), s1 = s0;
+  int i = lane;
+  for (; i + 32 < np; i += 64) {
+    const float4 p = a4[i], q = x4[i], p2 = a4[i + 32], q2 = x4[i + 32];
+    s0 = cfma(make_float2(p.x, p.y), make_float2(q.x, q.y), s0);
+    s1 = cfma(make_float2(p.z, p.w), make_float2(q.z, q.w), s1);
+    s0 = cfma(make_float2(p2.x, p2.y), make_float2(q2.x, q2.y), s0);
+    s1 = cfma(make_float2(p2.z, p2.w), make_float2(q2.z, q2.w), s1);
+  }
+  if (i < np) {
+    const float4 p = a4[i], q = x4[i];
+    s0 = cfma(make_float2(p.x, p.y), make_float2(q.x, q.y), s0);
+    s1 = cfma(make_float2(p.z, p.w), make_float2(q.z, q.w), s1);
+  }
+  return cadd(s0, s1);
+}
+__device__ __forceinline__ double2 row_dot(const double2* a, const double2* x, int nc, int lane) {
+  double2 s0 = make_double2(0.0, 0.0), s1 = s0;
+  int i = lane;
+  for (; i + 32 < nc; i += 64) {
+    s0 = cfma(a[i], x[i], s0);
+    s1 = cfma(a[i + 32], x[i + 32], s1);
+  }
+  if (i < nc) s0 = cfma(a[i], x[i], s0);
+  return cadd(s0, s1);
+}
+
+// ---------------------------------------------------------------------------
+// Block-diagonal pre-pass of the solve: p_J = Dinv[J] r_J for every block at
+// once (independent GEMVs over the whole GPU, one warp per row), written to uc.
+// ---------------------------------------------------------------------------
+template <typename T>
+__global__ void __launch_bounds__(256) k_block_gemv(const c2<T>* __restrict__ Dinv, const c2<T>* __restrict__ rc,
+                                                    c2<T>* __restrict__ out, CoarseLayout L, const int* active) {
+  using V = c2<T>;
+  if (active && *active == 0) return;
+  const int lane = threadIdx.x & 31;
+  const int64_t rows = (int64_t)L.nb * L.B;
+  const int64_t w0 = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+  const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  for (int64_t rw = w0; rw < rows; rw += nw) {
+    const int J = (int)(rw / L.B), a = (int)(rw - (int64_t)J * L.B);
+    V v = warp_sum(row_dot(Dinv + rw * L.ldb, rc + (int64_t)J * L.ldb, L.ldb, lane));
+    if (lane == 0) out[(int64_t)J * L.ldb + a] = v;
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Cluster solve kernel (blocks that fit one thread-block cluster).
+// With p_J = Dinv[J] r_J already in uc, every step is one dense GEMV:
+//   forward   y_J = p_J - C_J y_prev     (C = Lm on the top chain, Up on the bottom one)
+//   middle    x_m = p_m - (Lm[m] y_{m-1} + Up[m] y_{m+1})
+//   backward  x_J = y_J - C_J x_prev     (C = Up on the top chain, Lm on the bottom one)
+// CTA c of a 16-CTA cluster owns rows [cR, cR+R) of every matrix. A producer warp
+// streams the CTA's rows of each step's coupling matrix into a multi-stage
+// shared-memory ring with bulk copies (cp.async.bulk + mbarrier complete_tx);
+// consumer warps (one row each) wait on a slot's "full" barrier, reduce their
+// rows, release the slot on its "empty" barrier, and lanes 0..CS-1 push the row
+// value into every CTA's receive buffer with st.async (complete_tx on the
+// receiver's mbarrier). The gathered vector is the next step's GEMV input.
+// There is no CTA-wide barrier inside a step: every thread that reads data
+// produced elsewhere waits on the mbarrier (or flag) that publishes it.
 // ---------------------------------------------------------------------------
 struct SolveGeom {
   int R, CW, nchunk, S;
-  int maxc;   // max couplings of one DoF into an adjacent block: R (2R+1)^(dim-1)
-  size_t off_mbar, off_rbar, off_coef, off_z, off_gath, off_rbuf, off_acc, off_w, off_stage;
-  size_t off_clo, off_dn, off_up;
+  size_t off_mbar, off_misc, off_gath, off_w, off_stage;
   size_t total;
 };
 
 template <typename T>
-SolveGeom solve_geometry(const CoarseLayout& L, const GridDesc& gc, int CS, int CW, int S) {
-  int ncls = 1;
-  for (int ax = 0; ax < gc.dim; ++ax) ncls *= gc.C1;
-  const int noff = gc.noff;
+SolveGeom solve_geometry(const CoarseLayout& L, int CS, int CW, int S) {
   using V = c2<T>;
   SolveGeom G;
   G.R = (L.B + CS - 1) / CS;
@@ -463,284 +578,275 @@ SolveGeom solve_geometry(const CoarseLayout& L, const GridDesc& gc, int CS, int 
   G.S = S;
   auto al = [](size_t x) { return (x + 127) & ~size_t(127); };
   size_t o = 0;
-  G.off_mbar = o; o = al(o + 8 * S);
-  G.off_rbar = o; o = al(o + 48);   // rhs mbarriers [2], error word, receive mbarriers [2] at +24
-  G.off_coef = o; o = al(o + sizeof(V) * ncls * noff);
-  G.off_z = o; o = al(o + sizeof(V) * L.ldb);
+  G.off_mbar = o; o = al(o + 16 * S);   // full [S], empty [S]
+  G.off_misc = o; o = al(o + 32);       // receive mbarriers [2] (+0, +8), error word (+16)
   G.off_gath = o; o = al(o + sizeof(V) * 2 * L.ldb);
-  G.off_rbuf = o; o = al(o + sizeof(V) * 2 * L.ldb);
-  G.off_acc = o; o = al(o + sizeof(V) * G.R);
   G.off_w = o; o = al(o + sizeof(V) * (size_t)L.nb * G.R);
   G.off_stage = o; o = al(o + sizeof(V) * (size_t)S * G.R * CW);
-  G.maxc = coupling_max(gc);
-  // coupling lists, contiguous: clo [B], row [B], dn [B*maxc], up [B*maxc]
-  G.off_clo = o;
-  G.off_dn = o + sizeof(int) * 2 * (size_t)L.B;
-  G.off_up = G.off_dn + sizeof(int) * (size_t)L.B * G.maxc;
-  o = al(G.off_up + sizeof(int) * (size_t)L.B * G.maxc);
   G.total = o;
   return G;
 }
 
-constexpr int kRPW = 4;          // rows of the CTA slice per warp (registers)
-constexpr int kSolveMaxWarps = 18;
+constexpr int kRPW = 4;          // max rows of the CTA slice per consumer warp (registers)
+constexpr int kSolveMaxWarps = 18;   // consumer warps + 1 producer warp
 
-template <typename T>
-__global__ void __launch_bounds__(kSolveMaxWarps * 32, 1) k_coarse_solve(const c2<T>* __restrict__ Dinv, StencilView<T> Ac,
-                                                        CoarseLayout L, SolveGeom G,
-                                                        const int* __restrict__ cpl,
-                                                        const c2<T>* __restrict__ rc, c2<T>* __restrict__ uc,
-                                                        c2<T>* xmid, int* xflag,
-                                                        int* err, const int* active) {
+// mbarrier arrive (release, CTA scope)
+__device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
+
+template <typename T, int RPW>
+__global__ void __launch_bounds__(kSolveMaxWarps * 32, 1)
+    k_coarse_solve(const c2<T>* __restrict__ Lm, const c2<T>* __restrict__ Up, CoarseLayout L, SolveGeom G,
+                   c2<T>* uc, c2<T>* xmid, int* xflag, int* err, const int* active) {
   using V = c2<T>;
   if (active && *active == 0) return;
   extern __shared__ __align__(128) unsigned char sm[];
-  uint64_t* mbar = reinterpret_cast<uint64_t*>(sm + G.off_mbar);
-  uint64_t* rbar = reinterpret_cast<uint64_t*>(sm + G.off_rbar);
-  V* coef = reinterpret_cast<V*>(sm + G.off_coef);
-  V* zbuf = reinterpret_cast<V*>(sm + G.off_z);
+  uint64_t* full = reinterpret_cast<uint64_t*>(sm + G.off_mbar);
+  uint64_t* empty = full + G.S;
+  uint64_t* gbar = reinterpret_cast<uint64_t*>(sm + G.off_misc);   // receive barriers of gath[0/1]
+  int* s_err = reinterpret_cast<int*>(sm + G.off_misc + 16);
   V* gath = reinterpret_cast<V*>(sm + G.off_gath);
-  V* rbuf = reinterpret_cast<V*>(sm + G.off_rbuf);
   V* wrows = reinterpret_cast<V*>(sm + G.off_w);
   V* stage = reinterpret_cast<V*>(sm + G.off_stage);
-  int* clo = reinterpret_cast<int*>(sm + G.off_clo);   // [B] in-plane class part, [B] row in block
-  int* dn = reinterpret_cast<int*>(sm + G.off_dn);     // [B][maxc] (o | in << 8), -1 terminated
-  int* up = reinterpret_cast<int*>(sm + G.off_up);
-  int* s_err = reinterpret_cast<int*>(sm + G.off_rbar + 16);
-  uint64_t* gbar = reinterpret_cast<uint64_t*>(sm + G.off_rbar + 24);   // receive barriers of gath[0/1]
 
-  const GridDesc g = Ac.g;
   const unsigned rank = cluster_rank(), CS = cluster_size();
   const int B = L.B, ldb = L.ldb, nb = L.nb, R = G.R, CW = G.CW, nchunk = G.nchunk, S = G.S;
   const int r0 = (int)rank * R, r1 = min(B, r0 + R), nr = max(0, r1 - r0);
-  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nwarps = blockDim.x >> 5;
-  const int maxc = G.maxc;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int nwc = (int)(blockDim.x >> 5) - 1;   // consumer warps; warp nwc is the producer
   const V zero = mk(T(0), T(0));
 
   // This cluster's elimination chain. Cluster 0: forward over blocks 0..mid-1;
   // cluster 1 (twisted launch): forward over blocks nb-1..mid+1. Both then solve
-  // the middle block (its right-hand side takes both chains' couplings) and run
-  // their backward sweeps outwards.
+  // the middle block and run their backward sweeps outwards.
   const int ncl = (int)(gridDim.x / CS);
   unsigned cidu;
   asm volatile("mov.u32 %0, %%clusterid.x;" : "=r"(cidu));
   const int cid = ncl > 1 ? (int)cidu : 0;
   const int m = L.mid, dir = cid == 0 ? 1 : -1, J0 = cid == 0 ? 0 : nb - 1;
   const int nf = cid == 0 ? m : nb - 1 - m;
-  const int nsteps = 2 * nf + 1, U = nsteps * nchunk;
+  const int nsteps = 2 * nf + 1;
+  const int U = (nsteps - 1) * nchunk;   // ring units: the coupling GEMVs of steps 1..nsteps-1
   auto blockof = [&](int t) { return t < nf ? J0 + dir * t : (t == nf ? m : m - dir * (t - nf)); };
-  const int* lfwd = dir > 0 ? dn : up;   // couplings into the next block of the forward sweep
-  const int* lbwd = dir > 0 ? up : dn;   // couplings into the next block of the backward sweep
 
-  int ncls = 1, cmul_last = 1;
-  for (int ax = 0; ax < g.dim; ++ax) ncls *= g.C1;
-  for (int ax = 0; ax < g.dim - 1; ++ax) cmul_last *= g.C1;
-  if (tid == 0) *s_err = 0;
-  for (int i = tid; i < ncls * g.noff; i += blockDim.x) coef[i] = Ac.coef[i];
-  // coupling lists (built on the host by coupling_lists): plain copy
-  for (int i = tid; i < 2 * B + 2 * B * maxc; i += blockDim.x) clo[i] = cpl[i];
-  for (int i = tid; i < ldb; i += blockDim.x) {
-    zbuf[i] = nf > 0 ? rc[(size_t)J0 * ldb + i] : zero;   // first forward input z = r
-    gath[i] = zero;
-    gath[ldb + i] = zero;
-  }
   if (tid == 0) {
-    for (int q = 0; q < S; ++q) mbar_init(&mbar[q], 1);
-    mbar_init(&rbar[0], 1);
-    mbar_init(&rbar[1], 1);
+    *s_err = 0;
+    for (int q = 0; q < S; ++q) {
+      mbar_init(&full[q], 1);
+      mbar_init(&empty[q], (unsigned)nwc);
+    }
     mbar_init(&gbar[0], 1);
     mbar_init(&gbar[1], 1);
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
+  for (int i = tid; i < 2 * ldb; i += blockDim.x) gath[i] = zero;   // padding columns stay zero
   __syncthreads();
-
-  // producer: unit u = (step t, chunk c) -> stage slot u % S
-  auto issue = [&](int u) {
-    int t = u / nchunk, c = u - t * nchunk;
-    int blk = blockof(t);
-    int slot = u % S;
-    V* dst = stage + (size_t)slot * R * CW;
-    const V* src = Dinv + ((size_t)blk * B + r0) * ldb;
-    if (nr == 0) {
-      mbar_expect_tx(&mbar[slot], 0);
-      return;
-    }
-    if (nchunk == 1) {
-      unsigned bytes = (unsigned)(sizeof(V) * (size_t)nr * ldb);
-      mbar_expect_tx(&mbar[slot], bytes);
-      bulk_g2s(dst, src, bytes, &mbar[slot]);
-    } else {
-      int c0 = c * CW, nc = min(CW, ldb - c0);
-      unsigned bytes = (unsigned)(sizeof(V) * nc);
-      mbar_expect_tx(&mbar[slot], bytes * nr);
-      for (int r = 0; r < nr; ++r) bulk_g2s(dst + (size_t)r * CW, src + (size_t)r * ldb + c0, bytes, &mbar[slot]);
-    }
-  };
-  auto issue_r = [&](int t) {   // right-hand side block of step t (1 <= t <= nf) into rbuf[t & 1]
-    unsigned bytes = (unsigned)(sizeof(V) * ldb);
-    mbar_expect_tx(&rbar[t & 1], bytes);
-    bulk_g2s(rbuf + (size_t)(t & 1) * ldb, rc + (size_t)blockof(t) * ldb, bytes, &rbar[t & 1]);
-  };
-  if (tid == 0) {
-    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-    for (int u = 0; u < min(S, U); ++u) issue(u);
-    if (nf >= 1) issue_r(1);
-  }
   cluster_sync();   // every CTA's barriers initialised before any remote store
-  const unsigned rx_bytes = (unsigned)(sizeof(V) * B);   // one value per row, from its owner
 
-  // Middle-block right-hand side: zbuf holds this chain's coupling g; afterwards
-  // zbuf = r_mid - g - g_other, g_other published by the other cluster through
-  // global memory (release flag / bounded acquire spin).
-  auto finish_mid = [&](const V* rm) {
-    if (ncl > 1) {
-      if (rank == 0) {
-        for (int i = tid; i < B; i += blockDim.x) xmid[(size_t)cid * ldb + i] = zbuf[i];
-        __syncthreads();
-        if (tid == 0) {
-          __threadfence();
-          atomicExch(&xflag[cid], 1);
-        }
-      }
-      if (tid == 0) {
-        int ok = 0;
-        for (long long it = 0; it < (1ll << 24); ++it) {
-          int f;
-          asm volatile("ld.acquire.gpu.global.b32 %0, [%1];" : "=r"(f) : "l"(xflag + (1 - cid)) : "memory");
-          if (f) {
-            ok = 1;
-            break;
+  if (warp == nwc) {
+    // ---- producer warp: unit u = (step 1 + u / nchunk, chunk u % nchunk) -> slot u % S
+    for (int u = 0; u < U; ++u) {
+      const int slot = u % S;
+      if (u >= S) mbar_wait(&empty[slot], (unsigned)(((u / S) - 1) & 1), s_err, err);   // slot released
+      if (lane == 0) {
+        const int t = 1 + u / nchunk, c = u - (t - 1) * nchunk;
+        V* dst = stage + (size_t)slot * R * CW;
+        if (nr == 0) {
+          mbar_expect_tx(&full[slot], 0);
+        } else {
+          const V* M = ((t <= nf) == (dir > 0)) ? Lm : Up;   // forward/middle: previous block; backward: next
+          const V* src = M + ((size_t)blockof(t) * B + r0) * ldb;
+          asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+          if (nchunk == 1) {
+            const unsigned bytes = (unsigned)(sizeof(V) * (size_t)nr * ldb);
+            mbar_expect_tx(&full[slot], bytes);
+            bulk_g2s(dst, src, bytes, &full[slot]);
+          } else {
+            const int c0 = c * CW, nc = min(CW, ldb - c0);
+            const unsigned bytes = (unsigned)(sizeof(V) * nc);
+            mbar_expect_tx(&full[slot], bytes * nr);
+            for (int r = 0; r < nr; ++r)
+              bulk_g2s(dst + (size_t)r * CW, src + (size_t)r * ldb + c0, bytes, &full[slot]);
           }
-          if (*(volatile int*)s_err) break;
         }
-        if (!ok) {
-          *(volatile int*)s_err = 1;
-          atomicExch(err, HELM_ETIMEOUT);
+      }
+      __syncwarp();
+    }
+  } else {
+    // ---- consumer warps: warp w owns rows w, w + nwc, ... of the CTA's slice
+    const unsigned rx_bytes = (unsigned)(sizeof(V) * B);   // one value per row, from its owner
+    // p rows of the current forward / middle step, prefetched one step ahead. The loads
+    // are unconditional (rows outside the slice read entry 0 of the block) so that no
+    // select waits on them.
+    V pc[RPW];
+#pragma unroll
+    for (int q = 0; q < RPW; ++q) {
+      const int r = warp + q * nwc;
+      pc[q] = cvt_ldcg(uc + (size_t)blockof(0) * ldb + (r < nr ? r0 + r : 0));
+    }
+    int u = 0;
+    for (int t = 0; t < nsteps; ++t) {
+      const int blk = blockof(t);
+      const int kind = t < nf ? 0 : (t == nf ? 1 : 2);   // forward / middle / backward
+      if (tid == 0) mbar_expect_tx(&gbar[t & 1], rx_bytes);   // arm this step's receive phase
+      V pn[RPW];
+      {
+        const size_t nxt = (size_t)blockof(t + 1 <= nf ? t + 1 : t) * ldb;
+#pragma unroll
+        for (int q = 0; q < RPW; ++q) {
+          const int r = warp + q * nwc;
+          pn[q] = cvt_ldcg(uc + nxt + (r < nr ? r0 + r : 0));   // (a CTA with an empty slice has r0 >= B)
         }
-        __threadfence();
       }
-      __syncthreads();
-      const V* other = xmid + (size_t)(1 - cid) * ldb;
-      for (int i = tid; i < B; i += blockDim.x) {
-        V o = cvt_ldcg(other + i);
-        zbuf[i] = csub(csub(rm[i], zbuf[i]), o);
+      // GEMV with the coupling matrix on the previous step's gathered vector
+      V acc[RPW];
+#pragma unroll
+      for (int q = 0; q < RPW; ++q) acc[q] = zero;
+      if (t >= 1) {
+        const V* x = gath + (size_t)((t - 1) & 1) * ldb;
+        for (int c = 0; c < nchunk; ++c, ++u) {
+          const int slot = u % S;
+          mbar_wait(&full[slot], (unsigned)((u / S) & 1), s_err, err);
+          const V* st = stage + (size_t)slot * R * CW;
+          const int c0 = c * CW, nc = min(CW, ldb - c0);
+#pragma unroll
+          for (int q = 0; q < RPW; ++q) {
+            const int r = warp + q * nwc;
+            if (r < nr) acc[q] = cadd(acc[q], row_dot(st + (size_t)r * CW, x + c0, nc, lane));
+          }
+          __syncwarp();
+          if (lane == 0) mbar_arrive(&empty[slot]);   // this warp is done with the slot
+        }
       }
-    } else {
-      for (int i = tid; i < B; i += blockDim.x) zbuf[i] = csub(rm[i], zbuf[i]);
-    }
-  };
-  if (nf == 0) {   // the chain is empty: the middle block is the first step
-    finish_mid(rc + (size_t)m * ldb);
-    __syncthreads();
-  }
-
-  int u = 0;
-  for (int t = 0; t < nsteps; ++t) {
-    const int blk = blockof(t);
-    const int kind = t < nf ? 0 : (t == nf ? 1 : 2);   // forward / middle / backward
-    if (tid == 0) {
-      mbar_expect_tx(&gbar[t & 1], rx_bytes);   // arm this step's receive phase (arrival + bytes)
-      if (t + 2 <= nf) issue_r(t + 2);
-    }
-    // ---- GEMV: warp w owns rows w, w + nwarps, ... (at most kRPW) of the CTA's
-    // slice of Dinv[blk]; partial sums stay in registers across column chunks.
-    V accr[kRPW];
+      // this step's values for the warp's rows
 #pragma unroll
-    for (int q = 0; q < kRPW; ++q) accr[q] = zero;
-    for (int c = 0; c < nchunk; ++c, ++u) {
-      int slot = u % S;
-      mbar_wait(&mbar[slot], (unsigned)((u / S) & 1), s_err, err);
-      const V* st = stage + (size_t)slot * R * CW;
-      const int c0 = c * CW, nc = min(CW, B - c0);
-#pragma unroll
-      for (int q = 0; q < kRPW; ++q) {
-        const int r = warp + q * nwarps;
+      for (int q = 0; q < RPW; ++q) {
+        const int r = warp + q * nwc;
         if (r < nr) {
-          V a0 = zero, a1 = zero;   // two chains for ILP
-          int col = lane;
-          for (; col + 32 < nc; col += 64) {
-            a0 = cfma(st[(size_t)r * CW + col], zbuf[c0 + col], a0);
-            a1 = cfma(st[(size_t)r * CW + col + 32], zbuf[c0 + col + 32], a1);
+          const V a = t >= 1 ? warp_sum(acc[q]) : zero;
+          V val = a;
+          if (kind == 0) {
+            val = csub(pc[q], a);
+            if (lane == 0) wrows[(size_t)t * R + r] = val;
+          } else if (kind == 2) {
+            val = csub(wrows[(size_t)(2 * nf - t) * R + r], a);
+            if (lane == 0) uc[(size_t)blk * ldb + r0 + r] = val;
+          } else if (ncl > 1) {
+            // middle block: x_m = p_m - (g_0 + g_1), g_c = chain c's coupling term. The
+            // partials meet through global memory, one release flag per row and a
+            // bounded acquire spin (every lane spins: each one reads the partner's value).
+            const int row = r0 + r;
+            if (lane == 0) {
+              xmid[(size_t)cid * ldb + row] = a;
+              __threadfence();
+              asm volatile("st.release.gpu.global.b32 [%0], %1;" ::"l"(xflag + cid * ldb + row), "r"(1) : "memory");
+            }
+            int ok = 0;
+            for (long long it = 0; it < (1ll << 22); ++it) {
+              int f;
+              asm volatile("ld.acquire.gpu.global.b32 %0, [%1];" : "=r"(f) : "l"(xflag + (1 - cid) * ldb + row) : "memory");
+              if (f) {
+                ok = 1;
+                break;
+              }
+              if (*(volatile int*)s_err) break;
+            }
+            if (!ok) {
+              *(volatile int*)s_err = 1;
+              atomicExch(err, HELM_ETIMEOUT);
+            }
+            // both chains form the same sum (addition commutes), so both hold the same x_m
+            val = csub(pc[q], cadd(a, cvt_ldcg(xmid + (size_t)(1 - cid) * ldb + row)));
+            if (lane == 0 && cid == 0) uc[(size_t)blk * ldb + row] = val;
+          } else {
+            val = csub(pc[q], a);
+            if (lane == 0) uc[(size_t)blk * ldb + r0 + r] = val;
           }
-          if (col < nc) a0 = cfma(st[(size_t)r * CW + col], zbuf[c0 + col], a0);
-          accr[q] = cadd(accr[q], cadd(a0, a1));
+          acc[q] = val;
         }
       }
-      __syncthreads();   // every warp is done with this stage before it is refilled
-      if (tid == 0 && u + S < U) {
-        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-        issue(u + S);
-      }
-    }
-    // ---- row results: lanes 0..CS-1 of the owning warp broadcast to every CTA
-    V* gdst = gath + (size_t)(t & 1) * ldb;
+      // broadcast: lanes 0..CS-1 of the owning warp push the value to every CTA
+      V* gdst = gath + (size_t)(t & 1) * ldb;
 #pragma unroll
-    for (int q = 0; q < kRPW; ++q) {
-      const int r = warp + q * nwarps;
-      if (r < nr) {
-        V val = warp_sum(accr[q]);
-        if (kind == 2) val = csub(wrows[(size_t)(2 * nf - t) * R + r], val);   // x = w - Dinv q
-        if (lane == 0) {
-          if (kind == 0) wrows[(size_t)t * R + r] = val;
-          if (kind == 2 || (kind == 1 && cid == 0)) uc[(size_t)blk * ldb + r0 + r] = val;
-        }
-        if (lane < (int)CS) st_async(gdst + r0 + r, (unsigned)lane, val, &gbar[t & 1]);
+      for (int q = 0; q < RPW; ++q) {
+        const int r = warp + q * nwc;
+        if (r < nr && lane < (int)CS) st_async(gdst + r0 + r, (unsigned)lane, acc[q], &gbar[t & 1]);
       }
-    }
-    mbar_wait_cluster(&gbar[t & 1], (unsigned)((t >> 1) & 1), s_err, err);   // all B values arrived
-    // ---- next GEMV input, computed locally from the gathered block
-    if (t + 1 < nsteps) {
-      const int Jd = blockof(t + 1);
-      const bool fw = t + 1 <= nf;   // next step is forward or the middle: coupling of w
-      const int* lst = fw ? lfwd : lbwd;
-      const V* rb = rbuf + (size_t)((t + 1) & 1) * ldb;
-      if (fw) mbar_wait(&rbar[(t + 1) & 1], (unsigned)((t >> 1) & 1), s_err, err);
-      for (int i = tid; i < B; i += blockDim.x) {
-        const int lastc = Jd * L.rows + clo[B + i];
-        V a = zero;
-        if (lastc < g.W) {
-          const V* c = coef + (clo[i] + axis_class(lastc, g.W, g.R, g.q) * cmul_last) * g.noff;
-          for (int k = 0; k < maxc; ++k) {
-            const int e = lst[i * maxc + k];
-            if (e < 0) break;
-            a = cfma(c[e & 255], gdst[e >> 8], a);
-          }
-          if (fw && t + 1 < nf) a = csub(rb[i], a);
-        }
-        zbuf[i] = a;
-      }
-      __syncthreads();
-      if (t + 1 == nf) {   // next: the middle block
-        finish_mid(rb);
-        __syncthreads();
-      }
+      mbar_wait_cluster(&gbar[t & 1], (unsigned)((t >> 1) & 1), s_err, err);   // all B values arrived
+#pragma unroll
+      for (int q = 0; q < RPW; ++q) pc[q] = pn[q];
     }
   }
   cluster_sync();
 }
 
+// ---------------------------------------------------------------------------
+// Grid solve kernel (blocks too large for one cluster, e.g. 3D planes): one
+// chain over the whole cooperative grid, one grid barrier per step. The step's
+// input vector is staged in shared memory; warps stream matrix rows from HBM.
+// y_J, x_m and x_J overwrite p_J in place in uc (same element, same thread).
+// ---------------------------------------------------------------------------
+template <typename T>
+__global__ void __launch_bounds__(256) k_coarse_solve_grid(const c2<T>* __restrict__ Lm, const c2<T>* __restrict__ Up,
+                                                           CoarseLayout L, c2<T>* uc, unsigned* bar, int* err,
+                                                           const int* active) {
+  using V = c2<T>;
+  if (active && *active == 0) return;
+  extern __shared__ __align__(128) unsigned char sm[];
+  V* xs = reinterpret_cast<V*>(sm);
+  const int B = L.B, ldb = L.ldb, nb = L.nb, nf = nb - 1;
+  const int lane = threadIdx.x & 31;
+  const int gw = (int)((blockIdx.x * blockDim.x + threadIdx.x) >> 5), GW = (int)((gridDim.x * blockDim.x) >> 5);
+  const V zero = mk(T(0), T(0));
+  auto blockof = [&](int t) { return t <= nf ? t : 2 * nf - t; };
+  for (int t = 0; t <= 2 * nf; ++t) {
+    const int blk = blockof(t);
+    const V* M = nullptr;
+    if (t >= 1) {
+      M = (t <= nf ? Lm : Up) + (size_t)blk * B * ldb;
+      const V* prev = uc + (size_t)blockof(t - 1) * ldb;
+      for (int i = threadIdx.x; i < ldb; i += blockDim.x) xs[i] = i < B ? cvt_ldcg(prev + i) : zero;
+      __syncthreads();
+    }
+    for (int a = gw; a < B; a += GW) {
+      const V v = M ? warp_sum(row_dot(M + (size_t)a * ldb, xs, ldb, lane)) : zero;
+      if (lane == 0) {
+        V* o = uc + (size_t)blk * ldb + a;
+        *o = csub(cvt_ldcg(o), v);   // p - C y  (forward, middle)  or  y - C x  (backward)
+      }
+    }
+    if (!grid_barrier(bar, err, gridDim.x)) return;
+  }
+}
+
 }  // namespace
 
 template <typename T>
-int plan_coarse_solve(const CoarseLayout& L, const GridDesc& gc, CoarsePlan* plan) {
-  using V = c2<T>;
+int plan_coarse_solve(const CoarseLayout& L, CoarsePlan* plan) {
   int dev = 0;
   cudaGetDevice(&dev);
-  int optin = 0;
+  int optin = 0, nsm = 0;
   cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+  cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
   size_t budget = (size_t)optin - 1024;
-  cudaFuncSetAttribute(k_coarse_solve<T>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+  *plan = CoarsePlan{};
+  cudaFuncSetAttribute(k_coarse_solve<T, 1>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+  cudaFuncSetAttribute(k_coarse_solve<T, kRPW>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
   for (int CS : {16, 8, 4, 2, 1}) {
     const int R = (L.B + CS - 1) / CS;
-    // one warp per row of the CTA's slice (up to kRPW rows per warp)
-    const int nwarps = std::min(kSolveMaxWarps, std::max(4, R));
-    if ((R + nwarps - 1) / nwarps > kRPW) continue;
+    // one consumer warp per row of the CTA's slice (up to kRPW rows per warp) + a producer warp
+    const int nwc = std::min(kSolveMaxWarps - 1, std::max(4, R));
+    const int nwarps = nwc + 1;
+    if ((R + nwc - 1) / nwc > kRPW) continue;
     // widest chunk (even, <= ldb) that leaves room for >= 2 stages
     for (int CW = L.ldb; CW >= 2; CW = ((CW / 2) + 1) & ~1) {
       for (int S = 4; S >= 2; --S) {
-        SolveGeom G = solve_geometry<T>(L, gc, CS, CW, S);
+        SolveGeom G = solve_geometry<T>(L, CS, CW, S);
         if (G.total > budget) continue;
-        cudaFuncSetAttribute(k_coarse_solve<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)budget);
+        const bool one = (R + nwc - 1) / nwc == 1;
+        auto kern = one ? k_coarse_solve<T, 1> : k_coarse_solve<T, kRPW>;
+        cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)budget);
         cudaLaunchConfig_t cfg = {};
         cfg.gridDim = dim3(CS);
         cfg.blockDim = dim3(32 * nwarps);
@@ -753,7 +859,7 @@ int plan_coarse_solve(const CoarseLayout& L, const GridDesc& gc, CoarsePlan* pla
         cfg.attrs = at;
         cfg.numAttrs = 1;
         int ncl = 0;
-        if (cudaOccupancyMaxActiveClusters(&ncl, (void*)k_coarse_solve<T>, &cfg) != cudaSuccess || ncl < 1) {
+        if (cudaOccupancyMaxActiveClusters(&ncl, (void*)kern, &cfg) != cudaSuccess || ncl < 1) {
           cudaGetLastError();
           continue;
         }
@@ -780,10 +886,9 @@ int plan_coarse_solve(const CoarseLayout& L, const GridDesc& gc, CoarsePlan* pla
             cfg.gridDim = dim3(2 * CS);
             cfg.attrs = at2;
             cfg.numAttrs = 2;
-            StencilView<T> nov{};
-            cudaError_t e = cudaLaunchKernelEx(&cfg, k_coarse_solve<T>, (const c2<T>*)nullptr, nov, L2, G,
-                                               (const int*)nullptr, (const c2<T>*)nullptr, (c2<T>*)nullptr,
-                                               (c2<T>*)nullptr, (int*)nullptr, (int*)nullptr, (const int*)off);
+            cudaError_t e = cudaLaunchKernelEx(&cfg, kern, (const c2<T>*)nullptr, (const c2<T>*)nullptr,
+                                               L2, G, (c2<T>*)nullptr, (c2<T>*)nullptr, (int*)nullptr,
+                                               (int*)nullptr, (const int*)off);
             if (e == cudaSuccess) e = cudaDeviceSynchronize();
             if (e == cudaSuccess) plan->ncl = 2;
             cudaGetLastError();
@@ -795,18 +900,50 @@ int plan_coarse_solve(const CoarseLayout& L, const GridDesc& gc, CoarsePlan* pla
       if (CW == 2) break;
     }
   }
-  return HELM_ENOTSUP;
+  // Blocks too large for a cluster: whole-grid chain (cooperative, one CTA per SM).
+  const size_t smem = sizeof(c2<T>) * (size_t)L.ldb;
+  if (smem > budget) return HELM_ENOTSUP;
+  cudaFuncSetAttribute(k_coarse_solve_grid<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  int per_sm = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_coarse_solve_grid<T>, 256, smem) != cudaSuccess ||
+      per_sm < 1) {
+    cudaGetLastError();
+    return HELM_ENOTSUP;
+  }
+  plan->grid = 1;
+  plan->ncl = 1;
+  plan->nblk = nsm * std::min(per_sm, 2);
+  plan->threads = 256;
+  plan->smem = smem;
+  return HELM_OK;
 }
 
 template <typename T>
-void launch_coarse_solve(const CoarsePlan& plan, const c2<T>* Dinv, const StencilView<T>& Ac,
-                         const CoarseLayout& L, const int* cpl, const c2<T>* rc, c2<T>* uc, c2<T>* xmid,
-                         int* xflag, int* err, const int* active, cudaStream_t s) {
-  SolveGeom G = solve_geometry<T>(L, Ac.g, plan.CS, plan.CW, plan.S);
+void launch_coarse_solve(const CoarsePlan& plan, const c2<T>* Dinv, const c2<T>* Lm, const c2<T>* Up,
+                         const CoarseLayout& L, const c2<T>* rc, c2<T>* uc, c2<T>* xmid, int* xflag,
+                         unsigned* bar, int* err, const int* active, int nsm, cudaStream_t s) {
+  // p = blockdiag(Dinv) r for all blocks at once, into uc
+  k_block_gemv<T><<<nsm * 8, 256, 0, s>>>(Dinv, rc, uc, L, active);
+  if (plan.grid) {
+    cudaMemsetAsync(bar, 0, 2 * sizeof(unsigned), s);
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(plan.nblk);
+    cfg.blockDim = dim3(plan.threads);
+    cfg.dynamicSmemBytes = plan.smem;
+    cfg.stream = s;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeCooperative;
+    at[0].val.cooperative = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    cudaLaunchKernelEx(&cfg, k_coarse_solve_grid<T>, Lm, Up, L, uc, bar, err, active);
+    return;
+  }
+  SolveGeom G = solve_geometry<T>(L, plan.CS, plan.CW, plan.S);
   // (the function's dynamic shared-memory cap was raised to the device limit by
   // plan_coarse_solve, outside any stream capture)
   const int ncl = L.mid < L.nb - 1 ? 2 : 1;
-  if (ncl > 1) cudaMemsetAsync(xflag, 0, 2 * sizeof(int), s);
+  if (ncl > 1) cudaMemsetAsync(xflag, 0, 2 * (size_t)L.ldb * sizeof(int), s);
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3(plan.CS * ncl);
   cfg.blockDim = dim3(plan.threads);
@@ -822,7 +959,19 @@ void launch_coarse_solve(const CoarsePlan& plan, const c2<T>* Dinv, const Stenci
   at[1].val.cooperative = 1;
   cfg.attrs = at;
   cfg.numAttrs = ncl > 1 ? 2 : 1;
-  cudaLaunchKernelEx(&cfg, k_coarse_solve<T>, Dinv, Ac, L, G, cpl, rc, uc, xmid, xflag, err, active);
+  const int nwc = plan.threads / 32 - 1;
+  const bool one = (plan.R + nwc - 1) / nwc == 1;
+  cudaLaunchKernelEx(&cfg, one ? k_coarse_solve<T, 1> : k_coarse_solve<T, kRPW>, Lm, Up, L, G, uc, xmid, xflag, err,
+                     active);
+}
+
+template <typename TO>
+void launch_coarse_couple(const double2* D64, TO* Lm, TO* Up, const StencilView<double>& Ac, const CoarseLayout& L,
+                          int nsm, cudaStream_t s) {
+  int ncls = 1;
+  for (int ax = 0; ax < Ac.g.dim; ++ax) ncls *= Ac.g.C1;
+  const size_t smem = sizeof(double2) * (size_t)ncls * Ac.g.noff;
+  k_couple<TO><<<nsm * 8, 256, smem, s>>>(D64, Lm, Up, Ac, L);
 }
 
 template <typename T>
@@ -870,69 +1019,22 @@ int launch_coarse_factor(c2<T>* Dinv, c2<T>* tmp, c2<T>* piv, unsigned* bar, int
   return launch(mid, mid, 1);
 }
 
-int coupling_max(const GridDesc& g) {
-  int m = g.R;
-  for (int ax = 0; ax < g.dim - 1; ++ax) m *= 2 * g.R + 1;
-  return m;
-}
-
-// Coupling lists of the block-tridiagonal coarse matrix, per in-block index i:
-// the in-plane part of its class, its row in the block, and the box offsets o
-// whose neighbour lies in the previous (dn) / next (up) block, packed as
-// o | (neighbour's in-block index << 8), -1 terminated. They do not depend on
-// the block: only the class along the last axis does, and the kernel adds it.
-void coupling_lists(const GridDesc& g, const CoarseLayout& L, std::vector<int>& out) {
-  const int B = L.B, maxc = coupling_max(g);
-  out.assign(2 * (size_t)B + 2 * (size_t)B * maxc, -1);
-  int* clo = out.data();
-  int* dn = clo + 2 * B;
-  int* up = dn + (size_t)B * maxc;
-  const int side = 2 * g.R + 1;
-  for (int i = 0; i < B; ++i) {
-    int row = i / L.plane, t = i - row * L.plane, a[3] = {0, 0, 0}, lo = 0, mul = 1;
-    for (int ax = 0; ax < g.dim - 1; ++ax) {
-      a[ax] = t % g.W;
-      t /= g.W;
-      lo += axis_class(a[ax], g.W, g.R, g.q) * mul;
-      mul *= g.C1;
-    }
-    clo[i] = lo;
-    clo[B + i] = row;
-    int nd = 0, nu = 0;
-    for (int o = 0; o < g.noff; ++o) {
-      int d[3] = {0, 0, 0}, oo = o;
-      for (int ax = 0; ax < g.dim; ++ax) {
-        d[ax] = oo % side - g.R;
-        oo /= side;
-      }
-      int inpl = 0, m2 = 1;
-      bool ok = true;
-      for (int ax = 0; ax < g.dim - 1; ++ax) {
-        int b = a[ax] + d[ax];
-        ok &= (b >= 0 && b < g.W);
-        inpl += b * m2;
-        m2 *= g.W;
-      }
-      if (!ok) continue;
-      int rr = row + d[g.dim - 1];
-      if (rr < 0 && nd < maxc) dn[(size_t)i * maxc + nd++] = o | (((rr + L.rows) * L.plane + inpl) << 8);
-      if (rr >= L.rows && nu < maxc) up[(size_t)i * maxc + nu++] = o | (((rr - L.rows) * L.plane + inpl) << 8);
-    }
-  }
-}
-
 void launch_convert_factor(const double2* src, float2* dst, size_t n, cudaStream_t s) {
   k_convert<<<152 * 8, 256, 0, s>>>(src, dst, n);
 }
 
-template int plan_coarse_solve<float>(const CoarseLayout&, const GridDesc&, CoarsePlan*);
-template int plan_coarse_solve<double>(const CoarseLayout&, const GridDesc&, CoarsePlan*);
-template void launch_coarse_solve<float>(const CoarsePlan&, const float2*, const StencilView<float>&,
-                                         const CoarseLayout&, const int*, const float2*, float2*, float2*,
-                                         int*, int*, const int*, cudaStream_t);
-template void launch_coarse_solve<double>(const CoarsePlan&, const double2*, const StencilView<double>&,
-                                          const CoarseLayout&, const int*, const double2*, double2*,
-                                          double2*, int*, int*, const int*, cudaStream_t);
+template int plan_coarse_solve<float>(const CoarseLayout&, CoarsePlan*);
+template int plan_coarse_solve<double>(const CoarseLayout&, CoarsePlan*);
+template void launch_coarse_solve<float>(const CoarsePlan&, const float2*, const float2*, const float2*,
+                                         const CoarseLayout&, const float2*, float2*, float2*, int*, unsigned*,
+                                         int*, const int*, int, cudaStream_t);
+template void launch_coarse_solve<double>(const CoarsePlan&, const double2*, const double2*, const double2*,
+                                          const CoarseLayout&, const double2*, double2*, double2*, int*, unsigned*,
+                                          int*, const int*, int, cudaStream_t);
+template void launch_coarse_couple<float2>(const double2*, float2*, float2*, const StencilView<double>&,
+                                           const CoarseLayout&, int, cudaStream_t);
+template void launch_coarse_couple<double2>(const double2*, double2*, double2*, const StencilView<double>&,
+                                            const CoarseLayout&, int, cudaStream_t);
 template int launch_coarse_factor<double>(double2*, double2*, double2*, unsigned*, int*,
                                           const StencilView<double>&, const CoarseLayout&, int, cudaStream_t);
 template int launch_coarse_factor<float>(float2*, float2*, float2*, unsigned*, int*,

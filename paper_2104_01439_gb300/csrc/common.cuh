@@ -125,34 +125,39 @@ struct CoarseLayout {
 #if defined(__CUDACC__)
 // ----------------------------------------------------------------------------
 // Bounded software grid barrier for cooperative launches.
-// state[0] = arrival counter, state[1] = generation. On timeout the kernel's
-// error word gets HELM_ETIMEOUT and the barrier returns false.
+// state[0] = arrival counter, state[1] = generation. Every thread reads the
+// generation before its CTA arrives; thread 0 arrives after the CTA barrier
+// that closes the phase; then EVERY thread polls until the generation moves on
+// (lane-uniform, one load per warp), so no thread depends on a CTA barrier
+// placed after a wait to learn that the grid barrier opened.
+// On timeout the kernel's error word gets HELM_ETIMEOUT and it returns false.
 // ----------------------------------------------------------------------------
 __device__ inline bool grid_barrier(unsigned* state, int* err, unsigned nblocks) {
+  const unsigned gen = *(volatile unsigned*)(state + 1);
   __syncthreads();
-  __shared__ int ok_s;
   if (threadIdx.x == 0) {
-    int ok = 1;
-    volatile unsigned* vgen = state + 1;
-    unsigned gen = *vgen;
     __threadfence();
-    unsigned arrived = atomicAdd(state, 1u);
+    const unsigned arrived = atomicAdd(state, 1u);
     if (arrived == nblocks - 1) {
       atomicExch(state, 0u);
       __threadfence();
       atomicAdd(state + 1, 1u);
-    } else {
-      long long spins = 0;
-      while (*vgen == gen) {
-        if (++spins > (1ll << 24)) { atomicExch(err, HELM_ETIMEOUT); ok = 0; break; }
-        if (*(volatile int*)err != 0) { ok = 0; break; }
-      }
     }
-    __threadfence();
-    ok_s = ok;
   }
-  __syncthreads();
-  return ok_s != 0;
+  bool ok = true;
+  for (long long spins = 0; *(volatile unsigned*)(state + 1) == gen;) {
+    if (++spins > (1ll << 22)) {
+      atomicCAS(err, 0, HELM_ETIMEOUT);
+      ok = false;
+      break;
+    }
+    if (*(volatile int*)err != 0) {
+      ok = false;
+      break;
+    }
+  }
+  __threadfence();
+  return ok;
 }
 #endif
 

@@ -55,26 +55,31 @@ void launch_coarse_unpack(const GridDesc& gc, const CoarseLayout& L, const Vin* 
 
 // ---- coarse level (coarse.cu) ----------------------------------------------
 struct CoarsePlan {
+  int grid;     // 1: whole-grid chain (blocks too large for a cluster), 0: cluster kernel
   int ncl;      // clusters: 2 = twisted (top and bottom chains), 1 = single chain
   int CS;       // cluster size
   int R;        // rows per CTA
   int CW;       // columns per pipeline chunk (even)
   int nchunk;   // chunks per step
   int S;        // pipeline stages
+  int nblk;     // CTAs of the grid kernel
   size_t smem;  // dynamic shared memory bytes
   int threads;
 };
 template <typename T>
-int plan_coarse_solve(const CoarseLayout& L, const GridDesc& gc, CoarsePlan* plan);
-// uc = A^{-1} rc for the block-padded coarse vectors; L.mid < L.nb - 1 runs the
-// twisted form on two clusters (xmid: 2 x ldb, xflag: 2 ints of exchange space).
+int plan_coarse_solve(const CoarseLayout& L, CoarsePlan* plan);
+// uc = A^{-1} rc for the block-padded coarse vectors (uc also holds the block-diagonal
+// pre-pass p = Dinv r). L.mid < L.nb - 1 runs the twisted form on two clusters
+// (xmid: 2 x ldb values, xflag: 2 x ldb ints of exchange space); bar: 2 unsigned for the
+// grid kernel's barrier.
 template <typename T>
-void launch_coarse_solve(const CoarsePlan& plan, const c2<T>* Dinv, const StencilView<T>& Ac,
-                         const CoarseLayout& L, const int* cpl, const c2<T>* rc, c2<T>* uc, c2<T>* xmid,
-                         int* xflag, int* err, const int* active, cudaStream_t s);
-// host-built coupling lists of the coarse blocks (uploaded once per handle)
-int coupling_max(const GridDesc& g);
-void coupling_lists(const GridDesc& g, const CoarseLayout& L, std::vector<int>& out);
+void launch_coarse_solve(const CoarsePlan& plan, const c2<T>* Dinv, const c2<T>* Lm, const c2<T>* Up,
+                         const CoarseLayout& L, const c2<T>* rc, c2<T>* uc, c2<T>* xmid, int* xflag,
+                         unsigned* bar, int* err, const int* active, int nsm, cudaStream_t s);
+// Lm[J] = Dinv[J] A_J,J-1 and Up[J] = Dinv[J] A_J,J+1 from the FP64 inverses (nb x B x ldb each)
+template <typename TO>
+void launch_coarse_couple(const double2* D64, TO* Lm, TO* Up, const StencilView<double>& Ac, const CoarseLayout& L,
+                          int nsm, cudaStream_t s);
 // Block-Thomas factorisation: Dinv[J] = (A_JJ - A_J,J-1 Dinv[J-1] A_J-1,J)^{-1}.
 // tmp: 2 x B x ldb; piv: 2 x factor_workspace(L) elements; bar: 4 unsigned
 // (two halves of the grid factor the top and bottom chains concurrently).
