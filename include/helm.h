@@ -155,6 +155,11 @@ int helm_rhs_planewave(helm_t h, double theta, void* F_host);
 /* Load vector of f = exp(-|x - c|^2 / (2 sigma^2)) with g = 0: F = M (I_h f). */
 int helm_rhs_gaussian(helm_t h, double sigma, double cx, double cy, double cz, void* F_host);
 
+/* The same two load vectors without a handle (host only), for the mesh of
+ * (dim, order, h): F_host receives complex128[(order/h + 1)^dim]. */
+int helm_load_planewave(int dim, int order, double h, double k, double theta, void* F_host);
+int helm_load_gaussian(int dim, int order, double h, double sigma, double cx, double cy, double cz, void* F_host);
+
 /* ---- individual hot-path steps (device complex128 buffers) ------------- */
 
 /* y = A x with A = A0 (which = 0) or A_eps (which = 1), matrix-free, FP64 (Sec. 6). */
@@ -207,6 +212,76 @@ int helm_last_profile(helm_t h, int cap, const char** names, double* ms, int* ca
 
 /* Enable (1) / disable (0) per-phase CUDA-event timing inside helm_solve (default off). */
 int helm_set_profiling(helm_t h, int on);
+
+/* ---- request server: continuous batching of independent solves ----------
+ *
+ * A solve request carries its own (k, h, order, shift, opts). The server
+ * admits requests first-in first-out while the sum of their device-memory
+ * estimates (helm_request_bytes) stays within the budget and fewer than
+ * max_active are in flight; each admitted request gets its own CUDA stream and
+ * handle (operators, coarse factor, Krylov basis), its set-up runs on a setup
+ * thread, and one stepping thread advances every admitted solve without
+ * blocking (the captured FGMRES iterations of different requests overlap on
+ * the device). A finished request's solution is copied to its host buffer,
+ * its handle is destroyed and its memory returns to the budget, which admits
+ * the next waiting requests. This is the loop a shift-map study needs: many
+ * sample solves of different (k, h, shift) in flight at once (Sec. 5, data
+ * generation). The paper itself solves one problem at a time.
+ * Every result is the same as the result of the same request solved alone:
+ * the kernels, launch shapes and reductions do not depend on the mix.
+ */
+typedef struct helm_server* helm_server_t;
+
+typedef struct {
+  double k;         /* wavenumber > 0                                        */
+  double h;         /* mesh size: 1/h an even integer >= 4                   */
+  int order;        /* 1 or 2 (order 1 only in 3D)                           */
+  double shift;     /* epsilon >= 0 of A(k, eps)                             */
+  helm_opts opts;   /* dim, omega, nu, restart, maxit, tol, precision; the
+                       server owns the streams (opts.stream is ignored)      */
+} helm_request;
+
+typedef struct {
+  int rc;               /* HELM_OK, or the error that ended this request     */
+  helm_result res;      /* the solve's result (valid when rc == HELM_OK)     */
+  float setup_ms;       /* device time of the coarse factorisation           */
+  double t_submit;      /* host times in seconds since helm_server_create:   */
+  double t_admit;       /*   submitted, admitted (memory reserved),          */
+  double t_start;       /*   set up and solving,                             */
+  double t_done;        /*   finished (solution in x_host)                   */
+  size_t bytes;         /* device bytes reserved for the request             */
+} helm_ticket_info;
+
+/* Peak device bytes of one request (set-up workspace included); host only. */
+int helm_request_bytes(const helm_request* r, size_t* bytes);
+
+/* Device bytes currently held by a handle. */
+int helm_device_bytes(helm_t h, size_t* bytes);
+
+/* Start a server on the current CUDA device. budget_bytes > 0; max_active >= 1. */
+int helm_server_create(size_t budget_bytes, int max_active, helm_server_t* out);
+
+/*
+ * Queue a request. F_host: host complex128[N] load vector, copied before the
+ * call returns. x_host: host complex128[N] that receives the solution when the
+ * request finishes (NULL: discard); it must stay valid until then.
+ * A request whose estimate exceeds the whole budget fails at once with
+ * HELM_ENOMEM (in its ticket); invalid parameters return HELM_EINVAL here.
+ */
+int helm_server_submit(helm_server_t s, const helm_request* r, const void* F_host, void* x_host,
+                       int64_t* ticket);
+
+/* Non-blocking: *done = 1 and info filled when the ticket has finished. */
+int helm_server_poll(helm_server_t s, int64_t ticket, int* done, helm_ticket_info* info);
+
+/* Block until the ticket has finished; fills info (may be NULL). */
+int helm_server_wait(helm_server_t s, int64_t ticket, helm_ticket_info* info);
+
+/* Block until every submitted request has finished. */
+int helm_server_drain(helm_server_t s);
+
+/* Drain, stop the server's threads and free everything. NULL is ignored. */
+void helm_server_destroy(helm_server_t s);
 
 #ifdef __cplusplus
 }

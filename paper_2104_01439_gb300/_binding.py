@@ -23,6 +23,8 @@ EXPORTS = [
     "helm_solve", "helm_solve_host", "helm_batch_solve", "helm_destroy", "helm_strerror",
     "helm_rhs_planewave", "helm_rhs_gaussian", "helm_apply", "helm_vcycle", "helm_coarse_solve",
     "helm_last_profile", "helm_set_profiling", "helm_coarse_solve_noalloc",
+    "helm_request_bytes", "helm_device_bytes", "helm_server_create", "helm_server_submit", "helm_server_poll",
+    "helm_server_wait", "helm_server_drain", "helm_server_destroy", "helm_load_planewave", "helm_load_gaussian",
 ]
 
 
@@ -36,6 +38,17 @@ class HelmResult(ctypes.Structure):
     _fields_ = [("iters", ctypes.c_int), ("cycles", ctypes.c_int), ("status", ctypes.c_int),
                 ("relres_true", ctypes.c_double), ("relres_est", ctypes.c_double),
                 ("solve_ms", ctypes.c_float), ("kernels", ctypes.c_int)]
+
+
+class HelmRequest(ctypes.Structure):
+    _fields_ = [("k", ctypes.c_double), ("h", ctypes.c_double), ("order", ctypes.c_int), ("shift", ctypes.c_double),
+                ("opts", HelmOpts)]
+
+
+class HelmTicketInfo(ctypes.Structure):
+    _fields_ = [("rc", ctypes.c_int), ("res", HelmResult), ("setup_ms", ctypes.c_float),
+                ("t_submit", ctypes.c_double), ("t_admit", ctypes.c_double), ("t_start", ctypes.c_double),
+                ("t_done", ctypes.c_double), ("bytes", ctypes.c_size_t)]
 
 
 class HelmError(RuntimeError):
@@ -79,8 +92,21 @@ def load(path: str = LIB_PATH):
                                       ctypes.POINTER(i), ctypes.POINTER(i)]
     lib.helm_set_profiling.argtypes = [vp, i]
     lib.helm_coarse_solve_noalloc.argtypes = [vp, vp, vp]
+    szp = ctypes.POINTER(ctypes.c_size_t)
+    lib.helm_request_bytes.argtypes = [ctypes.POINTER(HelmRequest), szp]
+    lib.helm_device_bytes.argtypes = [vp, szp]
+    lib.helm_server_create.argtypes = [ctypes.c_size_t, i, ctypes.POINTER(vp)]
+    lib.helm_server_submit.argtypes = [vp, ctypes.POINTER(HelmRequest), vp, vp, i64p]
+    lib.helm_server_poll.argtypes = [vp, ctypes.c_int64, ctypes.POINTER(i), ctypes.POINTER(HelmTicketInfo)]
+    lib.helm_server_wait.argtypes = [vp, ctypes.c_int64, ctypes.POINTER(HelmTicketInfo)]
+    lib.helm_server_drain.argtypes = [vp]
+    lib.helm_server_destroy.argtypes = [vp]
+    lib.helm_server_destroy.restype = None
+    lib.helm_load_planewave.argtypes = [i, i, d, d, d, vp]
+    lib.helm_load_gaussian.argtypes = [i, i, d, d, d, d, d, vp]
     for name in EXPORTS:
-        if name not in ("helm_default_opts", "helm_destroy", "helm_strerror", "helm_last_cuda_error"):
+        if name not in ("helm_default_opts", "helm_destroy", "helm_strerror", "helm_last_cuda_error",
+                        "helm_server_destroy"):
             getattr(lib, name).restype = i
     _lib = lib
     return lib
@@ -224,3 +250,106 @@ def batch_solve(solvers, Fs, xs=None):
     res = (HelmResult * n)()
     _check(load().helm_batch_solve(n, hs, fp, xp, res))
     return xs, [_res(r) for r in res]
+
+
+# ---------------------------------------------------------------------------- request server
+
+def make_request(k: float, n: int, order: int = 1, shift: float = 0.0, dim: int = 2, omega: float = 0.6,
+                 nu: int = 2, restart: int = 50, maxit: int = 500, tol: float = 1e-8,
+                 precision: int = HELM_MIXED) -> HelmRequest:
+    lib = load()
+    o = HelmOpts()
+    lib.helm_default_opts(ctypes.byref(o))
+    o.dim, o.omega, o.nu, o.restart, o.maxit, o.tol, o.precision = dim, omega, nu, restart, maxit, tol, precision
+    return HelmRequest(float(k), 1.0 / n, order, float(shift), o)
+
+
+def request_bytes(req: HelmRequest) -> int:
+    """Peak device bytes the server reserves for one request (host-side estimate)."""
+    b = ctypes.c_size_t()
+    _check(load().helm_request_bytes(ctypes.byref(req), ctypes.byref(b)))
+    return b.value
+
+
+def num_dofs(req: HelmRequest) -> int:
+    n = round(1.0 / req.h)
+    return (req.order * n + 1) ** req.opts.dim
+
+
+@dataclass
+class TicketInfo:
+    rc: int
+    result: SolveResult
+    setup_ms: float
+    t_submit: float
+    t_admit: float
+    t_start: float
+    t_done: float
+    bytes: int
+
+    @property
+    def latency(self) -> float:
+        return self.t_done - self.t_submit
+
+
+def _info(i: HelmTicketInfo) -> TicketInfo:
+    return TicketInfo(i.rc, _res(i.res), i.setup_ms, i.t_submit, i.t_admit, i.t_start, i.t_done, i.bytes)
+
+
+class Server:
+    """helm_server_*: admits solve requests by a device-memory budget and overlaps them on the GPU."""
+
+    def __init__(self, budget_bytes: int, max_active: int = 8):
+        self._s = ctypes.c_void_p()
+        _check(load().helm_server_create(int(budget_bytes), int(max_active), ctypes.byref(self._s)))
+        self._keep = {}
+
+    def submit(self, req: HelmRequest, F_host, x_host=None) -> int:
+        """F_host: CPU complex128 tensor (copied at once); x_host: CPU complex128 tensor or None."""
+        t = ctypes.c_int64()
+        xp = ctypes.c_void_p(x_host.data_ptr()) if x_host is not None else None
+        _check(load().helm_server_submit(self._s, ctypes.byref(req), _ptr(F_host), xp, ctypes.byref(t)))
+        if x_host is not None:
+            self._keep[t.value] = x_host   # must outlive the request
+        return t.value
+
+    def poll(self, ticket: int):
+        done = ctypes.c_int()
+        info = HelmTicketInfo()
+        _check(load().helm_server_poll(self._s, ticket, ctypes.byref(done), ctypes.byref(info)))
+        return _info(info) if done.value else None
+
+    def wait(self, ticket: int) -> TicketInfo:
+        info = HelmTicketInfo()
+        _check(load().helm_server_wait(self._s, ticket, ctypes.byref(info)))
+        self._keep.pop(ticket, None)
+        return _info(info)
+
+    def drain(self):
+        _check(load().helm_server_drain(self._s))
+
+    def close(self):
+        if self._s:
+            load().helm_server_destroy(self._s)
+            self._s = ctypes.c_void_p()
+            self._keep.clear()
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def load_planewave(req: HelmRequest, theta: float = 0.3):
+    """Host complex128 load vector of the plane wave exp(i k d.x), d = (cos theta, sin theta)."""
+    import torch
+    F = torch.empty(num_dofs(req), dtype=torch.complex128)
+    _check(load().helm_load_planewave(req.opts.dim, req.order, req.h, req.k, theta, ctypes.c_void_p(F.data_ptr())))
+    return F

@@ -11,6 +11,7 @@
 #include <vector>
 
 #include "kernels.cuh"
+#include "runtime.h"
 
 using namespace helm;
 
@@ -65,6 +66,7 @@ struct helm_ctx {
   // Krylov
   KrylovBufs kb{};
   KState* st_h = nullptr;   // pinned mirror
+  int* err_h = nullptr;     // pinned mirror of the error word (read without blocking)
   int* err = nullptr;
   double2* rres = nullptr;  // true residual buffer
   double2* Fdev = nullptr;  // staging for host solves
@@ -76,10 +78,14 @@ struct helm_ctx {
   int iter_nodes = 0;          // kernel nodes in the captured iteration graph
   Profile prof;
   std::vector<void*> allocs;
+  size_t bytes = 0;            // device bytes held by the handle
 
-  template <typename P> cudaError_t alloc(P** p, size_t bytes) {
-    cudaError_t e = cudaMalloc((void**)p, std::max<size_t>(bytes, 16));
-    if (e == cudaSuccess) allocs.push_back(*p);
+  template <typename P> cudaError_t alloc(P** p, size_t nbytes) {
+    cudaError_t e = cudaMalloc((void**)p, std::max<size_t>(nbytes, 16));
+    if (e == cudaSuccess) {
+      allocs.push_back(*p);
+      bytes += std::max<size_t>(nbytes, 16);
+    }
     return e;
   }
   template <typename T> Prec<T>& prec();
@@ -403,6 +409,8 @@ bool solve_step(SolveTask& t, bool blocking) {
       launch_norm(kb, h->rres, 1, s);
       t.kernels += 5;
       cudaMemcpyAsync(h->st_h, kb.st, sizeof(KState), cudaMemcpyDeviceToHost, s);
+      cudaMemcpyAsync(h->err_h, h->err, sizeof(int), cudaMemcpyDeviceToHost, s);
+      cudaEventRecord(h->e1, s);
       cudaEventRecord(t.ready, s);
       t.cycles += 1;
       t.phase = SolveTask::WAIT_END;
@@ -421,10 +429,8 @@ bool solve_step(SolveTask& t, bool blocking) {
         t.phase = SolveTask::ITER;
         return false;
       }
-      cudaEventRecord(h->e1, s);
-      cudaEventSynchronize(h->e1);
-      int e = 0;
-      cudaMemcpy(&e, h->err, sizeof(int), cudaMemcpyDeviceToHost);
+      // (the state, the error word and e1 were recorded before `ready`, which has completed)
+      const int e = *h->err_h;
       cudaError_t ce = cudaGetLastError();
       if (ce != cudaSuccess) t.rc = cuda_fail(ce);
       else if (e != 0) t.rc = e;
@@ -454,6 +460,63 @@ bool solve_step(SolveTask& t, bool blocking) {
 }
 
 }  // namespace
+
+// ---- resumable solves and memory accounting for the request server (serve.cu) ----
+namespace helm {
+struct Task {
+  SolveTask t;
+  helm_result res{};
+};
+int task_create(helm_t h, const double2* F, double2* x, Task** out) {
+  Task* k = new (std::nothrow) Task();
+  if (!k) return HELM_ENOMEM;
+  k->t = SolveTask{h, F, x, &k->res};
+  int rc = solve_begin(k->t);
+  if (rc) {
+    delete k;
+    return rc;
+  }
+  *out = k;
+  return HELM_OK;
+}
+bool task_step(Task* k, bool blocking, helm_result* res, int* rc) {
+  if (!solve_step(k->t, blocking)) return false;
+  if (res) *res = k->res;
+  if (rc) *rc = k->t.rc;
+  return true;
+}
+void task_destroy(Task* k) {
+  if (k && k->t.ready) cudaEventDestroy(k->t.ready);
+  delete k;
+}
+size_t handle_bytes(helm_t h) { return h ? h->bytes : 0; }
+
+// Peak device bytes of helm_setup + helm_solve for one problem (mirrors the
+// allocations of setup_impl / setup_prec; the coefficient tables are bounded by
+// a fixed 1 MiB). Includes the FP64 factor workspace that setup frees again.
+size_t estimate_bytes(int dim, int order, int n, int precision, int restart) {
+  auto ipow = [](int64_t b, int d) {
+    int64_t r = 1;
+    for (int i = 0; i < d; ++i) r *= b;
+    return r;
+  };
+  const int64_t N = ipow((int64_t)order * n + 1, dim);
+  const int64_t Wc = (int64_t)order * (n / 2) + 1;
+  const int64_t rows = order, plane = ipow(Wc, dim - 1);
+  const int64_t nb = (Wc + rows - 1) / rows, B = rows * plane, ldb = (B + 1) & ~int64_t(1);
+  const int64_t blk = B * ldb;
+  const int64_t v = precision == HELM_MIXED ? 8 : 16;
+  const int64_t m = restart, ldN = (N + 31) & ~int64_t(31), nblk = std::max<int64_t>(1, (N + 255) / 256);
+  const int64_t prec = v * (4 * N + 2 * nb * ldb + 2 * ldb) + 4 * 2 * ldb + 64;
+  const int64_t factor = v * 3 * blk * nb;                        // Dinv, Lm, Up
+  const int64_t krylov = 16 * ldN * (m + 1) + 16 * 3 * ldN + 16 * ldN * m + 16 * ldN +
+                         16 * nblk * (m + 2) + 16 * (m + 2) * (m + 4);
+  const int64_t tables = 1 << 20;
+  const int64_t transient = (precision == HELM_MIXED ? 16 * blk * nb : 0) + 16 * 2 * blk +
+                            16 * 2 * (16 * ldb + 16 * B) + 64;
+  return (size_t)(prec + factor + krylov + tables + transient);
+}
+}  // namespace helm
 
 // ============================================================================
 extern "C" {
@@ -492,6 +555,7 @@ void helm_destroy(helm_t h) {
   if (h->iter) cudaGraphExecDestroy(h->iter);
   for (void* p : h->allocs) cudaFree(p);
   if (h->st_h) cudaFreeHost(h->st_h);
+  if (h->err_h) cudaFreeHost(h->err_h);
   if (h->e0) cudaEventDestroy(h->e0);
   if (h->e1) cudaEventDestroy(h->e1);
   for (auto& e : h->prof.ev) cudaEventDestroy(e);
@@ -593,6 +657,7 @@ static int setup_impl(helm_ctx* h) {
   } else {
     h->p64.Dinv = D64;
     h->allocs.push_back(D64);
+    h->bytes += sizeof(double2) * blk * L.nb;
   }
 
   // Krylov storage
@@ -619,6 +684,7 @@ static int setup_impl(helm_ctx* h) {
   CK(h->alloc(&kb.st, sizeof(KState)));
   CK(h->alloc(&h->rres, sizeof(double2) * kb.ldN));
   CK(cudaMallocHost(&h->st_h, sizeof(KState)));
+  CK(cudaMallocHost(&h->err_h, sizeof(int)));
   CK(cudaMemsetAsync(kb.Vs, 0, sizeof(float4) * kb.ldN * (m + 1), s));
   CK(cudaMemsetAsync(kb.vj, 0, sizeof(double2) * kb.ldN, s));
   CK(cudaMemsetAsync(kb.W, 0, sizeof(double2) * kb.ldN, s));
@@ -741,6 +807,29 @@ int helm_rhs_gaussian(helm_t h, double sigma, double cx, double cy, double cz, v
   if (!h || !F_host || !(sigma > 0)) return HELM_EINVAL;
   double c[3] = {cx, cy, cz};
   rhs_gaussian(h->dim, h->order, h->n, sigma, c, (double2*)F_host);
+  return HELM_OK;
+}
+
+static int mesh_n(int dim, int order, double h) {
+  if (!(h > 0) || !(dim == 2 || dim == 3) || !(order == 1 || order == 2) || (dim == 3 && order != 1)) return -1;
+  const double nn = 1.0 / h;
+  const int n = (int)std::lround(nn);
+  if (std::fabs(nn - n) > 1e-9 * nn || n < 4 || n % 2) return -1;
+  return n;
+}
+
+int helm_load_planewave(int dim, int order, double h, double k, double theta, void* F_host) {
+  const int n = mesh_n(dim, order, h);
+  if (n < 0 || !F_host || !(k > 0)) return HELM_EINVAL;
+  rhs_planewave(dim, order, n, k, theta, (double2*)F_host);
+  return HELM_OK;
+}
+
+int helm_load_gaussian(int dim, int order, double h, double sigma, double cx, double cy, double cz, void* F_host) {
+  const int n = mesh_n(dim, order, h);
+  if (n < 0 || !F_host || !(sigma > 0)) return HELM_EINVAL;
+  double c[3] = {cx, cy, cz};
+  rhs_gaussian(dim, order, n, sigma, c, (double2*)F_host);
   return HELM_OK;
 }
 

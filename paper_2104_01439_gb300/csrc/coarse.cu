@@ -26,6 +26,8 @@
 // (st.shared::cluster), one cluster barrier ends the step, and each CTA then
 // applies the sparse coupling for the next block locally.
 #include <algorithm>
+#include <mutex>
+#include <unordered_map>
 
 #include "kernels.cuh"
 
@@ -822,6 +824,9 @@ __global__ void __launch_bounds__(256) k_coarse_solve_grid(const c2<T>* __restri
 
 }  // namespace
 
+std::mutex g_twist_mu;
+std::unordered_map<long long, bool> g_twist_ok;   // launch shape -> two clusters co-resident
+
 template <typename T>
 int plan_coarse_solve(const CoarseLayout& L, CoarsePlan* plan) {
   int dev = 0;
@@ -871,8 +876,19 @@ int plan_coarse_solve(const CoarseLayout& L, CoarsePlan* plan) {
         plan->smem = G.total;
         plan->threads = 32 * nwarps;
         plan->ncl = 1;
-        // Twisted form: two co-resident clusters (cooperative launch). Validated by an
-        // inert trial launch whose 'active' flag is 0 (the kernel returns at entry).
+        // Twisted form: two co-resident clusters (cooperative launch). Validated once per
+        // launch shape by an inert trial launch whose 'active' flag is 0 (the kernel
+        // returns at entry); the answer is cached (the trial synchronises the device).
+        const long long key = ((long long)sizeof(T) << 56) ^ ((long long)CS << 48) ^ ((long long)nwarps << 40) ^
+                              (long long)G.total ^ ((long long)dev << 32);
+        {
+          std::lock_guard<std::mutex> lk(g_twist_mu);
+          auto it = g_twist_ok.find(key);
+          if (it != g_twist_ok.end()) {
+            plan->ncl = (L.nb >= 4 && ncl >= 2 && it->second) ? 2 : 1;
+            return HELM_OK;
+          }
+        }
         if (L.nb >= 4 && ncl >= 2) {
           int* off = nullptr;
           if (cudaMalloc(&off, sizeof(int)) == cudaSuccess) {
@@ -893,6 +909,8 @@ int plan_coarse_solve(const CoarseLayout& L, CoarsePlan* plan) {
             if (e == cudaSuccess) plan->ncl = 2;
             cudaGetLastError();
             cudaFree(off);
+            std::lock_guard<std::mutex> lk(g_twist_mu);
+            g_twist_ok[key] = plan->ncl == 2;
           }
         }
         return HELM_OK;

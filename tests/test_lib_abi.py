@@ -45,3 +45,22 @@ def test_product_path_has_no_cpu_fallback():
             if f.endswith(".py"):
                 txt = open(os.path.join(dirpath, f)).read()
                 assert not re.search(r"^\s*(from|import)\s+oracle", txt, flags=re.M), f
+
+
+def test_request_bytes_estimate_is_host_only_and_consistent():
+    """helm_request_bytes is pure host arithmetic: monotone in the mesh, the restart
+    length and the precision, and it counts the dense coarse blocks (nb * B^2 entries)."""
+    pytest.importorskip("torch")
+    from paper_2104_01439_gb300 import _binding, build
+    _binding.load(build.build())
+    rb = lambda **kw: _binding.request_bytes(_binding.make_request(100.0, **kw))  # noqa: E731
+    small, big = rb(n=64), rb(n=128)
+    assert 0 < small < big
+    assert rb(n=128, restart=80) > rb(n=128, restart=50)
+    assert rb(n=128, precision=_binding.HELM_FP64) > rb(n=128, precision=_binding.HELM_MIXED)
+    # 2D P1 n=512: three complex64 coarse matrices (Dinv, Lm, Up) of 257 blocks of 257 x 258
+    # plus the FP64 factor workspace: the estimate must cover at least those
+    coarse = 3 * 257 * 257 * 258 * 8 + 257 * 257 * 258 * 16
+    assert rb(n=512, restart=80) > coarse
+    with pytest.raises(_binding.HelmError):
+        rb(n=63)   # 1/h must be even
