@@ -147,6 +147,14 @@ def golden_section(problems, tol: float = 1e-2, maxit: int = 50, precision: int 
 
 # ---------------------------------------------------------------------------- the map
 
+# (kc0, kc1, a0, a1) per element order p as printed in Sec. 5, Table tab:optweights
+# (fitted by the paper for its Q_p elements); a default map until a sweep is fitted.
+PAPER_SHIFT_WEIGHTS = {
+    1: (0.4592788619853418, 2.5790032999702346, -0.6261637288068426, 1.7580549857142198),
+    2: (0.5736926870738827, 2.5729974893966001, -0.6615199737374460, 1.5966386518185063),
+    3: (0.6305770719029798, 2.4284320222555804, -0.4465407372367102, 0.1287828338493968),
+}
+
 def shift_exponent(params, k, ell):
     """Sec. 5, eq. shiftexp: sigma_p(k, l) = min(max(2 - exp(-alpha(l) (k - k_c(l))), 1), 2) with
     k_c(l) = kc1 exp(kc0 l) and alpha(l) = a1 exp(a0 l); params = (kc0, kc1, a0, a1)."""

@@ -59,3 +59,8 @@ def test_fit_recovers_map():
     p, loss = sweep.fit_shift_map(k, ell, y, epochs=20_000, lr=1e-2)
     pred = sweep.shift_exponent(p, k, ell)
     assert np.sqrt(np.mean((pred - y) ** 2)) < 0.05
+
+
+def test_package_weights_are_the_papers():
+    for p in (1, 2, 3):
+        assert sweep.PAPER_SHIFT_WEIGHTS[p] == shiftmap.PAPER_WEIGHTS[p]
