@@ -211,7 +211,7 @@ int setup_prec(helm_ctx* h, const std::vector<double2>& Ae, const std::vector<do
   CK(h->alloc(&p.uc, sizeof(c2<T>) * Nc));
   CK(h->alloc(&p.xmid, sizeof(c2<T>) * 2 * h->L.ldb));
   CK(h->alloc(&p.xflag, sizeof(int) * 2 * h->L.ldb));
-  CK(h->alloc(&p.gbar, sizeof(unsigned) * 2));
+  CK(h->alloc(&p.gbar, sizeof(unsigned) * kBarWords));
   if ((rc = plan_coarse_solve<T>(h->L, &p.plan))) return rc;
   // the elimination order (one chain, or two chains meeting in the middle) is fixed
   // here, before the factorisation, and used by both the factor and the solve
@@ -510,7 +510,7 @@ size_t estimate_bytes(int dim, int order, int n, int precision, int restart) {
   const int64_t prec = v * (4 * N + 2 * nb * ldb + 2 * ldb) + 4 * 2 * ldb + 64;
   const int64_t factor = v * 3 * blk * nb;                        // Dinv, Lm, Up
   const int64_t krylov = 16 * ldN * (m + 1) + 16 * 3 * ldN + 16 * ldN * m + 16 * ldN +
-                         16 * nblk * (m + 2) + 16 * (m + 2) * (m + 4);
+                         16 * std::max<int64_t>(nblk, (N + 127) / 128) * (m + 2) + 16 * (m + 2) * (m + 4);
   const int64_t tables = 1 << 20;
   const int64_t transient = (precision == HELM_MIXED ? 16 * blk * nb : 0) + 16 * 2 * blk +
                             16 * 2 * (16 * ldb + 16 * B) + 64;
@@ -599,20 +599,25 @@ static int setup_impl(helm_ctx* h) {
   }
   if ((rc = setup_prec<double>(h, Ae, wd, Ac, o.precision == HELM_FP64))) return rc;
 
-  // coarse factorisation in FP64 (Sec. 6: factor once, reuse)
+  // coarse factorisation (Sec. 6: factor once, reuse): complex128 for the FP64 form,
+  // complex double-float (16-byte float4 entries) for the mixed form, whose factor is
+  // rounded to complex64 for the V-cycle
+  const bool df = o.precision == HELM_MIXED;
   size_t blk = (size_t)L.B * L.ldb;
-  double2* D64 = nullptr;
+  double2* D64 = nullptr;   // 16 bytes per entry: double2 (FP64) or float4 (double-float)
   double2 *tmp = nullptr, *piv = nullptr;
   unsigned* bar = nullptr;
   CK(cudaMalloc(&D64, sizeof(double2) * blk * L.nb));
   CK(cudaMalloc(&tmp, sizeof(double2) * 2 * blk));
   CK(cudaMalloc(&piv, sizeof(double2) * 2 * factor_workspace(L)));
-  CK(cudaMalloc(&bar, 4 * sizeof(unsigned)));
+  CK(cudaMalloc(&bar, 2 * kBarWords * sizeof(unsigned)));
   CK(h->alloc(&h->err, sizeof(int)));
   CK(cudaMemsetAsync(h->err, 0, sizeof(int), s));
   CK(cudaEventRecord(h->e0, s));
   StencilView<double> Acv = make_view<double>(h->gc, h->p64.coefAc, nullptr);
-  rc = launch_coarse_factor<double>(D64, tmp, piv, bar, h->err, Acv, L, h->nsm, s);
+  rc = df ? coarse_factor_df(reinterpret_cast<float4*>(D64), reinterpret_cast<float4*>(tmp),
+                             reinterpret_cast<float4*>(piv), bar, h->err, Acv, L, h->nsm, s)
+          : coarse_factor_fp64(D64, tmp, piv, bar, h->err, Acv, L, h->nsm, s);
   h->setup_kernels = std::max(L.mid, L.nb - 1 - L.mid) + 1 + 1 + (o.precision == HELM_MIXED ? 1 : 0);
   // couplings folded into the inverses: Lm[J] = Dinv[J] A_J,J-1, Up[J] = Dinv[J] A_J,J+1
   if (rc == HELM_OK && o.precision == HELM_MIXED) {
@@ -622,8 +627,8 @@ static int setup_impl(helm_ctx* h) {
         h->alloc(&p.Up, sizeof(float2) * blk * L.nb) != cudaSuccess) {
       rc = HELM_ENOMEM;
     } else {
-      launch_convert_factor(D64, p.Dinv, blk * L.nb, s);
-      launch_coarse_couple<float2>(D64, p.Lm, p.Up, Acv, L, h->nsm, s);
+      convert_factor_df(reinterpret_cast<const float4*>(D64), p.Dinv, blk * L.nb, s);
+      coarse_couple_df(reinterpret_cast<const float4*>(D64), p.Lm, p.Up, Acv, L, h->nsm, s);
     }
   } else if (rc == HELM_OK) {
     Prec<double>& p = h->p64;
@@ -631,7 +636,7 @@ static int setup_impl(helm_ctx* h) {
         h->alloc(&p.Up, sizeof(double2) * blk * L.nb) != cudaSuccess) {
       rc = HELM_ENOMEM;
     } else {
-      launch_coarse_couple<double2>(D64, p.Lm, p.Up, Acv, L, h->nsm, s);
+      coarse_couple_fp64(D64, p.Lm, p.Up, Acv, L, h->nsm, s);
     }
   }
   cudaEventRecord(h->e1, s);
@@ -668,6 +673,9 @@ static int setup_impl(helm_ctx* h) {
   // element-wise Krylov kernels: one entry per thread; inner products: <= 4 per thread
   kb.nblk = (int)std::max<int64_t>(1, (kb.N + 255) / 256);
   kb.nblk_dots = (int)std::max<int64_t>(1, (kb.N + 1023) / 1024);
+  kb.m = m;
+  kb.nblk_upd = (int)std::max<int64_t>(1, (kb.N + 127) / 128);
+  kb.pstride = std::max(kb.nblk, std::max(kb.nblk_upd, kb.nblk_dots));
   CK(h->alloc(&kb.Vs, sizeof(float4) * kb.ldN * (m + 1)));
   CK(h->alloc(&kb.vj, sizeof(double2) * kb.ldN));
   CK(h->alloc(&kb.W, sizeof(double2) * kb.ldN));
@@ -680,7 +688,7 @@ static int setup_impl(helm_ctx* h) {
   CK(h->alloc(&kb.y, sizeof(double2) * m));
   CK(h->alloc(&kb.hcol, sizeof(double2) * (m + 2)));
   CK(h->alloc(&kb.hp, sizeof(double2) * (m + 2)));
-  CK(h->alloc(&kb.part, sizeof(double2) * (size_t)kb.nblk * (m + 2)));
+  CK(h->alloc(&kb.part, sizeof(double2) * (size_t)kb.pstride * (m + 2)));
   CK(h->alloc(&kb.st, sizeof(KState)));
   CK(h->alloc(&h->rres, sizeof(double2) * kb.ldN));
   CK(cudaMallocHost(&h->st_h, sizeof(KState)));

@@ -29,6 +29,7 @@
 #include <mutex>
 #include <unordered_map>
 
+#include "dfloat.cuh"
 #include "kernels.cuh"
 
 namespace helm {
@@ -202,9 +203,61 @@ __device__ __forceinline__ bool neighbour(const GridDesc& g, const CoarseLayout&
 }
 
 // ---------------------------------------------------------------------------
+// Arithmetic of the factorisation. ArithD: complex128, 8-pivot panels.
+// ArithDF: complex double-float (float4, ~48 bits) on the FP32 pipes, 16-pivot
+// panels; used for the mixed form, whose factor is rounded to complex64 anyway.
+// ---------------------------------------------------------------------------
+struct ArithD {
+  using V = double2;
+  static constexpr int P = 8;
+  __device__ static V zero() { return make_double2(0.0, 0.0); }
+  __device__ static V one() { return make_double2(1.0, 0.0); }
+  __device__ static V from(double2 c) { return c; }
+  __device__ static V neg(V a) { return make_double2(-a.x, -a.y); }
+  __device__ static V mul(V a, V b) { return cmul(a, b); }
+  __device__ static V fma(V a, V b, V c) { return cfma(a, b, c); }   // c + a b
+  __device__ static V sub(V a, V b) { return csub(a, b); }
+  __device__ static bool inv(V d, V* out) {
+    const double mag = d.x * d.x + d.y * d.y;
+    if (!(mag > 0.0) || !isfinite(mag)) return false;
+    const double rm = 1.0 / mag;
+    *out = make_double2(d.x * rm, -d.y * rm);
+    return true;
+  }
+  struct Acc {
+    V v;
+  };
+  __device__ static Acc acc(V c) { return Acc{c}; }
+  __device__ static void fnmac(V a, V b, Acc& s) {   // s -= a b
+    s.v.x = ::fma(-a.x, b.x, s.v.x);
+    s.v.x = ::fma(a.y, b.y, s.v.x);
+    s.v.y = ::fma(-a.x, b.y, s.v.y);
+    s.v.y = ::fma(-a.y, b.x, s.v.y);
+  }
+  __device__ static V fin(Acc s) { return s.v; }
+  __device__ static double2 out(V a) { return a; }
+};
+struct ArithDF {
+  using V = float4;
+  static constexpr int P = 16;
+  __device__ static V zero() { return dfc_zero(); }
+  __device__ static V one() { return make_float4(1.f, 0.f, 0.f, 0.f); }
+  __device__ static V from(double2 c) { return dfc_from(c); }
+  __device__ static V neg(V a) { return dfc_neg(a); }
+  __device__ static V mul(V a, V b) { return dfc_mul(a, b); }
+  __device__ static V fma(V a, V b, V c) { return dfc_fma(a, b, c); }
+  __device__ static V sub(V a, V b) { return dfc_sub(a, b); }
+  __device__ static bool inv(V d, V* out) { return dfc_inv(d, out); }
+  using Acc = DFC_ACC;
+  __device__ static Acc acc(V c) { return dfc_acc(c); }
+  __device__ static void fnmac(V a, V b, Acc& s) { dfc_mac(dfc_neg(a), b, s); }
+  __device__ static V fin(Acc s) { return dfc_fin(s); }
+  __device__ static float2 out(V a) { return dfc_round(a); }
+};
+
+// ---------------------------------------------------------------------------
 // Factorisation kernel: Schur update + in-place Gauss-Jordan of block J.
 // ---------------------------------------------------------------------------
-constexpr int kGJP = 8;   // pivots per Gauss-Jordan panel (factor_workspace assumes 8)
 
 // One block to invert: S_J = A_JJ - sum over factored neighbours Jn = J + d of
 // A_{J,Jn} Dinv[Jn] A_{Jn,J}  (d = -1: block J-1 of the top chain or the middle;
@@ -215,18 +268,22 @@ struct FactorJob {
   int dir[2];
 };
 
-template <typename T>
-__global__ void __launch_bounds__(256) k_factor_block(c2<T>* D, c2<T>* Tmp, c2<T>* piv,
-                                                      unsigned* bar, int* err, StencilView<T> Ac,
+// one CTA per SM; 32 warps hide the latency of the dependent double-float chains
+constexpr int kFactorThreads = 1024;
+
+template <typename A>
+__global__ void __launch_bounds__(kFactorThreads, 1) k_factor_block(typename A::V* D, typename A::V* Tmp, typename A::V* piv,
+                                                      unsigned* bar, int* err, StencilView<double> Ac,
                                                       CoarseLayout L, FactorJob job0, FactorJob job1,
                                                       int njobs, int stageR) {
-  using V = c2<T>;
+  using V = typename A::V;
+  constexpr int P = A::P;
   extern __shared__ __align__(128) unsigned char sm[];
   const GridDesc g = Ac.g;
   int ncls = 1;
   for (int ax = 0; ax < g.dim; ++ax) ncls *= g.C1;
   V* coef = reinterpret_cast<V*>(sm);
-  for (int i = threadIdx.x; i < ncls * g.noff; i += blockDim.x) coef[i] = Ac.coef[i];
+  for (int i = threadIdx.x; i < ncls * g.noff; i += blockDim.x) coef[i] = A::from(Ac.coef[i]);
   __syncthreads();
   const int B = L.B, ldb = L.ldb;
   const int64_t blk = (int64_t)B * ldb;
@@ -240,10 +297,10 @@ __global__ void __launch_bounds__(256) k_factor_block(c2<T>* D, c2<T>* Tmp, c2<T
   const int J = job.J;
   Tmp += grp * blk;
   piv += grp * (int64_t)factor_workspace(L);
-  bar += 2 * grp;
+  bar += kBarWords * grp;
   V* S = D + J * blk;
   const int gt = lb * blockDim.x + threadIdx.x, gs = G * blockDim.x;
-  const V zero = mk(T(0), T(0));
+  const V zero = A::zero();
 
   // Tmp[a][l] = sum_{o: l+o in block J+d} A[l][l+o] Dinv[J+d][a][l+o]   (= Dinv[J+d] A_{J+d,J})
   auto tmp_phase = [&](int d) {
@@ -257,7 +314,7 @@ __global__ void __launch_bounds__(256) k_factor_block(c2<T>* D, c2<T>* Tmp, c2<T
         for (int o = 0; o < g.noff; ++o) {
           int Jn, in;
           if (!neighbour(g, L, Ac.dx, o, c, &Jn, &in) || Jn != J + d) continue;
-          acc = cfma(cl[o], X[(int64_t)aa * ldb + in], acc);
+          acc = A::fma(cl[o], X[(int64_t)aa * ldb + in], acc);
         }
       }
       Tmp[(int64_t)aa * ldb + l] = acc;
@@ -265,8 +322,8 @@ __global__ void __launch_bounds__(256) k_factor_block(c2<T>* D, c2<T>* Tmp, c2<T
   };
   // snapshots of the first Gauss-Jordan panel (pivot rows and columns)
   auto snapshot = [&](int i, int l, V v) {
-    if (l < B && i < kGJP) piv[(int64_t)i * ldb + l] = v;
-    if (l < kGJP && l < B) piv[2 * kGJP * (int64_t)ldb + (int64_t)i * kGJP + l] = v;
+    if (l < B && i < P) piv[(int64_t)i * ldb + l] = v;
+    if (l < P && l < B) piv[2 * P * (int64_t)ldb + (int64_t)i * P + l] = v;
   };
   // S = A_JJ (identity on padding rows, zero padding columns)
   for (int64_t idx = gt; idx < (int64_t)B * ldb; idx += gs) {
@@ -277,7 +334,7 @@ __global__ void __launch_bounds__(256) k_factor_block(c2<T>* D, c2<T>* Tmp, c2<T
       bool ri = block_coords(g, L, J, i, ci);
       bool rl = block_coords(g, L, J, l, cl);
       if (!ri) {
-        v = i == l ? mk(T(1), T(0)) : zero;
+        v = i == l ? A::one() : zero;
       } else if (rl) {
         const V* c = coef + class_at(g, ci) * g.noff;
         int o = 0, mul = 1;
@@ -311,11 +368,13 @@ __global__ void __launch_bounds__(256) k_factor_block(c2<T>* D, c2<T>* Tmp, c2<T
       int ci[3];
       if (block_coords(g, L, J, i, ci)) {
         const V* c = coef + class_at(g, ci) * g.noff;
+        typename A::Acc acc = A::acc(v);
         for (int oo = 0; oo < g.noff; ++oo) {
           int Jn, inb;
           if (!neighbour(g, L, Ac.dx, oo, ci, &Jn, &inb) || Jn != J + d) continue;
-          v = csub(v, cmul(c[oo], Tmp[(int64_t)inb * ldb + l]));
+          A::fnmac(c[oo], Tmp[(int64_t)inb * ldb + l], acc);
         }
+        v = A::fin(acc);
         S[idx] = v;
       }
       if (last) snapshot(i, l, v);
@@ -323,82 +382,68 @@ __global__ void __launch_bounds__(256) k_factor_block(c2<T>* D, c2<T>* Tmp, c2<T
     if (!grid_barrier(bar, err, G)) return;
   }
 
-  // In-place blocked Gauss-Jordan inversion of S (no pivoting), kGJP pivots per
-  // panel. For the panel block P = S[k0:k1, k0:k1] with pivot rows R = S[k0:k1, :]
+  // In-place blocked Gauss-Jordan inversion of S (no pivoting), P pivots per
+  // panel. For the panel block Pb = S[k0:k1, k0:k1] with pivot rows R = S[k0:k1, :]
   // and the panel columns C = S[:, k0:k1]:
-  //   pivot rows:  R <- P^{-1} R,          panel block <- P^{-1}
-  //   other rows:  S[i,:] <- S[i,:] - (C_i P^{-1}) R,   C_i <- -C_i P^{-1}
-  // which equals kGJP consecutive scalar Gauss-Jordan steps. Every CTA inverts P
+  //   pivot rows:  R <- Pb^{-1} R,          panel block <- Pb^{-1}
+  //   other rows:  S[i,:] <- S[i,:] - (C_i Pb^{-1}) R,   C_i <- -C_i Pb^{-1}
+  // which equals P consecutive scalar Gauss-Jordan steps. Every CTA inverts Pb
   // itself; R and C are read from snapshots written while the previous panel was
   // updated, so each panel needs a single grid barrier. The B x B elements are
-  // split into contiguous row-major ranges, one per CTA (FP64 work is balanced).
+  // split into contiguous row-major ranges, one per CTA (the work is balanced).
   const int64_t BB = (int64_t)B * B;
   const int64_t epb = (BB + G - 1) / G;
   const int64_t e0 = (int64_t)lb * epb, e1 = min(BB, e0 + epb);
   const int i0 = (int)(e0 / B), i1 = e1 > e0 ? (int)((e1 - 1) / B) : i0 - 1;   // rows touched
-  V* Pm = coef + ncls * g.noff;                 // kGJP x kGJP panel block -> its inverse
-  V* cP = Pm + kGJP * kGJP;                     // (rows touched) x kGJP : C_i P^{-1}
-  V* Rsm = cP + (epb / B + 3) * kGJP;            // kGJP x ldb staged pivot rows (when stageR); the
+  V* Pm = coef + ncls * g.noff;                 // P x P panel block -> its inverse
+  V* cP = Pm + P * P;                           // (rows touched) x P : C_i Pb^{-1}
+  V* Rsm = cP + (epb / B + 3) * P;              // P x ldb staged pivot rows (when stageR); the
                                                 // host sizes cP for epb / B + 3 rows (>= rows touched)
   __shared__ int gj_bad_s;
-  int* gj_bad = &gj_bad_s;
-  if (threadIdx.x == 0) gj_bad_s = 0;
-  V* pbuf = piv;                                // 2 x [kGJP x ldb]  pivot-row snapshots
-  V* cbuf = piv + 2 * kGJP * (int64_t)ldb;      // 2 x [B x kGJP]    panel-column snapshots
-  for (int k0 = 0, q = 0; k0 < B; k0 += kGJP, ++q) {
-    const int p = min(kGJP, B - k0), k1 = k0 + p, k2 = min(B, k1 + kGJP);
-    const V* R = pbuf + (int64_t)(q & 1) * kGJP * ldb;
-    const V* C = cbuf + (int64_t)(q & 1) * B * kGJP;
-    V* Rn = pbuf + (int64_t)((q + 1) & 1) * kGJP * ldb;
-    V* Cn = cbuf + (int64_t)((q + 1) & 1) * B * kGJP;
-    // (1) P^{-1}: warp 0 runs Gauss-Jordan on the p x p block in shared memory
-    // (one reciprocal per pivot, warp-synchronous; the other warps wait below)
-    for (int t = threadIdx.x; t < p * p; t += blockDim.x) Pm[(t / p) * kGJP + t % p] = R[(int64_t)(t / p) * ldb + k0 + t % p];
+  V* pbuf = piv;                                // 2 x [P x ldb]  pivot-row snapshots
+  V* cbuf = piv + 2 * P * (int64_t)ldb;         // 2 x [B x P]    panel-column snapshots
+  for (int k0 = 0, q = 0; k0 < B; k0 += P, ++q) {
+    const int p = min(P, B - k0), k1 = k0 + p, k2 = min(B, k1 + P);
+    const V* R = pbuf + (int64_t)(q & 1) * P * ldb;
+    const V* C = cbuf + (int64_t)(q & 1) * B * P;
+    V* Rn = pbuf + (int64_t)((q + 1) & 1) * P * ldb;
+    V* Cn = cbuf + (int64_t)((q + 1) & 1) * B * P;
+    // (1) Pb^{-1} by Gauss-Jordan on the p x p block in shared memory: thread t < p*p
+    // owns element t and every step is straight-line code between two CTA barriers
+    // (each owner thread forms the pivot's reciprocal itself).
+    if (threadIdx.x == 0) gj_bad_s = 0;
+    for (int t = threadIdx.x; t < p * p; t += blockDim.x) Pm[(t / p) * P + t % p] = R[(int64_t)(t / p) * ldb + k0 + t % p];
     __syncthreads();
-    if (threadIdx.x < 32) {
-      const int lane = threadIdx.x;
-      for (int kk = 0; kk < p; ++kk) {
-        const V d = Pm[kk * kGJP + kk];
-        const T mag = d.x * d.x + d.y * d.y;
-        if (!(mag > T(0)) || !isfinite(mag)) {
-          if (lane == 0) *gj_bad = 1;
-          break;
+    const int te = threadIdx.x, ta = te / p, tb = te - ta * p;
+    const bool own = te < p * p;
+    for (int kk = 0; kk < p; ++kk) {
+      V nv = zero;
+      if (own) {
+        V pinv;
+        if (!A::inv(Pm[kk * P + kk], &pinv)) {
+          gj_bad_s = 1;   // every owner sees the same pivot
+        } else if (ta == kk) {
+          nv = tb == kk ? pinv : A::mul(pinv, Pm[kk * P + tb]);
+        } else {
+          const V f = A::mul(Pm[ta * P + kk], pinv);
+          nv = tb == kk ? A::neg(f) : A::sub(Pm[ta * P + tb], A::mul(f, Pm[kk * P + tb]));
         }
-        const T rm = T(1) / mag;
-        const V pinv = mk(d.x * rm, -d.y * rm);
-        V nv[2];
-        for (int h = 0; h < 2; ++h) {
-          const int e = lane + 32 * h, a = e / p, bc = e % p;
-          nv[h] = zero;
-          if (e < p * p) {
-            if (a == kk) {
-              nv[h] = bc == kk ? pinv : cmul(pinv, Pm[kk * kGJP + bc]);
-            } else {
-              const V f = cmul(Pm[a * kGJP + kk], pinv);
-              nv[h] = bc == kk ? mk(-f.x, -f.y) : csub(Pm[a * kGJP + bc], cmul(f, Pm[kk * kGJP + bc]));
-            }
-          }
-        }
-        __syncwarp();
-        for (int h = 0; h < 2; ++h) {
-          const int e = lane + 32 * h;
-          if (e < p * p) Pm[(e / p) * kGJP + e % p] = nv[h];
-        }
-        __syncwarp();
       }
+      __syncthreads();
+      if (own) Pm[ta * P + tb] = nv;
+      __syncthreads();
     }
-    __syncthreads();
-    if (*gj_bad) {
+    if (gj_bad_s) {
       if (threadIdx.x == 0) atomicCAS(err, 0, HELM_EZEROPIVOT);
       return;   // every CTA sees the same pivot block and returns
     }
-    // (2) C_i P^{-1} for the rows this CTA touches (non-pivot rows)
+    // (2) C_i Pb^{-1} for the rows this CTA touches (non-pivot rows)
     for (int t = threadIdx.x; t < (i1 - i0 + 1) * p; t += blockDim.x) {
       int r = t / p, c = t % p, i = i0 + r;
       V acc = zero;
       if (i < k0 || i >= k1)
-        for (int s2 = 0; s2 < p; ++s2) acc = cfma(C[(int64_t)i * kGJP + s2], Pm[s2 * kGJP + c], acc);
-      cP[r * kGJP + c] = acc;
+        for (int s2 = 0; s2 < p; ++s2) acc = A::fma(C[(int64_t)i * P + s2], Pm[s2 * P + c], acc);
+      cP[r * P + c] = acc;
     }
     __syncthreads();
     // (3) element update over the CTA's row-major range, row by row (no per-element
@@ -414,8 +459,8 @@ __global__ void __launch_bounds__(256) k_factor_block(c2<T>* D, c2<T>* Tmp, c2<T
       const int je = i == i1 ? (int)(e1 - (int64_t)i1 * B) : B;
       V* Si = S + (int64_t)i * ldb;
       const bool pivrow = i >= k0 && i < k1;
-      const V* pr = Pm + (i - k0) * kGJP;       // row of P^{-1} (pivot rows)
-      const V* ci = cP + (i - i0) * kGJP;       // C_i P^{-1} (other rows)
+      const V* pr = Pm + (i - k0) * P;          // row of Pb^{-1} (pivot rows)
+      const V* ci = cP + (i - i0) * P;          // C_i Pb^{-1} (other rows)
       V* rn = (i >= k1 && i < k2) ? Rn + (int64_t)(i - k1) * ldb : nullptr;
       for (int j = jb + threadIdx.x; j < je; j += blockDim.x) {
         V nv;
@@ -424,33 +469,24 @@ __global__ void __launch_bounds__(256) k_factor_block(c2<T>* D, c2<T>* Tmp, c2<T
           if (pcol) {
             nv = pr[j - k0];
           } else {
-            nv = zero;
-            for (int s2 = 0; s2 < p; ++s2) nv = cfma(pr[s2], Rs[s2 * ldb + j], nv);
+            typename A::Acc acc = A::acc(zero);
+            for (int s2 = 0; s2 < p; ++s2) A::fnmac(A::neg(pr[s2]), Rs[s2 * ldb + j], acc);
+            nv = A::fin(acc);
           }
         } else if (pcol) {
-          nv = mk(-ci[j - k0].x, -ci[j - k0].y);
+          nv = A::neg(ci[j - k0]);
         } else {
-          nv = Si[j];
-          for (int s2 = 0; s2 < p; ++s2) {
-            const V c = ci[s2], rr = Rs[s2 * ldb + j];
-            nv.x = fma(-c.x, rr.x, nv.x);
-            nv.x = fma(c.y, rr.y, nv.x);
-            nv.y = fma(-c.x, rr.y, nv.y);
-            nv.y = fma(-c.y, rr.x, nv.y);
-          }
+          typename A::Acc acc = A::acc(Si[j]);
+          for (int s2 = 0; s2 < p; ++s2) A::fnmac(ci[s2], Rs[s2 * ldb + j], acc);
+          nv = A::fin(acc);
         }
         Si[j] = nv;
         if (rn) rn[j] = nv;
-        if (j >= k1 && j < k2) Cn[(int64_t)i * kGJP + (j - k1)] = nv;
+        if (j >= k1 && j < k2) Cn[(int64_t)i * P + (j - k1)] = nv;
       }
     }
     if (!grid_barrier(bar, err, G)) return;
   }
-}
-
-__global__ void k_convert(const double2* __restrict__ s, float2* __restrict__ d, size_t n) {
-  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
-    d[i] = make_float2((float)s[i].x, (float)s[i].y);
 }
 
 // ---------------------------------------------------------------------------
@@ -459,16 +495,19 @@ __global__ void k_convert(const double2* __restrict__ s, float2* __restrict__ d,
 //   Up[J] = Dinv[J] A_J,J+1   (B x B, columns = DoFs of block J+1)
 // A is complex symmetric, so A_J,J-1[i][l] = A[l][i] is read from the stencil
 // row of DoF l (block J-1): Lm[J][a][l] = sum over l's neighbours i in block J
-// of A[l][i] Dinv[J][a][i]. Padding rows and columns are zero.
+// of A[l][i] Dinv[J][a][i]. Padding rows and columns are zero. Computed in the
+// factor's arithmetic and rounded to the solve's precision.
 // ---------------------------------------------------------------------------
-template <typename TO>
-__global__ void __launch_bounds__(256) k_couple(const double2* __restrict__ D, TO* __restrict__ Lm,
+template <typename A, typename TO>
+__global__ void __launch_bounds__(256) k_couple(const typename A::V* __restrict__ D, TO* __restrict__ Lm,
                                                 TO* __restrict__ Up, StencilView<double> Ac, CoarseLayout L) {
-  extern __shared__ __align__(16) double2 coef[];
+  using V = typename A::V;
+  extern __shared__ __align__(16) unsigned char csm[];
+  V* coef = reinterpret_cast<V*>(csm);
   const GridDesc g = Ac.g;
   int ncls = 1;
   for (int ax = 0; ax < g.dim; ++ax) ncls *= g.C1;
-  for (int i = threadIdx.x; i < ncls * g.noff; i += blockDim.x) coef[i] = Ac.coef[i];
+  for (int i = threadIdx.x; i < ncls * g.noff; i += blockDim.x) coef[i] = A::from(Ac.coef[i]);
   __syncthreads();
   const int B = L.B, ldb = L.ldb;
   const int64_t blk = (int64_t)B * ldb, total = 2 * (int64_t)L.nb * blk;
@@ -479,20 +518,24 @@ __global__ void __launch_bounds__(256) k_couple(const double2* __restrict__ D, T
     const int J = (int)(rem / blk);
     const int a = (int)((rem - (int64_t)J * blk) / ldb), l = (int)(rem - (int64_t)J * blk - (int64_t)a * ldb);
     const int Jl = which == 0 ? J - 1 : J + 1;   // block of column l
-    double2 acc = make_double2(0.0, 0.0);
+    V acc = A::zero();
     int c[3];
     if (l < B && Jl >= 0 && Jl < L.nb && block_coords(g, L, Jl, l, c)) {
-      const double2* cl = coef + class_at(g, c) * g.noff;
-      const double2* Drow = D + (int64_t)J * blk + (int64_t)a * ldb;
+      const V* cl = coef + class_at(g, c) * g.noff;
+      const V* Drow = D + (int64_t)J * blk + (int64_t)a * ldb;
       for (int o = 0; o < g.noff; ++o) {
         int Jn, in;
         if (!neighbour(g, L, Ac.dx, o, c, &Jn, &in) || Jn != J) continue;
-        acc = cfma(cl[o], Drow[in], acc);
+        acc = A::fma(cl[o], Drow[in], acc);
       }
     }
-    TO* out = (which == 0 ? Lm : Up) + rem;
-    *out = to<TO>(acc);
+    (which == 0 ? Lm : Up)[rem] = A::out(acc);
   }
+}
+
+__global__ void k_convert_df(const float4* __restrict__ s, float2* __restrict__ d, size_t n) {
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
+    d[i] = dfc_round(s[i]);
 }
 
 // ---- dense row x vector products (row and vector padded to an even length) ----
@@ -943,7 +986,7 @@ void launch_coarse_solve(const CoarsePlan& plan, const c2<T>* Dinv, const c2<T>*
   // p = blockdiag(Dinv) r for all blocks at once, into uc
   k_block_gemv<T><<<nsm * 8, 256, 0, s>>>(Dinv, rc, uc, L, active);
   if (plan.grid) {
-    cudaMemsetAsync(bar, 0, 2 * sizeof(unsigned), s);
+    cudaMemsetAsync(bar, 0, kBarWords * sizeof(unsigned), s);
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3(plan.nblk);
     cfg.blockDim = dim3(plan.threads);
@@ -983,43 +1026,46 @@ void launch_coarse_solve(const CoarsePlan& plan, const c2<T>* Dinv, const c2<T>*
                      active);
 }
 
-template <typename TO>
-void launch_coarse_couple(const double2* D64, TO* Lm, TO* Up, const StencilView<double>& Ac, const CoarseLayout& L,
-                          int nsm, cudaStream_t s) {
+namespace {
+template <typename A, typename TO>
+void launch_couple(const typename A::V* D, TO* Lm, TO* Up, const StencilView<double>& Ac, const CoarseLayout& L,
+                   int nsm, cudaStream_t s) {
   int ncls = 1;
   for (int ax = 0; ax < Ac.g.dim; ++ax) ncls *= Ac.g.C1;
-  const size_t smem = sizeof(double2) * (size_t)ncls * Ac.g.noff;
-  k_couple<TO><<<nsm * 8, 256, smem, s>>>(D64, Lm, Up, Ac, L);
+  const size_t smem = sizeof(typename A::V) * (size_t)ncls * Ac.g.noff;
+  k_couple<A, TO><<<nsm * 8, 256, smem, s>>>(D, Lm, Up, Ac, L);
 }
 
-template <typename T>
-int launch_coarse_factor(c2<T>* Dinv, c2<T>* tmp, c2<T>* piv, unsigned* bar, int* err,
-                         const StencilView<T>& Ac, const CoarseLayout& L, int nsm, cudaStream_t s) {
+template <typename A>
+int launch_factor(typename A::V* Dinv, typename A::V* tmp, typename A::V* piv, unsigned* bar, int* err,
+                  const StencilView<double>& Ac, const CoarseLayout& L, int nsm, cudaStream_t s) {
+  using V = typename A::V;
+  constexpr int P = A::P;
   int ncls = 1;
   for (int ax = 0; ax < Ac.g.dim; ++ax) ncls *= Ac.g.C1;
-  // one CTA per SM: the update is FP64-bound and every SM must take an equal share;
-  // while both chains run, each half of the grid owns one of them
+  // one CTA per SM: every SM takes an equal share of each panel update; while both
+  // chains run, each half of the grid owns one of them
   const int nblk = std::max(2, std::min(nsm, L.B * L.B));
   const int64_t epb = ((int64_t)L.B * L.B + nblk / 2 - 1) / (nblk / 2);
   const int rows = (int)(epb / L.B) + 3;
-  // +256: the grid barrier's static shared flags precede the 128-byte aligned dynamic window
-  size_t smem = sizeof(c2<T>) * ((size_t)ncls * Ac.g.noff + kGJP * kGJP + (size_t)rows * kGJP) + 256;
-  const size_t rstage = sizeof(c2<T>) * (size_t)kGJP * L.ldb;
+  // +256: the kernel's static shared words precede the 128-byte aligned dynamic window
+  size_t smem = sizeof(V) * ((size_t)ncls * Ac.g.noff + P * P + (size_t)rows * P) + 256;
+  const size_t rstage = sizeof(V) * (size_t)P * L.ldb;
   int stageR = smem + rstage <= 200 * 1024 ? 1 : 0;   // pivot rows in shared memory when they fit
   if (stageR) smem += rstage;
   int per_sm = 0;
-  cudaFuncSetAttribute(k_factor_block<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_factor_block<T>, 256, smem);
+  cudaFuncSetAttribute(k_factor_block<A>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_factor_block<A>, kFactorThreads, smem);
   if (per_sm < 1) return HELM_ENOTSUP;
   // top chain J = 0..mid-1 and bottom chain J = nb-1..mid+1 run concurrently, then
   // the middle block mid takes both neighbours (non-twisted: mid = nb-1, no bottom chain)
   const int m = L.mid, nf_top = m, nf_bot = L.nb - 1 - m;
   auto launch = [&](FactorJob j0, FactorJob j1, int njobs) -> int {
-    cudaMemsetAsync(bar, 0, 4 * sizeof(unsigned), s);
-    StencilView<T> acv = Ac;
+    cudaMemsetAsync(bar, 0, 2 * kBarWords * sizeof(unsigned), s);
+    StencilView<double> acv = Ac;
     CoarseLayout lv = L;
     void* args[] = {&Dinv, &tmp, &piv, &bar, &err, &acv, &lv, &j0, &j1, &njobs, &stageR};
-    cudaError_t e = cudaLaunchCooperativeKernel((void*)k_factor_block<T>, dim3(nblk), dim3(256), args, smem, s);
+    cudaError_t e = cudaLaunchCooperativeKernel((void*)k_factor_block<A>, dim3(nblk), dim3(kFactorThreads), args, smem, s);
     return e == cudaSuccess ? HELM_OK : HELM_ECUDA;
   };
   for (int t = 0; t < std::max(nf_top, nf_bot); ++t) {
@@ -1036,9 +1082,26 @@ int launch_coarse_factor(c2<T>* Dinv, c2<T>* tmp, c2<T>* piv, unsigned* bar, int
   if (m < L.nb - 1) mid.dir[mid.ndir++] = +1;
   return launch(mid, mid, 1);
 }
+}  // namespace
 
-void launch_convert_factor(const double2* src, float2* dst, size_t n, cudaStream_t s) {
-  k_convert<<<152 * 8, 256, 0, s>>>(src, dst, n);
+int coarse_factor_fp64(double2* Dinv, double2* tmp, double2* piv, unsigned* bar, int* err,
+                       const StencilView<double>& Ac, const CoarseLayout& L, int nsm, cudaStream_t s) {
+  return launch_factor<ArithD>(Dinv, tmp, piv, bar, err, Ac, L, nsm, s);
+}
+int coarse_factor_df(float4* Dinv, float4* tmp, float4* piv, unsigned* bar, int* err,
+                     const StencilView<double>& Ac, const CoarseLayout& L, int nsm, cudaStream_t s) {
+  return launch_factor<ArithDF>(Dinv, tmp, piv, bar, err, Ac, L, nsm, s);
+}
+void coarse_couple_fp64(const double2* D, double2* Lm, double2* Up, const StencilView<double>& Ac,
+                        const CoarseLayout& L, int nsm, cudaStream_t s) {
+  launch_couple<ArithD, double2>(D, Lm, Up, Ac, L, nsm, s);
+}
+void coarse_couple_df(const float4* D, float2* Lm, float2* Up, const StencilView<double>& Ac, const CoarseLayout& L,
+                      int nsm, cudaStream_t s) {
+  launch_couple<ArithDF, float2>(D, Lm, Up, Ac, L, nsm, s);
+}
+void convert_factor_df(const float4* src, float2* dst, size_t n, cudaStream_t s) {
+  k_convert_df<<<152 * 8, 256, 0, s>>>(src, dst, n);
 }
 
 template int plan_coarse_solve<float>(const CoarseLayout&, CoarsePlan*);
@@ -1049,13 +1112,4 @@ template void launch_coarse_solve<float>(const CoarsePlan&, const float2*, const
 template void launch_coarse_solve<double>(const CoarsePlan&, const double2*, const double2*, const double2*,
                                           const CoarseLayout&, const double2*, double2*, double2*, int*, unsigned*,
                                           int*, const int*, int, cudaStream_t);
-template void launch_coarse_couple<float2>(const double2*, float2*, float2*, const StencilView<double>&,
-                                           const CoarseLayout&, int, cudaStream_t);
-template void launch_coarse_couple<double2>(const double2*, double2*, double2*, const StencilView<double>&,
-                                            const CoarseLayout&, int, cudaStream_t);
-template int launch_coarse_factor<double>(double2*, double2*, double2*, unsigned*, int*,
-                                          const StencilView<double>&, const CoarseLayout&, int, cudaStream_t);
-template int launch_coarse_factor<float>(float2*, float2*, float2*, unsigned*, int*,
-                                         const StencilView<float>&, const CoarseLayout&, int, cudaStream_t);
-
 }  // namespace helm

@@ -125,15 +125,18 @@ struct CoarseLayout {
 #if defined(__CUDACC__)
 // ----------------------------------------------------------------------------
 // Bounded software grid barrier for cooperative launches.
-// state[0] = arrival counter, state[1] = generation. Every thread reads the
-// generation before its CTA arrives; thread 0 arrives after the CTA barrier
-// that closes the phase; then EVERY thread polls until the generation moves on
-// (lane-uniform, one load per warp), so no thread depends on a CTA barrier
-// placed after a wait to learn that the grid barrier opened.
+// state[0] = arrival counter, state[kBarGen] = generation, on separate 128-byte
+// lines (a barrier instance owns kBarWords words). Every thread reads the
+// generation before its CTA arrives; thread 0 arrives after the CTA barrier that
+// closes the phase; then EVERY thread polls until the generation moves on
+// (lane-uniform, one load per warp, with a short back-off), so no thread depends
+// on a CTA barrier placed after a wait to learn that the grid barrier opened.
 // On timeout the kernel's error word gets HELM_ETIMEOUT and it returns false.
 // ----------------------------------------------------------------------------
+constexpr int kBarGen = 32;     // words: the generation sits 128 bytes after the counter
+constexpr int kBarWords = 64;   // words per barrier instance
 __device__ inline bool grid_barrier(unsigned* state, int* err, unsigned nblocks) {
-  const unsigned gen = *(volatile unsigned*)(state + 1);
+  const unsigned gen = *(volatile unsigned*)(state + kBarGen);
   __syncthreads();
   if (threadIdx.x == 0) {
     __threadfence();
@@ -141,11 +144,11 @@ __device__ inline bool grid_barrier(unsigned* state, int* err, unsigned nblocks)
     if (arrived == nblocks - 1) {
       atomicExch(state, 0u);
       __threadfence();
-      atomicAdd(state + 1, 1u);
+      atomicAdd(state + kBarGen, 1u);
     }
   }
   bool ok = true;
-  for (long long spins = 0; *(volatile unsigned*)(state + 1) == gen;) {
+  for (long long spins = 0; *(volatile unsigned*)(state + kBarGen) == gen;) {
     if (++spins > (1ll << 22)) {
       atomicCAS(err, 0, HELM_ETIMEOUT);
       ok = false;
@@ -155,6 +158,7 @@ __device__ inline bool grid_barrier(unsigned* state, int* err, unsigned nblocks)
       ok = false;
       break;
     }
+    __nanosleep(32);
   }
   __threadfence();
   return ok;

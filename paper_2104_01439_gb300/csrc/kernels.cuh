@@ -70,24 +70,28 @@ template <typename T>
 int plan_coarse_solve(const CoarseLayout& L, CoarsePlan* plan);
 // uc = A^{-1} rc for the block-padded coarse vectors (uc also holds the block-diagonal
 // pre-pass p = Dinv r). L.mid < L.nb - 1 runs the twisted form on two clusters
-// (xmid: 2 x ldb values, xflag: 2 x ldb ints of exchange space); bar: 2 unsigned for the
-// grid kernel's barrier.
+// (xmid: 2 x ldb values, xflag: 2 x ldb ints of exchange space); bar: kBarWords unsigned for
+// the grid kernel's barrier.
 template <typename T>
 void launch_coarse_solve(const CoarsePlan& plan, const c2<T>* Dinv, const c2<T>* Lm, const c2<T>* Up,
                          const CoarseLayout& L, const c2<T>* rc, c2<T>* uc, c2<T>* xmid, int* xflag,
                          unsigned* bar, int* err, const int* active, int nsm, cudaStream_t s);
-// Lm[J] = Dinv[J] A_J,J-1 and Up[J] = Dinv[J] A_J,J+1 from the FP64 inverses (nb x B x ldb each)
-template <typename TO>
-void launch_coarse_couple(const double2* D64, TO* Lm, TO* Up, const StencilView<double>& Ac, const CoarseLayout& L,
-                          int nsm, cudaStream_t s);
-// Block-Thomas factorisation: Dinv[J] = (A_JJ - A_J,J-1 Dinv[J-1] A_J-1,J)^{-1}.
-// tmp: 2 x B x ldb; piv: 2 x factor_workspace(L) elements; bar: 4 unsigned
-// (two halves of the grid factor the top and bottom chains concurrently).
-__host__ __device__ inline size_t factor_workspace(const CoarseLayout& L) { return 2 * 8 * (size_t)L.ldb + 2 * 8 * (size_t)L.B; }
-template <typename T>
-int launch_coarse_factor(c2<T>* Dinv, c2<T>* tmp, c2<T>* piv, unsigned* bar, int* err,
-                         const StencilView<T>& Ac, const CoarseLayout& L, int nsm, cudaStream_t s);
-void launch_convert_factor(const double2* src, float2* dst, size_t n, cudaStream_t s);
+// Block-Thomas factorisation: Dinv[J] = (A_JJ - A_J,J-1 Dinv[J-1] A_J-1,J)^{-1} (two chains
+// meeting at L.mid), in complex128 (8-pivot Gauss-Jordan panels) or in complex double-float
+// (float4 hi/lo pairs, 16-pivot panels). tmp: 2 x B x ldb; piv: 2 x factor_workspace(L)
+// elements; bar: 2 x kBarWords unsigned (two halves of the grid factor the two chains concurrently).
+__host__ __device__ inline size_t factor_workspace(const CoarseLayout& L) { return 2 * 16 * (size_t)L.ldb + 2 * 16 * (size_t)L.B; }
+int coarse_factor_fp64(double2* Dinv, double2* tmp, double2* piv, unsigned* bar, int* err,
+                       const StencilView<double>& Ac, const CoarseLayout& L, int nsm, cudaStream_t s);
+int coarse_factor_df(float4* Dinv, float4* tmp, float4* piv, unsigned* bar, int* err,
+                     const StencilView<double>& Ac, const CoarseLayout& L, int nsm, cudaStream_t s);
+// Lm[J] = Dinv[J] A_J,J-1 and Up[J] = Dinv[J] A_J,J+1 from the inverses (nb x B x ldb each)
+void coarse_couple_fp64(const double2* D, double2* Lm, double2* Up, const StencilView<double>& Ac,
+                        const CoarseLayout& L, int nsm, cudaStream_t s);
+void coarse_couple_df(const float4* D, float2* Lm, float2* Up, const StencilView<double>& Ac, const CoarseLayout& L,
+                      int nsm, cudaStream_t s);
+// complex64 nearest to each double-float entry
+void convert_factor_df(const float4* src, float2* dst, size_t n, cudaStream_t s);
 
 // ---- Krylov (krylov.cu) ----------------------------------------------------
 struct KState {
@@ -130,6 +134,9 @@ struct KrylovBufs {
   double2* part;   // nblk x (m+2) partial sums (inner products: double-float as float4)
   int nblk;        // blocks of the element-wise Krylov kernels (256 threads, one entry per thread)
   int nblk_dots;   // blocks of the inner-product kernel (256 threads, <= 4 entries per thread)
+  int m;           // restart length (host copy of KState::m, sizes launches)
+  int nblk_upd;    // blocks of the update kernel (16 entries per warp)
+  int pstride;     // row stride of the partials buffer: max over the kernels that write it
   KState* st;
 };
 

@@ -16,6 +16,7 @@
 // |g_{j+1}| and the convergence test run on the device in one thread, so a
 // captured iteration never returns to the host. All kernels read the Arnoldi
 // index j and the 'active' flag from device state.
+#include "dfloat.cuh"
 #include "kernels.cuh"
 
 namespace helm {
@@ -38,34 +39,7 @@ __device__ __forceinline__ double wsum(double v) {
   return v;
 }
 
-// ---- double-float (hi + lo float) arithmetic --------------------------------
-struct DF {
-  float h, l;
-};
-__device__ __forceinline__ DF df_split(double d) {
-  float h = (float)d;
-  return DF{h, (float)(d - (double)h)};
-}
-// s += a * b  (TwoProduct by FMA, TwoSum on the high parts)
-__device__ __forceinline__ void df_mac(float ah, float al, float bh, float bl, DF& s) {
-  float p = ah * bh;
-  float e = fmaf(ah, bh, -p);
-  e = fmaf(ah, bl, e);
-  e = fmaf(al, bh, e);
-  float t = s.h + p;
-  float bp = t - s.h;
-  float err = (s.h - (t - bp)) + (p - bp);
-  s.h = t;
-  s.l += err + e;
-}
-__device__ __forceinline__ DF df_add(DF a, DF b) {
-  float s = a.h + b.h;
-  float bp = s - a.h;
-  float e = (a.h - (s - bp)) + (b.h - bp);
-  e += a.l + b.l;
-  float h = s + e;
-  return DF{h, e - (h - s)};
-}
+// ---- double-float helpers (dfloat.cuh): warp reduction --------------------------
 __device__ __forceinline__ DF df_wsum(DF v) {
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) {
@@ -74,7 +48,6 @@ __device__ __forceinline__ DF df_wsum(DF v) {
   }
   return v;
 }
-__device__ __forceinline__ double df_val(DF v) { return (double)v.h + (double)v.l; }
 
 constexpr int kE = 4;    // basis entries per thread in the inner-product kernel
 constexpr int kGD = 4;   // basis vectors per sweep of the inner-product kernel
@@ -90,18 +63,24 @@ __global__ void __launch_bounds__(kT) k_split_w(KrylovBufs kb) {
   }
 }
 
-// partial dots of w against the double-float basis V[0..j] (and ||w||^2 in the first pass)
-__global__ void __launch_bounds__(kT, 2) k_dots(KrylovBufs kb, int second) {
+// partial dots of w against the double-float basis V[0..j] (and ||w||^2 in the first pass).
+// Grid: x over chunks of w (kE entries per thread), y over groups of kGD basis vectors, so
+// that every (chunk, group) pair is its own block and many loads are in flight.
+__global__ void __launch_bounds__(kT) k_dots(KrylovBufs kb, int second) {
   KState* st = kb.st;
   if (!st->active || (second && !st->reorth)) return;
   const int j = st->j, m = st->m;
+  const int i0 = blockIdx.y * kGD;
+  if (i0 > j) return;
+  const int ng = min(kGD, j + 1 - i0);
   const int64_t N = kb.N, ld = kb.ldN;
   __shared__ float4 red[kT / 32][kGD];
   __shared__ double rn[kT / 32];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  double2* part = kb.part + (int64_t)blockIdx.x * (m + 2);
+  // partials are entry-major, part[i * pstride + block], so the reductions read them contiguously
+  const int64_t PS = kb.pstride;
   const int64_t stride = (int64_t)gridDim.x * blockDim.x, base = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  if (!second) {
+  if (!second && blockIdx.y == 0) {
     double s2 = 0.0;
 #pragma unroll
     for (int k = 0; k < kE; ++k) {
@@ -117,56 +96,53 @@ __global__ void __launch_bounds__(kT, 2) k_dots(KrylovBufs kb, int second) {
     if (threadIdx.x == 0) {
       double t = 0.0;
       for (int i = 0; i < kT / 32; ++i) t += rn[i];
-      part[m + 1] = make_double2(t, 0.0);
+      kb.part[(int64_t)(m + 1) * PS + blockIdx.x] = make_double2(t, 0.0);
     }
   }
-  float4* part4 = reinterpret_cast<float4*>(part);
-  for (int i0 = 0; i0 <= j; i0 += kGD) {
-    const int ng = min(kGD, j + 1 - i0);
-    DF ar[kGD], ai[kGD];
+  float4* part4 = reinterpret_cast<float4*>(kb.part);
+  DF ar[kGD], ai[kGD];
 #pragma unroll
-    for (int t = 0; t < kGD; ++t) ar[t] = ai[t] = DF{0.f, 0.f};
+  for (int t = 0; t < kGD; ++t) ar[t] = ai[t] = DF{0.f, 0.f};
 #pragma unroll
-    for (int k = 0; k < kE; ++k) {
-      const int64_t n = base + k * stride;
-      if (n >= N) break;
-      const float4 w = kb.Ws[n];   // (hr, hi, lr, li)
-#pragma unroll
-      for (int t = 0; t < kGD; ++t) {
-        if (t < ng) {
-          const float4 v = kb.Vs[(int64_t)(i0 + t) * ld + n];
-          // conj(v) w = (vr wr + vi wi) + i (vr wi - vi wr)
-          df_mac(v.x, v.z, w.x, w.z, ar[t]);
-          df_mac(v.y, v.w, w.y, w.w, ar[t]);
-          df_mac(v.x, v.z, w.y, w.w, ai[t]);
-          df_mac(-v.y, -v.w, w.x, w.z, ai[t]);
-        }
-      }
-    }
+  for (int k = 0; k < kE; ++k) {
+    const int64_t n = base + k * stride;
+    if (n >= N) break;
+    const float4 w = kb.Ws[n];   // (hr, hi, lr, li)
 #pragma unroll
     for (int t = 0; t < kGD; ++t) {
-      DF r = df_wsum(ar[t]), q = df_wsum(ai[t]);
-      if (lane == 0) red[warp][t] = make_float4(r.h, r.l, q.h, q.l);
-    }
-    __syncthreads();
-    if (threadIdx.x < ng) {   // block partial, still double-float (converted by k_reduce_h)
-      DF r{0.f, 0.f}, q{0.f, 0.f};
-      for (int wi2 = 0; wi2 < kT / 32; ++wi2) {
-        const float4 x = red[wi2][threadIdx.x];
-        r = df_add(r, DF{x.x, x.y});
-        q = df_add(q, DF{x.z, x.w});
+      if (t < ng) {
+        const float4 v = kb.Vs[(int64_t)(i0 + t) * ld + n];
+        // conj(v) w = (vr wr + vi wi) + i (vr wi - vi wr)
+        df_mac(v.x, v.z, w.x, w.z, ar[t]);
+        df_mac(v.y, v.w, w.y, w.w, ar[t]);
+        df_mac(v.x, v.z, w.y, w.w, ai[t]);
+        df_mac(-v.y, -v.w, w.x, w.z, ai[t]);
       }
-      part4[i0 + threadIdx.x] = make_float4(r.h, r.l, q.h, q.l);
     }
-    __syncthreads();
+  }
+#pragma unroll
+  for (int t = 0; t < kGD; ++t) {
+    DF r = df_wsum(ar[t]), q = df_wsum(ai[t]);
+    if (lane == 0) red[warp][t] = make_float4(r.h, r.l, q.h, q.l);
+  }
+  __syncthreads();
+  if (threadIdx.x < ng) {   // block partial, still double-float (converted by k_reduce_h)
+    DF r{0.f, 0.f}, q{0.f, 0.f};
+    for (int wi2 = 0; wi2 < kT / 32; ++wi2) {
+      const float4 x = red[wi2][threadIdx.x];
+      r = df_add(r, DF{x.x, x.y});
+      q = df_add(q, DF{x.z, x.w});
+    }
+    part4[(int64_t)(i0 + threadIdx.x) * PS + blockIdx.x] = make_float4(r.h, r.l, q.h, q.l);
   }
 }
 
-// Deterministic block reduction of the per-block partials: warp w sums entry
-// i (lanes stride over the blocks, then a fixed shuffle tree).
-__device__ __forceinline__ double2 sum_partials(const KrylovBufs& kb, int m, int i, int lane, int nrows) {
+// Deterministic reduction of the per-block partials of entry i by one warp (lanes
+// stride over the blocks, then a fixed shuffle tree).
+__device__ __forceinline__ double2 sum_partials(const KrylovBufs& kb, int i, int lane, int nrows) {
   double2 s = make_double2(0.0, 0.0);
-  for (int b = lane; b < nrows; b += 32) s = cadd(s, kb.part[(int64_t)b * (m + 2) + i]);
+  const double2* row = kb.part + (int64_t)i * kb.pstride;
+  for (int b = lane; b < nrows; b += 32) s = cadd(s, row[b]);
   return wsum(s);
 }
 
@@ -178,10 +154,11 @@ __global__ void __launch_bounds__(kT) k_reduce_h(KrylovBufs kb, double2* hp, int
   const int j = st->j, m = st->m;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
   const float4* p4 = reinterpret_cast<const float4*>(kb.part);
-  for (int i = warp; i <= j; i += nw) {
+  for (int i = blockIdx.x * nw + warp; i <= j; i += gridDim.x * nw) {
     DF r{0.f, 0.f}, q{0.f, 0.f};
+    const float4* row = p4 + (int64_t)i * kb.pstride;
     for (int b = lane; b < kb.nblk_dots; b += 32) {
-      const float4 x = p4[(int64_t)b * (m + 2) + i];
+      const float4 x = row[b];
       r = df_add(r, DF{x.x, x.y});
       q = df_add(q, DF{x.z, x.w});
     }
@@ -193,14 +170,15 @@ __global__ void __launch_bounds__(kT) k_reduce_h(KrylovBufs kb, double2* hp, int
       kb.hcol[i] = second ? cadd(kb.hcol[i], s2) : s2;
     }
   }
-  if (!second && warp == 0) {
-    double2 s2 = sum_partials(kb, m, m + 1, lane, kb.nblk_dots);   // ||w||^2 (FP64)
+  if (!second && blockIdx.x == 0 && warp == 0) {
+    double2 s2 = sum_partials(kb, m + 1, lane, kb.nblk_dots);   // ||w||^2 (FP64)
     if (lane == 0) st->wn0 = sqrt(s2.x);
   }
 }
 
 // w -= sum_i hp[i] V[i] (sum in double-float, subtraction in FP64);  partial ||w||^2.
-// One entry per thread; the basis loop is unrolled so that several loads are in flight.
+// A warp takes 16 entries; its two half-warps sum over the two halves of the basis
+// (twice the loads in flight) and meet with one shuffle; the low half-warp finishes.
 __global__ void __launch_bounds__(kT) k_update(KrylovBufs kb, const double2* hp, int second) {
   KState* st = kb.st;
   if (!st->active || (second && !st->reorth)) return;
@@ -212,28 +190,38 @@ __global__ void __launch_bounds__(kT) k_update(KrylovBufs kb, const double2* hp,
     hs4[i] = make_float4(r.h, r.l, q.h, q.l);
   }
   __syncthreads();
+  const int lane = threadIdx.x & 31, half = lane >> 4;
+  const int split = (j + 2) / 2;   // vectors [0, split) and [split, j]
+  const int ib = half ? split : 0, ie = half ? j + 1 : split;
   double s2 = 0.0;
-  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-  for (int64_t n = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; n < N; n += stride) {
+  const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;   // warps in the grid
+  for (int64_t wg = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5; wg * 16 < N; wg += nw) {
+    const int64_t n = wg * 16 + (lane & 15);
     DF cr{0.f, 0.f}, ci{0.f, 0.f};
-    const float4* vs = kb.Vs + n;
+    if (n < N) {
+      const float4* vs = kb.Vs + n;
 #pragma unroll 8
-    for (int i = 0; i <= j; ++i) {
-      const float4 v = vs[(int64_t)i * ld];   // (hr, hi, lr, li)
-      const float4 h = hs4[i];                // (re.h, re.l, im.h, im.l)
-      // h v = (hr vr - hi vi) + i (hr vi + hi vr)
-      df_mac(h.x, h.y, v.x, v.z, cr);
-      df_mac(-h.z, -h.w, v.y, v.w, cr);
-      df_mac(h.x, h.y, v.y, v.w, ci);
-      df_mac(h.z, h.w, v.x, v.z, ci);
+      for (int i = ib; i < ie; ++i) {
+        const float4 v = vs[(int64_t)i * ld];   // (hr, hi, lr, li)
+        const float4 h = hs4[i];                // (re.h, re.l, im.h, im.l)
+        // h v = (hr vr - hi vi) + i (hr vi + hi vr)
+        df_mac(h.x, h.y, v.x, v.z, cr);
+        df_mac(-h.z, -h.w, v.y, v.w, cr);
+        df_mac(h.x, h.y, v.y, v.w, ci);
+        df_mac(h.z, h.w, v.x, v.z, ci);
+      }
     }
-    double2 w = kb.W[n];
-    w.x -= df_val(cr);
-    w.y -= df_val(ci);
-    kb.W[n] = w;
-    DF r = df_split(w.x), q = df_split(w.y);
-    kb.Ws[n] = make_float4(r.h, q.h, r.l, q.l);
-    s2 = fma(w.x, w.x, fma(w.y, w.y, s2));
+    cr = df_add(cr, DF{__shfl_xor_sync(0xffffffffu, cr.h, 16), __shfl_xor_sync(0xffffffffu, cr.l, 16)});
+    ci = df_add(ci, DF{__shfl_xor_sync(0xffffffffu, ci.h, 16), __shfl_xor_sync(0xffffffffu, ci.l, 16)});
+    if (half == 0 && n < N) {
+      double2 w = kb.W[n];
+      w.x -= df_val(cr);
+      w.y -= df_val(ci);
+      kb.W[n] = w;
+      DF r = df_split(w.x), q = df_split(w.y);
+      kb.Ws[n] = make_float4(r.h, q.h, r.l, q.l);
+      s2 = fma(w.x, w.x, fma(w.y, w.y, s2));
+    }
   }
   __shared__ double rn[kT / 32];
   s2 = wsum(s2);
@@ -242,7 +230,7 @@ __global__ void __launch_bounds__(kT) k_update(KrylovBufs kb, const double2* hp,
   if (threadIdx.x == 0) {
     double t = 0.0;
     for (int i = 0; i < kT / 32; ++i) t += rn[i];
-    kb.part[(int64_t)blockIdx.x * (m + 2) + m + 1] = make_double2(t, 0.0);
+    kb.part[(int64_t)(m + 1) * kb.pstride + blockIdx.x] = make_double2(t, 0.0);
   }
 }
 
@@ -250,7 +238,7 @@ __global__ void k_reduce_norm(KrylovBufs kb, int second) {
   KState* st = kb.st;
   if (!st->active || (second && !st->reorth)) return;
   const int m = st->m;
-  double2 s2 = sum_partials(kb, m, m + 1, threadIdx.x & 31, kb.nblk);
+  double2 s2 = sum_partials(kb, m + 1, threadIdx.x & 31, kb.nblk_upd);
   if (threadIdx.x != 0) return;
   double wn = sqrt(s2.x);
   st->wn = wn;
@@ -278,68 +266,93 @@ __global__ void __launch_bounds__(kT) k_normalize(KrylovBufs kb) {
   }
 }
 
-__global__ void __launch_bounds__(kT) k_givens(KrylovBufs kb) {
+__device__ __forceinline__ double2 shfl_up2(double2 v, int d) {
+  return make_double2(__shfl_up_sync(0xffffffffu, v.x, d), __shfl_up_sync(0xffffffffu, v.y, d));
+}
+__device__ __forceinline__ double2 shfl2(double2 v, int src) {
+  return make_double2(__shfl_sync(0xffffffffu, v.x, src), __shfl_sync(0xffffffffu, v.y, src));
+}
+
+// Givens step for column j (one warp). The previous rotations turn the new column
+// h = (h_0..h_j, h_{j+1} = ||w||) into  col_i = c_i u_i + s_i h_{i+1}  with the carried
+// value  u_0 = h_0,  u_{i+1} = -conj(s_i) u_i + c_i h_{i+1}  -- an affine recurrence in u.
+// Each lane composes the maps of a contiguous chunk of rotations, a warp scan composes
+// the chunks ((a2, b2) o (a1, b1) = (a2 a1, a2 b1 + b2)), and each lane then replays its
+// chunk from its exclusive prefix. The new rotation [c s; -conj(s) c] zeroes h_{j+1}
+// against u_j; the residual estimate is |g_{j+1}| / ||F||.
+__global__ void __launch_bounds__(32) k_givens(KrylovBufs kb) {
   KState* st = kb.st;
   if (!st->active) return;
-  const int j = st->j, m = st->m;
-  __shared__ double2 col[513];
-  __shared__ double2 sn[512];
-  __shared__ double cs[512];
-  for (int i = threadIdx.x; i <= j; i += blockDim.x) {
-    col[i] = kb.hcol[i];
-    if (i < j) {
-      cs[i] = kb.cs[i];
-      sn[i] = kb.sn[i];
-    }
-  }
-  __syncthreads();
+  const int j = st->j, m = st->m, lane = threadIdx.x;
   const double wn = st->wn;
-  if (threadIdx.x == 0) {
-    col[j + 1] = make_double2(wn, 0.0);
-    for (int i = 0; i < j; ++i) {   // previous rotations
-      double c = cs[i];
-      double2 sv = sn[i], a = col[i], b = col[i + 1];
-      double2 sb = cmul(sv, b);
-      double2 nsa = cmul(make_double2(-sv.x, sv.y), a);   // -conj(s) a
-      col[i] = make_double2(c * a.x + sb.x, c * a.y + sb.y);
-      col[i + 1] = make_double2(nsa.x + c * b.x, nsa.y + c * b.y);
-    }
-    // new rotation zeroing col[j+1]: [c s; -conj(s) c] [a; b] = [r; 0]
-    double2 a = col[j], b = col[j + 1];
-    double aa = hypot(a.x, a.y), bb = hypot(b.x, b.y);
-    double c;
-    double2 sv, r;
-    if (bb == 0.0) {
-      c = 1.0; sv = make_double2(0.0, 0.0); r = a;
-    } else if (aa == 0.0) {
-      c = 0.0; sv = make_double2(1.0, 0.0); r = b;
-    } else {
-      double nu = hypot(aa, bb);
-      double2 ph = make_double2(a.x / aa, a.y / aa);
-      c = aa / nu;
-      sv = cmul(ph, make_double2(b.x / nu, -b.y / nu));
-      r = make_double2(ph.x * nu, ph.y * nu);
-    }
-    kb.cs[j] = c;
-    kb.sn[j] = sv;
-    col[j] = r;
-    col[j + 1] = make_double2(0.0, 0.0);
-    double2 gj = kb.g[j];
-    double2 gj1 = cmul(make_double2(-sv.x, sv.y), gj);
-    kb.g[j + 1] = gj1;
-    kb.g[j] = make_double2(c * gj.x, c * gj.y);
-    double est = hypot(gj1.x, gj1.y) / st->nF;
-    st->est = est;
-    st->j = j + 1;
-    st->total += 1;
-    if (!isfinite(est) || !isfinite(wn)) st->nonfinite = 1;
-    if (!(wn > 1e-14 * st->beta)) st->breakdown = 1;
-    if (est <= st->tol) st->converged = 1;
-    if (st->converged || st->breakdown || st->nonfinite || st->j >= m || st->total >= st->maxit) st->active = 0;
-  }
-  __syncthreads();
   double2* Hc = kb.H + (int64_t)j * (m + 1);
-  for (int i = threadIdx.x; i <= j + 1; i += blockDim.x) Hc[i] = col[i];
+  const int per = (j + 31) / 32;
+  const int i0 = min(j, lane * per), i1 = min(j, i0 + per);
+  double2 A = make_double2(1.0, 0.0), Bm = make_double2(0.0, 0.0);
+  for (int i = i0; i < i1; ++i) {
+    const double2 al = make_double2(-kb.sn[i].x, kb.sn[i].y);   // -conj(s_i)
+    const double c = kb.cs[i];
+    const double2 hn = kb.hcol[i + 1];
+    Bm = cfma(al, Bm, make_double2(c * hn.x, c * hn.y));
+    A = cmul(al, A);
+  }
+#pragma unroll
+  for (int d = 1; d < 32; d <<= 1) {
+    const double2 Ap = shfl_up2(A, d), Bp = shfl_up2(Bm, d);
+    if (lane >= d) {
+      Bm = cfma(A, Bp, Bm);
+      A = cmul(A, Ap);
+    }
+  }
+  double2 Ae = shfl_up2(A, 1), Be = shfl_up2(Bm, 1);
+  if (lane == 0) {
+    Ae = make_double2(1.0, 0.0);
+    Be = make_double2(0.0, 0.0);
+  }
+  double2 u = cfma(Ae, kb.hcol[0], Be);   // u at the start of this lane's chunk
+  for (int i = i0; i < i1; ++i) {
+    const double2 sv = kb.sn[i];
+    const double c = kb.cs[i];
+    const double2 hn = kb.hcol[i + 1];
+    Hc[i] = cfma(sv, hn, make_double2(c * u.x, c * u.y));
+    u = cfma(make_double2(-sv.x, sv.y), u, make_double2(c * hn.x, c * hn.y));
+  }
+  // u_j sits with the lane that replayed rotation j-1 (lane 0 when j == 0)
+  const int owner = j == 0 ? 0 : (j - 1) / per;
+  u = shfl2(u, owner);
+  if (lane != 0) return;
+  // new rotation zeroing (u_j, wn): [c s; -conj(s) c] [a; b] = [r; 0]
+  const double2 a = u, b = make_double2(wn, 0.0);
+  const double aa = hypot(a.x, a.y), bb = hypot(b.x, b.y);
+  double c;
+  double2 sv, r;
+  if (bb == 0.0) {
+    c = 1.0; sv = make_double2(0.0, 0.0); r = a;
+  } else if (aa == 0.0) {
+    c = 0.0; sv = make_double2(1.0, 0.0); r = b;
+  } else {
+    const double nu = hypot(aa, bb);
+    const double2 ph = make_double2(a.x / aa, a.y / aa);
+    c = aa / nu;
+    sv = cmul(ph, make_double2(b.x / nu, -b.y / nu));
+    r = make_double2(ph.x * nu, ph.y * nu);
+  }
+  kb.cs[j] = c;
+  kb.sn[j] = sv;
+  Hc[j] = r;
+  Hc[j + 1] = make_double2(0.0, 0.0);
+  const double2 gj = kb.g[j];
+  const double2 gj1 = cmul(make_double2(-sv.x, sv.y), gj);
+  kb.g[j + 1] = gj1;
+  kb.g[j] = make_double2(c * gj.x, c * gj.y);
+  const double est = hypot(gj1.x, gj1.y) / st->nF;
+  st->est = est;
+  st->j = j + 1;
+  st->total += 1;
+  if (!isfinite(est) || !isfinite(wn)) st->nonfinite = 1;
+  if (!(wn > 1e-14 * st->beta)) st->breakdown = 1;
+  if (est <= st->tol) st->converged = 1;
+  if (st->converged || st->breakdown || st->nonfinite || st->j >= m || st->total >= st->maxit) st->active = 0;
 }
 
 // ||v||^2 partials / final
@@ -357,13 +370,13 @@ __global__ void __launch_bounds__(kT) k_norm_part(KrylovBufs kb, const double2* 
   if (threadIdx.x == 0) {
     double t = 0.0;
     for (int i = 0; i < kT / 32; ++i) t += rn[i];
-    kb.part[(int64_t)blockIdx.x * (kb.st->m + 2) + kb.st->m + 1] = make_double2(t, 0.0);
+    kb.part[(int64_t)(kb.st->m + 1) * kb.pstride + blockIdx.x] = make_double2(t, 0.0);
   }
 }
 __global__ void k_norm_fin(KrylovBufs kb, int which) {
   KState* st = kb.st;
   const int m = st->m;
-  double2 s2 = sum_partials(kb, m, m + 1, threadIdx.x & 31, kb.nblk);
+  double2 s2 = sum_partials(kb, m + 1, threadIdx.x & 31, kb.nblk);
   if (threadIdx.x != 0) return;
   double nrm = sqrt(s2.x);
   if (which == 0) {
@@ -443,15 +456,15 @@ __global__ void __launch_bounds__(kT) k_update_x(KrylovBufs kb, double2* x) {
 void launch_cgs_pass(const KrylovBufs& kb, bool second, cudaStream_t s) {
   int sec = second ? 1 : 0;
   if (!second) k_split_w<<<kb.nblk, kT, 0, s>>>(kb);
-  k_dots<<<kb.nblk_dots, kT, 0, s>>>(kb, sec);
-  k_reduce_h<<<1, kT, 0, s>>>(kb, kb.hp, sec);
-  k_update<<<kb.nblk, kT, sizeof(float4) * 513, s>>>(kb, kb.hp, sec);
+  k_dots<<<dim3(kb.nblk_dots, (kb.m + 1 + kGD - 1) / kGD), kT, 0, s>>>(kb, sec);
+  k_reduce_h<<<(kb.m + 1 + kT / 32 - 1) / (kT / 32), kT, 0, s>>>(kb, kb.hp, sec);
+  k_update<<<kb.nblk_upd, kT, sizeof(float4) * 513, s>>>(kb, kb.hp, sec);
   k_reduce_norm<<<1, 32, 0, s>>>(kb, sec);
 }
 
 void launch_normalize(const KrylovBufs& kb, cudaStream_t s) { k_normalize<<<kb.nblk, kT, 0, s>>>(kb); }
 
-void launch_givens(const KrylovBufs& kb, cudaStream_t s) { k_givens<<<1, kT, 0, s>>>(kb); }
+void launch_givens(const KrylovBufs& kb, cudaStream_t s) { k_givens<<<1, 32, 0, s>>>(kb); }
 
 void launch_cycle_start(const KrylovBufs& kb, const double2* r, cudaStream_t s) {
   k_cycle_start<<<kb.nblk, kT, 0, s>>>(kb, r);
