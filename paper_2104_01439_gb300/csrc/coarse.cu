@@ -268,8 +268,11 @@ struct FactorJob {
   int dir[2];
 };
 
-// one CTA per SM; 32 warps hide the latency of the dependent double-float chains
+// one CTA per SM; 32 warps hide the latency of the dependent double-float chains. Warps
+// 0-7 form and invert the next panel's pivot block while warps 8-31 update the matrix.
 constexpr int kFactorThreads = 1024;
+constexpr int kLookThreads = 256;
+__device__ __forceinline__ void named_sync(int id, int n) { asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(n) : "memory"); }
 
 template <typename A>
 __global__ void __launch_bounds__(kFactorThreads, 1) k_factor_block(typename A::V* D, typename A::V* Tmp, typename A::V* piv,
@@ -321,9 +324,11 @@ __global__ void __launch_bounds__(kFactorThreads, 1) k_factor_block(typename A::
     }
   };
   // snapshots of the first Gauss-Jordan panel (pivot rows and columns)
+  V* pblk = piv + 2 * P * (int64_t)ldb + 2 * (int64_t)B * P;   // 2 x [P x P] pivot-block snapshots
   auto snapshot = [&](int i, int l, V v) {
     if (l < B && i < P) piv[(int64_t)i * ldb + l] = v;
     if (l < P && l < B) piv[2 * P * (int64_t)ldb + (int64_t)i * P + l] = v;
+    if (i >= P && i < 2 * P && l >= P && l < 2 * P && l < B) pblk[P * P + (i - P) * P + (l - P)] = v;   // panel 1
   };
   // S = A_JJ (identity on padding rows, zero padding columns)
   for (int64_t idx = gt; idx < (int64_t)B * ldb; idx += gs) {
@@ -395,96 +400,140 @@ __global__ void __launch_bounds__(kFactorThreads, 1) k_factor_block(typename A::
   const int64_t epb = (BB + G - 1) / G;
   const int64_t e0 = (int64_t)lb * epb, e1 = min(BB, e0 + epb);
   const int i0 = (int)(e0 / B), i1 = e1 > e0 ? (int)((e1 - 1) / B) : i0 - 1;   // rows touched
-  V* Pm = coef + ncls * g.noff;                 // P x P panel block -> its inverse
-  V* cP = Pm + P * P;                           // (rows touched) x P : C_i Pb^{-1}
+  V* Pm = coef + ncls * g.noff;                 // P x P: inverse of this panel's pivot block
+  V* Pn = Pm + P * P;                           // P x P: the next panel's block, inverted ahead
+  V* cpl = Pn + P * P;                          // P x P: C Pb^{-1} of the next panel's rows
+  V* cP = cpl + P * P;                          // (rows touched) x P : C_i Pb^{-1}
   V* Rsm = cP + (epb / B + 3) * P;              // P x ldb staged pivot rows (when stageR); the
                                                 // host sizes cP for epb / B + 3 rows (>= rows touched)
   __shared__ int gj_bad_s;
   V* pbuf = piv;                                // 2 x [P x ldb]  pivot-row snapshots
   V* cbuf = piv + 2 * P * (int64_t)ldb;         // 2 x [B x P]    panel-column snapshots
+  const bool look = threadIdx.x < kLookThreads;
+  const int te = threadIdx.x, ta = te / P, tb = te - ta * P;   // (row, column) of a P x P block element
+  // Gauss-Jordan inversion of the n x n block X in shared memory (no pivoting); element
+  // (t / P, t % P) of X is owned by thread t of the participating group when both indices
+  // are below n, every step is straight-line
+  // code between two barriers of that group (sync()), and each owner forms the pivot's
+  // reciprocal itself.
+  auto invert = [&](V* X, int n, auto sync) {
+    const bool own = te < P * P && ta < n && tb < n;
+    for (int kk = 0; kk < n; ++kk) {
+      V nv = zero;
+      if (own) {
+        V pinv;
+        if (!A::inv(X[kk * P + kk], &pinv)) {
+          gj_bad_s = 1;   // every owner sees the same pivot
+        } else if (ta == kk) {
+          nv = tb == kk ? pinv : A::mul(pinv, X[kk * P + tb]);
+        } else {
+          const V f = A::mul(X[ta * P + kk], pinv);
+          nv = tb == kk ? A::neg(f) : A::sub(X[ta * P + tb], A::mul(f, X[kk * P + tb]));
+        }
+      }
+      sync();
+      if (own) X[ta * P + tb] = nv;
+      sync();
+    }
+  };
+  if (threadIdx.x == 0) gj_bad_s = 0;
   for (int k0 = 0, q = 0; k0 < B; k0 += P, ++q) {
-    const int p = min(P, B - k0), k1 = k0 + p, k2 = min(B, k1 + P);
+    const int p = min(P, B - k0), k1 = k0 + p, k2 = min(B, k1 + P), k3 = min(B, k2 + P);
+    const int pn1 = k2 - k1;                    // size of the next panel's block (0: last panel)
     const V* R = pbuf + (int64_t)(q & 1) * P * ldb;
     const V* C = cbuf + (int64_t)(q & 1) * B * P;
     V* Rn = pbuf + (int64_t)((q + 1) & 1) * P * ldb;
     V* Cn = cbuf + (int64_t)((q + 1) & 1) * B * P;
-    // (1) Pb^{-1} by Gauss-Jordan on the p x p block in shared memory: thread t < p*p
-    // owns element t and every step is straight-line code between two CTA barriers
-    // (each owner thread forms the pivot's reciprocal itself).
-    if (threadIdx.x == 0) gj_bad_s = 0;
-    for (int t = threadIdx.x; t < p * p; t += blockDim.x) Pm[(t / p) * P + t % p] = R[(int64_t)(t / p) * ldb + k0 + t % p];
-    __syncthreads();
-    const int te = threadIdx.x, ta = te / p, tb = te - ta * p;
-    const bool own = te < p * p;
-    for (int kk = 0; kk < p; ++kk) {
-      V nv = zero;
-      if (own) {
-        V pinv;
-        if (!A::inv(Pm[kk * P + kk], &pinv)) {
-          gj_bad_s = 1;   // every owner sees the same pivot
-        } else if (ta == kk) {
-          nv = tb == kk ? pinv : A::mul(pinv, Pm[kk * P + tb]);
-        } else {
-          const V f = A::mul(Pm[ta * P + kk], pinv);
-          nv = tb == kk ? A::neg(f) : A::sub(Pm[ta * P + tb], A::mul(f, Pm[kk * P + tb]));
-        }
-      }
+    const V* snapn = pblk + (int64_t)((q + 1) & 1) * P * P;   // next block as of before this panel
+    V* snapnn = pblk + (int64_t)((q + 2) & 1) * P * P;        // the block after next, written below
+    // (1) Pb^{-1}: the first panel inverts its block here; later panels find it in Pm,
+    // inverted during the previous panel by the look-ahead warps
+    if (q == 0) {
+      for (int t = threadIdx.x; t < p * p; t += blockDim.x) Pm[(t / p) * P + t % p] = R[(int64_t)(t / p) * ldb + k0 + t % p];
       __syncthreads();
-      if (own) Pm[ta * P + tb] = nv;
-      __syncthreads();
+      invert(Pm, p, [] { __syncthreads(); });
     }
+    __syncthreads();
     if (gj_bad_s) {
       if (threadIdx.x == 0) atomicCAS(err, 0, HELM_EZEROPIVOT);
       return;   // every CTA sees the same pivot block and returns
     }
-    // (2) C_i Pb^{-1} for the rows this CTA touches (non-pivot rows)
-    for (int t = threadIdx.x; t < (i1 - i0 + 1) * p; t += blockDim.x) {
-      int r = t / p, c = t % p, i = i0 + r;
-      V acc = zero;
-      if (i < k0 || i >= k1)
-        for (int s2 = 0; s2 < p; ++s2) acc = A::fma(C[(int64_t)i * P + s2], Pm[s2 * P + c], acc);
-      cP[r * P + c] = acc;
-    }
-    __syncthreads();
-    // (3) element update over the CTA's row-major range, row by row (no per-element
-    // division); the pivot rows are staged in shared memory when they fit.
+    // stage the pivot rows in shared memory when they fit
     const V* Rs = R;
     if (stageR) {
       for (int t = threadIdx.x; t < p * B; t += blockDim.x) Rsm[(t / B) * ldb + t % B] = R[(int64_t)(t / B) * ldb + t % B];
       __syncthreads();
       Rs = Rsm;
     }
-    for (int i = i0; i <= i1; ++i) {
-      const int jb = i == i0 ? (int)(e0 - (int64_t)i0 * B) : 0;
-      const int je = i == i1 ? (int)(e1 - (int64_t)i1 * B) : B;
-      V* Si = S + (int64_t)i * ldb;
-      const bool pivrow = i >= k0 && i < k1;
-      const V* pr = Pm + (i - k0) * P;          // row of Pb^{-1} (pivot rows)
-      const V* ci = cP + (i - i0) * P;          // C_i Pb^{-1} (other rows)
-      V* rn = (i >= k1 && i < k2) ? Rn + (int64_t)(i - k1) * ldb : nullptr;
-      for (int j = jb + threadIdx.x; j < je; j += blockDim.x) {
-        V nv;
-        const bool pcol = j >= k0 && j < k1;
-        if (pivrow) {
-          if (pcol) {
-            nv = pr[j - k0];
+    if (look) {
+      // ---- look-ahead: the next panel's pivot block after this panel's update, formed
+      // with the same operations as the update below, then inverted into Pn
+      if (pn1 > 0) {
+        if (ta < pn1 && tb < p) {
+          V acc = zero;
+          for (int s2 = 0; s2 < p; ++s2) acc = A::fma(C[(int64_t)(k1 + ta) * P + s2], Pm[s2 * P + tb], acc);
+          cpl[ta * P + tb] = acc;
+        }
+        named_sync(1, kLookThreads);
+        if (ta < pn1 && tb < pn1) {
+          typename A::Acc acc = A::acc(snapn[ta * P + tb]);
+          for (int s2 = 0; s2 < p; ++s2) A::fnmac(cpl[ta * P + s2], Rs[s2 * ldb + k1 + tb], acc);
+          Pn[ta * P + tb] = A::fin(acc);
+        }
+        named_sync(1, kLookThreads);
+        invert(Pn, pn1, [] { named_sync(1, kLookThreads); });
+      }
+    } else {
+      // ---- update warps
+      const int tu = threadIdx.x - kLookThreads, nu = blockDim.x - kLookThreads;
+      // (2) C_i Pb^{-1} for the rows this CTA touches (non-pivot rows)
+      for (int t = tu; t < (i1 - i0 + 1) * p; t += nu) {
+        int r = t / p, c = t % p, i = i0 + r;
+        V acc = zero;
+        if (i < k0 || i >= k1)
+          for (int s2 = 0; s2 < p; ++s2) acc = A::fma(C[(int64_t)i * P + s2], Pm[s2 * P + c], acc);
+        cP[r * P + c] = acc;
+      }
+      named_sync(2, nu);
+      // (3) element update over the CTA's row-major range, row by row (no per-element division)
+      for (int i = i0; i <= i1; ++i) {
+        const int jb = i == i0 ? (int)(e0 - (int64_t)i0 * B) : 0;
+        const int je = i == i1 ? (int)(e1 - (int64_t)i1 * B) : B;
+        V* Si = S + (int64_t)i * ldb;
+        const bool pivrow = i >= k0 && i < k1;
+        const V* pr = Pm + (i - k0) * P;          // row of Pb^{-1} (pivot rows)
+        const V* ci = cP + (i - i0) * P;          // C_i Pb^{-1} (other rows)
+        V* rn = (i >= k1 && i < k2) ? Rn + (int64_t)(i - k1) * ldb : nullptr;
+        const bool nnrow = i >= k2 && i < k3;
+        for (int j = jb + tu; j < je; j += nu) {
+          V nv;
+          const bool pcol = j >= k0 && j < k1;
+          if (pivrow) {
+            if (pcol) {
+              nv = pr[j - k0];
+            } else {
+              typename A::Acc acc = A::acc(zero);
+              for (int s2 = 0; s2 < p; ++s2) A::fnmac(A::neg(pr[s2]), Rs[s2 * ldb + j], acc);
+              nv = A::fin(acc);
+            }
+          } else if (pcol) {
+            nv = A::neg(ci[j - k0]);
           } else {
-            typename A::Acc acc = A::acc(zero);
-            for (int s2 = 0; s2 < p; ++s2) A::fnmac(A::neg(pr[s2]), Rs[s2 * ldb + j], acc);
+            typename A::Acc acc = A::acc(Si[j]);
+            for (int s2 = 0; s2 < p; ++s2) A::fnmac(ci[s2], Rs[s2 * ldb + j], acc);
             nv = A::fin(acc);
           }
-        } else if (pcol) {
-          nv = A::neg(ci[j - k0]);
-        } else {
-          typename A::Acc acc = A::acc(Si[j]);
-          for (int s2 = 0; s2 < p; ++s2) A::fnmac(ci[s2], Rs[s2 * ldb + j], acc);
-          nv = A::fin(acc);
+          Si[j] = nv;
+          if (rn) rn[j] = nv;
+          if (j >= k1 && j < k2) Cn[(int64_t)i * P + (j - k1)] = nv;
+          if (nnrow && j >= k2 && j < k3) snapnn[(i - k2) * P + (j - k2)] = nv;   // block after next
         }
-        Si[j] = nv;
-        if (rn) rn[j] = nv;
-        if (j >= k1 && j < k2) Cn[(int64_t)i * P + (j - k1)] = nv;
       }
     }
+    if (!grid_barrier(bar, err, G)) return;
+    V* tpm = Pm;   // the next panel's inverse becomes current
+    Pm = Pn;
+    Pn = tpm;
     if (!grid_barrier(bar, err, G)) return;
   }
 }
@@ -1049,7 +1098,7 @@ int launch_factor(typename A::V* Dinv, typename A::V* tmp, typename A::V* piv, u
   const int64_t epb = ((int64_t)L.B * L.B + nblk / 2 - 1) / (nblk / 2);
   const int rows = (int)(epb / L.B) + 3;
   // +256: the kernel's static shared words precede the 128-byte aligned dynamic window
-  size_t smem = sizeof(V) * ((size_t)ncls * Ac.g.noff + P * P + (size_t)rows * P) + 256;
+  size_t smem = sizeof(V) * ((size_t)ncls * Ac.g.noff + 3 * P * P + (size_t)rows * P) + 256;
   const size_t rstage = sizeof(V) * (size_t)P * L.ldb;
   int stageR = smem + rstage <= 200 * 1024 ? 1 : 0;   // pivot rows in shared memory when they fit
   if (stageR) smem += rstage;

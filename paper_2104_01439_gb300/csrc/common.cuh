@@ -126,42 +126,45 @@ struct CoarseLayout {
 // ----------------------------------------------------------------------------
 // Bounded software grid barrier for cooperative launches.
 // state[0] = arrival counter, state[kBarGen] = generation, on separate 128-byte
-// lines (a barrier instance owns kBarWords words). Every thread reads the
-// generation before its CTA arrives; thread 0 arrives after the CTA barrier that
-// closes the phase; then EVERY thread polls until the generation moves on
-// (lane-uniform, one load per warp, with a short back-off), so no thread depends
-// on a CTA barrier placed after a wait to learn that the grid barrier opened.
-// On timeout the kernel's error word gets HELM_ETIMEOUT and it returns false.
+// lines (a barrier instance owns kBarWords words). Thread 0 of each CTA arrives
+// after the CTA barrier that closes the phase and polls the generation (with a
+// short back-off); the closing CTA barrier releases the other threads. On timeout
+// the kernel's error word gets HELM_ETIMEOUT and the barrier returns false.
 // ----------------------------------------------------------------------------
 constexpr int kBarGen = 32;     // words: the generation sits 128 bytes after the counter
 constexpr int kBarWords = 64;   // words per barrier instance
 __device__ inline bool grid_barrier(unsigned* state, int* err, unsigned nblocks) {
-  const unsigned gen = *(volatile unsigned*)(state + kBarGen);
+  __shared__ int bar_ok_s;
   __syncthreads();
   if (threadIdx.x == 0) {
+    int ok = 1;
+    volatile unsigned* vgen = state + kBarGen;
+    const unsigned gen = *vgen;
     __threadfence();
     const unsigned arrived = atomicAdd(state, 1u);
     if (arrived == nblocks - 1) {
       atomicExch(state, 0u);
       __threadfence();
       atomicAdd(state + kBarGen, 1u);
+    } else {
+      for (long long spins = 0; *vgen == gen;) {
+        if (++spins > (1ll << 22)) {
+          atomicCAS(err, 0, HELM_ETIMEOUT);
+          ok = 0;
+          break;
+        }
+        if (*(volatile int*)err != 0) {
+          ok = 0;
+          break;
+        }
+        __nanosleep(32);
+      }
     }
+    __threadfence();
+    bar_ok_s = ok;
   }
-  bool ok = true;
-  for (long long spins = 0; *(volatile unsigned*)(state + kBarGen) == gen;) {
-    if (++spins > (1ll << 22)) {
-      atomicCAS(err, 0, HELM_ETIMEOUT);
-      ok = false;
-      break;
-    }
-    if (*(volatile int*)err != 0) {
-      ok = false;
-      break;
-    }
-    __nanosleep(32);
-  }
-  __threadfence();
-  return ok;
+  __syncthreads();
+  return bar_ok_s != 0;
 }
 #endif
 

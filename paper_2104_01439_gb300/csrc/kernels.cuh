@@ -80,7 +80,9 @@ void launch_coarse_solve(const CoarsePlan& plan, const c2<T>* Dinv, const c2<T>*
 // meeting at L.mid), in complex128 (8-pivot Gauss-Jordan panels) or in complex double-float
 // (float4 hi/lo pairs, 16-pivot panels). tmp: 2 x B x ldb; piv: 2 x factor_workspace(L)
 // elements; bar: 2 x kBarWords unsigned (two halves of the grid factor the two chains concurrently).
-__host__ __device__ inline size_t factor_workspace(const CoarseLayout& L) { return 2 * 16 * (size_t)L.ldb + 2 * 16 * (size_t)L.B; }
+__host__ __device__ inline size_t factor_workspace(const CoarseLayout& L) {
+  return 2 * 16 * (size_t)L.ldb + 2 * 16 * (size_t)L.B + 2 * 16 * 16;
+}
 int coarse_factor_fp64(double2* Dinv, double2* tmp, double2* piv, unsigned* bar, int* err,
                        const StencilView<double>& Ac, const CoarseLayout& L, int nsm, cudaStream_t s);
 int coarse_factor_df(float4* Dinv, float4* tmp, float4* piv, unsigned* bar, int* err,
