@@ -510,7 +510,7 @@ size_t estimate_bytes(int dim, int order, int n, int precision, int restart) {
   const int64_t prec = v * (4 * N + 2 * nb * ldb + 2 * ldb) + 4 * 2 * ldb + 64;
   const int64_t factor = v * 3 * blk * nb;                        // Dinv, Lm, Up
   const int64_t krylov = 16 * ldN * (m + 1) + 16 * 3 * ldN + 16 * ldN * m + 16 * ldN +
-                         16 * std::max<int64_t>(nblk, (N + 127) / 128) * (m + 2) + 16 * (m + 2) * (m + 4);
+                         16 * std::max<int64_t>(nblk, (N + 255) / 256) * (m + 2) + 16 * (m + 2) * (m + 4);
   const int64_t tables = 1 << 20;
   const int64_t transient = (precision == HELM_MIXED ? 16 * blk * nb : 0) + 16 * 2 * blk +
                             16 * 2 * (16 * ldb + 16 * B) + 64;
@@ -674,7 +674,7 @@ static int setup_impl(helm_ctx* h) {
   kb.nblk = (int)std::max<int64_t>(1, (kb.N + 255) / 256);
   kb.nblk_dots = (int)std::max<int64_t>(1, (kb.N + 1023) / 1024);
   kb.m = m;
-  kb.nblk_upd = (int)std::max<int64_t>(1, (kb.N + 127) / 128);
+  kb.nblk_upd = (int)std::max<int64_t>(1, (kb.N + 255) / 256);
   kb.pstride = std::max(kb.nblk, std::max(kb.nblk_upd, kb.nblk_dots));
   CK(h->alloc(&kb.Vs, sizeof(float4) * kb.ldN * (m + 1)));
   CK(h->alloc(&kb.vj, sizeof(double2) * kb.ldN));

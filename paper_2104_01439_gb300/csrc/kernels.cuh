@@ -137,7 +137,7 @@ struct KrylovBufs {
   int nblk;        // blocks of the element-wise Krylov kernels (256 threads, one entry per thread)
   int nblk_dots;   // blocks of the inner-product kernel (256 threads, <= 4 entries per thread)
   int m;           // restart length (host copy of KState::m, sizes launches)
-  int nblk_upd;    // blocks of the update kernel (16 entries per warp)
+  int nblk_upd;    // blocks of the update kernel (32 entries per warp)
   int pstride;     // row stride of the partials buffer: max over the kernels that write it
   KState* st;
 };

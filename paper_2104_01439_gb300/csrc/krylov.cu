@@ -177,8 +177,9 @@ __global__ void __launch_bounds__(kT) k_reduce_h(KrylovBufs kb, double2* hp, int
 }
 
 // w -= sum_i hp[i] V[i] (sum in double-float, subtraction in FP64);  partial ||w||^2.
-// A warp takes 16 entries; its two half-warps sum over the two halves of the basis
-// (twice the loads in flight) and meet with one shuffle; the low half-warp finishes.
+// A warp takes 32 entries: its two half-warps sum over the two halves of the basis for two
+// entries per lane (four loads in flight per basis vector and lane pair), meet with one
+// shuffle, and then every lane finishes one entry (the FP64 tail uses all 32 lanes).
 __global__ void __launch_bounds__(kT) k_update(KrylovBufs kb, const double2* hp, int second) {
   KState* st = kb.st;
   if (!st->active || (second && !st->reorth)) return;
@@ -195,25 +196,37 @@ __global__ void __launch_bounds__(kT) k_update(KrylovBufs kb, const double2* hp,
   const int ib = half ? split : 0, ie = half ? j + 1 : split;
   double s2 = 0.0;
   const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;   // warps in the grid
-  for (int64_t wg = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5; wg * 16 < N; wg += nw) {
-    const int64_t n = wg * 16 + (lane & 15);
-    DF cr{0.f, 0.f}, ci{0.f, 0.f};
-    if (n < N) {
-      const float4* vs = kb.Vs + n;
-#pragma unroll 8
-      for (int i = ib; i < ie; ++i) {
-        const float4 v = vs[(int64_t)i * ld];   // (hr, hi, lr, li)
-        const float4 h = hs4[i];                // (re.h, re.l, im.h, im.l)
-        // h v = (hr vr - hi vi) + i (hr vi + hi vr)
-        df_mac(h.x, h.y, v.x, v.z, cr);
-        df_mac(-h.z, -h.w, v.y, v.w, cr);
-        df_mac(h.x, h.y, v.y, v.w, ci);
-        df_mac(h.z, h.w, v.x, v.z, ci);
-      }
+  for (int64_t wg = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5; wg * 32 < N; wg += nw) {
+    const int64_t na = wg * 32 + (lane & 15), nb2 = na + 16;   // this lane's two entries
+    DF ar{0.f, 0.f}, ai{0.f, 0.f}, br{0.f, 0.f}, bi{0.f, 0.f};
+    const bool va = na < N, vb = nb2 < N;
+    const float4* pa = kb.Vs + (va ? na : 0);
+    const float4* pb = kb.Vs + (vb ? nb2 : 0);
+#pragma unroll 4
+    for (int i = ib; i < ie; ++i) {
+      const float4 h = hs4[i];                          // (re.h, re.l, im.h, im.l)
+      const float4 v = pa[(int64_t)i * ld], u = pb[(int64_t)i * ld];   // (hr, hi, lr, li)
+      // h v = (hr vr - hi vi) + i (hr vi + hi vr)
+      df_mac(h.x, h.y, v.x, v.z, ar);
+      df_mac(-h.z, -h.w, v.y, v.w, ar);
+      df_mac(h.x, h.y, v.y, v.w, ai);
+      df_mac(h.z, h.w, v.x, v.z, ai);
+      df_mac(h.x, h.y, u.x, u.z, br);
+      df_mac(-h.z, -h.w, u.y, u.w, br);
+      df_mac(h.x, h.y, u.y, u.w, bi);
+      df_mac(h.z, h.w, u.x, u.z, bi);
     }
-    cr = df_add(cr, DF{__shfl_xor_sync(0xffffffffu, cr.h, 16), __shfl_xor_sync(0xffffffffu, cr.l, 16)});
-    ci = df_add(ci, DF{__shfl_xor_sync(0xffffffffu, ci.h, 16), __shfl_xor_sync(0xffffffffu, ci.l, 16)});
-    if (half == 0 && n < N) {
+    auto xsum = [](DF v) {
+      return df_add(v, DF{__shfl_xor_sync(0xffffffffu, v.h, 16), __shfl_xor_sync(0xffffffffu, v.l, 16)});
+    };
+    ar = xsum(ar);
+    ai = xsum(ai);
+    br = xsum(br);
+    bi = xsum(bi);
+    // lanes 0-15 finish entry na, lanes 16-31 entry nb2 (= wg * 32 + lane in both cases)
+    const int64_t n = wg * 32 + lane;
+    const DF cr = half ? br : ar, ci = half ? bi : ai;
+    if (n < N) {
       double2 w = kb.W[n];
       w.x -= df_val(cr);
       w.y -= df_val(ci);
