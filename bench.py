@@ -51,6 +51,66 @@ def workload_config(prec_name):
 
 # ---------------------------------------------------------------------------- helpers
 
+# stencil kernels at a size above L2: 2D P1, h = 1/4096 (16.8 M DoFs; one complex128
+# vector is 268 MB, twice the 129 MB L2), same kh and shift exponent as the solve workload
+STENCIL_N = 4096
+STENCIL_NU = 4
+
+
+def stencil_bytes_per_dof(nu, mixed):
+    """Algorithmic bytes per DoF of helm_apply and of nu smoothing sweeps from u = 0.
+
+    apply: read x, write y (complex128): 32 B.
+    mixed smoother (complex64 sweeps): the first kernel reads f (16) and writes u (8) and the
+    complex64 copy of f (8); every middle sweep reads f, u and writes u (8 + 8 + 8); the last
+    reads f, u (8 + 8) and writes complex128 (16). FP64: 16 B per vector access, no copy of f.
+    The first kernel runs two sweeps when nu >= 3 (u^1 at the neighbours recomputed from f)."""
+    first = 32
+    kernels = 1 + (nu - 1 - (2 if nu >= 3 else 1)) + 1
+    middle = kernels - 2
+    if mixed:
+        return {"apply": 32, "smooth": first + 24 * middle + 32, "kernels": kernels}
+    return {"apply": 32, "smooth": first + 48 * middle + 48, "kernels": kernels}
+
+
+def stencil_hbm(pkg, stream, dev, hbm, peak_kind, reps=20):
+    """CUDA-event times of helm_apply (A0, complex128) and of STENCIL_NU smoothing sweeps on
+    A_eps at h = 1/STENCIL_N, inputs resident and larger than L2 (no flush needed)."""
+    import torch
+    k = WL.k * STENCIL_N / WL.n
+    shift = k ** (math.log(WL.shift) / math.log(WL.k))
+    out = {"workload": f"2D P1, h=1/{STENCIL_N}, k={k:g}, eps=k^{math.log(WL.shift) / math.log(WL.k):.3f}",
+           "peak": hbm, "peak_kind": peak_kind, "l2": "each vector 2x L2; no flush"}
+    g = torch.Generator(device=dev).manual_seed(3)
+    for prec, name in ((pkg.HELM_MIXED, "mixed"), (pkg.HELM_FP64, "fp64")):
+        s = pkg.Solver(k, STENCIL_N, 1, shift, precision=prec, stream=stream, operator_only=True)
+        N = s.num_dofs
+        x = torch.randn(N, dtype=torch.complex128, device=dev, generator=g)
+        y = torch.empty_like(x)
+        bpd = stencil_bytes_per_dof(STENCIL_NU, prec == pkg.HELM_MIXED)
+        for label, fn, b in (("apply_A0", lambda: s.apply(x, 0, y), bpd["apply"]),
+                             (f"smooth_nu{STENCIL_NU}", lambda: s.smooth(x, STENCIL_NU, y), bpd["smooth"])):
+            if prec == pkg.HELM_FP64 and label == "apply_A0":
+                continue   # the outer apply is complex128 in both forms
+            for _ in range(3):
+                fn()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            torch.cuda.synchronize()
+            e0.record(stream)
+            for _ in range(reps):
+                fn()
+            e1.record(stream)
+            torch.cuda.synchronize()
+            ms = e0.elapsed_time(e1) / reps
+            gbs = b * N / (ms * 1e-3) / 1e9
+            key = label if label == "apply_A0" else f"{label}_{name}"
+            out[key] = {"ms": ms, "GBs": gbs, "frac": gbs / hbm, "bytes_per_dof": b, "dofs": N,
+                        "kernels_per_call": 1 if label == "apply_A0" else bpd["kernels"]}
+        s.close()
+        del x, y
+    return out
+
 def peaks():
     try:
         with open(PEAKS_FILE) as f:
@@ -310,12 +370,13 @@ def run_ours(args):
 
     if rank != 0:
         return
+    hbm, peak_kind = peaks()
+    stencil_large = stencil_hbm(pkg, stream, dev, hbm, peak_kind)
 
     # roofline of the dominant kernel (coarse triangular solves), from CUDA events inside the solve:
     # algorithmic bytes = the banded LU's two triangular factors read once, 2 b 8 B per coarse DoF
     # (complex64, b = W_c + 1), i.e. (2 W_c - 1) W_c^2 8 B for the 2D P1 coarse grid
     dom = max(prof, key=lambda k: prof[k][0])
-    hbm, peak_kind = peaks()
     Wc = WL.n // 2 + 1
     bytes_coarse = (2 * Wc - 1) * Wc * Wc * 8
     phase_ms = {k: v[0] / max(v[1], 1) for k, v in prof.items()}
@@ -329,7 +390,9 @@ def run_ours(args):
         "vcycle_fine_GBs": 52 * n_f / ((phase_ms["vcycle_pre_restrict"] + phase_ms["vcycle_prolong_post"]) * 1e-3)
         / 1e9,
         "peak_GBs": hbm,
-        "note": "algorithmic bytes / CUDA-event phase time; the phases include launch gaps",
+        "note": "algorithmic bytes / CUDA-event phase time inside the solve; the vectors are L2-resident "
+                "at this size and the phases include launch gaps",
+        "above_l2": stencil_large,
     }
 
     cpu = None
@@ -516,6 +579,16 @@ def run_kernel(args):
         v = torch.randn(s.num_dofs, dtype=torch.complex128, generator=g).cuda()
         for _ in range(args.steps):
             s.apply(v, 0)
+    elif args.kernel == "stencil":   # apply and smoother at h = 1/STENCIL_N (above L2)
+        s.close()
+        k = WL.k * STENCIL_N / WL.n
+        s = pkg.Solver(k, STENCIL_N, 1, k ** (math.log(WL.shift) / math.log(WL.k)), precision=prec,
+                       operator_only=True)
+        v = torch.randn(s.num_dofs, dtype=torch.complex128, generator=g).cuda()
+        y = torch.empty_like(v)
+        for _ in range(args.steps):
+            s.apply(v, 0, y)
+            s.smooth(v, STENCIL_NU, y)
     else:   # a full solve
         F = s.rhs_gaussian(2.0 / WL.n).cuda()
         for _ in range(args.steps):
@@ -532,7 +605,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--kernel", choices=["coarse", "vcycle", "apply", "solve"],
+    ap.add_argument("--kernel", choices=["coarse", "vcycle", "apply", "stencil", "solve"],
                     help="only launch one hot-path step --steps times (profiling aid)")
     ap.add_argument("--fp64", action="store_true", help="with --kernel: the all-FP64 form")
     ap.add_argument("--workload", default="solve", choices=["solve", "sweep", "serve"],

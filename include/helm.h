@@ -99,6 +99,15 @@ void helm_default_opts(helm_opts* opts);
  */
 int helm_setup(double k, double h, int order, double shift, const helm_opts* opts, helm_t* out);
 
+/*
+ * A handle with the fine-level operators only: the per-class stencils of A0 and A_eps,
+ * the Jacobi diagonal and the smoother's workspaces, but no coarse factor and no Krylov
+ * storage (set-up cost independent of the coarse solve). helm_apply and helm_smooth work
+ * on it; helm_solve, helm_solve_host, helm_batch_solve, helm_vcycle and the coarse solves
+ * return HELM_EINVAL. Same arguments and checks as helm_setup.
+ */
+int helm_operator_setup(double k, double h, int order, double shift, const helm_opts* opts, helm_t* out);
+
 /* Number of complex DoFs N = (order/h + 1)^dim of the fine space. */
 int helm_num_dofs(helm_t h, int64_t* n);
 
@@ -162,8 +171,20 @@ int helm_load_gaussian(int dim, int order, double h, double sigma, double cx, do
 
 /* ---- individual hot-path steps (device complex128 buffers) ------------- */
 
-/* y = A x with A = A0 (which = 0) or A_eps (which = 1), matrix-free, FP64 (Sec. 6). */
+/* y = A x with A = A0 (which = 0) or A_eps (which = 1), matrix-free, FP64 (Sec. 6).
+ * x, y: device complex128[N], not overlapping. Stream-ordered: the kernel is enqueued on
+ * the handle's stream (opts.stream) and the call returns without waiting for it; a
+ * launch failure returns HELM_ECUDA. */
 int helm_apply(helm_t h, int which, const void* x, void* y);
+
+/*
+ * u = nu damped-Jacobi sweeps on A_eps applied to f from u^0 = 0 (the presmoothing of
+ * Algorithm 1: u^{i+1} = u^i + omega D^{-1} (f - A_eps u^i)), in the handle's precision
+ * (the sweeps of the mixed form run in complex64, the last one writes complex128).
+ * f, u: device complex128[N], not overlapping; 2 <= nu <= 8 (else HELM_EINVAL).
+ * Stream-ordered like helm_apply. Works on full and operator-only handles.
+ */
+int helm_smooth(helm_t h, const void* f, void* u, int nu);
 
 /*
  * u = one twogrid V(nu,nu)-cycle on A_eps applied to f with u^0 = 0

@@ -25,6 +25,7 @@ EXPORTS = [
     "helm_last_profile", "helm_set_profiling", "helm_coarse_solve_noalloc",
     "helm_request_bytes", "helm_device_bytes", "helm_server_create", "helm_server_submit", "helm_server_poll",
     "helm_server_wait", "helm_server_drain", "helm_server_destroy", "helm_load_planewave", "helm_load_gaussian",
+    "helm_operator_setup", "helm_smooth",
 ]
 
 
@@ -103,6 +104,8 @@ def load(path: str = LIB_PATH):
     lib.helm_server_destroy.argtypes = [vp]
     lib.helm_server_destroy.restype = None
     lib.helm_load_planewave.argtypes = [i, i, d, d, d, vp]
+    lib.helm_operator_setup.argtypes = [d, d, i, d, ctypes.POINTER(HelmOpts), ctypes.POINTER(vp)]
+    lib.helm_smooth.argtypes = [vp, vp, vp, i]
     lib.helm_load_gaussian.argtypes = [i, i, d, d, d, d, d, vp]
     for name in EXPORTS:
         if name not in ("helm_default_opts", "helm_destroy", "helm_strerror", "helm_last_cuda_error",
@@ -147,7 +150,7 @@ class Solver:
 
     def __init__(self, k: float, n: int, order: int = 1, shift: float = 0.0, dim: int = 2,
                  omega: float = 0.6, nu: int = 2, restart: int = 50, maxit: int = 500,
-                 tol: float = 1e-8, precision: int = HELM_FP64, stream=None):
+                 tol: float = 1e-8, precision: int = HELM_FP64, stream=None, operator_only: bool = False):
         import torch
         lib = load()
         o = HelmOpts()
@@ -159,7 +162,8 @@ class Solver:
         o.stream = ctypes.c_void_p(stream.cuda_stream)
         self._h = ctypes.c_void_p()
         self.k, self.n, self.order, self.shift, self.dim, self.precision = k, n, order, shift, dim, precision
-        _check(lib.helm_setup(float(k), 1.0 / n, order, float(shift), ctypes.byref(o), ctypes.byref(self._h)))
+        setup = lib.helm_operator_setup if operator_only else lib.helm_setup
+        _check(setup(float(k), 1.0 / n, order, float(shift), ctypes.byref(o), ctypes.byref(self._h)))
         nd = ctypes.c_int64()
         _check(lib.helm_num_dofs(self._h, ctypes.byref(nd)))
         self.num_dofs = nd.value
@@ -200,10 +204,17 @@ class Solver:
         _check(load().helm_solve_host(self._h, _ptr(F_host), _ptr(x_host), ctypes.byref(r)))
         return _res(r)
 
-    def apply(self, x, which: int = 0):
-        y = self._dev()
+    def apply(self, x, which: int = 0, y=None):
+        """y = A0 x (which = 0) or A_eps x (which = 1); stream-ordered on the handle's stream."""
+        y = self._dev() if y is None else y
         _check(load().helm_apply(self._h, which, _ptr(x), _ptr(y)))
         return y
+
+    def smooth(self, f, nu: int = 2, u=None):
+        """nu damped-Jacobi sweeps on A_eps from u = 0 (helm_smooth); stream-ordered."""
+        u = self._dev() if u is None else u
+        _check(load().helm_smooth(self._h, _ptr(f), _ptr(u), int(nu)))
+        return u
 
     def vcycle(self, f):
         u = self._dev()

@@ -52,6 +52,7 @@ template <typename T> struct Prec {
 
 struct helm_ctx {
   int dim = 2, order = 1, n = 0;
+  bool op_only = false;        // fine-level operators only (helm_operator_setup)
   double k = 0, h = 0, shift = 0;
   helm_opts opts{};
   cudaStream_t s = nullptr;
@@ -519,6 +520,31 @@ size_t estimate_bytes(int dim, int order, int n, int precision, int restart) {
 }  // namespace helm
 
 // ============================================================================
+namespace {
+template <typename T>
+void enqueue_smooth(helm_ctx* h, const double2* f, double2* u, int nu, cudaStream_t s) {
+  using V = c2<T>;
+  Prec<T>& p = h->prec<T>();
+  StencilView<T> Ae = make_view<T>(h->gf, p.coefAe, p.wdinv);
+  V* cur = p.ua;
+  V* oth = p.ub;
+  const bool two = nu >= 3;   // the first two sweeps fused when two or more precede the last one
+  VecSel<const V> fT;
+  if constexpr (sizeof(V) == sizeof(double2)) {
+    launch_jacobi_from_zero<T, double2>(Ae, vsel<const double2>(f), cur, nullptr, two, nullptr, s);
+    fT = VecSel<const V>{reinterpret_cast<const V*>(f), 0, nullptr, 0};
+  } else {
+    launch_jacobi_from_zero<T, double2>(Ae, vsel<const double2>(f), cur, p.fT, two, nullptr, s);
+    fT = vsel<const V>(p.fT);
+  }
+  for (int done = two ? 2 : 1; done < nu - 1; ++done) {
+    launch_jacobi<T, V, V>(Ae, fT, cur, vsel<V>(oth), nullptr, s);
+    std::swap(cur, oth);
+  }
+  launch_jacobi<T, V, double2>(Ae, fT, cur, vsel<double2>(u), nullptr, s);   // last sweep writes complex128
+}
+}  // namespace
+
 extern "C" {
 
 void helm_default_opts(helm_opts* o) {
@@ -584,6 +610,26 @@ static int setup_impl(helm_ctx* h) {
   auto Ac = complex_table(h->tab.Kc, h->tab.Mc, h->tab.Bc, h->k, h->shift);
   auto wd = wdinv_table(Ae, h->ncls_f, h->gf.noff, o.omega);
   if ((rc = upload<double>(h, &h->coefA0, A0))) return rc;
+
+  if (h->op_only) {
+    // fine-level operators and the smoother's workspaces only
+    CK(h->alloc(&h->err, sizeof(int)));
+    CK(cudaMemsetAsync(h->err, 0, sizeof(int), s));
+    const size_t Nf = (size_t)h->gf.N;
+    if (o.precision == HELM_MIXED) {
+      if ((rc = setup_prec<float>(h, Ae, wd, Ac, false))) return rc;
+      CK(h->alloc(&h->p32.ua, sizeof(float2) * Nf));
+      CK(h->alloc(&h->p32.ub, sizeof(float2) * Nf));
+      CK(h->alloc(&h->p32.fT, sizeof(float2) * Nf));
+    }
+    if ((rc = setup_prec<double>(h, Ae, wd, Ac, false))) return rc;
+    if (o.precision == HELM_FP64) {
+      CK(h->alloc(&h->p64.ua, sizeof(double2) * Nf));
+      CK(h->alloc(&h->p64.ub, sizeof(double2) * Nf));
+    }
+    CK(cudaStreamSynchronize(s));
+    return HELM_OK;
+  }
 
   // coarse block layout
   CoarseLayout& L = h->L;
@@ -701,7 +747,8 @@ static int setup_impl(helm_ctx* h) {
   return capture_iteration(h);
 }
 
-int helm_setup(double k, double h, int order, double shift, const helm_opts* opts, helm_t* out) {
+static int setup_any(double k, double h, int order, double shift, const helm_opts* opts, helm_t* out,
+                     bool op_only) {
   if (!out) return HELM_EINVAL;
   *out = nullptr;
   helm_opts o;
@@ -725,6 +772,7 @@ int helm_setup(double k, double h, int order, double shift, const helm_opts* opt
   c->shift = shift;
   c->opts = o;
   c->s = (cudaStream_t)o.stream;
+  c->op_only = op_only;
   int rc = setup_impl(c);
   if (rc != HELM_OK) {
     helm_destroy(c);
@@ -732,6 +780,14 @@ int helm_setup(double k, double h, int order, double shift, const helm_opts* opt
   }
   *out = c;
   return HELM_OK;
+}
+
+int helm_setup(double k, double h, int order, double shift, const helm_opts* opts, helm_t* out) {
+  return setup_any(k, h, order, shift, opts, out, false);
+}
+
+int helm_operator_setup(double k, double h, int order, double shift, const helm_opts* opts, helm_t* out) {
+  return setup_any(k, h, order, shift, opts, out, true);
 }
 
 int helm_num_dofs(helm_t h, int64_t* n) {
@@ -754,7 +810,7 @@ int helm_setup_info(helm_t h, float* ms, int* kernels) {
 }
 
 int helm_solve(helm_t h, const void* F, void* x, helm_result* res) {
-  if (!h || !F || !x) return HELM_EINVAL;
+  if (!h || !F || !x || h->op_only) return HELM_EINVAL;
   SolveTask t{h, (const double2*)F, (double2*)x, res};
   int rc = solve_begin(t);
   if (rc) return rc;
@@ -764,7 +820,7 @@ int helm_solve(helm_t h, const void* F, void* x, helm_result* res) {
 }
 
 int helm_solve_host(helm_t h, const void* F_host, void* x_host, helm_result* res) {
-  if (!h || !F_host || !x_host) return HELM_EINVAL;
+  if (!h || !F_host || !x_host || h->op_only) return HELM_EINVAL;
   size_t bytes = sizeof(double2) * h->gf.N;
   if (!h->Fdev) {
     CK(h->alloc(&h->Fdev, bytes));
@@ -781,7 +837,7 @@ int helm_solve_host(helm_t h, const void* F_host, void* x_host, helm_result* res
 int helm_batch_solve(int count, const helm_t* hs, const void* const* F, void* const* x, helm_result* res) {
   if (count < 0 || (count > 0 && (!hs || !F || !x))) return HELM_EINVAL;
   for (int i = 0; i < count; ++i) {
-    if (!hs[i] || !F[i] || !x[i]) return HELM_EINVAL;
+    if (!hs[i] || !F[i] || !x[i] || hs[i]->op_only) return HELM_EINVAL;
     for (int j = 0; j < i; ++j)
       if (hs[j] == hs[i]) return HELM_EINVAL;
   }
@@ -848,12 +904,22 @@ int helm_apply(helm_t h, int which, const void* x, void* y) {
   launch_apply<double, double2, double2>(A, vsel<const double2>((const double2*)x), vsel<double2>((double2*)y),
                                          nullptr, h->s);
   CK(cudaGetLastError());
-  CK(cudaStreamSynchronize(h->s));
+  return HELM_OK;
+}
+
+
+int helm_smooth(helm_t h, const void* f, void* u, int nu) {
+  if (!h || !f || !u || nu < 2 || nu > 8) return HELM_EINVAL;
+  if (h->opts.precision == HELM_MIXED)
+    enqueue_smooth<float>(h, (const double2*)f, (double2*)u, nu, h->s);
+  else
+    enqueue_smooth<double>(h, (const double2*)f, (double2*)u, nu, h->s);
+  CK(cudaGetLastError());
   return HELM_OK;
 }
 
 int helm_vcycle(helm_t h, const void* f, void* u) {
-  if (!h || !f || !u) return HELM_EINVAL;
+  if (!h || !f || !u || h->op_only) return HELM_EINVAL;
   CK(cudaMemsetAsync(h->err, 0, sizeof(int), h->s));
   enqueue_vcycle_any(h, vsel<const double2>((const double2*)f), vsel<double2>((double2*)u), nullptr, h->s);
   CK(cudaGetLastError());
@@ -862,7 +928,7 @@ int helm_vcycle(helm_t h, const void* f, void* u) {
 }
 
 int helm_coarse_solve(helm_t h, const void* rc_nat, void* uc_nat) {
-  if (!h || !rc_nat || !uc_nat) return HELM_EINVAL;
+  if (!h || !rc_nat || !uc_nat || h->op_only) return HELM_EINVAL;
   CK(cudaMemsetAsync(h->err, 0, sizeof(int), h->s));
   if (h->opts.precision == HELM_MIXED) {
     Prec<float>& p = h->p32;
@@ -963,7 +1029,7 @@ int coarse_solve_noalloc(helm_t h, const double2* rc_nat, double2* uc_nat) {
 }  // namespace
 
 extern "C" int helm_coarse_solve_noalloc(helm_t h, const void* rc, void* uc) {
-  if (!h || !rc || !uc) return HELM_EINVAL;
+  if (!h || !rc || !uc || h->op_only) return HELM_EINVAL;
   if (h->opts.precision == HELM_MIXED)
     return coarse_solve_noalloc<float>(h, (const double2*)rc, (double2*)uc);
   return coarse_solve_noalloc<double>(h, (const double2*)rc, (double2*)uc);

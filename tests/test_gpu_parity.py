@@ -93,6 +93,28 @@ def test_vcycle(wl, prec, tol):
     s.close()
 
 
+@pytest.mark.parametrize("prec,tol", [(pkg.HELM_FP64, 1e-12), (pkg.HELM_MIXED, 2e-6)])
+@pytest.mark.parametrize("wl", CASES, ids=lambda w: w.name)
+def test_smooth_operator_handle(wl, prec, tol):
+    """nu damped-Jacobi sweeps from u = 0 on an operator-only handle against the oracle's
+    sweeps (Algorithm 1, smoothing); the handle refuses every call that needs the coarse level."""
+    pb = problem(wl)
+    s = pkg.Solver(wl.k, wl.n, wl.order, wl.shift, dim=wl.dim, precision=prec, operator_only=True)
+    f = crand(pb.mesh.num_dofs, 17)
+    dinv = 1.0 / pb.Aeps.diagonal()
+    for nu in (2, 3, 5):
+        u = s.smooth(dev(f), nu).cpu().numpy()
+        ref = osolver.jacobi_sweeps(pb.Aeps, dinv, f, np.zeros_like(f), 0.6, nu)
+        assert rel(u, ref) <= tol * nu, nu
+    x = crand(pb.mesh.num_dofs, 7)
+    assert rel(s.apply(dev(x), 1).cpu().numpy(), pb.Aeps @ x) <= 1e-12
+    for call in (lambda: s.vcycle(dev(f)), lambda: s.solve(dev(f)), lambda: s.smooth(dev(f), 1),
+                 lambda: s.smooth(dev(f), 9)):
+        with pytest.raises(pkg.HelmError):
+            call()
+    s.close()
+
+
 @pytest.mark.parametrize("wl", [CASES[1], CASES[2], CASES[4], CASES[5]], ids=lambda w: w.name)
 def test_rhs_builders(wl):
     pb = problem(wl)
