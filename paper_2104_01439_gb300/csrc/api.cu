@@ -25,7 +25,7 @@ struct Profile {
   std::vector<cudaEvent_t> ev;   // kPhases + 1 per iteration
 };
 const char* kPhaseNames[Profile::kPhases] = {"vcycle_pre_restrict", "coarse_solve", "vcycle_prolong_post",
-                                             "apply_A0", "arnoldi_cgs", "givens"};
+                                             "apply_A0", "arnoldi_dots_givens", "arnoldi_update"};
 
 template <typename T> struct Prec {
   c2<T>* coefAe = nullptr;   // fine A_eps
@@ -269,11 +269,13 @@ void enqueue_vcycle_any(helm_ctx* h, VecSel<const double2> f, VecSel<double2> z,
     enqueue_vcycle<double>(h, f, z, active, s, prof, ev0);
 }
 
-// One FGMRES/Arnoldi step j (device index): z_j = Vcycle(v_j), w = A0 z_j,
-// CGS(+DGKS) against V[0..j], v_{j+1} = w/||w||, Givens + convergence test.
+// One FGMRES/Arnoldi step j (device index): z_j = Vcycle(u_j), w = A0 z_j, then the
+// lagged Gram-Schmidt step (finishes v_j and column j-1 with its Givens rotation and
+// convergence test, orthogonalises w, u_{j+1} = w/||w||). A step with pre == 0 skips the
+// preconditioner and A0 and only finishes the last column of the cycle.
 void enqueue_iteration(helm_ctx* h, cudaStream_t s, Profile* prof = nullptr, int ev0 = 0) {
   const KrylovBufs& kb = h->kb;
-  const int* act = &kb.st->active;
+  const int* act = &kb.st->pre;
   const int* jsel = &kb.st->j;
   if (prof) cudaEventRecord(prof->ev[ev0 + 0], s);
   enqueue_vcycle_any(h, VecSel<const double2>{kb.vj, 0, nullptr, 0}, VecSel<double2>{kb.Z, kb.ldN, jsel, 0},
@@ -283,11 +285,7 @@ void enqueue_iteration(helm_ctx* h, cudaStream_t s, Profile* prof = nullptr, int
   launch_apply<double, double2, double2>(A0, VecSel<const double2>{kb.Z, kb.ldN, jsel, 0},
                                          VecSel<double2>{kb.W, 0, nullptr, 0}, act, s);
   if (prof) cudaEventRecord(prof->ev[ev0 + 4], s);
-  launch_cgs_pass(kb, false, s);
-  launch_cgs_pass(kb, true, s);
-  launch_normalize(kb, s);
-  if (prof) cudaEventRecord(prof->ev[ev0 + 5], s);
-  launch_givens(kb, s);
+  launch_arnoldi(kb, s, prof ? prof->ev[ev0 + 5] : nullptr);
   if (prof) cudaEventRecord(prof->ev[ev0 + 6], s);
 }
 
@@ -362,7 +360,8 @@ bool solve_step(SolveTask& t, bool blocking) {
   const int m = h->opts.restart, maxit = h->opts.maxit;
   switch (t.phase) {
     case SolveTask::ITER: {
-      int chunk = std::min({4, m - t.launched_in_cycle, maxit - t.launched_total});
+      // a cycle takes up to m + 1 steps: the last one only finishes column m - 1
+      int chunk = std::min(4, m + 1 - t.launched_in_cycle);
       if (chunk < 1) chunk = 1;
       for (int c = 0; c < chunk; ++c) {
         if (h->prof.on) {
@@ -398,7 +397,7 @@ bool solve_step(SolveTask& t, bool blocking) {
     case SolveTask::WAIT_ITER: {
       if (blocking) cudaEventSynchronize(t.ready);
       else if (cudaEventQuery(t.ready) == cudaErrorNotReady) return false;
-      if (h->st_h->active && t.launched_in_cycle < m && t.launched_total < maxit) {
+      if (h->st_h->active && t.launched_in_cycle < m + 1) {
         t.phase = SolveTask::ITER;
         return false;
       }
@@ -511,7 +510,7 @@ size_t estimate_bytes(int dim, int order, int n, int precision, int restart) {
   const int64_t prec = v * (4 * N + 2 * nb * ldb + 2 * ldb) + 4 * 2 * ldb + 64;
   const int64_t factor = v * 3 * blk * nb;                        // Dinv, Lm, Up
   const int64_t krylov = 16 * ldN * (m + 1) + 16 * 3 * ldN + 16 * ldN * m + 16 * ldN +
-                         16 * std::max<int64_t>(nblk, (N + 255) / 256) * (m + 2) + 16 * (m + 2) * (m + 4);
+                         16 * std::max<int64_t>(nblk, (N + 255) / 256) * kb_rows((int)m) + 16 * (m + 2) * (m + 6);
   const int64_t tables = 1 << 20;
   const int64_t transient = (precision == HELM_MIXED ? 16 * blk * nb : 0) + 16 * 2 * blk +
                             16 * 2 * (16 * ldb + 16 * B) + 64;
@@ -733,8 +732,10 @@ static int setup_impl(helm_ctx* h) {
   CK(h->alloc(&kb.g, sizeof(double2) * (m + 1)));
   CK(h->alloc(&kb.y, sizeof(double2) * m));
   CK(h->alloc(&kb.hcol, sizeof(double2) * (m + 2)));
+  CK(h->alloc(&kb.hfin, sizeof(double2) * (m + 2)));
   CK(h->alloc(&kb.hp, sizeof(double2) * (m + 2)));
-  CK(h->alloc(&kb.part, sizeof(double2) * (size_t)kb.pstride * (m + 2)));
+  CK(h->alloc(&kb.tp, sizeof(double2) * (m + 2)));
+  CK(h->alloc(&kb.part, sizeof(double2) * (size_t)kb.pstride * kb_rows(m)));
   CK(h->alloc(&kb.st, sizeof(KState)));
   CK(h->alloc(&h->rres, sizeof(double2) * kb.ldN));
   CK(cudaMallocHost(&h->st_h, sizeof(KState)));

@@ -97,12 +97,13 @@ void convert_factor_df(const float4* src, float2* dst, size_t n, cudaStream_t s)
 
 // ---- Krylov (krylov.cu) ----------------------------------------------------
 struct KState {
-  int j;           // Arnoldi column being built in this cycle
+  int j;           // Arnoldi step of this cycle (slot j holds the vector u_j being finished);
+                   // when the cycle stops: the number of finished columns
   int active;      // 1 while the cycle runs
-  int total;       // total Arnoldi steps
+  int total;       // finished Arnoldi columns over all cycles
   int converged;   // Givens estimate <= tol
   int breakdown;   // h_{j+1,j} == 0
-  int reorth;      // DGKS: second CGS pass needed
+  int pre;         // this step applies the preconditioner and A0 (else it only finishes column j-1)
   int m, maxit;
   int nonfinite;
   int pad_;
@@ -110,10 +111,18 @@ struct KState {
   double beta;     // cycle's initial residual norm
   double tol;
   double est;      // |g_{j+1}| / ||F||
-  double wn0;      // ||w|| before orthogonalisation
-  double wn;       // ||w|| after
+  double sig;      // ||w|| of the previous step (u_j = w / sig)
+  double irho;     // 1 / rho of this step
+  double2 hjj;     // h_jj of this step
   double relres;   // true relative residual at cycle end
 };
+
+// Rows of the partials buffer (entry-major, kb.pstride apart): the inner products
+// s_i = <v_i, u_j> (rows 0..m), t_i = <v_i, w> (rows m+1..2m+1) and one row of norms.
+__host__ __device__ inline int64_t kb_row_s(int i) { return i; }
+__host__ __device__ inline int64_t kb_row_t(int m, int i) { return (int64_t)m + 1 + i; }
+__host__ __device__ inline int64_t kb_row_norm(int m) { return 2 * (int64_t)m + 2; }
+__host__ __device__ inline int64_t kb_rows(int m) { return 2 * (int64_t)m + 3; }
 
 struct KrylovBufs {
   // Krylov basis V in double-float form: each complex128 entry as a pair of
@@ -131,9 +140,11 @@ struct KrylovBufs {
   double2* sn;     // m
   double2* g;      // m+1
   double2* y;      // m
-  double2* hcol;   // m+2 : accumulated h of the current column
-  double2* hp;     // m+1 : projection coefficients of the current CGS pass
-  double2* part;   // nblk x (m+2) partial sums (inner products: double-float as float4)
+  double2* hcol;   // m+2 : the column started by the previous step (finished by this one)
+  double2* hfin;   // m+2 : the finished column handed to the Givens step
+  double2* hp;     // m+1 : s_i = <v_i, u_j>
+  double2* tp;     // m+1 : t_i = <v_i, w>
+  double2* part;   // pstride x kb_rows(m) partial sums (inner products: double-float as float4)
   int nblk;        // blocks of the element-wise Krylov kernels (256 threads, one entry per thread)
   int nblk_dots;   // blocks of the inner-product kernel (256 threads, <= 4 entries per thread)
   int m;           // restart length (host copy of KState::m, sizes launches)
@@ -142,9 +153,10 @@ struct KrylovBufs {
   KState* st;
 };
 
-void launch_cgs_pass(const KrylovBufs& kb, bool second, cudaStream_t s);   // dots+reduce+update+norm
-void launch_normalize(const KrylovBufs& kb, cudaStream_t s);
-void launch_givens(const KrylovBufs& kb, cudaStream_t s);
+// One Arnoldi step after w = A0 z_j: inner products, coefficients (finishing column j-1 with
+// its Givens step), the joint correction sweep and u_{j+1} = w / ||w||. `mid` (may be null)
+// is recorded between the coefficient kernel and the correction sweep.
+void launch_arnoldi(const KrylovBufs& kb, cudaStream_t s, cudaEvent_t mid);
 void launch_cycle_start(const KrylovBufs& kb, const double2* r, cudaStream_t s);   // V0 = r / ||r||
 void launch_backsolve(const KrylovBufs& kb, cudaStream_t s);
 void launch_update_x(const KrylovBufs& kb, double2* x, cudaStream_t s);

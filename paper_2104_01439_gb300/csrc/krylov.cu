@@ -1,10 +1,15 @@
 // Flexible GMRES (Saad 1993; Sec. 4: A0 P^{-1} (P u) = F) in complex128.
 //
-// Arnoldi orthogonalisation is classical Gram-Schmidt with one conditional
-// second pass (DGKS criterion ||w_after|| < ||w_before|| / sqrt(2)); inner
-// products are Hermitian, <a, b> = sum conj(a_i) b_i. Each pass is a
-// grid-wide dot-product kernel (8 basis vectors per sweep over w), a one-block
-// deterministic reduction, and an update kernel that also accumulates ||w||^2.
+// Arnoldi orthogonalisation is classical Gram-Schmidt with reorthogonalisation,
+// in the lagged one-sweep form DCGS2 (Swirydowicz, Langou, Ananthan, Yang, Thomas,
+// "Low synchronization Gram-Schmidt and GMRES algorithms", 2020): step j holds the
+// vector u_j orthogonalised once; one sweep over the basis forms the inner products
+// of both u_j (its second pass) and w = A0 z_j (its first pass), and one sweep applies
+// both corrections. Column j-1 of the Hessenberg matrix is therefore finished one step
+// late, and each cycle of m columns ends with a step that only finishes column m-1.
+// The preconditioner sees u_j; FGMRES allows any z_j, and A0 z_j is expanded in the
+// final orthonormal basis, so the Arnoldi relation A0 Z_m = V_{m+1} H_m holds exactly
+// in exact arithmetic. Inner products are Hermitian, <a, b> = sum conj(a_i) b_i.
 //
 // GB300 issues FP64 at 1/58 of its FP32 rate, so the Gram-Schmidt arithmetic
 // is done in double-float: every basis entry is stored as hi + lo float pairs,
@@ -13,9 +18,9 @@
 // partials are converted to double. Inner products carry ~48 significant bits
 // (relative error ~1e-15 of sum |a_i b_i|), the vector w itself stays complex128.
 // Complex Givens rotations (c real, s complex), the residual estimate
-// |g_{j+1}| and the convergence test run on the device in one thread, so a
+// |g_{j+1}| and the convergence test run on the device in one warp, so a
 // captured iteration never returns to the host. All kernels read the Arnoldi
-// index j and the 'active' flag from device state.
+// index j and the 'active' / 'pre' flags from device state.
 #include "dfloat.cuh"
 #include "kernels.cuh"
 
@@ -55,7 +60,7 @@ constexpr int kGD = 4;   // basis vectors per sweep of the inner-product kernel
 // w -> (hi, lo) once per pass, so the inner products run on FP32 pipes only
 __global__ void __launch_bounds__(kT) k_split_w(KrylovBufs kb) {
   KState* st = kb.st;
-  if (!st->active) return;
+  if (!st->active || !st->pre) return;
   for (int64_t n = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; n < kb.N; n += (int64_t)gridDim.x * blockDim.x) {
     double2 v = kb.W[n];
     DF r = df_split(v.x), q = df_split(v.y);
@@ -63,219 +68,109 @@ __global__ void __launch_bounds__(kT) k_split_w(KrylovBufs kb) {
   }
 }
 
-// partial dots of w against the double-float basis V[0..j] (and ||w||^2 in the first pass).
-// Grid: x over chunks of w (kE entries per thread), y over groups of kGD basis vectors, so
-// that every (chunk, group) pair is its own block and many loads are in flight.
-__global__ void __launch_bounds__(kT) k_dots(KrylovBufs kb, int second) {
+// Inner products of the basis slots 0..j against two vectors in one sweep over V:
+//   s_i = <v_i, u_j>  (u_j = the once-orthogonalised vector in slot j; s_j = ||u_j||^2)
+//   t_i = <v_i, w>    (w = A0 z_j; only when this step applies the preconditioner)
+// Grid: x over chunks of the vectors (kE entries per thread), y over groups of kGD basis
+// slots, so every (chunk, group) pair is its own block. Block partials stay double-float.
+__global__ void __launch_bounds__(kT) k_dots2(KrylovBufs kb) {
   KState* st = kb.st;
-  if (!st->active || (second && !st->reorth)) return;
+  if (!st->active) return;
   const int j = st->j, m = st->m;
+  const bool pre = st->pre != 0;
   const int i0 = blockIdx.y * kGD;
   if (i0 > j) return;
   const int ng = min(kGD, j + 1 - i0);
   const int64_t N = kb.N, ld = kb.ldN;
-  __shared__ float4 red[kT / 32][kGD];
-  __shared__ double rn[kT / 32];
+  __shared__ float4 red[kT / 32][2 * kGD];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  // partials are entry-major, part[i * pstride + block], so the reductions read them contiguously
   const int64_t PS = kb.pstride;
   const int64_t stride = (int64_t)gridDim.x * blockDim.x, base = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  if (!second && blockIdx.y == 0) {
-    double s2 = 0.0;
-#pragma unroll
-    for (int k = 0; k < kE; ++k) {
-      const int64_t n = base + k * stride;
-      if (n < N) {
-        double2 v = kb.W[n];
-        s2 = fma(v.x, v.x, fma(v.y, v.y, s2));
-      }
-    }
-    s2 = wsum(s2);
-    if (lane == 0) rn[warp] = s2;
-    __syncthreads();
-    if (threadIdx.x == 0) {
-      double t = 0.0;
-      for (int i = 0; i < kT / 32; ++i) t += rn[i];
-      kb.part[(int64_t)(m + 1) * PS + blockIdx.x] = make_double2(t, 0.0);
-    }
-  }
   float4* part4 = reinterpret_cast<float4*>(kb.part);
-  DF ar[kGD], ai[kGD];
+  const float4* uj = kb.Vs + (int64_t)j * ld;
+  DF sr[kGD], si[kGD], tr[kGD], ti[kGD];
 #pragma unroll
-  for (int t = 0; t < kGD; ++t) ar[t] = ai[t] = DF{0.f, 0.f};
+  for (int t = 0; t < kGD; ++t) sr[t] = si[t] = tr[t] = ti[t] = DF{0.f, 0.f};
 #pragma unroll
   for (int k = 0; k < kE; ++k) {
     const int64_t n = base + k * stride;
     if (n >= N) break;
-    const float4 w = kb.Ws[n];   // (hr, hi, lr, li)
+    const float4 u = uj[n];                        // (hr, hi, lr, li)
+    const float4 w = pre ? kb.Ws[n] : dfc_zero();
 #pragma unroll
     for (int t = 0; t < kGD; ++t) {
       if (t < ng) {
         const float4 v = kb.Vs[(int64_t)(i0 + t) * ld + n];
-        // conj(v) w = (vr wr + vi wi) + i (vr wi - vi wr)
-        df_mac(v.x, v.z, w.x, w.z, ar[t]);
-        df_mac(v.y, v.w, w.y, w.w, ar[t]);
-        df_mac(v.x, v.z, w.y, w.w, ai[t]);
-        df_mac(-v.y, -v.w, w.x, w.z, ai[t]);
+        // conj(v) x = (vr xr + vi xi) + i (vr xi - vi xr)
+        df_mac(v.x, v.z, u.x, u.z, sr[t]);
+        df_mac(v.y, v.w, u.y, u.w, sr[t]);
+        df_mac(v.x, v.z, u.y, u.w, si[t]);
+        df_mac(-v.y, -v.w, u.x, u.z, si[t]);
+        if (pre) {
+          df_mac(v.x, v.z, w.x, w.z, tr[t]);
+          df_mac(v.y, v.w, w.y, w.w, tr[t]);
+          df_mac(v.x, v.z, w.y, w.w, ti[t]);
+          df_mac(-v.y, -v.w, w.x, w.z, ti[t]);
+        }
       }
     }
   }
 #pragma unroll
   for (int t = 0; t < kGD; ++t) {
-    DF r = df_wsum(ar[t]), q = df_wsum(ai[t]);
+    DF r = df_wsum(sr[t]), q = df_wsum(si[t]);
     if (lane == 0) red[warp][t] = make_float4(r.h, r.l, q.h, q.l);
+    if (pre) {
+      r = df_wsum(tr[t]);
+      q = df_wsum(ti[t]);
+      if (lane == 0) red[warp][kGD + t] = make_float4(r.h, r.l, q.h, q.l);
+    }
   }
   __syncthreads();
-  if (threadIdx.x < ng) {   // block partial, still double-float (converted by k_reduce_h)
+  const int nout = pre ? 2 * kGD : kGD;
+  if (threadIdx.x < nout && (threadIdx.x % kGD) < ng) {
     DF r{0.f, 0.f}, q{0.f, 0.f};
     for (int wi2 = 0; wi2 < kT / 32; ++wi2) {
       const float4 x = red[wi2][threadIdx.x];
       r = df_add(r, DF{x.x, x.y});
       q = df_add(q, DF{x.z, x.w});
     }
-    part4[(int64_t)(i0 + threadIdx.x) * PS + blockIdx.x] = make_float4(r.h, r.l, q.h, q.l);
+    const int t = threadIdx.x % kGD;
+    const int64_t row = threadIdx.x < kGD ? kb_row_s(i0 + t) : kb_row_t(m, i0 + t);
+    part4[row * PS + blockIdx.x] = make_float4(r.h, r.l, q.h, q.l);
   }
 }
 
-// Deterministic reduction of the per-block partials of entry i by one warp (lanes
+// Deterministic reduction of the per-block partials of row r by one warp (lanes
 // stride over the blocks, then a fixed shuffle tree).
-__device__ __forceinline__ double2 sum_partials(const KrylovBufs& kb, int i, int lane, int nrows) {
+__device__ __forceinline__ double2 sum_partials(const KrylovBufs& kb, int64_t r, int lane, int nrows) {
   double2 s = make_double2(0.0, 0.0);
-  const double2* row = kb.part + (int64_t)i * kb.pstride;
+  const double2* row = kb.part + r * kb.pstride;
   for (int b = lane; b < nrows; b += 32) s = cadd(s, row[b]);
   return wsum(s);
 }
 
-// h = sum of the inner-product partials (double-float, reduced in double-float and
-// converted once); hp = this pass's h, hcol accumulates over the passes.
-__global__ void __launch_bounds__(kT) k_reduce_h(KrylovBufs kb, double2* hp, int second) {
+// s_i, t_i = sums of the double-float block partials (reduced in double-float, converted once).
+// One warp per row; rows 0..j are s, then (when the step applied the preconditioner) t.
+__global__ void __launch_bounds__(kT) k_reduce2(KrylovBufs kb) {
   KState* st = kb.st;
-  if (!st->active || (second && !st->reorth)) return;
+  if (!st->active) return;
   const int j = st->j, m = st->m;
+  const int nrow = st->pre ? 2 * (j + 1) : j + 1;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
   const float4* p4 = reinterpret_cast<const float4*>(kb.part);
-  for (int i = blockIdx.x * nw + warp; i <= j; i += gridDim.x * nw) {
-    DF r{0.f, 0.f}, q{0.f, 0.f};
-    const float4* row = p4 + (int64_t)i * kb.pstride;
+  for (int q = blockIdx.x * nw + warp; q < nrow; q += gridDim.x * nw) {
+    const bool is_t = q > j;
+    const int i = is_t ? q - (j + 1) : q;
+    DF r{0.f, 0.f}, c{0.f, 0.f};
+    const float4* row = p4 + (is_t ? kb_row_t(m, i) : kb_row_s(i)) * kb.pstride;
     for (int b = lane; b < kb.nblk_dots; b += 32) {
       const float4 x = row[b];
       r = df_add(r, DF{x.x, x.y});
-      q = df_add(q, DF{x.z, x.w});
+      c = df_add(c, DF{x.z, x.w});
     }
     r = df_wsum(r);
-    q = df_wsum(q);
-    if (lane == 0) {
-      double2 s2 = make_double2(df_val(r), df_val(q));
-      hp[i] = s2;
-      kb.hcol[i] = second ? cadd(kb.hcol[i], s2) : s2;
-    }
-  }
-  if (!second && blockIdx.x == 0 && warp == 0) {
-    double2 s2 = sum_partials(kb, m + 1, lane, kb.nblk_dots);   // ||w||^2 (FP64)
-    if (lane == 0) st->wn0 = sqrt(s2.x);
-  }
-}
-
-// w -= sum_i hp[i] V[i] (sum in double-float, subtraction in FP64);  partial ||w||^2.
-// A warp takes 32 entries: its two half-warps sum over the two halves of the basis for two
-// entries per lane (four loads in flight per basis vector and lane pair), meet with one
-// shuffle, and then every lane finishes one entry (the FP64 tail uses all 32 lanes).
-__global__ void __launch_bounds__(kT) k_update(KrylovBufs kb, const double2* hp, int second) {
-  KState* st = kb.st;
-  if (!st->active || (second && !st->reorth)) return;
-  const int j = st->j, m = st->m;
-  const int64_t N = kb.N, ld = kb.ldN;
-  extern __shared__ float4 hs4[];   // per coefficient: (re.h, re.l, im.h, im.l)
-  for (int i = threadIdx.x; i <= j; i += blockDim.x) {
-    DF r = df_split(hp[i].x), q = df_split(hp[i].y);
-    hs4[i] = make_float4(r.h, r.l, q.h, q.l);
-  }
-  __syncthreads();
-  const int lane = threadIdx.x & 31, half = lane >> 4;
-  const int split = (j + 2) / 2;   // vectors [0, split) and [split, j]
-  const int ib = half ? split : 0, ie = half ? j + 1 : split;
-  double s2 = 0.0;
-  const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;   // warps in the grid
-  for (int64_t wg = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5; wg * 32 < N; wg += nw) {
-    const int64_t na = wg * 32 + (lane & 15), nb2 = na + 16;   // this lane's two entries
-    DF ar{0.f, 0.f}, ai{0.f, 0.f}, br{0.f, 0.f}, bi{0.f, 0.f};
-    const bool va = na < N, vb = nb2 < N;
-    const float4* pa = kb.Vs + (va ? na : 0);
-    const float4* pb = kb.Vs + (vb ? nb2 : 0);
-#pragma unroll 4
-    for (int i = ib; i < ie; ++i) {
-      const float4 h = hs4[i];                          // (re.h, re.l, im.h, im.l)
-      const float4 v = pa[(int64_t)i * ld], u = pb[(int64_t)i * ld];   // (hr, hi, lr, li)
-      // h v = (hr vr - hi vi) + i (hr vi + hi vr)
-      df_mac(h.x, h.y, v.x, v.z, ar);
-      df_mac(-h.z, -h.w, v.y, v.w, ar);
-      df_mac(h.x, h.y, v.y, v.w, ai);
-      df_mac(h.z, h.w, v.x, v.z, ai);
-      df_mac(h.x, h.y, u.x, u.z, br);
-      df_mac(-h.z, -h.w, u.y, u.w, br);
-      df_mac(h.x, h.y, u.y, u.w, bi);
-      df_mac(h.z, h.w, u.x, u.z, bi);
-    }
-    auto xsum = [](DF v) {
-      return df_add(v, DF{__shfl_xor_sync(0xffffffffu, v.h, 16), __shfl_xor_sync(0xffffffffu, v.l, 16)});
-    };
-    ar = xsum(ar);
-    ai = xsum(ai);
-    br = xsum(br);
-    bi = xsum(bi);
-    // lanes 0-15 finish entry na, lanes 16-31 entry nb2 (= wg * 32 + lane in both cases)
-    const int64_t n = wg * 32 + lane;
-    const DF cr = half ? br : ar, ci = half ? bi : ai;
-    if (n < N) {
-      double2 w = kb.W[n];
-      w.x -= df_val(cr);
-      w.y -= df_val(ci);
-      kb.W[n] = w;
-      DF r = df_split(w.x), q = df_split(w.y);
-      kb.Ws[n] = make_float4(r.h, q.h, r.l, q.l);
-      s2 = fma(w.x, w.x, fma(w.y, w.y, s2));
-    }
-  }
-  __shared__ double rn[kT / 32];
-  s2 = wsum(s2);
-  if ((threadIdx.x & 31) == 0) rn[threadIdx.x >> 5] = s2;
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    double t = 0.0;
-    for (int i = 0; i < kT / 32; ++i) t += rn[i];
-    kb.part[(int64_t)(m + 1) * kb.pstride + blockIdx.x] = make_double2(t, 0.0);
-  }
-}
-
-__global__ void k_reduce_norm(KrylovBufs kb, int second) {
-  KState* st = kb.st;
-  if (!st->active || (second && !st->reorth)) return;
-  const int m = st->m;
-  double2 s2 = sum_partials(kb, m + 1, threadIdx.x & 31, kb.nblk_upd);
-  if (threadIdx.x != 0) return;
-  double wn = sqrt(s2.x);
-  st->wn = wn;
-  if (!second) st->reorth = (wn < 0.70710678118654752 * st->wn0) ? 1 : 0;
-}
-
-// v_{j+1} = w / ||w||: stored split (hi + lo) in the basis and in complex128 for the preconditioner
-__device__ __forceinline__ void store_basis(const KrylovBufs& kb, int col, int64_t n, double2 v) {
-  DF r = df_split(v.x), q = df_split(v.y);
-  kb.Vs[(int64_t)col * kb.ldN + n] = make_float4(r.h, q.h, r.l, q.l);
-  kb.vj[n] = v;
-}
-
-__global__ void __launch_bounds__(kT) k_normalize(KrylovBufs kb) {
-  KState* st = kb.st;
-  if (!st->active) return;
-  const double wn = st->wn;
-  if (!(wn > 1e-14 * st->beta) || !isfinite(wn)) return;   // breakdown: handled by k_givens
-  const double inv = 1.0 / wn;
-  const int col = st->j + 1;
-  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-  for (int64_t n = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; n < kb.N; n += stride) {
-    double2 a = kb.W[n];
-    store_basis(kb, col, n, make_double2(a.x * inv, a.y * inv));
+    c = df_wsum(c);
+    if (lane == 0) (is_t ? kb.tp : kb.hp)[i] = make_double2(df_val(r), df_val(c));
   }
 }
 
@@ -286,27 +181,24 @@ __device__ __forceinline__ double2 shfl2(double2 v, int src) {
   return make_double2(__shfl_sync(0xffffffffu, v.x, src), __shfl_sync(0xffffffffu, v.y, src));
 }
 
-// Givens step for column j (one warp). The previous rotations turn the new column
-// h = (h_0..h_j, h_{j+1} = ||w||) into  col_i = c_i u_i + s_i h_{i+1}  with the carried
-// value  u_0 = h_0,  u_{i+1} = -conj(s_i) u_i + c_i h_{i+1}  -- an affine recurrence in u.
-// Each lane composes the maps of a contiguous chunk of rotations, a warp scan composes
-// the chunks ((a2, b2) o (a1, b1) = (a2 a1, a2 b1 + b2)), and each lane then replays its
-// chunk from its exclusive prefix. The new rotation [c s; -conj(s) c] zeroes h_{j+1}
-// against u_j; the residual estimate is |g_{j+1}| / ||F||.
-__global__ void __launch_bounds__(32) k_givens(KrylovBufs kb) {
-  KState* st = kb.st;
-  if (!st->active) return;
-  const int j = st->j, m = st->m, lane = threadIdx.x;
-  const double wn = st->wn;
-  double2* Hc = kb.H + (int64_t)j * (m + 1);
-  const int per = (j + 31) / 32;
-  const int i0 = min(j, lane * per), i1 = min(j, i0 + per);
+// Givens step for the finished column c (one warp). The previous rotations turn the column
+// h = (h_0..h_c, h_{c+1} = hsub) into  col_i = c_i u_i + s_i h_{i+1}  with the carried value
+// u_0 = h_0,  u_{i+1} = -conj(s_i) u_i + c_i h_{i+1}  -- an affine recurrence in u. Each lane
+// composes the maps of a contiguous chunk of rotations, a warp scan composes the chunks
+// ((a2, b2) o (a1, b1) = (a2 a1, a2 b1 + b2)), and each lane then replays its chunk from its
+// exclusive prefix. The new rotation [c s; -conj(s) c] zeroes h_{c+1} against u_c; the
+// residual estimate is |g_{c+1}| / ||F||. Returns (on every lane) whether the solve stops.
+__device__ int givens_column(const KrylovBufs& kb, KState* st, int c, const double2* hf, double hsub, int lane) {
+  const int m = st->m;
+  double2* Hc = kb.H + (int64_t)c * (m + 1);
+  const int per = (c + 31) / 32;
+  const int i0 = min(c, lane * per), i1 = min(c, i0 + per);
   double2 A = make_double2(1.0, 0.0), Bm = make_double2(0.0, 0.0);
   for (int i = i0; i < i1; ++i) {
     const double2 al = make_double2(-kb.sn[i].x, kb.sn[i].y);   // -conj(s_i)
-    const double c = kb.cs[i];
-    const double2 hn = kb.hcol[i + 1];
-    Bm = cfma(al, Bm, make_double2(c * hn.x, c * hn.y));
+    const double cc = kb.cs[i];
+    const double2 hn = hf[i + 1];
+    Bm = cfma(al, Bm, make_double2(cc * hn.x, cc * hn.y));
     A = cmul(al, A);
   }
 #pragma unroll
@@ -322,50 +214,226 @@ __global__ void __launch_bounds__(32) k_givens(KrylovBufs kb) {
     Ae = make_double2(1.0, 0.0);
     Be = make_double2(0.0, 0.0);
   }
-  double2 u = cfma(Ae, kb.hcol[0], Be);   // u at the start of this lane's chunk
+  double2 u = cfma(Ae, hf[0], Be);   // u at the start of this lane's chunk
   for (int i = i0; i < i1; ++i) {
     const double2 sv = kb.sn[i];
-    const double c = kb.cs[i];
-    const double2 hn = kb.hcol[i + 1];
-    Hc[i] = cfma(sv, hn, make_double2(c * u.x, c * u.y));
-    u = cfma(make_double2(-sv.x, sv.y), u, make_double2(c * hn.x, c * hn.y));
+    const double cc = kb.cs[i];
+    const double2 hn = hf[i + 1];
+    Hc[i] = cfma(sv, hn, make_double2(cc * u.x, cc * u.y));
+    u = cfma(make_double2(-sv.x, sv.y), u, make_double2(cc * hn.x, cc * hn.y));
   }
-  // u_j sits with the lane that replayed rotation j-1 (lane 0 when j == 0)
-  const int owner = j == 0 ? 0 : (j - 1) / per;
+  // u_c sits with the lane that replayed rotation c-1 (lane 0 when c == 0)
+  const int owner = c == 0 ? 0 : (c - 1) / per;
   u = shfl2(u, owner);
-  if (lane != 0) return;
-  // new rotation zeroing (u_j, wn): [c s; -conj(s) c] [a; b] = [r; 0]
-  const double2 a = u, b = make_double2(wn, 0.0);
-  const double aa = hypot(a.x, a.y), bb = hypot(b.x, b.y);
-  double c;
-  double2 sv, r;
-  if (bb == 0.0) {
-    c = 1.0; sv = make_double2(0.0, 0.0); r = a;
-  } else if (aa == 0.0) {
-    c = 0.0; sv = make_double2(1.0, 0.0); r = b;
-  } else {
-    const double nu = hypot(aa, bb);
-    const double2 ph = make_double2(a.x / aa, a.y / aa);
-    c = aa / nu;
-    sv = cmul(ph, make_double2(b.x / nu, -b.y / nu));
-    r = make_double2(ph.x * nu, ph.y * nu);
+  int stop = 0;
+  if (lane == 0) {
+    // new rotation zeroing (u_c, hsub): [c s; -conj(s) c] [a; b] = [r; 0]
+    const double2 a = u, b = make_double2(hsub, 0.0);
+    const double aa = hypot(a.x, a.y), bb = hypot(b.x, b.y);
+    double cr;
+    double2 sv, r;
+    if (bb == 0.0) {
+      cr = 1.0; sv = make_double2(0.0, 0.0); r = a;
+    } else if (aa == 0.0) {
+      cr = 0.0; sv = make_double2(1.0, 0.0); r = b;
+    } else {
+      const double nu = hypot(aa, bb);
+      const double2 ph = make_double2(a.x / aa, a.y / aa);
+      cr = aa / nu;
+      sv = cmul(ph, make_double2(b.x / nu, -b.y / nu));
+      r = make_double2(ph.x * nu, ph.y * nu);
+    }
+    kb.cs[c] = cr;
+    kb.sn[c] = sv;
+    Hc[c] = r;
+    Hc[c + 1] = make_double2(0.0, 0.0);
+    const double2 gc = kb.g[c];
+    const double2 gc1 = cmul(make_double2(-sv.x, sv.y), gc);
+    kb.g[c + 1] = gc1;
+    kb.g[c] = make_double2(cr * gc.x, cr * gc.y);
+    const double est = hypot(gc1.x, gc1.y) / st->nF;
+    st->est = est;
+    st->total += 1;
+    if (!isfinite(est) || !isfinite(hsub)) st->nonfinite = 1;
+    if (!(hsub > 1e-14 * st->beta)) st->breakdown = 1;
+    if (est <= st->tol) st->converged = 1;
+    stop = st->converged || st->breakdown || st->nonfinite;
   }
-  kb.cs[j] = c;
-  kb.sn[j] = sv;
-  Hc[j] = r;
-  Hc[j + 1] = make_double2(0.0, 0.0);
-  const double2 gj = kb.g[j];
-  const double2 gj1 = cmul(make_double2(-sv.x, sv.y), gj);
-  kb.g[j + 1] = gj1;
-  kb.g[j] = make_double2(c * gj.x, c * gj.y);
-  const double est = hypot(gj1.x, gj1.y) / st->nF;
-  st->est = est;
+  return __shfl_sync(0xffffffffu, stop, 0);
+}
+
+// Coefficients of the step (one warp), lagged classical Gram-Schmidt with
+// reorthogonalisation (Swirydowicz, Langou, Ananthan, Yang, Thomas 2020, DCGS2): the
+// vector u_j in slot j was orthogonalised once; here it is corrected,
+//   v_j = (u_j - sum_{i<j} s_i v_i) / rho,  rho^2 = ||u_j||^2 - sum_{i<j} |s_i|^2,
+// which finishes column j-1 of the Hessenberg matrix (the previous step wrote
+// A z_{j-1} = sum h_i v_i + sigma u_j):  h_i += sigma s_i (i < j), h_{j,j-1} = sigma rho,
+// followed by its Givens step and convergence test. The new column j starts as
+//   h_i = t_i (i < j),  h_jj = <v_j, w> = (t_j - sum_{i<j} conj(s_i) t_i) / rho.
+__global__ void __launch_bounds__(32) k_coef(KrylovBufs kb) {
+  KState* st = kb.st;
+  if (!st->active) return;
+  const int j = st->j, lane = threadIdx.x;
+  const bool pre = st->pre != 0;
+  const double2* s = kb.hp;
+  const double2* t = kb.tp;
+  double a = 0.0;
+  for (int i = lane; i < j; i += 32) a = fma(s[i].x, s[i].x, fma(s[i].y, s[i].y, a));
+  a = wsum(a);
+  const double rho2 = s[j].x - a;
+  const double rho = rho2 > 0.0 ? sqrt(rho2) : 0.0;
+  int stop = 0;
+  if (j == 0) {
+    // r = beta u_0 = beta rho v_0
+    if (lane == 0) kb.g[0] = make_double2(st->beta * rho, 0.0);
+  } else {
+    const double sig = st->sig;
+    for (int i = lane; i < j; i += 32) kb.hfin[i] = cfma(make_double2(sig, 0.0), s[i], kb.hcol[i]);
+    __syncwarp();
+    stop = givens_column(kb, st, j - 1, kb.hfin, sig * rho, lane);
+  }
+  if (!pre || !(rho > 0.0)) stop = 1;
+  if (stop) {
+    if (lane == 0) {
+      if (pre && !(rho > 0.0)) st->breakdown = 1;
+      st->active = 0;
+      st->pre = 0;
+    }
+    return;   // j columns are finished
+  }
+  double2 d = make_double2(0.0, 0.0);
+  for (int i = lane; i < j; i += 32) d = cfma(make_double2(s[i].x, -s[i].y), t[i], d);
+  d = wsum(d);
+  const double irho = 1.0 / rho;
+  const double2 hjj = make_double2((t[j].x - d.x) * irho, (t[j].y - d.y) * irho);
+  for (int i = lane; i < j; i += 32) kb.hcol[i] = t[i];
+  if (lane == 0) {
+    kb.hcol[j] = hjj;
+    st->hjj = hjj;
+    st->irho = irho;
+  }
+}
+
+// One sweep over V[0..j-1] for both corrections of the step:
+//   v_j = (u_j - sum s_i v_i) / rho   (written into slot j)
+//   w  <- w - sum t_i v_i - h_jj v_j   (complex128, FP64 subtraction), partial ||w||^2.
+// A warp takes 32 entries: its two half-warps sum over the two halves of the basis for two
+// entries per lane, meet with one shuffle, and then every lane finishes one entry.
+__global__ void __launch_bounds__(kT) k_update2(KrylovBufs kb) {
+  KState* st = kb.st;
+  if (!st->active) return;
+  const int j = st->j, m = st->m;
+  const int64_t N = kb.N, ld = kb.ldN;
+  extern __shared__ float4 hs4[];   // [0, j): s_i, [j, 2j): t_i as (re.h, re.l, im.h, im.l)
+  for (int i = threadIdx.x; i < 2 * j; i += blockDim.x) {
+    const double2 c = i < j ? kb.hp[i] : kb.tp[i - j];
+    DF r = df_split(c.x), q = df_split(c.y);
+    hs4[i] = make_float4(r.h, r.l, q.h, q.l);
+  }
+  const DF irho = df_split(st->irho);
+  const double2 hjj_d = st->hjj;
+  const float4 hjj = dfc_from(hjj_d);
+  __syncthreads();
+  const int lane = threadIdx.x & 31, half = lane >> 4;
+  const int split = (j + 1) / 2;   // slots [0, split) and [split, j)
+  const int ib = half ? split : 0, ie = half ? j : split;
+  double s2 = 0.0;
+  const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  for (int64_t wg = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5; wg * 32 < N; wg += nw) {
+    const int64_t na = wg * 32 + (lane & 15), nb2 = na + 16;
+    const bool va = na < N, vb = nb2 < N;
+    const float4* pa = kb.Vs + (va ? na : 0);
+    const float4* pb = kb.Vs + (vb ? nb2 : 0);
+    DFC_ACC ua{}, ub{}, wa{}, wb{};
+#pragma unroll 2
+    for (int i = ib; i < ie; ++i) {
+      const float4 hs = hs4[i], ht = hs4[j + i];   // (re.h, re.l, im.h, im.l)
+      const float4 v = pa[(int64_t)i * ld], u = pb[(int64_t)i * ld];
+      // c x = (cr xr - ci xi) + i (cr xi + ci xr), x in (hr, hi, lr, li) layout
+      df_mac(hs.x, hs.y, v.x, v.z, ua.re);
+      df_mac(-hs.z, -hs.w, v.y, v.w, ua.re);
+      df_mac(hs.x, hs.y, v.y, v.w, ua.im);
+      df_mac(hs.z, hs.w, v.x, v.z, ua.im);
+      df_mac(hs.x, hs.y, u.x, u.z, ub.re);
+      df_mac(-hs.z, -hs.w, u.y, u.w, ub.re);
+      df_mac(hs.x, hs.y, u.y, u.w, ub.im);
+      df_mac(hs.z, hs.w, u.x, u.z, ub.im);
+      df_mac(ht.x, ht.y, v.x, v.z, wa.re);
+      df_mac(-ht.z, -ht.w, v.y, v.w, wa.re);
+      df_mac(ht.x, ht.y, v.y, v.w, wa.im);
+      df_mac(ht.z, ht.w, v.x, v.z, wa.im);
+      df_mac(ht.x, ht.y, u.x, u.z, wb.re);
+      df_mac(-ht.z, -ht.w, u.y, u.w, wb.re);
+      df_mac(ht.x, ht.y, u.y, u.w, wb.im);
+      df_mac(ht.z, ht.w, u.x, u.z, wb.im);
+    }
+    auto xsum = [](DF v) {
+      return df_add(v, DF{__shfl_xor_sync(0xffffffffu, v.h, 16), __shfl_xor_sync(0xffffffffu, v.l, 16)});
+    };
+    ua.re = xsum(ua.re); ua.im = xsum(ua.im); ub.re = xsum(ub.re); ub.im = xsum(ub.im);
+    wa.re = xsum(wa.re); wa.im = xsum(wa.im); wb.re = xsum(wb.re); wb.im = xsum(wb.im);
+    // lanes 0-15 finish entry na, lanes 16-31 entry nb2 (= wg * 32 + lane in both cases)
+    const int64_t n = wg * 32 + lane;
+    if (n < N) {
+      const DFC_ACC cu = half ? ub : ua;
+      DFC_ACC cw = half ? wb : wa;
+      float4* slot = kb.Vs + (int64_t)j * ld + n;
+      const float4 d = dfc_sub(*slot, dfc_fin(cu));
+      const float4 v = dfc_make(df_mul(dfc_re(d), irho), df_mul(dfc_im(d), irho));
+      *slot = v;
+      dfc_mac(hjj, v, cw);
+      const float4 c = dfc_fin(cw);
+      double2 w = kb.W[n];
+      w.x -= df_val(dfc_re(c));
+      w.y -= df_val(dfc_im(c));
+      kb.W[n] = w;
+      s2 = fma(w.x, w.x, fma(w.y, w.y, s2));
+    }
+  }
+  __shared__ double rn[kT / 32];
+  s2 = wsum(s2);
+  if ((threadIdx.x & 31) == 0) rn[threadIdx.x >> 5] = s2;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double t = 0.0;
+    for (int i = 0; i < kT / 32; ++i) t += rn[i];
+    kb.part[kb_row_norm(m) * kb.pstride + blockIdx.x] = make_double2(t, 0.0);
+  }
+}
+
+// sigma_j = ||w||: the next step's u_{j+1} = w / sigma_j. Decides whether the next step
+// applies the preconditioner (room left in the cycle and in maxit) or only finishes column j.
+__global__ void k_reduce_norm2(KrylovBufs kb) {
+  KState* st = kb.st;
+  if (!st->active) return;
+  const int j = st->j, m = st->m;
+  double2 s2 = sum_partials(kb, kb_row_norm(m), threadIdx.x & 31, kb.nblk_upd);
+  if (threadIdx.x != 0) return;
+  const double sig = sqrt(s2.x);
+  st->sig = sig;
+  st->pre = (j + 1 < m && st->total + 2 <= st->maxit && sig > 1e-14 * st->beta && isfinite(sig)) ? 1 : 0;
   st->j = j + 1;
-  st->total += 1;
-  if (!isfinite(est) || !isfinite(wn)) st->nonfinite = 1;
-  if (!(wn > 1e-14 * st->beta)) st->breakdown = 1;
-  if (est <= st->tol) st->converged = 1;
-  if (st->converged || st->breakdown || st->nonfinite || st->j >= m || st->total >= st->maxit) st->active = 0;
+}
+
+// v_j slot of the basis stored split (hi + lo) and in complex128 for the preconditioner
+__device__ __forceinline__ void store_basis(const KrylovBufs& kb, int col, int64_t n, double2 v) {
+  DF r = df_split(v.x), q = df_split(v.y);
+  kb.Vs[(int64_t)col * kb.ldN + n] = make_float4(r.h, q.h, r.l, q.l);
+  kb.vj[n] = v;
+}
+
+// u_{j} = w / sigma (zero when w vanished: the next step then finds rho = 0)
+__global__ void __launch_bounds__(kT) k_normalize2(KrylovBufs kb) {
+  KState* st = kb.st;
+  if (!st->active) return;
+  const double sig = st->sig;
+  const double inv = sig > 1e-14 * st->beta ? 1.0 / sig : (sig == sig ? 0.0 : sig);
+  const int col = st->j;
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t n = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; n < kb.N; n += stride) {
+    double2 a = kb.W[n];
+    store_basis(kb, col, n, make_double2(a.x * inv, a.y * inv));
+  }
 }
 
 // ||v||^2 partials / final
@@ -383,13 +451,13 @@ __global__ void __launch_bounds__(kT) k_norm_part(KrylovBufs kb, const double2* 
   if (threadIdx.x == 0) {
     double t = 0.0;
     for (int i = 0; i < kT / 32; ++i) t += rn[i];
-    kb.part[(int64_t)(kb.st->m + 1) * kb.pstride + blockIdx.x] = make_double2(t, 0.0);
+    kb.part[kb_row_norm(kb.st->m) * kb.pstride + blockIdx.x] = make_double2(t, 0.0);
   }
 }
 __global__ void k_norm_fin(KrylovBufs kb, int which) {
   KState* st = kb.st;
   const int m = st->m;
-  double2 s2 = sum_partials(kb, m + 1, threadIdx.x & 31, kb.nblk);
+  double2 s2 = sum_partials(kb, kb_row_norm(m), threadIdx.x & 31, kb.nblk);
   if (threadIdx.x != 0) return;
   double nrm = sqrt(s2.x);
   if (which == 0) {
@@ -418,9 +486,10 @@ __global__ void __launch_bounds__(kT) k_cycle_start(KrylovBufs kb, const double2
     if (threadIdx.x == 0) {
       st->j = 0;
       st->active = ok ? 1 : 0;
+      st->pre = ok && st->m >= 1 && st->total + 1 <= st->maxit ? 1 : 0;
+      st->sig = 0.0;
       st->converged = 0;
       st->breakdown = 0;
-      st->reorth = 0;
       if (!isfinite(beta)) st->nonfinite = 1;
     }
   }
@@ -466,18 +535,16 @@ __global__ void __launch_bounds__(kT) k_update_x(KrylovBufs kb, double2* x) {
 
 }  // namespace
 
-void launch_cgs_pass(const KrylovBufs& kb, bool second, cudaStream_t s) {
-  int sec = second ? 1 : 0;
-  if (!second) k_split_w<<<kb.nblk, kT, 0, s>>>(kb);
-  k_dots<<<dim3(kb.nblk_dots, (kb.m + 1 + kGD - 1) / kGD), kT, 0, s>>>(kb, sec);
-  k_reduce_h<<<(kb.m + 1 + kT / 32 - 1) / (kT / 32), kT, 0, s>>>(kb, kb.hp, sec);
-  k_update<<<kb.nblk_upd, kT, sizeof(float4) * 513, s>>>(kb, kb.hp, sec);
-  k_reduce_norm<<<1, 32, 0, s>>>(kb, sec);
+void launch_arnoldi(const KrylovBufs& kb, cudaStream_t s, cudaEvent_t mid) {
+  k_split_w<<<kb.nblk, kT, 0, s>>>(kb);
+  k_dots2<<<dim3(kb.nblk_dots, (kb.m + 1 + kGD - 1) / kGD), kT, 0, s>>>(kb);
+  k_reduce2<<<(2 * (kb.m + 1) + kT / 32 - 1) / (kT / 32), kT, 0, s>>>(kb);
+  k_coef<<<1, 32, 0, s>>>(kb);
+  if (mid) cudaEventRecord(mid, s);
+  k_update2<<<kb.nblk_upd, kT, sizeof(float4) * 2 * kb.m, s>>>(kb);
+  k_reduce_norm2<<<1, 32, 0, s>>>(kb);
+  k_normalize2<<<kb.nblk, kT, 0, s>>>(kb);
 }
-
-void launch_normalize(const KrylovBufs& kb, cudaStream_t s) { k_normalize<<<kb.nblk, kT, 0, s>>>(kb); }
-
-void launch_givens(const KrylovBufs& kb, cudaStream_t s) { k_givens<<<1, 32, 0, s>>>(kb); }
 
 void launch_cycle_start(const KrylovBufs& kb, const double2* r, cudaStream_t s) {
   k_cycle_start<<<kb.nblk, kT, 0, s>>>(kb, r);
