@@ -46,6 +46,8 @@ template <typename T> struct Prec {
   c2<T>* xmid = nullptr;   // middle-block exchange of the twisted coarse solve (2 x ldb)
   int* xflag = nullptr;    // its ready flags (one per row of each chain)
   unsigned* gbar = nullptr;   // grid barrier of the whole-grid coarse solve
+  SegBufs<T> seg{};           // segmented solve workspaces (plan.seg)
+  const SegBufs<T>* segp() const { return plan.seg ? &seg : nullptr; }
 };
 
 }  // namespace
@@ -248,7 +250,7 @@ void enqueue_vcycle(helm_ctx* h, VecSel<const double2> f, VecSel<double2> z, con
   launch_restrict<T>(P, h->L, p.r, p.rc, active, s);
   if (prof) cudaEventRecord(prof->ev[ev0 + 1], s);
   launch_coarse_solve<T>(p.plan, p.Dinv, p.Lm, p.Up, h->L, p.rc, p.uc, p.xmid, p.xflag, p.gbar, h->err, active,
-                         h->nsm, s);
+                         h->nsm, s, p.segp());
   if (prof) cudaEventRecord(prof->ev[ev0 + 2], s);
   launch_prolong_add<T>(P, h->L, p.uc, cur, active, s);
   for (int it = 0; it < nu; ++it) {   // postsmoothing
@@ -508,7 +510,8 @@ size_t estimate_bytes(int dim, int order, int n, int precision, int restart) {
   const int64_t v = precision == HELM_MIXED ? 8 : 16;
   const int64_t m = restart, ldN = (N + 31) & ~int64_t(31), nblk = std::max<int64_t>(1, (N + 255) / 256);
   const int64_t prec = v * (4 * N + 2 * nb * ldb + 2 * ldb) + 4 * 2 * ldb + 64;
-  const int64_t factor = v * 3 * blk * nb;                        // Dinv, Lm, Up
+  // Dinv, Lm, Up; the mixed form's segmented solve adds two product sets and one vector
+  const int64_t factor = v * 3 * blk * nb + (precision == HELM_MIXED ? 8 * (2 * blk * nb + nb * ldb) : 0);
   const int64_t krylov = 16 * ldN * (m + 1) + 16 * 3 * ldN + 16 * ldN * m + 16 * ldN +
                          16 * std::max<int64_t>(nblk, (N + 255) / 256) * kb_rows((int)m) + 16 * (m + 2) * (m + 6);
   const int64_t tables = 1 << 20;
@@ -674,6 +677,18 @@ static int setup_impl(helm_ctx* h) {
     } else {
       convert_factor_df(reinterpret_cast<const float4*>(D64), p.Dinv, blk * L.nb, s);
       coarse_couple_df(reinterpret_cast<const float4*>(D64), p.Lm, p.Up, Acv, L, h->nsm, s);
+      if (p.plan.seg) {
+        float2 *yb = nullptr, *Pf = nullptr, *Pb = nullptr;
+        if (h->alloc(&yb, sizeof(float2) * (size_t)L.nb * L.ldb) != cudaSuccess ||
+            h->alloc(&Pf, sizeof(float2) * blk * L.nb) != cudaSuccess ||
+            h->alloc(&Pb, sizeof(float2) * blk * L.nb) != cudaSuccess) {
+          rc = HELM_ENOMEM;
+        } else {
+          p.seg = SegBufs<float>{yb, Pf, Pb};
+          coarse_seg_products(p.Lm, p.Up, Pf, Pb, L, p.plan, s);
+          h->setup_kernels += coarse_seg_launches(L, p.plan);
+        }
+      }
     }
   } else if (rc == HELM_OK) {
     Prec<double>& p = h->p64;
@@ -935,7 +950,7 @@ int helm_coarse_solve(helm_t h, const void* rc_nat, void* uc_nat) {
     Prec<float>& p = h->p32;
     launch_coarse_pack<double2, float2>(h->gc, h->L, (const double2*)rc_nat, p.rc, h->s);
     launch_coarse_solve<float>(p.plan, p.Dinv, p.Lm, p.Up, h->L, p.rc, p.uc, p.xmid, p.xflag, p.gbar, h->err,
-                               nullptr, h->nsm, h->s);
+                               nullptr, h->nsm, h->s, p.segp());
     launch_coarse_unpack<float2, double2>(h->gc, h->L, p.uc, (double2*)uc_nat, h->s);
   } else {
     Prec<double>& p = h->p64;
@@ -1021,7 +1036,7 @@ int coarse_solve_noalloc(helm_t h, const double2* rc_nat, double2* uc_nat) {
   CK(cudaMemsetAsync(h->err, 0, sizeof(int), h->s));   // the error word must start at zero
   launch_coarse_pack<double2, V>(h->gc, h->L, rc_nat, pad_rc, h->s);   // writes every padded entry
   launch_coarse_solve<T>(p.plan, p.Dinv, p.Lm, p.Up, h->L, pad_rc, pad_uc, p.xmid, p.xflag, p.gbar, h->err,
-                         nullptr, h->nsm, h->s);
+                         nullptr, h->nsm, h->s, p.segp());
   launch_coarse_unpack<V, double2>(h->gc, h->L, pad_uc, uc_nat, h->s);
   CK(cudaGetLastError());
   CK(cudaStreamSynchronize(h->s));

@@ -682,6 +682,7 @@ SolveGeom solve_geometry(const CoarseLayout& L, int CS, int CW, int S) {
 }
 
 constexpr int kRPW = 4;          // max rows of the CTA slice per consumer warp (registers)
+constexpr int kSegMaxLdb = 1040;   // block row length up to which the segmented solve applies
 constexpr int kSolveMaxWarps = 18;   // consumer warps + 1 producer warp
 
 // mbarrier arrive (release, CTA scope)
@@ -914,10 +915,352 @@ __global__ void __launch_bounds__(256) k_coarse_solve_grid(const c2<T>* __restri
   }
 }
 
+// ---------------------------------------------------------------------------
+// Segmented triangular solves of the twisted factorisation (mid = nb / 2).
+// Each sweep of a chain is a first-order block recurrence along a path of blocks,
+// J(q) = J0 + step q:
+//   forward, top     J = 0, 1, .., mid-1         y_q = p_q - Lm[J] y_{q-1}
+//   forward, bottom  J = nb-1, .., mid+1         y_q = p_q - Up[J] y_{q-1}
+//   middle           x_m = p_m - Lm[m] y_{m-1} - Up[m] y_{m+1}
+//   backward, top    J = mid, mid-1, .., 0       x_q = y_q - Up[J] x_{q-1}   (x_0 = x_m)
+//   backward, bottom J = mid, mid+1, .., nb-1    x_q = y_q - Lm[J] x_{q-1}   (x_0 = x_m)
+// A path is cut into segments of Ls positions. With the segment products
+//   P[J(kLs)] = C_{kLs},  P[J(q)] = -C_q P[J(q-1)]   (q inside segment k >= 1),
+// the solution inside segment k is  z_q = w_q - P[J(q)] z_e(k-1),  where w is the
+// recurrence restarted at the segment's first position with zero history. So, for the
+// two paths of a sweep at once:
+//   phase A: every segment's restarted recurrence (independent chains, one cluster each);
+//   phase B: the recurrence over the segment ends, z_e(k) = w_e(k) - P z_e(k-1);
+//   phase C: the remaining positions at once, z_q = w_q - P z_e(k-1).
+// Every block lies on one forward and one backward path, so the products are stored by
+// block (Pf, Pb). They are formed once per factorisation (complex64, FP32 accumulation).
+// ---------------------------------------------------------------------------
+struct SegPath {
+  int J0, step, n;   // blocks J0 + step * q, q = 0..n-1
+  int Ls, K;         // segment length and number of segments
+  int kc0;           // first phase-A cluster of this path
+};
+template <typename T> struct SegArgs {
+  const c2<T>* in;    // phase A: the recurrences' right-hand sides (block layout)
+  c2<T>* out;         // phase A: restarted recurrences; phase B: in place
+  const c2<T>* C[2];  // per path: Lm or Up
+  const c2<T>* P;     // segment products of this sweep, by block
+  SegPath path[2];
+  int phase;          // 0 = A, 1 = B
+};
+
+__host__ __device__ __forceinline__ int seg_end(int k, int Ls, int n) { return min((k + 1) * Ls, n) - 1; }
+__host__ __device__ __forceinline__ int path_block(const SegPath& p, int q) { return p.J0 + p.step * q; }
+
+template <typename T, int RPW>
+__global__ void __launch_bounds__(kSolveMaxWarps * 32, 1)
+    k_seg_chain(SegArgs<T> a, CoarseLayout L, SolveGeom G, int* err, const int* active) {
+  using V = c2<T>;
+  if (active && *active == 0) return;
+  extern __shared__ __align__(128) unsigned char sm[];
+  uint64_t* full = reinterpret_cast<uint64_t*>(sm + G.off_mbar);
+  uint64_t* empty = full + G.S;
+  uint64_t* gbar = reinterpret_cast<uint64_t*>(sm + G.off_misc);
+  int* s_err = reinterpret_cast<int*>(sm + G.off_misc + 16);
+  V* gath = reinterpret_cast<V*>(sm + G.off_gath);
+  V* stage = reinterpret_cast<V*>(sm + G.off_stage);
+
+  const unsigned rank = cluster_rank(), CS = cluster_size();
+  const int B = L.B, ldb = L.ldb, R = G.R, CW = G.CW, nchunk = G.nchunk, S = G.S;
+  const int r0 = (int)rank * R, r1 = min(B, r0 + R), nr = max(0, r1 - r0);
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int nwc = (int)(blockDim.x >> 5) - 1;
+  const V zero = mk(T(0), T(0));
+  unsigned cidu;
+  asm volatile("mov.u32 %0, %%clusterid.x;" : "=r"(cidu));
+  const int cid = (int)cidu;
+
+  // this cluster's chain: phase A, one segment of a path; phase B, one path's segment ends
+  const bool phA = a.phase == 0;
+  const int pi = phA ? (cid >= a.path[1].kc0 ? 1 : 0) : cid;
+  const SegPath pa = a.path[pi];
+  const V* C = a.C[pi];
+  const int seg = phA ? cid - pa.kc0 : 0;
+  const int q0 = seg * pa.Ls;
+  const int nsteps = phA ? max(0, min(pa.Ls, pa.n - q0)) : pa.K - 1;
+  auto pos = [&](int t) { return phA ? q0 + t : seg_end(t + 1, pa.Ls, pa.n); };
+  auto blk = [&](int t) { return path_block(pa, pos(t)); };
+  auto inv = [&](int t) -> const V* { return (phA ? a.in : a.out) + (size_t)blk(t) * ldb; };
+  auto mat = [&](int t) -> const V* { return (phA ? C : a.P) + (size_t)blk(t) * B * ldb; };
+  const V* x0 = phA ? nullptr : a.out + (size_t)path_block(pa, seg_end(0, pa.Ls, pa.n)) * ldb;
+  const int tm = phA ? 1 : 0;   // first step with a matrix
+  const int U = max(0, nsteps - tm) * nchunk;
+
+  if (tid == 0) {
+    *s_err = 0;
+    for (int q = 0; q < S; ++q) {
+      mbar_init(&full[q], 1);
+      mbar_init(&empty[q], (unsigned)nwc);
+    }
+    mbar_init(&gbar[0], 1);
+    mbar_init(&gbar[1], 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  for (int i = tid; i < 2 * ldb; i += blockDim.x) gath[i] = zero;
+  __syncthreads();
+  // the history of phase B's first step (the first segment's end), in the slot step 0 reads
+  if (x0 && nsteps > 0)
+    for (int i = tid; i < B; i += blockDim.x) gath[ldb + i] = cvt_ldcg(x0 + i);
+  __syncthreads();
+  cluster_sync();
+  if (nsteps == 0) return;
+
+  if (warp == nwc) {
+    for (int u = 0; u < U; ++u) {
+      const int slot = u % S;
+      if (u >= S) mbar_wait(&empty[slot], (unsigned)(((u / S) - 1) & 1), s_err, err);
+      if (lane == 0) {
+        const int t = tm + u / nchunk, c = u - (t - tm) * nchunk;
+        V* dst = stage + (size_t)slot * R * CW;
+        if (nr == 0) {
+          mbar_expect_tx(&full[slot], 0);
+        } else {
+          const V* src = mat(t) + (size_t)r0 * ldb;
+          asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+          if (nchunk == 1) {
+            const unsigned bytes = (unsigned)(sizeof(V) * (size_t)nr * ldb);
+            mbar_expect_tx(&full[slot], bytes);
+            bulk_g2s(dst, src, bytes, &full[slot]);
+          } else {
+            const int c0 = c * CW, nc = min(CW, ldb - c0);
+            const unsigned bytes = (unsigned)(sizeof(V) * nc);
+            mbar_expect_tx(&full[slot], bytes * nr);
+            for (int r = 0; r < nr; ++r)
+              bulk_g2s(dst + (size_t)r * CW, src + (size_t)r * ldb + c0, bytes, &full[slot]);
+          }
+        }
+      }
+      __syncwarp();
+    }
+  } else {
+    const unsigned rx_bytes = (unsigned)(sizeof(V) * B);
+    V pc[RPW];
+#pragma unroll
+    for (int q = 0; q < RPW; ++q) {
+      const int r = warp + q * nwc;
+      pc[q] = cvt_ldcg(inv(0) + (r < nr ? r0 + r : 0));
+    }
+    int u = 0;
+    for (int t = 0; t < nsteps; ++t) {
+      const bool more = t + 1 < nsteps;
+      if (tid == 0 && more) mbar_expect_tx(&gbar[t & 1], rx_bytes);
+      V pn[RPW];
+      {
+        const V* nx = inv(more ? t + 1 : t);
+#pragma unroll
+        for (int q = 0; q < RPW; ++q) {
+          const int r = warp + q * nwc;
+          pn[q] = cvt_ldcg(nx + (r < nr ? r0 + r : 0));
+        }
+      }
+      V acc[RPW];
+#pragma unroll
+      for (int q = 0; q < RPW; ++q) acc[q] = zero;
+      if (t >= tm) {
+        const V* x = gath + (size_t)((t - 1) & 1) * ldb;
+        for (int c = 0; c < nchunk; ++c, ++u) {
+          const int slot = u % S;
+          mbar_wait(&full[slot], (unsigned)((u / S) & 1), s_err, err);
+          const V* st = stage + (size_t)slot * R * CW;
+          const int c0 = c * CW, nc = min(CW, ldb - c0);
+#pragma unroll
+          for (int q = 0; q < RPW; ++q) {
+            const int r = warp + q * nwc;
+            if (r < nr) acc[q] = cadd(acc[q], row_dot(st + (size_t)r * CW, x + c0, nc, lane));
+          }
+          __syncwarp();
+          if (lane == 0) mbar_arrive(&empty[slot]);
+        }
+      }
+      V* o = a.out + (size_t)blk(t) * ldb;
+#pragma unroll
+      for (int q = 0; q < RPW; ++q) {
+        const int r = warp + q * nwc;
+        if (r < nr) {
+          const V val = t >= tm ? csub(pc[q], warp_sum(acc[q])) : pc[q];
+          if (lane == 0) o[r0 + r] = val;
+          acc[q] = val;
+        }
+      }
+      if (more) {
+        V* gdst = gath + (size_t)(t & 1) * ldb;
+#pragma unroll
+        for (int q = 0; q < RPW; ++q) {
+          const int r = warp + q * nwc;
+          if (r < nr && lane < (int)CS) st_async(gdst + r0 + r, (unsigned)lane, acc[q], &gbar[t & 1]);
+        }
+        mbar_wait_cluster(&gbar[t & 1], (unsigned)((t >> 1) & 1), s_err, err);
+      }
+#pragma unroll
+      for (int q = 0; q < RPW; ++q) pc[q] = pn[q];
+    }
+  }
+  cluster_sync();
+}
+
+// Middle block of the twisted form: x_m = p_m - Lm[m] y_{m-1} - Up[m] y_{m+1}, written to
+// out[m] (the backward paths' first position). One warp per row.
+template <typename T>
+__global__ void __launch_bounds__(256) k_seg_middle(const c2<T>* __restrict__ Lm, const c2<T>* __restrict__ Up,
+                                                    const c2<T>* __restrict__ p, c2<T>* __restrict__ y,
+                                                    CoarseLayout L, const int* active) {
+  using V = c2<T>;
+  if (active && *active == 0) return;
+  const int B = L.B, ldb = L.ldb, m = L.mid;
+  const int lane = threadIdx.x & 31;
+  const int a = (int)((blockIdx.x * blockDim.x + threadIdx.x) >> 5);
+  if (a >= B) return;
+  const V g = cadd(row_dot(Lm + ((size_t)m * B + a) * ldb, y + (size_t)(m - 1) * ldb, ldb, lane),
+                   row_dot(Up + ((size_t)m * B + a) * ldb, y + (size_t)(m + 1) * ldb, ldb, lane));
+  const V v = warp_sum(g);
+  if (lane == 0) y[(size_t)m * ldb + a] = csub(p[(size_t)m * ldb + a], v);
+}
+
+// Phase C: z_q -= P[J(q)] z_e(k-1) for every position q of segments k >= 1 except their
+// ends, on both paths of a sweep. One warp per row; the CTA's warps take consecutive rows
+// of one block, so the history vector is staged once per CTA in shared memory.
+template <typename T>
+__global__ void __launch_bounds__(256) k_seg_fixup(const c2<T>* __restrict__ P, c2<T>* __restrict__ Z,
+                                                   CoarseLayout L, SegPath p0, SegPath p1, const int* active) {
+  using V = c2<T>;
+  if (active && *active == 0) return;
+  __shared__ __align__(16) V xs[1040];
+  const int B = L.B, ldb = L.ldb;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int rpb = (B + 7) / 8;   // row groups of 8 per block
+  const int64_t n0 = (int64_t)max(0, p0.n - p0.Ls) * rpb, n1 = (int64_t)max(0, p1.n - p1.Ls) * rpb;
+  for (int64_t g = blockIdx.x; g < n0 + n1; g += gridDim.x) {
+    const bool second = g >= n0;
+    const SegPath& pp = second ? p1 : p0;
+    const int64_t gl = second ? g - n0 : g;
+    const int q = pp.Ls + (int)(gl / rpb), a = (int)(gl % rpb) * 8 + warp;
+    const int k = q / pp.Ls;
+    const bool skip = q == seg_end(k, pp.Ls, pp.n);
+    const V* src = Z + (size_t)path_block(pp, k * pp.Ls - 1) * ldb;
+    __syncthreads();
+    if (!skip)
+      for (int i = threadIdx.x; i < ldb; i += blockDim.x) xs[i] = i < B ? cvt_ldcg(src + i) : mk(T(0), T(0));
+    __syncthreads();
+    if (skip || a >= B) continue;
+    const int J = path_block(pp, q);
+    const V v = warp_sum(row_dot(P + ((size_t)J * B + a) * ldb, xs, ldb, lane));
+    if (lane == 0) {
+      V* o = Z + (size_t)J * ldb + a;
+      *o = csub(*o, v);
+    }
+  }
+}
+
+// Segment products, step i of every segment k >= 1 of one path (one z-slice per segment):
+// i = 0: P[J(kLs)] = C_J;  i >= 1: P[J(q)] = -C_{J(q)} P[J(q-1)], q = kLs + i.
+// Row-major B x ldb operands (inner dimension B; padding columns are zero and stay zero).
+// 64 x 64 output tile per CTA, 16 x 16 threads with 4 x 4 complex outputs each.
+struct SegProducts {
+  const float2* C[4];
+  float2* P[4];
+  SegPath path[4];
+  int zoff[5];   // z-slices of path p: [zoff[p], zoff[p+1]), one per segment k >= 1
+};
+__global__ void __launch_bounds__(256) k_seg_products(SegProducts sp, CoarseLayout L, int i) {
+  const int B = L.B, ldb = L.ldb;
+  const int z = blockIdx.z;
+  const int pi = z < sp.zoff[1] ? 0 : z < sp.zoff[2] ? 1 : z < sp.zoff[3] ? 2 : 3;
+  const SegPath pp = sp.path[pi];
+  const float2* __restrict__ C = sp.C[pi];
+  float2* __restrict__ P = sp.P[pi];
+  const int k = 1 + z - sp.zoff[pi];
+  const int q = k * pp.Ls + i;
+  if (q > seg_end(k, pp.Ls, pp.n)) return;
+  const float2* A = C + (size_t)path_block(pp, q) * B * ldb;
+  float2* Zq = P + (size_t)path_block(pp, q) * B * ldb;
+  const int row0 = blockIdx.y * 64, col0 = blockIdx.x * 64;
+  const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
+  if (i == 0) {
+    for (int e = threadIdx.x; e < 64 * 64; e += 256) {
+      const int r = row0 + e / 64, c = col0 + e % 64;
+      if (r < B && c < ldb) Zq[(size_t)r * ldb + c] = A[(size_t)r * ldb + c];
+    }
+    return;
+  }
+  const float2* X = P + (size_t)path_block(pp, q - 1) * B * ldb;
+  __shared__ float2 As[64][17];
+  __shared__ __align__(16) float2 Xs[16][64];
+  float2 acc[4][4];
+#pragma unroll
+  for (int r = 0; r < 4; ++r)
+#pragma unroll
+    for (int c = 0; c < 4; ++c) acc[r][c] = make_float2(0.f, 0.f);
+  for (int k0 = 0; k0 < B; k0 += 16) {
+    for (int e = threadIdx.x; e < 64 * 16; e += 256) {
+      const int r = e / 16, kk = e % 16;
+      const int gr = row0 + r, gk = k0 + kk;
+      As[r][kk] = (gr < B && gk < B) ? A[(size_t)gr * ldb + gk] : make_float2(0.f, 0.f);
+      const int xr = e / 64, xc = e % 64;
+      const int gxr = k0 + xr, gxc = col0 + xc;
+      Xs[xr][xc] = (gxr < B && gxc < ldb) ? X[(size_t)gxr * ldb + gxc] : make_float2(0.f, 0.f);
+    }
+    __syncthreads();
+#pragma unroll
+    for (int kk = 0; kk < 16; ++kk) {
+      float2 av[4], xv[4];
+#pragma unroll
+      for (int r = 0; r < 4; ++r) av[r] = As[ty * 4 + r][kk];
+      const float4 x01 = *reinterpret_cast<const float4*>(&Xs[kk][tx * 4]);
+      const float4 x23 = *reinterpret_cast<const float4*>(&Xs[kk][tx * 4 + 2]);
+      xv[0] = make_float2(x01.x, x01.y);
+      xv[1] = make_float2(x01.z, x01.w);
+      xv[2] = make_float2(x23.x, x23.y);
+      xv[3] = make_float2(x23.z, x23.w);
+#pragma unroll
+      for (int r = 0; r < 4; ++r)
+#pragma unroll
+        for (int c = 0; c < 4; ++c) acc[r][c] = cfma(av[r], xv[c], acc[r][c]);
+    }
+    __syncthreads();
+  }
+#pragma unroll
+  for (int r = 0; r < 4; ++r) {
+    const int gr = row0 + ty * 4 + r;
+    if (gr >= B) continue;
+#pragma unroll
+    for (int c = 0; c < 4; ++c) {
+      const int gc = col0 + tx * 4 + c;
+      if (gc < ldb) Zq[(size_t)gr * ldb + gc] = make_float2(-acc[r][c].x, -acc[r][c].y);
+    }
+  }
+}
+
 }  // namespace
 
 std::mutex g_twist_mu;
 std::unordered_map<long long, bool> g_twist_ok;   // launch shape -> two clusters co-resident
+
+namespace {
+SegPath make_path(int J0, int step, int n, int Kmax, int kc0) {
+  SegPath p;
+  p.J0 = J0;
+  p.step = step;
+  p.n = n;
+  const int K0 = std::max(1, std::min(Kmax, n));
+  p.Ls = (n + K0 - 1) / K0;
+  p.K = (n + p.Ls - 1) / p.Ls;
+  p.kc0 = kc0;
+  return p;
+}
+// the two forward and the two backward paths of the twisted sweeps (mid = L.mid)
+void seg_paths(const CoarseLayout& L, const CoarsePlan& plan, SegPath* f, SegPath* b) {
+  const int m = L.mid, nb = L.nb;
+  f[0] = make_path(0, 1, m, plan.K, 0);
+  f[1] = make_path(nb - 1, -1, nb - 1 - m, plan.K, f[0].K);
+  b[0] = make_path(m, -1, m + 1, plan.K, 0);
+  b[1] = make_path(m, 1, nb - m, plan.K, b[0].K);
+}
+}  // namespace
 
 template <typename T>
 int plan_coarse_solve(const CoarseLayout& L, CoarsePlan* plan) {
@@ -930,6 +1273,8 @@ int plan_coarse_solve(const CoarseLayout& L, CoarsePlan* plan) {
   *plan = CoarsePlan{};
   cudaFuncSetAttribute(k_coarse_solve<T, 1>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
   cudaFuncSetAttribute(k_coarse_solve<T, kRPW>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+  cudaFuncSetAttribute(k_seg_chain<T, 1>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+  cudaFuncSetAttribute(k_seg_chain<T, kRPW>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
   for (int CS : {16, 8, 4, 2, 1}) {
     const int R = (L.B + CS - 1) / CS;
     // one consumer warp per row of the CTA's slice (up to kRPW rows per warp) + a producer warp
@@ -944,6 +1289,8 @@ int plan_coarse_solve(const CoarseLayout& L, CoarsePlan* plan) {
         const bool one = (R + nwc - 1) / nwc == 1;
         auto kern = one ? k_coarse_solve<T, 1> : k_coarse_solve<T, kRPW>;
         cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)budget);
+        cudaFuncSetAttribute(one ? k_seg_chain<T, 1> : k_seg_chain<T, kRPW>,
+                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)budget);
         cudaLaunchConfig_t cfg = {};
         cfg.gridDim = dim3(CS);
         cfg.blockDim = dim3(32 * nwarps);
@@ -968,6 +1315,14 @@ int plan_coarse_solve(const CoarseLayout& L, CoarsePlan* plan) {
         plan->smem = G.total;
         plan->threads = 32 * nwarps;
         plan->ncl = 1;
+        // complex64 solves of long chains: segmented recurrences on the four half-sweeps of
+        // the twisted form, one co-resident cluster per segment in phase A
+        if (sizeof(T) == sizeof(float) && L.nb >= 16 && L.ldb <= kSegMaxLdb && ncl >= 4) {
+          plan->seg = 1;
+          plan->ncl = 2;           // twisted factorisation (mid = nb / 2)
+          plan->K = ncl / 2;       // phase-A clusters per path
+          return HELM_OK;
+        }
         // Twisted form: two co-resident clusters (cooperative launch). Validated once per
         // launch shape by an inert trial launch whose 'active' flag is 0 (the kernel
         // returns at entry); the answer is cached (the trial synchronises the device).
@@ -1031,9 +1386,43 @@ int plan_coarse_solve(const CoarseLayout& L, CoarsePlan* plan) {
 template <typename T>
 void launch_coarse_solve(const CoarsePlan& plan, const c2<T>* Dinv, const c2<T>* Lm, const c2<T>* Up,
                          const CoarseLayout& L, const c2<T>* rc, c2<T>* uc, c2<T>* xmid, int* xflag,
-                         unsigned* bar, int* err, const int* active, int nsm, cudaStream_t s) {
+                         unsigned* bar, int* err, const int* active, int nsm, cudaStream_t s,
+                         const SegBufs<T>* seg) {
   // p = blockdiag(Dinv) r for all blocks at once, into uc
   k_block_gemv<T><<<nsm * 8, 256, 0, s>>>(Dinv, rc, uc, L, active);
+  if (plan.seg && seg) {
+    SolveGeom G = solve_geometry<T>(L, plan.CS, plan.CW, plan.S);
+    const int nwc = plan.threads / 32 - 1;
+    auto kern = (plan.R + nwc - 1) / nwc == 1 ? k_seg_chain<T, 1> : k_seg_chain<T, kRPW>;
+    auto chain = [&](const SegArgs<T>& a, int nclusters) {
+      cudaLaunchConfig_t cfg = {};
+      cfg.gridDim = dim3(plan.CS * nclusters);
+      cfg.blockDim = dim3(plan.threads);
+      cfg.dynamicSmemBytes = G.total;
+      cfg.stream = s;
+      cudaLaunchAttribute at[1];
+      at[0].id = cudaLaunchAttributeClusterDimension;
+      at[0].val.clusterDim.x = plan.CS;
+      at[0].val.clusterDim.y = 1;
+      at[0].val.clusterDim.z = 1;
+      cfg.attrs = at;
+      cfg.numAttrs = 1;
+      cudaLaunchKernelEx(&cfg, kern, a, L, G, err, active);
+    };
+    SegPath f[2], b[2];
+    seg_paths(L, plan, f, b);
+    const int fix_grid = nsm * 8;
+    // forward sweeps: uc (p) -> yb (y); middle block x_m -> yb[mid]
+    chain(SegArgs<T>{uc, seg->yb, {Lm, Up}, seg->Pf, {f[0], f[1]}, 0}, f[0].K + f[1].K);
+    chain(SegArgs<T>{seg->yb, seg->yb, {Lm, Up}, seg->Pf, {f[0], f[1]}, 1}, 2);
+    k_seg_fixup<T><<<fix_grid, 256, 0, s>>>(seg->Pf, seg->yb, L, f[0], f[1], active);
+    k_seg_middle<T><<<(L.B * 32 + 255) / 256, 256, 0, s>>>(Lm, Up, uc, seg->yb, L, active);
+    // backward sweeps: yb (y, x_m) -> uc (x)
+    chain(SegArgs<T>{seg->yb, uc, {Up, Lm}, seg->Pb, {b[0], b[1]}, 0}, b[0].K + b[1].K);
+    chain(SegArgs<T>{uc, uc, {Up, Lm}, seg->Pb, {b[0], b[1]}, 1}, 2);
+    k_seg_fixup<T><<<fix_grid, 256, 0, s>>>(seg->Pb, uc, L, b[0], b[1], active);
+    return;
+  }
   if (plan.grid) {
     cudaMemsetAsync(bar, 0, kBarWords * sizeof(unsigned), s);
     cudaLaunchConfig_t cfg = {};
@@ -1153,12 +1542,39 @@ void convert_factor_df(const float4* src, float2* dst, size_t n, cudaStream_t s)
   k_convert_df<<<152 * 8, 256, 0, s>>>(src, dst, n);
 }
 
+void coarse_seg_products(const float2* Lm, const float2* Up, float2* Pf, float2* Pb, const CoarseLayout& L,
+                         const CoarsePlan& plan, cudaStream_t s) {
+  SegPath f[2], b[2];
+  seg_paths(L, plan, f, b);
+  SegProducts sp{};
+  const SegPath all[4] = {f[0], f[1], b[0], b[1]};
+  const float2* C[4] = {Lm, Up, Up, Lm};
+  float2* P[4] = {Pf, Pf, Pb, Pb};
+  int Lmax = 0;
+  sp.zoff[0] = 0;
+  for (int p = 0; p < 4; ++p) {
+    sp.C[p] = C[p];
+    sp.P[p] = P[p];
+    sp.path[p] = all[p];
+    sp.zoff[p + 1] = sp.zoff[p] + all[p].K - 1;
+    Lmax = std::max(Lmax, all[p].Ls);
+  }
+  if (sp.zoff[4] == 0) return;
+  const dim3 grid((L.ldb + 63) / 64, (L.B + 63) / 64, sp.zoff[4]);
+  for (int i = 0; i < Lmax; ++i) k_seg_products<<<grid, 256, 0, s>>>(sp, L, i);
+}
+int coarse_seg_launches(const CoarseLayout& L, const CoarsePlan& plan) {
+  SegPath f[2], b[2];
+  seg_paths(L, plan, f, b);
+  return std::max(std::max(f[0].Ls, f[1].Ls), std::max(b[0].Ls, b[1].Ls));
+}
+
 template int plan_coarse_solve<float>(const CoarseLayout&, CoarsePlan*);
 template int plan_coarse_solve<double>(const CoarseLayout&, CoarsePlan*);
 template void launch_coarse_solve<float>(const CoarsePlan&, const float2*, const float2*, const float2*,
                                          const CoarseLayout&, const float2*, float2*, float2*, int*, unsigned*,
-                                         int*, const int*, int, cudaStream_t);
+                                         int*, const int*, int, cudaStream_t, const SegBufs<float>*);
 template void launch_coarse_solve<double>(const CoarsePlan&, const double2*, const double2*, const double2*,
                                           const CoarseLayout&, const double2*, double2*, double2*, int*, unsigned*,
-                                          int*, const int*, int, cudaStream_t);
+                                          int*, const int*, int, cudaStream_t, const SegBufs<double>*);
 }  // namespace helm

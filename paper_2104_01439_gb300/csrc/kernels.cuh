@@ -65,6 +65,15 @@ struct CoarsePlan {
   int nblk;     // CTAs of the grid kernel
   size_t smem;  // dynamic shared memory bytes
   int threads;
+  int seg;      // 1: segmented triangular solves (complex64, twisted factorisation)
+  int K;        // phase-A clusters (segments) per half-sweep path
+};
+// Workspaces of the segmented solve: yb one block-padded coarse vector; Pf, Pb the
+// segment products of the forward and backward sweeps, nb x B x ldb each, by block.
+template <typename T> struct SegBufs {
+  c2<T>* yb;
+  const c2<T>* Pf;
+  const c2<T>* Pb;
 };
 template <typename T>
 int plan_coarse_solve(const CoarseLayout& L, CoarsePlan* plan);
@@ -75,7 +84,12 @@ int plan_coarse_solve(const CoarseLayout& L, CoarsePlan* plan);
 template <typename T>
 void launch_coarse_solve(const CoarsePlan& plan, const c2<T>* Dinv, const c2<T>* Lm, const c2<T>* Up,
                          const CoarseLayout& L, const c2<T>* rc, c2<T>* uc, c2<T>* xmid, int* xflag,
-                         unsigned* bar, int* err, const int* active, int nsm, cudaStream_t s);
+                         unsigned* bar, int* err, const int* active, int nsm, cudaStream_t s,
+                         const SegBufs<T>* seg = nullptr);
+// Segment products of both sweeps (plan.seg, complex64), and the number of launches it takes
+void coarse_seg_products(const float2* Lm, const float2* Up, float2* Pf, float2* Pb, const CoarseLayout& L,
+                         const CoarsePlan& plan, cudaStream_t s);
+int coarse_seg_launches(const CoarseLayout& L, const CoarsePlan& plan);
 // Block-Thomas factorisation: Dinv[J] = (A_JJ - A_J,J-1 Dinv[J-1] A_J-1,J)^{-1} (two chains
 // meeting at L.mid), in complex128 (8-pivot Gauss-Jordan panels) or in complex double-float
 // (float4 hi/lo pairs, 16-pivot panels). tmp: 2 x B x ldb; piv: 2 x factor_workspace(L)

@@ -48,8 +48,8 @@ def test_product_path_has_no_cpu_fallback():
 
 
 def test_request_bytes_estimate_is_host_only_and_consistent():
-    """helm_request_bytes is pure host arithmetic: monotone in the mesh, the restart
-    length and the precision, and it counts the dense coarse blocks (nb * B^2 entries)."""
+    """helm_request_bytes is pure host arithmetic: monotone in the mesh and the restart
+    length, and it counts the dense coarse blocks (nb * B^2 entries) of each form."""
     pytest.importorskip("torch")
     from paper_2104_01439_gb300 import _binding, build
     _binding.load(build.build())
@@ -57,10 +57,11 @@ def test_request_bytes_estimate_is_host_only_and_consistent():
     small, big = rb(n=64), rb(n=128)
     assert 0 < small < big
     assert rb(n=128, restart=80) > rb(n=128, restart=50)
-    assert rb(n=128, precision=_binding.HELM_FP64) > rb(n=128, precision=_binding.HELM_MIXED)
-    # 2D P1 n=512: three complex64 coarse matrices (Dinv, Lm, Up) of 257 blocks of 257 x 258
-    # plus the FP64 factor workspace: the estimate must cover at least those
-    coarse = 3 * 257 * 257 * 258 * 8 + 257 * 257 * 258 * 16
-    assert rb(n=512, restart=80) > coarse
+    # 2D P1 n=512, mixed: five complex64 coarse matrix sets (Dinv, Lm, Up and the two
+    # segment-product sets) of 257 blocks of 257 x 258, plus the double-float factor
+    # workspace; FP64: three complex128 sets
+    blk = 257 * 257 * 258
+    assert rb(n=512, restart=80) > 5 * blk * 8 + blk * 16
+    assert rb(n=512, restart=80, precision=_binding.HELM_FP64) > 3 * blk * 16
     with pytest.raises(_binding.HelmError):
         rb(n=63)   # 1/h must be even
