@@ -280,12 +280,12 @@ void enqueue_iteration(helm_ctx* h, cudaStream_t s, Profile* prof = nullptr, int
   const int* act = &kb.st->pre;
   const int* jsel = &kb.st->j;
   if (prof) cudaEventRecord(prof->ev[ev0 + 0], s);
-  enqueue_vcycle_any(h, VecSel<const double2>{kb.vj, 0, nullptr, 0}, VecSel<double2>{kb.Z, kb.ldN, jsel, 0},
+  enqueue_vcycle_any(h, VecSel<const double2>{kb.W, 0, nullptr, 0}, VecSel<double2>{kb.Z, kb.ldN, jsel, 0},
                      act, s, prof, ev0);
   if (prof) cudaEventRecord(prof->ev[ev0 + 3], s);
   StencilView<double> A0 = make_view<double>(h->gf, h->coefA0, nullptr);
   launch_apply<double, double2, double2>(A0, VecSel<const double2>{kb.Z, kb.ldN, jsel, 0},
-                                         VecSel<double2>{kb.W, 0, nullptr, 0}, act, s);
+                                         VecSel<double2>{kb.W, 0, nullptr, 0}, act, s, kb.Ws);
   if (prof) cudaEventRecord(prof->ev[ev0 + 4], s);
   launch_arnoldi(kb, s, prof ? prof->ev[ev0 + 5] : nullptr);
   if (prof) cudaEventRecord(prof->ev[ev0 + 6], s);
@@ -737,7 +737,6 @@ static int setup_impl(helm_ctx* h) {
   kb.nblk_upd = (int)std::max<int64_t>(1, (kb.N + 255) / 256);
   kb.pstride = std::max(kb.nblk, std::max(kb.nblk_upd, kb.nblk_dots));
   CK(h->alloc(&kb.Vs, sizeof(float4) * kb.ldN * (m + 1)));
-  CK(h->alloc(&kb.vj, sizeof(double2) * kb.ldN));
   CK(h->alloc(&kb.W, sizeof(double2) * kb.ldN));
   CK(h->alloc(&kb.Ws, sizeof(float4) * kb.ldN));
   CK(h->alloc(&kb.Z, sizeof(double2) * kb.ldN * m));
@@ -746,6 +745,7 @@ static int setup_impl(helm_ctx* h) {
   CK(h->alloc(&kb.sn, sizeof(double2) * m));
   CK(h->alloc(&kb.g, sizeof(double2) * (m + 1)));
   CK(h->alloc(&kb.y, sizeof(double2) * m));
+  CK(h->alloc(&kb.zs, sizeof(double) * m));
   CK(h->alloc(&kb.hcol, sizeof(double2) * (m + 2)));
   CK(h->alloc(&kb.hfin, sizeof(double2) * (m + 2)));
   CK(h->alloc(&kb.hp, sizeof(double2) * (m + 2)));
@@ -756,7 +756,6 @@ static int setup_impl(helm_ctx* h) {
   CK(cudaMallocHost(&h->st_h, sizeof(KState)));
   CK(cudaMallocHost(&h->err_h, sizeof(int)));
   CK(cudaMemsetAsync(kb.Vs, 0, sizeof(float4) * kb.ldN * (m + 1), s));
-  CK(cudaMemsetAsync(kb.vj, 0, sizeof(double2) * kb.ldN, s));
   CK(cudaMemsetAsync(kb.W, 0, sizeof(double2) * kb.ldN, s));
   CK(cudaMemsetAsync(kb.Z, 0, sizeof(double2) * kb.ldN * m, s));
   CK(cudaStreamSynchronize(s));

@@ -625,8 +625,8 @@ __device__ __forceinline__ double2 row_dot(const double2* a, const double2* x, i
 // once (independent GEMVs over the whole GPU, one warp per row), written to uc.
 // ---------------------------------------------------------------------------
 template <typename T>
-__global__ void __launch_bounds__(256) k_block_gemv(const c2<T>* __restrict__ Dinv, const c2<T>* __restrict__ rc,
-                                                    c2<T>* __restrict__ out, CoarseLayout L, const int* active) {
+__global__ void __launch_bounds__(256) k_block_gemv_wide(const c2<T>* __restrict__ Dinv, const c2<T>* __restrict__ rc,
+                                                         c2<T>* __restrict__ out, CoarseLayout L, const int* active) {
   using V = c2<T>;
   if (active && *active == 0) return;
   const int lane = threadIdx.x & 31;
@@ -1121,39 +1121,70 @@ __global__ void __launch_bounds__(256) k_seg_middle(const c2<T>* __restrict__ Lm
   if (lane == 0) y[(size_t)m * ldb + a] = csub(p[(size_t)m * ldb + a], v);
 }
 
-// Phase C: z_q -= P[J(q)] z_e(k-1) for every position q of segments k >= 1 except their
-// ends, on both paths of a sweep. One warp per row; the CTA's warps take consecutive rows
-// of one block, so the history vector is staged once per CTA in shared memory.
+// Rows of one dense B x ldb block times a vector staged in shared memory: each warp takes
+// 4 rows at a time (16-byte loads, up to 20 in flight per lane), 16 warps per CTA.
+// out[a] = sub ? out[a] - M[a] x : M[a] x.
+constexpr int kRowsThreads = 512;
+constexpr int kRowsSlab = 64;   // rows per CTA (one pass of 16 warps x 4 rows)
 template <typename T>
-__global__ void __launch_bounds__(256) k_seg_fixup(const c2<T>* __restrict__ P, c2<T>* __restrict__ Z,
-                                                   CoarseLayout L, SegPath p0, SegPath p1, const int* active) {
+__device__ __forceinline__ void block_rows(const c2<T>* __restrict__ M, const c2<T>* xs, c2<T>* out, int B, int ldb,
+                                           bool sub) {
   using V = c2<T>;
-  if (active && *active == 0) return;
-  __shared__ __align__(16) V xs[1040];
-  const int B = L.B, ldb = L.ldb;
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  const int rpb = (B + 7) / 8;   // row groups of 8 per block
-  const int64_t n0 = (int64_t)max(0, p0.n - p0.Ls) * rpb, n1 = (int64_t)max(0, p1.n - p1.Ls) * rpb;
-  for (int64_t g = blockIdx.x; g < n0 + n1; g += gridDim.x) {
-    const bool second = g >= n0;
-    const SegPath& pp = second ? p1 : p0;
-    const int64_t gl = second ? g - n0 : g;
-    const int q = pp.Ls + (int)(gl / rpb), a = (int)(gl % rpb) * 8 + warp;
-    const int k = q / pp.Ls;
-    const bool skip = q == seg_end(k, pp.Ls, pp.n);
-    const V* src = Z + (size_t)path_block(pp, k * pp.Ls - 1) * ldb;
-    __syncthreads();
-    if (!skip)
-      for (int i = threadIdx.x; i < ldb; i += blockDim.x) xs[i] = i < B ? cvt_ldcg(src + i) : mk(T(0), T(0));
-    __syncthreads();
-    if (skip || a >= B) continue;
-    const int J = path_block(pp, q);
-    const V v = warp_sum(row_dot(P + ((size_t)J * B + a) * ldb, xs, ldb, lane));
-    if (lane == 0) {
-      V* o = Z + (size_t)J * ldb + a;
-      *o = csub(*o, v);
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  const int abeg = blockIdx.y * kRowsSlab, aend = min(B, abeg + kRowsSlab);
+  for (int a0 = abeg + warp * 4; a0 < aend; a0 += nw * 4) {
+    V s[4];
+#pragma unroll
+    for (int r = 0; r < 4; ++r) {
+      const int a = min(a0 + r, aend - 1);
+      s[r] = row_dot(M + (size_t)a * ldb, xs, ldb, lane);
+    }
+#pragma unroll
+    for (int r = 0; r < 4; ++r) {
+      const V v = warp_sum(s[r]);
+      if (lane == 0 && a0 + r < aend) out[a0 + r] = sub ? csub(out[a0 + r], v) : v;
     }
   }
+}
+
+// Block-diagonal pre-pass with the block's vector staged in shared memory (one CTA per block).
+template <typename T>
+__global__ void __launch_bounds__(kRowsThreads) k_block_gemv(const c2<T>* __restrict__ Dinv,
+                                                             const c2<T>* __restrict__ rc, c2<T>* __restrict__ out,
+                                                             CoarseLayout L, const int* active) {
+  using V = c2<T>;
+  if (active && *active == 0) return;
+  extern __shared__ __align__(16) unsigned char smv[];
+  V* xs = reinterpret_cast<V*>(smv);
+  const int B = L.B, ldb = L.ldb, J = blockIdx.x;
+  for (int i = threadIdx.x; i < ldb; i += blockDim.x) xs[i] = cvt_ldcg(rc + (size_t)J * ldb + i);
+  __syncthreads();
+  block_rows<T>(Dinv + (size_t)J * B * ldb, xs, out + (size_t)J * ldb, B, ldb, false);
+}
+
+// Phase C: z_q -= P[J(q)] z_e(k-1) for every position q of segments k >= 1 except their
+// ends, on both paths of a sweep. One CTA per position; the history vector is staged once.
+template <typename T>
+__global__ void __launch_bounds__(kRowsThreads) k_seg_fixup(const c2<T>* __restrict__ P, c2<T>* __restrict__ Z,
+                                                            CoarseLayout L, SegPath p0, SegPath p1,
+                                                            const int* active) {
+  using V = c2<T>;
+  if (active && *active == 0) return;
+  __shared__ __align__(16) V xs[kSegMaxLdb];
+  const int B = L.B, ldb = L.ldb;
+  const int n0 = max(0, p0.n - p0.Ls);
+  const int g = blockIdx.x;
+  const bool second = g >= n0;
+  const SegPath& pp = second ? p1 : p0;
+  const int q = pp.Ls + (second ? g - n0 : g);
+  if (q >= pp.n) return;
+  const int k = q / pp.Ls;
+  if (q == seg_end(k, pp.Ls, pp.n)) return;   // done by phase B
+  const V* src = Z + (size_t)path_block(pp, k * pp.Ls - 1) * ldb;
+  for (int i = threadIdx.x; i < ldb; i += blockDim.x) xs[i] = i < B ? cvt_ldcg(src + i) : mk(T(0), T(0));
+  __syncthreads();
+  const int J = path_block(pp, q);
+  block_rows<T>(P + (size_t)J * B * ldb, xs, Z + (size_t)J * ldb, B, ldb, true);
 }
 
 // Segment products, step i of every segment k >= 1 of one path (one z-slice per segment):
@@ -1277,7 +1308,9 @@ int plan_coarse_solve(const CoarseLayout& L, CoarsePlan* plan) {
   cudaFuncSetAttribute(k_seg_chain<T, kRPW>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
   for (int CS : {16, 8, 4, 2, 1}) {
     const int R = (L.B + CS - 1) / CS;
-    // one consumer warp per row of the CTA's slice (up to kRPW rows per warp) + a producer warp
+    // one consumer warp per row of the CTA's slice (up to kRPW rows per warp) + a producer
+    // warp. (Two rows per warp sharing the vector's loads measured slower: the step is
+    // bound by the latency of each warp's dependent chain, not by shared-memory bandwidth.)
     const int nwc = std::min(kSolveMaxWarps - 1, std::max(4, R));
     const int nwarps = nwc + 1;
     if ((R + nwc - 1) / nwc > kRPW) continue;
@@ -1389,7 +1422,11 @@ void launch_coarse_solve(const CoarsePlan& plan, const c2<T>* Dinv, const c2<T>*
                          unsigned* bar, int* err, const int* active, int nsm, cudaStream_t s,
                          const SegBufs<T>* seg) {
   // p = blockdiag(Dinv) r for all blocks at once, into uc
-  k_block_gemv<T><<<nsm * 8, 256, 0, s>>>(Dinv, rc, uc, L, active);
+  if (sizeof(c2<T>) * L.ldb <= 48 * 1024)
+    k_block_gemv<T><<<dim3(L.nb, (L.B + kRowsSlab - 1) / kRowsSlab), kRowsThreads, sizeof(c2<T>) * L.ldb, s>>>(
+        Dinv, rc, uc, L, active);
+  else
+    k_block_gemv_wide<T><<<nsm * 8, 256, 0, s>>>(Dinv, rc, uc, L, active);
   if (plan.seg && seg) {
     SolveGeom G = solve_geometry<T>(L, plan.CS, plan.CW, plan.S);
     const int nwc = plan.threads / 32 - 1;
@@ -1411,16 +1448,18 @@ void launch_coarse_solve(const CoarsePlan& plan, const c2<T>* Dinv, const c2<T>*
     };
     SegPath f[2], b[2];
     seg_paths(L, plan, f, b);
-    const int fix_grid = nsm * 8;
     // forward sweeps: uc (p) -> yb (y); middle block x_m -> yb[mid]
     chain(SegArgs<T>{uc, seg->yb, {Lm, Up}, seg->Pf, {f[0], f[1]}, 0}, f[0].K + f[1].K);
     chain(SegArgs<T>{seg->yb, seg->yb, {Lm, Up}, seg->Pf, {f[0], f[1]}, 1}, 2);
-    k_seg_fixup<T><<<fix_grid, 256, 0, s>>>(seg->Pf, seg->yb, L, f[0], f[1], active);
+    const int slabs = (L.B + kRowsSlab - 1) / kRowsSlab;
+    k_seg_fixup<T><<<dim3(std::max(1, f[0].n - f[0].Ls + f[1].n - f[1].Ls), slabs), kRowsThreads, 0, s>>>(
+        seg->Pf, seg->yb, L, f[0], f[1], active);
     k_seg_middle<T><<<(L.B * 32 + 255) / 256, 256, 0, s>>>(Lm, Up, uc, seg->yb, L, active);
     // backward sweeps: yb (y, x_m) -> uc (x)
     chain(SegArgs<T>{seg->yb, uc, {Up, Lm}, seg->Pb, {b[0], b[1]}, 0}, b[0].K + b[1].K);
     chain(SegArgs<T>{uc, uc, {Up, Lm}, seg->Pb, {b[0], b[1]}, 1}, 2);
-    k_seg_fixup<T><<<fix_grid, 256, 0, s>>>(seg->Pb, uc, L, b[0], b[1], active);
+    k_seg_fixup<T><<<dim3(std::max(1, b[0].n - b[0].Ls + b[1].n - b[1].Ls), slabs), kRowsThreads, 0, s>>>(
+        seg->Pb, uc, L, b[0], b[1], active);
     return;
   }
   if (plan.grid) {

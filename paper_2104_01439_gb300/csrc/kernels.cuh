@@ -23,7 +23,7 @@ template <typename V> inline VecSel<V> vsel(V* p) { return VecSel<V>{p, 0, nullp
 // y = A x
 template <typename T, typename Vin, typename Vout>
 void launch_apply(const StencilView<T>& A, VecSel<const Vin> x, VecSel<Vout> y, const int* active,
-                  cudaStream_t s);
+                  cudaStream_t s, float4* ws = nullptr);   // ws: optional double-float split of y
 // r = f - A u
 template <typename T, typename Vf, typename Vr>
 void launch_residual(const StencilView<T>& A, VecSel<const Vf> f, const c2<T>* u, Vr* r,
@@ -118,14 +118,15 @@ struct KState {
   int converged;   // Givens estimate <= tol
   int breakdown;   // h_{j+1,j} == 0
   int pre;         // this step applies the preconditioner and A0 (else it only finishes column j-1)
+  int ju;          // step whose correction sweep runs (j is already the next step by then)
   int m, maxit;
   int nonfinite;
-  int pad_;
   double nF;       // ||F||
   double beta;     // cycle's initial residual norm
   double tol;
   double est;      // |g_{j+1}| / ||F||
-  double sig;      // ||w|| of the previous step (u_j = w / sig)
+  double gabs;     // |g| of the last rotated column (|g_{c+1}| = |s_c| |g_c|)
+  double inv_nF;   // 1 / ||F||
   double irho;     // 1 / rho of this step
   double2 hjj;     // h_jj of this step
   double relres;   // true relative residual at cycle end
@@ -143,8 +144,8 @@ struct KrylovBufs {
   // complex64 (hi + lo), 16 bytes like complex128, used by the Gram-Schmidt
   // kernels at FP32 throughput with ~48-bit accurate inner products.
   float4* Vs;      // (m+1) x ldN: (hi.re, hi.im, lo.re, lo.im) per entry
-  double2* vj;     // current basis vector v_j in complex128 (preconditioner input)
-  double2* W;      // w = A0 z_j being orthogonalised (complex128)
+  double2* W;      // w = A0 z_j being orthogonalised (complex128); after the step u_{j+1},
+                   // the next step's preconditioner input
   float4* Ws;      // w split into hi + lo (read by the inner-product kernel)
   double2* Z;      // m x ldN preconditioned vectors
   int64_t ldN;
@@ -154,6 +155,7 @@ struct KrylovBufs {
   double2* sn;     // m
   double2* g;      // m+1
   double2* y;      // m
+  double* zs;      // m : scale of each preconditioned vector (1 / rho of its step)
   double2* hcol;   // m+2 : the column started by the previous step (finished by this one)
   double2* hfin;   // m+2 : the finished column handed to the Givens step
   double2* hp;     // m+1 : s_i = <v_i, u_j>

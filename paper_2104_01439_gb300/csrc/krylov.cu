@@ -57,17 +57,6 @@ __device__ __forceinline__ DF df_wsum(DF v) {
 constexpr int kE = 4;    // basis entries per thread in the inner-product kernel
 constexpr int kGD = 4;   // basis vectors per sweep of the inner-product kernel
 
-// w -> (hi, lo) once per pass, so the inner products run on FP32 pipes only
-__global__ void __launch_bounds__(kT) k_split_w(KrylovBufs kb) {
-  KState* st = kb.st;
-  if (!st->active || !st->pre) return;
-  for (int64_t n = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; n < kb.N; n += (int64_t)gridDim.x * blockDim.x) {
-    double2 v = kb.W[n];
-    DF r = df_split(v.x), q = df_split(v.y);
-    kb.Ws[n] = make_float4(r.h, q.h, r.l, q.l);
-  }
-}
-
 // Inner products of the basis slots 0..j against two vectors in one sweep over V:
 //   s_i = <v_i, u_j>  (u_j = the once-orthogonalised vector in slot j; s_j = ||u_j||^2)
 //   t_i = <v_i, w>    (w = A0 z_j; only when this step applies the preconditioner)
@@ -181,116 +170,130 @@ __device__ __forceinline__ double2 shfl2(double2 v, int src) {
   return make_double2(__shfl_sync(0xffffffffu, v.x, src), __shfl_sync(0xffffffffu, v.y, src));
 }
 
-// Givens step for the finished column c (one warp). The previous rotations turn the column
-// h = (h_0..h_c, h_{c+1} = hsub) into  col_i = c_i u_i + s_i h_{i+1}  with the carried value
-// u_0 = h_0,  u_{i+1} = -conj(s_i) u_i + c_i h_{i+1}  -- an affine recurrence in u. Each lane
-// composes the maps of a contiguous chunk of rotations, a warp scan composes the chunks
-// ((a2, b2) o (a1, b1) = (a2 a1, a2 b1 + b2)), and each lane then replays its chunk from its
-// exclusive prefix. The new rotation [c s; -conj(s) c] zeroes h_{c+1} against u_c; the
-// residual estimate is |g_{c+1}| / ||F||. Returns (on every lane) whether the solve stops.
-__device__ int givens_column(const KrylovBufs& kb, KState* st, int c, const double2* hf, double hsub, int lane) {
-  const int m = st->m;
-  double2* Hc = kb.H + (int64_t)c * (m + 1);
-  const int per = (c + 31) / 32;
-  const int i0 = min(c, lane * per), i1 = min(c, i0 + per);
-  double2 A = make_double2(1.0, 0.0), Bm = make_double2(0.0, 0.0);
-  for (int i = i0; i < i1; ++i) {
-    const double2 al = make_double2(-kb.sn[i].x, kb.sn[i].y);   // -conj(s_i)
-    const double cc = kb.cs[i];
-    const double2 hn = hf[i + 1];
-    Bm = cfma(al, Bm, make_double2(cc * hn.x, cc * hn.y));
-    A = cmul(al, A);
-  }
-#pragma unroll
-  for (int d = 1; d < 32; d <<= 1) {
-    const double2 Ap = shfl_up2(A, d), Bp = shfl_up2(Bm, d);
-    if (lane >= d) {
-      Bm = cfma(A, Bp, Bm);
-      A = cmul(A, Ap);
-    }
-  }
-  double2 Ae = shfl_up2(A, 1), Be = shfl_up2(Bm, 1);
-  if (lane == 0) {
-    Ae = make_double2(1.0, 0.0);
-    Be = make_double2(0.0, 0.0);
-  }
-  double2 u = cfma(Ae, hf[0], Be);   // u at the start of this lane's chunk
-  for (int i = i0; i < i1; ++i) {
-    const double2 sv = kb.sn[i];
-    const double cc = kb.cs[i];
-    const double2 hn = hf[i + 1];
-    Hc[i] = cfma(sv, hn, make_double2(cc * u.x, cc * u.y));
-    u = cfma(make_double2(-sv.x, sv.y), u, make_double2(cc * hn.x, cc * hn.y));
-  }
-  // u_c sits with the lane that replayed rotation c-1 (lane 0 when c == 0)
-  const int owner = c == 0 ? 0 : (c - 1) / per;
-  u = shfl2(u, owner);
-  int stop = 0;
-  if (lane == 0) {
-    // new rotation zeroing (u_c, hsub): [c s; -conj(s) c] [a; b] = [r; 0]
-    const double2 a = u, b = make_double2(hsub, 0.0);
-    const double aa = hypot(a.x, a.y), bb = hypot(b.x, b.y);
-    double cr;
-    double2 sv, r;
-    if (bb == 0.0) {
-      cr = 1.0; sv = make_double2(0.0, 0.0); r = a;
-    } else if (aa == 0.0) {
-      cr = 0.0; sv = make_double2(1.0, 0.0); r = b;
-    } else {
-      const double nu = hypot(aa, bb);
-      const double2 ph = make_double2(a.x / aa, a.y / aa);
-      cr = aa / nu;
-      sv = cmul(ph, make_double2(b.x / nu, -b.y / nu));
-      r = make_double2(ph.x * nu, ph.y * nu);
-    }
-    kb.cs[c] = cr;
-    kb.sn[c] = sv;
-    Hc[c] = r;
-    Hc[c + 1] = make_double2(0.0, 0.0);
-    const double2 gc = kb.g[c];
-    const double2 gc1 = cmul(make_double2(-sv.x, sv.y), gc);
-    kb.g[c + 1] = gc1;
-    kb.g[c] = make_double2(cr * gc.x, cr * gc.y);
-    const double est = hypot(gc1.x, gc1.y) / st->nF;
-    st->est = est;
-    st->total += 1;
-    if (!isfinite(est) || !isfinite(hsub)) st->nonfinite = 1;
-    if (!(hsub > 1e-14 * st->beta)) st->breakdown = 1;
-    if (est <= st->tol) st->converged = 1;
-    stop = st->converged || st->breakdown || st->nonfinite;
-  }
-  return __shfl_sync(0xffffffffu, stop, 0);
-}
-
 // Coefficients of the step (one warp), lagged classical Gram-Schmidt with
 // reorthogonalisation (Swirydowicz, Langou, Ananthan, Yang, Thomas 2020, DCGS2): the
 // vector u_j in slot j was orthogonalised once; here it is corrected,
 //   v_j = (u_j - sum_{i<j} s_i v_i) / rho,  rho^2 = ||u_j||^2 - sum_{i<j} |s_i|^2,
-// which finishes column j-1 of the Hessenberg matrix (the previous step wrote
-// A z_{j-1} = sum h_i v_i + sigma u_j):  h_i += sigma s_i (i < j), h_{j,j-1} = sigma rho,
-// followed by its Givens step and convergence test. The new column j starts as
-//   h_i = t_i (i < j),  h_jj = <v_j, w> = (t_j - sum_{i<j} conj(s_i) t_i) / rho.
+// which finishes column c = j-1 of the Hessenberg matrix (the previous step wrote
+// A z_{j-1} = sum h_i v_i + u_j, u_j unnormalised):  h_i += s_i (i < j), h_{j,j-1} = rho.
+// Its Givens step: the previous rotations turn the column h into
+// col_i = c_i w_i + s_i h_{i+1} with the carried value w_0 = h_0,
+// w_{i+1} = -conj(s_i) w_i + c_i h_{i+1} -- an affine recurrence in w. Each lane composes
+// the maps of a contiguous chunk of rotations, a warp scan composes the chunks
+// ((a2, b2) o (a1, b1) = (a2 a1, a2 b1 + b2)), and each lane replays its chunk from its
+// exclusive prefix. The new rotation [c s; -conj(s) c] zeroes h_{c+1} against w_c; the
+// residual estimate is |g_{c+1}| / ||F|| with |g_{c+1}| = |s| |g_c|. The new column j
+// starts as  h_i = t_i (i < j),  h_jj = <v_j, w> = (t_j - sum_{i<j} conj(s_i) t_i) / rho,
+// both divided by rho once more (the step's vector is z_j / rho).
+// All operands are fetched into shared memory in one round before the arithmetic.
+constexpr int kCoefMax = 520;   // restart length + 2 (helm_opts.restart <= 512)
 __global__ void __launch_bounds__(32) k_coef(KrylovBufs kb) {
   KState* st = kb.st;
   if (!st->active) return;
-  const int j = st->j, lane = threadIdx.x;
+  __shared__ double2 s_s[kCoefMax], s_t[kCoefMax], s_h[kCoefMax], s_sn[kCoefMax];
+  __shared__ double s_cs[kCoefMax];
+  const int j = st->j, m = st->m, lane = threadIdx.x;
   const bool pre = st->pre != 0;
-  const double2* s = kb.hp;
-  const double2* t = kb.tp;
+  const double beta = st->beta;
+  for (int i = lane; i <= j; i += 32) {
+    s_s[i] = kb.hp[i];
+    if (pre) s_t[i] = kb.tp[i];
+    if (i < j) s_h[i] = kb.hcol[i];
+    if (i + 1 < j) {
+      s_sn[i] = kb.sn[i];
+      s_cs[i] = kb.cs[i];
+    }
+  }
+  const double2 gc = j >= 1 ? kb.g[j - 1] : make_double2(0.0, 0.0);
+  __syncwarp();
   double a = 0.0;
-  for (int i = lane; i < j; i += 32) a = fma(s[i].x, s[i].x, fma(s[i].y, s[i].y, a));
+  for (int i = lane; i < j; i += 32) a = fma(s_s[i].x, s_s[i].x, fma(s_s[i].y, s_s[i].y, a));
   a = wsum(a);
-  const double rho2 = s[j].x - a;
-  const double rho = rho2 > 0.0 ? sqrt(rho2) : 0.0;
+  const double rho2 = s_s[j].x - a;
+  const double irho = rho2 > 0.0 ? rsqrt(rho2) : 0.0;
+  const double rho = rho2 > 0.0 ? rho2 * irho : 0.0;
   int stop = 0;
   if (j == 0) {
     // r = beta u_0 = beta rho v_0
-    if (lane == 0) kb.g[0] = make_double2(st->beta * rho, 0.0);
+    if (lane == 0) {
+      kb.g[0] = make_double2(beta * rho, 0.0);
+      st->gabs = beta * rho;
+    }
   } else {
-    const double sig = st->sig;
-    for (int i = lane; i < j; i += 32) kb.hfin[i] = cfma(make_double2(sig, 0.0), s[i], kb.hcol[i]);
+    // finished column c = j - 1 (h_0..h_c), in place in s_h
+    const int c = j - 1;
+    for (int i = lane; i < j; i += 32) s_h[i] = cadd(s_h[i], s_s[i]);
     __syncwarp();
-    stop = givens_column(kb, st, j - 1, kb.hfin, sig * rho, lane);
+    const double hsub = rho;
+    double2* Hc = kb.H + (int64_t)c * (m + 1);
+    const int per = (c + 31) / 32;
+    const int i0 = min(c, lane * per), i1 = min(c, i0 + per);
+    double2 A = make_double2(1.0, 0.0), Bm = make_double2(0.0, 0.0);
+    for (int i = i0; i < i1; ++i) {
+      const double2 al = make_double2(-s_sn[i].x, s_sn[i].y);   // -conj(s_i)
+      const double2 hn = s_h[i + 1];
+      Bm = cfma(al, Bm, make_double2(s_cs[i] * hn.x, s_cs[i] * hn.y));
+      A = cmul(al, A);
+    }
+#pragma unroll
+    for (int d = 1; d < 32; d <<= 1) {
+      const double2 Ap = shfl_up2(A, d), Bp = shfl_up2(Bm, d);
+      if (lane >= d) {
+        Bm = cfma(A, Bp, Bm);
+        A = cmul(A, Ap);
+      }
+    }
+    double2 Ae = shfl_up2(A, 1), Be = shfl_up2(Bm, 1);
+    if (lane == 0) {
+      Ae = make_double2(1.0, 0.0);
+      Be = make_double2(0.0, 0.0);
+    }
+    double2 w = cfma(Ae, s_h[0], Be);   // w at the start of this lane's chunk
+    for (int i = i0; i < i1; ++i) {
+      const double2 sv = s_sn[i];
+      const double cc = s_cs[i];
+      const double2 hn = s_h[i + 1];
+      Hc[i] = cfma(sv, hn, make_double2(cc * w.x, cc * w.y));
+      w = cfma(make_double2(-sv.x, sv.y), w, make_double2(cc * hn.x, cc * hn.y));
+    }
+    // w_c sits with the lane that replayed rotation c-1 (lane 0 when c == 0)
+    w = shfl2(w, c == 0 ? 0 : (c - 1) / per);
+    if (lane == 0) {
+      // new rotation zeroing (w_c, hsub): c = |w|/nu, s = (w/|w|) hsub/nu, r = (w/|w|) nu
+      const double aa2 = w.x * w.x + w.y * w.y;
+      double cr, sabs;
+      double2 sv, r;
+      if (!(hsub != 0.0)) {
+        cr = 1.0; sv = make_double2(0.0, 0.0); r = w; sabs = 0.0;
+      } else if (aa2 == 0.0) {
+        cr = 0.0; sv = make_double2(1.0, 0.0); r = make_double2(hsub, 0.0); sabs = 1.0;
+      } else {
+        const double nu2 = fma(hsub, hsub, aa2);
+        const double inu = rsqrt(nu2), iaa = rsqrt(aa2);
+        const double nu = nu2 * inu, aa = aa2 * iaa;
+        cr = aa * inu;
+        sabs = hsub * inu;
+        const double fs = sabs * iaa, fr = nu * iaa;
+        sv = make_double2(w.x * fs, w.y * fs);
+        r = make_double2(w.x * fr, w.y * fr);
+      }
+      kb.cs[c] = cr;
+      kb.sn[c] = sv;
+      Hc[c] = r;
+      Hc[c + 1] = make_double2(0.0, 0.0);
+      kb.g[c + 1] = cmul(make_double2(-sv.x, sv.y), gc);
+      kb.g[c] = make_double2(cr * gc.x, cr * gc.y);
+      const double gabs = sabs * st->gabs;
+      st->gabs = gabs;
+      const double est = gabs * st->inv_nF;
+      st->est = est;
+      st->total += 1;
+      if (!isfinite(est) || !isfinite(hsub)) st->nonfinite = 1;
+      if (!(hsub > 1e-14 * beta)) st->breakdown = 1;
+      if (est <= st->tol) st->converged = 1;
+      stop = st->converged || st->breakdown || st->nonfinite;
+    }
+    stop = __shfl_sync(0xffffffffu, stop, 0);
   }
   if (!pre || !(rho > 0.0)) stop = 1;
   if (stop) {
@@ -301,43 +304,53 @@ __global__ void __launch_bounds__(32) k_coef(KrylovBufs kb) {
     }
     return;   // j columns are finished
   }
+  // z_j is used scaled, zhat_j = z_j / rho (u_j is unnormalised): A0 zhat_j = w / rho, so the
+  // new column and w carry a factor 1 / rho and the solution update takes y_j / rho
   double2 d = make_double2(0.0, 0.0);
-  for (int i = lane; i < j; i += 32) d = cfma(make_double2(s[i].x, -s[i].y), t[i], d);
+  for (int i = lane; i < j; i += 32) d = cfma(make_double2(s_s[i].x, -s_s[i].y), s_t[i], d);
   d = wsum(d);
-  const double irho = 1.0 / rho;
-  const double2 hjj = make_double2((t[j].x - d.x) * irho, (t[j].y - d.y) * irho);
-  for (int i = lane; i < j; i += 32) kb.hcol[i] = t[i];
+  const double i2 = irho * irho;
+  const double2 hjj = make_double2((s_t[j].x - d.x) * i2, (s_t[j].y - d.y) * i2);
+  for (int i = lane; i < j; i += 32) kb.hcol[i] = make_double2(s_t[i].x * irho, s_t[i].y * irho);
   if (lane == 0) {
+    kb.zs[j] = irho;
     kb.hcol[j] = hjj;
     st->hjj = hjj;
     st->irho = irho;
+    // the correction sweep of this step reads ju; the next step (its preconditioner and A0
+    // included) runs at j + 1 and builds column total + 2 if it applies the preconditioner
+    st->ju = j;
+    st->j = j + 1;
+    st->pre = (j + 1 < m && st->total + 2 <= st->maxit) ? 1 : 0;
   }
 }
 
 // One sweep over V[0..j-1] for both corrections of the step:
-//   v_j = (u_j - sum s_i v_i) / rho   (written into slot j)
-//   w  <- w - sum t_i v_i - h_jj v_j   (complex128, FP64 subtraction), partial ||w||^2.
+//   v_j = (u_j - sum s_i v_i) / rho          (written into slot j)
+//   w  <- w / rho - sum t'_i v_i - h_jj v_j   (complex128, FP64 subtraction; t'_i = t_i / rho)
+// and w, unnormalised, becomes u_{j+1}: slot j+1 of the basis (double-float) and the next
+// step's preconditioner input (W, complex128). Normalisation is lagged into rho.
 // A warp takes 32 entries: its two half-warps sum over the two halves of the basis for two
 // entries per lane, meet with one shuffle, and then every lane finishes one entry.
 __global__ void __launch_bounds__(kT) k_update2(KrylovBufs kb) {
   KState* st = kb.st;
   if (!st->active) return;
-  const int j = st->j, m = st->m;
+  const int j = st->ju;
   const int64_t N = kb.N, ld = kb.ldN;
   extern __shared__ float4 hs4[];   // [0, j): s_i, [j, 2j): t_i as (re.h, re.l, im.h, im.l)
+  const double irho_d = st->irho;
   for (int i = threadIdx.x; i < 2 * j; i += blockDim.x) {
-    const double2 c = i < j ? kb.hp[i] : kb.tp[i - j];
+    const double2 c = i < j ? kb.hp[i] : kb.hcol[i - j];   // s_i, and t_i / rho from the new column
     DF r = df_split(c.x), q = df_split(c.y);
     hs4[i] = make_float4(r.h, r.l, q.h, q.l);
   }
-  const DF irho = df_split(st->irho);
+  const DF irho = df_split(irho_d);
   const double2 hjj_d = st->hjj;
   const float4 hjj = dfc_from(hjj_d);
   __syncthreads();
   const int lane = threadIdx.x & 31, half = lane >> 4;
   const int split = (j + 1) / 2;   // slots [0, split) and [split, j)
   const int ib = half ? split : 0, ie = half ? j : split;
-  double s2 = 0.0;
   const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
   for (int64_t wg = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5; wg * 32 < N; wg += nw) {
     const int64_t na = wg * 32 + (lane & 15), nb2 = na + 16;
@@ -384,55 +397,11 @@ __global__ void __launch_bounds__(kT) k_update2(KrylovBufs kb) {
       dfc_mac(hjj, v, cw);
       const float4 c = dfc_fin(cw);
       double2 w = kb.W[n];
-      w.x -= df_val(dfc_re(c));
-      w.y -= df_val(dfc_im(c));
+      w.x = fma(w.x, irho_d, -df_val(dfc_re(c)));
+      w.y = fma(w.y, irho_d, -df_val(dfc_im(c)));
       kb.W[n] = w;
-      s2 = fma(w.x, w.x, fma(w.y, w.y, s2));
+      slot[ld] = dfc_from(w);
     }
-  }
-  __shared__ double rn[kT / 32];
-  s2 = wsum(s2);
-  if ((threadIdx.x & 31) == 0) rn[threadIdx.x >> 5] = s2;
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    double t = 0.0;
-    for (int i = 0; i < kT / 32; ++i) t += rn[i];
-    kb.part[kb_row_norm(m) * kb.pstride + blockIdx.x] = make_double2(t, 0.0);
-  }
-}
-
-// sigma_j = ||w||: the next step's u_{j+1} = w / sigma_j. Decides whether the next step
-// applies the preconditioner (room left in the cycle and in maxit) or only finishes column j.
-__global__ void k_reduce_norm2(KrylovBufs kb) {
-  KState* st = kb.st;
-  if (!st->active) return;
-  const int j = st->j, m = st->m;
-  double2 s2 = sum_partials(kb, kb_row_norm(m), threadIdx.x & 31, kb.nblk_upd);
-  if (threadIdx.x != 0) return;
-  const double sig = sqrt(s2.x);
-  st->sig = sig;
-  st->pre = (j + 1 < m && st->total + 2 <= st->maxit && sig > 1e-14 * st->beta && isfinite(sig)) ? 1 : 0;
-  st->j = j + 1;
-}
-
-// v_j slot of the basis stored split (hi + lo) and in complex128 for the preconditioner
-__device__ __forceinline__ void store_basis(const KrylovBufs& kb, int col, int64_t n, double2 v) {
-  DF r = df_split(v.x), q = df_split(v.y);
-  kb.Vs[(int64_t)col * kb.ldN + n] = make_float4(r.h, q.h, r.l, q.l);
-  kb.vj[n] = v;
-}
-
-// u_{j} = w / sigma (zero when w vanished: the next step then finds rho = 0)
-__global__ void __launch_bounds__(kT) k_normalize2(KrylovBufs kb) {
-  KState* st = kb.st;
-  if (!st->active) return;
-  const double sig = st->sig;
-  const double inv = sig > 1e-14 * st->beta ? 1.0 / sig : (sig == sig ? 0.0 : sig);
-  const int col = st->j;
-  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-  for (int64_t n = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; n < kb.N; n += stride) {
-    double2 a = kb.W[n];
-    store_basis(kb, col, n, make_double2(a.x * inv, a.y * inv));
   }
 }
 
@@ -462,6 +431,7 @@ __global__ void k_norm_fin(KrylovBufs kb, int which) {
   double nrm = sqrt(s2.x);
   if (which == 0) {
     st->nF = nrm;
+    st->inv_nF = nrm > 0.0 ? 1.0 / nrm : 0.0;
     st->beta = nrm;
   } else {
     st->beta = nrm;
@@ -479,7 +449,9 @@ __global__ void __launch_bounds__(kT) k_cycle_start(KrylovBufs kb, const double2
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
   for (int64_t n = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; n < kb.N; n += stride) {
     double2 a = r[n];
-    store_basis(kb, 0, n, make_double2(a.x * inv, a.y * inv));
+    const double2 v = make_double2(a.x * inv, a.y * inv);
+    kb.Vs[n] = dfc_from(v);   // slot 0
+    kb.W[n] = v;              // the first step's preconditioner input
   }
   if (blockIdx.x == 0) {
     for (int i = threadIdx.x; i <= st->m; i += blockDim.x) kb.g[i] = make_double2(i == 0 ? beta : 0.0, 0.0);
@@ -487,7 +459,7 @@ __global__ void __launch_bounds__(kT) k_cycle_start(KrylovBufs kb, const double2
       st->j = 0;
       st->active = ok ? 1 : 0;
       st->pre = ok && st->m >= 1 && st->total + 1 <= st->maxit ? 1 : 0;
-      st->sig = 0.0;
+      st->gabs = beta;
       st->converged = 0;
       st->breakdown = 0;
       if (!isfinite(beta)) st->nonfinite = 1;
@@ -508,7 +480,7 @@ __global__ void __launch_bounds__(kT) k_backsolve(KrylovBufs kb) {
     const double2* Ri = kb.H + (int64_t)i * (m + 1);   // column i
     if (threadIdx.x == 0) {
       double2 yi = cmul(rhs[i], cinv(Ri[i]));
-      kb.y[i] = yi;
+      kb.y[i] = make_double2(yi.x * kb.zs[i], yi.y * kb.zs[i]);   // the step used z_i / rho_i
       yi_s = yi;
     }
     __syncthreads();
@@ -536,14 +508,11 @@ __global__ void __launch_bounds__(kT) k_update_x(KrylovBufs kb, double2* x) {
 }  // namespace
 
 void launch_arnoldi(const KrylovBufs& kb, cudaStream_t s, cudaEvent_t mid) {
-  k_split_w<<<kb.nblk, kT, 0, s>>>(kb);
   k_dots2<<<dim3(kb.nblk_dots, (kb.m + 1 + kGD - 1) / kGD), kT, 0, s>>>(kb);
   k_reduce2<<<(2 * (kb.m + 1) + kT / 32 - 1) / (kT / 32), kT, 0, s>>>(kb);
   k_coef<<<1, 32, 0, s>>>(kb);
   if (mid) cudaEventRecord(mid, s);
   k_update2<<<kb.nblk_upd, kT, sizeof(float4) * 2 * kb.m, s>>>(kb);
-  k_reduce_norm2<<<1, 32, 0, s>>>(kb);
-  k_normalize2<<<kb.nblk, kT, 0, s>>>(kb);
 }
 
 void launch_cycle_start(const KrylovBufs& kb, const double2* r, cudaStream_t s) {

@@ -9,6 +9,7 @@
 // parameter so the offset loop is fully unrolled.
 #include <algorithm>
 
+#include "dfloat.cuh"
 #include "kernels.cuh"
 
 namespace helm {
@@ -71,9 +72,14 @@ __device__ __forceinline__ c2<T> row_apply(const StencilView<T>& s, const c2<T>*
   return acc;
 }
 
+// the product's double-float split (hi + lo), read by the Gram-Schmidt inner products
+__device__ __forceinline__ void store_split(float4* ws, int p, double2 v) { ws[p] = dfc_from(v); }
+__device__ __forceinline__ void store_split(float4*, int, float2) {}
+
 template <int NOFF, typename T, typename Vin, typename Vout>
 __global__ void __launch_bounds__(kThreads) k_apply(StencilView<T> s, VecSel<const Vin> xs,
-                                                     VecSel<Vout> ys, const int* active) {
+                                                     VecSel<Vout> ys, float4* __restrict__ ws,
+                                                     const int* active) {
   if (active && *active == 0) return;
   extern __shared__ __align__(16) unsigned char sm[];
   c2<T>* coef = reinterpret_cast<c2<T>*>(sm);
@@ -85,7 +91,9 @@ __global__ void __launch_bounds__(kThreads) k_apply(StencilView<T> s, VecSel<con
   for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < N; p += gridDim.x * blockDim.x) {
     int a[3];
     int cls = decode(s.g, p, a);
-    y[p] = to<Vout>(row_apply<NOFF>(s, coef + cls * NOFF, p, N, x));
+    const c2<T> v = row_apply<NOFF>(s, coef + cls * NOFF, p, N, x);
+    y[p] = to<Vout>(v);
+    if (ws) store_split(ws, p, v);
   }
 }
 
@@ -314,12 +322,12 @@ size_t table_smem(const GridDesc& g, bool with_dinv) {
 
 template <typename T, typename Vin, typename Vout>
 void launch_apply(const StencilView<T>& A, VecSel<const Vin> x, VecSel<Vout> y, const int* active,
-                  cudaStream_t s) {
+                  cudaStream_t s, float4* ws) {
   int g = grid_for(A.g.N);
   size_t sm = table_smem<T>(A.g, false);
-  HELM_SWITCH_NOFF(A.g.noff, (k_apply<9, T, Vin, Vout><<<g, kThreads, sm, s>>>(A, x, y, active)),
-                   (k_apply<25, T, Vin, Vout><<<g, kThreads, sm, s>>>(A, x, y, active)),
-                   (k_apply<27, T, Vin, Vout><<<g, kThreads, sm, s>>>(A, x, y, active)));
+  HELM_SWITCH_NOFF(A.g.noff, (k_apply<9, T, Vin, Vout><<<g, kThreads, sm, s>>>(A, x, y, ws, active)),
+                   (k_apply<25, T, Vin, Vout><<<g, kThreads, sm, s>>>(A, x, y, ws, active)),
+                   (k_apply<27, T, Vin, Vout><<<g, kThreads, sm, s>>>(A, x, y, ws, active)));
 }
 
 template <typename T, typename Vf, typename Vr>
@@ -396,7 +404,7 @@ template void launch_coarse_pack<double2, float2>(const GridDesc&, const CoarseL
 template void launch_coarse_unpack<float2, double2>(const GridDesc&, const CoarseLayout&, const float2*,
                                                     double2*, cudaStream_t);
 template void launch_apply<float, float2, float2>(const StencilView<float>&, VecSel<const float2>,
-                                                  VecSel<float2>, const int*, cudaStream_t);
+                                                  VecSel<float2>, const int*, cudaStream_t, float4*);
 // complex128 everywhere
 template void launch_jacobi_from_zero<double, double2>(const StencilView<double>&, VecSel<const double2>,
                                                        double2*, double2*, bool, const int*, cudaStream_t);
@@ -414,6 +422,6 @@ template void launch_coarse_pack<double2, double2>(const GridDesc&, const Coarse
 template void launch_coarse_unpack<double2, double2>(const GridDesc&, const CoarseLayout&, const double2*,
                                                      double2*, cudaStream_t);
 template void launch_apply<double, double2, double2>(const StencilView<double>&, VecSel<const double2>,
-                                                     VecSel<double2>, const int*, cudaStream_t);
+                                                     VecSel<double2>, const int*, cudaStream_t, float4*);
 
 }  // namespace helm
