@@ -61,16 +61,15 @@ def stencil_bytes_per_dof(nu, mixed):
     """Algorithmic bytes per DoF of helm_apply and of nu smoothing sweeps from u = 0.
 
     apply: read x, write y (complex128): 32 B.
-    mixed smoother (complex64 sweeps): the first kernel reads f (16) and writes u (8) and the
-    complex64 copy of f (8); every middle sweep reads f, u and writes u (8 + 8 + 8); the last
-    reads f, u (8 + 8) and writes complex128 (16). FP64: 16 B per vector access, no copy of f.
-    The first kernel runs two sweeps when nu >= 3 (u^1 at the neighbours recomputed from f)."""
-    first = 32
-    kernels = 1 + (nu - 1 - (2 if nu >= 3 else 1)) + 1
-    middle = kernels - 2
+    mixed smoother (complex64 sweeps, one kernel per sweep): the first reads f (16) and
+    writes u (8) and the complex64 copy of f (8); every middle sweep reads f, u and writes u
+    (8 + 8 + 8); the last reads f, u (8 + 8) and writes complex128 (16).
+    FP64: 16 B per vector access, no copy of f; its first kernel runs two sweeps when nu >= 3
+    (u^1 at the neighbours recomputed from f)."""
     if mixed:
-        return {"apply": 32, "smooth": first + 24 * middle + 32, "kernels": kernels}
-    return {"apply": 32, "smooth": first + 48 * middle + 48, "kernels": kernels}
+        return {"apply": 32, "smooth": 32 + 24 * (nu - 2) + 32, "kernels": nu}
+    kernels = 1 + (nu - 1 - (2 if nu >= 3 else 1)) + 1
+    return {"apply": 32, "smooth": 32 + 48 * (kernels - 2) + 48, "kernels": kernels}
 
 
 def stencil_hbm(pkg, stream, dev, hbm, peak_kind, reps=20):

@@ -239,8 +239,11 @@ void enqueue_vcycle(helm_ctx* h, VecSel<const double2> f, VecSel<double2> z, con
     launch_jacobi_from_zero<T, double2>(Ae, f, cur, nullptr, nu >= 2, active, s);
     fT = VecSel<const V>{reinterpret_cast<const V*>(f.base), f.stride, f.jsel, f.jadd};
   } else {
-    launch_jacobi_from_zero<T, double2>(Ae, f, cur, p.fT, nu >= 2, active, s);
+    // complex64: u^1 = w D^-1 f with f converted once (the fused two-sweep kernel would
+    // convert f at every neighbour on the slow double-to-float path), then one sweep
+    launch_jacobi_from_zero<T, double2>(Ae, f, nu >= 2 ? oth : cur, p.fT, false, active, s);
     fT = vsel<const V>(p.fT);
+    if (nu >= 2) launch_jacobi<T, V, V>(Ae, fT, oth, vsel<V>(cur), active, s);
   }
   for (int it = 2; it < nu; ++it) {   // presmoothing steps 3..nu
     launch_jacobi<T, V, V>(Ae, fT, cur, vsel<V>(oth), active, s);
@@ -536,8 +539,9 @@ void enqueue_smooth(helm_ctx* h, const double2* f, double2* u, int nu, cudaStrea
     launch_jacobi_from_zero<T, double2>(Ae, vsel<const double2>(f), cur, nullptr, two, nullptr, s);
     fT = VecSel<const V>{reinterpret_cast<const V*>(f), 0, nullptr, 0};
   } else {
-    launch_jacobi_from_zero<T, double2>(Ae, vsel<const double2>(f), cur, p.fT, two, nullptr, s);
+    launch_jacobi_from_zero<T, double2>(Ae, vsel<const double2>(f), two ? oth : cur, p.fT, false, nullptr, s);
     fT = vsel<const V>(p.fT);
+    if (two) launch_jacobi<T, V, V>(Ae, fT, oth, vsel<V>(cur), nullptr, s);
   }
   for (int done = two ? 2 : 1; done < nu - 1; ++done) {
     launch_jacobi<T, V, V>(Ae, fT, cur, vsel<V>(oth), nullptr, s);
@@ -730,9 +734,9 @@ static int setup_impl(helm_ctx* h) {
   const int m = o.restart;
   kb.N = h->gf.N;
   kb.ldN = (kb.N + 31) & ~int64_t(31);
-  // element-wise Krylov kernels: one entry per thread; inner products: <= 4 per thread
+  // element-wise Krylov kernels: one entry per thread; inner products: <= 8 per thread
   kb.nblk = (int)std::max<int64_t>(1, (kb.N + 255) / 256);
-  kb.nblk_dots = (int)std::max<int64_t>(1, (kb.N + 1023) / 1024);
+  kb.nblk_dots = (int)std::max<int64_t>(1, (kb.N + 2047) / 2048);   // 8 entries per thread
   kb.m = m;
   kb.nblk_upd = (int)std::max<int64_t>(1, (kb.N + 255) / 256);
   kb.pstride = std::max(kb.nblk, std::max(kb.nblk_upd, kb.nblk_dots));

@@ -162,7 +162,7 @@ struct KrylovBufs {
   double2* tp;     // m+1 : t_i = <v_i, w>
   double2* part;   // pstride x kb_rows(m) partial sums (inner products: double-float as float4)
   int nblk;        // blocks of the element-wise Krylov kernels (256 threads, one entry per thread)
-  int nblk_dots;   // blocks of the inner-product kernel (256 threads, <= 4 entries per thread)
+  int nblk_dots;   // blocks of the inner-product kernel (256 threads, <= 8 entries per thread)
   int m;           // restart length (host copy of KState::m, sizes launches)
   int nblk_upd;    // blocks of the update kernel (32 entries per warp)
   int pstride;     // row stride of the partials buffer: max over the kernels that write it

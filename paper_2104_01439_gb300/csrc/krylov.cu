@@ -54,7 +54,7 @@ __device__ __forceinline__ DF df_wsum(DF v) {
   return v;
 }
 
-constexpr int kE = 4;    // basis entries per thread in the inner-product kernel
+constexpr int kE = 8;    // basis entries per thread in the inner-product kernel
 constexpr int kGD = 4;   // basis vectors per sweep of the inner-product kernel
 
 // Inner products of the basis slots 0..j against two vectors in one sweep over V:
@@ -80,27 +80,36 @@ __global__ void __launch_bounds__(kT) k_dots2(KrylovBufs kb) {
   DF sr[kGD], si[kGD], tr[kGD], ti[kGD];
 #pragma unroll
   for (int t = 0; t < kGD; ++t) sr[t] = si[t] = tr[t] = ti[t] = DF{0.f, 0.f};
+  // entries base + k * stride, k < kE, in batches of two: the next batch's loads are issued
+  // before the current batch's arithmetic. Out-of-range entries load entry 0 and are weighted 0.
+  float4 u[2], w[2], v[2][kGD];
+  auto load = [&](int k, int b) {
+    const int64_t n = base + k * stride;
+    const int64_t nn = n < N ? n : 0;
+    const float4 z = dfc_zero();
+    u[b] = n < N ? uj[nn] : z;
+    w[b] = (pre && n < N) ? kb.Ws[nn] : z;
+#pragma unroll
+    for (int t = 0; t < kGD; ++t) v[b][t] = t < ng ? kb.Vs[(int64_t)(i0 + t) * ld + nn] : z;
+  };
+  load(0, 0);
 #pragma unroll
   for (int k = 0; k < kE; ++k) {
-    const int64_t n = base + k * stride;
-    if (n >= N) break;
-    const float4 u = uj[n];                        // (hr, hi, lr, li)
-    const float4 w = pre ? kb.Ws[n] : dfc_zero();
+    const int b = k & 1;
+    if (k + 1 < kE) load(k + 1, b ^ 1);
 #pragma unroll
     for (int t = 0; t < kGD; ++t) {
-      if (t < ng) {
-        const float4 v = kb.Vs[(int64_t)(i0 + t) * ld + n];
-        // conj(v) x = (vr xr + vi xi) + i (vr xi - vi xr)
-        df_mac(v.x, v.z, u.x, u.z, sr[t]);
-        df_mac(v.y, v.w, u.y, u.w, sr[t]);
-        df_mac(v.x, v.z, u.y, u.w, si[t]);
-        df_mac(-v.y, -v.w, u.x, u.z, si[t]);
-        if (pre) {
-          df_mac(v.x, v.z, w.x, w.z, tr[t]);
-          df_mac(v.y, v.w, w.y, w.w, tr[t]);
-          df_mac(v.x, v.z, w.y, w.w, ti[t]);
-          df_mac(-v.y, -v.w, w.x, w.z, ti[t]);
-        }
+      const float4 vv = v[b][t], uu = u[b], ww = w[b];
+      // conj(v) x = (vr xr + vi xi) + i (vr xi - vi xr)
+      df_mac(vv.x, vv.z, uu.x, uu.z, sr[t]);
+      df_mac(vv.y, vv.w, uu.y, uu.w, sr[t]);
+      df_mac(vv.x, vv.z, uu.y, uu.w, si[t]);
+      df_mac(-vv.y, -vv.w, uu.x, uu.z, si[t]);
+      if (pre) {
+        df_mac(vv.x, vv.z, ww.x, ww.z, tr[t]);
+        df_mac(vv.y, vv.w, ww.y, ww.w, tr[t]);
+        df_mac(vv.x, vv.z, ww.y, ww.w, ti[t]);
+        df_mac(-vv.y, -vv.w, ww.x, ww.z, ti[t]);
       }
     }
   }
