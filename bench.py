@@ -372,15 +372,16 @@ def run_ours(args):
     hbm, peak_kind = peaks()
     stencil_large = stencil_hbm(pkg, stream, dev, hbm, peak_kind)
 
-    # roofline of the dominant kernel (coarse triangular solves), from CUDA events inside the solve:
-    # algorithmic bytes = the banded LU's two triangular factors read once, 2 b 8 B per coarse DoF
-    # (complex64, b = W_c + 1), i.e. (2 W_c - 1) W_c^2 8 B for the 2D P1 coarse grid
+    # roofline of the dominant phase (the coarse solve: block pre-pass, segment chains, segment
+    # fix-ups, middle block), from CUDA events inside the solve: algorithmic bytes = the banded
+    # LU's two triangular factors read once, 2 b 8 B per coarse DoF (complex64, b = W_c + 1),
+    # i.e. (2 W_c - 1) W_c^2 8 B for the 2D P1 coarse grid
     dom = max(prof, key=lambda k: prof[k][0])
     Wc = WL.n // 2 + 1
     bytes_coarse = (2 * Wc - 1) * Wc * Wc * 8
     phase_ms = {k: v[0] / max(v[1], 1) for k, v in prof.items()}
     achieved = bytes_coarse / (phase_ms["coarse_solve"] * 1e-3) / 1e9
-    traffic = None   # no ncu counters for the current coarse kernels (fault record)
+    traffic = None   # the cluster chain kernels are kept out of multi-pass ncu captures
     # stencil kernels: outer apply reads z and writes w (32 B/DoF, complex128); the fine level of
     # the V-cycle moves >= 52 B/DoF (read v_j 16, u 8 + 8, write z_j 16, transfers ~4)
     n_f = WL.num_dofs
@@ -428,7 +429,8 @@ def run_ours(args):
                  "mixed_speedup": value / (world * len(t_fp64) / fp64_total)},
         "phase_ms_per_iteration": phase_ms,
         "stencil": stencil,
-        "roofline": {"kernel": "k_coarse_solve<float> (" + dom + " dominant)", "bound": "hbm",
+        "roofline": {"kernel": "coarse solve phase: k_block_gemv + 4 k_seg_chain + 2 k_seg_fixup + k_seg_middle ("
+                               + dom + " dominant)", "bound": "hbm",
                      "achieved": achieved, "peak": hbm, "unit": "GB/s", "frac": achieved / hbm,
                      "peak_kind": peak_kind, "traffic": traffic,
                      "algorithmic_bytes": bytes_coarse},

@@ -1122,25 +1122,26 @@ __global__ void __launch_bounds__(256) k_seg_middle(const c2<T>* __restrict__ Lm
 }
 
 // Rows of one dense B x ldb block times a vector staged in shared memory: each warp takes
-// 4 rows at a time (16-byte loads, up to 20 in flight per lane), 16 warps per CTA.
+// kRowsWarp rows at a time (16-byte loads, several per row in flight per lane), 16 warps per CTA.
 // out[a] = sub ? out[a] - M[a] x : M[a] x.
 constexpr int kRowsThreads = 512;
 constexpr int kRowsSlab = 64;   // rows per CTA (one pass of 16 warps x 4 rows)
+constexpr int kRowsWarp = 4;    // rows in flight per warp (8 measured slower)
 template <typename T>
 __device__ __forceinline__ void block_rows(const c2<T>* __restrict__ M, const c2<T>* xs, c2<T>* out, int B, int ldb,
                                            bool sub) {
   using V = c2<T>;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
   const int abeg = blockIdx.y * kRowsSlab, aend = min(B, abeg + kRowsSlab);
-  for (int a0 = abeg + warp * 4; a0 < aend; a0 += nw * 4) {
-    V s[4];
+  for (int a0 = abeg + warp * kRowsWarp; a0 < aend; a0 += nw * kRowsWarp) {
+    V s[kRowsWarp];
 #pragma unroll
-    for (int r = 0; r < 4; ++r) {
+    for (int r = 0; r < kRowsWarp; ++r) {
       const int a = min(a0 + r, aend - 1);
       s[r] = row_dot(M + (size_t)a * ldb, xs, ldb, lane);
     }
 #pragma unroll
-    for (int r = 0; r < 4; ++r) {
+    for (int r = 0; r < kRowsWarp; ++r) {
       const V v = warp_sum(s[r]);
       if (lane == 0 && a0 + r < aend) out[a0 + r] = sub ? csub(out[a0 + r], v) : v;
     }

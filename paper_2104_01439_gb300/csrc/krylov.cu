@@ -55,7 +55,7 @@ __device__ __forceinline__ DF df_wsum(DF v) {
 }
 
 constexpr int kE = 8;    // basis entries per thread in the inner-product kernel
-constexpr int kGD = 4;   // basis vectors per sweep of the inner-product kernel
+constexpr int kGD = 2;   // basis vectors per sweep of the inner-product kernel
 
 // Inner products of the basis slots 0..j against two vectors in one sweep over V:
 //   s_i = <v_i, u_j>  (u_j = the once-orthogonalised vector in slot j; s_j = ||u_j||^2)
