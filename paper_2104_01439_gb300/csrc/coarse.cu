@@ -530,11 +530,13 @@ __global__ void __launch_bounds__(kFactorThreads, 1) k_factor_block(typename A::
         }
       }
     }
+    // one grid barrier per panel: after it every CTA has finished reading this panel's
+    // snapshots (R, C, the next block) and written the next panel's (Rn, Cn, the block after
+    // next, double-buffered by panel parity), and this CTA's look-ahead warps have written Pn
     if (!grid_barrier(bar, err, G)) return;
     V* tpm = Pm;   // the next panel's inverse becomes current
     Pm = Pn;
     Pn = tpm;
-    if (!grid_barrier(bar, err, G)) return;
   }
 }
 
