@@ -223,8 +223,10 @@ int setup_prec(helm_ctx* h, const std::vector<double2>& Ae, const std::vector<do
 }
 
 // One V(nu,nu)-cycle on A_eps (Algorithm 1, two levels): z = Vcycle(f), u^0 = 0.
-template <typename T>
-void enqueue_vcycle(helm_ctx* h, VecSel<const double2> f, VecSel<double2> z, const int* active,
+// f: complex128, or (complex64 form) a double-float Krylov slot read through its high
+// parts; z: complex128, or complex64 (the complex64 form's preconditioned vectors).
+template <typename T, typename Vf, typename Vz>
+void enqueue_vcycle(helm_ctx* h, VecSel<const Vf> f, VecSel<Vz> z, const int* active,
                     cudaStream_t s, Profile* prof, int ev0) {
   using V = c2<T>;
   Prec<T>& p = h->prec<T>();
@@ -241,7 +243,7 @@ void enqueue_vcycle(helm_ctx* h, VecSel<const double2> f, VecSel<double2> z, con
   } else {
     // complex64: u^1 = w D^-1 f with f converted once (the fused two-sweep kernel would
     // convert f at every neighbour on the slow double-to-float path), then one sweep
-    launch_jacobi_from_zero<T, double2>(Ae, f, nu >= 2 ? oth : cur, p.fT, false, active, s);
+    launch_jacobi_from_zero<T, Vf>(Ae, f, nu >= 2 ? oth : cur, p.fT, false, active, s);
     fT = vsel<const V>(p.fT);
     if (nu >= 2) launch_jacobi<T, V, V>(Ae, fT, oth, vsel<V>(cur), active, s);
   }
@@ -258,7 +260,7 @@ void enqueue_vcycle(helm_ctx* h, VecSel<const double2> f, VecSel<double2> z, con
   launch_prolong_add<T>(P, h->L, p.uc, cur, active, s);
   for (int it = 0; it < nu; ++it) {   // postsmoothing
     if (it == nu - 1) {
-      launch_jacobi<T, V, double2>(Ae, fT, cur, z, active, s);
+      launch_jacobi<T, V, Vz>(Ae, fT, cur, z, active, s);
     } else {
       launch_jacobi<T, V, V>(Ae, fT, cur, vsel<V>(oth), active, s);
       std::swap(cur, oth);
@@ -269,9 +271,9 @@ void enqueue_vcycle(helm_ctx* h, VecSel<const double2> f, VecSel<double2> z, con
 void enqueue_vcycle_any(helm_ctx* h, VecSel<const double2> f, VecSel<double2> z, const int* active,
                         cudaStream_t s, Profile* prof = nullptr, int ev0 = 0) {
   if (h->opts.precision == HELM_MIXED)
-    enqueue_vcycle<float>(h, f, z, active, s, prof, ev0);
+    enqueue_vcycle<float, double2, double2>(h, f, z, active, s, prof, ev0);
   else
-    enqueue_vcycle<double>(h, f, z, active, s, prof, ev0);
+    enqueue_vcycle<double, double2, double2>(h, f, z, active, s, prof, ev0);
 }
 
 // One FGMRES/Arnoldi step j (device index): z_j = Vcycle(u_j), w = A0 z_j, then the
@@ -283,12 +285,22 @@ void enqueue_iteration(helm_ctx* h, cudaStream_t s, Profile* prof = nullptr, int
   const int* act = &kb.st->pre;
   const int* jsel = &kb.st->j;
   if (prof) cudaEventRecord(prof->ev[ev0 + 0], s);
-  enqueue_vcycle_any(h, VecSel<const double2>{kb.W, 0, nullptr, 0}, VecSel<double2>{kb.Z, kb.ldN, jsel, 0},
-                     act, s, prof, ev0);
-  if (prof) cudaEventRecord(prof->ev[ev0 + 3], s);
   StencilView<double> A0 = make_view<double>(h->gf, h->coefA0, nullptr);
-  launch_apply<double, double2, double2>(A0, VecSel<const double2>{kb.Z, kb.ldN, jsel, 0},
-                                         VecSel<double2>{kb.W, 0, nullptr, 0}, act, s, kb.Ws);
+  if (h->opts.precision == HELM_MIXED) {
+    // complex64 form: the preconditioner reads slot j of the basis (high parts), z_j is
+    // complex64, and w = A0 z_j is formed in double-float from it (exact products of the
+    // complex64 z_j with the split complex128 coefficients)
+    enqueue_vcycle<float, float4, float2>(h, VecSel<const float4>{kb.Vs, kb.ldN, jsel, 0},
+                                          VecSel<float2>{kb.Z32, kb.ldN, jsel, 0}, act, s, prof, ev0);
+    if (prof) cudaEventRecord(prof->ev[ev0 + 3], s);
+    launch_apply_df(A0, VecSel<const float2>{kb.Z32, kb.ldN, jsel, 0}, kb.Ws, act, s);
+  } else {
+    enqueue_vcycle<double, double2, double2>(h, VecSel<const double2>{kb.W, 0, nullptr, 0},
+                                             VecSel<double2>{kb.Z, kb.ldN, jsel, 0}, act, s, prof, ev0);
+    if (prof) cudaEventRecord(prof->ev[ev0 + 3], s);
+    launch_apply<double, double2, double2>(A0, VecSel<const double2>{kb.Z, kb.ldN, jsel, 0},
+                                           VecSel<double2>{nullptr, 0, nullptr, 0}, act, s, kb.Ws);
+  }
   if (prof) cudaEventRecord(prof->ev[ev0 + 4], s);
   launch_arnoldi(kb, s, prof ? prof->ev[ev0 + 5] : nullptr);
   if (prof) cudaEventRecord(prof->ev[ev0 + 6], s);
@@ -515,7 +527,9 @@ size_t estimate_bytes(int dim, int order, int n, int precision, int restart) {
   const int64_t prec = v * (4 * N + 2 * nb * ldb + 2 * ldb) + 4 * 2 * ldb + 64;
   // Dinv, Lm, Up; the mixed form's segmented solve adds two product sets and one vector
   const int64_t factor = v * 3 * blk * nb + (precision == HELM_MIXED ? 8 * (2 * blk * nb + nb * ldb) : 0);
-  const int64_t krylov = 16 * ldN * (m + 1) + 16 * 3 * ldN + 16 * ldN * m + 16 * ldN +
+  // basis (double-float), w split, Z (complex64 in the mixed form), W (FP64 form), residual
+  const int64_t krylov = 16 * ldN * (m + 1) + 16 * ldN + v * ldN * m + (precision == HELM_MIXED ? 0 : 16 * ldN) +
+                         16 * ldN +
                          16 * std::max<int64_t>(nblk, (N + 255) / 256) * kb_rows((int)m) + 16 * (m + 2) * (m + 6);
   const int64_t tables = 1 << 20;
   const int64_t transient = (precision == HELM_MIXED ? 16 * blk * nb : 0) + 16 * 2 * blk +
@@ -741,9 +755,19 @@ static int setup_impl(helm_ctx* h) {
   kb.nblk_upd = (int)std::max<int64_t>(1, (kb.N + 255) / 256);
   kb.pstride = std::max(kb.nblk, std::max(kb.nblk_upd, kb.nblk_dots));
   CK(h->alloc(&kb.Vs, sizeof(float4) * kb.ldN * (m + 1)));
-  CK(h->alloc(&kb.W, sizeof(double2) * kb.ldN));
   CK(h->alloc(&kb.Ws, sizeof(float4) * kb.ldN));
-  CK(h->alloc(&kb.Z, sizeof(double2) * kb.ldN * m));
+  if (o.precision == HELM_MIXED) {
+    kb.W = nullptr;
+    kb.Z = nullptr;
+    CK(h->alloc(&kb.Z32, sizeof(float2) * kb.ldN * m));
+    CK(cudaMemsetAsync(kb.Z32, 0, sizeof(float2) * kb.ldN * m, s));
+  } else {
+    kb.Z32 = nullptr;
+    CK(h->alloc(&kb.W, sizeof(double2) * kb.ldN));
+    CK(h->alloc(&kb.Z, sizeof(double2) * kb.ldN * m));
+    CK(cudaMemsetAsync(kb.W, 0, sizeof(double2) * kb.ldN, s));
+    CK(cudaMemsetAsync(kb.Z, 0, sizeof(double2) * kb.ldN * m, s));
+  }
   CK(h->alloc(&kb.H, sizeof(double2) * (m + 1) * m));
   CK(h->alloc(&kb.cs, sizeof(double) * m));
   CK(h->alloc(&kb.sn, sizeof(double2) * m));
@@ -760,8 +784,6 @@ static int setup_impl(helm_ctx* h) {
   CK(cudaMallocHost(&h->st_h, sizeof(KState)));
   CK(cudaMallocHost(&h->err_h, sizeof(int)));
   CK(cudaMemsetAsync(kb.Vs, 0, sizeof(float4) * kb.ldN * (m + 1), s));
-  CK(cudaMemsetAsync(kb.W, 0, sizeof(double2) * kb.ldN, s));
-  CK(cudaMemsetAsync(kb.Z, 0, sizeof(double2) * kb.ldN * m, s));
   CK(cudaStreamSynchronize(s));
   return capture_iteration(h);
 }

@@ -54,6 +54,9 @@ __device__ inline float2 cvt(double2 v, float2*) { return make_float2((float)v.x
 __device__ inline double2 cvt(float2 v, double2*) { return make_double2(v.x, v.y); }
 __device__ inline float2 cvt(float2 v, float2*) { return v; }
 __device__ inline double2 cvt(double2 v, double2*) { return v; }
+// a double-float pair (hi.re, hi.im, lo.re, lo.im) read as complex64: its high parts, the
+// nearest complex64 value of a normalised pair
+__device__ inline float2 cvt(float4 v, float2*) { return make_float2(v.x, v.y); }
 template <typename To, typename From> __device__ inline To to(From v) { return cvt(v, (To*)nullptr); }
 #endif
 

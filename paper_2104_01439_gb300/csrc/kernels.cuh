@@ -24,6 +24,11 @@ template <typename V> inline VecSel<V> vsel(V* p) { return VecSel<V>{p, 0, nullp
 template <typename T, typename Vin, typename Vout>
 void launch_apply(const StencilView<T>& A, VecSel<const Vin> x, VecSel<Vout> y, const int* active,
                   cudaStream_t s, float4* ws = nullptr);   // ws: optional double-float split of y
+                                                          // (y.base null: ws only)
+// ws = A x in double-float from complex64 x and the complex128 table A (products exact to
+// the double-float rounding of the coefficients)
+void launch_apply_df(const StencilView<double>& A, VecSel<const float2> x, float4* ws, const int* active,
+                     cudaStream_t s);
 // r = f - A u
 template <typename T, typename Vf, typename Vr>
 void launch_residual(const StencilView<T>& A, VecSel<const Vf> f, const c2<T>* u, Vr* r,
@@ -144,10 +149,11 @@ struct KrylovBufs {
   // complex64 (hi + lo), 16 bytes like complex128, used by the Gram-Schmidt
   // kernels at FP32 throughput with ~48-bit accurate inner products.
   float4* Vs;      // (m+1) x ldN: (hi.re, hi.im, lo.re, lo.im) per entry
-  double2* W;      // w = A0 z_j being orthogonalised (complex128); after the step u_{j+1},
-                   // the next step's preconditioner input
-  float4* Ws;      // w split into hi + lo (read by the inner-product kernel)
-  double2* Z;      // m x ldN preconditioned vectors
+  double2* W;      // FP64 form: u_{j+1} in complex128, the next step's preconditioner input
+                   // (null in the complex64 form, whose preconditioner reads slot j + 1)
+  float4* Ws;      // w = A0 z_j as a double-float pair per entry (written by the apply)
+  double2* Z;      // m x ldN preconditioned vectors, complex128 (FP64 form), or
+  float2* Z32;     // the same in complex64 (complex64 form, where z_j is complex64 exactly)
   int64_t ldN;
   int64_t N;
   double2* H;      // (m+1) x m column-major, rotated (upper triangular R)

@@ -334,11 +334,12 @@ __global__ void __launch_bounds__(32) k_coef(KrylovBufs kb) {
   }
 }
 
-// One sweep over V[0..j-1] for both corrections of the step:
+// One sweep over V[0..j-1] for both corrections of the step, all in double-float:
 //   v_j = (u_j - sum s_i v_i) / rho          (written into slot j)
-//   w  <- w / rho - sum t'_i v_i - h_jj v_j   (complex128, FP64 subtraction; t'_i = t_i / rho)
-// and w, unnormalised, becomes u_{j+1}: slot j+1 of the basis (double-float) and the next
-// step's preconditioner input (W, complex128). Normalisation is lagged into rho.
+//   w  <- w / rho - sum t'_i v_i - h_jj v_j   (t'_i = t_i / rho)
+// and w, unnormalised, becomes u_{j+1}: slot j+1 of the basis, the next step's
+// preconditioner input (the FP64 form also gets it in complex128, W). Normalisation is
+// lagged into rho.
 // A warp takes 32 entries: its two half-warps sum over the two halves of the basis for two
 // entries per lane, meet with one shuffle, and then every lane finishes one entry.
 __global__ void __launch_bounds__(kT) k_update2(KrylovBufs kb) {
@@ -405,11 +406,10 @@ __global__ void __launch_bounds__(kT) k_update2(KrylovBufs kb) {
       *slot = v;
       dfc_mac(hjj, v, cw);
       const float4 c = dfc_fin(cw);
-      double2 w = kb.W[n];
-      w.x = fma(w.x, irho_d, -df_val(dfc_re(c)));
-      w.y = fma(w.y, irho_d, -df_val(dfc_im(c)));
-      kb.W[n] = w;
-      slot[ld] = dfc_from(w);
+      const float4 wd = kb.Ws[n];
+      const float4 w = dfc_sub(dfc_make(df_mul(dfc_re(wd), irho), df_mul(dfc_im(wd), irho)), c);
+      slot[ld] = w;
+      if (kb.W) kb.W[n] = dfc_to_double(w);   // FP64 form: the next preconditioner input
     }
   }
 }
@@ -459,8 +459,8 @@ __global__ void __launch_bounds__(kT) k_cycle_start(KrylovBufs kb, const double2
   for (int64_t n = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; n < kb.N; n += stride) {
     double2 a = r[n];
     const double2 v = make_double2(a.x * inv, a.y * inv);
-    kb.Vs[n] = dfc_from(v);   // slot 0
-    kb.W[n] = v;              // the first step's preconditioner input
+    kb.Vs[n] = dfc_from(v);   // slot 0: the first step's preconditioner input
+    if (kb.W) kb.W[n] = v;    // (in complex128 for the FP64 form)
   }
   if (blockIdx.x == 0) {
     for (int i = threadIdx.x; i <= st->m; i += blockDim.x) kb.g[i] = make_double2(i == 0 ? beta : 0.0, 0.0);
@@ -509,7 +509,10 @@ __global__ void __launch_bounds__(kT) k_update_x(KrylovBufs kb, double2* x) {
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
   for (int64_t n = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; n < kb.N; n += stride) {
     double2 a = x[n];
-    for (int i = 0; i < jj; ++i) a = cfma(ys[i], kb.Z[(int64_t)i * kb.ldN + n], a);
+    if (kb.Z32)
+      for (int i = 0; i < jj; ++i) a = cfma(ys[i], to<double2>(kb.Z32[(int64_t)i * kb.ldN + n]), a);
+    else
+      for (int i = 0; i < jj; ++i) a = cfma(ys[i], kb.Z[(int64_t)i * kb.ldN + n], a);
     x[n] = a;
   }
 }

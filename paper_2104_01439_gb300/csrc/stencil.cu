@@ -106,15 +106,62 @@ __global__ void __launch_bounds__(kThreads) k_apply(StencilView<T> s, VecSel<con
   }
   stage_tables(s, coef, (c2<T>*)nullptr, ncls);   // (ends with a block barrier)
   const Vin* x = xs.ptr();
-  Vout* y = ys.ptr();
+  Vout* y = ys.base ? ys.ptr() : nullptr;
   const int N = (int)s.g.N;
   for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < N; p += gridDim.x * blockDim.x) {
     int a[3];
     int cls = decode(s.g, p, a);
     const bool real = sizeof(T) == sizeof(double) && real_cls[cls] != 0;
     const c2<T> v = row_apply<NOFF>(s, coef + cls * NOFF, p, N, x, real);
-    y[p] = to<Vout>(v);
+    if (y) y[p] = to<Vout>(v);
     if (ws) store_split(ws, p, v);
+  }
+}
+
+// ws = A x in double-float: complex64 x (exact), complex128 coefficients split into
+// double-float pairs once per CTA; a real class takes two products per offset.
+template <int NOFF>
+__global__ void __launch_bounds__(kThreads) k_apply_df(StencilView<double> s, VecSel<const float2> xs,
+                                                        float4* __restrict__ ws, const int* active) {
+  if (active && *active == 0) return;
+  extern __shared__ __align__(16) unsigned char sm[];
+  float4* coef = reinterpret_cast<float4*>(sm);
+  __shared__ int real_cls[kMaxCls];
+  const int ncls = ncls_of(s.g);
+  for (int i = threadIdx.x; i < ncls * NOFF; i += blockDim.x) coef[i] = dfc_from(s.coef[i]);
+  if (threadIdx.x < ncls) {
+    bool r = true;
+    for (int o = 0; o < NOFF; ++o) r = r && s.coef[threadIdx.x * NOFF + o].y == 0.0;
+    real_cls[threadIdx.x] = r ? 1 : 0;
+  }
+  __syncthreads();
+  const float2* x = xs.ptr();
+  const int N = (int)s.g.N;
+  for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < N; p += gridDim.x * blockDim.x) {
+    int a[3];
+    const int cls = decode(s.g, p, a);
+    const float4* c = coef + cls * NOFF;
+    float2 xv[NOFF];
+#pragma unroll
+    for (int o = 0; o < NOFF; ++o) xv[o] = x[min(max(p + s.off[o], 0), N - 1)];
+    DFC_ACC acc{DF{0.f, 0.f}, DF{0.f, 0.f}};
+    if (real_cls[cls]) {
+#pragma unroll
+      for (int o = 0; o < NOFF; ++o) {
+        df_mac(c[o].x, c[o].z, xv[o].x, 0.f, acc.re);
+        df_mac(c[o].x, c[o].z, xv[o].y, 0.f, acc.im);
+      }
+    } else {
+#pragma unroll
+      for (int o = 0; o < NOFF; ++o) {
+        // c x = (cr xr - ci xi) + i (cr xi + ci xr)
+        df_mac(c[o].x, c[o].z, xv[o].x, 0.f, acc.re);
+        df_mac(-c[o].y, -c[o].w, xv[o].y, 0.f, acc.re);
+        df_mac(c[o].x, c[o].z, xv[o].y, 0.f, acc.im);
+        df_mac(c[o].y, c[o].w, xv[o].x, 0.f, acc.im);
+      }
+    }
+    ws[p] = dfc_fin(acc);
   }
 }
 
@@ -351,6 +398,15 @@ void launch_apply(const StencilView<T>& A, VecSel<const Vin> x, VecSel<Vout> y, 
                    (k_apply<27, T, Vin, Vout><<<g, kThreads, sm, s>>>(A, x, y, ws, active)));
 }
 
+void launch_apply_df(const StencilView<double>& A, VecSel<const float2> x, float4* ws, const int* active,
+                     cudaStream_t s) {
+  int g = grid_for(A.g.N);
+  size_t sm = table_smem<double>(A.g, false);   // 16 bytes per coefficient either way
+  HELM_SWITCH_NOFF(A.g.noff, (k_apply_df<9><<<g, kThreads, sm, s>>>(A, x, ws, active)),
+                   (k_apply_df<25><<<g, kThreads, sm, s>>>(A, x, ws, active)),
+                   (k_apply_df<27><<<g, kThreads, sm, s>>>(A, x, ws, active)));
+}
+
 template <typename T, typename Vf, typename Vr>
 void launch_residual(const StencilView<T>& A, VecSel<const Vf> f, const c2<T>* u, Vr* r,
                      const int* active, cudaStream_t s) {
@@ -410,6 +466,8 @@ void launch_coarse_unpack(const GridDesc& gc, const CoarseLayout& L, const Vin* 
 // kept as complex64; the last post-smoothing sweep writes z_j in complex128.
 template void launch_jacobi_from_zero<float, double2>(const StencilView<float>&, VecSel<const double2>,
                                                       float2*, float2*, bool, const int*, cudaStream_t);
+template void launch_jacobi_from_zero<float, float4>(const StencilView<float>&, VecSel<const float4>,
+                                                     float2*, float2*, bool, const int*, cudaStream_t);
 template void launch_residual<float, float2, float2>(const StencilView<float>&, VecSel<const float2>,
                                                      const float2*, float2*, const int*, cudaStream_t);
 template void launch_jacobi<float, float2, float2>(const StencilView<float>&, VecSel<const float2>,
