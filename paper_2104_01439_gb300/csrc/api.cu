@@ -774,6 +774,7 @@ static int setup_impl(helm_ctx* h) {
   CK(h->alloc(&kb.g, sizeof(double2) * (m + 1)));
   CK(h->alloc(&kb.y, sizeof(double2) * m));
   CK(h->alloc(&kb.zs, sizeof(double) * m));
+  CK(h->alloc(&kb.cdf, sizeof(double2) * (2 * m + 2)));
   CK(h->alloc(&kb.hcol, sizeof(double2) * (m + 2)));
   CK(h->alloc(&kb.hfin, sizeof(double2) * (m + 2)));
   CK(h->alloc(&kb.hp, sizeof(double2) * (m + 2)));

@@ -162,6 +162,7 @@ struct KrylovBufs {
   double2* g;      // m+1
   double2* y;      // m
   double* zs;      // m : scale of each preconditioned vector (1 / rho of its step)
+  double2* cdf;    // 2m + 2 (as float4): the correction sweep's coefficients in double-float
   double2* hcol;   // m+2 : the column started by the previous step (finished by this one)
   double2* hfin;   // m+2 : the finished column handed to the Givens step
   double2* hp;     // m+1 : s_i = <v_i, u_j>

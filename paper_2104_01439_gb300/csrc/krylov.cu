@@ -320,8 +320,23 @@ __global__ void __launch_bounds__(32) k_coef(KrylovBufs kb) {
   d = wsum(d);
   const double i2 = irho * irho;
   const double2 hjj = make_double2((s_t[j].x - d.x) * i2, (s_t[j].y - d.y) * i2);
-  for (int i = lane; i < j; i += 32) kb.hcol[i] = make_double2(s_t[i].x * irho, s_t[i].y * irho);
+  // the correction sweep's coefficients as double-float pairs (re.h, re.l, im.h, im.l):
+  // [0, j) s_i, [j, 2j) t_i / rho, then h_jj and 1 / rho
+  float4* cdf = reinterpret_cast<float4*>(kb.cdf);
+  for (int i = lane; i < j; i += 32) {
+    const double2 tn = make_double2(s_t[i].x * irho, s_t[i].y * irho);
+    kb.hcol[i] = tn;
+    DF a = df_split(s_s[i].x), b = df_split(s_s[i].y);
+    cdf[i] = make_float4(a.h, a.l, b.h, b.l);
+    a = df_split(tn.x);
+    b = df_split(tn.y);
+    cdf[j + i] = make_float4(a.h, a.l, b.h, b.l);
+  }
   if (lane == 0) {
+    DF a = df_split(hjj.x), b = df_split(hjj.y);
+    cdf[2 * j] = make_float4(a.h, a.l, b.h, b.l);
+    a = df_split(irho);
+    cdf[2 * j + 1] = make_float4(a.h, a.l, 0.f, 0.f);
     kb.zs[j] = irho;
     kb.hcol[j] = hjj;
     st->hjj = hjj;
@@ -348,15 +363,12 @@ __global__ void __launch_bounds__(kT) k_update2(KrylovBufs kb) {
   const int j = st->ju;
   const int64_t N = kb.N, ld = kb.ldN;
   extern __shared__ float4 hs4[];   // [0, j): s_i, [j, 2j): t_i as (re.h, re.l, im.h, im.l)
-  const double irho_d = st->irho;
-  for (int i = threadIdx.x; i < 2 * j; i += blockDim.x) {
-    const double2 c = i < j ? kb.hp[i] : kb.hcol[i - j];   // s_i, and t_i / rho from the new column
-    DF r = df_split(c.x), q = df_split(c.y);
-    hs4[i] = make_float4(r.h, r.l, q.h, q.l);
-  }
-  const DF irho = df_split(irho_d);
-  const double2 hjj_d = st->hjj;
-  const float4 hjj = dfc_from(hjj_d);
+  // s_i, t_i / rho, h_jj, 1 / rho as double-float pairs, prepared by the coefficient kernel
+  const float4* cdf = reinterpret_cast<const float4*>(kb.cdf);
+  for (int i = threadIdx.x; i < 2 * j; i += blockDim.x) hs4[i] = cdf[i];
+  const float4 hq = cdf[2 * j], iq = cdf[2 * j + 1];
+  const DF irho{iq.x, iq.y};
+  const float4 hjj = make_float4(hq.x, hq.z, hq.y, hq.w);   // (hr, hi, lr, li) layout
   __syncthreads();
   const int lane = threadIdx.x & 31, half = lane >> 4;
   const int split = (j + 1) / 2;   // slots [0, split) and [split, j)
