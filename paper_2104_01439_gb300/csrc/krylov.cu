@@ -62,7 +62,7 @@ constexpr int kGD = 2;   // basis vectors per sweep of the inner-product kernel
 //   t_i = <v_i, w>    (w = A0 z_j; only when this step applies the preconditioner)
 // Grid: x over chunks of the vectors (kE entries per thread), y over groups of kGD basis
 // slots, so every (chunk, group) pair is its own block. Block partials stay double-float.
-__global__ void __launch_bounds__(kT) k_dots2(KrylovBufs kb) {
+__global__ void __launch_bounds__(kT, 5) k_dots2(KrylovBufs kb) {
   KState* st = kb.st;
   if (!st->active) return;
   const int j = st->j, m = st->m;
@@ -357,7 +357,7 @@ __global__ void __launch_bounds__(32) k_coef(KrylovBufs kb) {
 // lagged into rho.
 // A warp takes 32 entries: its two half-warps sum over the two halves of the basis for two
 // entries per lane, meet with one shuffle, and then every lane finishes one entry.
-__global__ void __launch_bounds__(kT) k_update2(KrylovBufs kb) {
+__global__ void __launch_bounds__(kT, 5) k_update2(KrylovBufs kb) {
   KState* st = kb.st;
   if (!st->active) return;
   const int j = st->ju;
