@@ -665,7 +665,7 @@ struct SolveGeom {
 };
 
 template <typename T>
-SolveGeom solve_geometry(const CoarseLayout& L, int CS, int CW, int S) {
+SolveGeom solve_geometry(const CoarseLayout& L, int CS, int CW, int S, bool with_w = true) {
   using V = c2<T>;
   SolveGeom G;
   G.R = (L.B + CS - 1) / CS;
@@ -677,7 +677,7 @@ SolveGeom solve_geometry(const CoarseLayout& L, int CS, int CW, int S) {
   G.off_mbar = o; o = al(o + 16 * S);   // full [S], empty [S]
   G.off_misc = o; o = al(o + 32);       // receive mbarriers [2] (+0, +8), error word (+16)
   G.off_gath = o; o = al(o + sizeof(V) * 2 * L.ldb);
-  G.off_w = o; o = al(o + sizeof(V) * (size_t)L.nb * G.R);
+  G.off_w = o; o = al(o + (with_w ? sizeof(V) * (size_t)L.nb * G.R : 0));   // forward values (twisted kernel)
   G.off_stage = o; o = al(o + sizeof(V) * (size_t)S * G.R * CW);
   G.total = o;
   return G;
@@ -685,6 +685,7 @@ SolveGeom solve_geometry(const CoarseLayout& L, int CS, int CW, int S) {
 
 constexpr int kRPW = 4;          // max rows of the CTA slice per consumer warp (registers)
 constexpr int kSegMaxLdb = 1040;   // block row length up to which the segmented solve applies
+constexpr int kSegClusterFirst = 8;   // cluster size tried first for the segment chains (8 or 16)
 constexpr int kSolveMaxWarps = 18;   // consumer warps + 1 producer warp
 
 // mbarrier arrive (release, CTA scope)
@@ -1309,6 +1310,81 @@ int plan_coarse_solve(const CoarseLayout& L, CoarsePlan* plan) {
   cudaFuncSetAttribute(k_coarse_solve<T, kRPW>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
   cudaFuncSetAttribute(k_seg_chain<T, 1>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
   cudaFuncSetAttribute(k_seg_chain<T, kRPW>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+  // complex64 solves of long chains: segmented recurrences on the four half-sweeps of the
+  // twisted form, one co-resident cluster per segment in phase A. Eight-CTA clusters give
+  // twice as many concurrent segments as sixteen-CTA ones for a slower step.
+  if (sizeof(T) == sizeof(float) && L.nb >= 16 && L.ldb <= kSegMaxLdb) {
+    // widest chunk and deepest ring that fit, for a cluster of CS CTAs; returns the number of
+    // co-resident clusters (0 if none fits)
+    auto seg_geom = [&](int CS, int* R, int* CW, int* nchunk, int* S, size_t* smem, int* threads) -> int {
+      const int Rr = (L.B + CS - 1) / CS;
+      const int nwc = std::min(kSolveMaxWarps - 1, std::max(4, Rr));
+      if ((Rr + nwc - 1) / nwc > kRPW) return 0;
+      const bool one = (Rr + nwc - 1) / nwc == 1;
+      auto kern = one ? k_seg_chain<T, 1> : k_seg_chain<T, kRPW>;
+      cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)budget);
+      for (int cw = L.ldb; cw >= 2; cw = ((cw / 2) + 1) & ~1) {
+        for (int st = 4; st >= 2; --st) {
+          SolveGeom G = solve_geometry<T>(L, CS, cw, st, false);
+          if (G.total > budget) continue;
+          cudaLaunchConfig_t cfg = {};
+          cfg.gridDim = dim3(CS);
+          cfg.blockDim = dim3(32 * (nwc + 1));
+          cfg.dynamicSmemBytes = G.total;
+          cudaLaunchAttribute at[1];
+          at[0].id = cudaLaunchAttributeClusterDimension;
+          at[0].val.clusterDim.x = CS;
+          at[0].val.clusterDim.y = 1;
+          at[0].val.clusterDim.z = 1;
+          cfg.attrs = at;
+          cfg.numAttrs = 1;
+          int ncl = 0;
+          if (cudaOccupancyMaxActiveClusters(&ncl, (void*)kern, &cfg) != cudaSuccess || ncl < 1) {
+            cudaGetLastError();
+            continue;
+          }
+          *R = G.R;
+          *CW = cw;
+          *nchunk = G.nchunk;
+          *S = st;
+          *smem = G.total;
+          *threads = 32 * (nwc + 1);
+          return ncl;
+        }
+        if (cw == 2) break;
+      }
+      return 0;
+    };
+    // phase A: eight-CTA clusters give twice as many concurrent segments as sixteen-CTA ones
+    // for a slower step; phase B (two clusters) takes the fastest step
+    for (int CS : {kSegClusterFirst, 24 - kSegClusterFirst}) {
+      const int ncl = seg_geom(CS, &plan->R, &plan->CW, &plan->nchunk, &plan->S, &plan->smem, &plan->threads);
+      if (ncl < 4) continue;
+      plan->CS = CS;
+      plan->seg = 1;
+      plan->ncl = 2;          // twisted factorisation (mid = nb / 2)
+      plan->K = ncl / 2;      // phase-A clusters per path
+      plan->CSb = CS;
+      plan->Rb = plan->R;
+      plan->CWb = plan->CW;
+      plan->nchunkb = plan->nchunk;
+      plan->Sb = plan->S;
+      plan->smemb = plan->smem;
+      plan->threadsb = plan->threads;
+      int Rb, CWb, nchunkb, Sb, threadsb;
+      size_t smemb;
+      if (CS != 16 && seg_geom(16, &Rb, &CWb, &nchunkb, &Sb, &smemb, &threadsb) >= 2) {
+        plan->CSb = 16;
+        plan->Rb = Rb;
+        plan->CWb = CWb;
+        plan->nchunkb = nchunkb;
+        plan->Sb = Sb;
+        plan->smemb = smemb;
+        plan->threadsb = threadsb;
+      }
+      return HELM_OK;
+    }
+  }
   for (int CS : {16, 8, 4, 2, 1}) {
     const int R = (L.B + CS - 1) / CS;
     // one consumer warp per row of the CTA's slice (up to kRPW rows per warp) + a producer
@@ -1351,14 +1427,6 @@ int plan_coarse_solve(const CoarseLayout& L, CoarsePlan* plan) {
         plan->smem = G.total;
         plan->threads = 32 * nwarps;
         plan->ncl = 1;
-        // complex64 solves of long chains: segmented recurrences on the four half-sweeps of
-        // the twisted form, one co-resident cluster per segment in phase A
-        if (sizeof(T) == sizeof(float) && L.nb >= 16 && L.ldb <= kSegMaxLdb && ncl >= 4) {
-          plan->seg = 1;
-          plan->ncl = 2;           // twisted factorisation (mid = nb / 2)
-          plan->K = ncl / 2;       // phase-A clusters per path
-          return HELM_OK;
-        }
         // Twisted form: two co-resident clusters (cooperative launch). Validated once per
         // launch shape by an inert trial launch whose 'active' flag is 0 (the kernel
         // returns at entry); the answer is cached (the trial synchronises the device).
@@ -1431,18 +1499,21 @@ void launch_coarse_solve(const CoarsePlan& plan, const c2<T>* Dinv, const c2<T>*
   else
     k_block_gemv_wide<T><<<nsm * 8, 256, 0, s>>>(Dinv, rc, uc, L, active);
   if (plan.seg && seg) {
-    SolveGeom G = solve_geometry<T>(L, plan.CS, plan.CW, plan.S);
-    const int nwc = plan.threads / 32 - 1;
-    auto kern = (plan.R + nwc - 1) / nwc == 1 ? k_seg_chain<T, 1> : k_seg_chain<T, kRPW>;
+    // phase A (a.phase == 0) and phase B launch with their own cluster geometries
     auto chain = [&](const SegArgs<T>& a, int nclusters) {
+      const bool b = a.phase == 1;
+      const int CS = b ? plan.CSb : plan.CS, R = b ? plan.Rb : plan.R, threads = b ? plan.threadsb : plan.threads;
+      SolveGeom G = solve_geometry<T>(L, CS, b ? plan.CWb : plan.CW, b ? plan.Sb : plan.S, false);
+      const int nwc = threads / 32 - 1;
+      auto kern = (R + nwc - 1) / nwc == 1 ? k_seg_chain<T, 1> : k_seg_chain<T, kRPW>;
       cudaLaunchConfig_t cfg = {};
-      cfg.gridDim = dim3(plan.CS * nclusters);
-      cfg.blockDim = dim3(plan.threads);
+      cfg.gridDim = dim3(CS * nclusters);
+      cfg.blockDim = dim3(threads);
       cfg.dynamicSmemBytes = G.total;
       cfg.stream = s;
       cudaLaunchAttribute at[1];
       at[0].id = cudaLaunchAttributeClusterDimension;
-      at[0].val.clusterDim.x = plan.CS;
+      at[0].val.clusterDim.x = CS;
       at[0].val.clusterDim.y = 1;
       at[0].val.clusterDim.z = 1;
       cfg.attrs = at;

@@ -72,6 +72,9 @@ struct CoarsePlan {
   int threads;
   int seg;      // 1: segmented triangular solves (complex64, twisted factorisation)
   int K;        // phase-A clusters (segments) per half-sweep path
+  // phase B of the segmented solve (two clusters): its own cluster geometry
+  int CSb, Rb, CWb, nchunkb, Sb, threadsb;
+  size_t smemb;
 };
 // Workspaces of the segmented solve: yb one block-padded coarse vector; Pf, Pb the
 // segment products of the forward and backward sweeps, nb x B x ldb each, by block.
