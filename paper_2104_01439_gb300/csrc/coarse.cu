@@ -458,13 +458,6 @@ __global__ void __launch_bounds__(kFactorThreads, 1) k_factor_block(typename A::
       if (threadIdx.x == 0) atomicCAS(err, 0, HELM_EZEROPIVOT);
       return;   // every CTA sees the same pivot block and returns
     }
-    // stage the pivot rows in shared memory when they fit
-    const V* Rs = R;
-    if (stageR) {
-      for (int t = threadIdx.x; t < p * B; t += blockDim.x) Rsm[(t / B) * ldb + t % B] = R[(int64_t)(t / B) * ldb + t % B];
-      __syncthreads();
-      Rs = Rsm;
-    }
     if (look) {
       // ---- look-ahead: the next panel's pivot block after this panel's update, formed
       // with the same operations as the update below, then inverted into Pn
@@ -476,8 +469,10 @@ __global__ void __launch_bounds__(kFactorThreads, 1) k_factor_block(typename A::
         }
         named_sync(1, kLookThreads);
         if (ta < pn1 && tb < pn1) {
+          // the pivot rows' block columns straight from the snapshot (the update warps stage
+          // the full rows in shared memory for themselves)
           typename A::Acc acc = A::acc(snapn[ta * P + tb]);
-          for (int s2 = 0; s2 < p; ++s2) A::fnmac(cpl[ta * P + s2], Rs[s2 * ldb + k1 + tb], acc);
+          for (int s2 = 0; s2 < p; ++s2) A::fnmac(cpl[ta * P + s2], R[(int64_t)s2 * ldb + k1 + tb], acc);
           Pn[ta * P + tb] = A::fin(acc);
         }
         named_sync(1, kLookThreads);
@@ -486,6 +481,12 @@ __global__ void __launch_bounds__(kFactorThreads, 1) k_factor_block(typename A::
     } else {
       // ---- update warps
       const int tu = threadIdx.x - kLookThreads, nu = blockDim.x - kLookThreads;
+      // stage the pivot rows in shared memory when they fit
+      const V* Rs = R;
+      if (stageR) {
+        for (int t = tu; t < p * B; t += nu) Rsm[(t / B) * ldb + t % B] = R[(int64_t)(t / B) * ldb + t % B];
+        Rs = Rsm;   // (published by the named barrier below)
+      }
       // (2) C_i Pb^{-1} for the rows this CTA touches (non-pivot rows)
       for (int t = tu; t < (i1 - i0 + 1) * p; t += nu) {
         int r = t / p, c = t % p, i = i0 + r;
@@ -495,17 +496,17 @@ __global__ void __launch_bounds__(kFactorThreads, 1) k_factor_block(typename A::
         cP[r * P + c] = acc;
       }
       named_sync(2, nu);
-      // (3) element update over the CTA's row-major range, row by row (no per-element division)
-      for (int i = i0; i <= i1; ++i) {
-        const int jb = i == i0 ? (int)(e0 - (int64_t)i0 * B) : 0;
-        const int je = i == i1 ? (int)(e1 - (int64_t)i1 * B) : B;
-        V* Si = S + (int64_t)i * ldb;
-        const bool pivrow = i >= k0 && i < k1;
-        const V* pr = Pm + (i - k0) * P;          // row of Pb^{-1} (pivot rows)
-        const V* ci = cP + (i - i0) * P;          // C_i Pb^{-1} (other rows)
-        V* rn = (i >= k1 && i < k2) ? Rn + (int64_t)(i - k1) * ldb : nullptr;
-        const bool nnrow = i >= k2 && i < k3;
-        for (int j = jb + tu; j < je; j += nu) {
+      // (3) element update over the CTA's row-major range, every update thread on its own
+      // elements (a row has fewer elements than there are update threads)
+      for (int e = (int)e0 + tu; e < (int)e1; e += nu) {
+        {
+          const int i = e / B, j = e - i * B;
+          V* Si = S + (int64_t)i * ldb;
+          const bool pivrow = i >= k0 && i < k1;
+          const V* pr = Pm + (i - k0) * P;          // row of Pb^{-1} (pivot rows)
+          const V* ci = cP + (i - i0) * P;          // C_i Pb^{-1} (other rows)
+          V* rn = (i >= k1 && i < k2) ? Rn + (int64_t)(i - k1) * ldb : nullptr;
+          const bool nnrow = i >= k2 && i < k3;
           V nv;
           const bool pcol = j >= k0 && j < k1;
           if (pivrow) {
