@@ -86,10 +86,15 @@ struct GridDesc {
   int64_t N;    // W^dim
 };
 
+// division and remainder by a small lattice period or transfer period (1, 2 and 4 are the
+// periods of P1 and P2; they take shifts instead of an integer division)
+__host__ __device__ inline int div_period(int a, int d) { return d == 1 ? a : d == 2 ? a >> 1 : d == 4 ? a >> 2 : a / d; }
+__host__ __device__ inline int mod_period(int a, int d) { return d == 1 ? 0 : d == 2 ? a & 1 : d == 4 ? a & 3 : a % d; }
+
 __host__ __device__ inline int axis_class(int a, int W, int R, int q) {
   if (a < R) return a;
   if (a >= W - R) return R + q + (a - (W - R));
-  return R + (a % q);
+  return R + mod_period(a, q);
 }
 
 // Device view of one operator's stencil table: coef[cls * noff + o].

@@ -269,9 +269,9 @@ __global__ void __launch_bounds__(kThreads) k_prolong_add(TransferView<T> P, Coa
     decode(P.fine, p, a);
     int cls = 0, mul = 1, anc[3];
     for (int ax = 0; ax < P.fine.dim; ++ax) {
-      cls += (a[ax] % P.pf) * mul;
+      cls += mod_period(a[ax], P.pf) * mul;
       mul *= P.pf;
-      anc[ax] = (a[ax] / P.pf) * q;
+      anc[ax] = div_period(a[ax], P.pf) * q;
     }
     c2<T> acc = mk(T(0), T(0));
     for (int o = 0; o < P.npo; ++o) {
@@ -313,9 +313,9 @@ __global__ void __launch_bounds__(kThreads) k_restrict(TransferView<T> P, Coarse
       int lo[3], hi[3];
       for (int ax = 0; ax < 3; ++ax) {
         if (ax < d) {
-          int cmin = (A[ax] + q - 1) / q - 1;   // ceil((A-q)/q) for A >= 0
+          int cmin = div_period(A[ax] + q - 1, q) - 1;   // ceil((A-q)/q) for A >= 0
           lo[ax] = max(0, pf * cmin);
-          hi[ax] = min(Wf - 1, pf * (A[ax] / q) + pf - 1);
+          hi[ax] = min(Wf - 1, pf * div_period(A[ax], q) + pf - 1);
         } else {
           lo[ax] = hi[ax] = 0;
         }
@@ -327,9 +327,9 @@ __global__ void __launch_bounds__(kThreads) k_restrict(TransferView<T> P, Coarse
             int cls = 0, mul = 1, o = 0, omul = 1;
             bool ok = true;
             for (int ax = 0; ax < d; ++ax) {
-              cls += (a[ax] % pf) * mul;
+              cls += mod_period(a[ax], pf) * mul;
               mul *= pf;
-              int oo = A[ax] - (a[ax] / pf) * q;
+              int oo = A[ax] - div_period(a[ax], pf) * q;
               ok &= (oo >= 0 && oo <= q);
               o += oo * omul;
               omul *= q + 1;
