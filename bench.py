@@ -51,6 +51,8 @@ def workload_config(prec_name):
 
 # ---------------------------------------------------------------------------- helpers
 
+COARSE_TRAFFIC_BYTES = 646.7e6   # see the roofline object in run_ours
+
 # stencil kernels at a size above L2: 2D P1, h = 1/4096 (16.8 M DoFs; one complex128
 # vector is 268 MB, twice the 129 MB L2), same kh and shift exponent as the solve workload
 STENCIL_N = 4096
@@ -381,7 +383,11 @@ def run_ours(args):
     bytes_coarse = (2 * Wc - 1) * Wc * Wc * 8
     phase_ms = {k: v[0] / max(v[1], 1) for k, v in prof.items()}
     achieved = bytes_coarse / (phase_ms["coarse_solve"] * 1e-3) / 1e9
-    traffic = None   # the cluster chain kernels are kept out of multi-pass ncu captures
+    # DRAM bytes of one coarse solve at this workload (dram__bytes_read.sum + dram__bytes_write.sum
+    # of k_block_gemv, the four k_seg_chain launches, the two k_seg_fixup launches and k_seg_middle,
+    # one-pass ncu capture of `bench.py --kernel coarse`): the dense inverses and segment products
+    # read once each
+    traffic = COARSE_TRAFFIC_BYTES
     # stencil kernels: outer apply reads z and writes w (32 B/DoF, complex128); the fine level of
     # the V-cycle moves >= 52 B/DoF (read v_j 16, u 8 + 8, write z_j 16, transfers ~4)
     n_f = WL.num_dofs
