@@ -12,19 +12,21 @@
 // Im(x^H A x) < 0 for every leading block, so all Schur complements are
 // invertible (an ADR-style argument); a zero/non-finite pivot is reported.
 //
-// Factorisation: one cooperative grid per block; the Schur update uses the
-// sparse couplings straight from the coarse stencil; the inverse is formed by
-// in-place Gauss-Jordan with one grid barrier per pivot (pivot row double
-// buffered in global memory). FP64 on GB300 is ALU-bound, so all SMs work on
-// each block.
+// Factorisation: one cooperative grid per block step (the two chains of the twisted
+// elimination on the two halves of the grid); the Schur update uses the sparse couplings
+// straight from the coarse stencil; the inverse is formed by in-place blocked Gauss-Jordan
+// (P pivots per panel, one grid barrier per panel, the next panel's pivot block inverted
+// ahead by a warp group while the others update). FP64 on GB300 is ALU-bound, so all SMs
+// work on each block; the complex64 form factors in double-float.
 //
-// Solve: one thread-block cluster (16 CTAs where the device allows, else 8).
-// CTA c owns rows [cR, cR+R) of every Dinv[J]; those rows are streamed through
-// a multi-stage shared-memory ring by bulk TMA copies (cp.async.bulk +
-// mbarrier complete_tx), so a step's GEMV reads shared memory only. After the
-// GEMV each CTA broadcasts its R results into every CTA's shared memory
-// (st.shared::cluster), one cluster barrier ends the step, and each CTA then
-// applies the sparse coupling for the next block locally.
+// Solve: the couplings are folded into the inverses (Lm, Up) and the right-hand side part
+// Dinv r of every block is formed first, so each dependent step is one dense GEMV.
+// Chain kernels run on thread-block clusters: CTA c owns rows [cR, cR+R) of every matrix,
+// streamed through a multi-stage shared-memory ring by bulk copies (cp.async.bulk +
+// mbarrier complete_tx), and each CTA pushes its R results into every CTA's shared memory
+// with st.async. FP64 form: two clusters run the two chains of the twisted form. Complex64
+// form: each half-sweep is cut into segments (segmented recurrences, see k_seg_chain).
+// Blocks too large for a cluster (3D planes): one chain over the cooperative grid.
 #include <algorithm>
 #include <mutex>
 #include <unordered_map>
@@ -686,7 +688,7 @@ SolveGeom solve_geometry(const CoarseLayout& L, int CS, int CW, int S, bool with
 
 constexpr int kRPW = 4;          // max rows of the CTA slice per consumer warp (registers)
 constexpr int kSegMaxLdb = 1040;   // block row length up to which the segmented solve applies
-constexpr int kSegClusterFirst = 8;   // cluster size tried first for the segment chains (8 or 16)
+constexpr int kSegClusterA[2] = {8, 16};   // cluster sizes tried for the segment chains, in order
 constexpr int kSolveMaxWarps = 18;   // consumer warps + 1 producer warp
 
 // mbarrier arrive (release, CTA scope)
@@ -1358,7 +1360,7 @@ int plan_coarse_solve(const CoarseLayout& L, CoarsePlan* plan) {
     };
     // phase A: eight-CTA clusters give twice as many concurrent segments as sixteen-CTA ones
     // for a slower step; phase B (two clusters) takes the fastest step
-    for (int CS : {kSegClusterFirst, 24 - kSegClusterFirst}) {
+    for (int CS : kSegClusterA) {
       const int ncl = seg_geom(CS, &plan->R, &plan->CW, &plan->nchunk, &plan->S, &plan->smem, &plan->threads);
       if (ncl < 4) continue;
       plan->CS = CS;

@@ -86,9 +86,10 @@ template <typename T> struct SegBufs {
 template <typename T>
 int plan_coarse_solve(const CoarseLayout& L, CoarsePlan* plan);
 // uc = A^{-1} rc for the block-padded coarse vectors (uc also holds the block-diagonal
-// pre-pass p = Dinv r). L.mid < L.nb - 1 runs the twisted form on two clusters
-// (xmid: 2 x ldb values, xflag: 2 x ldb ints of exchange space); bar: kBarWords unsigned for
-// the grid kernel's barrier.
+// pre-pass p = Dinv r). plan.seg with seg given: the segmented half-sweeps of the twisted
+// form (seg->yb holds the forward sweep). Otherwise L.mid < L.nb - 1 runs the twisted form
+// on two clusters (xmid: 2 x ldb values, xflag: 2 x ldb ints of exchange space); bar:
+// kBarWords unsigned for the grid kernel's barrier.
 template <typename T>
 void launch_coarse_solve(const CoarsePlan& plan, const c2<T>* Dinv, const c2<T>* Lm, const c2<T>* Up,
                          const CoarseLayout& L, const c2<T>* rc, c2<T>* uc, c2<T>* xmid, int* xflag,
