@@ -28,6 +28,7 @@ namespace helm {
 namespace {
 
 constexpr int kT = 256;
+constexpr int kMaxRestart = 512;   // helm_opts.restart <= 512
 constexpr int kG = 8;   // basis vectors per sweep
 
 __device__ __forceinline__ double2 wsum(double2 v) {
@@ -511,20 +512,33 @@ __global__ void __launch_bounds__(kT) k_backsolve(KrylovBufs kb) {
   }
 }
 
-// x += sum_i y_i Z[i]
+// x += sum_i y_i Z[i]; complex64 Z: the sum in double-float (y_i split once per block,
+// exact products with the complex64 entries), converted to complex128 once per entry
 __global__ void __launch_bounds__(kT) k_update_x(KrylovBufs kb, double2* x) {
   KState* st = kb.st;
   const int jj = st->j;
   extern __shared__ double2 ys[];
-  for (int i = threadIdx.x; i < jj; i += blockDim.x) ys[i] = kb.y[i];
+  float4* yd = reinterpret_cast<float4*>(ys + kMaxRestart);
+  for (int i = threadIdx.x; i < jj; i += blockDim.x) {
+    ys[i] = kb.y[i];
+    yd[i] = dfc_from(kb.y[i]);
+  }
   __syncthreads();
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
   for (int64_t n = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; n < kb.N; n += stride) {
     double2 a = x[n];
-    if (kb.Z32)
-      for (int i = 0; i < jj; ++i) a = cfma(ys[i], to<double2>(kb.Z32[(int64_t)i * kb.ldN + n]), a);
-    else
+    if (kb.Z32) {
+      DFC_ACC acc{DF{0.f, 0.f}, DF{0.f, 0.f}};
+      for (int i = 0; i < jj; ++i) {
+        const float2 z = kb.Z32[(int64_t)i * kb.ldN + n];
+        dfc_mac(yd[i], make_float4(z.x, z.y, 0.f, 0.f), acc);
+      }
+      const double2 d = dfc_to_double(dfc_fin(acc));
+      a.x += d.x;
+      a.y += d.y;
+    } else {
       for (int i = 0; i < jj; ++i) a = cfma(ys[i], kb.Z[(int64_t)i * kb.ldN + n], a);
+    }
     x[n] = a;
   }
 }
@@ -546,7 +560,7 @@ void launch_cycle_start(const KrylovBufs& kb, const double2* r, cudaStream_t s) 
 void launch_backsolve(const KrylovBufs& kb, cudaStream_t s) { k_backsolve<<<1, kT, 0, s>>>(kb); }
 
 void launch_update_x(const KrylovBufs& kb, double2* x, cudaStream_t s) {
-  k_update_x<<<kb.nblk, kT, sizeof(double2) * 512, s>>>(kb, x);
+  k_update_x<<<kb.nblk, kT, (sizeof(double2) + sizeof(float4)) * kMaxRestart, s>>>(kb, x);
 }
 
 void launch_norm(const KrylovBufs& kb, const double2* v, int which, cudaStream_t s) {
