@@ -55,9 +55,10 @@ extern "C" {
 /* ---- precision of the preconditioner (opts.precision) ---------------- */
 #define HELM_FP64 0          /* everything in complex128 */
 #define HELM_MIXED 1         /* V-cycle (smoother, transfers, coarse triangular
-                                solves) in complex64; outer apply, Arnoldi,
-                                Givens, true residual and the coarse
-                                factorisation in complex128 */
+                                solves) in complex64; outer apply, Arnoldi basis
+                                and coarse factorisation in double-float pairs
+                                (~48 significant bits); Hessenberg, Givens and the
+                                true residual in complex128 */
 
 typedef struct helm_ctx* helm_t;
 
@@ -66,14 +67,16 @@ typedef struct {
   double omega;     /* Jacobi damping (paper: 2/3, Sec. 4; default 0.6)   */
   int nu;           /* pre- and post-smoothing steps of V(nu,nu), 1..8    */
   int restart;      /* FGMRES restart length m, 1..512                    */
-  int maxit;        /* cap on total Arnoldi steps (paper: 500, Sec. 6)    */
+  int maxit;        /* cap on total Arnoldi columns (paper: 500, Sec. 6)  */
   double tol;       /* on the TRUE relative residual ||F - A0 x||/||F||   */
   int precision;    /* HELM_FP64 or HELM_MIXED                            */
   void* stream;     /* cudaStream_t for all work of this handle (NULL = legacy default) */
 } helm_opts;
 
 typedef struct {
-  int iters;            /* total Arnoldi steps = preconditioner applications */
+  int iters;            /* total finished Arnoldi columns (each one preconditioner
+                           application; the orthogonalisation finishes a column one
+                           step late, so a converged cycle may apply it once more) */
   int cycles;           /* FGMRES cycles (restarts + 1)                      */
   int status;           /* HELM_CONVERGED / HELM_MAXIT / HELM_BREAKDOWN / HELM_NONFINITE */
   double relres_true;   /* ||F - A0 x|| / ||F|| recomputed in FP64 at the end */
