@@ -688,7 +688,8 @@ SolveGeom solve_geometry(const CoarseLayout& L, int CS, int CW, int S, bool with
 
 constexpr int kRPW = 4;          // max rows of the CTA slice per consumer warp (registers)
 constexpr int kSegMaxLdb = 1040;   // block row length up to which the segmented solve applies
-constexpr int kSegClusterA[2] = {8, 16};   // cluster sizes tried for the segment chains, in order
+constexpr int kSegClusterA[3] = {9, 8, 16};   // cluster sizes tried for the segment chains, in order
+constexpr int kSegWideWarps = 32;   // one row per warp for slices of 18..31 rows (64 registers)
 constexpr int kSolveMaxWarps = 18;   // consumer warps + 1 producer warp
 
 // mbarrier arrive (release, CTA scope)
@@ -958,8 +959,8 @@ template <typename T> struct SegArgs {
 __host__ __device__ __forceinline__ int seg_end(int k, int Ls, int n) { return min((k + 1) * Ls, n) - 1; }
 __host__ __device__ __forceinline__ int path_block(const SegPath& p, int q) { return p.J0 + p.step * q; }
 
-template <typename T, int RPW>
-__global__ void __launch_bounds__(kSolveMaxWarps * 32, 1)
+template <typename T, int RPW, int MAXW = kSolveMaxWarps>
+__global__ void __launch_bounds__(MAXW * 32, 1)
     k_seg_chain(SegArgs<T> a, CoarseLayout L, SolveGeom G, int* err, const int* active) {
   using V = c2<T>;
   if (active && *active == 0) return;
@@ -1313,6 +1314,7 @@ int plan_coarse_solve(const CoarseLayout& L, CoarsePlan* plan) {
   cudaFuncSetAttribute(k_coarse_solve<T, kRPW>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
   cudaFuncSetAttribute(k_seg_chain<T, 1>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
   cudaFuncSetAttribute(k_seg_chain<T, kRPW>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+  cudaFuncSetAttribute(k_seg_chain<T, 1, kSegWideWarps>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
   // complex64 solves of long chains: segmented recurrences on the four half-sweeps of the
   // twisted form, one co-resident cluster per segment in phase A. Eight-CTA clusters give
   // twice as many concurrent segments as sixteen-CTA ones for a slower step.
@@ -1321,10 +1323,13 @@ int plan_coarse_solve(const CoarseLayout& L, CoarsePlan* plan) {
     // co-resident clusters (0 if none fits)
     auto seg_geom = [&](int CS, int* R, int* CW, int* nchunk, int* S, size_t* smem, int* threads) -> int {
       const int Rr = (L.B + CS - 1) / CS;
-      const int nwc = std::min(kSolveMaxWarps - 1, std::max(4, Rr));
+      // one consumer warp per row where the slice allows (slices of up to kSegWideWarps - 1
+      // rows take the wide kernel), else up to kRPW rows per warp
+      const bool wide = Rr >= kSolveMaxWarps && Rr < kSegWideWarps;
+      const int nwc = wide ? Rr : std::min(kSolveMaxWarps - 1, std::max(4, Rr));
       if ((Rr + nwc - 1) / nwc > kRPW) return 0;
       const bool one = (Rr + nwc - 1) / nwc == 1;
-      auto kern = one ? k_seg_chain<T, 1> : k_seg_chain<T, kRPW>;
+      auto kern = wide ? k_seg_chain<T, 1, kSegWideWarps> : one ? k_seg_chain<T, 1> : k_seg_chain<T, kRPW>;
       cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)budget);
       for (int cw = L.ldb; cw >= 2; cw = ((cw / 2) + 1) & ~1) {
         for (int st = 4; st >= 2; --st) {
@@ -1508,7 +1513,9 @@ void launch_coarse_solve(const CoarsePlan& plan, const c2<T>* Dinv, const c2<T>*
       const int CS = b ? plan.CSb : plan.CS, R = b ? plan.Rb : plan.R, threads = b ? plan.threadsb : plan.threads;
       SolveGeom G = solve_geometry<T>(L, CS, b ? plan.CWb : plan.CW, b ? plan.Sb : plan.S, false);
       const int nwc = threads / 32 - 1;
-      auto kern = (R + nwc - 1) / nwc == 1 ? k_seg_chain<T, 1> : k_seg_chain<T, kRPW>;
+      auto kern = nwc >= kSolveMaxWarps ? k_seg_chain<T, 1, kSegWideWarps>
+                  : (R + nwc - 1) / nwc == 1 ? k_seg_chain<T, 1>
+                                             : k_seg_chain<T, kRPW>;
       cudaLaunchConfig_t cfg = {};
       cfg.gridDim = dim3(CS * nclusters);
       cfg.blockDim = dim3(threads);
