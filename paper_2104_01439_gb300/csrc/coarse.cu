@@ -418,23 +418,39 @@ __global__ void __launch_bounds__(kFactorThreads, 1) k_factor_block(typename A::
   // are below n, every step is straight-line
   // code between two barriers of that group (sync()), and each owner forms the pivot's
   // reciprocal itself.
-  auto invert = [&](V* X, int n, auto sync) {
+  // With a second n x n buffer Y the steps alternate between X and Y, one barrier each
+  // (the result is copied back into X at the end when it lands in Y).
+  auto invert = [&](V* X, int n, auto sync, V* Y = nullptr) {
     const bool own = te < P * P && ta < n && tb < n;
+    V* cur = X;
+    V* nxt = Y;
     for (int kk = 0; kk < n; ++kk) {
       V nv = zero;
       if (own) {
         V pinv;
-        if (!A::inv(X[kk * P + kk], &pinv)) {
+        if (!A::inv(cur[kk * P + kk], &pinv)) {
           gj_bad_s = 1;   // every owner sees the same pivot
         } else if (ta == kk) {
-          nv = tb == kk ? pinv : A::mul(pinv, X[kk * P + tb]);
+          nv = tb == kk ? pinv : A::mul(pinv, cur[kk * P + tb]);
         } else {
-          const V f = A::mul(X[ta * P + kk], pinv);
-          nv = tb == kk ? A::neg(f) : A::sub(X[ta * P + tb], A::mul(f, X[kk * P + tb]));
+          const V f = A::mul(cur[ta * P + kk], pinv);
+          nv = tb == kk ? A::neg(f) : A::sub(cur[ta * P + tb], A::mul(f, cur[kk * P + tb]));
         }
       }
-      sync();
-      if (own) X[ta * P + tb] = nv;
+      if (Y) {
+        if (own) nxt[ta * P + tb] = nv;
+        sync();
+        V* t = cur;
+        cur = nxt;
+        nxt = t;
+      } else {
+        sync();
+        if (own) X[ta * P + tb] = nv;
+        sync();
+      }
+    }
+    if (Y && cur != X) {
+      if (own) X[ta * P + tb] = cur[ta * P + tb];
       sync();
     }
   };
@@ -478,7 +494,7 @@ __global__ void __launch_bounds__(kFactorThreads, 1) k_factor_block(typename A::
           Pn[ta * P + tb] = A::fin(acc);
         }
         named_sync(1, kLookThreads);
-        invert(Pn, pn1, [] { named_sync(1, kLookThreads); });
+        invert(Pn, pn1, [] { named_sync(1, kLookThreads); }, cpl);   // cpl is free again
       }
     } else {
       // ---- update warps

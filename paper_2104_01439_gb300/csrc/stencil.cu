@@ -22,12 +22,18 @@ inline int grid_for(int64_t n, int per_block = kThreads) {
   return (int)std::min<int64_t>(std::max<int64_t>(b, 1), 152 * 16);
 }
 
+// lattice coordinates and class of DoF p (the last coordinate is what remains after the
+// divisions of the others: no division for it)
 __device__ __forceinline__ int decode(const GridDesc& g, int p, int* a) {
   int cls = 0, mul = 1, t = p;
   for (int ax = 0; ax < g.dim; ++ax) {
-    int q = t / g.W;
-    a[ax] = t - q * g.W;
-    t = q;
+    if (ax == g.dim - 1) {
+      a[ax] = t;
+    } else {
+      const int q = t / g.W;
+      a[ax] = t - q * g.W;
+      t = q;
+    }
     cls += axis_class(a[ax], g.W, g.R, g.q) * mul;
     mul *= g.C1;
   }
