@@ -1,0 +1,229 @@
+"""Algebraic identities the GPU kernels rely on, checked on small dense models (CPU).
+
+* The coarse solve of the complex64 form runs each half-sweep of the twisted block
+  elimination as a segmented recurrence (k_seg_chain phases A and B, k_seg_fixup phase C,
+  k_seg_middle): the model below follows the same index logic (paths, segment lengths, segment
+  ends, products by block) and must reproduce a dense solve of the block-tridiagonal system.
+* The Arnoldi process is lagged classical Gram-Schmidt with reorthogonalisation and lagged
+  normalisation (k_dots2, k_coef, k_update2): the model below follows the same state machine
+  (column j-1 finished at step j, a final step that only finishes the last column, z_j scaled by
+  1/rho_j) and must give the residual history and iteration count of a textbook FGMRES with
+  modified Gram-Schmidt.
+"""
+import numpy as np
+import pytest
+
+
+# ---------------------------------------------------------------- segmented twisted solve
+
+def _make_path(J0, step, n, kmax, kc0):
+    k0 = max(1, min(kmax, n))
+    ls = (n + k0 - 1) // k0
+    return dict(J0=J0, step=step, n=n, Ls=ls, K=(n + ls - 1) // ls, kc0=kc0)
+
+
+def _seg_end(k, ls, n):
+    return min((k + 1) * ls, n) - 1
+
+
+def _blk(p, q):
+    return p["J0"] + p["step"] * q
+
+
+def _segmented_twisted_solve(D, Lo, Uo, r, kp):
+    nb, B = len(D), D[0].shape[0]
+    m = nb // 2
+    dinv = [None] * nb
+    for J in range(m):                                   # top chain
+        S = D[J] if J == 0 else D[J] - Lo[J] @ dinv[J - 1] @ Uo[J - 1]
+        dinv[J] = np.linalg.inv(S)
+    for J in range(nb - 1, m, -1):                       # bottom chain
+        S = D[J] if J == nb - 1 else D[J] - Uo[J] @ dinv[J + 1] @ Lo[J + 1]
+        dinv[J] = np.linalg.inv(S)
+    dinv[m] = np.linalg.inv(D[m] - Lo[m] @ dinv[m - 1] @ Uo[m - 1] - Uo[m] @ dinv[m + 1] @ Lo[m + 1])
+    Lm = [None if J == 0 else dinv[J] @ Lo[J] for J in range(nb)]
+    Up = [None if J == nb - 1 else dinv[J] @ Uo[J] for J in range(nb)]
+    uc = [dinv[J] @ r[J * B:(J + 1) * B] for J in range(nb)]          # pre-pass p = Dinv r
+    yb = [np.zeros(B, complex) for _ in range(nb)]
+    f = [_make_path(0, 1, m, kp, 0)]
+    f.append(_make_path(nb - 1, -1, nb - 1 - m, kp, f[0]["K"]))
+    b = [_make_path(m, -1, m + 1, kp, 0)]
+    b.append(_make_path(m, 1, nb - m, kp, b[0]["K"]))
+    Pf, Pb = [None] * nb, [None] * nb
+    for paths, Cs, P in ((f, (Lm, Up), Pf), (b, (Up, Lm), Pb)):
+        for pi, p in enumerate(paths):
+            for k in range(1, p["K"]):
+                for i in range(p["Ls"]):
+                    q = k * p["Ls"] + i
+                    if q > _seg_end(k, p["Ls"], p["n"]):
+                        continue
+                    C = Cs[pi][_blk(p, q)]
+                    P[_blk(p, q)] = C.copy() if i == 0 else -C @ P[_blk(p, q - 1)]
+
+    def phase_a(inp, out, Cs, paths):
+        for pi, p in enumerate(paths):
+            for seg in range(p["K"]):
+                q0, prev = seg * p["Ls"], None
+                for t in range(max(0, min(p["Ls"], p["n"] - q0))):
+                    J = _blk(p, q0 + t)
+                    v = inp[J].copy() if t == 0 else inp[J] - Cs[pi][J] @ prev
+                    out[J], prev = v, v
+
+    def phase_b(z, P, paths):
+        for p in paths:
+            prev = z[_blk(p, _seg_end(0, p["Ls"], p["n"]))].copy()
+            for t in range(p["K"] - 1):
+                J = _blk(p, _seg_end(t + 1, p["Ls"], p["n"]))
+                z[J] = z[J] - P[J] @ prev
+                prev = z[J]
+
+    def phase_c(z, P, paths):
+        for p in paths:
+            for q in range(p["Ls"], p["n"]):
+                k = q // p["Ls"]
+                if q == _seg_end(k, p["Ls"], p["n"]):
+                    continue
+                J = _blk(p, q)
+                z[J] = z[J] - P[J] @ z[_blk(p, k * p["Ls"] - 1)]
+
+    phase_a(uc, yb, (Lm, Up), f)
+    phase_b(yb, Pf, f)
+    phase_c(yb, Pf, f)
+    yb[m] = uc[m] - Lm[m] @ yb[m - 1] - Up[m] @ yb[m + 1]
+    phase_a(yb, uc, (Up, Lm), b)
+    phase_b(uc, Pb, b)
+    phase_c(uc, Pb, b)
+    return np.concatenate(uc)
+
+
+@pytest.mark.parametrize("nb,kp", [(16, 2), (17, 2), (19, 4), (33, 4), (40, 3), (64, 8)])
+def test_segmented_twisted_solve_equals_direct(nb, kp):
+    rng = np.random.default_rng(nb * 10 + kp)
+    B = 5
+    cplx = lambda *s: rng.standard_normal(s) + 1j * rng.standard_normal(s)  # noqa: E731
+    D = [np.eye(B) * 4 + 0.3 * cplx(B, B) for _ in range(nb)]
+    Lo = [None] + [0.5 * cplx(B, B) for _ in range(1, nb)]
+    Uo = [0.5 * cplx(B, B) for _ in range(nb - 1)] + [None]
+    A = np.zeros((nb * B, nb * B), complex)
+    for J in range(nb):
+        A[J * B:(J + 1) * B, J * B:(J + 1) * B] = D[J]
+        if J > 0:
+            A[J * B:(J + 1) * B, (J - 1) * B:J * B] = Lo[J]
+        if J < nb - 1:
+            A[J * B:(J + 1) * B, (J + 1) * B:(J + 2) * B] = Uo[J]
+    r = cplx(nb * B)
+    x = _segmented_twisted_solve(D, Lo, Uo, r, kp)
+    xe = np.linalg.solve(A, r)
+    assert np.linalg.norm(x - xe) <= 1e-12 * np.linalg.norm(xe)
+
+
+# ---------------------------------------------------------------- lagged CGS2 FGMRES
+
+def _fgmres_mgs(A, M, F, m, tol, maxit):
+    n = len(F)
+    x = np.zeros(n, complex)
+    nF, tot, hist = np.linalg.norm(F), 0, []
+    while True:
+        r = F - A @ x
+        beta = np.linalg.norm(r)
+        if beta / nF <= tol or tot >= maxit:
+            return x, tot, hist
+        V, Z, H = [r / beta], [], np.zeros((m + 1, m), complex)
+        for j in range(m):
+            z = M @ V[j]
+            w = A @ z
+            Z.append(z)
+            for i in range(j + 1):
+                H[i, j] = np.vdot(V[i], w)
+                w = w - H[i, j] * V[i]
+            H[j + 1, j] = np.linalg.norm(w)
+            V.append(w / H[j + 1, j])
+            tot += 1
+            e = np.zeros(j + 2, complex)
+            e[0] = beta
+            y = np.linalg.lstsq(H[:j + 2, :j + 1], e, rcond=None)[0]
+            hist.append(np.linalg.norm(e - H[:j + 2, :j + 1] @ y) / nF)
+            if hist[-1] <= tol or tot >= maxit:
+                break
+        x = x + np.array(Z).T @ y
+
+
+def _fgmres_lagged(A, M, F, m, tol, maxit):
+    n = len(F)
+    x = np.zeros(n, complex)
+    nF, total, hist = np.linalg.norm(F), 0, []
+    while True:
+        r = F - A @ x
+        beta = np.linalg.norm(r)
+        if beta / nF <= tol or total >= maxit:
+            return x, total, hist
+        Vs = np.zeros((m + 1, n), complex)
+        Vs[0] = r / beta
+        Z = np.zeros((m, n), complex)
+        g = np.zeros(m + 1, complex)
+        cs, sn = np.zeros(m), np.zeros(m, complex)
+        H = np.zeros((m + 1, m), complex)
+        zs = np.zeros(m)
+        hcol = np.zeros(m + 2, complex)
+        j, pre, W = 0, m >= 1 and total + 1 <= maxit, None
+        while True:
+            if pre:                                      # preconditioner and A0 on slot j
+                Z[j] = M @ Vs[j]
+                W = A @ Z[j]
+            s = np.array([np.vdot(Vs[i], Vs[j]) for i in range(j + 1)])        # k_dots2
+            t = np.array([np.vdot(Vs[i], W) for i in range(j + 1)]) if pre else None
+            rho2 = s[j].real - np.sum(np.abs(s[:j]) ** 2)                      # k_coef
+            rho = np.sqrt(rho2) if rho2 > 0 else 0.0
+            stop = False
+            if j == 0:
+                g[0] = beta * rho
+            else:                                        # finish column j-1, Givens
+                c = j - 1
+                hf, hsub = hcol[:j] + s[:j], rho
+                u = hf[0]
+                for i in range(c):
+                    H[i, c] = cs[i] * u + sn[i] * hf[i + 1]
+                    u = -np.conj(sn[i]) * u + cs[i] * hf[i + 1]
+                aa = abs(u)
+                if hsub == 0:
+                    cr, sv, rr = 1.0, 0.0, u
+                elif aa == 0:
+                    cr, sv, rr = 0.0, 1.0, hsub
+                else:
+                    nu = np.hypot(aa, hsub)
+                    cr, sv, rr = aa / nu, (u / aa) * hsub / nu, (u / aa) * nu
+                cs[c], sn[c], H[c, c] = cr, sv, rr
+                g[c + 1], g[c] = -np.conj(sv) * g[c], cr * g[c]
+                total += 1
+                hist.append(abs(g[c + 1]) / nF)
+                stop = hist[-1] <= tol or not hsub > 1e-14 * beta
+            if not pre or not rho > 0 or stop:
+                break
+            d = np.sum(np.conj(s[:j]) * t[:j])
+            hjj = (t[j] - d) / rho / rho                 # the step uses z_j / rho
+            hcol[:j], hcol[j], zs[j] = t[:j] / rho, hjj, 1.0 / rho
+            v = (Vs[j] - s[:j] @ Vs[:j]) / rho           # k_update2
+            Vs[j] = v
+            W = W / rho - hcol[:j] @ Vs[:j] - hjj * v
+            pre = j + 1 < m and total + 2 <= maxit
+            j += 1
+            Vs[j] = W                                    # unnormalised u_{j+1}
+        y = np.linalg.solve(np.triu(H[:j, :j]), g[:j]) * zs[:j] if j > 0 else np.zeros(0)
+        x = x + Z[:j].T @ y
+
+
+@pytest.mark.parametrize("m,maxit", [(20, 500), (7, 500), (1, 40), (20, 13)])
+def test_lagged_cgs2_fgmres_matches_mgs_fgmres(m, maxit):
+    rng = np.random.default_rng(3)
+    n = 120
+    A = np.eye(n) * 4 + 0.3 * (rng.standard_normal((n, n)) + 1j * rng.standard_normal((n, n)))
+    M = np.linalg.inv(A + 0.05 * rng.standard_normal((n, n)))      # inexact preconditioner
+    F = rng.standard_normal(n) + 1j * rng.standard_normal(n)
+    x1, it1, h1 = _fgmres_mgs(A, M, F, m, 1e-10, maxit)
+    x2, it2, h2 = _fgmres_lagged(A, M, F, m, 1e-10, maxit)
+    assert it1 == it2
+    k = min(len(h1), len(h2))
+    assert np.allclose(np.log10(h1[:k]), np.log10(h2[:k]), atol=1e-3)
+    r1 = np.linalg.norm(F - A @ x1)
+    r2 = np.linalg.norm(F - A @ x2)
+    assert abs(r1 - r2) <= 1e-6 * np.linalg.norm(F) + 1e-3 * r1
