@@ -142,3 +142,27 @@ def test_solve_parity(wl, prec):
     assert abs(res.iters - ref.iters) <= slack, (res.iters, ref.iters)
     assert rel(xh, ref.x) <= 1e-5
     s.close()
+
+
+@pytest.mark.parametrize("prec", [pkg.HELM_FP64, pkg.HELM_MIXED])
+def test_batch_and_host_solves_match_single(prec):
+    """helm_batch_solve (several handles interleaved on their own streams) and
+    helm_solve_host (host buffers, copies inside the call) give what helm_solve gives."""
+    wls = [CASES[1], CASES[2], CASES[4]]
+    solvers = [pkg.Solver(w.k, w.n, w.order, w.shift, dim=w.dim, restart=w.restart, maxit=w.maxit,
+                          tol=w.tol, precision=prec) for w in wls]
+    Fs = [dev(problem(w).F) for w in wls]
+    singles = [s.solve(F) for s, F in zip(solvers, Fs)]
+    xs, results = pkg.batch_solve(solvers, Fs)
+    for (x1, r1), x2, r2 in zip(singles, xs, results):
+        assert r2.status == "converged" and r2.iters == r1.iters
+        a, b = x1.cpu().numpy(), x2.cpu().numpy()
+        assert rel(b, a) <= 1e-12
+    for s, F, (x1, r1) in zip(solvers, Fs, singles):
+        Fh = F.cpu().pin_memory()
+        xh = torch.empty_like(Fh).pin_memory()
+        r3 = s.solve_host(Fh, xh)
+        assert r3.status == "converged" and r3.iters == r1.iters
+        assert rel(xh.numpy(), x1.cpu().numpy()) <= 1e-12
+    for s in solvers:
+        s.close()
