@@ -227,3 +227,73 @@ def test_lagged_cgs2_fgmres_matches_mgs_fgmres(m, maxit):
     r1 = np.linalg.norm(F - A @ x1)
     r2 = np.linalg.norm(F - A @ x2)
     assert abs(r1 - r2) <= 1e-6 * np.linalg.norm(F) + 1e-3 * r1
+
+
+def test_segment_products_bounded_on_helmholtz_coarse_operator():
+    """On a rediscretised coarse Helmholtz operator (2D P1, 128 x 128 cells, k = 100,
+    eps = 0.5 k^2, impedance boundary) with lexicographic line blocks: the segment products of
+    the forward sweep (products of the folded couplings Lm = Dinv A_J,J-1 over up to 16 blocks)
+    keep spectral norms below one, and a complex64 segmented forward/backward solve is as
+    accurate as the complex64 sequential one against a sparse direct solve."""
+    import scipy.sparse.linalg as spla
+    from oracle import fem
+    nc, k = 128, 100.0
+    cm = fem.build_mesh(2, 1, nc)
+    Kc, Mc, Bc = fem.assemble(cm)
+    A = fem.system_matrix(Kc, Mc, Bc, k, 0.5 * k * k).tocsr()
+    W = nc + 1
+    blk = lambda I, J: A[I * W:(I + 1) * W, J * W:(J + 1) * W].toarray()  # noqa: E731
+    assert A[0:W, 2 * W:3 * W].nnz == 0          # block tridiagonal over grid lines
+    dinv, Lm, Up = [None] * W, [None] * W, [None] * W
+    S = blk(0, 0)
+    for J in range(W):                            # single chain (top-down) Schur complements
+        if J > 0:
+            S = blk(J, J) - blk(J, J - 1) @ (dinv[J - 1] @ blk(J - 1, J))
+        dinv[J] = np.linalg.inv(S)
+        if J > 0:
+            Lm[J] = dinv[J] @ blk(J, J - 1)
+        if J < W - 1:
+            Up[J] = dinv[J] @ blk(J, J + 1)
+    rng = np.random.default_rng(5)
+    r = rng.standard_normal(W * W) + 1j * rng.standard_normal(W * W)
+    xe = spla.spsolve(A.tocsc(), r)
+    c64 = np.complex64
+
+    def sweep(p, C, order, ls):
+        n = len(order)
+        q = [None] * n
+        for t in range(n):                        # phase A: restarted recurrences
+            q[t] = p[order[t]] if t % ls == 0 else p[order[t]] - C[order[t]].astype(c64) @ q[t - 1]
+        P, norms = {}, []
+        for t in range(ls, n):                    # segment products
+            C_t = C[order[t]].astype(c64)
+            P[t] = C_t if t % ls == 0 else -C_t @ P[t - 1]
+            norms.append(np.linalg.norm(P[t], 2))
+        y = list(q)
+        ends = [min(kk * ls + ls, n) - 1 for kk in range(n // ls + 1) if kk * ls < n]
+        for e_prev, e in zip(ends[:-1], ends[1:]):   # phase B: z_e = w_e - P_e z_e(prev)
+            y[e] = q[e] - P[e] @ y[e_prev]
+        for t in range(ls, n):                    # phase C: z_t = w_t - P_t z_e(k-1)
+            if t not in ends:
+                y[t] = q[t] - P[t] @ y[(t // ls) * ls - 1]
+        out = [None] * n
+        for t in range(n):
+            out[order[t]] = y[t]
+        return out, max(norms)
+
+    p = [(dinv[J].astype(c64) @ r[J * W:(J + 1) * W].astype(c64)) for J in range(W)]
+    y, nf = sweep(p, Lm, list(range(W)), 16)
+    x, nb = sweep(y, Up, list(range(W - 1, -1, -1)), 16)
+    xs = np.concatenate(x)
+    ys = [p[0]]
+    for J in range(1, W):
+        ys.append(p[J] - Lm[J].astype(c64) @ ys[-1])
+    xq = [None] * W
+    xq[-1] = ys[-1]
+    for J in range(W - 2, -1, -1):
+        xq[J] = ys[J] - Up[J].astype(c64) @ xq[J + 1]
+    xq = np.concatenate(xq)
+    err_seg = np.linalg.norm(xs - xe) / np.linalg.norm(xe)
+    err_seq = np.linalg.norm(xq - xe) / np.linalg.norm(xe)
+    assert nf < 1.0 and nb < 1.0, (nf, nb)
+    assert err_seg <= 2.0 * err_seq + 1e-7, (err_seg, err_seq)
