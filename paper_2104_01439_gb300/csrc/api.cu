@@ -776,7 +776,6 @@ static int setup_impl(helm_ctx* h) {
   CK(h->alloc(&kb.zs, sizeof(double) * m));
   CK(h->alloc(&kb.cdf, sizeof(double2) * (2 * m + 2)));
   CK(h->alloc(&kb.hcol, sizeof(double2) * (m + 2)));
-  CK(h->alloc(&kb.hfin, sizeof(double2) * (m + 2)));
   CK(h->alloc(&kb.hp, sizeof(double2) * (m + 2)));
   CK(h->alloc(&kb.tp, sizeof(double2) * (m + 2)));
   CK(h->alloc(&kb.part, sizeof(double2) * (size_t)kb.pstride * kb_rows(m)));

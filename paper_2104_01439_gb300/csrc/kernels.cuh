@@ -136,8 +136,6 @@ struct KState {
   double est;      // |g_{j+1}| / ||F||
   double gabs;     // |g| of the last rotated column (|g_{c+1}| = |s_c| |g_c|)
   double inv_nF;   // 1 / ||F||
-  double irho;     // 1 / rho of this step
-  double2 hjj;     // h_jj of this step
   double relres;   // true relative residual at cycle end
 };
 
@@ -168,7 +166,6 @@ struct KrylovBufs {
   double* zs;      // m : scale of each preconditioned vector (1 / rho of its step)
   double2* cdf;    // 2m + 2 (as float4): the correction sweep's coefficients in double-float
   double2* hcol;   // m+2 : the column started by the previous step (finished by this one)
-  double2* hfin;   // m+2 : the finished column handed to the Givens step
   double2* hp;     // m+1 : s_i = <v_i, u_j>
   double2* tp;     // m+1 : t_i = <v_i, w>
   double2* part;   // pstride x kb_rows(m) partial sums (inner products: double-float as float4)

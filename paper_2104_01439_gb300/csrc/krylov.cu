@@ -340,8 +340,6 @@ __global__ void __launch_bounds__(32) k_coef(KrylovBufs kb) {
     cdf[2 * j + 1] = make_float4(a.h, a.l, 0.f, 0.f);
     kb.zs[j] = irho;
     kb.hcol[j] = hjj;
-    st->hjj = hjj;
-    st->irho = irho;
     // the correction sweep of this step reads ju; the next step (its preconditioner and A0
     // included) runs at j + 1 and builds column total + 2 if it applies the preconditioner
     st->ju = j;
