@@ -15,6 +15,9 @@ What it computes (the exact discrete method, assembled, in complex128):
                  modified Gram-Schmidt and complex Givens rotations (Sec. 4).
   * shiftmap.py -- the fitted shift-exponent map of eq. shiftexp with the
                  weights of Table tab:optweights (Sec. 5).
+  * lfa.py    -- local Fourier analysis of the twogrid method (Sec. 3): stencil
+                 symbols, the 4 x 4 harmonic matrix T_hat, rho_loc(sigma) and
+                 sigma_c, for the paper's Q1 and the solver's P1 Kuhn triangles.
 
 Pins: see tests/test_oracle_*.py. Every function is pinned by a closed form,
 an invariant, a textbook special case or brute force; the iteration counts
