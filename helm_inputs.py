@@ -128,3 +128,33 @@ def serving_requests(seed: int = 5, count: int = 2000,
     ns = g.choice(np.asarray(grids), count)
     ks = g.uniform(k_range[0], k_range[1], count)
     return [(int(orders[i]), int(ns[i]), float(ks[i]), seed + i) for i in range(count)]
+
+
+# Heterogeneous wavenumber k(x) = k_max * mu(x) with a scaled profile mu: Omega -> [0, 1]
+# (Sec. 6). The paper's profiles (wedge, geological cross-sections) are not available; these
+# synthetic profiles stand in for them.
+WEDGE_VALUES = (1.0, 0.7, 0.45)    # mu above, inside and below the wedge
+
+
+def wedge_profile(x: np.ndarray) -> np.ndarray:
+    """Three-valued wedge: a layer between the lines y = 0.62 + 0.18 (x - 0.5) and
+    y = 0.38 - 0.12 (x - 0.5), which close towards x = 0 less than towards x = 1, splits the
+    square into an upper, a wedge and a lower region. x: (P, d) points; returns mu (P,)."""
+    x = np.asarray(x, dtype=float)
+    top = 0.62 + 0.18 * (x[:, 0] - 0.5)
+    bot = 0.38 - 0.12 * (x[:, 0] - 0.5)
+    y = x[:, 1]
+    return np.where(y > top, WEDGE_VALUES[0], np.where(y >= bot, WEDGE_VALUES[1], WEDGE_VALUES[2]))
+
+
+def cell_profile(x: np.ndarray, cells: int, seed: int) -> np.ndarray:
+    """Piecewise-constant mu on a cells^d grid of squares/cubes, values U[0.4, 1] from
+    PCG64(seed) in lexicographic cell order (x fastest). x: (P, d) points inside the cells."""
+    x = np.asarray(x, dtype=float)
+    d = x.shape[1]
+    vals = np.random.Generator(np.random.PCG64(seed)).uniform(0.4, 1.0, cells ** d)
+    idx = np.minimum((x * cells).astype(np.int64), cells - 1)
+    lin = np.zeros(x.shape[0], dtype=np.int64)
+    for ax in reversed(range(d)):
+        lin = lin * cells + idx[:, ax]
+    return vals[lin]

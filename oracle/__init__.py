@@ -9,10 +9,13 @@ What it computes (the exact discrete method, assembled, in complex128):
                  square/cube; element matrices by exact integration of
                  barycentric monomials; assembled CSR K, M, B (Sec. 2,
                  eq. discreteproblem / sys_matrix); load vectors; canonical
-                 interpolation P between the 2h and h spaces (Sec. 4).
+                 interpolation P between the 2h and h spaces (Sec. 4);
+                 heterogeneous wavenumbers k(x) = k_max mu(x) with one value
+                 per simplex (Sec. 2 with k in L^inf, Sec. 6).
   * solver.py -- damped Jacobi, the twogrid V(nu,nu)-cycle of Algorithm 1 with
                  a direct coarse solve, and flexible GMRES(m) (Saad 1993) with
-                 modified Gram-Schmidt and complex Givens rotations (Sec. 4).
+                 modified Gram-Schmidt and complex Givens rotations (Sec. 4);
+                 problems with constant or heterogeneous k.
   * shiftmap.py -- the fitted shift-exponent map of eq. shiftexp with the
                  weights of Table tab:optweights (Sec. 5).
   * lfa.py    -- local Fourier analysis of the twogrid method (Sec. 3): stencil

@@ -163,6 +163,7 @@ class Mesh:
     elem_verts: np.ndarray  # (E, dim+1) vertex DoF indices
     facets: np.ndarray     # (F, nfloc) boundary facet DoF indices (facet basis order)
     facet_normals: np.ndarray  # (F, dim) outward unit normals
+    facet_elems: np.ndarray = None  # (F,) element (simplex) owning each boundary facet
 
     @property
     def num_dofs(self):
@@ -230,8 +231,8 @@ def build_mesh(dim, order, n):
 
     # Boundary facets: faces of cell simplices lying in a side of the box.
     fnodes = lagrange_basis(dim - 1, order)[1]
-    facets, normals = [], []
-    for simp in templates:
+    facets, normals, owners = [], [], []
+    for s_idx, simp in enumerate(templates):
         sv = np.asarray(simp, dtype=np.int64)
         for face in itertools.combinations(range(dim + 1), dim):
             fv = sv[list(face)]
@@ -247,8 +248,9 @@ def build_mesh(dim, order, n):
                     nrm = np.zeros((base.shape[0], dim))
                     nrm[:, ax] = -1.0 if side == 0 else 1.0
                     normals.append(nrm)
+                    owners.append(np.nonzero(sel)[0] * S + s_idx)   # elements are (cell, simplex)
     return Mesh(dim, order, n, coords, elems, everts,
-                np.concatenate(facets), np.concatenate(normals))
+                np.concatenate(facets), np.concatenate(normals), np.concatenate(owners))
 
 
 # ----------------------------------------------------------------------------
@@ -307,6 +309,62 @@ def assemble(mesh):
 def system_matrix(K, M, B, k, eps):
     """A(k, eps) = K - (k^2 + i eps) M - i k B  (eq. sys_matrix; the boundary term is unshifted)."""
     return (K.astype(np.complex128) - (k * k + 1j * eps) * M - 1j * k * B).tocsr()
+
+
+# ----------------------------------------------------------------------------
+# Heterogeneous wavenumber (Sec. 2 with k in L^inf; Sec. 6: k(x) = k_max mu(x)).
+# The coefficient is element-local: one value per simplex, taken at its centroid.
+# ----------------------------------------------------------------------------
+
+
+def element_centroids(mesh):
+    """(E, dim) centroids of the simplices."""
+    return mesh.coords[mesh.elem_verts].mean(axis=1)
+
+
+def _scatter_scaled(N, locs, mats, scales):
+    """Sum scales[g][e] * mats[g] into an N x N CSR at DoFs locs[g][e]."""
+    rows, cols, vals = [], [], []
+    for loc, mat, sc in zip(locs, mats, scales):
+        nl = loc.shape[1]
+        rows.append(np.repeat(loc, nl, axis=1).ravel())
+        cols.append(np.tile(loc, (1, nl)).ravel())
+        vals.append((sc[:, None] * mat.ravel()[None, :]).ravel())
+    A = sp.csr_matrix((np.concatenate(vals), (np.concatenate(rows), np.concatenate(cols))),
+                      shape=(N, N))
+    A.sum_duplicates()
+    A.sort_indices()
+    return A
+
+
+def assemble_weighted(mesh, k_elem):
+    """K, M_k = m(.,.;k,0) = sum_e k_e^2 M_e, M (unit mass), B (unit boundary mass) and
+    B_k = b(.,.;k) = sum_F k_F B_F for a wavenumber k_e per simplex; a boundary facet takes its
+    owning simplex's value."""
+    k_elem = np.asarray(k_elem, dtype=float)
+    N = mesh.num_dofs
+    K, M, B = assemble(mesh)
+    groups = _group_by_shape(mesh, mesh.elem_verts, mesh.dim + 1)
+    locs, Ms, sc = [], [], []
+    for sel in groups:
+        _, Me = element_matrices(mesh.coords[mesh.elem_verts[sel[0]]], mesh.order)
+        locs.append(mesh.elems[sel])
+        Ms.append(Me)
+        sc.append(k_elem[sel] ** 2)
+    Mk = _scatter_scaled(N, locs, Ms, sc)
+    fgroups = _group_by_shape(mesh, mesh.facets, mesh.dim)
+    flocs, Bs, fsc = [], [], []
+    for sel in fgroups:
+        flocs.append(mesh.facets[sel])
+        Bs.append(facet_mass(mesh.coords[mesh.facets[sel[0]][:mesh.dim]], mesh.order))
+        fsc.append(k_elem[mesh.facet_elems[sel]])
+    Bk = _scatter_scaled(N, flocs, Bs, fsc)
+    return K, Mk, M, B, Bk
+
+
+def system_matrix_het(K, Mk, M, Bk, eps):
+    """A(k, eps) = K - M(k, eps) - i B(k) with M(k, eps) = M_k + i eps M (eq. sys_matrix)."""
+    return (K.astype(np.complex128) - Mk - 1j * eps * M - 1j * Bk).tocsr()
 
 
 # ----------------------------------------------------------------------------

@@ -226,3 +226,23 @@ def build_problem(wl):
     P = fem.prolongation(cmesh, mesh)
     F = load_vector(wl, mesh, M)
     return Problem(wl, mesh, cmesh, K, M, B, A0, Aeps, Aeps_c, P, F)
+
+
+def build_problem_het(wl, mu, source=None):
+    """Problem with the heterogeneous wavenumber k(x) = wl.k * mu(x) (Sec. 6): wl.k is k_max,
+    mu maps (P, dim) points to [0, 1] and is taken at each simplex's centroid, on the fine mesh
+    and again on the coarse mesh (the coarse operator is rediscretised, Sec. 4). The shift
+    wl.shift is one real number for the whole domain (eq. Helmholtz_shift). The load is the
+    paper's source f = 2 exp(-1000 |x - s|^2), g = 0 (Sec. 6), s = source (default: centre)."""
+    mesh = fem.build_mesh(wl.dim, wl.order, wl.n)
+    cmesh = fem.build_mesh(wl.dim, wl.order, wl.n // 2)
+    K, Mk, M, B, Bk = fem.assemble_weighted(mesh, wl.k * mu(fem.element_centroids(mesh)))
+    Kc, Mkc, Mc, _, Bkc = fem.assemble_weighted(cmesh, wl.k * mu(fem.element_centroids(cmesh)))
+    A0 = fem.system_matrix_het(K, Mk, M, Bk, 0.0)
+    Aeps = fem.system_matrix_het(K, Mk, M, Bk, wl.shift)
+    Aeps_c = fem.system_matrix_het(Kc, Mkc, Mc, Bkc, wl.shift)
+    P = fem.prolongation(cmesh, mesh)
+    s = np.full(wl.dim, 0.5) if source is None else np.asarray(source, dtype=float)
+    f = 2.0 * np.exp(-1000.0 * np.sum((mesh.coords - s) ** 2, axis=1))
+    F = fem.load_from_nodal(mesh, M, f)
+    return Problem(wl, mesh, cmesh, K, M, B, A0, Aeps, Aeps_c, P, F)
