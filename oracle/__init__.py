@@ -16,6 +16,8 @@ What it computes (the exact discrete method, assembled, in complex128):
                  a direct coarse solve, and flexible GMRES(m) (Saad 1993) with
                  modified Gram-Schmidt and complex Givens rotations (Sec. 4);
                  problems with constant or heterogeneous k.
+  * qfem.py   -- tensor-product Q_p elements (p = 1..3) on squares / cubes, the
+                 paper's own discretisation (Sec. 2), with optional element-local k.
   * shiftmap.py -- the fitted shift-exponent map of eq. shiftexp with the
                  weights of Table tab:optweights (Sec. 5).
   * lfa.py    -- local Fourier analysis of the twogrid method (Sec. 3): stencil

@@ -246,3 +246,37 @@ def build_problem_het(wl, mu, source=None):
     f = 2.0 * np.exp(-1000.0 * np.sum((mesh.coords - s) ** 2, axis=1))
     F = fem.load_from_nodal(mesh, M, f)
     return Problem(wl, mesh, cmesh, K, M, B, A0, Aeps, Aeps_c, P, F)
+
+
+def build_problem_q(wl, mu=None, source=None):
+    """Problem on tensor-product Q_p elements (p = wl.order in 1..3, Sec. 2), optionally with the
+    heterogeneous wavenumber k(x) = wl.k * mu(x) taken at the element centres (Sec. 6). Loads:
+    'planewave' (impedance data of exp(i k d.x); constant k only), 'source' (the paper's
+    f = 2 exp(-1000 |x - s|^2), g = 0, s = source or the centre), 'random' (seeded F)."""
+    from . import qfem
+    mesh = qfem.build_mesh(wl.dim, wl.order, wl.n)
+    cmesh = qfem.build_mesh(wl.dim, wl.order, wl.n // 2)
+    kf = None if mu is None else wl.k * mu(mesh.centres)
+    kc = None if mu is None else wl.k * mu(cmesh.centres)
+    K, Mk, M, B, Bk = qfem.assemble(mesh, kf)
+    Kc, Mkc, Mc, Bc, Bkc = qfem.assemble(cmesh, kc)
+    if mu is None:
+        A0 = fem.system_matrix(K, M, B, wl.k, 0.0)
+        Aeps = fem.system_matrix(K, M, B, wl.k, wl.shift)
+        Aeps_c = fem.system_matrix(Kc, Mc, Bc, wl.k, wl.shift)
+    else:
+        A0 = fem.system_matrix_het(K, Mk, M, Bk, 0.0)
+        Aeps = fem.system_matrix_het(K, Mk, M, Bk, wl.shift)
+        Aeps_c = fem.system_matrix_het(Kc, Mkc, Mc, Bkc, wl.shift)
+    P = qfem.prolongation(cmesh, mesh)
+    if wl.rhs == "planewave":
+        assert mu is None
+        F = qfem.load_planewave(mesh, M, wl.k, wl.theta)
+    elif wl.rhs == "source":
+        F = qfem.load_source(mesh, M, np.full(wl.dim, 0.5) if source is None else source)
+    elif wl.rhs == "random":
+        import helm_inputs
+        F = helm_inputs.random_load(mesh.num_dofs, wl.seed)
+    else:
+        raise ValueError(wl.rhs)
+    return Problem(wl, mesh, cmesh, K, M, B, A0, Aeps, Aeps_c, P, F)
