@@ -407,6 +407,9 @@ bool solve_step(SolveTask& t, bool blocking) {
       t.launched_in_cycle += chunk;
       t.launched_total += chunk;
       cudaMemcpyAsync(h->st_h, kb.st, sizeof(KState), cudaMemcpyDeviceToHost, s);
+      // the error word too: a bounded device wait that timed out ends the solve at the next
+      // chunk boundary (every later launch would otherwise wait out its own limit again)
+      cudaMemcpyAsync(h->err_h, h->err, sizeof(int), cudaMemcpyDeviceToHost, s);
       cudaEventRecord(t.ready, s);
       t.phase = SolveTask::WAIT_ITER;
       return false;
@@ -414,7 +417,7 @@ bool solve_step(SolveTask& t, bool blocking) {
     case SolveTask::WAIT_ITER: {
       if (blocking) cudaEventSynchronize(t.ready);
       else if (cudaEventQuery(t.ready) == cudaErrorNotReady) return false;
-      if (h->st_h->active && t.launched_in_cycle < m + 1) {
+      if (h->st_h->active && *h->err_h == 0 && t.launched_in_cycle < m + 1) {
         t.phase = SolveTask::ITER;
         return false;
       }
@@ -437,8 +440,10 @@ bool solve_step(SolveTask& t, bool blocking) {
       if (blocking) cudaEventSynchronize(t.ready);
       else if (cudaEventQuery(t.ready) == cudaErrorNotReady) return false;
       KState* st = h->st_h;
+      // (the state, the error word and e1 were recorded before `ready`, which has completed)
+      const int e = *h->err_h;
       bool done = st->relres <= h->opts.tol || st->total >= maxit || st->breakdown || st->nonfinite ||
-                  !(st->relres == st->relres);
+                  !(st->relres == st->relres) || e != 0;
       if (!done) {
         launch_cycle_start(kb, h->rres, s);   // restart from r = F - A0 x
         t.kernels += 1;
@@ -446,8 +451,6 @@ bool solve_step(SolveTask& t, bool blocking) {
         t.phase = SolveTask::ITER;
         return false;
       }
-      // (the state, the error word and e1 were recorded before `ready`, which has completed)
-      const int e = *h->err_h;
       cudaError_t ce = cudaGetLastError();
       if (ce != cudaSuccess) t.rc = cuda_fail(ce);
       else if (e != 0) t.rc = e;
