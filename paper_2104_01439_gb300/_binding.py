@@ -138,10 +138,20 @@ def _res(r: HelmResult) -> SolveResult:
                        r.relres_est, r.solve_ms, r.kernels)
 
 
-def _ptr(t):
+def _ptr(t, n=None, device=True):
+    """Address of a contiguous complex128 tensor holding at least n values, on the GPU
+    (device=True) or in host memory (device=False). The library cannot tell a host address from
+    a device one, nor a buffer's length, so a mismatch is refused here instead of reaching a
+    kernel or a host copy."""
     import torch
     if not isinstance(t, torch.Tensor) or t.dtype != torch.complex128 or not t.is_contiguous():
         raise TypeError("expected a contiguous complex128 tensor")
+    if device and not t.is_cuda:
+        raise TypeError("expected a CUDA tensor (device buffer)")
+    if not device and t.is_cuda:
+        raise TypeError("expected a CPU tensor (host buffer)")
+    if n is not None and t.numel() < n:
+        raise ValueError(f"buffer holds {t.numel()} values, {n} needed")
     return ctypes.c_void_p(t.data_ptr())
 
 
@@ -196,34 +206,37 @@ class Solver:
     def solve(self, F, x=None) -> tuple:
         x = self._dev() if x is None else x
         r = HelmResult()
-        _check(load().helm_solve(self._h, _ptr(F), _ptr(x), ctypes.byref(r)))
+        N = self.num_dofs
+        _check(load().helm_solve(self._h, _ptr(F, N), _ptr(x, N), ctypes.byref(r)))
         return x, _res(r)
 
     def solve_host(self, F_host, x_host) -> SolveResult:
         r = HelmResult()
-        _check(load().helm_solve_host(self._h, _ptr(F_host), _ptr(x_host), ctypes.byref(r)))
+        N = self.num_dofs
+        _check(load().helm_solve_host(self._h, _ptr(F_host, N, device=False), _ptr(x_host, N, device=False),
+                                      ctypes.byref(r)))
         return _res(r)
 
     def apply(self, x, which: int = 0, y=None):
         """y = A0 x (which = 0) or A_eps x (which = 1); stream-ordered on the handle's stream."""
         y = self._dev() if y is None else y
-        _check(load().helm_apply(self._h, which, _ptr(x), _ptr(y)))
+        _check(load().helm_apply(self._h, which, _ptr(x, self.num_dofs), _ptr(y, self.num_dofs)))
         return y
 
     def smooth(self, f, nu: int = 2, u=None):
         """nu damped-Jacobi sweeps on A_eps from u = 0 (helm_smooth); stream-ordered."""
         u = self._dev() if u is None else u
-        _check(load().helm_smooth(self._h, _ptr(f), _ptr(u), int(nu)))
+        _check(load().helm_smooth(self._h, _ptr(f, self.num_dofs), _ptr(u, self.num_dofs), int(nu)))
         return u
 
     def vcycle(self, f):
         u = self._dev()
-        _check(load().helm_vcycle(self._h, _ptr(f), _ptr(u)))
+        _check(load().helm_vcycle(self._h, _ptr(f, self.num_dofs), _ptr(u, self.num_dofs)))
         return u
 
     def coarse_solve(self, rc):
         uc = self._dev(self.num_coarse_dofs)
-        _check(load().helm_coarse_solve(self._h, _ptr(rc), _ptr(uc)))
+        _check(load().helm_coarse_solve(self._h, _ptr(rc, self.num_coarse_dofs), _ptr(uc, self.num_coarse_dofs)))
         return uc
 
     def rhs_planewave(self, theta: float = 0.3):
@@ -256,8 +269,10 @@ def batch_solve(solvers, Fs, xs=None):
     n = len(solvers)
     xs = [s._dev() for s in solvers] if xs is None else xs
     hs = (ctypes.c_void_p * n)(*[s.handle.value for s in solvers])
-    fp = (ctypes.c_void_p * n)(*[F.data_ptr() for F in Fs])
-    xp = (ctypes.c_void_p * n)(*[x.data_ptr() for x in xs])
+    if len(Fs) != n or len(xs) != n:
+        raise ValueError("one load vector and one solution buffer per solver")
+    fp = (ctypes.c_void_p * n)(*[_ptr(F, s.num_dofs).value for s, F in zip(solvers, Fs)])
+    xp = (ctypes.c_void_p * n)(*[_ptr(x, s.num_dofs).value for s, x in zip(solvers, xs)])
     res = (HelmResult * n)()
     _check(load().helm_batch_solve(n, hs, fp, xp, res))
     return xs, [_res(r) for r in res]
@@ -318,8 +333,10 @@ class Server:
     def submit(self, req: HelmRequest, F_host, x_host=None) -> int:
         """F_host: CPU complex128 tensor (copied at once); x_host: CPU complex128 tensor or None."""
         t = ctypes.c_int64()
-        xp = ctypes.c_void_p(x_host.data_ptr()) if x_host is not None else None
-        _check(load().helm_server_submit(self._s, ctypes.byref(req), _ptr(F_host), xp, ctypes.byref(t)))
+        N = num_dofs(req)
+        xp = _ptr(x_host, N, device=False) if x_host is not None else None
+        _check(load().helm_server_submit(self._s, ctypes.byref(req), _ptr(F_host, N, device=False), xp,
+                                         ctypes.byref(t)))
         if x_host is not None:
             self._keep[t.value] = x_host   # must outlive the request
         return t.value

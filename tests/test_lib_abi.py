@@ -65,3 +65,24 @@ def test_request_bytes_estimate_is_host_only_and_consistent():
     assert rb(n=512, restart=80, precision=_binding.HELM_FP64) > 3 * blk * 16
     with pytest.raises(_binding.HelmError):
         rb(n=63)   # 1/h must be even
+
+
+def test_binding_refuses_wrong_buffers():
+    """The library cannot tell host from device addresses or a buffer's length, so the binding
+    refuses mismatches before any call: wrong dtype or layout, a host tensor where a device
+    buffer is needed (and the reverse), and buffers shorter than the operand."""
+    import torch
+    from paper_2104_01439_gb300 import _binding as b
+    good = torch.zeros(8, dtype=torch.complex128)
+    assert b._ptr(good, 8, device=False).value == good.data_ptr()
+    assert b._ptr(good, 5, device=False).value == good.data_ptr()    # a longer buffer is fine
+    with pytest.raises(TypeError):
+        b._ptr(good, 8)                                              # host tensor, device expected
+    with pytest.raises(ValueError):
+        b._ptr(good, 9, device=False)                                # too short
+    with pytest.raises(TypeError):
+        b._ptr(torch.zeros(8, dtype=torch.complex64), 8, device=False)
+    with pytest.raises(TypeError):
+        b._ptr(torch.zeros(8, 2, dtype=torch.complex128).t(), 8, device=False)   # not contiguous
+    with pytest.raises(TypeError):
+        b._ptr(good.numpy(), 8, device=False)                        # not a tensor
