@@ -168,7 +168,9 @@ int helm_rhs_planewave(helm_t h, double theta, void* F_host);
 int helm_rhs_gaussian(helm_t h, double sigma, double cx, double cy, double cz, void* F_host);
 
 /* The same two load vectors without a handle (host only), for the mesh of
- * (dim, order, h): F_host receives complex128[(order/h + 1)^dim]. */
+ * (dim, order, h): F_host receives complex128[(order/h + 1)^dim]. HELM_EINVAL for a
+ * mesh helm_setup would refuse (1/h not an even integer >= 4, dim/order not supported,
+ * 2^30 DoFs or more), a null F_host, k <= 0 or sigma <= 0; nothing is written then. */
 int helm_load_planewave(int dim, int order, double h, double k, double theta, void* F_host);
 int helm_load_gaussian(int dim, int order, double h, double sigma, double cx, double cy, double cz, void* F_host);
 

@@ -921,8 +921,12 @@ int helm_rhs_gaussian(helm_t h, double sigma, double cx, double cy, double cz, v
 static int mesh_n(int dim, int order, double h) {
   if (!(h > 0) || !(dim == 2 || dim == 3) || !(order == 1 || order == 2) || (dim == 3 && order != 1)) return -1;
   const double nn = 1.0 / h;
+  if (!(nn < 1e6)) return -1;   // beyond any mesh whose DoF count fits the cap below
   const int n = (int)std::lround(nn);
   if (std::fabs(nn - n) > 1e-9 * nn || n < 4 || n % 2) return -1;
+  int64_t N = 1;
+  for (int d = 0; d < dim; ++d) N *= (int64_t)order * n + 1;
+  if (N >= (1ll << 31) / 2) return -1;   // the solver's DoF cap
   return n;
 }
 

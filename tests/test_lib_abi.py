@@ -1,11 +1,13 @@
 """CPU-side checks of the C ABI library: it builds, loads, and exports every
-function declared in include/helm.h. No compute call is made without a GPU."""
+function declared in include/helm.h; host-only entry points (request sizing, load
+vectors) are exercised; no GPU compute call is made."""
 import os
 import re
 
 import pytest
 
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HEADER = os.path.join(ROOT, "include", "helm.h")
 
 
 def _declared():
@@ -86,3 +88,43 @@ def test_binding_refuses_wrong_buffers():
         b._ptr(torch.zeros(8, 2, dtype=torch.complex128).t(), 8, device=False)   # not contiguous
     with pytest.raises(TypeError):
         b._ptr(good.numpy(), 8, device=False)                        # not a tensor
+
+
+@pytest.mark.parametrize("dim,order,n", [(2, 1, 16), (2, 2, 8), (3, 1, 6)])
+def test_host_load_builders_match_the_oracle(dim, order, n):
+    """helm_load_planewave / helm_load_gaussian run on the host only, so their parity with the
+    oracle's load vectors (Sec. 2, F(v) = int f v + int_dOmega g v) is checked here."""
+    import ctypes
+    import numpy as np
+    from oracle import fem
+    from paper_2104_01439_gb300 import _binding as b
+    lib = b.load()
+    mesh = fem.build_mesh(dim, order, n)
+    _, M, _ = fem.assemble(mesh)
+    k, theta, sigma = 11.0, 0.3, 2.0 / n
+    F = np.empty(mesh.num_dofs, dtype=np.complex128)
+    ptr = ctypes.c_void_p(F.ctypes.data)
+    assert lib.helm_load_planewave(dim, order, 1.0 / n, k, theta, ptr) == 0
+    ref = fem.load_planewave(mesh, M, k, theta)
+    assert np.linalg.norm(F - ref) <= 1e-12 * np.linalg.norm(ref)
+    assert lib.helm_load_gaussian(dim, order, 1.0 / n, sigma, 0.5, 0.5, 0.5, ptr) == 0
+    ref = fem.load_gaussian(mesh, M, sigma)
+    assert np.linalg.norm(F - ref) <= 1e-12 * np.linalg.norm(ref)
+
+
+def test_host_load_builders_refuse_bad_meshes():
+    import ctypes
+    import numpy as np
+    from paper_2104_01439_gb300 import _binding as b
+    lib = b.load()
+    F = np.zeros(4, dtype=np.complex128)
+    ptr = ctypes.c_void_p(F.ctypes.data)
+    bad = [(2, 1, 1.0 / 5), (2, 1, 1.0 / 2), (3, 2, 1.0 / 8), (4, 1, 1.0 / 8), (2, 1, 1e-7),
+           (2, 1, 1.0 / 65536), (3, 1, 1.0 / 1024), (2, 1, 0.0), (2, 1, -0.25)]
+    einval = int(re.search(r"#define HELM_EINVAL \((-?\d+)\)", open(HEADER).read()).group(1))
+    for dim, order, h in bad:
+        assert lib.helm_load_planewave(dim, order, h, 10.0, 0.3, ptr) == einval, (dim, order, h)
+        assert lib.helm_load_gaussian(dim, order, h, 0.1, 0.5, 0.5, 0.5, ptr) == einval, (dim, order, h)
+    assert lib.helm_load_planewave(2, 1, 1.0 / 8, 10.0, 0.3, None) == einval
+    assert lib.helm_load_planewave(2, 1, 1.0 / 8, 0.0, 0.3, ptr) == einval
+    assert np.all(F == 0)
