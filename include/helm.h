@@ -43,7 +43,7 @@ extern "C" {
 #define HELM_ECUDA (-3)      /* a CUDA runtime call failed */
 #define HELM_EZEROPIVOT (-4) /* coarse factorisation met a zero/non-finite pivot (eps = 0 can) */
 #define HELM_ETIMEOUT (-5)   /* a bounded device-side wait ran out */
-#define HELM_ENOTSUP (-6)    /* configuration not supported by this build/device */
+#define HELM_ENOTSUP (-6)    /* configuration the library or the device does not support */
 #define HELM_ESCRATCH (-7)   /* problem too large for the fixed scratch of helm_coarse_solve_noalloc */
 
 /* ---- helm_result.status (non-fatal outcome of a solve) --------------- */
