@@ -174,6 +174,30 @@ int helm_rhs_gaussian(helm_t h, double sigma, double cx, double cy, double cz, v
 int helm_load_planewave(int dim, int order, double h, double k, double theta, void* F_host);
 int helm_load_gaussian(int dim, int order, double h, double sigma, double cx, double cy, double cz, void* F_host);
 
+/* ---- host-only inspection of the operator tables (no GPU work) ----------- */
+
+/* Element families: Lagrange P_order on the cells split into triangles / Kuhn tetrahedra
+ * (the solver's discretisation), or tensor-product Q_order on squares / cubes (Sec. 2). */
+#define HELM_SIMPLICES 0
+#define HELM_TENSOR 1
+
+/* Row `dof` of the unit-coefficient matrices K (stiffness), M (mass) and B (boundary mass)
+ * on the mesh of (dim, order, h), read from the per-class tables that the matrix-free kernels
+ * use (Sec. 2, eq. discreteproblem): coefficient o belongs to the neighbour at per-axis offset
+ * d_ax = (o / (2R+1)^ax) mod (2R+1) - R, x first, R = order; neighbours outside the lattice get
+ * 0. K, M, B: caller arrays of (2*order+1)^dim doubles. dof: lexicographic lattice index, x
+ * fastest. HELM_EINVAL for a mesh helm_setup refuses, an element family not supported, a dof out
+ * of range or a null array. */
+int helm_host_stencil_row(int dim, int order, int elements, double h, int64_t dof, double* K, double* M,
+                          double* B);
+
+/* Row `fine_dof` of the canonical interpolation P from the 2h space to the h space (Sec. 4,
+ * the matrix I^(l)), read from the per-class weights the transfer kernels use: *count entries,
+ * coarse lattice indices in cols (x fastest) and weights in w (arrays of (order+1)^dim).
+ * HELM_EINVAL as for helm_host_stencil_row. */
+int helm_host_prolongation_row(int dim, int order, int elements, double h, int64_t fine_dof, int64_t* cols,
+                               double* w, int* count);
+
 /* ---- individual hot-path steps (device complex128 buffers) ------------- */
 
 /* y = A x with A = A0 (which = 0) or A_eps (which = 1), matrix-free, FP64 (Sec. 6).

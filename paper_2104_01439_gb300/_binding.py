@@ -14,6 +14,8 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "libhelm.so")
 
 HELM_OK = 0
+HELM_SIMPLICES = 0
+HELM_TENSOR = 1
 HELM_FP64 = 0
 HELM_MIXED = 1
 STATUS = {0: "converged", 1: "maxit", 2: "breakdown", 3: "nonfinite"}
@@ -25,7 +27,7 @@ EXPORTS = [
     "helm_last_profile", "helm_set_profiling", "helm_coarse_solve_noalloc",
     "helm_request_bytes", "helm_device_bytes", "helm_server_create", "helm_server_submit", "helm_server_poll",
     "helm_server_wait", "helm_server_drain", "helm_server_destroy", "helm_load_planewave", "helm_load_gaussian",
-    "helm_operator_setup", "helm_smooth",
+    "helm_operator_setup", "helm_smooth", "helm_host_stencil_row", "helm_host_prolongation_row",
 ]
 
 
@@ -107,6 +109,9 @@ def load(path: str = LIB_PATH):
     lib.helm_operator_setup.argtypes = [d, d, i, d, ctypes.POINTER(HelmOpts), ctypes.POINTER(vp)]
     lib.helm_smooth.argtypes = [vp, vp, vp, i]
     lib.helm_load_gaussian.argtypes = [i, i, d, d, d, d, d, vp]
+    dp = ctypes.POINTER(ctypes.c_double)
+    lib.helm_host_stencil_row.argtypes = [i, i, i, d, ctypes.c_int64, dp, dp, dp]
+    lib.helm_host_prolongation_row.argtypes = [i, i, i, d, ctypes.c_int64, i64p, dp, ctypes.POINTER(i)]
     for name in EXPORTS:
         if name not in ("helm_default_opts", "helm_destroy", "helm_strerror", "helm_last_cuda_error",
                         "helm_server_destroy"):

@@ -937,6 +937,24 @@ int helm_load_planewave(int dim, int order, double h, double k, double theta, vo
   return HELM_OK;
 }
 
+int helm_host_stencil_row(int dim, int order, int elements, double h, int64_t dof, double* K, double* M,
+                          double* B) {
+  const int n = mesh_n(dim, order, h);
+  if (n < 0 || elements != HELM_SIMPLICES || !K || !M || !B) return HELM_EINVAL;
+  HostTables t;
+  const int rc = build_tables(dim, order, n, &t);
+  return rc != HELM_OK ? rc : host_stencil_row(t, dof, K, M, B);
+}
+
+int helm_host_prolongation_row(int dim, int order, int elements, double h, int64_t fine_dof, int64_t* cols,
+                               double* w, int* count) {
+  const int n = mesh_n(dim, order, h);
+  if (n < 0 || elements != HELM_SIMPLICES || !cols || !w || !count) return HELM_EINVAL;
+  HostTables t;
+  const int rc = build_tables(dim, order, n, &t);
+  return rc != HELM_OK ? rc : host_prolongation_row(t, fine_dof, cols, w, count);
+}
+
 int helm_load_gaussian(int dim, int order, double h, double sigma, double cx, double cy, double cz, void* F_host) {
   const int n = mesh_n(dim, order, h);
   if (n < 0 || !F_host || !(sigma > 0)) return HELM_EINVAL;

@@ -190,6 +190,8 @@ struct HostTables {
 };
 
 int build_tables(int dim, int order, int n, HostTables* t);
+int host_stencil_row(const HostTables& t, int64_t dof, double* K, double* M, double* B);
+int host_prolongation_row(const HostTables& t, int64_t fine_dof, int64_t* cols, double* w, int* count);
 void rhs_planewave(int dim, int order, int n, double k, double theta, double2* F);
 void rhs_gaussian(int dim, int order, int n, double sigma, const double* c, double2* F);
 

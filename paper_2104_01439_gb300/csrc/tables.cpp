@@ -500,6 +500,70 @@ int build_tables(int d, int order, int n, HostTables* t) {
   return HELM_OK;
 }
 
+// Host inspection of the tables, with the kernels' own class and transfer mapping.
+int host_stencil_row(const HostTables& t, int64_t dof, double* K, double* M, double* B) {
+  const GridDesc& g = t.fine;
+  if (dof < 0 || dof >= g.N) return HELM_EINVAL;
+  int a[3] = {0, 0, 0};
+  int64_t r = dof;
+  int cls = 0, mul = 1;
+  for (int ax = 0; ax < g.dim; ++ax) {
+    a[ax] = (int)(r % g.W);
+    r /= g.W;
+    cls += axis_class(a[ax], g.W, g.R, g.q) * mul;
+    mul *= g.C1;
+  }
+  const int side = 2 * g.R + 1;
+  for (int o = 0; o < g.noff; ++o) {
+    int oo = o;
+    bool in = true;
+    for (int ax = 0; ax < g.dim; ++ax) {
+      const int b = a[ax] + oo % side - g.R;
+      oo /= side;
+      in &= b >= 0 && b < g.W;
+    }
+    const size_t i = (size_t)cls * g.noff + o;
+    K[o] = in ? t.Kf[i] : 0.0;
+    M[o] = in ? t.Mf[i] : 0.0;
+    B[o] = in ? t.Bf[i] : 0.0;
+  }
+  return HELM_OK;
+}
+
+int host_prolongation_row(const HostTables& t, int64_t fine_dof, int64_t* cols, double* w, int* count) {
+  const GridDesc &f = t.fine, &c = t.coarse;
+  if (fine_dof < 0 || fine_dof >= f.N) return HELM_EINVAL;
+  int a[3] = {0, 0, 0}, anc[3] = {0, 0, 0};
+  int64_t r = fine_dof;
+  int cls = 0, mul = 1;
+  for (int ax = 0; ax < f.dim; ++ax) {
+    a[ax] = (int)(r % f.W);
+    r /= f.W;
+    cls += mod_period(a[ax], t.pf) * mul;
+    mul *= t.pf;
+    anc[ax] = div_period(a[ax], t.pf) * c.q;
+  }
+  int n = 0;
+  for (int o = 0; o < t.npo; ++o) {
+    const double wv = t.pw[(size_t)cls * t.npo + o];
+    if (wv == 0.0) continue;
+    int oo = o;
+    int64_t col = 0, st = 1;
+    for (int ax = 0; ax < f.dim; ++ax) {
+      const int A = anc[ax] + oo % (c.q + 1);
+      oo /= c.q + 1;
+      if (A < 0 || A >= c.W) return HELM_EINVAL;   // a nonzero weight outside the coarse lattice
+      col += (int64_t)A * st;
+      st *= c.W;
+    }
+    cols[n] = col;
+    w[n] = wv;
+    ++n;
+  }
+  *count = n;
+  return HELM_OK;
+}
+
 void rhs_planewave(int d, int order, int n, double k, double theta, double2* F) {
   SMesh m{d, order, n, order * n + 1, 1.0 / n};
   int64_t N = 1;

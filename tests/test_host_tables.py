@@ -1,0 +1,101 @@
+"""Host tables of the matrix-free operators against the oracle's assembled matrices (CPU).
+
+The CUDA kernels apply K, M, B and the interpolation P from per-class tables built on the host
+(coefficients read off a small reference mesh, prolongation weights per position class). The
+C ABI's inspection entry points return any row of those tables through the kernels' own class
+mapping, so every row can be compared with the oracle's assembled CSR matrices (Sec. 2,
+eq. discreteproblem; Sec. 4, the interpolation I^(l)) without a GPU.
+"""
+import ctypes
+
+import numpy as np
+import pytest
+
+from oracle import fem
+from paper_2104_01439_gb300 import _binding as b
+
+CASES = [(2, 1, 8), (2, 1, 10), (2, 2, 6), (2, 2, 8), (3, 1, 4), (3, 1, 6)]
+
+
+def _stencil_rows(lib, dim, order, elements, h, N):
+    R = order
+    side = 2 * R + 1
+    noff = side ** dim
+    K, M, B = ((ctypes.c_double * noff)() for _ in range(3))
+    rows = []
+    for dof in range(N):
+        assert lib.helm_host_stencil_row(dim, order, elements, h, dof, K, M, B) == 0
+        rows.append((np.array(K[:]), np.array(M[:]), np.array(B[:])))
+    return rows, side, noff
+
+
+def _offsets(dim, side, R, W):
+    """Linear lattice offset of every box point (x fastest)."""
+    out = []
+    for o in range(side ** dim):
+        oo, lin, st = o, 0, 1
+        for _ in range(dim):
+            lin += (oo % side - R) * st
+            oo //= side
+            st *= W
+        out.append(lin)
+    return np.array(out)
+
+
+def _compare_rows(rows, mats, dim, order, W):
+    side = 2 * order + 1
+    offs = _offsets(dim, side, order, W)
+    for dof, got in enumerate(rows):
+        for g, A in zip(got, mats):
+            ref = A.getrow(dof)
+            dense = dict(zip(ref.indices, ref.data))
+            cols = dof + offs
+            # every nonzero of the oracle row lies in the box, and the box values agree
+            inbox = {c for c, v in zip(cols, g) if v != 0.0}
+            assert set(k for k, v in dense.items() if abs(v) > 1e-15) <= set(cols.tolist())
+            for c, v in zip(cols, g):
+                if v != 0.0:
+                    assert c in dense, (dof, c)
+                assert abs(v - dense.get(c, 0.0)) <= 1e-13 * max(1.0, abs(v)), (dof, c, v, dense.get(c))
+            assert inbox <= set(dense)
+
+
+@pytest.mark.parametrize("dim,order,n", CASES)
+def test_stencil_tables_equal_assembled_rows(dim, order, n):
+    lib = b.load()
+    for level_n in (n, n // 2):
+        if level_n < 4 or level_n % 2:
+            continue                          # the ABI takes meshes with an even 1/h >= 4
+        mesh = fem.build_mesh(dim, order, level_n)
+        K, M, B = fem.assemble(mesh)
+        rows, _, _ = _stencil_rows(lib, dim, order, b.HELM_SIMPLICES, 1.0 / level_n, mesh.num_dofs)
+        _compare_rows(rows, (K, M, B), dim, order, order * level_n + 1)
+
+
+@pytest.mark.parametrize("dim,order,n", CASES)
+def test_prolongation_weights_equal_interpolation(dim, order, n):
+    lib = b.load()
+    fine, coarse = fem.build_mesh(dim, order, n), fem.build_mesh(dim, order, n // 2)
+    P = fem.prolongation(coarse, fine).tocsr()
+    cap = (order + 1) ** dim
+    cols = (ctypes.c_int64 * cap)()
+    w = (ctypes.c_double * cap)()
+    cnt = ctypes.c_int()
+    for dof in range(fine.num_dofs):
+        assert lib.helm_host_prolongation_row(dim, order, b.HELM_SIMPLICES, 1.0 / n, dof, cols, w,
+                                              ctypes.byref(cnt)) == 0
+        got = {cols[i]: w[i] for i in range(cnt.value)}
+        row = P.getrow(dof)
+        ref = {c: v for c, v in zip(row.indices, row.data) if abs(v) > 1e-15}
+        assert set(got) == set(ref), dof
+        for c in ref:
+            assert abs(got[c] - ref[c]) <= 1e-14, (dof, c)
+
+
+def test_inspection_refuses_bad_arguments():
+    lib = b.load()
+    K, M, B = ((ctypes.c_double * 9)() for _ in range(3))
+    assert lib.helm_host_stencil_row(2, 1, b.HELM_SIMPLICES, 1.0 / 8, 81, K, M, B) == -1   # dof out of range
+    assert lib.helm_host_stencil_row(2, 1, b.HELM_SIMPLICES, 1.0 / 7, 0, K, M, B) == -1    # odd n
+    assert lib.helm_host_stencil_row(2, 1, 7, 1.0 / 8, 0, K, M, B) == -1                   # unknown family
+    assert lib.helm_host_stencil_row(2, 1, b.HELM_SIMPLICES, 1.0 / 8, -1, K, M, B) == -1
