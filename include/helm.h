@@ -53,6 +53,11 @@ extern "C" {
 #define HELM_NONFINITE 3     /* NaN/Inf met in the residual; x is not meaningful */
 
 /* ---- precision of the preconditioner (opts.precision) ---------------- */
+/* Element families: Lagrange P_order on the cells split into triangles / Kuhn tetrahedra
+ * (helm_setup), or tensor-product Q_order on squares / cubes (helm_setup_q; Sec. 2). */
+#define HELM_SIMPLICES 0
+#define HELM_TENSOR 1
+
 #define HELM_FP64 0          /* everything in complex128 */
 #define HELM_MIXED 1         /* V-cycle (smoother, transfers, coarse triangular
                                 solves) in complex64; outer apply, Arnoldi basis
@@ -110,6 +115,15 @@ int helm_setup(double k, double h, int order, double shift, const helm_opts* opt
  * return HELM_EINVAL. Same arguments and checks as helm_setup.
  */
 int helm_operator_setup(double k, double h, int order, double shift, const helm_opts* opts, helm_t* out);
+
+/*
+ * helm_setup with the paper's own elements: tensor-product Lagrange Q_order on the squares
+ * (cubes) of the uniform grid, order 1 or 2 in 2D and 1 in 3D (Sec. 2: "standard Q_p"; the
+ * lattice points are the Gauss-Lobatto points, equispaced for these orders). The lattice, DoF
+ * numbering, buffers and every other call are those of helm_setup; the stencils, transfers
+ * and load vectors are the Q_order ones. Same checks and errors as helm_setup.
+ */
+int helm_setup_q(double k, double h, int order, double shift, const helm_opts* opts, helm_t* out);
 
 /* Number of complex DoFs N = (order/h + 1)^dim of the fine space. */
 int helm_num_dofs(helm_t h, int64_t* n);
@@ -173,13 +187,13 @@ int helm_rhs_gaussian(helm_t h, double sigma, double cx, double cy, double cz, v
  * 2^30 DoFs or more), a null F_host, k <= 0 or sigma <= 0; nothing is written then. */
 int helm_load_planewave(int dim, int order, double h, double k, double theta, void* F_host);
 int helm_load_gaussian(int dim, int order, double h, double sigma, double cx, double cy, double cz, void* F_host);
+/* The same with the element family given (HELM_SIMPLICES as above, or HELM_TENSOR for the
+ * Q_order meshes of helm_setup_q). */
+int helm_load_planewave_e(int dim, int order, int elements, double h, double k, double theta, void* F_host);
+int helm_load_gaussian_e(int dim, int order, int elements, double h, double sigma, double cx, double cy, double cz,
+                         void* F_host);
 
 /* ---- host-only inspection of the operator tables (no GPU work) ----------- */
-
-/* Element families: Lagrange P_order on the cells split into triangles / Kuhn tetrahedra
- * (the solver's discretisation), or tensor-product Q_order on squares / cubes (Sec. 2). */
-#define HELM_SIMPLICES 0
-#define HELM_TENSOR 1
 
 /* Row `dof` of the unit-coefficient matrices K (stiffness), M (mass) and B (boundary mass)
  * on the mesh of (dim, order, h), read from the per-class tables that the matrix-free kernels

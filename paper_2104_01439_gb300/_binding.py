@@ -28,6 +28,7 @@ EXPORTS = [
     "helm_request_bytes", "helm_device_bytes", "helm_server_create", "helm_server_submit", "helm_server_poll",
     "helm_server_wait", "helm_server_drain", "helm_server_destroy", "helm_load_planewave", "helm_load_gaussian",
     "helm_operator_setup", "helm_smooth", "helm_host_stencil_row", "helm_host_prolongation_row",
+    "helm_setup_q", "helm_load_planewave_e", "helm_load_gaussian_e",
 ]
 
 
@@ -107,6 +108,9 @@ def load(path: str = LIB_PATH):
     lib.helm_server_destroy.restype = None
     lib.helm_load_planewave.argtypes = [i, i, d, d, d, vp]
     lib.helm_operator_setup.argtypes = [d, d, i, d, ctypes.POINTER(HelmOpts), ctypes.POINTER(vp)]
+    lib.helm_setup_q.argtypes = [d, d, i, d, ctypes.POINTER(HelmOpts), ctypes.POINTER(vp)]
+    lib.helm_load_planewave_e.argtypes = [i, i, i, d, d, d, vp]
+    lib.helm_load_gaussian_e.argtypes = [i, i, i, d, d, d, d, d, vp]
     lib.helm_smooth.argtypes = [vp, vp, vp, i]
     lib.helm_load_gaussian.argtypes = [i, i, d, d, d, d, d, vp]
     dp = ctypes.POINTER(ctypes.c_double)
@@ -165,7 +169,8 @@ class Solver:
 
     def __init__(self, k: float, n: int, order: int = 1, shift: float = 0.0, dim: int = 2,
                  omega: float = 0.6, nu: int = 2, restart: int = 50, maxit: int = 500,
-                 tol: float = 1e-8, precision: int = HELM_FP64, stream=None, operator_only: bool = False):
+                 tol: float = 1e-8, precision: int = HELM_FP64, stream=None, operator_only: bool = False,
+                 elements: int = HELM_SIMPLICES):
         import torch
         lib = load()
         o = HelmOpts()
@@ -177,7 +182,10 @@ class Solver:
         o.stream = ctypes.c_void_p(stream.cuda_stream)
         self._h = ctypes.c_void_p()
         self.k, self.n, self.order, self.shift, self.dim, self.precision = k, n, order, shift, dim, precision
-        setup = lib.helm_operator_setup if operator_only else lib.helm_setup
+        if elements not in (HELM_SIMPLICES, HELM_TENSOR) or (operator_only and elements != HELM_SIMPLICES):
+            raise ValueError("elements: HELM_SIMPLICES, or HELM_TENSOR for a full solver handle")
+        setup = (lib.helm_operator_setup if operator_only
+                 else lib.helm_setup_q if elements == HELM_TENSOR else lib.helm_setup)
         _check(setup(float(k), 1.0 / n, order, float(shift), ctypes.byref(o), ctypes.byref(self._h)))
         nd = ctypes.c_int64()
         _check(lib.helm_num_dofs(self._h, ctypes.byref(nd)))

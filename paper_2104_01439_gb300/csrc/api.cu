@@ -55,6 +55,7 @@ template <typename T> struct Prec {
 struct helm_ctx {
   int dim = 2, order = 1, n = 0;
   bool op_only = false;        // fine-level operators only (helm_operator_setup)
+  int elements = HELM_SIMPLICES;   // HELM_TENSOR: Q_order on squares / cubes (helm_setup_q)
   double k = 0, h = 0, shift = 0;
   helm_opts opts{};
   cudaStream_t s = nullptr;
@@ -613,7 +614,7 @@ void helm_destroy(helm_t h) {
 
 static int setup_impl(helm_ctx* h) {
   const helm_opts& o = h->opts;
-  int rc = build_tables(o.dim, h->order, h->n, &h->tab);
+  int rc = build_tables(o.dim, h->order, h->n, &h->tab, h->elements);
   if (rc) return rc;
   h->gf = h->tab.fine;
   h->gc = h->tab.coarse;
@@ -792,7 +793,7 @@ static int setup_impl(helm_ctx* h) {
 }
 
 static int setup_any(double k, double h, int order, double shift, const helm_opts* opts, helm_t* out,
-                     bool op_only) {
+                     bool op_only, int elements = HELM_SIMPLICES) {
   if (!out) return HELM_EINVAL;
   *out = nullptr;
   helm_opts o;
@@ -817,6 +818,7 @@ static int setup_any(double k, double h, int order, double shift, const helm_opt
   c->opts = o;
   c->s = (cudaStream_t)o.stream;
   c->op_only = op_only;
+  c->elements = elements;
   int rc = setup_impl(c);
   if (rc != HELM_OK) {
     helm_destroy(c);
@@ -832,6 +834,10 @@ int helm_setup(double k, double h, int order, double shift, const helm_opts* opt
 
 int helm_operator_setup(double k, double h, int order, double shift, const helm_opts* opts, helm_t* out) {
   return setup_any(k, h, order, shift, opts, out, true);
+}
+
+int helm_setup_q(double k, double h, int order, double shift, const helm_opts* opts, helm_t* out) {
+  return setup_any(k, h, order, shift, opts, out, false, HELM_TENSOR);
 }
 
 int helm_num_dofs(helm_t h, int64_t* n) {
@@ -907,14 +913,14 @@ int helm_batch_solve(int count, const helm_t* hs, const void* const* F, void* co
 
 int helm_rhs_planewave(helm_t h, double theta, void* F_host) {
   if (!h || !F_host) return HELM_EINVAL;
-  rhs_planewave(h->dim, h->order, h->n, h->k, theta, (double2*)F_host);
+  rhs_planewave(h->dim, h->order, h->n, h->k, theta, (double2*)F_host, h->elements);
   return HELM_OK;
 }
 
 int helm_rhs_gaussian(helm_t h, double sigma, double cx, double cy, double cz, void* F_host) {
   if (!h || !F_host || !(sigma > 0)) return HELM_EINVAL;
   double c[3] = {cx, cy, cz};
-  rhs_gaussian(h->dim, h->order, h->n, sigma, c, (double2*)F_host);
+  rhs_gaussian(h->dim, h->order, h->n, sigma, c, (double2*)F_host, h->elements);
   return HELM_OK;
 }
 
@@ -937,21 +943,39 @@ int helm_load_planewave(int dim, int order, double h, double k, double theta, vo
   return HELM_OK;
 }
 
+int helm_load_planewave_e(int dim, int order, int elements, double h, double k, double theta, void* F_host) {
+  const int n = mesh_n(dim, order, h);
+  if (n < 0 || !(elements == HELM_SIMPLICES || elements == HELM_TENSOR) || !F_host || !(k > 0)) return HELM_EINVAL;
+  rhs_planewave(dim, order, n, k, theta, (double2*)F_host, elements);
+  return HELM_OK;
+}
+
+int helm_load_gaussian_e(int dim, int order, int elements, double h, double sigma, double cx, double cy, double cz,
+                         void* F_host) {
+  const int n = mesh_n(dim, order, h);
+  if (n < 0 || !(elements == HELM_SIMPLICES || elements == HELM_TENSOR) || !F_host || !(sigma > 0))
+    return HELM_EINVAL;
+  double c[3] = {cx, cy, cz};
+  rhs_gaussian(dim, order, n, sigma, c, (double2*)F_host, elements);
+  return HELM_OK;
+}
+
 int helm_host_stencil_row(int dim, int order, int elements, double h, int64_t dof, double* K, double* M,
                           double* B) {
   const int n = mesh_n(dim, order, h);
-  if (n < 0 || elements != HELM_SIMPLICES || !K || !M || !B) return HELM_EINVAL;
+  if (n < 0 || !(elements == HELM_SIMPLICES || elements == HELM_TENSOR) || !K || !M || !B) return HELM_EINVAL;
   HostTables t;
-  const int rc = build_tables(dim, order, n, &t);
+  const int rc = build_tables(dim, order, n, &t, elements);
   return rc != HELM_OK ? rc : host_stencil_row(t, dof, K, M, B);
 }
 
 int helm_host_prolongation_row(int dim, int order, int elements, double h, int64_t fine_dof, int64_t* cols,
                                double* w, int* count) {
   const int n = mesh_n(dim, order, h);
-  if (n < 0 || elements != HELM_SIMPLICES || !cols || !w || !count) return HELM_EINVAL;
+  if (n < 0 || !(elements == HELM_SIMPLICES || elements == HELM_TENSOR) || !cols || !w || !count)
+    return HELM_EINVAL;
   HostTables t;
-  const int rc = build_tables(dim, order, n, &t);
+  const int rc = build_tables(dim, order, n, &t, elements);
   return rc != HELM_OK ? rc : host_prolongation_row(t, fine_dof, cols, w, count);
 }
 

@@ -241,6 +241,7 @@ void cell_simplices(int d, std::vector<std::array<std::array<int, 3>, 4>>& out) 
 struct SMesh {
   int d, order, n, W;
   double h;
+  int elements = HELM_SIMPLICES;   // or HELM_TENSOR: one square / cube element per cell
   int64_t idx(const int* c) const {
     int64_t s = 0;
     for (int ax = d - 1; ax >= 0; --ax) s = s * W + c[ax];
@@ -326,6 +327,156 @@ template <typename Fn> void for_each_boundary_facet(const SMesh& m, Fn fn) {
       }
 }
 
+// ---------------------------------------------------------------------------
+// Tensor-product Q_p elements (p <= 2: the Gauss-Lobatto points are the equispaced
+// ones): 1D Lagrange basis on [0, 1] at x_l = l / p, 1D element matrices on [0, h]
+// integrated exactly by 4-point Gauss-Legendre, element matrices as tensor products with
+// the local index x fastest (l = sum_ax l_ax (p+1)^ax).
+// ---------------------------------------------------------------------------
+double lagrange1(int p, int l, double x) {
+  if (p == 1) return l == 0 ? 1.0 - x : x;
+  return l == 0 ? (2.0 * x - 1.0) * (x - 1.0) : l == 1 ? 4.0 * x * (1.0 - x) : x * (2.0 * x - 1.0);
+}
+double lagrange1_d(int p, int l, double x) {
+  if (p == 1) return l == 0 ? -1.0 : 1.0;
+  return l == 0 ? 4.0 * x - 3.0 : l == 1 ? 4.0 - 8.0 * x : 4.0 * x - 1.0;
+}
+void element_1d(int p, double h, std::vector<double>& K1, std::vector<double>& M1) {
+  std::vector<double> x, w;
+  gauss_legendre01(4, x, w);
+  const int nb = p + 1;
+  K1.assign(nb * nb, 0.0);
+  M1.assign(nb * nb, 0.0);
+  for (size_t q = 0; q < x.size(); ++q)
+    for (int i = 0; i < nb; ++i)
+      for (int j = 0; j < nb; ++j) {
+        K1[i * nb + j] += w[q] * lagrange1_d(p, i, x[q]) * lagrange1_d(p, j, x[q]) / h;
+        M1[i * nb + j] += w[q] * lagrange1(p, i, x[q]) * lagrange1(p, j, x[q]) * h;
+      }
+}
+// local index l -> per-axis indices (x fastest)
+void split_local(int l, int nb1, int dims, int* la) {
+  for (int ax = 0; ax < dims; ++ax) {
+    la[ax] = l % nb1;
+    l /= nb1;
+  }
+}
+// tensor-product stiffness / mass of a d-cube and mass of a (d-1)-face
+void element_km_tensor(int d, int p, double h, std::vector<double>& K, std::vector<double>& M) {
+  std::vector<double> K1, M1;
+  element_1d(p, h, K1, M1);
+  const int nb1 = p + 1;
+  int nb = 1;
+  for (int ax = 0; ax < d; ++ax) nb *= nb1;
+  K.assign((size_t)nb * nb, 0.0);
+  M.assign((size_t)nb * nb, 0.0);
+  for (int i = 0; i < nb; ++i)
+    for (int j = 0; j < nb; ++j) {
+      int li[3], lj[3];
+      split_local(i, nb1, d, li);
+      split_local(j, nb1, d, lj);
+      double mass = 1.0, stiff = 0.0;
+      for (int ax = 0; ax < d; ++ax) {
+        double term = K1[li[ax] * nb1 + lj[ax]];
+        for (int bx = 0; bx < d; ++bx)
+          if (bx != ax) term *= M1[li[bx] * nb1 + lj[bx]];
+        stiff += term;
+        mass *= M1[li[ax] * nb1 + lj[ax]];
+      }
+      K[(size_t)i * nb + j] = stiff;
+      M[(size_t)i * nb + j] = mass;
+    }
+}
+void face_mass_tensor(int d, int p, double h, std::vector<double>& B) {
+  std::vector<double> K1, M1;
+  element_1d(p, h, K1, M1);
+  const int nb1 = p + 1, fd = d - 1;
+  int nb = 1;
+  for (int ax = 0; ax < fd; ++ax) nb *= nb1;
+  B.assign((size_t)nb * nb, 0.0);
+  for (int i = 0; i < nb; ++i)
+    for (int j = 0; j < nb; ++j) {
+      int li[3], lj[3];
+      split_local(i, nb1, fd, li);
+      split_local(j, nb1, fd, lj);
+      double v = 1.0;
+      for (int ax = 0; ax < fd; ++ax) v *= M1[li[ax] * nb1 + lj[ax]];
+      B[(size_t)i * nb + j] = v;
+    }
+}
+
+// Every element with its matrices: fn(local DoF lattice coords, Ke, Me).
+template <typename Fn> void for_each_element_km(const SMesh& m, Fn fn) {
+  if (m.elements == HELM_SIMPLICES) {
+    std::vector<double> Ke, Me;
+    for_each_element(m, [&](const std::vector<std::array<int, 3>>& loc, const double (*vx)[3]) {
+      element_km(m.d, m.order, vx, Ke, Me);
+      fn(loc, Ke, Me);
+    });
+    return;
+  }
+  std::vector<double> Ke, Me;
+  element_km_tensor(m.d, m.order, m.h, Ke, Me);
+  const int nb1 = m.order + 1;
+  int nb = 1;
+  for (int ax = 0; ax < m.d; ++ax) nb *= nb1;
+  std::vector<std::array<int, 3>> loc(nb);
+  const int nc3 = m.d == 3 ? m.n : 1;
+  for (int cz = 0; cz < nc3; ++cz)
+    for (int cy = 0; cy < m.n; ++cy)
+      for (int cx = 0; cx < m.n; ++cx) {
+        const int cell[3] = {cx, cy, cz};
+        for (int l = 0; l < nb; ++l) {
+          int la[3] = {0, 0, 0};
+          split_local(l, nb1, m.d, la);
+          for (int ax = 0; ax < 3; ++ax) loc[l][ax] = ax < m.d ? cell[ax] * m.order + la[ax] : 0;
+        }
+        fn(loc, Ke, Me);
+      }
+}
+
+// Every boundary facet with its mass matrix: fn(facet DoF lattice coords, Be, outward normal).
+template <typename Fn> void for_each_facet_mass(const SMesh& m, Fn fn) {
+  if (m.elements == HELM_SIMPLICES) {
+    std::vector<double> Be;
+    for_each_boundary_facet(m, [&](const std::vector<std::array<int, 3>>& loc, const double (*vx)[3],
+                                   const double* nrm) {
+      facet_mass(m.d, m.order, vx, Be);
+      fn(loc, Be, nrm);
+    });
+    return;
+  }
+  std::vector<double> Be;
+  face_mass_tensor(m.d, m.order, m.h, Be);
+  const int nb1 = m.order + 1, fd = m.d - 1;
+  int nb = 1;
+  for (int ax = 0; ax < fd; ++ax) nb *= nb1;
+  std::vector<std::array<int, 3>> loc(nb);
+  const int nc3 = m.d == 3 ? m.n : 1;
+  for (int cz = 0; cz < nc3; ++cz)
+    for (int cy = 0; cy < m.n; ++cy)
+      for (int cx = 0; cx < m.n; ++cx) {
+        const int cell[3] = {cx, cy, cz};
+        for (int ax = 0; ax < m.d; ++ax)
+          for (int side = 0; side < 2; ++side) {
+            if (cell[ax] != (side == 0 ? 0 : m.n - 1)) continue;
+            int others[2] = {0, 0}, no = 0;
+            for (int bx = 0; bx < m.d; ++bx)
+              if (bx != ax) others[no++] = bx;
+            for (int l = 0; l < nb; ++l) {
+              int la[3] = {0, 0, 0};
+              split_local(l, nb1, fd, la);
+              for (int bx = 0; bx < 3; ++bx) loc[l][bx] = 0;
+              loc[l][ax] = cell[ax] * m.order + (side == 0 ? 0 : m.order);
+              for (int k = 0; k < fd; ++k) loc[l][others[k]] = cell[others[k]] * m.order + la[k];
+            }
+            double nrm[3] = {0, 0, 0};
+            nrm[ax] = side == 0 ? -1.0 : 1.0;
+            fn(loc, Be, nrm);
+          }
+      }
+}
+
 // Dense assembly of K, M, B on a small mesh.
 void assemble_dense(const SMesh& m, std::vector<double>& K, std::vector<double>& M,
                     std::vector<double>& B) {
@@ -334,9 +485,8 @@ void assemble_dense(const SMesh& m, std::vector<double>& K, std::vector<double>&
   K.assign(N * N, 0.0);
   M.assign(N * N, 0.0);
   B.assign(N * N, 0.0);
-  std::vector<double> Ke, Me, Be;
-  for_each_element(m, [&](const std::vector<std::array<int, 3>>& loc, const double (*vx)[3]) {
-    element_km(m.d, m.order, vx, Ke, Me);
+  for_each_element_km(m, [&](const std::vector<std::array<int, 3>>& loc, const std::vector<double>& Ke,
+                             const std::vector<double>& Me) {
     int nb = (int)loc.size();
     for (int i = 0; i < nb; ++i)
       for (int j = 0; j < nb; ++j) {
@@ -345,9 +495,8 @@ void assemble_dense(const SMesh& m, std::vector<double>& K, std::vector<double>&
         M[r * N + c] += Me[i * nb + j];
       }
   });
-  for_each_boundary_facet(m, [&](const std::vector<std::array<int, 3>>& loc, const double (*vx)[3],
-                                 const double*) {
-    facet_mass(m.d, m.order, vx, Be);
+  for_each_facet_mass(m, [&](const std::vector<std::array<int, 3>>& loc, const std::vector<double>& Be,
+                             const double*) {
     int nb = (int)loc.size();
     for (int i = 0; i < nb; ++i)
       for (int j = 0; j < nb; ++j) {
@@ -368,7 +517,8 @@ int class_rep(int c, int Wr, int R, int q) {
 }
 
 void level_stencils(int d, int order, int n, GridDesc& g, std::vector<double>& Ks,
-                    std::vector<double>& Ms, std::vector<double>& Bs, int& ncls) {
+                    std::vector<double>& Ms, std::vector<double>& Bs, int& ncls,
+                    int elements = HELM_SIMPLICES) {
   g.dim = d;
   g.R = order;
   g.q = order;
@@ -385,7 +535,7 @@ void level_stencils(int d, int order, int n, GridDesc& g, std::vector<double>& K
   // reference mesh: smallest n_ref with a full interior period
   int nref = order == 1 ? 2 : 4;
   nref = std::min(nref, n);
-  SMesh rm{d, order, nref, order * nref + 1, 1.0 / n};   // same h as the target level
+  SMesh rm{d, order, nref, order * nref + 1, 1.0 / n, elements};   // same h as the target level
   std::vector<double> K, M, B;
   assemble_dense(rm, K, M, B);
   int64_t Nr = 1;
@@ -427,11 +577,12 @@ void level_stencils(int d, int order, int n, GridDesc& g, std::vector<double>& K
 
 }  // namespace
 
-int build_tables(int d, int order, int n, HostTables* t) {
+int build_tables(int d, int order, int n, HostTables* t, int elements) {
   if (!(d == 2 || d == 3) || !(order == 1 || order == 2) || (d == 3 && order != 1)) return HELM_EINVAL;
   if (n < 4 || n % 2) return HELM_EINVAL;
-  level_stencils(d, order, n, t->fine, t->Kf, t->Mf, t->Bf, t->ncls_f);
-  level_stencils(d, order, n / 2, t->coarse, t->Kc, t->Mc, t->Bc, t->ncls_c);
+  if (elements != HELM_SIMPLICES && elements != HELM_TENSOR) return HELM_EINVAL;
+  level_stencils(d, order, n, t->fine, t->Kf, t->Mf, t->Bf, t->ncls_f, elements);
+  level_stencils(d, order, n / 2, t->coarse, t->Kc, t->Mc, t->Bc, t->ncls_c, elements);
   // prolongation weights: evaluate coarse basis functions at fine positions
   int q = order;
   t->pf = 2 * q;
@@ -442,6 +593,26 @@ int build_tables(int d, int order, int n, HostTables* t) {
     t->npo *= q + 1;
   }
   t->pw.assign((size_t)t->npc * t->npo, 0.0);
+  if (elements == HELM_TENSOR) {
+    // Q_p: the coarse basis at fine position class c is the product of 1D Lagrange values at
+    // xi_ax = (c_ax / pf) in the coarse cell; coarse local node l is the box offset o = l
+    for (int c = 0; c < t->npc; ++c) {
+      double xi[3] = {0, 0, 0};
+      int tt = c;
+      for (int ax = 0; ax < d; ++ax) {
+        xi[ax] = (double)(tt % t->pf) / t->pf;
+        tt /= t->pf;
+      }
+      for (int o = 0; o < t->npo; ++o) {
+        int la[3] = {0, 0, 0};
+        split_local(o, q + 1, d, la);
+        double wv = 1.0;
+        for (int ax = 0; ax < d; ++ax) wv *= lagrange1(q, la[ax], xi[ax]);
+        if (std::fabs(wv) >= 1e-15) t->pw[(size_t)c * t->npo + o] = wv;
+      }
+    }
+    return HELM_OK;
+  }
   std::vector<std::array<std::array<int, 3>, 4>> simp;
   cell_simplices(d, simp);
   int nb = nbasis(d, order);
@@ -564,16 +735,14 @@ int host_prolongation_row(const HostTables& t, int64_t fine_dof, int64_t* cols, 
   return HELM_OK;
 }
 
-void rhs_planewave(int d, int order, int n, double k, double theta, double2* F) {
-  SMesh m{d, order, n, order * n + 1, 1.0 / n};
+void rhs_planewave(int d, int order, int n, double k, double theta, double2* F, int elements) {
+  SMesh m{d, order, n, order * n + 1, 1.0 / n, elements};
   int64_t N = 1;
   for (int ax = 0; ax < d; ++ax) N *= m.W;
   std::memset(F, 0, sizeof(double2) * N);
   double dir[3] = {std::cos(theta), std::sin(theta), 0.0};
-  std::vector<double> Be;
-  for_each_boundary_facet(m, [&](const std::vector<std::array<int, 3>>& loc, const double (*vx)[3],
-                                 const double* nrm) {
-    facet_mass(d, order, vx, Be);
+  for_each_facet_mass(m, [&](const std::vector<std::array<int, 3>>& loc, const std::vector<double>& Be,
+                             const double* nrm) {
     int nb = (int)loc.size();
     double dn = dir[0] * nrm[0] + dir[1] * nrm[1] + dir[2] * nrm[2];
     for (int j = 0; j < nb; ++j) {
@@ -590,11 +759,11 @@ void rhs_planewave(int d, int order, int n, double k, double theta, double2* F) 
   });
 }
 
-void rhs_gaussian(int d, int order, int n, double sigma, const double* c, double2* F) {
+void rhs_gaussian(int d, int order, int n, double sigma, const double* c, double2* F, int elements) {
   GridDesc g;
   std::vector<double> Ks, Ms, Bs;
   int ncls;
-  level_stencils(d, order, n, g, Ks, Ms, Bs, ncls);
+  level_stencils(d, order, n, g, Ks, Ms, Bs, ncls, elements);
   double h = 1.0 / n / order;
   int W = g.W, side = 2 * g.R + 1;
   std::vector<double> f(g.N);

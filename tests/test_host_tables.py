@@ -99,3 +99,72 @@ def test_inspection_refuses_bad_arguments():
     assert lib.helm_host_stencil_row(2, 1, b.HELM_SIMPLICES, 1.0 / 7, 0, K, M, B) == -1    # odd n
     assert lib.helm_host_stencil_row(2, 1, 7, 1.0 / 8, 0, K, M, B) == -1                   # unknown family
     assert lib.helm_host_stencil_row(2, 1, b.HELM_SIMPLICES, 1.0 / 8, -1, K, M, B) == -1
+
+
+Q_CASES = [(2, 1, 8), (2, 1, 12), (2, 2, 6), (2, 2, 8), (3, 1, 4), (3, 1, 6)]
+
+
+@pytest.mark.parametrize("dim,order,n", Q_CASES)
+def test_tensor_tables_equal_assembled_q_rows(dim, order, n):
+    """Q_order on squares / cubes (Sec. 2): the tables equal the rows of oracle/qfem.py's
+    element-by-element assembly, fine and coarse level, and the transfer weights equal its
+    tensor-product interpolation."""
+    from oracle import qfem
+    lib = b.load()
+    for level_n in (n, n // 2):
+        if level_n < 4 or level_n % 2:
+            continue
+        mesh = qfem.build_mesh(dim, order, level_n)
+        K, _, M, B, _ = qfem.assemble(mesh)
+        rows, _, _ = _stencil_rows(lib, dim, order, b.HELM_TENSOR, 1.0 / level_n, mesh.num_dofs)
+        _compare_rows(rows, (K, M, B), dim, order, order * level_n + 1)
+    fine, coarse = qfem.build_mesh(dim, order, n), qfem.build_mesh(dim, order, n // 2)
+    P = qfem.prolongation(coarse, fine).tocsr()
+    cap = (order + 1) ** dim
+    cols, w, cnt = (ctypes.c_int64 * cap)(), (ctypes.c_double * cap)(), ctypes.c_int()
+    for dof in range(fine.num_dofs):
+        assert lib.helm_host_prolongation_row(dim, order, b.HELM_TENSOR, 1.0 / n, dof, cols, w,
+                                              ctypes.byref(cnt)) == 0
+        got = {cols[i]: w[i] for i in range(cnt.value)}
+        row = P.getrow(dof)
+        ref = {c: v for c, v in zip(row.indices, row.data) if abs(v) > 1e-15}
+        assert set(got) == set(ref), dof
+        assert all(abs(got[c] - ref[c]) <= 1e-14 for c in ref), dof
+
+
+def test_q1_stencil_differs_from_p1():
+    """The two families really give different operators (Q1 couples all eight neighbours)."""
+    lib = b.load()
+    K, M, B = ((ctypes.c_double * 9)() for _ in range(3))
+    dof = 4 + 9 * 4                                # an interior DoF of the 8 x 8 mesh
+    assert lib.helm_host_stencil_row(2, 1, b.HELM_SIMPLICES, 1.0 / 8, dof, K, M, B) == 0
+    p1 = np.array(K[:])
+    assert lib.helm_host_stencil_row(2, 1, b.HELM_TENSOR, 1.0 / 8, dof, K, M, B) == 0
+    q1 = np.array(K[:])
+    assert np.count_nonzero(p1) == 5 and np.count_nonzero(q1) == 9
+    assert np.allclose(q1 * 3, [-1, -1, -1, -1, 8, -1, -1, -1, -1])
+
+
+@pytest.mark.parametrize("dim,order,n", [(2, 1, 8), (2, 2, 8), (3, 1, 6)])
+def test_tensor_load_vectors_equal_oracle(dim, order, n):
+    """Q_order load vectors (Sec. 2, F(v) = int f v + int_dOmega g v): the plane wave's impedance
+    data per boundary face and the interpolated Gaussian times the mass matrix."""
+    from oracle import qfem
+    lib = b.load()
+    mesh = qfem.build_mesh(dim, order, n)
+    _, _, M, _, _ = qfem.assemble(mesh)
+    F = np.empty(mesh.num_dofs, dtype=np.complex128)
+    ptr = ctypes.c_void_p(F.ctypes.data)
+    k, theta, sigma = 9.0, 0.3, 2.0 / n
+    assert lib.helm_load_planewave_e(dim, order, b.HELM_TENSOR, 1.0 / n, k, theta, ptr) == 0
+    ref = qfem.load_planewave(mesh, M, k, theta)
+    assert np.linalg.norm(F - ref) <= 1e-12 * np.linalg.norm(ref)
+    assert lib.helm_load_gaussian_e(dim, order, b.HELM_TENSOR, 1.0 / n, sigma, 0.5, 0.5, 0.5, ptr) == 0
+    f = np.exp(-np.sum((mesh.coords - 0.5) ** 2, axis=1) / (2 * sigma * sigma))
+    ref = M @ f
+    assert np.linalg.norm(F - ref) <= 1e-12 * np.linalg.norm(ref)
+    # the simplex family through the same entry point equals the original builder
+    G = np.empty_like(F)
+    assert lib.helm_load_planewave_e(dim, order, b.HELM_SIMPLICES, 1.0 / n, k, theta, ptr) == 0
+    assert lib.helm_load_planewave(dim, order, 1.0 / n, k, theta, ctypes.c_void_p(G.ctypes.data)) == 0
+    assert np.array_equal(F, G)
