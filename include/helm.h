@@ -196,14 +196,16 @@ int helm_load_gaussian_e(int dim, int order, int elements, double h, double sigm
 /* ---- host-only inspection of the operator tables (no GPU work) ----------- */
 
 /* Row `dof` of the unit-coefficient matrices K (stiffness), M (mass) and B (boundary mass)
- * on the mesh of (dim, order, h), read from the per-class tables that the matrix-free kernels
- * use (Sec. 2, eq. discreteproblem): coefficient o belongs to the neighbour at per-axis offset
+ * of the solver for the mesh of (dim, order, h): level 0 is that mesh, level 1 its coarse
+ * mesh of spacing 2h (the twogrid coarse level, built by the solver from these tables). The
+ * row is read from the per-class tables that the matrix-free kernels use (Sec. 2,
+ * eq. discreteproblem): coefficient o belongs to the neighbour at per-axis offset
  * d_ax = (o / (2R+1)^ax) mod (2R+1) - R, x first, R = order; neighbours outside the lattice get
- * 0. K, M, B: caller arrays of (2*order+1)^dim doubles. dof: lexicographic lattice index, x
- * fastest. HELM_EINVAL for a mesh helm_setup refuses, an element family not supported, a dof out
- * of range or a null array. */
-int helm_host_stencil_row(int dim, int order, int elements, double h, int64_t dof, double* K, double* M,
-                          double* B);
+ * 0. K, M, B: caller arrays of (2*order+1)^dim doubles. dof: lexicographic lattice index of that
+ * level, x fastest. HELM_EINVAL for a mesh helm_setup refuses, an element family not supported,
+ * a level other than 0 or 1, a dof out of range or a null array. */
+int helm_host_stencil_row(int dim, int order, int elements, double h, int level, int64_t dof, double* K,
+                          double* M, double* B);
 
 /* Row `fine_dof` of the canonical interpolation P from the 2h space to the h space (Sec. 4,
  * the matrix I^(l)), read from the per-class weights the transfer kernels use: *count entries,

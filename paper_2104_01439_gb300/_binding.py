@@ -114,7 +114,7 @@ def load(path: str = LIB_PATH):
     lib.helm_smooth.argtypes = [vp, vp, vp, i]
     lib.helm_load_gaussian.argtypes = [i, i, d, d, d, d, d, vp]
     dp = ctypes.POINTER(ctypes.c_double)
-    lib.helm_host_stencil_row.argtypes = [i, i, i, d, ctypes.c_int64, dp, dp, dp]
+    lib.helm_host_stencil_row.argtypes = [i, i, i, d, i, ctypes.c_int64, dp, dp, dp]
     lib.helm_host_prolongation_row.argtypes = [i, i, i, d, ctypes.c_int64, i64p, dp, ctypes.POINTER(i)]
     for name in EXPORTS:
         if name not in ("helm_default_opts", "helm_destroy", "helm_strerror", "helm_last_cuda_error",

@@ -960,13 +960,15 @@ int helm_load_gaussian_e(int dim, int order, int elements, double h, double sigm
   return HELM_OK;
 }
 
-int helm_host_stencil_row(int dim, int order, int elements, double h, int64_t dof, double* K, double* M,
-                          double* B) {
+int helm_host_stencil_row(int dim, int order, int elements, double h, int level, int64_t dof, double* K,
+                          double* M, double* B) {
   const int n = mesh_n(dim, order, h);
-  if (n < 0 || !(elements == HELM_SIMPLICES || elements == HELM_TENSOR) || !K || !M || !B) return HELM_EINVAL;
+  if (n < 0 || !(elements == HELM_SIMPLICES || elements == HELM_TENSOR) || !(level == 0 || level == 1) || !K ||
+      !M || !B)
+    return HELM_EINVAL;
   HostTables t;
   const int rc = build_tables(dim, order, n, &t, elements);
-  return rc != HELM_OK ? rc : host_stencil_row(t, dof, K, M, B);
+  return rc != HELM_OK ? rc : host_stencil_row(t, level, dof, K, M, B);
 }
 
 int helm_host_prolongation_row(int dim, int order, int elements, double h, int64_t fine_dof, int64_t* cols,

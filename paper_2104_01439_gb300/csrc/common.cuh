@@ -191,7 +191,7 @@ struct HostTables {
 
 // elements: HELM_SIMPLICES (P_order on triangles / Kuhn tetrahedra) or HELM_TENSOR (Q_order)
 int build_tables(int dim, int order, int n, HostTables* t, int elements = HELM_SIMPLICES);
-int host_stencil_row(const HostTables& t, int64_t dof, double* K, double* M, double* B);
+int host_stencil_row(const HostTables& t, int level, int64_t dof, double* K, double* M, double* B);
 int host_prolongation_row(const HostTables& t, int64_t fine_dof, int64_t* cols, double* w, int* count);
 void rhs_planewave(int dim, int order, int n, double k, double theta, double2* F, int elements = HELM_SIMPLICES);
 void rhs_gaussian(int dim, int order, int n, double sigma, const double* c, double2* F,

@@ -672,8 +672,11 @@ int build_tables(int d, int order, int n, HostTables* t, int elements) {
 }
 
 // Host inspection of the tables, with the kernels' own class and transfer mapping.
-int host_stencil_row(const HostTables& t, int64_t dof, double* K, double* M, double* B) {
-  const GridDesc& g = t.fine;
+int host_stencil_row(const HostTables& t, int level, int64_t dof, double* K, double* M, double* B) {
+  const GridDesc& g = level == 0 ? t.fine : t.coarse;
+  const std::vector<double>& Kt = level == 0 ? t.Kf : t.Kc;
+  const std::vector<double>& Mt = level == 0 ? t.Mf : t.Mc;
+  const std::vector<double>& Bt = level == 0 ? t.Bf : t.Bc;
   if (dof < 0 || dof >= g.N) return HELM_EINVAL;
   int a[3] = {0, 0, 0};
   int64_t r = dof;
@@ -694,9 +697,9 @@ int host_stencil_row(const HostTables& t, int64_t dof, double* K, double* M, dou
       in &= b >= 0 && b < g.W;
     }
     const size_t i = (size_t)cls * g.noff + o;
-    K[o] = in ? t.Kf[i] : 0.0;
-    M[o] = in ? t.Mf[i] : 0.0;
-    B[o] = in ? t.Bf[i] : 0.0;
+    K[o] = in ? Kt[i] : 0.0;
+    M[o] = in ? Mt[i] : 0.0;
+    B[o] = in ? Bt[i] : 0.0;
   }
   return HELM_OK;
 }

@@ -14,17 +14,17 @@ import pytest
 from oracle import fem
 from paper_2104_01439_gb300 import _binding as b
 
-CASES = [(2, 1, 8), (2, 1, 10), (2, 2, 6), (2, 2, 8), (3, 1, 4), (3, 1, 6)]
+CASES = [(2, 1, 8), (2, 1, 10), (2, 2, 6), (2, 2, 8), (2, 2, 22), (3, 1, 4), (3, 1, 6)]
 
 
-def _stencil_rows(lib, dim, order, elements, h, N):
+def _stencil_rows(lib, dim, order, elements, fine_n, level, N):
     R = order
     side = 2 * R + 1
     noff = side ** dim
     K, M, B = ((ctypes.c_double * noff)() for _ in range(3))
     rows = []
     for dof in range(N):
-        assert lib.helm_host_stencil_row(dim, order, elements, h, dof, K, M, B) == 0
+        assert lib.helm_host_stencil_row(dim, order, elements, 1.0 / fine_n, level, dof, K, M, B) == 0
         rows.append((np.array(K[:]), np.array(M[:]), np.array(B[:])))
     return rows, side, noff
 
@@ -63,12 +63,10 @@ def _compare_rows(rows, mats, dim, order, W):
 @pytest.mark.parametrize("dim,order,n", CASES)
 def test_stencil_tables_equal_assembled_rows(dim, order, n):
     lib = b.load()
-    for level_n in (n, n // 2):
-        if level_n < 4 or level_n % 2:
-            continue                          # the ABI takes meshes with an even 1/h >= 4
+    for level, level_n in ((0, n), (1, n // 2)):   # the coarse level may have an odd n
         mesh = fem.build_mesh(dim, order, level_n)
         K, M, B = fem.assemble(mesh)
-        rows, _, _ = _stencil_rows(lib, dim, order, b.HELM_SIMPLICES, 1.0 / level_n, mesh.num_dofs)
+        rows, _, _ = _stencil_rows(lib, dim, order, b.HELM_SIMPLICES, n, level, mesh.num_dofs)
         _compare_rows(rows, (K, M, B), dim, order, order * level_n + 1)
 
 
@@ -95,13 +93,17 @@ def test_prolongation_weights_equal_interpolation(dim, order, n):
 def test_inspection_refuses_bad_arguments():
     lib = b.load()
     K, M, B = ((ctypes.c_double * 9)() for _ in range(3))
-    assert lib.helm_host_stencil_row(2, 1, b.HELM_SIMPLICES, 1.0 / 8, 81, K, M, B) == -1   # dof out of range
-    assert lib.helm_host_stencil_row(2, 1, b.HELM_SIMPLICES, 1.0 / 7, 0, K, M, B) == -1    # odd n
-    assert lib.helm_host_stencil_row(2, 1, 7, 1.0 / 8, 0, K, M, B) == -1                   # unknown family
-    assert lib.helm_host_stencil_row(2, 1, b.HELM_SIMPLICES, 1.0 / 8, -1, K, M, B) == -1
+    S = b.HELM_SIMPLICES
+    assert lib.helm_host_stencil_row(2, 1, S, 1.0 / 8, 0, 81, K, M, B) == -1   # dof out of range
+    assert lib.helm_host_stencil_row(2, 1, S, 1.0 / 8, 1, 25, K, M, B) == -1   # (coarse level: 5 x 5)
+    assert lib.helm_host_stencil_row(2, 1, S, 1.0 / 8, 1, 24, K, M, B) == 0
+    assert lib.helm_host_stencil_row(2, 1, S, 1.0 / 7, 0, 0, K, M, B) == -1    # odd n
+    assert lib.helm_host_stencil_row(2, 1, 7, 1.0 / 8, 0, 0, K, M, B) == -1    # unknown family
+    assert lib.helm_host_stencil_row(2, 1, S, 1.0 / 8, 2, 0, K, M, B) == -1    # unknown level
+    assert lib.helm_host_stencil_row(2, 1, S, 1.0 / 8, 0, -1, K, M, B) == -1
 
 
-Q_CASES = [(2, 1, 8), (2, 1, 12), (2, 2, 6), (2, 2, 8), (3, 1, 4), (3, 1, 6)]
+Q_CASES = [(2, 1, 8), (2, 1, 10), (2, 1, 12), (2, 2, 6), (2, 2, 8), (2, 2, 22), (3, 1, 4), (3, 1, 6)]
 
 
 @pytest.mark.parametrize("dim,order,n", Q_CASES)
@@ -111,12 +113,10 @@ def test_tensor_tables_equal_assembled_q_rows(dim, order, n):
     tensor-product interpolation."""
     from oracle import qfem
     lib = b.load()
-    for level_n in (n, n // 2):
-        if level_n < 4 or level_n % 2:
-            continue
+    for level, level_n in ((0, n), (1, n // 2)):
         mesh = qfem.build_mesh(dim, order, level_n)
         K, _, M, B, _ = qfem.assemble(mesh)
-        rows, _, _ = _stencil_rows(lib, dim, order, b.HELM_TENSOR, 1.0 / level_n, mesh.num_dofs)
+        rows, _, _ = _stencil_rows(lib, dim, order, b.HELM_TENSOR, n, level, mesh.num_dofs)
         _compare_rows(rows, (K, M, B), dim, order, order * level_n + 1)
     fine, coarse = qfem.build_mesh(dim, order, n), qfem.build_mesh(dim, order, n // 2)
     P = qfem.prolongation(coarse, fine).tocsr()
@@ -137,9 +137,9 @@ def test_q1_stencil_differs_from_p1():
     lib = b.load()
     K, M, B = ((ctypes.c_double * 9)() for _ in range(3))
     dof = 4 + 9 * 4                                # an interior DoF of the 8 x 8 mesh
-    assert lib.helm_host_stencil_row(2, 1, b.HELM_SIMPLICES, 1.0 / 8, dof, K, M, B) == 0
+    assert lib.helm_host_stencil_row(2, 1, b.HELM_SIMPLICES, 1.0 / 8, 0, dof, K, M, B) == 0
     p1 = np.array(K[:])
-    assert lib.helm_host_stencil_row(2, 1, b.HELM_TENSOR, 1.0 / 8, dof, K, M, B) == 0
+    assert lib.helm_host_stencil_row(2, 1, b.HELM_TENSOR, 1.0 / 8, 0, dof, K, M, B) == 0
     q1 = np.array(K[:])
     assert np.count_nonzero(p1) == 5 and np.count_nonzero(q1) == 9
     assert np.allclose(q1 * 3, [-1, -1, -1, -1, 8, -1, -1, -1, -1])
