@@ -207,6 +207,17 @@ int helm_load_gaussian_e(int dim, int order, int elements, double h, double sigm
 int helm_host_stencil_row(int dim, int order, int elements, double h, int level, int64_t dof, double* K,
                           double* M, double* B);
 
+/* Heterogeneous wavenumber k(x) = k_max mu(x) (Sec. 2 with k in L^inf; Sec. 6): row `dof` of
+ * K, M_k = sum_e k_e^2 M_e (the k-weighted mass), M and B_k = sum_F k_F B_F (the k-weighted
+ * boundary mass) on level 0 or 1 of the mesh of (dim, order, h), in the box layout of
+ * helm_host_stencil_row. k_elem: one wavenumber per element of that level (n = 1/h or 1/(2h)
+ * cells per side), cells in lexicographic order, x fastest, and within a cell its simplices in
+ * the order (0,0)-(1,0)-(1,1), (0,0)-(1,1)-(0,1) (2D) or the Kuhn tetrahedra of the axis
+ * permutations in lexicographic order (3D); one element per cell for HELM_TENSOR. A boundary
+ * facet takes its element's value. HELM_EINVAL as for helm_host_stencil_row. */
+int helm_host_het_row(int dim, int order, int elements, double h, int level, const double* k_elem, int64_t dof,
+                      double* K, double* Mk, double* M, double* Bk);
+
 /* Row `fine_dof` of the canonical interpolation P from the 2h space to the h space (Sec. 4,
  * the matrix I^(l)), read from the per-class weights the transfer kernels use: *count entries,
  * coarse lattice indices in cols (x fastest) and weights in w (arrays of (order+1)^dim).

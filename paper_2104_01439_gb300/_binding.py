@@ -28,7 +28,7 @@ EXPORTS = [
     "helm_request_bytes", "helm_device_bytes", "helm_server_create", "helm_server_submit", "helm_server_poll",
     "helm_server_wait", "helm_server_drain", "helm_server_destroy", "helm_load_planewave", "helm_load_gaussian",
     "helm_operator_setup", "helm_smooth", "helm_host_stencil_row", "helm_host_prolongation_row",
-    "helm_setup_q", "helm_load_planewave_e", "helm_load_gaussian_e",
+    "helm_setup_q", "helm_load_planewave_e", "helm_load_gaussian_e", "helm_host_het_row",
 ]
 
 
@@ -116,6 +116,7 @@ def load(path: str = LIB_PATH):
     dp = ctypes.POINTER(ctypes.c_double)
     lib.helm_host_stencil_row.argtypes = [i, i, i, d, i, ctypes.c_int64, dp, dp, dp]
     lib.helm_host_prolongation_row.argtypes = [i, i, i, d, ctypes.c_int64, i64p, dp, ctypes.POINTER(i)]
+    lib.helm_host_het_row.argtypes = [i, i, i, d, i, dp, ctypes.c_int64, dp, dp, dp, dp]
     for name in EXPORTS:
         if name not in ("helm_default_opts", "helm_destroy", "helm_strerror", "helm_last_cuda_error",
                         "helm_server_destroy"):

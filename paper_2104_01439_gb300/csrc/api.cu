@@ -971,6 +971,24 @@ int helm_host_stencil_row(int dim, int order, int elements, double h, int level,
   return rc != HELM_OK ? rc : host_stencil_row(t, level, dof, K, M, B);
 }
 
+int helm_host_het_row(int dim, int order, int elements, double h, int level, const double* k_elem, int64_t dof,
+                      double* K, double* Mk, double* M, double* Bk) {
+  const int n = mesh_n(dim, order, h);
+  if (n < 0 || !(level == 0 || level == 1) || !k_elem || !K || !Mk || !M || !Bk) return HELM_EINVAL;
+  HetRows r;
+  const int rc = build_het_rows(dim, order, level == 0 ? n : n / 2, elements, k_elem, &r);
+  if (rc != HELM_OK) return rc;
+  if (dof < 0 || dof >= r.g.N) return HELM_EINVAL;
+  for (int o = 0; o < r.g.noff; ++o) {
+    const size_t i = (size_t)dof * r.g.noff + o;
+    K[o] = r.K[i];
+    Mk[o] = r.Mk[i];
+    M[o] = r.M[i];
+    Bk[o] = r.Bk[i];
+  }
+  return HELM_OK;
+}
+
 int helm_host_prolongation_row(int dim, int order, int elements, double h, int64_t fine_dof, int64_t* cols,
                                double* w, int* count) {
   const int n = mesh_n(dim, order, h);

@@ -192,6 +192,18 @@ struct HostTables {
 // elements: HELM_SIMPLICES (P_order on triangles / Kuhn tetrahedra) or HELM_TENSOR (Q_order)
 int build_tables(int dim, int order, int n, HostTables* t, int elements = HELM_SIMPLICES);
 int host_stencil_row(const HostTables& t, int level, int64_t dof, double* K, double* M, double* B);
+
+// Heterogeneous wavenumber (Sec. 2 with k in L^inf; Sec. 6, k(x) = k_max mu(x)): per-DoF rows
+// (box offsets, as in the class tables) of K, M_k = sum_e k_e^2 M_e, M and B_k = sum_F k_F B_F
+// on the full lattice of one level, from one wavenumber per element in the element order of the
+// setup's iteration (cells x fastest, then the simplices of a cell); a boundary facet takes its
+// element's value.
+struct HetRows {
+  GridDesc g;
+  std::vector<double> K, Mk, M, Bk;   // [N * noff]
+};
+int64_t num_elements(int dim, int n, int elements);
+int build_het_rows(int dim, int order, int n, int elements, const double* k_elem, HetRows* out);
 int host_prolongation_row(const HostTables& t, int64_t fine_dof, int64_t* cols, double* w, int* count);
 void rhs_planewave(int dim, int order, int n, double k, double theta, double2* F, int elements = HELM_SIMPLICES);
 void rhs_gaussian(int dim, int order, int n, double sigma, const double* c, double2* F,

@@ -276,7 +276,8 @@ template <typename Fn> void for_each_element(const SMesh& m, Fn fn) {
         }
 }
 
-// Calls fn(facet DoF lattice coords, facet vertex coords [d][3], outward normal[3]) per boundary facet.
+// Calls fn(facet DoF lattice coords, facet vertex coords [d][3], outward normal[3], owner) per
+// boundary facet; owner = the simplex's index in for_each_element's order.
 template <typename Fn> void for_each_boundary_facet(const SMesh& m, Fn fn) {
   std::vector<std::array<std::array<int, 3>, 4>> simp;
   cell_simplices(m.d, simp);
@@ -292,7 +293,9 @@ template <typename Fn> void for_each_boundary_facet(const SMesh& m, Fn fn) {
         bool bnd = false;
         for (int ax = 0; ax < m.d; ++ax) bnd |= (cell[ax] == 0 || cell[ax] == m.n - 1);
         if (!bnd) continue;
-        for (auto& s : simp) {
+        for (size_t si = 0; si < simp.size(); ++si) {
+          const auto& s = simp[si];
+          const int64_t owner = ((int64_t)(cz * m.n + cy) * m.n + cx) * (int64_t)simp.size() + (int64_t)si;
           // faces: drop one vertex
           for (int drop = 0; drop <= m.d; ++drop) {
             int fv[3][3];
@@ -320,7 +323,7 @@ template <typename Fn> void for_each_boundary_facet(const SMesh& m, Fn fn) {
                   for (int x = 0; x < 3; ++x) vx[a][x] = fv[a][x] * m.h;
                 double nrm[3] = {0, 0, 0};
                 nrm[ax] = side == 0 ? -1.0 : 1.0;
-                fn(loc, vx, nrm);
+                fn(loc, vx, nrm, owner);
               }
           }
         }
@@ -435,14 +438,15 @@ template <typename Fn> void for_each_element_km(const SMesh& m, Fn fn) {
       }
 }
 
-// Every boundary facet with its mass matrix: fn(facet DoF lattice coords, Be, outward normal).
+// Every boundary facet with its mass matrix: fn(facet DoF lattice coords, Be, outward normal,
+// owning element in for_each_element_km's order).
 template <typename Fn> void for_each_facet_mass(const SMesh& m, Fn fn) {
   if (m.elements == HELM_SIMPLICES) {
     std::vector<double> Be;
     for_each_boundary_facet(m, [&](const std::vector<std::array<int, 3>>& loc, const double (*vx)[3],
-                                   const double* nrm) {
+                                   const double* nrm, int64_t owner) {
       facet_mass(m.d, m.order, vx, Be);
-      fn(loc, Be, nrm);
+      fn(loc, Be, nrm, owner);
     });
     return;
   }
@@ -472,7 +476,7 @@ template <typename Fn> void for_each_facet_mass(const SMesh& m, Fn fn) {
             }
             double nrm[3] = {0, 0, 0};
             nrm[ax] = side == 0 ? -1.0 : 1.0;
-            fn(loc, Be, nrm);
+            fn(loc, Be, nrm, ((int64_t)cz * m.n + cy) * m.n + cx);
           }
       }
 }
@@ -496,7 +500,7 @@ void assemble_dense(const SMesh& m, std::vector<double>& K, std::vector<double>&
       }
   });
   for_each_facet_mass(m, [&](const std::vector<std::array<int, 3>>& loc, const std::vector<double>& Be,
-                             const double*) {
+                             const double*, int64_t) {
     int nb = (int)loc.size();
     for (int i = 0; i < nb; ++i)
       for (int j = 0; j < nb; ++j) {
@@ -671,6 +675,70 @@ int build_tables(int d, int order, int n, HostTables* t, int elements) {
   return HELM_OK;
 }
 
+int64_t num_elements(int d, int n, int elements) {
+  int64_t c = 1;
+  for (int ax = 0; ax < d; ++ax) c *= n;
+  return elements == HELM_TENSOR ? c : c * (d == 2 ? 2 : 6);
+}
+
+int build_het_rows(int d, int order, int n, int elements, const double* k_elem, HetRows* out) {
+  if (!(d == 2 || d == 3) || !(order == 1 || order == 2) || (d == 3 && order != 1) || n < 2) return HELM_EINVAL;
+  if (elements != HELM_SIMPLICES && elements != HELM_TENSOR) return HELM_EINVAL;
+  SMesh m{d, order, n, order * n + 1, 1.0 / n, elements};
+  GridDesc& g = out->g;
+  g.dim = d;
+  g.R = order;
+  g.q = order;
+  g.W = m.W;
+  g.C1 = 2 * g.R + g.q;
+  g.noff = 1;
+  g.N = 1;
+  for (int ax = 0; ax < d; ++ax) {
+    g.noff *= 2 * g.R + 1;
+    g.N *= g.W;
+  }
+  const size_t total = (size_t)g.N * g.noff;
+  out->K.assign(total, 0.0);
+  out->Mk.assign(total, 0.0);
+  out->M.assign(total, 0.0);
+  out->Bk.assign(total, 0.0);
+  const int side = 2 * g.R + 1;
+  auto box = [&](const std::array<int, 3>& a, const std::array<int, 3>& b) {
+    int o = 0, mul = 1;
+    for (int ax = 0; ax < d; ++ax) {
+      o += (b[ax] - a[ax] + g.R) * mul;
+      mul *= side;
+    }
+    return o;
+  };
+  int64_t e = 0;
+  for_each_element_km(m, [&](const std::vector<std::array<int, 3>>& loc, const std::vector<double>& Ke,
+                             const std::vector<double>& Me) {
+    const double k2 = k_elem[e] * k_elem[e];
+    ++e;
+    const int nb = (int)loc.size();
+    for (int i = 0; i < nb; ++i) {
+      const size_t r = (size_t)m.idx(loc[i].data()) * g.noff;
+      for (int j = 0; j < nb; ++j) {
+        const size_t c = r + box(loc[i], loc[j]);
+        out->K[c] += Ke[i * nb + j];
+        out->M[c] += Me[i * nb + j];
+        out->Mk[c] += k2 * Me[i * nb + j];
+      }
+    }
+  });
+  for_each_facet_mass(m, [&](const std::vector<std::array<int, 3>>& loc, const std::vector<double>& Be,
+                             const double*, int64_t owner) {
+    const double kf = k_elem[owner];
+    const int nb = (int)loc.size();
+    for (int i = 0; i < nb; ++i) {
+      const size_t r = (size_t)m.idx(loc[i].data()) * g.noff;
+      for (int j = 0; j < nb; ++j) out->Bk[r + box(loc[i], loc[j])] += kf * Be[i * nb + j];
+    }
+  });
+  return HELM_OK;
+}
+
 // Host inspection of the tables, with the kernels' own class and transfer mapping.
 int host_stencil_row(const HostTables& t, int level, int64_t dof, double* K, double* M, double* B) {
   const GridDesc& g = level == 0 ? t.fine : t.coarse;
@@ -745,7 +813,7 @@ void rhs_planewave(int d, int order, int n, double k, double theta, double2* F, 
   std::memset(F, 0, sizeof(double2) * N);
   double dir[3] = {std::cos(theta), std::sin(theta), 0.0};
   for_each_facet_mass(m, [&](const std::vector<std::array<int, 3>>& loc, const std::vector<double>& Be,
-                             const double* nrm) {
+                             const double* nrm, int64_t) {
     int nb = (int)loc.size();
     double dn = dir[0] * nrm[0] + dir[1] * nrm[1] + dir[2] * nrm[2];
     for (int j = 0; j < nb; ++j) {
