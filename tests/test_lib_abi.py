@@ -128,3 +128,19 @@ def test_host_load_builders_refuse_bad_meshes():
     assert lib.helm_load_planewave(2, 1, 1.0 / 8, 10.0, 0.3, None) == einval
     assert lib.helm_load_planewave(2, 1, 1.0 / 8, 0.0, 0.3, ptr) == einval
     assert np.all(F == 0)
+
+
+def test_package_names_used_by_gpu_code_exist():
+    """The GPU tests, bench.py and smoke() cannot run without a GPU; every package attribute they
+    use (pkg.X) must exist, so that none of them fails on a missing name at run time."""
+    import glob
+    import py_compile
+    import paper_2104_01439_gb300 as pkg
+    files = glob.glob(os.path.join(ROOT, "tests", "test_*.py")) + [
+        os.path.join(ROOT, "bench.py"), os.path.join(ROOT, "__graft_entry__.py"),
+        os.path.join(ROOT, "paper_2104_01439_gb300", "sweep.py")]
+    used = set()
+    for f in files:
+        py_compile.compile(f, doraise=True)
+        used |= set(re.findall(r"\bpkg\.([A-Za-z_][A-Za-z_0-9]*)", open(f).read()))
+    assert used and not [n for n in sorted(used) if not hasattr(pkg, n)]
