@@ -131,8 +131,8 @@ def test_host_load_builders_refuse_bad_meshes():
 
 
 def test_package_names_used_by_gpu_code_exist():
-    """The GPU tests, bench.py and smoke() cannot run without a GPU; every package attribute they
-    use (pkg.X) must exist, so that none of them fails on a missing name at run time."""
+    """The GPU tests, bench.py and smoke() cannot run without a GPU; every attribute of the package
+    module they use must exist, so that none of them fails on a missing name at run time."""
     import glob
     import py_compile
     import paper_2104_01439_gb300 as pkg
