@@ -674,9 +674,27 @@ static int setup_impl(helm_ctx* h) {
   // rounded to complex64 for the V-cycle
   const bool df = o.precision == HELM_MIXED;
   size_t blk = (size_t)L.B * L.ldb;
-  double2* D64 = nullptr;   // 16 bytes per entry: double2 (FP64) or float4 (double-float)
-  double2 *tmp = nullptr, *piv = nullptr;
-  unsigned* bar = nullptr;
+  // scratch of the factorisation, freed on every early return; the work buffers are released
+  // before the Krylov storage is allocated, and D64 is either kept by the handle or freed
+  struct FactorScratch {
+    double2 *D64 = nullptr, *tmp = nullptr, *piv = nullptr;
+    unsigned* bar = nullptr;
+    void free_work() {
+      cudaFree(tmp);
+      cudaFree(piv);
+      cudaFree(bar);
+      tmp = piv = nullptr;
+      bar = nullptr;
+    }
+    ~FactorScratch() {
+      free_work();
+      cudaFree(D64);
+    }
+  } fs;
+  double2*& D64 = fs.D64;   // 16 bytes per entry: double2 (FP64) or float4 (double-float)
+  double2*& tmp = fs.tmp;
+  double2*& piv = fs.piv;
+  unsigned*& bar = fs.bar;
   CK(cudaMalloc(&D64, sizeof(double2) * blk * L.nb));
   CK(cudaMalloc(&tmp, sizeof(double2) * 2 * blk));
   CK(cudaMalloc(&piv, sizeof(double2) * 2 * factor_workspace(L)));
@@ -724,9 +742,7 @@ static int setup_impl(helm_ctx* h) {
   cudaEventRecord(h->e1, s);
   cudaEventSynchronize(h->e1);
   cudaEventElapsedTime(&h->setup_ms, h->e0, h->e1);
-  cudaFree(tmp);
-  cudaFree(piv);
-  cudaFree(bar);
+  fs.free_work();
   if (rc == HELM_OK) {
     cudaError_t le = cudaGetLastError();
     if (le != cudaSuccess) rc = cuda_fail(le);
@@ -735,16 +751,15 @@ static int setup_impl(helm_ctx* h) {
     int e = check_err(h);
     if (e) rc = e;
   }
-  if (rc != HELM_OK) {
-    cudaFree(D64);
-    return rc;
-  }
+  if (rc != HELM_OK) return rc;   // (fs frees D64)
   if (o.precision == HELM_MIXED) {
     cudaFree(D64);
+    D64 = nullptr;
   } else {
     h->p64.Dinv = D64;
     h->allocs.push_back(D64);
     h->bytes += sizeof(double2) * blk * L.nb;
+    D64 = nullptr;   // owned by the handle now
   }
 
   // Krylov storage
