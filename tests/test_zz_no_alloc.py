@@ -2,7 +2,8 @@
 device memory when they call (fixed memory budget, their own allocator, or no
 room for the synchronisation a cudaMalloc may cause). It must give what
 helm_coarse_solve gives, call after call, using only the library's fixed 4 MiB
-scratch array, and refuse problems that do not fit. Collected last on purpose.
+scratch array, and refuse problems that do not fit. Collected after the main parity tests
+(only the Q_p parity tests of test_zzz_gpu_qp come later).
 """
 import ctypes
 
