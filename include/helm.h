@@ -202,8 +202,9 @@ int helm_load_gaussian_e(int dim, int order, int elements, double h, double sigm
  * eq. discreteproblem): coefficient o belongs to the neighbour at per-axis offset
  * d_ax = (o / (2R+1)^ax) mod (2R+1) - R, x first, R = order; neighbours outside the lattice get
  * 0. K, M, B: caller arrays of (2*order+1)^dim doubles. dof: lexicographic lattice index of that
- * level, x fastest. HELM_EINVAL for a mesh helm_setup refuses, an element family not supported,
- * a level other than 0 or 1, a dof out of range or a null array. */
+ * level, x fastest. Besides the meshes helm_setup takes, HELM_TENSOR accepts order 3 in 2D here
+ * (Q3 at the Gauss-Lobatto points; tables only, no solver). HELM_EINVAL for a mesh refused, an
+ * element family not supported, a level other than 0 or 1, a dof out of range or a null array. */
 int helm_host_stencil_row(int dim, int order, int elements, double h, int level, int64_t dof, double* K,
                           double* M, double* B);
 

@@ -939,8 +939,10 @@ int helm_rhs_gaussian(helm_t h, double sigma, double cx, double cy, double cz, v
   return HELM_OK;
 }
 
-static int mesh_n(int dim, int order, double h) {
-  if (!(h > 0) || !(dim == 2 || dim == 3) || !(order == 1 || order == 2) || (dim == 3 && order != 1)) return -1;
+static int mesh_n(int dim, int order, double h, bool q3_ok = false) {
+  const bool q3 = q3_ok && dim == 2 && order == 3;
+  if (!(h > 0) || !(dim == 2 || dim == 3) || !(order == 1 || order == 2 || q3) || (dim == 3 && order != 1))
+    return -1;
   const double nn = 1.0 / h;
   if (!(nn < 1e6)) return -1;   // beyond any mesh whose DoF count fits the cap below
   const int n = (int)std::lround(nn);
@@ -977,7 +979,7 @@ int helm_load_gaussian_e(int dim, int order, int elements, double h, double sigm
 
 int helm_host_stencil_row(int dim, int order, int elements, double h, int level, int64_t dof, double* K,
                           double* M, double* B) {
-  const int n = mesh_n(dim, order, h);
+  const int n = mesh_n(dim, order, h, elements == HELM_TENSOR);
   if (n < 0 || !(elements == HELM_SIMPLICES || elements == HELM_TENSOR) || !(level == 0 || level == 1) || !K ||
       !M || !B)
     return HELM_EINVAL;
@@ -988,7 +990,7 @@ int helm_host_stencil_row(int dim, int order, int elements, double h, int level,
 
 int helm_host_het_row(int dim, int order, int elements, double h, int level, const double* k_elem, int64_t dof,
                       double* K, double* Mk, double* M, double* Bk) {
-  const int n = mesh_n(dim, order, h);
+  const int n = mesh_n(dim, order, h, elements == HELM_TENSOR);
   if (n < 0 || !(level == 0 || level == 1) || !k_elem || !K || !Mk || !M || !Bk) return HELM_EINVAL;
   HetRows r;
   const int rc = build_het_rows(dim, order, level == 0 ? n : n / 2, elements, k_elem, &r);
@@ -1006,7 +1008,7 @@ int helm_host_het_row(int dim, int order, int elements, double h, int level, con
 
 int helm_host_prolongation_row(int dim, int order, int elements, double h, int64_t fine_dof, int64_t* cols,
                                double* w, int* count) {
-  const int n = mesh_n(dim, order, h);
+  const int n = mesh_n(dim, order, h, elements == HELM_TENSOR);
   if (n < 0 || !(elements == HELM_SIMPLICES || elements == HELM_TENSOR) || !cols || !w || !count)
     return HELM_EINVAL;
   HostTables t;

@@ -331,18 +331,33 @@ template <typename Fn> void for_each_boundary_facet(const SMesh& m, Fn fn) {
 }
 
 // ---------------------------------------------------------------------------
-// Tensor-product Q_p elements (p <= 2: the Gauss-Lobatto points are the equispaced
-// ones): 1D Lagrange basis on [0, 1] at x_l = l / p, 1D element matrices on [0, h]
-// integrated exactly by 4-point Gauss-Legendre, element matrices as tensor products with
-// the local index x fastest (l = sum_ax l_ax (p+1)^ax).
+// Tensor-product Q_p elements: 1D Lagrange basis on [0, 1] at the Gauss-Lobatto points (0, 1
+// and the roots of P_p'; equispaced for p <= 2, 1/2 -+ sqrt(5)/10 inside for p = 3), 1D element
+// matrices on [0, h] integrated exactly by 4-point Gauss-Legendre (degree <= 6 for p <= 3),
+// element matrices as tensor products with the local index x fastest (l = sum_ax l_ax (p+1)^ax).
 // ---------------------------------------------------------------------------
+double gll01(int p, int l) {
+  if (p == 3 && (l == 1 || l == 2)) return l == 1 ? 0.5 - std::sqrt(5.0) / 10.0 : 0.5 + std::sqrt(5.0) / 10.0;
+  return (double)l / p;
+}
 double lagrange1(int p, int l, double x) {
-  if (p == 1) return l == 0 ? 1.0 - x : x;
-  return l == 0 ? (2.0 * x - 1.0) * (x - 1.0) : l == 1 ? 4.0 * x * (1.0 - x) : x * (2.0 * x - 1.0);
+  double v = 1.0;
+  for (int j = 0; j <= p; ++j)
+    if (j != l) v *= (x - gll01(p, j)) / (gll01(p, l) - gll01(p, j));
+  return v;
 }
 double lagrange1_d(int p, int l, double x) {
-  if (p == 1) return l == 0 ? -1.0 : 1.0;
-  return l == 0 ? 4.0 * x - 3.0 : l == 1 ? 4.0 - 8.0 * x : 4.0 * x - 1.0;
+  double den = 1.0, s = 0.0;
+  for (int j = 0; j <= p; ++j)
+    if (j != l) den *= gll01(p, l) - gll01(p, j);
+  for (int m = 0; m <= p; ++m) {
+    if (m == l) continue;
+    double t = 1.0;
+    for (int j = 0; j <= p; ++j)
+      if (j != l && j != m) t *= x - gll01(p, j);
+    s += t;
+  }
+  return s / den;
 }
 void element_1d(int p, double h, std::vector<double>& K1, std::vector<double>& M1) {
   std::vector<double> x, w;
@@ -582,7 +597,8 @@ void level_stencils(int d, int order, int n, GridDesc& g, std::vector<double>& K
 }  // namespace
 
 int build_tables(int d, int order, int n, HostTables* t, int elements) {
-  if (!(d == 2 || d == 3) || !(order == 1 || order == 2) || (d == 3 && order != 1)) return HELM_EINVAL;
+  const bool q3 = elements == HELM_TENSOR && d == 2 && order == 3;   // host tables only
+  if (!(d == 2 || d == 3) || !(order == 1 || order == 2 || q3) || (d == 3 && order != 1)) return HELM_EINVAL;
   if (n < 4 || n % 2) return HELM_EINVAL;
   if (elements != HELM_SIMPLICES && elements != HELM_TENSOR) return HELM_EINVAL;
   level_stencils(d, order, n, t->fine, t->Kf, t->Mf, t->Bf, t->ncls_f, elements);
@@ -604,7 +620,8 @@ int build_tables(int d, int order, int n, HostTables* t, int elements) {
       double xi[3] = {0, 0, 0};
       int tt = c;
       for (int ax = 0; ax < d; ++ax) {
-        xi[ax] = (double)(tt % t->pf) / t->pf;
+        const int cc = tt % t->pf;   // fine sub-cell cc / q, its local point cc % q
+        xi[ax] = (cc / q + gll01(q, cc % q)) / 2.0;
         tt /= t->pf;
       }
       for (int o = 0; o < t->npo; ++o) {
@@ -682,7 +699,9 @@ int64_t num_elements(int d, int n, int elements) {
 }
 
 int build_het_rows(int d, int order, int n, int elements, const double* k_elem, HetRows* out) {
-  if (!(d == 2 || d == 3) || !(order == 1 || order == 2) || (d == 3 && order != 1) || n < 2) return HELM_EINVAL;
+  const bool q3 = elements == HELM_TENSOR && d == 2 && order == 3;
+  if (!(d == 2 || d == 3) || !(order == 1 || order == 2 || q3) || (d == 3 && order != 1) || n < 2)
+    return HELM_EINVAL;
   if (elements != HELM_SIMPLICES && elements != HELM_TENSOR) return HELM_EINVAL;
   SMesh m{d, order, n, order * n + 1, 1.0 / n, elements};
   GridDesc& g = out->g;

@@ -82,7 +82,7 @@ def test_simplex_het_rows_equal_oracle(dim, order, n):
         _rows_match(lib, dim, order, b.HELM_SIMPLICES, n, level, k_doc, (K, Mk, M, Bk), order * ln + 1)
 
 
-@pytest.mark.parametrize("dim,order,n", [(2, 1, 8), (2, 2, 6), (2, 2, 10), (3, 1, 4)])
+@pytest.mark.parametrize("dim,order,n", [(2, 1, 8), (2, 2, 6), (2, 2, 10), (2, 3, 6), (3, 1, 4)])
 def test_tensor_het_rows_equal_oracle(dim, order, n):
     lib = b.load()
     for level, ln in ((0, n), (1, n // 2)):

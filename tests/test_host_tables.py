@@ -43,6 +43,9 @@ def _offsets(dim, side, R, W):
 
 
 def _compare_rows(rows, mats, dim, order, W):
+    # relative tolerance: 1e-13; 1e-12 for order 3, whose oracle matrices come from monomial-basis
+    # polynomial integration pinned to 1e-12 (test_oracle_qfem.test_p3_matrices_against_quadrature)
+    tol = 1e-12 if order == 3 else 1e-13
     side = 2 * order + 1
     offs = _offsets(dim, side, order, W)
     for dof, got in enumerate(rows):
@@ -56,7 +59,7 @@ def _compare_rows(rows, mats, dim, order, W):
             for c, v in zip(cols, g):
                 if v != 0.0:
                     assert c in dense, (dof, c)
-                assert abs(v - dense.get(c, 0.0)) <= 1e-13 * max(1.0, abs(v)), (dof, c, v, dense.get(c))
+                assert abs(v - dense.get(c, 0.0)) <= tol * max(1.0, abs(v)), (dof, c, v, dense.get(c))
             assert inbox <= set(dense)
 
 
@@ -103,7 +106,8 @@ def test_inspection_refuses_bad_arguments():
     assert lib.helm_host_stencil_row(2, 1, S, 1.0 / 8, 0, -1, K, M, B) == -1
 
 
-Q_CASES = [(2, 1, 8), (2, 1, 10), (2, 1, 12), (2, 2, 6), (2, 2, 8), (2, 2, 22), (3, 1, 4), (3, 1, 6)]
+Q_CASES = [(2, 1, 8), (2, 1, 10), (2, 1, 12), (2, 2, 6), (2, 2, 8), (2, 2, 22), (2, 3, 6), (2, 3, 10),
+           (3, 1, 4), (3, 1, 6)]
 
 
 @pytest.mark.parametrize("dim,order,n", Q_CASES)
