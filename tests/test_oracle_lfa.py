@@ -290,3 +290,15 @@ def test_sigma_c_is_the_convergence_threshold():
     assert f(s) < 1.0 <= f(s - 2 * tol)
     # a well-resolved low wavenumber converges for every sigma in [1, 2]
     assert lfa.sigma_c(lfa.Q1, 1.0, h, omega, nu, nu, m=16, steps=4) == 1.0
+
+
+def test_sigma_c_depends_on_h_not_on_the_smoother():
+    """Sec. 3: for kh < 0.75, varying the smoothing steps and the damping barely moves sigma_c,
+    while the mesh size at fixed kh moves it markedly."""
+    sc = lambda k, h, om, nu: lfa.sigma_c(lfa.Q1, k, h, om, nu, nu, m=32, steps=16, tol=1e-3)  # noqa: E731
+    h = 2.0 ** -6
+    for kh in (0.5, 0.7):
+        vals = [sc(kh / h, h, om, nu) for nu, om in ((2, 0.6), (3, 2.0 / 3.0), (1, 0.8))]
+        assert max(vals) - min(vals) <= 0.02, (kh, vals)
+    kh = 0.7
+    assert sc(kh / 2.0 ** -7, 2.0 ** -7, 2.0 / 3.0, 3) - sc(kh / 2.0 ** -5, 2.0 ** -5, 2.0 / 3.0, 3) >= 0.1
