@@ -31,6 +31,9 @@ def test_library_builds_and_exports_every_declared_symbol():
     for name in _declared():
         assert hasattr(lib, name), name
     assert set(_binding.EXPORTS) == set(_declared())
+    # every entry point has its argument types declared (ctypes would otherwise pass Python
+    # floats and ints with default conversions)
+    assert not [n for n in _binding.EXPORTS if getattr(lib, n).argtypes is None]
     # pure host functions are safe to call without a GPU
     assert lib.helm_strerror(-4).decode().startswith("zero")
     o = _binding.HelmOpts()
