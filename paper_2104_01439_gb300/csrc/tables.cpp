@@ -1,11 +1,15 @@
 // Host-side setup of the matrix-free operators: per-class stencil
 // coefficients of K, M, B (Sec. 2, eq. discreteproblem), prolongation weights
-// of the canonical interpolation V_2h -> V_h (Sec. 4), and load vectors.
+// of the canonical interpolation V_2h -> V_h (Sec. 4), and load vectors, for
+// Lagrange P_p on simplices (the solver's elements) and tensor-product Q_p on
+// squares / cubes (the paper's); per-DoF rows for a heterogeneous wavenumber
+// with one value per element (Sec. 6); host inspection of all of these.
 //
-// Element integrals use Gauss-Legendre quadrature in collapsed (Duffy)
+// Simplex integrals use Gauss-Legendre quadrature in collapsed (Duffy)
 // coordinates on the reference simplex, exact for the polynomial degrees met
-// here (<= 4 for the P2 mass matrix). The stencil of each DoF class is read
-// off a small reference mesh that contains every class at least once.
+// here (<= 4 for the P2 mass matrix); tensor-product elements use exact 1D
+// integrals. The stencil of each DoF class is read off a small reference mesh
+// that contains every class at least once.
 #include <algorithm>
 #include <array>
 #include <cmath>
@@ -836,7 +840,7 @@ void rhs_planewave(int d, int order, int n, double k, double theta, double2* F, 
     int nb = (int)loc.size();
     double dn = dir[0] * nrm[0] + dir[1] * nrm[1] + dir[2] * nrm[2];
     for (int j = 0; j < nb; ++j) {
-      double ph = 0;
+      double ph = 0;   // lattice points are equispaced for the orders the load builders take (<= 2)
       for (int ax = 0; ax < d; ++ax) ph += dir[ax] * loc[j][ax] * m.h / order;
       // g = i k (d.n - 1) exp(i k d.x)
       double gr = -k * (dn - 1.0) * std::sin(k * ph), gi = k * (dn - 1.0) * std::cos(k * ph);
