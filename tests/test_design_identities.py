@@ -379,3 +379,33 @@ def test_segment_products_bounded_on_q_coarse_operators(p, nc, k):
         assert nf < 1.0 and nbk < 1.0, (nf, nbk)
     assert nf <= 1.05 * nf1 and nbk <= 1.05 * nb1, (nf, nf1, nbk, nb1)
     assert err_seg <= 2.0 * err_seq + 1e-7, (err_seg, err_seq)
+
+
+def test_schur_complements_converge_along_the_chain_for_large_shifts():
+    """Premise of reusing converged Schur inverses in the coarse factorisation: the coarse
+    operator of the benchmark (2D P1, 256 x 256 cells, k = 200) is block tridiagonal with the same
+    blocks on every interior line, so S_J = A - A_J,J-1 S_J-1^-1 A_J-1,J follows one recurrence.
+    For eps = k^2 / 2 the inverse stops changing at complex64 level (1e-9 relative) after about
+    50 of the 127 blocks of a chain and at FP64 level after about 90; for eps = k it keeps changing
+    to the end, so any reuse has to test convergence as it goes."""
+    from oracle import fem
+    nc, k = 256, 200.0
+    cm = fem.build_mesh(2, 1, nc)
+    K, M, B = fem.assemble(cm)
+    W = nc + 1
+
+    def changes(eps, steps):
+        A = fem.system_matrix(K, M, B, k, eps).tocsr()
+        blk = lambda I, J: A[I * W:(I + 1) * W, J * W:(J + 1) * W].toarray()  # noqa: E731
+        Dprev = np.linalg.inv(blk(0, 0))
+        out = []
+        for J in range(1, steps + 1):
+            D = np.linalg.inv(blk(J, J) - blk(J, J - 1) @ (Dprev @ blk(J - 1, J)))
+            out.append(np.linalg.norm(D - Dprev) / np.linalg.norm(D))
+            Dprev = D
+        return out
+
+    big = changes(0.5 * k * k, 100)
+    assert max(big[59:]) < 1e-9 and max(big[94:]) < 1e-14
+    small = changes(k, 127)
+    assert min(small) > 1e-6
