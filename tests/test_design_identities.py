@@ -409,3 +409,46 @@ def test_schur_complements_converge_along_the_chain_for_large_shifts():
     assert max(big[59:]) < 1e-9 and max(big[94:]) < 1e-14
     small = changes(k, 127)
     assert min(small) > 1e-6
+
+
+def test_reused_schur_inverses_keep_the_coarse_solve_below_complex64_rounding():
+    """Freezing Dinv once consecutive inverses agree to 1e-9 (relative) on the benchmark's coarse
+    operator (the last, boundary block still recomputed) needs about a fifth of the inversions of
+    the top-down chain and changes the coarse solve by less than complex64 rounding."""
+    import scipy.sparse.linalg as spla
+    from oracle import fem
+    nc, k = 256, 200.0
+    cm = fem.build_mesh(2, 1, nc)
+    K, M, B = fem.assemble(cm)
+    A = fem.system_matrix(K, M, B, k, 0.5 * k * k).tocsr()
+    W = nc + 1
+    blk = lambda I, J: A[I * W:(I + 1) * W, J * W:(J + 1) * W].toarray()  # noqa: E731
+
+    def factor(tol):
+        D, frozen, inversions = [np.linalg.inv(blk(0, 0))], None, 1
+        for J in range(1, W):
+            if frozen is not None and J < W - 1:
+                D.append(frozen)
+                continue
+            D.append(np.linalg.inv(blk(J, J) - blk(J, J - 1) @ (D[J - 1] @ blk(J - 1, J))))
+            inversions += 1
+            if tol and J < W - 1 and np.linalg.norm(D[J] - D[J - 1]) / np.linalg.norm(D[J]) < tol:
+                frozen = D[J]
+        return D, inversions
+
+    def solve(D, r):
+        y = [D[0] @ r[:W]]
+        for J in range(1, W):
+            y.append(D[J] @ (r[J * W:(J + 1) * W] - blk(J, J - 1) @ y[-1]))
+        x = [None] * W
+        x[-1] = y[-1]
+        for J in range(W - 2, -1, -1):
+            x[J] = y[J] - D[J] @ (blk(J, J + 1) @ x[J + 1])
+        return np.concatenate(x)
+
+    rng = np.random.default_rng(3)
+    r = rng.standard_normal(W * W) + 1j * rng.standard_normal(W * W)
+    xe = spla.spsolve(A.tocsc(), r)
+    Dr, inv_r = factor(1e-9)
+    err = np.linalg.norm(solve(Dr, r) - xe) / np.linalg.norm(xe)
+    assert inv_r <= 60 and err < 1e-8, (inv_r, err)
