@@ -232,7 +232,6 @@ void enqueue_vcycle(helm_ctx* h, VecSel<const Vf> f, VecSel<Vz> z, const int* ac
   using V = c2<T>;
   Prec<T>& p = h->prec<T>();
   StencilView<T> Ae = make_view<T>(h->gf, p.coefAe, p.wdinv);
-  StencilView<T> Ac = make_view<T>(h->gc, p.coefAc, nullptr);
   TransferView<T> P = make_transfer<T>(h, p.pw);
   const int nu = h->opts.nu;
   V* cur = p.ua;

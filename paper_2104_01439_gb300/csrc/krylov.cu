@@ -29,7 +29,6 @@ namespace {
 
 constexpr int kT = 256;
 constexpr int kMaxRestart = 512;   // helm_opts.restart <= 512
-constexpr int kG = 8;   // basis vectors per sweep
 
 __device__ __forceinline__ double2 wsum(double2 v) {
 #pragma unroll
