@@ -272,11 +272,17 @@ int helm_coarse_solve(helm_t h, const void* rc, void* uc);
  *     coarse grid of P1 h=1/512; complex64: twice that). Larger problems get
  *     HELM_ESCRATCH and nothing is launched.
  *   - The first call on a device looks up the array's device address for that
- *     device; make that first call outside any stream capture.
+ *     device and keeps it; make that first call outside any stream capture. The
+ *     kept address does not survive cudaDeviceReset: do not call this entry
+ *     point again after a reset of the device in the same process.
+ *   - The device current at the call must be the one the handle was set up
+ *     on; otherwise the call returns HELM_EINVAL and launches nothing.
  *   - All calls share the one array and it keeps the previous call's contents
  *     (every entry a call reads is written by that call first). Calls whose
  *     work overlaps on the GPU -- several streams, several host threads -- race
- *     on it: serialise them.
+ *     on it: serialise them. Calls on different handles share only this array;
+ *     each handle's own state (its error word, the segment workspace of the
+ *     complex64 form) is still per handle.
  * rc, uc: device complex128[Nc] as for helm_coarse_solve; synchronous.
  */
 int helm_coarse_solve_noalloc(helm_t h, const void* rc, void* uc);

@@ -43,8 +43,6 @@ template <typename T> struct Prec {
   c2<T>* fT = nullptr;
   c2<T>* rc = nullptr;
   c2<T>* uc = nullptr;
-  c2<T>* xmid = nullptr;   // middle-block exchange of the twisted coarse solve (2 x ldb)
-  int* xflag = nullptr;    // its ready flags (one per row of each chain)
   unsigned* gbar = nullptr;   // grid barrier of the whole-grid coarse solve
   SegBufs<T> seg{};           // segmented solve workspaces (plan.seg)
   const SegBufs<T>* segp() const { return plan.seg ? &seg : nullptr; }
@@ -59,6 +57,7 @@ struct helm_ctx {
   double k = 0, h = 0, shift = 0;
   helm_opts opts{};
   cudaStream_t s = nullptr;
+  int dev = 0;                 // device the handle was set up on
   int nsm = 0;
   HostTables tab;
   GridDesc gf{}, gc{};
@@ -213,8 +212,6 @@ int setup_prec(helm_ctx* h, const std::vector<double2>& Ae, const std::vector<do
   CK(h->alloc(&p.fT, sizeof(c2<T>) * Nf));
   CK(h->alloc(&p.rc, sizeof(c2<T>) * Nc));
   CK(h->alloc(&p.uc, sizeof(c2<T>) * Nc));
-  CK(h->alloc(&p.xmid, sizeof(c2<T>) * 2 * h->L.ldb));
-  CK(h->alloc(&p.xflag, sizeof(int) * 2 * h->L.ldb));
   CK(h->alloc(&p.gbar, sizeof(unsigned) * kBarWords));
   if ((rc = plan_coarse_solve<T>(h->L, &p.plan))) return rc;
   // the elimination order (one chain, or two chains meeting in the middle) is fixed
@@ -254,7 +251,7 @@ void enqueue_vcycle(helm_ctx* h, VecSel<const Vf> f, VecSel<Vz> z, const int* ac
   launch_residual<T, V, V>(Ae, fT, cur, p.r, active, s);
   launch_restrict<T>(P, h->L, p.r, p.rc, active, s);
   if (prof) cudaEventRecord(prof->ev[ev0 + 1], s);
-  launch_coarse_solve<T>(p.plan, p.Dinv, p.Lm, p.Up, h->L, p.rc, p.uc, p.xmid, p.xflag, p.gbar, h->err, active,
+  launch_coarse_solve<T>(p.plan, p.Dinv, p.Lm, p.Up, h->L, p.rc, p.uc, p.gbar, h->err, active,
                          h->nsm, s, p.segp());
   if (prof) cudaEventRecord(prof->ev[ev0 + 2], s);
   launch_prolong_add<T>(P, h->L, p.uc, cur, active, s);
@@ -527,7 +524,7 @@ size_t estimate_bytes(int dim, int order, int n, int precision, int restart) {
   const int64_t blk = B * ldb;
   const int64_t v = precision == HELM_MIXED ? 8 : 16;
   const int64_t m = restart, ldN = (N + 31) & ~int64_t(31), nblk = std::max<int64_t>(1, (N + 255) / 256);
-  const int64_t prec = v * (4 * N + 2 * nb * ldb + 2 * ldb) + 4 * 2 * ldb + 64;
+  const int64_t prec = v * (4 * N + 2 * nb * ldb) + 64;
   // Dinv, Lm, Up; the mixed form's segmented solve adds two product sets and one vector
   const int64_t factor = v * 3 * blk * nb + (precision == HELM_MIXED ? 8 * (2 * blk * nb + nb * ldb) : 0);
   // basis (double-float), w split, Z (complex64 in the mixed form), W (FP64 form), residual
@@ -620,9 +617,8 @@ static int setup_impl(helm_ctx* h) {
   h->ncls_f = h->tab.ncls_f;
   h->ncls_c = h->tab.ncls_c;
   if (h->gf.N >= (1ll << 31) / 2) return HELM_ENOTSUP;
-  int dev = 0;
-  CK(cudaGetDevice(&dev));
-  CK(cudaDeviceGetAttribute(&h->nsm, cudaDevAttrMultiProcessorCount, dev));
+  CK(cudaGetDevice(&h->dev));
+  CK(cudaDeviceGetAttribute(&h->nsm, cudaDevAttrMultiProcessorCount, h->dev));
   CK(cudaEventCreate(&h->e0));
   CK(cudaEventCreate(&h->e1));
   cudaStream_t s = h->s;
@@ -1059,13 +1055,13 @@ int helm_coarse_solve(helm_t h, const void* rc_nat, void* uc_nat) {
   if (h->opts.precision == HELM_MIXED) {
     Prec<float>& p = h->p32;
     launch_coarse_pack<double2, float2>(h->gc, h->L, (const double2*)rc_nat, p.rc, h->s);
-    launch_coarse_solve<float>(p.plan, p.Dinv, p.Lm, p.Up, h->L, p.rc, p.uc, p.xmid, p.xflag, p.gbar, h->err,
+    launch_coarse_solve<float>(p.plan, p.Dinv, p.Lm, p.Up, h->L, p.rc, p.uc, p.gbar, h->err,
                                nullptr, h->nsm, h->s, p.segp());
     launch_coarse_unpack<float2, double2>(h->gc, h->L, p.uc, (double2*)uc_nat, h->s);
   } else {
     Prec<double>& p = h->p64;
     launch_coarse_pack<double2, double2>(h->gc, h->L, (const double2*)rc_nat, p.rc, h->s);
-    launch_coarse_solve<double>(p.plan, p.Dinv, p.Lm, p.Up, h->L, p.rc, p.uc, p.xmid, p.xflag, p.gbar, h->err,
+    launch_coarse_solve<double>(p.plan, p.Dinv, p.Lm, p.Up, h->L, p.rc, p.uc, p.gbar, h->err,
                                 nullptr, h->nsm, h->s);
     launch_coarse_unpack<double2, double2>(h->gc, h->L, p.uc, (double2*)uc_nat, h->s);
   }
@@ -1117,10 +1113,12 @@ void* g_noalloc_ptr[kMaxDevices] = {nullptr};
 static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocScratchBytes];
 
 namespace {
-// Device address of the scratch array on the current device (first call: lookup).
-int noalloc_scratch(void** out) {
-  int dev = 0;
-  CK(cudaGetDevice(&dev));
+// Device address of the scratch array on device `dev`, which must be the current device
+// (first call on that device: lookup).
+int noalloc_scratch(int dev, void** out) {
+  int cur = -1;
+  CK(cudaGetDevice(&cur));
+  if (cur != dev) return HELM_EINVAL;
   if (dev < 0 || dev >= kMaxDevices) return HELM_ENOTSUP;
   std::lock_guard<std::mutex> lock(g_noalloc_mu);
   if (!g_noalloc_ptr[dev]) {
@@ -1139,13 +1137,13 @@ int coarse_solve_noalloc(helm_t h, const double2* rc_nat, double2* uc_nat) {
   const size_t nvec = (size_t)h->L.nb * h->L.ldb;
   if (2 * nvec * sizeof(V) > kNoAllocScratchBytes) return HELM_ESCRATCH;
   void* base = nullptr;
-  int rc = noalloc_scratch(&base);
+  int rc = noalloc_scratch(h->dev, &base);
   if (rc) return rc;
   V* pad_rc = static_cast<V*>(base);
   V* pad_uc = pad_rc + nvec;   // 16-byte aligned: nvec * sizeof(V) is a multiple of 16 (ldb even)
   CK(cudaMemsetAsync(h->err, 0, sizeof(int), h->s));   // the error word must start at zero
   launch_coarse_pack<double2, V>(h->gc, h->L, rc_nat, pad_rc, h->s);   // writes every padded entry
-  launch_coarse_solve<T>(p.plan, p.Dinv, p.Lm, p.Up, h->L, pad_rc, pad_uc, p.xmid, p.xflag, p.gbar, h->err,
+  launch_coarse_solve<T>(p.plan, p.Dinv, p.Lm, p.Up, h->L, pad_rc, pad_uc, p.gbar, h->err,
                          nullptr, h->nsm, h->s, p.segp());
   launch_coarse_unpack<V, double2>(h->gc, h->L, pad_uc, uc_nat, h->s);
   CK(cudaGetLastError());

@@ -24,7 +24,8 @@
 // Chain kernels run on thread-block clusters: CTA c owns rows [cR, cR+R) of every matrix,
 // streamed through a multi-stage shared-memory ring by bulk copies (cp.async.bulk +
 // mbarrier complete_tx), and each CTA pushes its R results into every CTA's shared memory
-// with st.async. FP64 form: two clusters run the two chains of the twisted form. Complex64
+// with st.async. FP64 form: the two chains of the twisted form, one cluster each, forward and
+// backward in separate launches around the middle block. Complex64
 // form: each half-sweep is cut into segments (segmented recurrences, see k_seg_chain).
 // Blocks too large for a cluster (3D planes): one chain over the cooperative grid.
 #include <algorithm>
@@ -70,16 +71,46 @@ __device__ __forceinline__ bool mbar_test_wait(uint64_t* bar, unsigned parity) {
       : "memory");
   return ok != 0;
 }
-// Bounded wait: gives up after 2^20 polls, flags HELM_ETIMEOUT in the CTA's
-// shared error word and in global memory; once flagged, later waits return at
-// once so that a failed solve ends quickly instead of waiting out every step.
-__device__ __forceinline__ void mbar_wait(uint64_t* bar, unsigned parity, int* s_err, int* err) {
-  if (mbar_test_wait(bar, parity)) return;   // usually complete already: no suspend
-  if (*(volatile int*)s_err) return;
-  for (int i = 0; i < (1 << 20); ++i)
-    if (mbar_try_wait(bar, parity)) return;
+// Bounded waits. A wait that runs out flags HELM_ETIMEOUT in the CTA's shared error word
+// and in global memory and returns false; no wait is ever skipped because an earlier one ran
+// out, so every asynchronous copy or store a CTA has armed is still waited on (see
+// chain_exit). kWaitPolls bounds every wait on the normal path; once the CTA has flagged an
+// error, the in-loop receive waits use the short bound (their values are garbage by then),
+// while the waits that guard the CTA's exit take the longest one.
+constexpr int kWaitPolls = 1 << 20;
+constexpr int kWaitPollsAfterError = 1 << 10;
+constexpr int kDrainPolls = 1 << 22;   // chain_exit's waits on the error path
+__device__ __forceinline__ void flag_timeout(int* s_err, int* err) {
   *(volatile int*)s_err = 1;
   atomicExch(err, HELM_ETIMEOUT);
+}
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, unsigned parity, int* s_err, int* err,
+                                          int polls = kWaitPolls) {
+  if (mbar_test_wait(bar, parity)) return true;   // usually complete already: no suspend
+  for (int i = 0; i < polls; ++i)
+    if (mbar_try_wait(bar, parity)) return true;
+  flag_timeout(s_err, err);
+  return false;
+}
+// Consumer wait for ring unit u (its slot's full barrier, phase parity `parity`). True once
+// the unit's bulk copy has landed; false when the producer stopped before issuing the unit
+// (s_issued <= u: nothing in flight for it) or the bounded wait ran out (flagged). s_issued is
+// read before the barrier, so a slot left a phase behind by an unissued unit is never mistaken
+// for a completed one.
+__device__ __noinline__ bool ring_wait_slow(uint64_t* bar, unsigned parity, int u, const int* s_issued, int* s_err,
+                                           int* err) {
+  for (int i = 0; i < kWaitPolls; ++i) {
+    if (mbar_try_wait(bar, parity)) return true;
+    if ((i & 63) == 63 && u >= *(volatile const int*)s_issued) return false;
+  }
+  flag_timeout(s_err, err);
+  return false;
+}
+__device__ __forceinline__ bool ring_wait(uint64_t* bar, unsigned parity, int u, const int* s_issued, int* s_err,
+                                          int* err) {
+  if (u >= *(volatile const int*)s_issued) return false;
+  if (mbar_test_wait(bar, parity)) return true;   // usually complete already
+  return ring_wait_slow(bar, parity, u, s_issued, s_err, err);
 }
 __device__ __forceinline__ void bulk_g2s(void* dst, const void* src, unsigned bytes, uint64_t* bar) {
   asm volatile(
@@ -136,12 +167,14 @@ __device__ __forceinline__ bool mbar_try_wait_cluster(uint64_t* bar, unsigned pa
   return ok != 0;
 }
 // Bounded wait for data pushed by the other CTAs of the cluster (acquire at cluster scope).
-__device__ __forceinline__ void mbar_wait_cluster(uint64_t* bar, unsigned parity, int* s_err, int* err) {
-  if (*(volatile int*)s_err) return;
-  for (int i = 0; i < (1 << 20); ++i)
-    if (mbar_try_wait_cluster(bar, parity)) return;
-  *(volatile int*)s_err = 1;
-  atomicExch(err, HELM_ETIMEOUT);
+__device__ __forceinline__ bool mbar_wait_cluster(uint64_t* bar, unsigned parity, int* s_err, int* err, int polls) {
+  for (int i = 0; i < polls; ++i)
+    if (mbar_try_wait_cluster(bar, parity)) return true;
+  flag_timeout(s_err, err);
+  return false;
+}
+__device__ __forceinline__ int rx_polls(const int* s_err) {
+  return *(volatile const int*)s_err ? kWaitPollsAfterError : kWaitPolls;
 }
 
 __device__ __forceinline__ float2 cvt_ldcg(const float2* p) { return __ldcg(p); }
@@ -657,7 +690,7 @@ __global__ void __launch_bounds__(256) k_block_gemv_wide(const c2<T>* __restrict
 //   forward   y_J = p_J - C_J y_prev     (C = Lm on the top chain, Up on the bottom one)
 //   middle    x_m = p_m - (Lm[m] y_{m-1} + Up[m] y_{m+1})
 //   backward  x_J = y_J - C_J x_prev     (C = Up on the top chain, Lm on the bottom one)
-// CTA c of a 16-CTA cluster owns rows [cR, cR+R) of every matrix. A producer warp
+// CTA c of a cluster owns rows [cR, cR+R) of every matrix. A producer warp
 // streams the CTA's rows of each step's coupling matrix into a multi-stage
 // shared-memory ring with bulk copies (cp.async.bulk + mbarrier complete_tx);
 // consumer warps (one row each) wait on a slot's "full" barrier, reduce their
@@ -665,32 +698,42 @@ __global__ void __launch_bounds__(256) k_block_gemv_wide(const c2<T>* __restrict
 // value into every CTA's receive buffer with st.async (complete_tx on the
 // receiver's mbarrier). The gathered vector is the next step's GEMV input.
 // There is no CTA-wide barrier inside a step: every thread that reads data
-// produced elsewhere waits on the mbarrier (or flag) that publishes it.
+// produced elsewhere waits on the mbarrier that publishes it.
+// The twisted form runs as three launches that need no two clusters at the same time:
+// the two forward chains (one cluster each), the middle block (k_seg_middle), and the
+// two backward chains from x_m.
 // ---------------------------------------------------------------------------
 struct SolveGeom {
-  int R, CW, nchunk, S;
-  size_t off_mbar, off_misc, off_gath, off_w, off_stage;
+  int R, CW, nchunk, S, nrx;
+  size_t off_mbar, off_misc, off_rx, off_gath, off_w, off_stage;
   size_t total;
 };
 
+// Shared-memory layout of a chain CTA. nrx: receive barriers, one per step that gathers a
+// vector (an upper bound of the launch's steps).
 template <typename T>
-SolveGeom solve_geometry(const CoarseLayout& L, int CS, int CW, int S, bool with_w = true) {
+SolveGeom solve_geometry(const CoarseLayout& L, int CS, int CW, int S, bool with_w, int nrx) {
   using V = c2<T>;
   SolveGeom G;
   G.R = (L.B + CS - 1) / CS;
   G.CW = CW;
   G.nchunk = (L.ldb + CW - 1) / CW;
   G.S = S;
+  G.nrx = nrx;
   auto al = [](size_t x) { return (x + 127) & ~size_t(127); };
   size_t o = 0;
   G.off_mbar = o; o = al(o + 16 * S);   // full [S], empty [S]
-  G.off_misc = o; o = al(o + 32);       // receive mbarriers [2] (+0, +8), error word (+16)
+  G.off_misc = o; o = al(o + 32);       // error word (+0), units issued (+4)
+  G.off_rx = o; o = al(o + 8 * (size_t)nrx);   // receive barriers, one per step
   G.off_gath = o; o = al(o + sizeof(V) * 2 * L.ldb);
-  G.off_w = o; o = al(o + (with_w ? sizeof(V) * (size_t)L.nb * G.R : 0));   // forward values (twisted kernel)
+  G.off_w = o; o = al(o + (with_w ? sizeof(V) * (size_t)L.nb * G.R : 0));   // forward values (single chain)
   G.off_stage = o; o = al(o + sizeof(V) * (size_t)S * G.R * CW);
   G.total = o;
   return G;
 }
+// receive barriers a chain launch needs: the single chain takes 2 nb - 1 steps, a twisted
+// launch at most nb / 2 + 1, a segmented chain at most one path's positions (<= nb / 2 + 1)
+inline int chain_rx(const CoarseLayout& L, bool single) { return single ? 2 * L.nb : L.nb / 2 + 2; }
 
 constexpr int kRPW = 4;          // max rows of the CTA slice per consumer warp (registers)
 constexpr int kSegMaxLdb = 1040;   // block row length up to which the segmented solve applies
@@ -703,20 +746,122 @@ __device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
   asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
 }
 
+// Shared-memory state of one chain CTA (the layout of SolveGeom).
+template <typename V> struct ChainSmem {
+  uint64_t* full;    // [S] ring slot filled (one arrival + the copy's bytes)
+  uint64_t* empty;   // [S] ring slot released (one arrival per consumer warp)
+  uint64_t* rx;      // [nrx] receive barrier of step s: B values from the cluster, one phase
+  int* s_err;        // set after any timeout in this CTA
+  int* s_issued;     // ring units the producer issued (U until it stops early)
+  V* gath;           // 2 x ldb gathered vectors (step s fills gath[s & 1])
+  V* wrows;          // forward values (single chain only)
+  V* stage;          // S x R x CW ring
+  __device__ ChainSmem(unsigned char* sm, const SolveGeom& G) {
+    full = reinterpret_cast<uint64_t*>(sm + G.off_mbar);
+    empty = full + G.S;
+    rx = reinterpret_cast<uint64_t*>(sm + G.off_rx);
+    s_err = reinterpret_cast<int*>(sm + G.off_misc);
+    s_issued = reinterpret_cast<int*>(sm + G.off_misc + 4);
+    gath = reinterpret_cast<V*>(sm + G.off_gath);
+    wrows = reinterpret_cast<V*>(sm + G.off_w);
+    stage = reinterpret_cast<V*>(sm + G.off_stage);
+  }
+};
+
+// Barrier set-up of a chain CTA, before the cluster barrier that publishes it. The receive
+// barrier of every step that gathers (steps 0..nsteps-2) is armed here for its B values, once:
+// each is used for a single phase, so a store that lands late can only complete its own step.
+template <typename V>
+__device__ __forceinline__ void chain_init(const ChainSmem<V>& c, int S, int nwc, int U, int nsteps,
+                                           unsigned rx_bytes) {
+  if (threadIdx.x == 0) {
+    *c.s_err = 0;
+    *c.s_issued = U;
+    for (int q = 0; q < S; ++q) {
+      mbar_init(&c.full[q], 1);
+      mbar_init(&c.empty[q], (unsigned)nwc);
+    }
+  }
+  for (int s = threadIdx.x; s < nsteps - 1; s += blockDim.x) {
+    mbar_init(&c.rx[s], 1);
+    mbar_expect_tx(&c.rx[s], rx_bytes);
+  }
+  asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+
+// Producer of the coupling-row ring (lane 0 of the producer warp). Unit u is chunk u % nchunk
+// of step t0 + u / nchunk and fills slot u % S; rows(t) points at the first of the CTA's nr
+// rows of that step's matrix. A slot is refilled only after every consumer warp released it.
+// After a timeout anywhere in the CTA (s_err), or when a release does not come, no further
+// copy is issued and the count issued is published in s_issued (consumers do not wait for
+// the rest; chain_exit waits for the last copy issued into every slot).
+template <typename V, typename RowsF>
+__device__ void ring_produce(const ChainSmem<V>& c, RowsF rows, int t0, int U, int nchunk, int S, int R, int CW,
+                             int ldb, int nr, int* err) {
+  int issued = 0;
+  for (int u = 0; u < U; ++u) {
+    const int slot = u % S;
+    if (u >= S && !mbar_wait(&c.empty[slot], (unsigned)(((u / S) - 1) & 1), c.s_err, err)) break;
+    if (*(volatile int*)c.s_err) break;
+    const int t = t0 + u / nchunk, ch = u - (t - t0) * nchunk;
+    V* dst = c.stage + (size_t)slot * R * CW;
+    if (nr == 0) {
+      mbar_expect_tx(&c.full[slot], 0);
+    } else {
+      const V* src = rows(t);
+      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+      if (nchunk == 1) {
+        const unsigned bytes = (unsigned)(sizeof(V) * (size_t)nr * ldb);
+        mbar_expect_tx(&c.full[slot], bytes);
+        bulk_g2s(dst, src, bytes, &c.full[slot]);
+      } else {
+        const int c0 = ch * CW, nc = min(CW, ldb - c0);
+        const unsigned bytes = (unsigned)(sizeof(V) * nc);
+        mbar_expect_tx(&c.full[slot], bytes * nr);
+        for (int r = 0; r < nr; ++r) bulk_g2s(dst + (size_t)r * CW, src + (size_t)r * ldb + c0, bytes, &c.full[slot]);
+      }
+    }
+    issued = u + 1;
+  }
+  if (issued < U) *(volatile int*)c.s_issued = issued;
+}
+
+// Exit of a chain kernel: no CTA may leave while a bulk copy into its ring or an st.async of
+// a peer into its receive buffers is in flight. Without a timeout in the CTA (s_err clear)
+// every consumer thread saw every ring copy and every receive phase complete, so nothing is in
+// flight. Otherwise, after the cluster barrier (every peer has issued its last stores and this
+// CTA's producer has published how many copies it issued), the CTA's threads wait, bounded
+// by kDrainPolls, for every receive barrier and for the last copy issued into every ring slot
+// (a slot never holds two copies in flight, so that copy's phase parity is unambiguous). What
+// these waits cover is every operation that lands within that bound of the last thread
+// reaching the exit; copies and stores take microseconds, the bound is far longer.
+template <typename V>
+__device__ __forceinline__ void chain_exit(const ChainSmem<V>& c, int nsteps, int S, int* err) {
+  cluster_sync();
+  if (!*(volatile int*)c.s_err) return;
+  for (int s = threadIdx.x; s < nsteps - 1; s += blockDim.x)
+    mbar_wait_cluster(&c.rx[s], 0u, c.s_err, err, kDrainPolls);
+  const int issued = *(volatile int*)c.s_issued;
+  for (int slot = threadIdx.x; slot < S && slot < issued; slot += blockDim.x) {
+    const int ul = slot + ((issued - 1 - slot) / S) * S;   // last unit issued into this slot
+    mbar_wait(&c.full[slot], (unsigned)((ul / S) & 1), c.s_err, err, kDrainPolls);
+  }
+}
+
+// mode 0: single chain (forward over blocks 0..nb-2, the last block, backward), one cluster,
+//         forward values kept in shared memory;
+// mode 1: forward chains of the twisted form (cluster 0: blocks 0..mid-1; cluster 1: blocks
+//         nb-1..mid+1), y written over p in uc;
+// mode 2: backward chains of the twisted form from x_m (formed in uc by k_seg_middle), y read
+//         from uc and x written over it.
 template <typename T, int RPW>
 __global__ void __launch_bounds__(kSolveMaxWarps * 32, 1)
     k_coarse_solve(const c2<T>* __restrict__ Lm, const c2<T>* __restrict__ Up, CoarseLayout L, SolveGeom G,
-                   c2<T>* uc, c2<T>* xmid, int* xflag, int* err, const int* active) {
+                   c2<T>* uc, int mode, int* err, const int* active) {
   using V = c2<T>;
   if (active && *active == 0) return;
   extern __shared__ __align__(128) unsigned char sm[];
-  uint64_t* full = reinterpret_cast<uint64_t*>(sm + G.off_mbar);
-  uint64_t* empty = full + G.S;
-  uint64_t* gbar = reinterpret_cast<uint64_t*>(sm + G.off_misc);   // receive barriers of gath[0/1]
-  int* s_err = reinterpret_cast<int*>(sm + G.off_misc + 16);
-  V* gath = reinterpret_cast<V*>(sm + G.off_gath);
-  V* wrows = reinterpret_cast<V*>(sm + G.off_w);
-  V* stage = reinterpret_cast<V*>(sm + G.off_stage);
+  const ChainSmem<V> c(sm, G);
 
   const unsigned rank = cluster_rank(), CS = cluster_size();
   const int B = L.B, ldb = L.ldb, nb = L.nb, R = G.R, CW = G.CW, nchunk = G.nchunk, S = G.S;
@@ -725,106 +870,89 @@ __global__ void __launch_bounds__(kSolveMaxWarps * 32, 1)
   const int nwc = (int)(blockDim.x >> 5) - 1;   // consumer warps; warp nwc is the producer
   const V zero = mk(T(0), T(0));
 
-  // This cluster's elimination chain. Cluster 0: forward over blocks 0..mid-1;
-  // cluster 1 (twisted launch): forward over blocks nb-1..mid+1. Both then solve
-  // the middle block and run their backward sweeps outwards.
-  const int ncl = (int)(gridDim.x / CS);
+  // This cluster's chain in global steps t: forward t < nf, middle t == nf, backward t > nf.
   unsigned cidu;
   asm volatile("mov.u32 %0, %%clusterid.x;" : "=r"(cidu));
-  const int cid = ncl > 1 ? (int)cidu : 0;
+  const int cid = mode == 0 ? 0 : (int)cidu;
   const int m = L.mid, dir = cid == 0 ? 1 : -1, J0 = cid == 0 ? 0 : nb - 1;
   const int nf = cid == 0 ? m : nb - 1 - m;
-  const int nsteps = 2 * nf + 1;
-  const int U = (nsteps - 1) * nchunk;   // ring units: the coupling GEMVs of steps 1..nsteps-1
+  const int tbeg = mode == 2 ? nf + 1 : 0, tend = mode == 1 ? nf : 2 * nf + 1;
+  const int nsteps = max(0, tend - tbeg);
+  const int tm = max(tbeg, 1);                    // first step with a coupling GEMV
+  const int U = max(0, tend - tm) * nchunk;       // ring units
   auto blockof = [&](int t) { return t < nf ? J0 + dir * t : (t == nf ? m : m - dir * (t - nf)); };
 
-  if (tid == 0) {
-    *s_err = 0;
-    for (int q = 0; q < S; ++q) {
-      mbar_init(&full[q], 1);
-      mbar_init(&empty[q], (unsigned)nwc);
-    }
-    mbar_init(&gbar[0], 1);
-    mbar_init(&gbar[1], 1);
-    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  const unsigned rx_bytes = (unsigned)(sizeof(V) * B);   // one value per row, from its owner
+  if (nsteps - 1 > G.nrx) {   // (the host sizes nrx for every launch; all CTAs agree)
+    if (tid == 0) atomicExch(err, HELM_EINVAL);
+    return;
   }
-  for (int i = tid; i < 2 * ldb; i += blockDim.x) gath[i] = zero;   // padding columns stay zero
+  chain_init(c, S, nwc, U, nsteps, rx_bytes);
+  for (int i = tid; i < 2 * ldb; i += blockDim.x) c.gath[i] = zero;   // padding columns stay zero
+  __syncthreads();
+  // mode 2: x_m is the first step's GEMV input, in the buffer step -1 would have filled
+  if (mode == 2 && nsteps > 0)
+    for (int i = tid; i < B; i += blockDim.x) c.gath[ldb + i] = cvt_ldcg(uc + (size_t)m * ldb + i);
   __syncthreads();
   cluster_sync();   // every CTA's barriers initialised before any remote store
+  if (nsteps == 0) return;
 
   if (warp == nwc) {
-    // ---- producer warp: unit u = (step 1 + u / nchunk, chunk u % nchunk) -> slot u % S
-    for (int u = 0; u < U; ++u) {
-      const int slot = u % S;
-      if (u >= S) mbar_wait(&empty[slot], (unsigned)(((u / S) - 1) & 1), s_err, err);   // slot released
-      if (lane == 0) {
-        const int t = 1 + u / nchunk, c = u - (t - 1) * nchunk;
-        V* dst = stage + (size_t)slot * R * CW;
-        if (nr == 0) {
-          mbar_expect_tx(&full[slot], 0);
-        } else {
-          const V* M = ((t <= nf) == (dir > 0)) ? Lm : Up;   // forward/middle: previous block; backward: next
-          const V* src = M + ((size_t)blockof(t) * B + r0) * ldb;
-          asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-          if (nchunk == 1) {
-            const unsigned bytes = (unsigned)(sizeof(V) * (size_t)nr * ldb);
-            mbar_expect_tx(&full[slot], bytes);
-            bulk_g2s(dst, src, bytes, &full[slot]);
-          } else {
-            const int c0 = c * CW, nc = min(CW, ldb - c0);
-            const unsigned bytes = (unsigned)(sizeof(V) * nc);
-            mbar_expect_tx(&full[slot], bytes * nr);
-            for (int r = 0; r < nr; ++r)
-              bulk_g2s(dst + (size_t)r * CW, src + (size_t)r * ldb + c0, bytes, &full[slot]);
-          }
-        }
-      }
-      __syncwarp();
+    if (lane == 0) {
+      auto rows = [&](int t) {
+        const V* M = ((t <= nf) == (dir > 0)) ? Lm : Up;   // forward/middle: previous block; backward: next
+        return M + ((size_t)blockof(t) * B + r0) * ldb;
+      };
+      ring_produce<V>(c, rows, tm, U, nchunk, S, R, CW, ldb, nr, err);
     }
+    __syncwarp();
   } else {
     // ---- consumer warps: warp w owns rows w, w + nwc, ... of the CTA's slice
-    const unsigned rx_bytes = (unsigned)(sizeof(V) * B);   // one value per row, from its owner
-    // p rows of the current forward / middle step, prefetched one step ahead. The loads
-    // are unconditional (rows outside the slice read entry 0 of the block) so that no
-    // select waits on them.
+    // the step's p (forward, middle) or y (backward) rows, prefetched one step ahead. The
+    // loads are unconditional (rows outside the slice read entry 0 of the block) so that no
+    // select waits on them; mode 0's backward steps read y from shared memory instead.
+    auto src_of = [&](int t) { return uc + (size_t)blockof(t) * ldb; };
     V pc[RPW];
 #pragma unroll
     for (int q = 0; q < RPW; ++q) {
       const int r = warp + q * nwc;
-      pc[q] = cvt_ldcg(uc + (size_t)blockof(0) * ldb + (r < nr ? r0 + r : 0));
+      pc[q] = cvt_ldcg(src_of(tbeg) + (r < nr ? r0 + r : 0));
     }
     int u = 0;
-    for (int t = 0; t < nsteps; ++t) {
-      const int blk = blockof(t);
+    for (int s = 0; s < nsteps; ++s) {
+      const int t = tbeg + s, blk = blockof(t);
+      const bool more = s + 1 < nsteps;
       const int kind = t < nf ? 0 : (t == nf ? 1 : 2);   // forward / middle / backward
-      if (tid == 0) mbar_expect_tx(&gbar[t & 1], rx_bytes);   // arm this step's receive phase
       V pn[RPW];
       {
-        const size_t nxt = (size_t)blockof(t + 1 <= nf ? t + 1 : t) * ldb;
+        const V* nx = src_of(more ? t + 1 : t);   // (a CTA with an empty slice has r0 >= B)
 #pragma unroll
         for (int q = 0; q < RPW; ++q) {
           const int r = warp + q * nwc;
-          pn[q] = cvt_ldcg(uc + nxt + (r < nr ? r0 + r : 0));   // (a CTA with an empty slice has r0 >= B)
+          pn[q] = cvt_ldcg(nx + (r < nr ? r0 + r : 0));
         }
       }
       // GEMV with the coupling matrix on the previous step's gathered vector
       V acc[RPW];
 #pragma unroll
       for (int q = 0; q < RPW; ++q) acc[q] = zero;
-      if (t >= 1) {
-        const V* x = gath + (size_t)((t - 1) & 1) * ldb;
-        for (int c = 0; c < nchunk; ++c, ++u) {
+      if (t >= tm) {
+        const V* x = c.gath + (size_t)((s - 1) & 1) * ldb;
+        for (int ch = 0; ch < nchunk; ++ch, ++u) {
           const int slot = u % S;
-          mbar_wait(&full[slot], (unsigned)((u / S) & 1), s_err, err);
-          const V* st = stage + (size_t)slot * R * CW;
-          const int c0 = c * CW, nc = min(CW, ldb - c0);
+          const bool ok =
+              __all_sync(0xffffffffu, ring_wait(&c.full[slot], (unsigned)((u / S) & 1), u, c.s_issued, c.s_err, err));
+          if (ok) {
+            const V* st = c.stage + (size_t)slot * R * CW;
+            const int c0 = ch * CW, nc = min(CW, ldb - c0);
 #pragma unroll
-          for (int q = 0; q < RPW; ++q) {
-            const int r = warp + q * nwc;
-            if (r < nr) acc[q] = cadd(acc[q], row_dot(st + (size_t)r * CW, x + c0, nc, lane));
+            for (int q = 0; q < RPW; ++q) {
+              const int r = warp + q * nwc;
+              if (r < nr) acc[q] = cadd(acc[q], row_dot(st + (size_t)r * CW, x + c0, nc, lane));
+            }
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&c.empty[slot]);   // released only after a landed copy
           }
-          __syncwarp();
-          if (lane == 0) mbar_arrive(&empty[slot]);   // this warp is done with the slot
         }
       }
       // this step's values for the warp's rows
@@ -832,61 +960,36 @@ __global__ void __launch_bounds__(kSolveMaxWarps * 32, 1)
       for (int q = 0; q < RPW; ++q) {
         const int r = warp + q * nwc;
         if (r < nr) {
-          const V a = t >= 1 ? warp_sum(acc[q]) : zero;
-          V val = a;
-          if (kind == 0) {
-            val = csub(pc[q], a);
-            if (lane == 0) wrows[(size_t)t * R + r] = val;
-          } else if (kind == 2) {
-            val = csub(wrows[(size_t)(2 * nf - t) * R + r], a);
-            if (lane == 0) uc[(size_t)blk * ldb + r0 + r] = val;
-          } else if (ncl > 1) {
-            // middle block: x_m = p_m - (g_0 + g_1), g_c = chain c's coupling term. The
-            // partials meet through global memory, one release flag per row and a
-            // bounded acquire spin (every lane spins: each one reads the partner's value).
-            const int row = r0 + r;
-            if (lane == 0) {
-              xmid[(size_t)cid * ldb + row] = a;
-              __threadfence();
-              asm volatile("st.release.gpu.global.b32 [%0], %1;" ::"l"(xflag + cid * ldb + row), "r"(1) : "memory");
-            }
-            int ok = 0;
-            for (long long it = 0; it < (1ll << 22); ++it) {
-              int f;
-              asm volatile("ld.acquire.gpu.global.b32 %0, [%1];" : "=r"(f) : "l"(xflag + (1 - cid) * ldb + row) : "memory");
-              if (f) {
-                ok = 1;
-                break;
-              }
-              if (*(volatile int*)s_err) break;
-            }
-            if (!ok) {
-              *(volatile int*)s_err = 1;
-              atomicExch(err, HELM_ETIMEOUT);
-            }
-            // both chains form the same sum (addition commutes), so both hold the same x_m
-            val = csub(pc[q], cadd(a, cvt_ldcg(xmid + (size_t)(1 - cid) * ldb + row)));
-            if (lane == 0 && cid == 0) uc[(size_t)blk * ldb + row] = val;
+          const V a = t >= tm ? warp_sum(acc[q]) : zero;
+          V val;
+          if (kind == 2 && mode == 0) {
+            val = csub(c.wrows[(size_t)(2 * nf - t) * R + r], a);
           } else {
             val = csub(pc[q], a);
-            if (lane == 0) uc[(size_t)blk * ldb + r0 + r] = val;
+          }
+          if (kind == 0 && mode == 0) {
+            if (lane == 0) c.wrows[(size_t)t * R + r] = val;
+          } else if (lane == 0) {
+            uc[(size_t)blk * ldb + r0 + r] = val;
           }
           acc[q] = val;
         }
       }
-      // broadcast: lanes 0..CS-1 of the owning warp push the value to every CTA
-      V* gdst = gath + (size_t)(t & 1) * ldb;
+      if (more) {
+        // broadcast: lanes 0..CS-1 of the owning warp push the value to every CTA
+        V* gdst = c.gath + (size_t)(s & 1) * ldb;
 #pragma unroll
-      for (int q = 0; q < RPW; ++q) {
-        const int r = warp + q * nwc;
-        if (r < nr && lane < (int)CS) st_async(gdst + r0 + r, (unsigned)lane, acc[q], &gbar[t & 1]);
+        for (int q = 0; q < RPW; ++q) {
+          const int r = warp + q * nwc;
+          if (r < nr && lane < (int)CS) st_async(gdst + r0 + r, (unsigned)lane, acc[q], &c.rx[s]);
+        }
+        mbar_wait_cluster(&c.rx[s], 0u, c.s_err, err, rx_polls(c.s_err));   // all B values arrived
       }
-      mbar_wait_cluster(&gbar[t & 1], (unsigned)((t >> 1) & 1), s_err, err);   // all B values arrived
 #pragma unroll
       for (int q = 0; q < RPW; ++q) pc[q] = pn[q];
     }
   }
-  cluster_sync();
+  chain_exit(c, nsteps, S, err);
 }
 
 // ---------------------------------------------------------------------------
@@ -971,12 +1074,7 @@ __global__ void __launch_bounds__(MAXW * 32, 1)
   using V = c2<T>;
   if (active && *active == 0) return;
   extern __shared__ __align__(128) unsigned char sm[];
-  uint64_t* full = reinterpret_cast<uint64_t*>(sm + G.off_mbar);
-  uint64_t* empty = full + G.S;
-  uint64_t* gbar = reinterpret_cast<uint64_t*>(sm + G.off_misc);
-  int* s_err = reinterpret_cast<int*>(sm + G.off_misc + 16);
-  V* gath = reinterpret_cast<V*>(sm + G.off_gath);
-  V* stage = reinterpret_cast<V*>(sm + G.off_stage);
+  const ChainSmem<V> c(sm, G);
 
   const unsigned rank = cluster_rank(), CS = cluster_size();
   const int B = L.B, ldb = L.ldb, R = G.R, CW = G.CW, nchunk = G.nchunk, S = G.S;
@@ -1004,54 +1102,28 @@ __global__ void __launch_bounds__(MAXW * 32, 1)
   const int tm = phA ? 1 : 0;   // first step with a matrix
   const int U = max(0, nsteps - tm) * nchunk;
 
-  if (tid == 0) {
-    *s_err = 0;
-    for (int q = 0; q < S; ++q) {
-      mbar_init(&full[q], 1);
-      mbar_init(&empty[q], (unsigned)nwc);
-    }
-    mbar_init(&gbar[0], 1);
-    mbar_init(&gbar[1], 1);
-    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  const unsigned rx_bytes = (unsigned)(sizeof(V) * B);
+  if (nsteps - 1 > G.nrx) {   // (the host sizes nrx for every launch; all CTAs agree)
+    if (tid == 0) atomicExch(err, HELM_EINVAL);
+    return;
   }
-  for (int i = tid; i < 2 * ldb; i += blockDim.x) gath[i] = zero;
+  chain_init(c, S, nwc, U, nsteps, rx_bytes);
+  for (int i = tid; i < 2 * ldb; i += blockDim.x) c.gath[i] = zero;
   __syncthreads();
   // the history of phase B's first step (the first segment's end), in the slot step 0 reads
   if (x0 && nsteps > 0)
-    for (int i = tid; i < B; i += blockDim.x) gath[ldb + i] = cvt_ldcg(x0 + i);
+    for (int i = tid; i < B; i += blockDim.x) c.gath[ldb + i] = cvt_ldcg(x0 + i);
   __syncthreads();
   cluster_sync();
   if (nsteps == 0) return;
 
   if (warp == nwc) {
-    for (int u = 0; u < U; ++u) {
-      const int slot = u % S;
-      if (u >= S) mbar_wait(&empty[slot], (unsigned)(((u / S) - 1) & 1), s_err, err);
-      if (lane == 0) {
-        const int t = tm + u / nchunk, c = u - (t - tm) * nchunk;
-        V* dst = stage + (size_t)slot * R * CW;
-        if (nr == 0) {
-          mbar_expect_tx(&full[slot], 0);
-        } else {
-          const V* src = mat(t) + (size_t)r0 * ldb;
-          asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-          if (nchunk == 1) {
-            const unsigned bytes = (unsigned)(sizeof(V) * (size_t)nr * ldb);
-            mbar_expect_tx(&full[slot], bytes);
-            bulk_g2s(dst, src, bytes, &full[slot]);
-          } else {
-            const int c0 = c * CW, nc = min(CW, ldb - c0);
-            const unsigned bytes = (unsigned)(sizeof(V) * nc);
-            mbar_expect_tx(&full[slot], bytes * nr);
-            for (int r = 0; r < nr; ++r)
-              bulk_g2s(dst + (size_t)r * CW, src + (size_t)r * ldb + c0, bytes, &full[slot]);
-          }
-        }
-      }
-      __syncwarp();
+    if (lane == 0) {
+      auto rows = [&](int t) { return mat(t) + (size_t)r0 * ldb; };
+      ring_produce<V>(c, rows, tm, U, nchunk, S, R, CW, ldb, nr, err);
     }
+    __syncwarp();
   } else {
-    const unsigned rx_bytes = (unsigned)(sizeof(V) * B);
     V pc[RPW];
 #pragma unroll
     for (int q = 0; q < RPW; ++q) {
@@ -1061,7 +1133,6 @@ __global__ void __launch_bounds__(MAXW * 32, 1)
     int u = 0;
     for (int t = 0; t < nsteps; ++t) {
       const bool more = t + 1 < nsteps;
-      if (tid == 0 && more) mbar_expect_tx(&gbar[t & 1], rx_bytes);
       V pn[RPW];
       {
         const V* nx = inv(more ? t + 1 : t);
@@ -1075,19 +1146,22 @@ __global__ void __launch_bounds__(MAXW * 32, 1)
 #pragma unroll
       for (int q = 0; q < RPW; ++q) acc[q] = zero;
       if (t >= tm) {
-        const V* x = gath + (size_t)((t - 1) & 1) * ldb;
-        for (int c = 0; c < nchunk; ++c, ++u) {
+        const V* x = c.gath + (size_t)((t - 1) & 1) * ldb;
+        for (int ch = 0; ch < nchunk; ++ch, ++u) {
           const int slot = u % S;
-          mbar_wait(&full[slot], (unsigned)((u / S) & 1), s_err, err);
-          const V* st = stage + (size_t)slot * R * CW;
-          const int c0 = c * CW, nc = min(CW, ldb - c0);
+          const bool ok =
+              __all_sync(0xffffffffu, ring_wait(&c.full[slot], (unsigned)((u / S) & 1), u, c.s_issued, c.s_err, err));
+          if (ok) {
+            const V* st = c.stage + (size_t)slot * R * CW;
+            const int c0 = ch * CW, nc = min(CW, ldb - c0);
 #pragma unroll
-          for (int q = 0; q < RPW; ++q) {
-            const int r = warp + q * nwc;
-            if (r < nr) acc[q] = cadd(acc[q], row_dot(st + (size_t)r * CW, x + c0, nc, lane));
+            for (int q = 0; q < RPW; ++q) {
+              const int r = warp + q * nwc;
+              if (r < nr) acc[q] = cadd(acc[q], row_dot(st + (size_t)r * CW, x + c0, nc, lane));
+            }
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&c.empty[slot]);
           }
-          __syncwarp();
-          if (lane == 0) mbar_arrive(&empty[slot]);
         }
       }
       V* o = a.out + (size_t)blk(t) * ldb;
@@ -1101,26 +1175,27 @@ __global__ void __launch_bounds__(MAXW * 32, 1)
         }
       }
       if (more) {
-        V* gdst = gath + (size_t)(t & 1) * ldb;
+        V* gdst = c.gath + (size_t)(t & 1) * ldb;
 #pragma unroll
         for (int q = 0; q < RPW; ++q) {
           const int r = warp + q * nwc;
-          if (r < nr && lane < (int)CS) st_async(gdst + r0 + r, (unsigned)lane, acc[q], &gbar[t & 1]);
+          if (r < nr && lane < (int)CS) st_async(gdst + r0 + r, (unsigned)lane, acc[q], &c.rx[t]);
         }
-        mbar_wait_cluster(&gbar[t & 1], (unsigned)((t >> 1) & 1), s_err, err);
+        mbar_wait_cluster(&c.rx[t], 0u, c.s_err, err, rx_polls(c.s_err));
       }
 #pragma unroll
       for (int q = 0; q < RPW; ++q) pc[q] = pn[q];
     }
   }
-  cluster_sync();
+  chain_exit(c, nsteps, S, err);
 }
 
 // Middle block of the twisted form: x_m = p_m - Lm[m] y_{m-1} - Up[m] y_{m+1}, written to
-// out[m] (the backward paths' first position). One warp per row.
+// y[m] (the backward chains' first input). One warp per row. p and y may be the same vector
+// (each lane reads p_m's row before its warp writes that row; y_{m-1}, y_{m+1} are not written).
 template <typename T>
 __global__ void __launch_bounds__(256) k_seg_middle(const c2<T>* __restrict__ Lm, const c2<T>* __restrict__ Up,
-                                                    const c2<T>* __restrict__ p, c2<T>* __restrict__ y,
+                                                    const c2<T>* p, c2<T>* y,
                                                     CoarseLayout L, const int* active) {
   using V = c2<T>;
   if (active && *active == 0) return;
@@ -1282,9 +1357,6 @@ __global__ void __launch_bounds__(256) k_seg_products(SegProducts sp, CoarseLayo
 
 }  // namespace
 
-std::mutex g_twist_mu;
-std::unordered_map<long long, bool> g_twist_ok;   // launch shape -> two clusters co-resident
-
 namespace {
 SegPath make_path(int J0, int step, int n, int Kmax, int kc0) {
   SegPath p;
@@ -1339,7 +1411,7 @@ int plan_coarse_solve(const CoarseLayout& L, CoarsePlan* plan) {
       cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)budget);
       for (int cw = L.ldb; cw >= 2; cw = ((cw / 2) + 1) & ~1) {
         for (int st = 4; st >= 2; --st) {
-          SolveGeom G = solve_geometry<T>(L, CS, cw, st, false);
+          SolveGeom G = solve_geometry<T>(L, CS, cw, st, false, chain_rx(L, false));
           if (G.total > budget) continue;
           cudaLaunchConfig_t cfg = {};
           cfg.gridDim = dim3(CS);
@@ -1399,6 +1471,10 @@ int plan_coarse_solve(const CoarseLayout& L, CoarsePlan* plan) {
       return HELM_OK;
     }
   }
+  // Twisted form (two chains meeting in the middle block) wherever the coarse grid has four or
+  // more blocks: its forward and backward chains are separate launches, so the two clusters of
+  // a launch never wait for one another and need not be resident at the same time.
+  const int ncl = L.nb >= 4 ? 2 : 1;
   for (int CS : {16, 8, 4, 2, 1}) {
     const int R = (L.B + CS - 1) / CS;
     // one consumer warp per row of the CTA's slice (up to kRPW rows per warp) + a producer
@@ -1410,7 +1486,7 @@ int plan_coarse_solve(const CoarseLayout& L, CoarsePlan* plan) {
     // widest chunk (even, <= ldb) that leaves room for >= 2 stages
     for (int CW = L.ldb; CW >= 2; CW = ((CW / 2) + 1) & ~1) {
       for (int S = 4; S >= 2; --S) {
-        SolveGeom G = solve_geometry<T>(L, CS, CW, S);
+        SolveGeom G = solve_geometry<T>(L, CS, CW, S, ncl == 1, chain_rx(L, ncl == 1));
         if (G.total > budget) continue;
         const bool one = (R + nwc - 1) / nwc == 1;
         auto kern = one ? k_coarse_solve<T, 1> : k_coarse_solve<T, kRPW>;
@@ -1428,8 +1504,8 @@ int plan_coarse_solve(const CoarseLayout& L, CoarsePlan* plan) {
         at[0].val.clusterDim.z = 1;
         cfg.attrs = at;
         cfg.numAttrs = 1;
-        int ncl = 0;
-        if (cudaOccupancyMaxActiveClusters(&ncl, (void*)kern, &cfg) != cudaSuccess || ncl < 1) {
+        int nact = 0;
+        if (cudaOccupancyMaxActiveClusters(&nact, (void*)kern, &cfg) != cudaSuccess || nact < 1) {
           cudaGetLastError();
           continue;
         }
@@ -1440,44 +1516,7 @@ int plan_coarse_solve(const CoarseLayout& L, CoarsePlan* plan) {
         plan->S = S;
         plan->smem = G.total;
         plan->threads = 32 * nwarps;
-        plan->ncl = 1;
-        // Twisted form: two co-resident clusters (cooperative launch). Validated once per
-        // launch shape by an inert trial launch whose 'active' flag is 0 (the kernel
-        // returns at entry); the answer is cached (the trial synchronises the device).
-        const long long key = ((long long)sizeof(T) << 56) ^ ((long long)CS << 48) ^ ((long long)nwarps << 40) ^
-                              (long long)G.total ^ ((long long)dev << 32);
-        {
-          std::lock_guard<std::mutex> lk(g_twist_mu);
-          auto it = g_twist_ok.find(key);
-          if (it != g_twist_ok.end()) {
-            plan->ncl = (L.nb >= 4 && ncl >= 2 && it->second) ? 2 : 1;
-            return HELM_OK;
-          }
-        }
-        if (L.nb >= 4 && ncl >= 2) {
-          int* off = nullptr;
-          if (cudaMalloc(&off, sizeof(int)) == cudaSuccess) {
-            cudaMemset(off, 0, sizeof(int));
-            CoarseLayout L2 = L;
-            L2.mid = L.nb / 2;
-            cudaLaunchAttribute at2[2];
-            at2[0] = at[0];
-            at2[1].id = cudaLaunchAttributeCooperative;
-            at2[1].val.cooperative = 1;
-            cfg.gridDim = dim3(2 * CS);
-            cfg.attrs = at2;
-            cfg.numAttrs = 2;
-            cudaError_t e = cudaLaunchKernelEx(&cfg, kern, (const c2<T>*)nullptr, (const c2<T>*)nullptr,
-                                               L2, G, (c2<T>*)nullptr, (c2<T>*)nullptr, (int*)nullptr,
-                                               (int*)nullptr, (const int*)off);
-            if (e == cudaSuccess) e = cudaDeviceSynchronize();
-            if (e == cudaSuccess) plan->ncl = 2;
-            cudaGetLastError();
-            cudaFree(off);
-            std::lock_guard<std::mutex> lk(g_twist_mu);
-            g_twist_ok[key] = plan->ncl == 2;
-          }
-        }
+        plan->ncl = ncl;
         return HELM_OK;
       }
       if (CW == 2) break;
@@ -1503,9 +1542,8 @@ int plan_coarse_solve(const CoarseLayout& L, CoarsePlan* plan) {
 
 template <typename T>
 void launch_coarse_solve(const CoarsePlan& plan, const c2<T>* Dinv, const c2<T>* Lm, const c2<T>* Up,
-                         const CoarseLayout& L, const c2<T>* rc, c2<T>* uc, c2<T>* xmid, int* xflag,
-                         unsigned* bar, int* err, const int* active, int nsm, cudaStream_t s,
-                         const SegBufs<T>* seg) {
+                         const CoarseLayout& L, const c2<T>* rc, c2<T>* uc, unsigned* bar, int* err,
+                         const int* active, int nsm, cudaStream_t s, const SegBufs<T>* seg) {
   // p = blockdiag(Dinv) r for all blocks at once, into uc
   if (sizeof(c2<T>) * L.ldb <= 48 * 1024)
     k_block_gemv<T><<<dim3(L.nb, (L.B + kRowsSlab - 1) / kRowsSlab), kRowsThreads, sizeof(c2<T>) * L.ldb, s>>>(
@@ -1517,7 +1555,7 @@ void launch_coarse_solve(const CoarsePlan& plan, const c2<T>* Dinv, const c2<T>*
     auto chain = [&](const SegArgs<T>& a, int nclusters) {
       const bool b = a.phase == 1;
       const int CS = b ? plan.CSb : plan.CS, R = b ? plan.Rb : plan.R, threads = b ? plan.threadsb : plan.threads;
-      SolveGeom G = solve_geometry<T>(L, CS, b ? plan.CWb : plan.CW, b ? plan.Sb : plan.S, false);
+      SolveGeom G = solve_geometry<T>(L, CS, b ? plan.CWb : plan.CW, b ? plan.Sb : plan.S, false, chain_rx(L, false));
       const int nwc = threads / 32 - 1;
       auto kern = nwc >= kSolveMaxWarps ? k_seg_chain<T, 1, kSegWideWarps>
                   : (R + nwc - 1) / nwc == 1 ? k_seg_chain<T, 1>
@@ -1567,30 +1605,34 @@ void launch_coarse_solve(const CoarsePlan& plan, const c2<T>* Dinv, const c2<T>*
     cudaLaunchKernelEx(&cfg, k_coarse_solve_grid<T>, Lm, Up, L, uc, bar, err, active);
     return;
   }
-  SolveGeom G = solve_geometry<T>(L, plan.CS, plan.CW, plan.S);
+  SolveGeom G = solve_geometry<T>(L, plan.CS, plan.CW, plan.S, plan.ncl == 1, chain_rx(L, plan.ncl == 1));
   // (the function's dynamic shared-memory cap was raised to the device limit by
   // plan_coarse_solve, outside any stream capture)
   const int ncl = L.mid < L.nb - 1 ? 2 : 1;
-  if (ncl > 1) cudaMemsetAsync(xflag, 0, 2 * (size_t)L.ldb * sizeof(int), s);
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3(plan.CS * ncl);
   cfg.blockDim = dim3(plan.threads);
   cfg.dynamicSmemBytes = G.total;
   cfg.stream = s;
-  cudaLaunchAttribute at[2];
+  cudaLaunchAttribute at[1];
   at[0].id = cudaLaunchAttributeClusterDimension;
   at[0].val.clusterDim.x = plan.CS;
   at[0].val.clusterDim.y = 1;
   at[0].val.clusterDim.z = 1;
-  // the two clusters exchange the middle block's couplings: they must be co-resident
-  at[1].id = cudaLaunchAttributeCooperative;
-  at[1].val.cooperative = 1;
   cfg.attrs = at;
-  cfg.numAttrs = ncl > 1 ? 2 : 1;
+  cfg.numAttrs = 1;
   const int nwc = plan.threads / 32 - 1;
   const bool one = (plan.R + nwc - 1) / nwc == 1;
-  cudaLaunchKernelEx(&cfg, one ? k_coarse_solve<T, 1> : k_coarse_solve<T, kRPW>, Lm, Up, L, G, uc, xmid, xflag, err,
-                     active);
+  auto kern = one ? k_coarse_solve<T, 1> : k_coarse_solve<T, kRPW>;
+  if (ncl == 1) {
+    cudaLaunchKernelEx(&cfg, kern, Lm, Up, L, G, uc, 0, err, active);
+    return;
+  }
+  // twisted form: forward chains, middle block, backward chains (three launches, no
+  // dependence between the clusters of one launch)
+  cudaLaunchKernelEx(&cfg, kern, Lm, Up, L, G, uc, 1, err, active);
+  k_seg_middle<T><<<(L.B * 32 + 255) / 256, 256, 0, s>>>(Lm, Up, uc, uc, L, active);
+  cudaLaunchKernelEx(&cfg, kern, Lm, Up, L, G, uc, 2, err, active);
 }
 
 namespace {
@@ -1701,9 +1743,9 @@ int coarse_seg_launches(const CoarseLayout& L, const CoarsePlan& plan) {
 template int plan_coarse_solve<float>(const CoarseLayout&, CoarsePlan*);
 template int plan_coarse_solve<double>(const CoarseLayout&, CoarsePlan*);
 template void launch_coarse_solve<float>(const CoarsePlan&, const float2*, const float2*, const float2*,
-                                         const CoarseLayout&, const float2*, float2*, float2*, int*, unsigned*,
-                                         int*, const int*, int, cudaStream_t, const SegBufs<float>*);
+                                         const CoarseLayout&, const float2*, float2*, unsigned*, int*, const int*,
+                                         int, cudaStream_t, const SegBufs<float>*);
 template void launch_coarse_solve<double>(const CoarsePlan&, const double2*, const double2*, const double2*,
-                                          const CoarseLayout&, const double2*, double2*, double2*, int*, unsigned*,
-                                          int*, const int*, int, cudaStream_t, const SegBufs<double>*);
+                                          const CoarseLayout&, const double2*, double2*, unsigned*, int*,
+                                          const int*, int, cudaStream_t, const SegBufs<double>*);
 }  // namespace helm

@@ -88,13 +88,12 @@ int plan_coarse_solve(const CoarseLayout& L, CoarsePlan* plan);
 // uc = A^{-1} rc for the block-padded coarse vectors (uc also holds the block-diagonal
 // pre-pass p = Dinv r). plan.seg with seg given: the segmented half-sweeps of the twisted
 // form (seg->yb holds the forward sweep). Otherwise L.mid < L.nb - 1 runs the twisted form
-// on two clusters (xmid: 2 x ldb values, xflag: 2 x ldb ints of exchange space); bar:
-// kBarWords unsigned for the grid kernel's barrier.
+// as three launches (forward chains, middle block, backward chains); bar: kBarWords unsigned
+// for the grid kernel's barrier.
 template <typename T>
 void launch_coarse_solve(const CoarsePlan& plan, const c2<T>* Dinv, const c2<T>* Lm, const c2<T>* Up,
-                         const CoarseLayout& L, const c2<T>* rc, c2<T>* uc, c2<T>* xmid, int* xflag,
-                         unsigned* bar, int* err, const int* active, int nsm, cudaStream_t s,
-                         const SegBufs<T>* seg = nullptr);
+                         const CoarseLayout& L, const c2<T>* rc, c2<T>* uc, unsigned* bar, int* err,
+                         const int* active, int nsm, cudaStream_t s, const SegBufs<T>* seg = nullptr);
 // Segment products of both sweeps (plan.seg, complex64), and the number of launches it takes
 void coarse_seg_products(const float2* Lm, const float2* Up, float2* Pf, float2* Pb, const CoarseLayout& L,
                          const CoarsePlan& plan, cudaStream_t s);

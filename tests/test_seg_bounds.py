@@ -32,11 +32,12 @@ def coarse_layout(dim, order, n):
     return nb, B, ldb
 
 
-def solve_geometry(B, ldb, CS, CW, S):
+def solve_geometry(B, ldb, CS, CW, S, nrx):
     al = lambda x: (x + 127) & ~127  # noqa: E731
     R = (B + CS - 1) // CS
     o = al(16 * S)                  # full[S], empty[S]
-    o = al(o + 32)                  # receive barriers, error word
+    o = al(o + 32)                  # error word, units issued
+    o = al(o + 8 * nrx)             # receive barriers, one per gathering step
     o_gath = o
     o = al(o + ELEM * 2 * ldb)      # receive buffers
     o = al(o)                       # no forward-value rows
@@ -45,7 +46,7 @@ def solve_geometry(B, ldb, CS, CW, S):
     return dict(R=R, CW=CW, nchunk=(ldb + CW - 1) // CW, S=S, off_gath=o_gath, off_stage=o_stage, total=o)
 
 
-def seg_geom(B, ldb, CS):
+def seg_geom(B, ldb, CS, nb):
     """Chunk width and ring depth the plan picks for a cluster of CS CTAs (None: none fits)."""
     R = (B + CS - 1) // CS
     wide = SOLVE_MAX_WARPS <= R < SEG_WIDE_WARPS
@@ -56,9 +57,9 @@ def seg_geom(B, ldb, CS):
     cw = ldb
     while cw >= 2:
         for S in (4, 3, 2):
-            G = solve_geometry(B, ldb, CS, cw, S)
+            G = solve_geometry(B, ldb, CS, cw, S, nb // 2 + 2)
             if G["total"] <= SMEM_BUDGET:
-                G.update(CS=CS, nwc=nwc, rpw=rpw, threads=32 * (nwc + 1))
+                G.update(CS=CS, nwc=nwc, rpw=rpw, threads=32 * (nwc + 1), nrx=nb // 2 + 2)
                 return G
         if cw == 2:
             break
@@ -109,6 +110,7 @@ def check_chain(nb, B, ldb, G, pp, phase):
         nsteps = max(0, min(p["Ls"], p["n"] - q0)) if phase == 0 else p["K"] - 1
         pos = (lambda t: q0 + t) if phase == 0 else (lambda t: seg_end(t + 1, p["Ls"], p["n"]))
         tm = 1 if phase == 0 else 0
+        assert nsteps - 1 <= G["nrx"]                  # one receive barrier per gathering step
         writes[cid] = set()
         if phase == 1 and nsteps > 0:
             x0 = blk(p, seg_end(0, p["Ls"], p["n"]))
@@ -208,10 +210,10 @@ def test_segment_kernels_stay_in_bounds(dim, order, n):
         pytest.skip("the plan does not take the segmented solve for this layout")
     checked = 0
     for CS in (9, 8, 16):
-        GA = seg_geom(B, ldb, CS)
+        GA = seg_geom(B, ldb, CS, nb)
         if GA is None:
             continue
-        GBs = [GA] + ([seg_geom(B, ldb, 16)] if CS != 16 and seg_geom(B, ldb, 16) else [])
+        GBs = [GA] + ([seg_geom(B, ldb, 16, nb)] if CS != 16 and seg_geom(B, ldb, 16, nb) else [])
         for K in (2, 3, 4, 5, 6, 7, 8, 9, 11, 13, 16, 19, 24, 32, 40):
             m, f, b = seg_paths(nb, K)
             for pp, allowed in ((f, set()), (b, {m})):

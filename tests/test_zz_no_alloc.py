@@ -2,13 +2,18 @@
 device memory when they call (fixed memory budget, their own allocator, or no
 room for the synchronisation a cudaMalloc may cause). It must give what
 helm_coarse_solve gives, call after call, using only the library's fixed 4 MiB
-scratch array, and refuse problems that do not fit. Collected after the main parity tests
-(only the Q_p parity tests of test_zzz_gpu_qp come later).
+scratch array, and refuse problems that do not fit. Both are also held, entry by
+entry, to the oracle's sparse direct solve of its own assembled coarse matrix
+(independent of the library's factor). Collected after the main parity tests (only
+the Q_p parity tests of test_zzz_gpu_qp come later).
 """
 import ctypes
 
 import numpy as np
 import pytest
+import scipy.sparse.linalg as spla
+
+from oracle import fem
 
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
@@ -38,6 +43,11 @@ def _noalloc(s, rc):
 ])
 def test_noalloc_matches_coarse_solve_twice(order, n, k, prec, tol):
     s = pkg.Solver(k, n, order, 0.5 * k * k, precision=prec)
+    cmesh = fem.build_mesh(2, order, n // 2)
+    Kc, Mc, Bc = fem.assemble(cmesh)
+    Ac = fem.system_matrix(Kc, Mc, Bc, k, 0.5 * k * k).tocsc()
+    lu = spla.splu(Ac)
+    a2 = np.sqrt(spla.norm(Ac, 1) * spla.norm(Ac, np.inf))     # >= ||Ac||_2
     g = np.random.default_rng(17)
     for call in range(2):                   # two calls in a row: no state may leak between calls
         r = g.standard_normal(s.num_coarse_dofs) + 1j * g.standard_normal(s.num_coarse_dofs)
@@ -45,6 +55,11 @@ def test_noalloc_matches_coarse_solve_twice(order, n, k, prec, tol):
         ref = s.coarse_solve(rc).cpu().numpy()
         got = _noalloc(s, rc).cpu().numpy()
         assert np.linalg.norm(got - ref) <= tol * np.linalg.norm(ref), call
+        exact = lu.solve(r)                 # the oracle's coarse matrix, its own direct solve
+        for u in (got, ref):
+            assert np.max(np.abs(u - exact)) <= tol * np.max(np.abs(exact)), call
+            # ||Ac u - r|| = ||Ac (u - exact)|| <= ||Ac|| ||u - exact||
+            assert np.linalg.norm(Ac @ u - r) <= tol * a2 * np.linalg.norm(exact), call
     s.close()
 
 
