@@ -92,6 +92,14 @@ def random_load(num_dofs: int, seed: int) -> np.ndarray:
     return re + 1j * im
 
 
+def uniform_loads(sizes, seed: int = 0):
+    """Load vectors with entries uniform in [-1, 1] (real), one per size, drawn in order from
+    PCG64(seed): the right-hand sides of the shift search's sample solves (Sec. 5, data
+    generation: f ~ U[-1, 1], g = 0; the draw is taken as the load vector itself)."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    return [rng.uniform(-1.0, 1.0, n).astype(np.complex128) for n in sizes]
+
+
 def shift_sweep(seed: int = 4, n_pairs: int = 32, n_shifts: int = 16,
                 n_min: int = 32, n_max: int = 1024):
     """Batched shift-sample sweep: (k, kh) pairs times a log grid of shifts.

@@ -280,3 +280,52 @@ def build_problem_q(wl, mu=None, source=None):
     else:
         raise ValueError(wl.rhs)
     return Problem(wl, mesh, cmesh, K, M, B, A0, Aeps, Aeps_c, P, F)
+
+
+# ----------------------------------------------------------------------------
+# Sec. 5, data generation: the optimal shift exponent of one problem by a golden-section
+# search over sigma in [1, 2] (eps = k^sigma), objective the average convergence rate.
+# ----------------------------------------------------------------------------
+
+
+def shift_rate(k, n, order, sigma, F, maxit=50, omega=0.6, nu=2, dim=2):
+    """rho = (r_end / r_0)^(1/end) of FGMRES without restart, stopped at relative residual
+    1e-8 or after maxit iterations, right-preconditioned by the twogrid cycle on the shift
+    eps = k^sigma; x0 = 0, so r_0 = ||F||, and r_end is the true residual (Sec. 5)."""
+    mesh = fem.build_mesh(dim, order, n)
+    cmesh = fem.build_mesh(dim, order, n // 2)
+    K, M, B = fem.assemble(mesh)
+    Kc, Mc, Bc = fem.assemble(cmesh)
+    eps = k ** sigma
+    tg = TwoGrid(fem.system_matrix(K, M, B, k, eps), fem.system_matrix(Kc, Mc, Bc, k, eps),
+                 fem.prolongation(cmesh, mesh), omega, nu)
+    r = fgmres(fem.system_matrix(K, M, B, k, 0.0), F, tg.apply, restart=maxit, tol=1e-8, maxit=maxit)
+    return r.relres_true ** (1.0 / r.iters) if r.relres_true > 0 else 0.0
+
+
+def golden_section_min(f, lo, hi, tol):
+    """Minimum of a unimodal f on [lo, hi] by golden-section search (Kiefer 1953): the two
+    interior points divide the bracket in the golden ratio, the bracket keeps the side of the
+    smaller value and reuses the other point, until it is narrower than tol. Returns
+    (x, f(x), evaluations) for the better of the two last interior points."""
+    r = (math.sqrt(5.0) - 1.0) / 2.0          # 1 / golden ratio
+    a, b = lo, hi
+    x1, x2 = b - r * (b - a), a + r * (b - a)
+    f1, f2 = f(x1), f(x2)
+    count = 2
+    while b - a > tol:
+        if f1 < f2:                            # the minimum lies in [a, x2]
+            b, x2, f2 = x2, x1, f1
+            x1 = b - r * (b - a)
+            f1 = f(x1)
+        else:                                  # the minimum lies in [x1, b]
+            a, x1, f1 = x1, x2, f2
+            x2 = a + r * (b - a)
+            f2 = f(x2)
+        count += 1
+    return (x1, f1, count) if f1 < f2 else (x2, f2, count)
+
+
+def optimal_shift_exponent(k, n, order, F, tol=1e-2, maxit=50):
+    """sigma_hat = argmin over [1, 2] of shift_rate (golden-section search to tol)."""
+    return golden_section_min(lambda s: shift_rate(k, n, order, s, F, maxit), 1.0, 2.0, tol)

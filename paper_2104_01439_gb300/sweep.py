@@ -132,9 +132,10 @@ def golden_section(problems, tol: float = 1e-2, maxit: int = 50, precision: int 
 
     problems: list of (k, n, order). Returns a list of (sigma_hat, rho_hat, evaluations)."""
     import torch
-    rng = np.random.Generator(np.random.PCG64(seed))
-    loads = [torch.from_numpy(rng.uniform(-1.0, 1.0, (order * n + 1) ** 2).astype(np.complex128))
-             for k, n, order in problems]
+
+    import helm_inputs
+    loads = [torch.from_numpy(F) for F in
+             helm_inputs.uniform_loads([(order * n + 1) ** 2 for k, n, order in problems], seed)]
 
     def evaluate(points):
         samples = [Sample(problems[i][0], problems[i][1], problems[i][0] ** x, problems[i][2]) for i, x in points]

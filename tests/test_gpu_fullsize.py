@@ -5,7 +5,9 @@ against the oracle's assembled CSR matrix, the true residual of the GPU
 solution recomputed with the oracle's A0, the coarse residual with the
 oracle's assembled coarse matrix, and the iteration count against the
 oracle's own full solve (tests/golden/oracle_iterations.json, written by a
-script that runs only the oracle)."""
+script that runs only the oracle). The benchmark's workload is also solved by
+the oracle here (about a minute of CPU time) and both GPU forms are compared
+with its solution entry by entry."""
 import json
 import os
 
@@ -13,7 +15,8 @@ import numpy as np
 import pytest
 
 import helm_inputs as hi
-from oracle import fem
+from oracle import fem, solver as osolver
+from parity import assert_entrywise
 
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
@@ -59,6 +62,37 @@ def test_fullsize_solve(wl):
     if wl.name in GOLDEN:
         assert abs(r.iters - GOLDEN[wl.name]["iters"]) <= 3, (r.iters, GOLDEN[wl.name]["iters"])
     s.close()
+
+
+_ORACLE = {}
+
+
+def oracle_solve(wl):
+    """The oracle's problem and its full FGMRES solve (Sec. 4), once per workload."""
+    if wl.name not in _ORACLE:
+        pb = osolver.build_problem(wl)
+        _ORACLE[wl.name] = (pb, pb.solve())
+    return _ORACLE[wl.name]
+
+
+@pytest.mark.parametrize("prec,slack", [(pkg.HELM_FP64, 1), (pkg.HELM_MIXED, 3)], ids=["fp64", "mixed"])
+def test_fullsize_solution_matches_oracle(prec, slack):
+    """The benchmark's workload (2D P1, h = 1/512, k = 200) in both forms against the oracle's
+    own solve: iterations within +-1 (FP64) / +-3 (complex64 preconditioner), true residual
+    <= 1e-8, and the solution within 1e-5 normwise and entry by entry in every DoF class."""
+    wl = hi.GAUSS_P1
+    pb, ref = oracle_solve(wl)
+    assert ref.iters == GOLDEN[wl.name]["iters"]
+    s = pkg.Solver(wl.k, wl.n, wl.order, wl.shift, dim=wl.dim, restart=wl.restart, maxit=wl.maxit, tol=wl.tol,
+                   precision=prec)
+    x, r = s.solve(dev(pb.F))
+    xh = x.cpu().numpy()
+    s.close()
+    relres = np.linalg.norm(pb.F - pb.A0 @ xh) / np.linalg.norm(pb.F)
+    assert r.status == "converged" and relres <= 1e-8 and abs(relres - r.relres_true) <= 1e-10
+    assert abs(r.iters - ref.iters) <= slack, (r.iters, ref.iters)
+    assert np.linalg.norm(xh - ref.x) / np.linalg.norm(ref.x) <= 1e-5
+    assert_entrywise(xh, ref.x, pb.mesh.coords, 1e-5, "solution")
 
 
 @pytest.mark.parametrize("prec,tol", [(pkg.HELM_FP64, 1e-10), (pkg.HELM_MIXED, 1e-4)])

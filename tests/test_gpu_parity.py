@@ -16,6 +16,7 @@ import pytest
 
 import helm_inputs as hi
 from oracle import fem, solver as osolver
+from parity import assert_entrywise
 
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
@@ -66,6 +67,7 @@ def test_apply_fp64(wl):
     for which, A in ((0, pb.A0), (1, pb.Aeps)):
         y = s.apply(dev(x), which).cpu().numpy()
         assert rel(y, A @ x) <= 1e-12
+        assert_entrywise(y, A @ x, pb.mesh.coords, 1e-12, f"A{which} x")
     s.close()
 
 
@@ -78,6 +80,7 @@ def test_coarse_solve(wl, prec, tol):
     uc = s.coarse_solve(dev(r)).cpu().numpy()
     ref = pb.twogrid().coarse_solve(r)
     assert rel(uc, ref) <= tol
+    assert_entrywise(uc, ref, pb.cmesh.coords, tol, "coarse solve")
     s.close()
 
 
@@ -90,6 +93,7 @@ def test_vcycle(wl, prec, tol):
     u = s.vcycle(dev(f)).cpu().numpy()
     ref = pb.twogrid().apply(f)
     assert rel(u, ref) <= tol
+    assert_entrywise(u, ref, pb.mesh.coords, tol, "V-cycle")
     s.close()
 
 
@@ -106,6 +110,7 @@ def test_smooth_operator_handle(wl, prec, tol):
         u = s.smooth(dev(f), nu).cpu().numpy()
         ref = osolver.jacobi_sweeps(pb.Aeps, dinv, f, np.zeros_like(f), 0.6, nu)
         assert rel(u, ref) <= tol * nu, nu
+        assert_entrywise(u, ref, pb.mesh.coords, tol * nu, f"{nu} sweeps")
     x = crand(pb.mesh.num_dofs, 7)
     assert rel(s.apply(dev(x), 1).cpu().numpy(), pb.Aeps @ x) <= 1e-12
     for call in (lambda: s.vcycle(dev(f)), lambda: s.solve(dev(f)), lambda: s.smooth(dev(f), 1),
@@ -141,6 +146,7 @@ def test_solve_parity(wl, prec):
     slack = 1 if prec == pkg.HELM_FP64 else 3
     assert abs(res.iters - ref.iters) <= slack, (res.iters, ref.iters)
     assert rel(xh, ref.x) <= 1e-5
+    assert_entrywise(xh, ref.x, pb.mesh.coords, 1e-5, "solution")
     s.close()
 
 

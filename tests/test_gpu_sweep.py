@@ -32,10 +32,22 @@ def test_sweep_matches_single_solves(pkg):
         assert b.iters == min(r.iters for r in grp)
 
 
-def test_golden_section_batched(pkg):
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+def test_golden_section_batched(pkg, prec):
+    """The batched golden-section search of Sec. 5 (all searches advanced together through the
+    request server) against the oracle's one-problem-at-a-time search on the same loads: the
+    exponents agree within the search tolerance (a comparison of two nearly equal rates may
+    go either way, which moves the final bracket by at most one reduction) and the rates."""
+    import helm_inputs as hi
+    from oracle import solver as osolver
     from paper_2104_01439_gb300 import sweep
-    out = sweep.golden_section([(12.0, 32, 1), (20.0, 32, 1)], tol=1e-2, maxit=50, max_active=4)
-    for s, rho, n in out:
-        assert 1.0 <= s <= 2.0
-        assert 0.0 < rho < 1.0
-        assert n == 12
+    problems = [(12.0, 32, 1), (20.0, 32, 1)]
+    precision = pkg.HELM_FP64 if prec == "fp64" else pkg.HELM_MIXED
+    out = sweep.golden_section(problems, tol=1e-2, maxit=50, max_active=4, precision=precision, seed=7)
+    loads = hi.uniform_loads([(o * n + 1) ** 2 for _, n, o in problems], seed=7)
+    for (k, n, order), F, (s, rho, cnt) in zip(problems, loads, out):
+        s_ref, rho_ref, cnt_ref = osolver.optimal_shift_exponent(k, n, order, F, tol=1e-2, maxit=50)
+        assert 1.0 <= s <= 2.0 and 0.0 < rho < 1.0
+        assert cnt == cnt_ref == 12
+        assert abs(s - s_ref) <= 2e-2, (k, s, s_ref)
+        assert abs(rho - rho_ref) <= 1e-3 * rho_ref, (k, rho, rho_ref)

@@ -202,3 +202,49 @@ def test_planewave_is_not_solution_with_flipped_boundary_sign():
     ui = fem.plane_wave(m.coords, 6.0, [math.cos(0.3), math.sin(0.3)])
     e = u - ui
     assert math.sqrt(abs(np.vdot(e, M @ e)) / abs(np.vdot(ui, M @ ui))) > 0.1
+
+
+# ---------------------------------------------------------------- Gaussian point source
+
+@pytest.mark.parametrize("dim,order,n,sigma,x0", [
+    (2, 1, 64, 0.06, (0.5, 0.5)),
+    (2, 1, 64, 0.05, (0.42, 0.57)),
+    (2, 2, 32, 0.05, (0.45, 0.52)),
+    (3, 1, 24, 0.08, (0.5, 0.47, 0.53)),
+])
+def test_gaussian_load_moments(dim, order, n, sigma, x0):
+    """F = M I_h f for f = exp(-|x - x0|^2 / (2 sigma^2)) (the benchmark's point source).
+
+    The basis sums to one, so sum_i F_i = int I_h f, which for a Gaussian well inside the
+    domain (tail e^{-(dist to the boundary)^2 / (2 sigma^2)} < 1e-8 here) is the closed form
+    (2 pi sigma^2)^{dim/2} up to the interpolation error. Its centroid sum x_i F_i / sum F_i
+    is x0 and its second moment sum |x_i - x0|^2 F_i / sum F_i is dim sigma^2 (the variance of
+    a normal distribution), both up to O(h^2) (the mass matrix spreads each nodal value over
+    neighbouring nodes). A sigma^2 for 2 sigma^2 mistake (factor 2 in the integral and the
+    moment) or a shifted centre fails these."""
+    mesh = fem.build_mesh(dim, order, n)
+    _, M, _ = fem.assemble(mesh)
+    F = fem.load_gaussian(mesh, M, sigma, center=np.array(x0))
+    assert np.allclose(F.imag, 0.0)
+    F = F.real
+    total = F.sum()
+    assert abs(total / (2 * math.pi * sigma ** 2) ** (dim / 2) - 1.0) <= 1e-3
+    x = mesh.coords
+    h = 1.0 / n
+    np.testing.assert_allclose((x * F[:, None]).sum(0) / total, x0, atol=h * h)
+    second = (np.sum((x - np.array(x0)) ** 2, axis=1) * F).sum() / total
+    assert abs(second / (dim * sigma ** 2) - 1.0) <= 4 * h * h / sigma ** 2
+
+
+def test_gaussian_load_centre_and_width_are_the_arguments():
+    """The default centre is the domain's centre, and the width enters as exp(-r^2 / (2 s^2))."""
+    mesh = fem.build_mesh(2, 1, 32)
+    _, M, _ = fem.assemble(mesh)
+    a = fem.load_gaussian(mesh, M, 0.07)
+    b = fem.load_gaussian(mesh, M, 0.07, center=np.array([0.5, 0.5]))
+    np.testing.assert_allclose(a, b, rtol=0, atol=0)
+    # f at a DoF r away from the centre relative to the centre's: e^{-r^2 / (2 sigma^2)}
+    f = np.linalg.solve(M.toarray(), a.real)
+    i0 = np.argmin(np.sum((mesh.coords - 0.5) ** 2, axis=1))
+    i1 = np.argmin(np.sum((mesh.coords - [0.5 + 3 / 32, 0.5]) ** 2, axis=1))
+    assert abs(f[i1] / f[i0] - math.exp(-(3 / 32) ** 2 / (2 * 0.07 ** 2))) <= 1e-12

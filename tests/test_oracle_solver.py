@@ -164,3 +164,75 @@ def test_shift_map_properties():
             assert min(s) >= 1.0 and max(s) <= 2.0
             assert all(b >= a - 1e-15 for a, b in zip(s, s[1:]))     # non-decreasing in k
         assert abs(shiftmap.shift(450.0, 10, w) - 450.0 ** shiftmap.sigma(450.0, 10, w)) < 1e-9
+
+
+# Values of eq. shiftexp worked out by hand from the columns of Table tab:optweights (Sec. 5):
+#   p = 1, l = 10: k_c = 2.5790033 e^{4.5927886} = 2.5790033 * (90.017131 * 1.0972292) = 254.7268
+#                  alpha = 1.7580550 e^{-6.2616373} = 1.7580550 * (2.478752e-3 * 0.769765) = 3.35458e-3
+#                  k = 450: beta = 2 - e^{-3.35458e-3 * 195.2732} = 2 - e^{-0.655058} = 1.480589
+#                  k = k_c + 1/alpha = 254.7268 + 298.1003 = 552.8271: beta = 2 - e^{-1} = 1.632121
+#   p = 2, l = 10: k_c = 2.5729975 e^{5.7369269} = 2.5729975 * (298.86740 * 1.0376171) = 797.912
+#                  alpha = 1.5966387 e^{-6.6151997} = 1.5966387 * (1.5034392e-3 * 0.8911834) = 2.13925e-3
+#                  k = 1100: beta = 2 - e^{-2.13925e-3 * 302.088} = 2 - e^{-0.646242} = 1.475989
+#   p = 1, l = 8:  k_c = 2.5790033 e^{3.6742309} = 2.5790033 * (36.598234 * 1.0770554) = 101.660
+#                  alpha = 1.7580550 e^{-5.0093098} = 1.7580550 * (6.737947e-3 * 0.990733) = 1.17359e-2
+#                  k = 150: beta = 2 - e^{-1.17359e-2 * 48.340} = 2 - e^{-0.567314} = 1.432954
+#   p = 1, l = 6:  k_c = 2.5790033 e^{2.7556732} = 2.5790033 * (14.879732 * 1.0572520) = 40.572 > k = 20:
+#                  beta < 1, clamped to 1
+# Swapping the two weights of k_c(l) or of alpha(l), or a sign, moves them.
+SHIFT_MAP_BY_HAND = [   # p, l, k, sigma
+    (1, 10, 450.0, 1.480589),
+    (1, 10, 552.8271, 1.632121),
+    (2, 10, 1100.0, 1.475989),
+    (1, 8, 150.0, 1.432954),
+    (1, 6, 20.0, 1.0),
+]
+
+
+@pytest.mark.parametrize("p,lvl,k,expected", SHIFT_MAP_BY_HAND)
+def test_shift_map_values_worked_by_hand(p, lvl, k, expected):
+    assert abs(shiftmap.sigma(k, lvl, shiftmap.PAPER_WEIGHTS[p]) - expected) <= 2e-6
+
+
+def test_shift_map_pins_catch_swapped_weights():
+    """Planted mistakes in the map's weights fail the hand-worked values above."""
+    kc0, kc1, a0, a1 = shiftmap.PAPER_WEIGHTS[1]
+
+    def off(w, lvl, k, s):
+        try:
+            return abs(shiftmap.sigma(k, lvl, w) - s) > 1e-3
+        except OverflowError:        # e^{-alpha (k - k_c)} beyond float range: not the value either
+            return True
+    for bad in ((kc0, kc1, a1, a0), (kc1, kc0, a0, a1), (kc0, kc1, -a0, a1), (-kc0, kc1, a0, a1)):
+        assert any(off(bad, lvl, k, s) for p, lvl, k, s in SHIFT_MAP_BY_HAND if p == 1)
+
+
+def test_golden_section_min_closed_forms():
+    """The oracle's golden-section search: minima of closed-form unimodal functions, inside the
+    final bracket, with the textbook evaluation count (2 + one per bracket reduction by the
+    golden ratio r: the bracket after j reductions is r^j of the start)."""
+    r = (math.sqrt(5) - 1) / 2
+    for x0, tol in ((1.37, 1e-2), (1.0, 1e-3), (1.9, 1e-4)):
+        x, fx, count = solver.golden_section_min(lambda s: (s - x0) ** 2, 1.0, 2.0, tol)
+        assert abs(x - x0) <= tol
+        assert count == 2 + math.ceil(math.log(tol) / math.log(r))
+    x, _, _ = solver.golden_section_min(lambda s: abs(math.sin(3 * s)), 0.5, 1.5, 1e-6)
+    assert abs(x - math.pi / 3) <= 1e-6
+
+
+def test_shift_rate_is_the_average_reduction():
+    """rho^iterations equals the true relative residual, and a capped solve has rho < 1."""
+    import helm_inputs as hi
+    F = hi.uniform_loads([33 * 33], seed=1)[0]
+    for sigma in (1.0, 1.6):
+        rho = solver.shift_rate(12.0, 32, 1, sigma, F, maxit=50)
+        assert 0.0 < rho < 1.0
+    rho_cap = solver.shift_rate(12.0, 32, 1, 2.0, F, maxit=5)
+    mesh = fem.build_mesh(2, 1, 32)
+    cm = fem.build_mesh(2, 1, 16)
+    K, M, B = fem.assemble(mesh)
+    Kc, Mc, Bc = fem.assemble(cm)
+    tg = solver.TwoGrid(fem.system_matrix(K, M, B, 12.0, 144.0), fem.system_matrix(Kc, Mc, Bc, 12.0, 144.0),
+                        fem.prolongation(cm, mesh))
+    ref = solver.fgmres(fem.system_matrix(K, M, B, 12.0, 0.0), F, tg.apply, restart=5, tol=1e-8, maxit=5)
+    assert ref.iters == 5 and abs(rho_cap ** 5 - ref.relres_true) <= 1e-12

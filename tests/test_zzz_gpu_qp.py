@@ -12,6 +12,7 @@ import pytest
 
 import helm_inputs as hi
 from oracle import qfem, solver as osolver
+from parity import assert_entrywise
 
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
@@ -62,7 +63,9 @@ def test_apply_q(wl):
     assert s.num_dofs == pb.mesh.num_dofs
     x = crand(pb.mesh.num_dofs, 7)
     for which, A in ((0, pb.A0), (1, pb.Aeps)):
-        assert rel(s.apply(dev(x), which).cpu().numpy(), A @ x) <= 1e-12
+        y = s.apply(dev(x), which).cpu().numpy()
+        assert rel(y, A @ x) <= 1e-12
+        assert_entrywise(y, A @ x, pb.mesh.coords, 1e-12, f"A{which} x")
     s.close()
 
 
@@ -72,9 +75,13 @@ def test_coarse_solve_and_vcycle_q(wl, prec, tol):
     pb = problem(wl)
     s = solver_q(wl, precision=prec)
     r = crand(pb.cmesh.num_dofs, 11)
-    assert rel(s.coarse_solve(dev(r)).cpu().numpy(), pb.twogrid().coarse_solve(r)) <= tol
+    uc, ucr = s.coarse_solve(dev(r)).cpu().numpy(), pb.twogrid().coarse_solve(r)
+    assert rel(uc, ucr) <= tol
+    assert_entrywise(uc, ucr, pb.cmesh.coords, tol, "coarse solve")
     f = crand(pb.mesh.num_dofs, 13)
-    assert rel(s.vcycle(dev(f)).cpu().numpy(), pb.twogrid().apply(f)) <= tol
+    u, ur = s.vcycle(dev(f)).cpu().numpy(), pb.twogrid().apply(f)
+    assert rel(u, ur) <= tol
+    assert_entrywise(u, ur, pb.mesh.coords, tol, "V-cycle")
     s.close()
 
 
@@ -92,6 +99,7 @@ def test_solve_parity_q(wl, prec):
     slack = 1 if prec == pkg.HELM_FP64 else 3
     assert abs(res.iters - ref.iters) <= slack, (res.iters, ref.iters)
     assert rel(xh, ref.x) <= 1e-5
+    assert_entrywise(xh, ref.x, pb.mesh.coords, 1e-5, "solution")
     s.close()
 
 
