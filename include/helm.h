@@ -136,6 +136,19 @@ int helm_num_coarse_dofs(helm_t h, int64_t* n);
 int helm_setup_info(helm_t h, float* ms, int* kernels);
 
 /*
+ * Coarse factorisation (Sec. 6: the coarse LU is computed once per (k, h, shift) and reused
+ * by every iteration) as block elimination along two chains of coarse blocks. The interior
+ * blocks of the coarse operator are all alike, so each chain's Schur complement follows one
+ * recurrence; where it has converged (the relative change of the block inverse stays below
+ * 1e-9 for the complex64 form's double-float factor, 1e-11 for the FP64 form, two steps in a
+ * row) the remaining blocks of that chain take the converged inverse instead of being
+ * factored. This happens for large shifts (e.g. eps = k^2 / 2) and not for small ones.
+ * Reports how many of the nb coarse blocks were factored and how many reused (either
+ * pointer may be NULL). HELM_EINVAL for an operator-only handle.
+ */
+int helm_factor_info(helm_t h, int* factored, int* reused);
+
+/*
  * Solve A0 x = F (Sec. 4: FGMRES right-preconditioned by the twogrid
  * V-cycle on A_eps). F, x: device complex128[N], caller-owned; x is
  * overwritten (x0 = 0 is used, any input content is ignored).

@@ -29,6 +29,7 @@ EXPORTS = [
     "helm_server_wait", "helm_server_drain", "helm_server_destroy", "helm_load_planewave", "helm_load_gaussian",
     "helm_operator_setup", "helm_smooth", "helm_host_stencil_row", "helm_host_prolongation_row",
     "helm_setup_q", "helm_load_planewave_e", "helm_load_gaussian_e", "helm_host_het_row",
+    "helm_factor_info",
 ]
 
 
@@ -77,6 +78,7 @@ def load(path: str = LIB_PATH):
     lib.helm_num_dofs.argtypes = [vp, i64p]
     lib.helm_num_coarse_dofs.argtypes = [vp, i64p]
     lib.helm_setup_info.argtypes = [vp, ctypes.POINTER(ctypes.c_float), ctypes.POINTER(ctypes.c_int)]
+    lib.helm_factor_info.argtypes = [vp, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int)]
     lib.helm_solve.argtypes = [vp, vp, vp, ctypes.POINTER(HelmResult)]
     lib.helm_solve_host.argtypes = [vp, vp, vp, ctypes.POINTER(HelmResult)]
     lib.helm_batch_solve.argtypes = [i, ctypes.POINTER(vp), ctypes.POINTER(vp), ctypes.POINTER(vp),
@@ -197,6 +199,11 @@ class Solver:
         _check(lib.helm_setup_info(self._h, ctypes.byref(ms), ctypes.byref(nk)))
         self.setup_ms = ms.value
         self.setup_kernels = nk.value
+        self.factored_blocks = self.reused_blocks = 0
+        if not operator_only:
+            nf, nr = ctypes.c_int(), ctypes.c_int()
+            _check(lib.helm_factor_info(self._h, ctypes.byref(nf), ctypes.byref(nr)))
+            self.factored_blocks, self.reused_blocks = nf.value, nr.value
 
     @property
     def handle(self):

@@ -78,6 +78,7 @@ struct helm_ctx {
   cudaEvent_t e0 = nullptr, e1 = nullptr;
   float setup_ms = 0.f;
   int setup_kernels = 0;
+  int reused_blocks = 0;       // coarse blocks whose inverse was copied from a converged chain
   int iter_nodes = 0;          // kernel nodes in the captured iteration graph
   Profile prof;
   std::vector<void*> allocs;
@@ -674,12 +675,15 @@ static int setup_impl(helm_ctx* h) {
   struct FactorScratch {
     double2 *D64 = nullptr, *tmp = nullptr, *piv = nullptr;
     unsigned* bar = nullptr;
+    int* reuse = nullptr;
     void free_work() {
       cudaFree(tmp);
       cudaFree(piv);
       cudaFree(bar);
+      cudaFree(reuse);
       tmp = piv = nullptr;
       bar = nullptr;
+      reuse = nullptr;
     }
     ~FactorScratch() {
       free_work();
@@ -694,13 +698,14 @@ static int setup_impl(helm_ctx* h) {
   CK(cudaMalloc(&tmp, sizeof(double2) * 2 * blk));
   CK(cudaMalloc(&piv, sizeof(double2) * 2 * factor_workspace(L)));
   CK(cudaMalloc(&bar, 2 * kBarWords * sizeof(unsigned)));
+  CK(cudaMalloc(&fs.reuse, kReuseStateInts * sizeof(int)));
   CK(h->alloc(&h->err, sizeof(int)));
   CK(cudaMemsetAsync(h->err, 0, sizeof(int), s));
   CK(cudaEventRecord(h->e0, s));
   StencilView<double> Acv = make_view<double>(h->gc, h->p64.coefAc, nullptr);
   rc = df ? coarse_factor_df(reinterpret_cast<float4*>(D64), reinterpret_cast<float4*>(tmp),
-                             reinterpret_cast<float4*>(piv), bar, h->err, Acv, L, h->nsm, s)
-          : coarse_factor_fp64(D64, tmp, piv, bar, h->err, Acv, L, h->nsm, s);
+                             reinterpret_cast<float4*>(piv), bar, h->err, Acv, L, h->nsm, s, fs.reuse)
+          : coarse_factor_fp64(D64, tmp, piv, bar, h->err, Acv, L, h->nsm, s, fs.reuse);
   h->setup_kernels = std::max(L.mid, L.nb - 1 - L.mid) + 1 + 1 + (o.precision == HELM_MIXED ? 1 : 0);
   // couplings folded into the inverses: Lm[J] = Dinv[J] A_J,J-1, Up[J] = Dinv[J] A_J,J+1
   if (rc == HELM_OK && o.precision == HELM_MIXED) {
@@ -737,6 +742,11 @@ static int setup_impl(helm_ctx* h) {
   cudaEventRecord(h->e1, s);
   cudaEventSynchronize(h->e1);
   cudaEventElapsedTime(&h->setup_ms, h->e0, h->e1);
+  if (rc == HELM_OK) {
+    int st[kReuseStateInts];
+    if (cudaMemcpy(st, fs.reuse, sizeof(st), cudaMemcpyDeviceToHost) == cudaSuccess)
+      h->reused_blocks = coarse_reused_blocks(st, L);
+  }
   fs.free_work();
   if (rc == HELM_OK) {
     cudaError_t le = cudaGetLastError();
@@ -859,6 +869,13 @@ int helm_num_dofs(helm_t h, int64_t* n) {
 int helm_num_coarse_dofs(helm_t h, int64_t* n) {
   if (!h || !n) return HELM_EINVAL;
   *n = h->gc.N;
+  return HELM_OK;
+}
+
+int helm_factor_info(helm_t h, int* factored, int* reused) {
+  if (!h || h->op_only) return HELM_EINVAL;
+  if (factored) *factored = h->L.nb - h->reused_blocks;
+  if (reused) *reused = h->reused_blocks;
   return HELM_OK;
 }
 

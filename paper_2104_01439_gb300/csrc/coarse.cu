@@ -291,7 +291,26 @@ struct FactorJob {
   int J;
   int ndir;
   int dir[2];
+  int chain;   // 0: top chain, 1: bottom chain, -1: the middle block (always factored)
 };
+
+// Reuse of converged Schur inverses. Interior blocks of the coarse operator are all the same,
+// so along a chain S_J = A_JJ - A_J,J-1 S_{J-1}^{-1} A_J-1,J iterates one fixed map; for large
+// shifts it contracts and the inverse stops changing. Per chain (kReuseWords ints):
+//   [0] frozen: later blocks of the chain copy the last inverse instead of factoring
+//   [1] consecutive steps whose relative change max|D[J] - D[J-1]| / max|D[J]| was <= tol
+//   [2] max |D[J] - D[J-1]| of the current step (float bits, non-negative)
+//   [3] max |D[J]| (float bits)      [4] CTAs of the delta kernel that finished
+//   [5] block at which the chain froze (-1: never)
+constexpr int kReuseWords = 8;
+constexpr int kReuseSteps = 2;   // steps in a row below the tolerance before a chain freezes
+// Tolerances on the relative change: the frozen inverses then differ from the ones a full
+// factorisation would give by about the last change times q / (1 - q), q the contraction rate
+// of the recurrence (< 1 where it freezes). Double-float (complex64 solve): far below complex64
+// rounding (6e-8). FP64 form: far below the FP64 solve's accuracy (the Schur blocks' condition
+// numbers times 1e-16).
+constexpr float kReuseTolDf = 1e-9f;
+constexpr float kReuseTolFp64 = 1e-11f;
 
 // one CTA per SM; 32 warps hide the latency of the dependent double-float chains. Warps
 // 0-7 form and invert the next panel's pivot block while warps 8-31 update the matrix.
@@ -303,16 +322,11 @@ template <typename A>
 __global__ void __launch_bounds__(kFactorThreads, 1) k_factor_block(typename A::V* D, typename A::V* Tmp, typename A::V* piv,
                                                       unsigned* bar, int* err, StencilView<double> Ac,
                                                       CoarseLayout L, FactorJob job0, FactorJob job1,
-                                                      int njobs, int stageR) {
+                                                      int njobs, int stageR, const int* reuse) {
   using V = typename A::V;
   constexpr int P = A::P;
   extern __shared__ __align__(128) unsigned char sm[];
   const GridDesc g = Ac.g;
-  int ncls = 1;
-  for (int ax = 0; ax < g.dim; ++ax) ncls *= g.C1;
-  V* coef = reinterpret_cast<V*>(sm);
-  for (int i = threadIdx.x; i < ncls * g.noff; i += blockDim.x) coef[i] = A::from(Ac.coef[i]);
-  __syncthreads();
   const int B = L.B, ldb = L.ldb;
   const int64_t blk = (int64_t)B * ldb;
   // two independent jobs (top and bottom chain) share the grid: each half has its
@@ -323,11 +337,24 @@ __global__ void __launch_bounds__(kFactorThreads, 1) k_factor_block(typename A::
   const int lb = (int)blockIdx.x - (grp ? half : 0);
   const FactorJob job = grp ? job1 : job0;
   const int J = job.J;
+  const int gt = lb * blockDim.x + threadIdx.x, gs = G * blockDim.x;
+  if (reuse && job.chain >= 0 && *(volatile const int*)(reuse + job.chain * kReuseWords) != 0) {
+    // converged chain (set by k_factor_delta before this launch; every CTA of the half reads
+    // the same flag): Dinv[J] = Dinv[J + dir], no Schur update, no barrier
+    const V* src = D + (int64_t)(J + job.dir[0]) * blk;
+    V* dst = D + (int64_t)J * blk;
+    for (int64_t idx = gt; idx < blk; idx += gs) dst[idx] = src[idx];
+    return;
+  }
+  int ncls = 1;
+  for (int ax = 0; ax < g.dim; ++ax) ncls *= g.C1;
+  V* coef = reinterpret_cast<V*>(sm);
+  for (int i = threadIdx.x; i < ncls * g.noff; i += blockDim.x) coef[i] = A::from(Ac.coef[i]);
+  __syncthreads();
   Tmp += grp * blk;
   piv += grp * (int64_t)factor_workspace(L);
   bar += kBarWords * grp;
   V* S = D + J * blk;
-  const int gt = lb * blockDim.x + threadIdx.x, gs = G * blockDim.x;
   const V zero = A::zero();
 
   // Tmp[a][l] = sum_{o: l+o in block J+d} A[l][l+o] Dinv[J+d][a][l+o]   (= Dinv[J+d] A_{J+d,J})
@@ -579,6 +606,71 @@ __global__ void __launch_bounds__(kFactorThreads, 1) k_factor_block(typename A::
     V* tpm = Pm;   // the next panel's inverse becomes current
     Pm = Pn;
     Pn = tpm;
+  }
+}
+
+// Relative change of the inverse along each chain after a block step (see kReuseWords):
+// blockIdx.y = chain, Jc[c] = the block just factored (-1: none). The last CTA of a chain
+// updates the chain's count of steps below tol and freezes it after kReuseSteps of them.
+__device__ __forceinline__ float entry_diff(double2 a, double2 b) {
+  return (float)fmax(fabs(a.x - b.x), fabs(a.y - b.y));
+}
+__device__ __forceinline__ float entry_abs(double2 a) { return (float)fmax(fabs(a.x), fabs(a.y)); }
+__device__ __forceinline__ float entry_diff(float4 a, float4 b) {   // double-float: hi + lo parts
+  return fmaxf(fabsf((a.x - b.x) + (a.z - b.z)), fabsf((a.y - b.y) + (a.w - b.w)));
+}
+__device__ __forceinline__ float entry_abs(float4 a) { return fmaxf(fabsf(a.x), fabsf(a.y)); }
+
+template <typename V>
+__global__ void __launch_bounds__(256) k_factor_delta(const V* __restrict__ D, CoarseLayout L, int J0, int J1,
+                                                      int d0, int d1, float tol, int* reuse) {
+  const int c = blockIdx.y;
+  const int J = c == 0 ? J0 : J1, dir = c == 0 ? d0 : d1;
+  int* st = reuse + c * kReuseWords;
+  if (J < 0 || *(volatile int*)st != 0) return;   // no step on this chain, or already frozen
+  const int64_t blk = (int64_t)L.B * L.ldb;
+  const V* a = D + (int64_t)J * blk;
+  const V* b = D + (int64_t)(J + dir) * blk;
+  float dm = 0.f, am = 0.f;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < blk; i += (int64_t)gridDim.x * blockDim.x) {
+    const V x = a[i];
+    dm = fmaxf(dm, entry_diff(x, b[i]));
+    am = fmaxf(am, entry_abs(x));
+  }
+  for (int o = 16; o > 0; o >>= 1) {
+    dm = fmaxf(dm, __shfl_xor_sync(0xffffffffu, dm, o));
+    am = fmaxf(am, __shfl_xor_sync(0xffffffffu, am, o));
+  }
+  __shared__ float sd[8], sa[8];
+  __shared__ int last;
+  if ((threadIdx.x & 31) == 0) {
+    sd[threadIdx.x >> 5] = dm;
+    sa[threadIdx.x >> 5] = am;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    for (int w = 1; w < (int)(blockDim.x >> 5); ++w) {
+      dm = fmaxf(dm, sd[w]);
+      am = fmaxf(am, sa[w]);
+    }
+    // non-negative floats order like their bit patterns (a NaN orders above all of them)
+    atomicMax(reinterpret_cast<unsigned*>(st + 2), __float_as_uint(dm));
+    atomicMax(reinterpret_cast<unsigned*>(st + 3), __float_as_uint(am));
+    __threadfence();
+    last = atomicAdd(st + 4, 1) == (int)gridDim.x - 1;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0 && last) {
+    __threadfence();
+    const float dmax = __uint_as_float(atomicExch(reinterpret_cast<unsigned*>(st + 2), 0u));
+    const float amax = __uint_as_float(atomicExch(reinterpret_cast<unsigned*>(st + 3), 0u));
+    st[4] = 0;
+    const bool small = amax > 0.f && dmax <= tol * amax;   // (false for NaN)
+    st[1] = small ? st[1] + 1 : 0;
+    if (st[1] >= kReuseSteps) {
+      st[5] = J;
+      st[0] = 1;
+    }
   }
 }
 
@@ -1647,7 +1739,8 @@ void launch_couple(const typename A::V* D, TO* Lm, TO* Up, const StencilView<dou
 
 template <typename A>
 int launch_factor(typename A::V* Dinv, typename A::V* tmp, typename A::V* piv, unsigned* bar, int* err,
-                  const StencilView<double>& Ac, const CoarseLayout& L, int nsm, cudaStream_t s) {
+                  const StencilView<double>& Ac, const CoarseLayout& L, int nsm, cudaStream_t s, int* reuse,
+                  float reuse_tol) {
   using V = typename A::V;
   constexpr int P = A::P;
   int ncls = 1;
@@ -1673,20 +1766,29 @@ int launch_factor(typename A::V* Dinv, typename A::V* tmp, typename A::V* piv, u
     cudaMemsetAsync(bar, 0, 2 * kBarWords * sizeof(unsigned), s);
     StencilView<double> acv = Ac;
     CoarseLayout lv = L;
-    void* args[] = {&Dinv, &tmp, &piv, &bar, &err, &acv, &lv, &j0, &j1, &njobs, &stageR};
+    const int* rz = reuse;
+    void* args[] = {&Dinv, &tmp, &piv, &bar, &err, &acv, &lv, &j0, &j1, &njobs, &stageR, &rz};
     cudaError_t e = cudaLaunchCooperativeKernel((void*)k_factor_block<A>, dim3(nblk), dim3(kFactorThreads), args, smem, s);
     return e == cudaSuccess ? HELM_OK : HELM_ECUDA;
   };
+  if (reuse) cudaMemsetAsync(reuse, 0, 2 * kReuseWords * sizeof(int), s);
   for (int t = 0; t < std::max(nf_top, nf_bot); ++t) {
-    FactorJob top{t, t > 0 ? 1 : 0, {-1, 0}};
-    FactorJob bot{L.nb - 1 - t, t > 0 ? 1 : 0, {+1, 0}};
+    FactorJob top{t, t > 0 ? 1 : 0, {-1, 0}, 0};
+    FactorJob bot{L.nb - 1 - t, t > 0 ? 1 : 0, {+1, 0}, 1};
     int rc;
     if (t < nf_top && t < nf_bot) rc = launch(top, bot, 2);
     else if (t < nf_top) rc = launch(top, top, 1);
     else rc = launch(bot, bot, 1);
     if (rc) return rc;
+    // blocks 0 and nb-1 carry the boundary; the interior recurrence starts at block 1 / nb-2,
+    // so the change is measured from the second interior block on
+    if (reuse && t >= 2) {
+      const int jt = t < nf_top ? t : -1, jb = t < nf_bot ? L.nb - 1 - t : -1;
+      k_factor_delta<typename A::V><<<dim3(std::max(1, nsm / 2), 2), 256, 0, s>>>(Dinv, L, jt, jb, -1, +1,
+                                                                                  reuse_tol, reuse);
+    }
   }
-  FactorJob mid{m, 0, {0, 0}};
+  FactorJob mid{m, 0, {0, 0}, -1};
   if (m > 0) mid.dir[mid.ndir++] = -1;
   if (m < L.nb - 1) mid.dir[mid.ndir++] = +1;
   return launch(mid, mid, 1);
@@ -1694,12 +1796,20 @@ int launch_factor(typename A::V* Dinv, typename A::V* tmp, typename A::V* piv, u
 }  // namespace
 
 int coarse_factor_fp64(double2* Dinv, double2* tmp, double2* piv, unsigned* bar, int* err,
-                       const StencilView<double>& Ac, const CoarseLayout& L, int nsm, cudaStream_t s) {
-  return launch_factor<ArithD>(Dinv, tmp, piv, bar, err, Ac, L, nsm, s);
+                       const StencilView<double>& Ac, const CoarseLayout& L, int nsm, cudaStream_t s, int* reuse) {
+  return launch_factor<ArithD>(Dinv, tmp, piv, bar, err, Ac, L, nsm, s, reuse, kReuseTolFp64);
 }
 int coarse_factor_df(float4* Dinv, float4* tmp, float4* piv, unsigned* bar, int* err,
-                     const StencilView<double>& Ac, const CoarseLayout& L, int nsm, cudaStream_t s) {
-  return launch_factor<ArithDF>(Dinv, tmp, piv, bar, err, Ac, L, nsm, s);
+                     const StencilView<double>& Ac, const CoarseLayout& L, int nsm, cudaStream_t s, int* reuse) {
+  return launch_factor<ArithDF>(Dinv, tmp, piv, bar, err, Ac, L, nsm, s, reuse, kReuseTolDf);
+}
+int coarse_reused_blocks(const int* reuse_host, const CoarseLayout& L) {
+  const int m = L.mid;
+  int n = 0;
+  if (reuse_host[0] && reuse_host[5] >= 0) n += std::max(0, m - 1 - reuse_host[5]);                   // top: J .. m-1
+  if (reuse_host[kReuseWords] && reuse_host[kReuseWords + 5] >= 0)
+    n += std::max(0, reuse_host[kReuseWords + 5] - (m + 1));                                           // bottom: m+1 .. J
+  return n;
 }
 void coarse_couple_fp64(const double2* D, double2* Lm, double2* Up, const StencilView<double>& Ac,
                         const CoarseLayout& L, int nsm, cudaStream_t s) {

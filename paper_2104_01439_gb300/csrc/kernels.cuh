@@ -105,10 +105,16 @@ int coarse_seg_launches(const CoarseLayout& L, const CoarsePlan& plan);
 __host__ __device__ inline size_t factor_workspace(const CoarseLayout& L) {
   return 2 * 16 * (size_t)L.ldb + 2 * 16 * (size_t)L.B + 2 * 16 * 16;
 }
+// reuse (may be null): 2 x 8 ints of device state; when given, a chain whose inverse stopped
+// changing (relative change below the precision's tolerance twice in a row) copies it to the
+// rest of the chain instead of factoring; coarse_reused_blocks counts the copied blocks from a
+// host copy of that state.
 int coarse_factor_fp64(double2* Dinv, double2* tmp, double2* piv, unsigned* bar, int* err,
-                       const StencilView<double>& Ac, const CoarseLayout& L, int nsm, cudaStream_t s);
+                       const StencilView<double>& Ac, const CoarseLayout& L, int nsm, cudaStream_t s, int* reuse);
 int coarse_factor_df(float4* Dinv, float4* tmp, float4* piv, unsigned* bar, int* err,
-                     const StencilView<double>& Ac, const CoarseLayout& L, int nsm, cudaStream_t s);
+                     const StencilView<double>& Ac, const CoarseLayout& L, int nsm, cudaStream_t s, int* reuse);
+constexpr int kReuseStateInts = 16;
+int coarse_reused_blocks(const int* reuse_host, const CoarseLayout& L);
 // Lm[J] = Dinv[J] A_J,J-1 and Up[J] = Dinv[J] A_J,J+1 from the inverses (nb x B x ldb each)
 void coarse_couple_fp64(const double2* D, double2* Lm, double2* Up, const StencilView<double>& Ac,
                         const CoarseLayout& L, int nsm, cudaStream_t s);

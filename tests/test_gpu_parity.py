@@ -172,3 +172,44 @@ def test_batch_and_host_solves_match_single(prec):
         assert rel(xh.numpy(), x1.cpu().numpy()) <= 1e-12
     for s in solvers:
         s.close()
+
+
+_COARSE = {}
+
+
+def coarse_direct(n, k, shift):
+    """The oracle's assembled coarse matrix (2h mesh) and its sparse direct factorisation."""
+    key = (n, k, shift)
+    if key not in _COARSE:
+        import scipy.sparse.linalg as spla
+        cm = fem.build_mesh(2, 1, n // 2)
+        Kc, Mc, Bc = fem.assemble(cm)
+        _COARSE[key] = (cm, spla.splu(fem.system_matrix(Kc, Mc, Bc, k, shift).tocsc()))
+    return _COARSE[key]
+
+
+@pytest.mark.parametrize("prec,tol", [(pkg.HELM_FP64, 1e-9), (pkg.HELM_MIXED, 2e-5)], ids=["fp64", "mixed"])
+@pytest.mark.parametrize("n,k,expo", [(64, 20.0, 2.0), (64, 20.0, 1.0), (64, 20.0, 1.5),
+                                      (512, 200.0, 2.0), (512, 200.0, 1.0), (512, 200.0, 1.5)],
+                         ids=lambda v: str(v))
+def test_factor_reuse_coarse_solve(n, k, expo, prec, tol):
+    """Coarse factorisation with the reuse of converged Schur inverses (Sec. 6's factor-once
+    LU, computed along two block chains): for eps = k^2 / 2 the chains converge and later blocks
+    reuse the converged inverse; for eps = k and k^1.5 they do not, and every block is factored.
+    Either way the coarse solve matches the oracle's sparse direct solve of its own coarse
+    matrix, normwise and entry by entry."""
+    shift = 0.5 * k * k if expo == 2.0 else k ** expo
+    s = pkg.Solver(k, n, 1, shift, precision=prec)
+    cm, lu = coarse_direct(n, k, shift)
+    r = crand(cm.num_dofs, 19)
+    uc = s.coarse_solve(dev(r)).cpu().numpy()
+    ref = lu.solve(r)
+    assert rel(uc, ref) <= tol
+    assert_entrywise(uc, ref, cm.coords, tol, "coarse solve")
+    nb = n // 2 + 1
+    assert s.factored_blocks + s.reused_blocks == nb
+    if n == 512 and expo == 2.0:
+        assert s.reused_blocks >= nb // 3, s.reused_blocks     # the chains converge (large shift)
+    if expo == 1.0:
+        assert s.reused_blocks == 0                            # no convergence: all factored
+    s.close()
