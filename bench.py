@@ -217,68 +217,101 @@ def replica_rate(units_per_rank, seconds, dist, device):
 
 # ---------------------------------------------------------------------------- CPU oracle leg
 
-def _oracle_sample(n_iters, q):
-    """Bounded sample of the oracle on this workload (runs in a spawned process)."""
-    os.environ.setdefault("OMP_NUM_THREADS", "1")
+_ONE_THREAD = {k: "1" for k in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS")}
+
+
+def _oracle_full_solve(want_x):
+    """One full oracle solve of the workload (assembly, sparse LU of the coarse matrix, FGMRES
+    to relres 1e-8: every iteration, nothing extrapolated), in a spawned worker process."""
     sys.path.insert(0, ROOT)
     from oracle import solver
     t0 = time.perf_counter()
     pb = solver.build_problem(WL)
-    tg = pb.twogrid()
+    r = pb.solve()
     t1 = time.perf_counter()
-    r = solver.fgmres(pb.A0, pb.F, tg.apply, WL.restart, WL.tol, n_iters)
-    t2 = time.perf_counter()
-    q.put({"setup_s": t1 - t0, "iter_s": (t2 - t1) / max(r.iters, 1), "iters": r.iters})
+    return {"seconds": t1 - t0, "iters": r.iters, "relres": r.relres_true, "x": r.x if want_x else None}
 
 
-def oracle_baseline(n_iters=30):
-    """Oracle setup + n_iters FGMRES iterations, extrapolated to a full solve with the
-    oracle's own iteration count (tests/golden/oracle_iterations.json)."""
-    env_threads = {k: "1" for k in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS")}
-    old = {k: os.environ.get(k) for k in env_threads}
-    os.environ.update(env_threads)
+def host_info():
+    """Host cores and CPU model (lscpu when present)."""
+    ncpu = len(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity") else os.cpu_count()
+    model = None
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.split(":")[0].strip() in ("Model name", "Vendor ID") and ":" in line:
+                model = (model + " / " if model else "") + line.split(":", 1)[1].strip()
+    except Exception:
+        pass
+    import platform
+    return ncpu, model or platform.processor() or platform.machine()
+
+
+def oracle_pool_run(n_solves, procs, warm=0, want_x=False):
+    """n_solves full oracle solves on `procs` single-threaded processes (spawned; a process
+    pool forked after GPU work could hang). Returns the wall time of the n_solves (after `warm`
+    untimed ones on the same pool) and each solve's own record."""
+    old = {k: os.environ.get(k) for k in _ONE_THREAD}
+    os.environ.update(_ONE_THREAD)
     try:
         ctx = mp.get_context("spawn")
-        q = ctx.Queue()
-        p = ctx.Process(target=_oracle_sample, args=(n_iters, q))
-        p.start()
-        res = q.get(timeout=900)
-        p.join(timeout=60)
+        with ctx.Pool(procs) as pool:
+            if warm:
+                pool.map(_oracle_full_solve, [False] * warm, chunksize=1)
+            t0 = time.perf_counter()
+            recs = pool.map(_oracle_full_solve, [want_x and i == 0 for i in range(n_solves)], chunksize=1)
+            wall = time.perf_counter() - t0
     finally:
         for k, v in old.items():
             if v is None:
                 os.environ.pop(k, None)
             else:
                 os.environ[k] = v
-    with open(GOLDEN) as f:
-        full_iters = json.load(f)[WL.name]["iters"]
-    t_full = res["setup_s"] + res["iter_s"] * full_iters
-    return {
-        "value": 1.0 / t_full, "unit": "solves/s", "cores": 1, "kind": "oracle",
-        "sample": f"oracle (numpy/scipy, 1 thread) assembly + sparse LU setup ({res['setup_s']:.1f} s) "
-                  f"and the first {res['iters']} FGMRES iterations ({res['iter_s'] * 1e3:.0f} ms each), "
-                  f"extrapolated to the oracle's full {full_iters} iterations",
-        "seconds_per_solve": t_full,
+    return wall, recs
+
+
+def oracle_baseline(want_x=False):
+    """The oracle timed on the host cores: one full solve per process, one process per core
+    (at most 16), all at once. value = solves / wall time; the one-core rate is 1 / the
+    median solve's own time."""
+    ncpu, model = host_info()
+    procs = max(1, min(16, ncpu))
+    wall, recs = oracle_pool_run(procs, procs, want_x=want_x)
+    per = statistics.median(r["seconds"] for r in recs)
+    out = {
+        "value": len(recs) / wall, "unit": "solves/s", "cores": procs, "kind": "oracle",
+        "sample": f"{len(recs)} full oracle solves of this workload at once (numpy/scipy, one thread each: "
+                  f"assembly, sparse LU, all {recs[0]['iters']} FGMRES iterations; nothing extrapolated), "
+                  f"{wall:.1f} s wall",
+        "single_core": {"value": 1.0 / per, "unit": "solves/s", "seconds_per_solve": per},
+        "nproc": ncpu, "cpu_model": model,
+        "iters": recs[0]["iters"], "relres_true": recs[0]["relres"],
     }
+    return out, recs[0]["x"]
 
 
 def run_reference(args):
     world, rank, local, dist = dist_setup()
     if rank != 0:
         return
-    samples = []
-    for i in range(args.warmup + args.steps):
-        b = oracle_baseline(n_iters=20)
-        if i >= args.warmup:
-            samples.append(b)
-    v = statistics.mean(s["value"] for s in samples)
+    ncpu, model = host_info()
+    procs = max(1, min(16, ncpu, max(args.steps, args.warmup)))
+    wall, recs = oracle_pool_run(args.steps, procs, warm=args.warmup)
+    v = len(recs) / wall
+    per = statistics.median(r["seconds"] for r in recs)
+    cpu = {"value": v, "unit": "solves/s", "cores": min(procs, len(recs)), "kind": "oracle",
+           "sample": f"{len(recs)} full oracle solves (numpy/scipy, one thread each, {procs} processes: assembly, "
+                     f"sparse LU, all {recs[0]['iters']} FGMRES iterations; nothing extrapolated) after "
+                     f"{args.warmup} untimed ones",
+           "single_core": {"value": 1.0 / per, "unit": "solves/s", "seconds_per_solve": per},
+           "nproc": ncpu, "cpu_model": model}
     line = {
         "impl": "reference", "metric": METRIC, "value": v, "unit": "solves/s", "n_gpus": args.gpus,
-        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 / v, "higher_is_better": True,
-        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * wall / len(recs),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
         "config": workload_config("FP64 oracle (CPU)"),
-        "cpu_baseline": {"value": v, "unit": "solves/s", "cores": 1, "kind": "oracle",
-                         "sample": samples[-1]["sample"]},
+        "iters": recs[0]["iters"], "relres_true": recs[0]["relres"],
+        "cpu_baseline": cpu,
         "e2e": {"value": v, "unit": "solves/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
@@ -359,14 +392,18 @@ def run_ours(args):
         flush.fill_(1.0)
         _, r = s.solve(F, x)
         solve_ms.append(r.solve_ms)
+    x_mixed = x.cpu().numpy()
     s.set_profiling(True)
     _, rp = s.solve(F, x)
     prof = s.profile()
     s.set_profiling(False)
+    reuse_mixed = (s.factored_blocks, s.reused_blocks)
     s.close()
     s64 = make(pkg.HELM_FP64)
     setup_ms_fp64 = s64.setup_ms
     _, r64 = s64.solve(F, x)
+    x_fp64 = x.cpu().numpy()
+    reuse_fp64 = (s64.factored_blocks, s64.reused_blocks)
     s64.close()
 
     if rank != 0:
@@ -401,10 +438,31 @@ def run_ours(args):
         "above_l2": stencil_large,
     }
 
-    cpu = None
+    cpu, x_orc = None, None
     if not args.no_cpu_baseline and world == 1:
-        cpu = oracle_baseline(n_iters=30)
-        cpu.pop("seconds_per_solve", None)
+        cpu, x_orc = oracle_baseline(want_x=True)
+
+    def accuracy(xg, r):
+        """This result against the FP64 oracle's solution of the same problem (Sec. 4 FGMRES)."""
+        out = {"iters": r.iters, "relres_true": r.relres_true, "relres_givens": r.relres_est,
+               # |Givens estimate - true residual| at the last cycle's end: zero when the Arnoldi
+               # relation A0 Z = V Hbar holds with an orthonormal V, so it measures both at once
+               "residual_gap": abs(r.relres_est - r.relres_true) / r.relres_true if r.relres_true else None}
+        if x_orc is not None:
+            import numpy as np
+            out["x_rel_err_vs_oracle"] = float(np.linalg.norm(xg - x_orc) / np.linalg.norm(x_orc))
+            out["iters_minus_oracle"] = r.iters - cpu["iters"]
+        return out
+
+    legs = {}
+    if world == 1 and not args.no_legs:
+        with ClockSampler(local) as ck:
+            legs["sweep"] = sweep_leg(pkg, args.pairs, args.max_n, args.fp64_samples, args.max_active)
+        legs["sweep"]["clocks"] = ck.summary()
+        with ClockSampler(local) as ck:
+            legs["serve"] = serve_leg(pkg, args.requests, args.rate, tuple(int(g) for g in args.grids.split(",")),
+                                      args.max_active)
+        legs["serve"]["clocks"] = ck.summary()
 
     lat = sorted(t * 1e3 for t in t_mixed)
     p99 = lat[min(len(lat) - 1, math.ceil(0.99 * len(lat)) - 1)]
@@ -433,6 +491,11 @@ def run_ours(args):
         "fp64": {"value": world * len(t_fp64) / fp64_total, "unit": "solves/s", "iters": r64.iters,
                  "relres_true": r64.relres_true, "setup_ms": setup_ms_fp64, "solve_ms": r64.solve_ms,
                  "mixed_speedup": value / (world * len(t_fp64) / fp64_total)},
+        "accuracy": {"mixed": accuracy(x_mixed, r), "fp64": accuracy(x_fp64, r64),
+                     "note": "complex64 V-cycle with double-float (~48-bit) Arnoldi basis and coarse factor "
+                             "(mixed); complex128 throughout except the double-float Gram-Schmidt (fp64)"},
+        "coarse_factor": {"mixed": {"factored_blocks": reuse_mixed[0], "reused_blocks": reuse_mixed[1]},
+                          "fp64": {"factored_blocks": reuse_fp64[0], "reused_blocks": reuse_fp64[1]}},
         "phase_ms_per_iteration": phase_ms,
         "stencil": stencil,
         "roofline": {"kernel": "coarse solve phase: k_block_gemv + 4 k_seg_chain + 2 k_seg_fixup + k_seg_middle ("
@@ -446,6 +509,7 @@ def run_ours(args):
         "gpu_launches": kern_mixed,
         "clocks": clocks,
     }
+    line.update(legs)
     print(json.dumps(line), flush=True)
 
 
@@ -454,32 +518,28 @@ def _host_load(req, pkg, seed):
     return torch.from_numpy(hi.random_load(pkg.num_dofs(req), seed))
 
 
-def run_sweep_bench(args):
+def sweep_leg(pkg, n_pairs, max_n, fp64_samples, max_active):
     """Batched shift sweep: (k, kh) pairs x 16 shifts on a log grid in [0.05 k^2, 2 k^2], 2D P1,
     plane wave, restart 50, cap 500. Mixed precision through the request server (all samples
     in flight together) against the plain FP64 form solved one problem at a time."""
     import torch
-    import __graft_entry__
-    __graft_entry__.build()
-    import paper_2104_01439_gb300 as pkg
     from paper_2104_01439_gb300 import sweep
-    wls = [w for w in hi.shift_sweep(seed=4) if w.n <= args.max_n][: 16 * args.pairs]
+    wls = [w for w in hi.shift_sweep(seed=4) if w.n <= max_n][: 16 * n_pairs]
     samples = [sweep.Sample(w.k, w.n, w.shift) for w in wls]
     pairs = len({(s.k, s.n) for s in samples})
-    # warm-up: one small sweep (library load, first-launch costs)
-    sweep.run_sweep(samples[:2], max_active=2)
+    sweep.run_sweep(samples[:2], max_active=2)   # warm-up (library load, first-launch costs)
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     res = sweep.run_sweep(samples, theta=0.3, restart=50, maxit=500, precision=pkg.HELM_MIXED,
-                          budget_bytes=150 << 30, max_active=args.max_active)
+                          budget_bytes=150 << 30, max_active=max_active)
     torch.cuda.synchronize()
     wall = time.perf_counter() - t0
     # plain FP64 per-solve form on a bounded prefix of the same samples
-    nf = min(len(samples), args.fp64_samples)
+    nf = min(len(samples), fp64_samples)
     t1 = time.perf_counter()
     it64 = []
-    for s in samples[:nf]:
-        slv = pkg.Solver(s.k, s.n, 1, s.shift, restart=50, maxit=500, tol=1e-8, precision=pkg.HELM_FP64)
+    for smp in samples[:nf]:
+        slv = pkg.Solver(smp.k, smp.n, 1, smp.shift, restart=50, maxit=500, tol=1e-8, precision=pkg.HELM_FP64)
         F = slv.rhs_planewave(0.3).cuda()
         _, r = slv.solve(F)
         it64.append(r.iters)
@@ -489,18 +549,13 @@ def run_sweep_bench(args):
     best = sweep.best_shifts(res)
     params, loss = sweep.fit_shift_map([b.sample.k for b in best], [b.sample.ell for b in best],
                                        [b.sample.sigma for b in best])
-    v = len(samples) / wall
-    v64 = nf / wall64
-    line = {
-        "metric": METRIC, "value": v, "unit": "solves/s", "n_gpus": 1, "steps": 1, "warmup": 1,
-        "ms_per_step": 1e3 * wall, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-        "dtype": "f32+f64", "data": "synthetic",
-        "config": {"workload": f"shift sweep: {pairs} (k, kh) pairs (k~U[10,300], kh~U[0.3,0.8], seed 4, "
-                               f"n <= {args.max_n}) x 16 shifts log-spaced in [0.05k^2, 2k^2], 2D P1, plane wave "
-                               f"theta=0.3, FGMRES(50) cap 500, relres 1e-8",
-                   "step": "all samples through the request server (complex64 V-cycle), setup included",
-                   "parallelism": f"request server, max_active={args.max_active}, budget 150 GB"},
-        "solves": len(samples),
+    v, v64 = len(samples) / wall, nf / wall64
+    return {
+        "workload": f"shift sweep: {pairs} (k, kh) pairs (k~U[10,300], kh~U[0.3,0.8], seed 4, n <= {max_n}) "
+                    f"x 16 shifts log-spaced in [0.05k^2, 2k^2], 2D P1, plane wave theta=0.3, FGMRES(50) "
+                    f"cap 500, relres 1e-8; all samples through the request server (complex64 V-cycle, "
+                    f"max_active={max_active}, budget 150 GB), setup included",
+        "value": v, "unit": "solves/s", "wall_s": wall, "solves": len(samples),
         "iters": {"min": min(r.iters for r in res), "max": max(r.iters for r in res),
                   "mean": statistics.mean(r.iters for r in res),
                   "capped": sum(r.status != "converged" for r in res)},
@@ -509,21 +564,30 @@ def run_sweep_bench(args):
                            "batched_mixed_speedup": v / v64},
         "best_shift_fit": {"params": [float(x) for x in params], "loss": loss, "points": len(best)},
     }
-    print(json.dumps(line), flush=True)
 
 
-def run_serve_bench(args):
-    """Serving loop: Poisson arrivals (200/s), P1/P2 50/50, n from the grid set, k~U[20,400],
-    eps = k^sigma_p(k, log2 n) from the shift map (the paper's printed weights), random
-    N(0,1) complex load vectors, 150 GB budget. p50/p99 latency and solves/s, mixed vs FP64."""
-    import torch
+def run_sweep_bench(args):
     import __graft_entry__
     __graft_entry__.build()
     import paper_2104_01439_gb300 as pkg
+    leg = sweep_leg(pkg, args.pairs, args.max_n, args.fp64_samples, args.max_active)
+    line = {
+        "metric": METRIC, "value": leg["value"], "unit": "solves/s", "n_gpus": 1, "steps": 1, "warmup": 1,
+        "ms_per_step": 1e3 * leg["wall_s"], "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f32+f64", "data": "synthetic",
+        "config": {"workload": leg["workload"], "step": "all samples of the sweep", "parallelism": "request server"},
+        "sweep": leg,
+    }
+    print(json.dumps(line), flush=True)
+
+
+def serve_leg(pkg, requests, rate, grids, max_active):
+    """Serving loop: Poisson arrivals, P1/P2 50/50, n from the grid set, k~U[20,400],
+    eps = k^sigma_p(k, log2 n) from the shift map (the paper's printed weights), random
+    N(0,1) complex load vectors, 150 GB budget. p50/p99 latency and solves/s, mixed vs FP64."""
     from paper_2104_01439_gb300 import sweep
-    grids = tuple(int(g) for g in args.grids.split(","))
-    arr = hi.poisson_arrivals(seed=5, rate=args.rate, count=args.requests)
-    reqs = hi.serving_requests(seed=5, count=args.requests, grids=grids)
+    arr = hi.poisson_arrivals(seed=5, rate=rate, count=requests)
+    reqs = hi.serving_requests(seed=5, count=requests, grids=grids)
     out = {}
     for prec, name in ((pkg.HELM_MIXED, "mixed"), (pkg.HELM_FP64, "fp64")):
         rq = []
@@ -531,7 +595,7 @@ def run_serve_bench(args):
             eps = sweep.shift_of(sweep.PAPER_SHIFT_WEIGHTS[order], k, n)
             r = pkg.make_request(k, n, order, eps, restart=50, maxit=500, tol=1e-8, precision=prec)
             rq.append((r, _host_load(r, pkg, seed)))
-        with pkg.Server(150 << 30, args.max_active) as srv:
+        with pkg.Server(150 << 30, max_active) as srv:
             srv.submit(*rq[0])   # warm-up request (first-launch costs), not counted
             srv.drain()
             t0 = time.perf_counter()
@@ -549,18 +613,29 @@ def run_serve_bench(args):
                      "p99_ms": lat[min(len(lat) - 1, math.ceil(0.99 * len(lat)) - 1)], "makespan_s": wall,
                      "failed": len(infos) - len(ok), "capped": sum(i.result.status != "converged" for i in ok),
                      "mean_iters": statistics.mean(i.result.iters for i in ok) if ok else None}
-    m = out["mixed"]
+    return {
+        "workload": f"serving trace: {requests} requests, Poisson arrivals {rate:g}/s (seed 5), P1/P2 50/50, "
+                    f"n in {list(grids)}, k~U[20,400], eps from the paper's shift map, random N(0,1) complex "
+                    f"load, FGMRES(50) cap 500, relres 1e-8; request server (max_active={max_active}, "
+                    f"budget 150 GB), setup included",
+        "value": out["mixed"]["solves_per_s"], "unit": "solves/s",
+        "p50_ms": out["mixed"]["p50_ms"], "p99_ms": out["mixed"]["p99_ms"],
+        "mixed": out["mixed"], "fp64": out["fp64"],
+        "mixed_vs_fp64": out["mixed"]["solves_per_s"] / out["fp64"]["solves_per_s"],
+    }
+
+
+def run_serve_bench(args):
+    import __graft_entry__
+    __graft_entry__.build()
+    import paper_2104_01439_gb300 as pkg
+    leg = serve_leg(pkg, args.requests, args.rate, tuple(int(g) for g in args.grids.split(",")), args.max_active)
     line = {
-        "metric": METRIC, "value": m["solves_per_s"], "unit": "solves/s", "n_gpus": 1, "steps": 1, "warmup": 1,
-        "ms_per_step": 1e3 * m["makespan_s"], "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-        "dtype": "f32+f64", "data": "synthetic",
-        "config": {"workload": f"serving trace: {args.requests} requests, Poisson arrivals {args.rate:g}/s (seed 5), "
-                               f"P1/P2 50/50, n in {list(grids)}, k~U[20,400], eps from the paper's shift map, "
-                               f"random N(0,1) complex load, FGMRES(50) cap 500, relres 1e-8",
-                   "step": "whole trace: submit at arrival times, wait for every result (setup included)",
-                   "parallelism": f"request server, max_active={args.max_active}, budget 150 GB"},
-        "p50_ms": m["p50_ms"], "p99_ms": m["p99_ms"], "serve": out,
-        "mixed_vs_fp64": m["solves_per_s"] / out["fp64"]["solves_per_s"],
+        "metric": METRIC, "value": leg["value"], "unit": "solves/s", "n_gpus": 1, "steps": 1, "warmup": 1,
+        "ms_per_step": 1e3 * leg["mixed"]["makespan_s"], "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic",
+        "config": {"workload": leg["workload"], "step": "whole trace", "parallelism": "request server"},
+        "p50_ms": leg["p50_ms"], "p99_ms": leg["p99_ms"], "serve": leg,
     }
     print(json.dumps(line), flush=True)
 
@@ -612,6 +687,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-legs", action="store_true", help="skip the sweep and serve legs of the default line")
     ap.add_argument("--kernel", choices=["coarse", "vcycle", "apply", "stencil", "solve"],
                     help="only launch one hot-path step --steps times (profiling aid)")
     ap.add_argument("--fp64", action="store_true", help="with --kernel: the all-FP64 form")
@@ -621,9 +697,9 @@ def main():
     ap.add_argument("--max-n", type=int, default=256, help="sweep: keep pairs whose mesh has n <= this")
     ap.add_argument("--fp64-samples", type=int, default=32, help="sweep: samples of the FP64 per-solve form")
     ap.add_argument("--max-active", type=int, default=16, help="sweep/serve: requests in flight")
-    ap.add_argument("--requests", type=int, default=200, help="serve: requests in the trace")
+    ap.add_argument("--requests", type=int, default=120, help="serve: requests in the trace")
     ap.add_argument("--rate", type=float, default=200.0, help="serve: mean arrival rate (1/s)")
-    ap.add_argument("--grids", default="128,256", help="serve: mesh sizes n of the trace")
+    ap.add_argument("--grids", default="128,256,512", help="serve: mesh sizes n of the trace")
     args = ap.parse_args()
     if args.kernel:
         run_kernel(args)

@@ -26,6 +26,8 @@ def test_reference_arm_prints_one_contract_line():
     assert d["config"]["workload"].startswith(bench.WL.name)
     cb = d["cpu_baseline"]
     assert cb["kind"] == "oracle" and cb["cores"] == 1 and cb["value"] == d["value"] and cb["sample"]
+    assert cb["nproc"] >= 1 and cb["cpu_model"] and cb["single_core"]["seconds_per_solve"] > 0
+    assert d["iters"] == 163 and d["relres_true"] <= 1e-8      # a full solve, nothing extrapolated
     assert d["e2e"] == {"value": d["value"], "unit": "solves/s", "h2d_bytes_per_step": 0,
                         "d2h_bytes_per_step": 0}
 
