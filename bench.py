@@ -52,7 +52,7 @@ def workload_config(prec_name):
 
 # ---------------------------------------------------------------------------- helpers
 
-COARSE_TRAFFIC_BYTES = 646.7e6   # see the roofline object in run_ours
+COARSE_TRAFFIC_BYTES = 296.5e6   # ncu DRAM bytes of one coarse solve (profiles/coarse_solve_p1_n512.md)
 
 # stencil kernels at a size above L2: 2D P1, h = 1/4096 (16.8 M DoFs; one complex128
 # vector is 268 MB, twice the 129 MB L2), same kh and shift exponent as the solve workload
@@ -422,8 +422,8 @@ def run_ours(args):
     achieved = bytes_coarse / (phase_ms["coarse_solve"] * 1e-3) / 1e9
     # DRAM bytes of one coarse solve at this workload (dram__bytes_read.sum + dram__bytes_write.sum
     # of k_block_gemv, the four k_seg_chain launches, the two k_seg_fixup launches and k_seg_middle,
-    # one-pass ncu capture of `bench.py --kernel coarse`): the dense inverses and segment products
-    # read once each
+    # one-pass ncu capture of `bench.py --kernel coarse`): the distinct inverses, couplings and
+    # segment products read once each (repeated blocks of converged chains come from L2)
     traffic = COARSE_TRAFFIC_BYTES
     # stencil kernels: outer apply reads z and writes w (32 B/DoF, complex128); the fine level of
     # the V-cycle moves >= 52 B/DoF (read v_j 16, u 8 + 8, write z_j 16, transfers ~4)

@@ -525,7 +525,7 @@ size_t estimate_bytes(int dim, int order, int n, int precision, int restart) {
   const int64_t blk = B * ldb;
   const int64_t v = precision == HELM_MIXED ? 8 : 16;
   const int64_t m = restart, ldN = (N + 31) & ~int64_t(31), nblk = std::max<int64_t>(1, (N + 255) / 256);
-  const int64_t prec = v * (4 * N + 2 * nb * ldb) + 64;
+  const int64_t prec = v * (4 * N + 2 * nb * ldb) + 64 + 3 * 4 * nb;   // (+ the coarse block maps)
   // Dinv, Lm, Up; the mixed form's segmented solve adds two product sets and one vector
   const int64_t factor = v * 3 * blk * nb + (precision == HELM_MIXED ? 8 * (2 * blk * nb + nb * ldb) : 0);
   // basis (double-float), w split, Z (complex64 in the mixed form), W (FP64 form), residual
@@ -707,6 +707,32 @@ static int setup_impl(helm_ctx* h) {
                              reinterpret_cast<float4*>(piv), bar, h->err, Acv, L, h->nsm, s, fs.reuse)
           : coarse_factor_fp64(D64, tmp, piv, bar, h->err, Acv, L, h->nsm, s, fs.reuse);
   h->setup_kernels = std::max(L.mid, L.nb - 1 - L.mid) + 1 + 1 + (o.precision == HELM_MIXED ? 1 : 0);
+  // which chains converged: the repeated blocks are mapped to the converged one (CoarseLayout)
+  std::vector<int> cmap, pmapf, pmapb;
+  if (rc == HELM_OK) {
+    int st[kReuseStateInts];
+    cudaError_t e = cudaMemcpyAsync(st, fs.reuse, sizeof(st), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) {
+      rc = cuda_fail(e);
+    } else {
+      h->reused_blocks = coarse_reused_blocks(st, L);
+      const CoarsePlan* plan = o.precision == HELM_MIXED ? &h->p32.plan : &h->p64.plan;
+      coarse_block_maps(L, plan, st, &cmap, &pmapf, &pmapb);
+      auto put = [&](const std::vector<int>& v, const int** dst) -> int {
+        if (v.empty() || h->reused_blocks == 0) return HELM_OK;   // identity
+        int* d = nullptr;
+        CK(h->alloc(&d, sizeof(int) * v.size()));
+        CK(cudaMemcpyAsync(d, v.data(), sizeof(int) * v.size(), cudaMemcpyHostToDevice, s));
+        *dst = d;
+        return HELM_OK;
+      };
+      if (!rc) rc = put(cmap, &L.cmap);
+      if (!rc) rc = put(pmapf, &L.pmapf);
+      if (!rc) rc = put(pmapb, &L.pmapb);
+      if (h->reused_blocks == 0) cmap.clear();
+    }
+  }
   // couplings folded into the inverses: Lm[J] = Dinv[J] A_J,J-1, Up[J] = Dinv[J] A_J,J+1
   if (rc == HELM_OK && o.precision == HELM_MIXED) {
     Prec<float>& p = h->p32;
@@ -725,7 +751,7 @@ static int setup_impl(helm_ctx* h) {
           rc = HELM_ENOMEM;
         } else {
           p.seg = SegBufs<float>{yb, Pf, Pb};
-          coarse_seg_products(p.Lm, p.Up, Pf, Pb, L, p.plan, s);
+          coarse_seg_products(p.Lm, p.Up, Pf, Pb, L, p.plan, s, cmap);
           h->setup_kernels += coarse_seg_launches(L, p.plan);
         }
       }
@@ -742,11 +768,6 @@ static int setup_impl(helm_ctx* h) {
   cudaEventRecord(h->e1, s);
   cudaEventSynchronize(h->e1);
   cudaEventElapsedTime(&h->setup_ms, h->e0, h->e1);
-  if (rc == HELM_OK) {
-    int st[kReuseStateInts];
-    if (cudaMemcpy(st, fs.reuse, sizeof(st), cudaMemcpyDeviceToHost) == cudaSuccess)
-      h->reused_blocks = coarse_reused_blocks(st, L);
-  }
   fs.free_work();
   if (rc == HELM_OK) {
     cudaError_t le = cudaGetLastError();

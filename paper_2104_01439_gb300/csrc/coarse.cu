@@ -31,6 +31,7 @@
 #include <algorithm>
 #include <mutex>
 #include <unordered_map>
+#include <vector>
 
 #include "dfloat.cuh"
 #include "kernels.cuh"
@@ -703,6 +704,7 @@ __global__ void __launch_bounds__(256) k_couple(const typename A::V* __restrict_
     const int J = (int)(rem / blk);
     const int a = (int)((rem - (int64_t)J * blk) / ldb), l = (int)(rem - (int64_t)J * blk - (int64_t)a * ldb);
     const int Jl = which == 0 ? J - 1 : J + 1;   // block of column l
+    if (map_block(L.cmap, J) != J) continue;     // a repeat of a converged block: never read
     V acc = A::zero();
     int c[3];
     if (l < B && Jl >= 0 && Jl < L.nb && block_coords(g, L, Jl, l, c)) {
@@ -771,7 +773,8 @@ __global__ void __launch_bounds__(256) k_block_gemv_wide(const c2<T>* __restrict
   const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
   for (int64_t rw = w0; rw < rows; rw += nw) {
     const int J = (int)(rw / L.B), a = (int)(rw - (int64_t)J * L.B);
-    V v = warp_sum(row_dot(Dinv + rw * L.ldb, rc + (int64_t)J * L.ldb, L.ldb, lane));
+    V v = warp_sum(row_dot(Dinv + ((int64_t)map_block(L.cmap, J) * L.B + a) * L.ldb, rc + (int64_t)J * L.ldb,
+                           L.ldb, lane));
     if (lane == 0) out[(int64_t)J * L.ldb + a] = v;
   }
 }
@@ -993,7 +996,7 @@ __global__ void __launch_bounds__(kSolveMaxWarps * 32, 1)
     if (lane == 0) {
       auto rows = [&](int t) {
         const V* M = ((t <= nf) == (dir > 0)) ? Lm : Up;   // forward/middle: previous block; backward: next
-        return M + ((size_t)blockof(t) * B + r0) * ldb;
+        return M + ((size_t)map_block(L.cmap, blockof(t)) * B + r0) * ldb;
       };
       ring_produce<V>(c, rows, tm, U, nchunk, S, R, CW, ldb, nr, err);
     }
@@ -1107,7 +1110,7 @@ __global__ void __launch_bounds__(256) k_coarse_solve_grid(const c2<T>* __restri
     const int blk = blockof(t);
     const V* M = nullptr;
     if (t >= 1) {
-      M = (t <= nf ? Lm : Up) + (size_t)blk * B * ldb;
+      M = (t <= nf ? Lm : Up) + (size_t)map_block(L.cmap, blk) * B * ldb;
       const V* prev = uc + (size_t)blockof(t - 1) * ldb;
       for (int i = threadIdx.x; i < ldb; i += blockDim.x) xs[i] = i < B ? cvt_ldcg(prev + i) : zero;
       __syncthreads();
@@ -1153,6 +1156,7 @@ template <typename T> struct SegArgs {
   c2<T>* out;         // phase A: restarted recurrences; phase B: in place
   const c2<T>* C[2];  // per path: Lm or Up
   const c2<T>* P;     // segment products of this sweep, by block
+  const int* pmap;    // their block map (L.pmapf or L.pmapb; null = identity)
   SegPath path[2];
   int phase;          // 0 = A, 1 = B
 };
@@ -1189,7 +1193,9 @@ __global__ void __launch_bounds__(MAXW * 32, 1)
   auto pos = [&](int t) { return phA ? q0 + t : seg_end(t + 1, pa.Ls, pa.n); };
   auto blk = [&](int t) { return path_block(pa, pos(t)); };
   auto inv = [&](int t) -> const V* { return (phA ? a.in : a.out) + (size_t)blk(t) * ldb; };
-  auto mat = [&](int t) -> const V* { return (phA ? C : a.P) + (size_t)blk(t) * B * ldb; };
+  auto mat = [&](int t) -> const V* {
+    return phA ? C + (size_t)map_block(L.cmap, blk(t)) * B * ldb : a.P + (size_t)map_block(a.pmap, blk(t)) * B * ldb;
+  };
   const V* x0 = phA ? nullptr : a.out + (size_t)path_block(pa, seg_end(0, pa.Ls, pa.n)) * ldb;
   const int tm = phA ? 1 : 0;   // first step with a matrix
   const int U = max(0, nsteps - tm) * nchunk;
@@ -1295,8 +1301,9 @@ __global__ void __launch_bounds__(256) k_seg_middle(const c2<T>* __restrict__ Lm
   const int lane = threadIdx.x & 31;
   const int a = (int)((blockIdx.x * blockDim.x + threadIdx.x) >> 5);
   if (a >= B) return;
-  const V g = cadd(row_dot(Lm + ((size_t)m * B + a) * ldb, y + (size_t)(m - 1) * ldb, ldb, lane),
-                   row_dot(Up + ((size_t)m * B + a) * ldb, y + (size_t)(m + 1) * ldb, ldb, lane));
+  const size_t mc = (size_t)map_block(L.cmap, m);
+  const V g = cadd(row_dot(Lm + (mc * B + a) * ldb, y + (size_t)(m - 1) * ldb, ldb, lane),
+                   row_dot(Up + (mc * B + a) * ldb, y + (size_t)(m + 1) * ldb, ldb, lane));
   const V v = warp_sum(g);
   if (lane == 0) y[(size_t)m * ldb + a] = csub(p[(size_t)m * ldb + a], v);
 }
@@ -1340,7 +1347,7 @@ __global__ void __launch_bounds__(kRowsThreads) k_block_gemv(const c2<T>* __rest
   const int B = L.B, ldb = L.ldb, J = blockIdx.x;
   for (int i = threadIdx.x; i < ldb; i += blockDim.x) xs[i] = cvt_ldcg(rc + (size_t)J * ldb + i);
   __syncthreads();
-  block_rows<T>(Dinv + (size_t)J * B * ldb, xs, out + (size_t)J * ldb, B, ldb, false);
+  block_rows<T>(Dinv + (size_t)map_block(L.cmap, J) * B * ldb, xs, out + (size_t)J * ldb, B, ldb, false);
 }
 
 // Phase C: z_q -= P[J(q)] z_e(k-1) for every position q of segments k >= 1 except their
@@ -1348,7 +1355,7 @@ __global__ void __launch_bounds__(kRowsThreads) k_block_gemv(const c2<T>* __rest
 template <typename T>
 __global__ void __launch_bounds__(kRowsThreads) k_seg_fixup(const c2<T>* __restrict__ P, c2<T>* __restrict__ Z,
                                                             CoarseLayout L, SegPath p0, SegPath p1,
-                                                            const int* active) {
+                                                            const int* pmap, const int* active) {
   using V = c2<T>;
   if (active && *active == 0) return;
   __shared__ __align__(16) V xs[kSegMaxLdb];
@@ -1365,7 +1372,7 @@ __global__ void __launch_bounds__(kRowsThreads) k_seg_fixup(const c2<T>* __restr
   for (int i = threadIdx.x; i < ldb; i += blockDim.x) xs[i] = i < B ? cvt_ldcg(src + i) : mk(T(0), T(0));
   __syncthreads();
   const int J = path_block(pp, q);
-  block_rows<T>(P + (size_t)J * B * ldb, xs, Z + (size_t)J * ldb, B, ldb, true);
+  block_rows<T>(P + (size_t)map_block(pmap, J) * B * ldb, xs, Z + (size_t)J * ldb, B, ldb, true);
 }
 
 // Segment products, step i of every segment k >= 1 of one path (one z-slice per segment):
@@ -1377,6 +1384,8 @@ struct SegProducts {
   float2* P[4];
   SegPath path[4];
   int zoff[5];   // z-slices of path p: [zoff[p], zoff[p+1]), one per segment k >= 1
+  int dlo[4], dhi[4];   // segments [dlo, dhi] of path p repeat an earlier one (not computed)
+  const int* cmap;
 };
 __global__ void __launch_bounds__(256) k_seg_products(SegProducts sp, CoarseLayout L, int i) {
   const int B = L.B, ldb = L.ldb;
@@ -1387,8 +1396,8 @@ __global__ void __launch_bounds__(256) k_seg_products(SegProducts sp, CoarseLayo
   float2* __restrict__ P = sp.P[pi];
   const int k = 1 + z - sp.zoff[pi];
   const int q = k * pp.Ls + i;
-  if (q > seg_end(k, pp.Ls, pp.n)) return;
-  const float2* A = C + (size_t)path_block(pp, q) * B * ldb;
+  if (q > seg_end(k, pp.Ls, pp.n) || (k >= sp.dlo[pi] && k <= sp.dhi[pi])) return;
+  const float2* A = C + (size_t)map_block(sp.cmap, path_block(pp, q)) * B * ldb;
   float2* Zq = P + (size_t)path_block(pp, q) * B * ldb;
   const int row0 = blockIdx.y * 64, col0 = blockIdx.x * 64;
   const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
@@ -1669,17 +1678,17 @@ void launch_coarse_solve(const CoarsePlan& plan, const c2<T>* Dinv, const c2<T>*
     SegPath f[2], b[2];
     seg_paths(L, plan, f, b);
     // forward sweeps: uc (p) -> yb (y); middle block x_m -> yb[mid]
-    chain(SegArgs<T>{uc, seg->yb, {Lm, Up}, seg->Pf, {f[0], f[1]}, 0}, f[0].K + f[1].K);
-    chain(SegArgs<T>{seg->yb, seg->yb, {Lm, Up}, seg->Pf, {f[0], f[1]}, 1}, 2);
+    chain(SegArgs<T>{uc, seg->yb, {Lm, Up}, seg->Pf, L.pmapf, {f[0], f[1]}, 0}, f[0].K + f[1].K);
+    chain(SegArgs<T>{seg->yb, seg->yb, {Lm, Up}, seg->Pf, L.pmapf, {f[0], f[1]}, 1}, 2);
     const int slabs = (L.B + kRowsSlab - 1) / kRowsSlab;
     k_seg_fixup<T><<<dim3(std::max(1, f[0].n - f[0].Ls + f[1].n - f[1].Ls), slabs), kRowsThreads, 0, s>>>(
-        seg->Pf, seg->yb, L, f[0], f[1], active);
+        seg->Pf, seg->yb, L, f[0], f[1], L.pmapf, active);
     k_seg_middle<T><<<(L.B * 32 + 255) / 256, 256, 0, s>>>(Lm, Up, uc, seg->yb, L, active);
     // backward sweeps: yb (y, x_m) -> uc (x)
-    chain(SegArgs<T>{seg->yb, uc, {Up, Lm}, seg->Pb, {b[0], b[1]}, 0}, b[0].K + b[1].K);
-    chain(SegArgs<T>{uc, uc, {Up, Lm}, seg->Pb, {b[0], b[1]}, 1}, 2);
+    chain(SegArgs<T>{seg->yb, uc, {Up, Lm}, seg->Pb, L.pmapb, {b[0], b[1]}, 0}, b[0].K + b[1].K);
+    chain(SegArgs<T>{uc, uc, {Up, Lm}, seg->Pb, L.pmapb, {b[0], b[1]}, 1}, 2);
     k_seg_fixup<T><<<dim3(std::max(1, b[0].n - b[0].Ls + b[1].n - b[1].Ls), slabs), kRowsThreads, 0, s>>>(
-        seg->Pb, uc, L, b[0], b[1], active);
+        seg->Pb, uc, L, b[0], b[1], L.pmapb, active);
     return;
   }
   if (plan.grid) {
@@ -1823,11 +1832,68 @@ void convert_factor_df(const float4* src, float2* dst, size_t n, cudaStream_t s)
   k_convert_df<<<152 * 8, 256, 0, s>>>(src, dst, n);
 }
 
+namespace {
+// Segments k >= 1 of path p whose blocks all repeat a converged block (cmap[J] != J): the first
+// of the run is computed, the rest of the run repeat it position by position.
+void repeat_run(const SegPath& p, const std::vector<int>& cmap, int* kstar, int* lo, int* hi) {
+  *kstar = -1;
+  *lo = 1;
+  *hi = 0;
+  if (cmap.empty()) return;
+  for (int k = 1; k < p.K; ++k) {
+    bool all = true;
+    for (int q = k * p.Ls; q <= seg_end(k, p.Ls, p.n); ++q) {
+      const int J = path_block(p, q);
+      all &= cmap[J] != J;
+    }
+    if (all && *kstar < 0) {
+      *kstar = k;
+    } else if (all) {
+      if (*lo > *hi) *lo = k;
+      *hi = k;
+    } else if (*kstar >= 0) {
+      break;
+    }
+  }
+}
+}  // namespace
+
+void coarse_block_maps(const CoarseLayout& L, const CoarsePlan* plan, const int* reuse_host, std::vector<int>* cmap,
+                       std::vector<int>* pmapf, std::vector<int>* pmapb) {
+  const int nb = L.nb, m = L.mid;
+  cmap->assign(nb, 0);
+  for (int J = 0; J < nb; ++J) (*cmap)[J] = J;
+  const int* top = reuse_host;
+  const int* bot = reuse_host + kReuseWords;
+  if (top[0] && top[5] >= 1)
+    for (int J = top[5] + 1; J < m; ++J) (*cmap)[J] = top[5];
+  if (bot[0] && bot[5] <= nb - 2)
+    for (int J = m + 1; J < bot[5]; ++J) (*cmap)[J] = bot[5];
+  pmapf->clear();
+  pmapb->clear();
+  if (!plan || !plan->seg) return;
+  SegPath f[2], b[2];
+  seg_paths(L, *plan, f, b);
+  for (int sweep = 0; sweep < 2; ++sweep) {
+    std::vector<int>& pm = sweep == 0 ? *pmapf : *pmapb;
+    pm.resize(nb);
+    for (int J = 0; J < nb; ++J) pm[J] = J;
+    for (const SegPath& p : sweep == 0 ? f : b) {
+      int ks, lo, hi;
+      repeat_run(p, *cmap, &ks, &lo, &hi);
+      for (int k = lo; k <= hi; ++k)
+        for (int q = k * p.Ls; q <= seg_end(k, p.Ls, p.n); ++q)
+          pm[path_block(p, q)] = path_block(p, ks * p.Ls + (q - k * p.Ls));
+    }
+  }
+}
+
 void coarse_seg_products(const float2* Lm, const float2* Up, float2* Pf, float2* Pb, const CoarseLayout& L,
-                         const CoarsePlan& plan, cudaStream_t s) {
+                         const CoarsePlan& plan, cudaStream_t s, const std::vector<int>& cmap_host) {
   SegPath f[2], b[2];
   seg_paths(L, plan, f, b);
   SegProducts sp{};
+  sp.cmap = L.cmap;
   const SegPath all[4] = {f[0], f[1], b[0], b[1]};
   const float2* C[4] = {Lm, Up, Up, Lm};
   float2* P[4] = {Pf, Pf, Pb, Pb};
@@ -1837,6 +1903,8 @@ void coarse_seg_products(const float2* Lm, const float2* Up, float2* Pf, float2*
     sp.C[p] = C[p];
     sp.P[p] = P[p];
     sp.path[p] = all[p];
+    int ks;
+    repeat_run(all[p], cmap_host, &ks, &sp.dlo[p], &sp.dhi[p]);
     sp.zoff[p + 1] = sp.zoff[p] + all[p].K - 1;
     Lmax = std::max(Lmax, all[p].Ls);
   }

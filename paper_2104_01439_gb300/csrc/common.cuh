@@ -128,7 +128,23 @@ struct CoarseLayout {
   int plane;    // W^(dim-1)
   int mid;      // middle block: top chain 0..mid-1 and bottom chain nb-1..mid+1 meet here
                 // (twisted elimination); mid = nb-1 means a single top-down chain
+  // Block maps of the coarse factor (device arrays of nb ints; null = identity). Where a
+  // chain's Schur inverse converged during the factorisation, every later block of that chain
+  // has the same inverse and the same couplings, and the segment products of whole segments
+  // inside that range repeat: cmap[J] names the block whose Dinv, Lm and Up block J uses,
+  // pmapf[J] / pmapb[J] the block whose forward / backward segment product it uses. The
+  // repeated blocks are then read from one place (L2) and computed once.
+  const int* cmap = nullptr;
+  const int* pmapf = nullptr;
+  const int* pmapb = nullptr;
 };
+__host__ __device__ inline int map_block(const int* map, int J) {
+#if defined(__CUDA_ARCH__)
+  return map ? __ldg(map + J) : J;
+#else
+  return map ? map[J] : J;
+#endif
+}
 
 #if defined(__CUDACC__)
 // ----------------------------------------------------------------------------

@@ -1,6 +1,8 @@
 // Launchers of the hot-path kernels (internal to the library).
 #pragma once
 
+#include <vector>
+
 #include "common.cuh"
 
 namespace helm {
@@ -94,9 +96,15 @@ template <typename T>
 void launch_coarse_solve(const CoarsePlan& plan, const c2<T>* Dinv, const c2<T>* Lm, const c2<T>* Up,
                          const CoarseLayout& L, const c2<T>* rc, c2<T>* uc, unsigned* bar, int* err,
                          const int* active, int nsm, cudaStream_t s, const SegBufs<T>* seg = nullptr);
-// Segment products of both sweeps (plan.seg, complex64), and the number of launches it takes
+// Segment products of both sweeps (plan.seg, complex64), and the number of launches it takes;
+// segments that only repeat an earlier one (cmap_host: the host copy of L.cmap, may be empty)
+// are not computed
 void coarse_seg_products(const float2* Lm, const float2* Up, float2* Pf, float2* Pb, const CoarseLayout& L,
-                         const CoarsePlan& plan, cudaStream_t s);
+                         const CoarsePlan& plan, cudaStream_t s, const std::vector<int>& cmap_host);
+// Host block maps (see CoarseLayout) from the factorisation's reuse state (host copy): cmap for
+// the inverses and couplings, pmapf / pmapb for the segment products (left empty without plan.seg)
+void coarse_block_maps(const CoarseLayout& L, const CoarsePlan* plan, const int* reuse_host, std::vector<int>* cmap,
+                       std::vector<int>* pmapf, std::vector<int>* pmapb);
 int coarse_seg_launches(const CoarseLayout& L, const CoarsePlan& plan);
 // Block-Thomas factorisation: Dinv[J] = (A_JJ - A_J,J-1 Dinv[J-1] A_J-1,J)^{-1} (two chains
 // meeting at L.mid), in complex128 (8-pivot Gauss-Jordan panels) or in complex double-float
