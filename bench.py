@@ -61,18 +61,13 @@ STENCIL_NU = 4
 
 
 def stencil_bytes_per_dof(nu, mixed):
-    """Algorithmic bytes per DoF of helm_apply and of nu smoothing sweeps from u = 0.
+    """Algorithmic bytes per DoF of helm_apply and of nu smoothing sweeps from u = 0 (2D).
 
     apply: read x, write y (complex128): 32 B.
-    mixed smoother (complex64 sweeps, one kernel per sweep): the first reads f (16) and
-    writes u (8) and the complex64 copy of f (8); every middle sweep reads f, u and writes u
-    (8 + 8 + 8); the last reads f, u (8 + 8) and writes complex128 (16).
-    FP64: 16 B per vector access, no copy of f; its first kernel runs two sweeps when nu >= 3
-    (u^1 at the neighbours recomputed from f)."""
-    if mixed:
-        return {"apply": 32, "smooth": 32 + 24 * (nu - 2) + 32, "kernels": nu}
-    kernels = 1 + (nu - 1 - (2 if nu >= 3 else 1)) + 1
-    return {"apply": 32, "smooth": 32 + 48 * (kernels - 2) + 48, "kernels": kernels}
+    smoother: the sweeps run fused on shared-memory tiles (one kernel), so the operation's own
+    traffic is all it moves: read f (complex128, 16 B) and write u^nu (complex128, 16 B),
+    32 B in both precisions (the complex64 form converts on the way in and out)."""
+    return {"apply": 32, "smooth": 32, "kernels": 1}
 
 
 def stencil_hbm(pkg, stream, dev, hbm, peak_kind, reps=20):

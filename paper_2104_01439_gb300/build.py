@@ -16,7 +16,7 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 OUT_DIR = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libhelm.so")
-SOURCES = ["tables.cpp", "stencil.cu", "coarse.cu", "krylov.cu", "api.cu", "serve.cu"]
+SOURCES = ["tables.cpp", "stencil.cu", "smooth.cu", "coarse.cu", "krylov.cu", "api.cu", "serve.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

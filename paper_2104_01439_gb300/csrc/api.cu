@@ -234,6 +234,18 @@ void enqueue_vcycle(helm_ctx* h, VecSel<const Vf> f, VecSel<Vz> z, const int* ac
   const int nu = h->opts.nu;
   V* cur = p.ua;
   V* oth = p.ub;
+  // 2D: presmoothing and the residual in one tiled kernel, the prolongation and the
+  // postsmoothing in another (smooth.cu)
+  if (launch_smooth_tile<T, Vf, V>(Ae, f, nullptr, nullptr, nullptr, nullptr, nu, vsel<V>(cur), p.r, active, s)) {
+    launch_restrict<T>(P, h->L, p.r, p.rc, active, s);
+    if (prof) cudaEventRecord(prof->ev[ev0 + 1], s);
+    launch_coarse_solve<T>(p.plan, p.Dinv, p.Lm, p.Up, h->L, p.rc, p.uc, p.gbar, h->err, active, h->nsm, s,
+                           p.segp());
+    if (prof) cudaEventRecord(prof->ev[ev0 + 2], s);
+    if (launch_smooth_tile<T, Vf, Vz>(Ae, f, cur, &P, &h->L, p.uc, nu, z, nullptr, active, s)) return;
+    launch_prolong_add<T>(P, h->L, p.uc, cur, active, s);   // (not reached: both tiles fit alike)
+    return;
+  }
   VecSel<const V> fT;
   if constexpr (sizeof(V) == sizeof(double2)) {
     launch_jacobi_from_zero<T, double2>(Ae, f, cur, nullptr, nu >= 2, active, s);
@@ -546,6 +558,9 @@ void enqueue_smooth(helm_ctx* h, const double2* f, double2* u, int nu, cudaStrea
   using V = c2<T>;
   Prec<T>& p = h->prec<T>();
   StencilView<T> Ae = make_view<T>(h->gf, p.coefAe, p.wdinv);
+  if (launch_smooth_tile<T, double2, double2>(Ae, vsel<const double2>(f), nullptr, nullptr, nullptr, nullptr, nu,
+                                              vsel<double2>(u), nullptr, nullptr, s))
+    return;   // 2D: all nu sweeps in one tiled kernel
   V* cur = p.ua;
   V* oth = p.ub;
   const bool two = nu >= 3;   // the first two sweeps fused when two or more precede the last one
@@ -620,6 +635,8 @@ static int setup_impl(helm_ctx* h) {
   if (h->gf.N >= (1ll << 31) / 2) return HELM_ENOTSUP;
   CK(cudaGetDevice(&h->dev));
   CK(cudaDeviceGetAttribute(&h->nsm, cudaDevAttrMultiProcessorCount, h->dev));
+  smooth_tile_prepare<float>();
+  smooth_tile_prepare<double>();
   CK(cudaEventCreate(&h->e0));
   CK(cudaEventCreate(&h->e1));
   cudaStream_t s = h->s;

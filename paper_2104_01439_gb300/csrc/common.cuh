@@ -147,6 +147,19 @@ __host__ __device__ inline int map_block(const int* map, int J) {
 }
 
 #if defined(__CUDACC__)
+// Index of coarse lattice point A (per-axis coordinates) in the block-padded coarse vector.
+__device__ __forceinline__ int coarse_pad_index(const GridDesc& gc, const CoarseLayout& L, const int* A) {
+  int last = gc.dim - 1;
+  int J = A[last] / L.rows;
+  int i = (A[last] - J * L.rows) * L.plane;
+  int mul = 1;
+  for (int ax = 0; ax < last; ++ax) {
+    i += A[ax] * mul;
+    mul *= gc.W;
+  }
+  return J * L.ldb + i;
+}
+
 // ----------------------------------------------------------------------------
 // Bounded software grid barrier for cooperative launches.
 // state[0] = arrival counter, state[kBarGen] = generation, on separate 128-byte

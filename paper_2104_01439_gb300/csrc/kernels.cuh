@@ -53,6 +53,16 @@ template <typename T>
 void launch_restrict(const TransferView<T>& P, const CoarseLayout& L, const c2<T>* r, c2<T>* rc,
                      const int* active, cudaStream_t s);
 // padded <-> natural coarse ordering (with precision conversion)
+// nu damped-Jacobi sweeps fused on 2D tiles (smooth.cu): from u^0 = 0 (u0 null) or from
+// u^0 = u0 + P uc (post-smoothing; uc null: u0 alone); writes u^nu to out and, when r is
+// given, the residual f - A u^nu. Returns false (nothing launched) where it does not apply
+// (3D, or a tile that does not fit shared memory): the caller then runs the per-sweep kernels.
+template <typename T>
+void smooth_tile_prepare();   // raises the kernels' shared-memory limit (outside stream capture)
+template <typename T, typename Vf, typename Vout>
+bool launch_smooth_tile(const StencilView<T>& A, VecSel<const Vf> f, const c2<T>* u0, const TransferView<T>* P,
+                        const CoarseLayout* L, const c2<T>* uc, int nu, VecSel<Vout> out, c2<T>* r,
+                        const int* active, cudaStream_t s);
 template <typename Vin, typename Vout>
 void launch_coarse_pack(const GridDesc& gc, const CoarseLayout& L, const Vin* nat, Vout* pad,
                         cudaStream_t s);

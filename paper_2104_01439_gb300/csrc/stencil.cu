@@ -250,19 +250,6 @@ __global__ void __launch_bounds__(kThreads) k_jacobi(StencilView<T> s, VecSel<co
   }
 }
 
-__device__ __forceinline__ int coarse_pad_index(const GridDesc& gc, const CoarseLayout& L,
-                                                const int* A) {
-  int last = gc.dim - 1;
-  int J = A[last] / L.rows;
-  int i = (A[last] - J * L.rows) * L.plane;
-  int mul = 1;
-  for (int ax = 0; ax < last; ++ax) {
-    i += A[ax] * mul;
-    mul *= gc.W;
-  }
-  return J * L.ldb + i;
-}
-
 template <typename T>
 __global__ void __launch_bounds__(kThreads) k_prolong_add(TransferView<T> P, CoarseLayout L,
                                                            const c2<T>* __restrict__ uc,
