@@ -125,6 +125,29 @@ int helm_operator_setup(double k, double h, int order, double shift, const helm_
  */
 int helm_setup_q(double k, double h, int order, double shift, const helm_opts* opts, helm_t* out);
 
+/*
+ * Heterogeneous wavenumber k(x) (Sec. 2 with k in L^inf; Sec. 6, where k(x) = k_max mu(x) comes
+ * from a velocity model): helm_setup for the operators
+ *   A(k, eps) = K - sum_e (k_e^2 + i eps) M_e - i sum_F k_F B_F    (eq. sys_matrix)
+ * with one wavenumber per element, on the fine mesh and, rediscretised from the coarse
+ * elements' own values, on the 2h mesh (Sec. 4). elements: HELM_SIMPLICES or HELM_TENSOR;
+ * k_fine: one k >= 0 per element of the mesh of spacing h, k_coarse: one per element of the
+ * 2h mesh, both in the element order of helm_host_het_row (copied; the caller keeps them). A
+ * boundary facet takes its element's k. shift: one real eps >= 0 for the whole domain (eq.
+ * Helmholtz_shift). The shifted operator's class stencils hold K - i eps M, and the
+ * k-dependent part -M_k - i B_k is added from per-DoF rows (complex64 in the V-cycle of the
+ * HELM_MIXED form, complex128 in the outer apply and in the coarse factorisation), with a
+ * per-DoF Jacobi diagonal. The coarse factorisation factors every block (no reuse of
+ * converged inverses). Everything else is as for helm_setup. HELM_EINVAL for a null or
+ * non-finite k array or a mesh helm_setup refuses.
+ */
+int helm_setup_het(int elements, const double* k_fine, const double* k_coarse, double h, int order, double shift,
+                   const helm_opts* opts, helm_t* out);
+
+/* Load vector of the paper's point source (Sec. 6): f = 2 exp(-1000 |x - s|^2), g = 0, F = M f
+ * interpolated at the DoFs (host, complex128[N]). Works on every handle. */
+int helm_rhs_source(helm_t h, double sx, double sy, double sz, void* F_host);
+
 /* Number of complex DoFs N = (order/h + 1)^dim of the fine space. */
 int helm_num_dofs(helm_t h, int64_t* n);
 
@@ -187,7 +210,8 @@ const char* helm_last_cuda_error(void);
 /*
  * Load vector of the plane wave u = exp(i k d.x), d = (cos theta, sin theta[, 0]):
  * f = 0 and impedance data g = i k (d.n - 1) u on each boundary facet with
- * that facet's outward normal (Sec. 2, F(v) = int f v + int_dOmega g v).
+ * that facet's outward normal (Sec. 2, F(v) = int f v + int_dOmega g v). HELM_EINVAL for a
+ * handle of helm_setup_het (no single k).
  */
 int helm_rhs_planewave(helm_t h, double theta, void* F_host);
 

@@ -29,7 +29,7 @@ EXPORTS = [
     "helm_server_wait", "helm_server_drain", "helm_server_destroy", "helm_load_planewave", "helm_load_gaussian",
     "helm_operator_setup", "helm_smooth", "helm_host_stencil_row", "helm_host_prolongation_row",
     "helm_setup_q", "helm_load_planewave_e", "helm_load_gaussian_e", "helm_host_het_row",
-    "helm_factor_info",
+    "helm_factor_info", "helm_setup_het", "helm_rhs_source",
 ]
 
 
@@ -111,6 +111,9 @@ def load(path: str = LIB_PATH):
     lib.helm_load_planewave.argtypes = [i, i, d, d, d, vp]
     lib.helm_operator_setup.argtypes = [d, d, i, d, ctypes.POINTER(HelmOpts), ctypes.POINTER(vp)]
     lib.helm_setup_q.argtypes = [d, d, i, d, ctypes.POINTER(HelmOpts), ctypes.POINTER(vp)]
+    lib.helm_setup_het.argtypes = [i, ctypes.POINTER(d), ctypes.POINTER(d), d, i, d, ctypes.POINTER(HelmOpts),
+                                   ctypes.POINTER(vp)]
+    lib.helm_rhs_source.argtypes = [vp, d, d, d, vp]
     lib.helm_load_planewave_e.argtypes = [i, i, i, d, d, d, vp]
     lib.helm_load_gaussian_e.argtypes = [i, i, i, d, d, d, d, d, vp]
     lib.helm_smooth.argtypes = [vp, vp, vp, i]
@@ -173,7 +176,9 @@ class Solver:
     def __init__(self, k: float, n: int, order: int = 1, shift: float = 0.0, dim: int = 2,
                  omega: float = 0.6, nu: int = 2, restart: int = 50, maxit: int = 500,
                  tol: float = 1e-8, precision: int = HELM_FP64, stream=None, operator_only: bool = False,
-                 elements: int = HELM_SIMPLICES):
+                 elements: int = HELM_SIMPLICES, k_fine=None, k_coarse=None):
+        """k_fine / k_coarse (helm_setup_het): one wavenumber per element of the fine and of the
+        coarse mesh, in the element order of helm_host_het_row; k is then ignored."""
         import torch
         lib = load()
         o = HelmOpts()
@@ -187,9 +192,20 @@ class Solver:
         self.k, self.n, self.order, self.shift, self.dim, self.precision = k, n, order, shift, dim, precision
         if elements not in (HELM_SIMPLICES, HELM_TENSOR) or (operator_only and elements != HELM_SIMPLICES):
             raise ValueError("elements: HELM_SIMPLICES, or HELM_TENSOR for a full solver handle")
-        setup = (lib.helm_operator_setup if operator_only
-                 else lib.helm_setup_q if elements == HELM_TENSOR else lib.helm_setup)
-        _check(setup(float(k), 1.0 / n, order, float(shift), ctypes.byref(o), ctypes.byref(self._h)))
+        if k_fine is not None:
+            if operator_only or k_coarse is None:
+                raise ValueError("a heterogeneous wavenumber needs k_fine and k_coarse and a full solver handle")
+            import numpy as np
+            kf = np.ascontiguousarray(k_fine, dtype=np.float64)
+            kc = np.ascontiguousarray(k_coarse, dtype=np.float64)
+            self._k_arrays = (kf, kc)
+            dp = ctypes.POINTER(ctypes.c_double)
+            _check(lib.helm_setup_het(elements, kf.ctypes.data_as(dp), kc.ctypes.data_as(dp), 1.0 / n, order,
+                                      float(shift), ctypes.byref(o), ctypes.byref(self._h)))
+        else:
+            setup = (lib.helm_operator_setup if operator_only
+                     else lib.helm_setup_q if elements == HELM_TENSOR else lib.helm_setup)
+            _check(setup(float(k), 1.0 / n, order, float(shift), ctypes.byref(o), ctypes.byref(self._h)))
         nd = ctypes.c_int64()
         _check(lib.helm_num_dofs(self._h, ctypes.byref(nd)))
         self.num_dofs = nd.value
@@ -264,6 +280,14 @@ class Solver:
         import torch
         F = torch.empty(self.num_dofs, dtype=torch.complex128)
         _check(load().helm_rhs_planewave(self._h, theta, ctypes.c_void_p(F.data_ptr())))
+        return F
+
+    def rhs_source(self, center=(0.5, 0.5, 0.5)):
+        """The paper's point source f = 2 exp(-1000 |x - s|^2), g = 0 (helm_rhs_source)."""
+        import torch
+        F = torch.empty(self.num_dofs, dtype=torch.complex128)
+        c = list(center) + [0.5] * (3 - len(center))
+        _check(load().helm_rhs_source(self._h, c[0], c[1], c[2], ctypes.c_void_p(F.data_ptr())))
         return F
 
     def rhs_gaussian(self, sigma: float, center=(0.5, 0.5, 0.5)):

@@ -8,6 +8,7 @@
 #include <cstring>
 #include <mutex>
 #include <new>
+#include <type_traits>
 #include <vector>
 
 #include "kernels.cuh"
@@ -28,8 +29,11 @@ const char* kPhaseNames[Profile::kPhases] = {"vcycle_pre_restrict", "coarse_solv
                                              "apply_A0", "arnoldi_dots_givens", "arnoldi_update"};
 
 template <typename T> struct Prec {
+  using value_type = T;
   c2<T>* coefAe = nullptr;   // fine A_eps
   c2<T>* wdinv = nullptr;    // fine omega/diag(A_eps)
+  c2<T>* hrow = nullptr;     // heterogeneous k: per-DoF rows of -M_k - i B_k (fine), N x noff
+  c2<T>* hwd = nullptr;      // heterogeneous k: per-DoF omega / diag(A_eps)
   c2<T>* coefAc = nullptr;   // coarse A_eps
   T* pw = nullptr;           // prolongation weights
   c2<T>* Dinv = nullptr;     // coarse factor: inverses of the Schur blocks
@@ -55,6 +59,10 @@ struct helm_ctx {
   bool op_only = false;        // fine-level operators only (helm_operator_setup)
   int elements = HELM_SIMPLICES;   // HELM_TENSOR: Q_order on squares / cubes (helm_setup_q)
   double k = 0, h = 0, shift = 0;
+  bool het = false;                // one wavenumber per element (helm_setup_het)
+  std::vector<double> kf, kc;      // ... of the fine and of the coarse elements
+  double2* hrowA0 = nullptr;       // per-DoF rows of the fine operators' k-dependent part (complex128)
+  double2* hrowC = nullptr;        // the same on the coarse level (read by the factorisation)
   helm_opts opts{};
   cudaStream_t s = nullptr;
   int dev = 0;                 // device the handle was set up on
@@ -113,10 +121,13 @@ int cuda_fail(cudaError_t e) {
   } while (0)
 
 template <typename T>
-StencilView<T> make_view(const GridDesc& g, const c2<T>* coef, const c2<T>* wdinv) {
+StencilView<T> make_view(const GridDesc& g, const c2<T>* coef, const c2<T>* wdinv, const c2<T>* hrow = nullptr,
+                         const c2<T>* hwd = nullptr) {
   StencilView<T> v{};
   v.coef = coef;
   v.wdinv = wdinv;
+  v.hrow = hrow;
+  v.hwd = hwd;
   v.g = g;
   int side = 2 * g.R + 1;
   for (int o = 0; o < g.noff; ++o) {
@@ -229,7 +240,7 @@ void enqueue_vcycle(helm_ctx* h, VecSel<const Vf> f, VecSel<Vz> z, const int* ac
                     cudaStream_t s, Profile* prof, int ev0) {
   using V = c2<T>;
   Prec<T>& p = h->prec<T>();
-  StencilView<T> Ae = make_view<T>(h->gf, p.coefAe, p.wdinv);
+  StencilView<T> Ae = make_view<T>(h->gf, p.coefAe, p.wdinv, p.hrow, p.hwd);
   TransferView<T> P = make_transfer<T>(h, p.pw);
   const int nu = h->opts.nu;
   V* cur = p.ua;
@@ -295,7 +306,7 @@ void enqueue_iteration(helm_ctx* h, cudaStream_t s, Profile* prof = nullptr, int
   const int* act = &kb.st->pre;
   const int* jsel = &kb.st->j;
   if (prof) cudaEventRecord(prof->ev[ev0 + 0], s);
-  StencilView<double> A0 = make_view<double>(h->gf, h->coefA0, nullptr);
+  StencilView<double> A0 = make_view<double>(h->gf, h->coefA0, nullptr, h->hrowA0);
   if (h->opts.precision == HELM_MIXED) {
     // complex64 form: the preconditioner reads slot j of the basis (high parts), z_j is
     // complex64, and w = A0 z_j is formed in double-float from it (exact products of the
@@ -434,7 +445,7 @@ bool solve_step(SolveTask& t, bool blocking) {
       // cycle end: y = R^{-1} g, x += Z y, true residual
       launch_backsolve(kb, s);
       launch_update_x(kb, t.x, s);
-      StencilView<double> A0 = make_view<double>(h->gf, h->coefA0, nullptr);
+      StencilView<double> A0 = make_view<double>(h->gf, h->coefA0, nullptr, h->hrowA0);
       launch_residual<double, double2, double2>(A0, vsel<const double2>(t.F), t.x, h->rres, nullptr, s);
       launch_norm(kb, h->rres, 1, s);
       t.kernels += 5;
@@ -557,7 +568,7 @@ template <typename T>
 void enqueue_smooth(helm_ctx* h, const double2* f, double2* u, int nu, cudaStream_t s) {
   using V = c2<T>;
   Prec<T>& p = h->prec<T>();
-  StencilView<T> Ae = make_view<T>(h->gf, p.coefAe, p.wdinv);
+  StencilView<T> Ae = make_view<T>(h->gf, p.coefAe, p.wdinv, p.hrow, p.hwd);
   if (launch_smooth_tile<T, double2, double2>(Ae, vsel<const double2>(f), nullptr, nullptr, nullptr, nullptr, nu,
                                               vsel<double2>(u), nullptr, nullptr, s))
     return;   // 2D: all nu sweeps in one tiled kernel
@@ -641,12 +652,53 @@ static int setup_impl(helm_ctx* h) {
   CK(cudaEventCreate(&h->e1));
   cudaStream_t s = h->s;
 
-  // coefficient tables (Sec. 2, eq. sys_matrix): A0 = A(k, 0), A_eps = A(k, eps)
-  auto A0 = complex_table(h->tab.Kf, h->tab.Mf, h->tab.Bf, h->k, 0.0);
-  auto Ae = complex_table(h->tab.Kf, h->tab.Mf, h->tab.Bf, h->k, h->shift);
-  auto Ac = complex_table(h->tab.Kc, h->tab.Mc, h->tab.Bc, h->k, h->shift);
+  // coefficient tables (Sec. 2, eq. sys_matrix): A0 = A(k, 0), A_eps = A(k, eps). With one
+  // wavenumber per element the class tables hold K - i eps M and the k-dependent part
+  // -M_k - i B_k comes as per-DoF rows (eq. sys_matrix with k in L^inf, Sec. 6).
+  const double kt = h->het ? 0.0 : h->k;
+  auto A0 = complex_table(h->tab.Kf, h->tab.Mf, h->tab.Bf, kt, 0.0);
+  auto Ae = complex_table(h->tab.Kf, h->tab.Mf, h->tab.Bf, kt, h->shift);
+  auto Ac = complex_table(h->tab.Kc, h->tab.Mc, h->tab.Bc, kt, h->shift);
   auto wd = wdinv_table(Ae, h->ncls_f, h->gf.noff, o.omega);
   if ((rc = upload<double>(h, &h->coefA0, A0))) return rc;
+  std::vector<double2> hrf, hwdf;   // fine per-DoF rows and omega / diag(A_eps)
+  if (h->het) {
+    HetRows hf, hc;
+    if ((rc = build_het_rows(o.dim, h->order, h->n, h->elements, h->kf.data(), &hf))) return rc;
+    if ((rc = build_het_rows(o.dim, h->order, h->n / 2, h->elements, h->kc.data(), &hc))) return rc;
+    auto rows = [](const HetRows& r) {
+      std::vector<double2> v(r.Mk.size());
+      for (size_t i = 0; i < v.size(); ++i) v[i] = make_double2(-r.Mk[i], -r.Bk[i]);
+      return v;
+    };
+    hrf = rows(hf);
+    const std::vector<double2> hrc = rows(hc);
+    if ((rc = upload<double>(h, &h->hrowA0, hrf))) return rc;
+    if ((rc = upload<double>(h, &h->hrowC, hrc))) return rc;
+    // omega / diag: the class table's centre plus the DoF's own centre coefficient
+    const int noff = h->gf.noff, ctr = noff / 2;
+    hwdf.resize((size_t)h->gf.N);
+    for (int64_t pdof = 0; pdof < h->gf.N; ++pdof) {
+      int64_t t = pdof;
+      int cls = 0, mul = 1;
+      for (int ax = 0; ax < o.dim; ++ax) {
+        const int a = (int)(t % h->gf.W);
+        t /= h->gf.W;
+        cls += axis_class(a, h->gf.W, h->gf.R, h->gf.q) * mul;
+        mul *= h->gf.C1;
+      }
+      const double2 c = Ae[(size_t)cls * noff + ctr], e = hrf[(size_t)pdof * noff + ctr];
+      const double dr = c.x + e.x, di = c.y + e.y, m2 = dr * dr + di * di;
+      hwdf[pdof] = m2 > 0 ? make_double2(o.omega * dr / m2, -o.omega * di / m2) : make_double2(0, 0);
+    }
+  }
+  auto upload_het = [&](auto& p) -> int {
+    using TT = typename std::remove_reference_t<decltype(p)>::value_type;
+    if (!h->het) return HELM_OK;
+    int r2;
+    if ((r2 = upload<TT>(h, &p.hrow, hrf))) return r2;
+    return upload<TT>(h, &p.hwd, hwdf);
+  };
 
   if (h->op_only) {
     // fine-level operators and the smoother's workspaces only
@@ -679,8 +731,10 @@ static int setup_impl(helm_ctx* h) {
   L.mid = L.nb - 1;   // single chain unless the solve plan runs two clusters (set below)
   if (o.precision == HELM_MIXED) {
     if ((rc = setup_prec<float>(h, Ae, wd, Ac, true))) return rc;
+    if ((rc = upload_het(h->p32))) return rc;
   }
   if ((rc = setup_prec<double>(h, Ae, wd, Ac, o.precision == HELM_FP64))) return rc;
+  if ((rc = upload_het(h->p64))) return rc;
 
   // coarse factorisation (Sec. 6: factor once, reuse): complex128 for the FP64 form,
   // complex double-float (16-byte float4 entries) for the mixed form, whose factor is
@@ -719,10 +773,13 @@ static int setup_impl(helm_ctx* h) {
   CK(h->alloc(&h->err, sizeof(int)));
   CK(cudaMemsetAsync(h->err, 0, sizeof(int), s));
   CK(cudaEventRecord(h->e0, s));
-  StencilView<double> Acv = make_view<double>(h->gc, h->p64.coefAc, nullptr);
+  StencilView<double> Acv = make_view<double>(h->gc, h->p64.coefAc, nullptr, h->hrowC);
+  // (blocks of a heterogeneous operator differ from line to line: no reuse of inverses)
+  int* reuse = h->het ? nullptr : fs.reuse;
+  if (h->het) CK(cudaMemsetAsync(fs.reuse, 0, kReuseStateInts * sizeof(int), s));
   rc = df ? coarse_factor_df(reinterpret_cast<float4*>(D64), reinterpret_cast<float4*>(tmp),
-                             reinterpret_cast<float4*>(piv), bar, h->err, Acv, L, h->nsm, s, fs.reuse)
-          : coarse_factor_fp64(D64, tmp, piv, bar, h->err, Acv, L, h->nsm, s, fs.reuse);
+                             reinterpret_cast<float4*>(piv), bar, h->err, Acv, L, h->nsm, s, reuse)
+          : coarse_factor_fp64(D64, tmp, piv, bar, h->err, Acv, L, h->nsm, s, reuse);
   h->setup_kernels = std::max(L.mid, L.nb - 1 - L.mid) + 1 + 1 + (o.precision == HELM_MIXED ? 1 : 0);
   // which chains converged: the repeated blocks are mapped to the converged one (CoarseLayout)
   std::vector<int> cmap, pmapf, pmapb;
@@ -851,7 +908,8 @@ static int setup_impl(helm_ctx* h) {
 }
 
 static int setup_any(double k, double h, int order, double shift, const helm_opts* opts, helm_t* out,
-                     bool op_only, int elements = HELM_SIMPLICES) {
+                     bool op_only, int elements = HELM_SIMPLICES, const double* k_fine = nullptr,
+                     const double* k_coarse = nullptr) {
   if (!out) return HELM_EINVAL;
   *out = nullptr;
   helm_opts o;
@@ -877,6 +935,20 @@ static int setup_any(double k, double h, int order, double shift, const helm_opt
   c->s = (cudaStream_t)o.stream;
   c->op_only = op_only;
   c->elements = elements;
+  if (k_fine) {
+    // one wavenumber per element of each level (copied; k is their maximum, for reference)
+    const int64_t nf = num_elements(o.dim, n, elements), nc = num_elements(o.dim, n / 2, elements);
+    c->het = true;
+    c->kf.assign(k_fine, k_fine + nf);
+    c->kc.assign(k_coarse, k_coarse + nc);
+    bool ok = true;
+    for (double v : c->kf) ok = ok && std::isfinite(v) && v >= 0;
+    for (double v : c->kc) ok = ok && std::isfinite(v) && v >= 0;
+    if (!ok) {
+      delete c;
+      return HELM_EINVAL;
+    }
+  }
   int rc = setup_impl(c);
   if (rc != HELM_OK) {
     helm_destroy(c);
@@ -888,6 +960,23 @@ static int setup_any(double k, double h, int order, double shift, const helm_opt
 
 int helm_setup(double k, double h, int order, double shift, const helm_opts* opts, helm_t* out) {
   return setup_any(k, h, order, shift, opts, out, false);
+}
+
+int helm_setup_het(int elements, const double* k_fine, const double* k_coarse, double h, int order, double shift,
+                   const helm_opts* opts, helm_t* out) {
+  if (!k_fine || !k_coarse || !(elements == HELM_SIMPLICES || elements == HELM_TENSOR) || !out) return HELM_EINVAL;
+  double kmax = 0;
+  helm_opts o;
+  helm_default_opts(&o);
+  if (opts) o = *opts;
+  const double nn = 1.0 / h;
+  if (!(h > 0) || !(nn < 1e6) || !(o.dim == 2 || o.dim == 3)) return HELM_EINVAL;
+  const int n = (int)std::lround(nn);
+  if (n < 4 || n % 2) return HELM_EINVAL;
+  const int64_t nf = num_elements(o.dim, n, elements);
+  for (int64_t i = 0; i < nf; ++i) kmax = std::max(kmax, std::isfinite(k_fine[i]) ? k_fine[i] : -1.0);
+  if (!(kmax > 0)) return HELM_EINVAL;
+  return setup_any(kmax, h, order, shift, opts, out, false, elements, k_fine, k_coarse);
 }
 
 int helm_operator_setup(double k, double h, int order, double shift, const helm_opts* opts, helm_t* out) {
@@ -977,8 +1066,18 @@ int helm_batch_solve(int count, const helm_t* hs, const void* const* F, void* co
 }
 
 int helm_rhs_planewave(helm_t h, double theta, void* F_host) {
-  if (!h || !F_host) return HELM_EINVAL;
+  if (!h || !F_host || h->het) return HELM_EINVAL;   // (the plane wave needs one wavenumber)
   rhs_planewave(h->dim, h->order, h->n, h->k, theta, (double2*)F_host, h->elements);
+  return HELM_OK;
+}
+
+int helm_rhs_source(helm_t h, double sx, double sy, double sz, void* F_host) {
+  if (!h || !F_host) return HELM_EINVAL;
+  // f = 2 exp(-1000 |x - s|^2) = 2 exp(-|x - s|^2 / (2 sigma^2)) with sigma^2 = 1 / 2000, g = 0
+  double c[3] = {sx, sy, sz};
+  rhs_gaussian(h->dim, h->order, h->n, std::sqrt(1.0 / 2000.0), c, (double2*)F_host, h->elements);
+  double2* F = (double2*)F_host;
+  for (int64_t i = 0; i < h->gf.N; ++i) F[i] = make_double2(2.0 * F[i].x, 2.0 * F[i].y);
   return HELM_OK;
 }
 
@@ -1076,8 +1175,8 @@ int helm_load_gaussian(int dim, int order, double h, double sigma, double cx, do
 
 int helm_apply(helm_t h, int which, const void* x, void* y) {
   if (!h || !x || !y || (which != 0 && which != 1)) return HELM_EINVAL;
-  StencilView<double> A = which == 0 ? make_view<double>(h->gf, h->coefA0, nullptr)
-                                     : make_view<double>(h->gf, h->p64.coefAe, nullptr);
+  StencilView<double> A = which == 0 ? make_view<double>(h->gf, h->coefA0, nullptr, h->hrowA0)
+                                     : make_view<double>(h->gf, h->p64.coefAe, nullptr, h->hrowA0);
   launch_apply<double, double2, double2>(A, vsel<const double2>((const double2*)x), vsel<double2>((double2*)y),
                                          nullptr, h->s);
   CK(cudaGetLastError());

@@ -209,6 +209,22 @@ __device__ __forceinline__ int class_at(const GridDesc& g, const int* a) {
   }
   return cls;
 }
+// Lexicographic lattice index of point a (x fastest).
+__device__ __forceinline__ int64_t lattice_index(const GridDesc& g, const int* a) {
+  int64_t p = 0;
+  for (int ax = g.dim - 1; ax >= 0; --ax) p = p * g.W + a[ax];
+  return p;
+}
+// Coefficient o of lattice point a's row: the class stencil plus, for a heterogeneous
+// wavenumber, the point's own row (complex128, converted to the arithmetic A).
+template <typename A>
+__device__ __forceinline__ typename A::V coef_of(const StencilView<double>& Ac, const typename A::V* cls_row,
+                                                 const int* a, int o) {
+  typename A::V v = cls_row[o];
+  if (Ac.hrow) v = A::add(v, A::from(Ac.hrow[lattice_index(Ac.g, a) * Ac.g.noff + o]));
+  return v;
+}
+
 // Neighbour of lattice point a along box offset o: returns its block and in-block index.
 __device__ __forceinline__ bool neighbour(const GridDesc& g, const CoarseLayout& L,
                                           const int (*dx)[3], int o, const int* a, int* Jn, int* in) {
@@ -243,6 +259,7 @@ struct ArithD {
   __device__ static V mul(V a, V b) { return cmul(a, b); }
   __device__ static V fma(V a, V b, V c) { return cfma(a, b, c); }   // c + a b
   __device__ static V sub(V a, V b) { return csub(a, b); }
+  __device__ static V add(V a, V b) { return cadd(a, b); }
   __device__ static bool inv(V d, V* out) {
     const double mag = d.x * d.x + d.y * d.y;
     if (!(mag > 0.0) || !isfinite(mag)) return false;
@@ -273,6 +290,7 @@ struct ArithDF {
   __device__ static V mul(V a, V b) { return dfc_mul(a, b); }
   __device__ static V fma(V a, V b, V c) { return dfc_fma(a, b, c); }
   __device__ static V sub(V a, V b) { return dfc_sub(a, b); }
+  __device__ static V add(V a, V b) { return dfc_add(a, b); }
   __device__ static bool inv(V d, V* out) { return dfc_inv(d, out); }
   using Acc = DFC_ACC;
   __device__ static Acc acc(V c) { return dfc_acc(c); }
@@ -370,7 +388,7 @@ __global__ void __launch_bounds__(kFactorThreads, 1) k_factor_block(typename A::
         for (int o = 0; o < g.noff; ++o) {
           int Jn, in;
           if (!neighbour(g, L, Ac.dx, o, c, &Jn, &in) || Jn != J + d) continue;
-          acc = A::fma(cl[o], X[(int64_t)aa * ldb + in], acc);
+          acc = A::fma(coef_of<A>(Ac, cl, c, o), X[(int64_t)aa * ldb + in], acc);
         }
       }
       Tmp[(int64_t)aa * ldb + l] = acc;
@@ -403,7 +421,7 @@ __global__ void __launch_bounds__(kFactorThreads, 1) k_factor_block(typename A::
           o += (dd + g.R) * mul;
           mul *= 2 * g.R + 1;
         }
-        if (in) v = c[o];
+        if (in) v = coef_of<A>(Ac, c, ci, o);
       }
     }
     S[idx] = v;
@@ -430,7 +448,7 @@ __global__ void __launch_bounds__(kFactorThreads, 1) k_factor_block(typename A::
         for (int oo = 0; oo < g.noff; ++oo) {
           int Jn, inb;
           if (!neighbour(g, L, Ac.dx, oo, ci, &Jn, &inb) || Jn != J + d) continue;
-          A::fnmac(c[oo], Tmp[(int64_t)inb * ldb + l], acc);
+          A::fnmac(coef_of<A>(Ac, c, ci, oo), Tmp[(int64_t)inb * ldb + l], acc);
         }
         v = A::fin(acc);
         S[idx] = v;
@@ -713,7 +731,7 @@ __global__ void __launch_bounds__(256) k_couple(const typename A::V* __restrict_
       for (int o = 0; o < g.noff; ++o) {
         int Jn, in;
         if (!neighbour(g, L, Ac.dx, o, c, &Jn, &in) || Jn != J) continue;
-        acc = A::fma(cl[o], Drow[in], acc);
+        acc = A::fma(coef_of<A>(Ac, cl, c, o), Drow[in], acc);
       }
     }
     (which == 0 ? Lm : Up)[rem] = A::out(acc);

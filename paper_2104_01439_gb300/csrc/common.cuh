@@ -104,6 +104,11 @@ template <typename T> struct StencilView {
   GridDesc g;
   int off[kMaxOff];    // linear index offset of box point o
   int dx[kMaxOff][3];  // per-axis offset of box point o
+  // Heterogeneous wavenumber (k per element): the operator is the class stencil plus a per-DoF
+  // row, hrow[p * noff + o], in the same box layout (the k-dependent part -M_k - i B_k; null for
+  // constant k). hwd[p] then replaces the class table's omega / diag.
+  const c2<T>* hrow;
+  const c2<T>* hwd;
 };
 
 // Prolongation (canonical interpolation V_2h -> V_h) as per-class weights.

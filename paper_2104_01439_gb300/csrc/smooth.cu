@@ -131,7 +131,8 @@ template <int R, typename T> struct Strip {
 template <int R, typename T, bool FAST, typename Emit>
 __device__ __forceinline__ void sweep_region(const c2<T>* __restrict__ u, int RY, int m, const int* cx, const int* cy,
                                              const c2<T>* coef, const c2<T> (&creg)[(2 * R + 1) * (2 * R + 1)],
-                                             const Sym9& sym, Emit emit) {
+                                             const Sym9& sym, const c2<T>* __restrict__ hrow, int gx0, int gy0,
+                                             int W, Emit emit) {
   using V = c2<T>;
   constexpr int SIDE = 2 * R + 1, NO = SIDE * SIDE, VS = Strip<R, T>::VS;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
@@ -191,6 +192,13 @@ __device__ __forceinline__ void sweep_region(const c2<T>* __restrict__ u, int RY
           for (int dy = 0; dy < SIDE; ++dy)
 #pragma unroll
             for (int dx = 0; dx < SIDE; ++dx) acc = cfma(c[dy * SIDE + dx], win[v + dy][dx], acc);
+          if (hrow) {   // heterogeneous wavenumber: the point's own row
+            const V* hr = hrow + ((int64_t)(gy0 + ly) * W + gx0 + lx) * NO;
+#pragma unroll
+            for (int dy = 0; dy < SIDE; ++dy)
+#pragma unroll
+              for (int dx = 0; dx < SIDE; ++dx) acc = cfma(hr[dy * SIDE + dx], win[v + dy][dx], acc);
+          }
           emit(ly, lx, cxv + cyv, acc, win[v + R][R]);
         }
       }
@@ -223,7 +231,7 @@ __global__ void __launch_bounds__(kTileThreads, sizeof(T) == 4 ? (R == 1 ? 4 : 3
   const V zero = mk(T(0), T(0));
 
   for (int i = tid; i < ncls * NO; i += blockDim.x) coef[i] = s.coef[i];
-  for (int i = tid; i < ncls; i += blockDim.x) dinv[i] = s.wdinv[i];
+  for (int i = tid; i < ncls && s.wdinv; i += blockDim.x) dinv[i] = s.wdinv[i];
   for (int i = tid; i < RX; i += blockDim.x) {
     const int gx = gx0 + i;
     cx[i] = gx >= 0 && gx < W ? axis_class(gx, W, R, g.q) : -1;
@@ -235,7 +243,11 @@ __global__ void __launch_bounds__(kTileThreads, sizeof(T) == 4 ? (R == 1 ? 4 : 3
   // one class for the whole staged region: a period-1 lattice whose region lies inside the
   // interior band [R, W - R) on both axes
   // (reach 1 only: a reach-2 stencil belongs to a period-2 lattice, whose classes alternate)
-  bool fast = R == 1 && g.q == 1 && gx0 >= R && gx0 + RX <= W - R && gy0 >= R && gy0 + RY <= W - R;
+  bool fast = !s.hrow && R == 1 && g.q == 1 && gx0 >= R && gx0 + RX <= W - R && gy0 >= R && gy0 + RY <= W - R;
+  // omega / diag of a staged point: per DoF for a heterogeneous wavenumber, else per class
+  auto dg = [&](int cls, int ly, int lx) -> V {
+    return s.hwd ? s.hwd[(int64_t)(gy0 + ly) * W + gx0 + lx] : dinv[cls];
+  };
   // f on the whole region, zero outside the domain: every load of the thread is issued
   // before the first store (rows warp + 8 i, i < kLoadRows)
   const Vf* f = fs.ptr();
@@ -325,7 +337,7 @@ __global__ void __launch_bounds__(kTileThreads, sizeof(T) == 4 ? (R == 1 ? 4 : 3
 #pragma unroll
       for (int half = 0; half < 2; ++half) {
         const int lx = lane + 32 * half, cxv = cx[lx];
-        cur[ly * RX + lx] = (cxv >= 0 && cyv >= 0) ? cmul(fast ? dreg : dinv[cxv + cyv], fsm[ly * RX + lx]) : zero;
+        cur[ly * RX + lx] = (cxv >= 0 && cyv >= 0) ? cmul(fast ? dreg : dg(cxv + cyv, ly, lx), fsm[ly * RX + lx]) : zero;
       }
     }
     done = 1;
@@ -336,15 +348,17 @@ __global__ void __launch_bounds__(kTileThreads, sizeof(T) == 4 ? (R == 1 ? 4 : 3
     V* out = nxt;
     const V* in = cur;
     if (fast)
-      sweep_region<R, T, true>(in, RY, k * R, cx, cy, coef, creg, sym, [&](int ly, int lx, int, V Au, V uc) {
-        const int i = ly * RX + lx;
-        out[i] = jacobi_step(dreg, fsm[i], Au, uc);
-      });
+      sweep_region<R, T, true>(in, RY, k * R, cx, cy, coef, creg, sym, s.hrow, gx0, gy0, W,
+                               [&](int ly, int lx, int, V Au, V uc) {
+                                 const int i = ly * RX + lx;
+                                 out[i] = jacobi_step(dreg, fsm[i], Au, uc);
+                               });
     else
-      sweep_region<R, T, false>(in, RY, k * R, cx, cy, coef, creg, sym, [&](int ly, int lx, int cls, V Au, V uc) {
-        const int i = ly * RX + lx;
-        out[i] = cls < 0 ? zero : jacobi_step(dinv[cls], fsm[i], Au, uc);
-      });
+      sweep_region<R, T, false>(in, RY, k * R, cx, cy, coef, creg, sym, s.hrow, gx0, gy0, W,
+                                [&](int ly, int lx, int cls, V Au, V uc) {
+                                  const int i = ly * RX + lx;
+                                  out[i] = cls < 0 ? zero : jacobi_step(dg(cls, ly, lx), fsm[i], Au, uc);
+                                });
     V* t = cur;
     cur = nxt;
     nxt = t;
@@ -361,9 +375,9 @@ __global__ void __launch_bounds__(kTileThreads, sizeof(T) == 4 ? (R == 1 ? 4 : 3
       rout[p] = csub(fsm[i], Au);
     };
     if (fast)
-      sweep_region<R, T, true>(cur, RY, H, cx, cy, coef, creg, sym, emit);
+      sweep_region<R, T, true>(cur, RY, H, cx, cy, coef, creg, sym, s.hrow, gx0, gy0, W, emit);
     else
-      sweep_region<R, T, false>(cur, RY, H, cx, cy, coef, creg, sym, emit);
+      sweep_region<R, T, false>(cur, RY, H, cx, cy, coef, creg, sym, s.hrow, gx0, gy0, W, emit);
   } else {
     for (int ly = H + warp; ly < H + TY; ly += nw) {
       if (cy[ly] < 0) continue;
@@ -414,7 +428,8 @@ bool launch_smooth_tile(const StencilView<T>& A, VecSel<const Vf> f, const c2<T>
                         const CoarseLayout* L, const c2<T>* uc, int nu, VecSel<Vout> out, c2<T>* r,
                         const int* active, cudaStream_t s) {
   const GridDesc& g = A.g;
-  if (g.dim != 2 || (g.R != 1 && g.R != 2) || nu < 1 || !A.wdinv || (uc && (!u0 || !P || !L))) return false;
+  if (g.dim != 2 || (g.R != 1 && g.R != 2) || nu < 1 || (!A.wdinv && !A.hwd) || (uc && (!u0 || !P || !L)))
+    return false;
   // sweeps with neighbours: all of them from a start vector, all but the first from zero
   const int full = u0 ? nu : nu - 1;
   const int H = full * g.R + (r ? g.R : 0);

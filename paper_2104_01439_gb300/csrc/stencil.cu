@@ -91,6 +91,15 @@ __device__ __forceinline__ c2<T> row_apply(const StencilView<T>& s, const c2<T>*
   }
   return acc;
 }
+// the per-DoF part of a heterogeneous-wavenumber operator, added to a class-stencil row
+template <int NOFF, typename T, typename Vin>
+__device__ __forceinline__ c2<T> het_apply(const StencilView<T>& s, int p, int N, const Vin* __restrict__ x,
+                                           c2<T> acc) {
+  const c2<T>* h = s.hrow + (int64_t)p * NOFF;
+#pragma unroll
+  for (int o = 0; o < NOFF; ++o) acc = cfma(h[o], to<c2<T>>(x[min(max(p + s.off[o], 0), N - 1)]), acc);
+  return acc;
+}
 
 // the product's double-float split (hi + lo), read by the Gram-Schmidt inner products
 __device__ __forceinline__ void store_split(float4* ws, int p, double2 v) { ws[p] = dfc_from(v); }
@@ -118,7 +127,8 @@ __global__ void __launch_bounds__(kThreads) k_apply(StencilView<T> s, VecSel<con
     int a[3];
     int cls = decode(s.g, p, a);
     const bool real = sizeof(T) == sizeof(double) && real_cls[cls] != 0;
-    const c2<T> v = row_apply<NOFF>(s, coef + cls * NOFF, p, N, x, real);
+    c2<T> v = row_apply<NOFF>(s, coef + cls * NOFF, p, N, x, real);
+    if (s.hrow) v = het_apply<NOFF>(s, p, N, x, v);
     if (y) y[p] = to<Vout>(v);
     if (ws) store_split(ws, p, v);
   }
@@ -167,6 +177,17 @@ __global__ void __launch_bounds__(kThreads) k_apply_df(StencilView<double> s, Ve
         df_mac(c[o].y, c[o].w, xv[o].x, 0.f, acc.im);
       }
     }
+    if (s.hrow) {   // heterogeneous wavenumber: the DoF's own row, split into double-float pairs
+      const double2* hr = s.hrow + (int64_t)p * NOFF;
+#pragma unroll
+      for (int o = 0; o < NOFF; ++o) {
+        const float4 h = dfc_from(hr[o]);
+        df_mac(h.x, h.z, xv[o].x, 0.f, acc.re);
+        df_mac(-h.y, -h.w, xv[o].y, 0.f, acc.re);
+        df_mac(h.x, h.z, xv[o].y, 0.f, acc.im);
+        df_mac(h.y, h.w, xv[o].x, 0.f, acc.im);
+      }
+    }
     ws[p] = dfc_fin(acc);
   }
 }
@@ -186,6 +207,7 @@ __global__ void __launch_bounds__(kThreads) k_residual(StencilView<T> s, VecSel<
     int a[3];
     int cls = decode(s.g, p, a);
     c2<T> Au = row_apply<NOFF>(s, coef + cls * NOFF, p, N, u);
+    if (s.hrow) Au = het_apply<NOFF>(s, p, N, u, Au);
     r[p] = to<Vr>(csub(to<c2<T>>(f[p]), Au));
   }
 }
@@ -210,7 +232,8 @@ __global__ void __launch_bounds__(kThreads) k_jacobi0(StencilView<T> s, VecSel<c
     int cls = decode(s.g, p, a);
     c2<T> fp = to<c2<T>>(f[p]);
     if (fcopy) fcopy[p] = fp;
-    c2<T> u1 = cmul(dinv[cls], fp);
+    const c2<T> dp = s.hwd ? s.hwd[p] : dinv[cls];
+    c2<T> u1 = cmul(dp, fp);
     if (!two) {
       uout[p] = u1;
       continue;
@@ -222,10 +245,11 @@ __global__ void __launch_bounds__(kThreads) k_jacobi0(StencilView<T> s, VecSel<c
       int na[3];
       for (int ax = 0; ax < 3; ++ax) na[ax] = ax < s.g.dim ? min(max(a[ax] + s.dx[o][ax], 0), s.g.W - 1) : 0;
       int q = min(max(p + s.off[o], 0), N - 1);
-      c2<T> uq = cmul(dinv[class_of(s.g, na)], to<c2<T>>(f[q]));
+      c2<T> uq = cmul(s.hwd ? s.hwd[q] : dinv[class_of(s.g, na)], to<c2<T>>(f[q]));
       Au = cfma(c[o], uq, Au);
+      if (s.hrow) Au = cfma(s.hrow[(int64_t)p * NOFF + o], uq, Au);
     }
-    uout[p] = cfma(dinv[cls], csub(fp, Au), u1);
+    uout[p] = cfma(dp, csub(fp, Au), u1);
   }
 }
 
@@ -246,7 +270,8 @@ __global__ void __launch_bounds__(kThreads) k_jacobi(StencilView<T> s, VecSel<co
     int a[3];
     int cls = decode(s.g, p, a);
     c2<T> Au = row_apply<NOFF>(s, coef + cls * NOFF, p, N, u);
-    out[p] = to<Vout>(cfma(dinv[cls], csub(to<c2<T>>(f[p]), Au), u[p]));
+    if (s.hrow) Au = het_apply<NOFF>(s, p, N, u, Au);
+    out[p] = to<Vout>(cfma(s.hwd ? s.hwd[p] : dinv[cls], csub(to<c2<T>>(f[p]), Au), u[p]));
   }
 }
 
