@@ -648,6 +648,7 @@ static int setup_impl(helm_ctx* h) {
   CK(cudaDeviceGetAttribute(&h->nsm, cudaDevAttrMultiProcessorCount, h->dev));
   smooth_tile_prepare<float>();
   smooth_tile_prepare<double>();
+  stencil_prepare();
   CK(cudaEventCreate(&h->e0));
   CK(cudaEventCreate(&h->e1));
   cudaStream_t s = h->s;
@@ -919,7 +920,9 @@ static int setup_any(double k, double h, int order, double shift, const helm_opt
   double nn = 1.0 / h;
   int n = (int)std::lround(nn);
   if (std::fabs(nn - n) > 1e-9 * nn || n < 4 || n % 2) return HELM_EINVAL;
-  if (!(o.dim == 2 || o.dim == 3) || !(order == 1 || order == 2) || (o.dim == 3 && order != 1)) return HELM_EINVAL;
+  const bool q3 = elements == HELM_TENSOR && o.dim == 2 && order == 3;   // Q3 (2D, Gauss-Lobatto nodes)
+  if (!(o.dim == 2 || o.dim == 3) || !(order == 1 || order == 2 || q3) || (o.dim == 3 && order != 1))
+    return HELM_EINVAL;
   if (o.nu < 1 || o.nu > 8 || o.restart < 1 || o.restart > 512 || o.maxit < 1 || !(o.tol > 0) ||
       !(o.omega > 0) || !(o.precision == HELM_FP64 || o.precision == HELM_MIXED))
     return HELM_EINVAL;
@@ -1110,7 +1113,7 @@ int helm_load_planewave(int dim, int order, double h, double k, double theta, vo
 }
 
 int helm_load_planewave_e(int dim, int order, int elements, double h, double k, double theta, void* F_host) {
-  const int n = mesh_n(dim, order, h);
+  const int n = mesh_n(dim, order, h, elements == HELM_TENSOR);
   if (n < 0 || !(elements == HELM_SIMPLICES || elements == HELM_TENSOR) || !F_host || !(k > 0)) return HELM_EINVAL;
   rhs_planewave(dim, order, n, k, theta, (double2*)F_host, elements);
   return HELM_OK;
@@ -1118,7 +1121,7 @@ int helm_load_planewave_e(int dim, int order, int elements, double h, double k, 
 
 int helm_load_gaussian_e(int dim, int order, int elements, double h, double sigma, double cx, double cy, double cz,
                          void* F_host) {
-  const int n = mesh_n(dim, order, h);
+  const int n = mesh_n(dim, order, h, elements == HELM_TENSOR);
   if (n < 0 || !(elements == HELM_SIMPLICES || elements == HELM_TENSOR) || !F_host || !(sigma > 0))
     return HELM_EINVAL;
   double c[3] = {cx, cy, cz};

@@ -1761,6 +1761,7 @@ void launch_couple(const typename A::V* D, TO* Lm, TO* Up, const StencilView<dou
   int ncls = 1;
   for (int ax = 0; ax < Ac.g.dim; ++ax) ncls *= Ac.g.C1;
   const size_t smem = sizeof(typename A::V) * (size_t)ncls * Ac.g.noff;
+  if (smem > 48 * 1024) cudaFuncSetAttribute(k_couple<A, TO>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   k_couple<A, TO><<<nsm * 8, 256, smem, s>>>(D, Lm, Up, Ac, L);
 }
 

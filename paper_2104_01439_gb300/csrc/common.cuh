@@ -71,10 +71,10 @@ template <typename To, typename From> __device__ inline To to(From v) { return c
 // classes. Every DoF of a class has the same stencil (constant k, uniform
 // mesh), with noff = (2R+1)^dim offsets in lexicographic box order.
 // ----------------------------------------------------------------------------
-constexpr int kMaxOff = 27;   // (2*1+1)^3 or (2*2+1)^2 = 25
-constexpr int kMaxCls = 36;   // (2*2+2)^2 = 36 or (2+1)^3 = 27
-constexpr int kMaxPW = 16;    // prolongation classes: (2q)^dim <= 16
-constexpr int kMaxPO = 9;     // prolongation offsets: (q+1)^dim <= 9
+constexpr int kMaxOff = 49;   // (2*1+1)^3 = 27, (2*2+1)^2 = 25, (2*3+1)^2 = 49 (Q3)
+constexpr int kMaxCls = 81;   // (2*2+2)^2 = 36, (2+1)^3 = 27, (2*3+3)^2 = 81 (Q3)
+constexpr int kMaxPW = 36;    // prolongation classes: (2q)^dim <= 36
+constexpr int kMaxPO = 16;    // prolongation offsets: (q+1)^dim <= 16
 
 struct GridDesc {
   int dim;      // 2 or 3

@@ -58,7 +58,8 @@ void launch_restrict(const TransferView<T>& P, const CoarseLayout& L, const c2<T
 // given, the residual f - A u^nu. Returns false (nothing launched) where it does not apply
 // (3D, or a tile that does not fit shared memory): the caller then runs the per-sweep kernels.
 template <typename T>
-void smooth_tile_prepare();   // raises the kernels' shared-memory limit (outside stream capture)
+void smooth_tile_prepare();
+void stencil_prepare();   // (the same for the per-sweep and apply kernels' 49-point tables)   // raises the kernels' shared-memory limit (outside stream capture)
 template <typename T, typename Vf, typename Vout>
 bool launch_smooth_tile(const StencilView<T>& A, VecSel<const Vf> f, const c2<T>* u0, const TransferView<T>* P,
                         const CoarseLayout* L, const c2<T>* uc, int nu, VecSel<Vout> out, c2<T>* r,

@@ -16,6 +16,7 @@
 // along each axis) from two per-axis arrays; points outside the domain hold zero, which is
 // what the class stencils assume (their coefficients towards outside points are zero).
 #include <algorithm>
+#include <type_traits>
 
 #include "kernels.cuh"
 
@@ -118,7 +119,7 @@ constexpr int kLoadRows = 10;  // staged rows per warp: RY = TY + 2H <= 8 * kLoa
 
 // rows of the vertical strip one thread computes in a sweep (register blocking)
 template <int R, typename T> struct Strip {
-  static constexpr int VS = sizeof(T) == 8 ? (R == 1 ? 2 : 1) : (R == 1 ? 4 : 2);
+  static constexpr int VS = R >= 3 ? 1 : sizeof(T) == 8 ? (R == 1 ? 2 : 1) : (R == 1 ? 4 : 2);
 };
 
 // One sweep region of the tile: rows [m, RY - m), columns [m, kRegionX - m) of the staged
@@ -128,7 +129,7 @@ template <int R, typename T> struct Strip {
 // coefficients the caller holds in registers (creg, indexed by compile-time offsets only);
 // otherwise each point's class comes from the per-axis arrays and its stencil from shared
 // memory, and points outside the domain are emitted with class -1.
-template <int R, typename T, bool FAST, typename Emit>
+template <int R, typename T, bool FAST, bool HET, typename Emit>
 __device__ __forceinline__ void sweep_region(const c2<T>* __restrict__ u, int RY, int m, const int* cx, const int* cy,
                                              const c2<T>* coef, const c2<T> (&creg)[(2 * R + 1) * (2 * R + 1)],
                                              const Sym9& sym, const c2<T>* __restrict__ hrow, int gx0, int gy0,
@@ -192,7 +193,7 @@ __device__ __forceinline__ void sweep_region(const c2<T>* __restrict__ u, int RY
           for (int dy = 0; dy < SIDE; ++dy)
 #pragma unroll
             for (int dx = 0; dx < SIDE; ++dx) acc = cfma(c[dy * SIDE + dx], win[v + dy][dx], acc);
-          if (hrow) {   // heterogeneous wavenumber: the point's own row
+          if constexpr (HET) {   // heterogeneous wavenumber: the point's own row
             const V* hr = hrow + ((int64_t)(gy0 + ly) * W + gx0 + lx) * NO;
 #pragma unroll
             for (int dy = 0; dy < SIDE; ++dy)
@@ -206,8 +207,9 @@ __device__ __forceinline__ void sweep_region(const c2<T>* __restrict__ u, int RY
   }
 }
 
-template <int R, typename T, typename Vf, typename Vout>
-__global__ void __launch_bounds__(kTileThreads, sizeof(T) == 4 ? (R == 1 ? 4 : 3) : 2) k_smooth_tile(StencilView<T> s, VecSel<const Vf> fs,
+template <int R, typename T, typename Vf, typename Vout, bool HET>
+__global__ void __launch_bounds__(kTileThreads, sizeof(T) == 4 ? (R == 1 ? 4 : R == 2 ? 3 : 2) : (R == 3 ? 1 : 2))
+    k_smooth_tile(StencilView<T> s, VecSel<const Vf> fs,
                                                                const c2<T>* __restrict__ u0, TransferView<T> P,
                                                                CoarseLayout L, const c2<T>* __restrict__ uc, int nu,
                                                                int TY, int H, VecSel<Vout> outs,
@@ -243,10 +245,14 @@ __global__ void __launch_bounds__(kTileThreads, sizeof(T) == 4 ? (R == 1 ? 4 : 3
   // one class for the whole staged region: a period-1 lattice whose region lies inside the
   // interior band [R, W - R) on both axes
   // (reach 1 only: a reach-2 stencil belongs to a period-2 lattice, whose classes alternate)
-  bool fast = !s.hrow && R == 1 && g.q == 1 && gx0 >= R && gx0 + RX <= W - R && gy0 >= R && gy0 + RY <= W - R;
+  // (HET: a heterogeneous wavenumber, whose per-DoF rows and diagonal the kernel reads; the
+  // constant-k instantiations carry none of that code)
+  const V* hrow = HET ? s.hrow : nullptr;
+  bool fast = !HET && R == 1 && g.q == 1 && gx0 >= R && gx0 + RX <= W - R && gy0 >= R && gy0 + RY <= W - R;
   // omega / diag of a staged point: per DoF for a heterogeneous wavenumber, else per class
   auto dg = [&](int cls, int ly, int lx) -> V {
-    return s.hwd ? s.hwd[(int64_t)(gy0 + ly) * W + gx0 + lx] : dinv[cls];
+    if constexpr (HET) return s.hwd[(int64_t)(gy0 + ly) * W + gx0 + lx];
+    else return dinv[cls];
   };
   // f on the whole region, zero outside the domain: every load of the thread is issued
   // before the first store (rows warp + 8 i, i < kLoadRows)
@@ -348,13 +354,13 @@ __global__ void __launch_bounds__(kTileThreads, sizeof(T) == 4 ? (R == 1 ? 4 : 3
     V* out = nxt;
     const V* in = cur;
     if (fast)
-      sweep_region<R, T, true>(in, RY, k * R, cx, cy, coef, creg, sym, s.hrow, gx0, gy0, W,
+      sweep_region<R, T, true, HET>(in, RY, k * R, cx, cy, coef, creg, sym, hrow, gx0, gy0, W,
                                [&](int ly, int lx, int, V Au, V uc) {
                                  const int i = ly * RX + lx;
                                  out[i] = jacobi_step(dreg, fsm[i], Au, uc);
                                });
     else
-      sweep_region<R, T, false>(in, RY, k * R, cx, cy, coef, creg, sym, s.hrow, gx0, gy0, W,
+      sweep_region<R, T, false, HET>(in, RY, k * R, cx, cy, coef, creg, sym, hrow, gx0, gy0, W,
                                 [&](int ly, int lx, int cls, V Au, V uc) {
                                   const int i = ly * RX + lx;
                                   out[i] = cls < 0 ? zero : jacobi_step(dg(cls, ly, lx), fsm[i], Au, uc);
@@ -375,9 +381,9 @@ __global__ void __launch_bounds__(kTileThreads, sizeof(T) == 4 ? (R == 1 ? 4 : 3
       rout[p] = csub(fsm[i], Au);
     };
     if (fast)
-      sweep_region<R, T, true>(cur, RY, H, cx, cy, coef, creg, sym, s.hrow, gx0, gy0, W, emit);
+      sweep_region<R, T, true, HET>(cur, RY, H, cx, cy, coef, creg, sym, hrow, gx0, gy0, W, emit);
     else
-      sweep_region<R, T, false>(cur, RY, H, cx, cy, coef, creg, sym, s.hrow, gx0, gy0, W, emit);
+      sweep_region<R, T, false, HET>(cur, RY, H, cx, cy, coef, creg, sym, hrow, gx0, gy0, W, emit);
   } else {
     for (int ly = H + warp; ly < H + TY; ly += nw) {
       if (cy[ly] < 0) continue;
@@ -412,13 +418,25 @@ void smooth_tile_prepare() {
     cudaDeviceGetAttribute(&g_smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
   }
   const int lim = std::max(0, g_smem_optin - 1024);
-  cudaFuncSetAttribute(k_smooth_tile<1, T, double2, double2>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
-  cudaFuncSetAttribute(k_smooth_tile<2, T, double2, double2>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
-  cudaFuncSetAttribute(k_smooth_tile<1, T, double2, c2<T>>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
-  cudaFuncSetAttribute(k_smooth_tile<2, T, double2, c2<T>>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
-  if constexpr (sizeof(T) == sizeof(float)) {   // the complex64 V-cycle reads f from a double-float slot
-    cudaFuncSetAttribute(k_smooth_tile<1, T, float4, c2<T>>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
-    cudaFuncSetAttribute(k_smooth_tile<2, T, float4, c2<T>>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
+  auto set = [&](auto kern) { cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, lim); };
+  auto all_r = [&](auto vf, auto vout, auto het) {
+    using VF = decltype(vf);
+    using VO = decltype(vout);
+    constexpr bool HT = decltype(het)::value;
+    set(k_smooth_tile<1, T, VF, VO, HT>);
+    set(k_smooth_tile<2, T, VF, VO, HT>);
+    set(k_smooth_tile<3, T, VF, VO, HT>);
+  };
+  for (int het = 0; het < 2; ++het) {
+    auto with = [&](auto h) {
+      all_r(double2{}, double2{}, h);
+      all_r(double2{}, c2<T>{}, h);
+      if constexpr (sizeof(T) == sizeof(float)) all_r(float4{}, c2<T>{}, h);   // the complex64 V-cycle's f
+    };
+    if (het)
+      with(std::true_type{});
+    else
+      with(std::false_type{});
   }
   cudaGetLastError();
 }
@@ -428,7 +446,7 @@ bool launch_smooth_tile(const StencilView<T>& A, VecSel<const Vf> f, const c2<T>
                         const CoarseLayout* L, const c2<T>* uc, int nu, VecSel<Vout> out, c2<T>* r,
                         const int* active, cudaStream_t s) {
   const GridDesc& g = A.g;
-  if (g.dim != 2 || (g.R != 1 && g.R != 2) || nu < 1 || (!A.wdinv && !A.hwd) || (uc && (!u0 || !P || !L)))
+  if (g.dim != 2 || g.R < 1 || g.R > 3 || nu < 1 || (!A.wdinv && !A.hwd) || (uc && (!u0 || !P || !L)))
     return false;
   // sweeps with neighbours: all of them from a start vector, all but the first from zero
   const int full = u0 ? nu : nu - 1;
@@ -459,10 +477,19 @@ bool launch_smooth_tile(const StencilView<T>& A, VecSel<const Vf> f, const c2<T>
   const dim3 grid((g.W + TX - 1) / TX, (g.W + TY - 1) / TY);
   TransferView<T> pv = P ? *P : TransferView<T>{};
   CoarseLayout lv = L ? *L : CoarseLayout{};
-  if (g.R == 1)
-    k_smooth_tile<1, T, Vf, Vout><<<grid, kTileThreads, smem, s>>>(A, f, u0, pv, lv, uc, nu, TY, H, out, r, active);
+  auto go = [&](auto het) {
+    constexpr bool HT = decltype(het)::value;
+    if (g.R == 1)
+      k_smooth_tile<1, T, Vf, Vout, HT><<<grid, kTileThreads, smem, s>>>(A, f, u0, pv, lv, uc, nu, TY, H, out, r, active);
+    else if (g.R == 2)
+      k_smooth_tile<2, T, Vf, Vout, HT><<<grid, kTileThreads, smem, s>>>(A, f, u0, pv, lv, uc, nu, TY, H, out, r, active);
+    else
+      k_smooth_tile<3, T, Vf, Vout, HT><<<grid, kTileThreads, smem, s>>>(A, f, u0, pv, lv, uc, nu, TY, H, out, r, active);
+  };
+  if (A.hrow)
+    go(std::true_type{});
   else
-    k_smooth_tile<2, T, Vf, Vout><<<grid, kTileThreads, smem, s>>>(A, f, u0, pv, lv, uc, nu, TY, H, out, r, active);
+    go(std::false_type{});
   return true;
 }
 

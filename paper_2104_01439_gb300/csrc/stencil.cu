@@ -398,12 +398,13 @@ size_t table_smem(const GridDesc& g, bool with_dinv) {
 
 }  // namespace
 
-#define HELM_SWITCH_NOFF(noff, CALL9, CALL25, CALL27) \
-  switch (noff) {                                      \
-    case 9: CALL9; break;                              \
-    case 25: CALL25; break;                            \
-    case 27: CALL27; break;                            \
-    default: break;                                    \
+#define HELM_SWITCH_NOFF(noff, CALL9, CALL25, CALL27, CALL49) \
+  switch (noff) {                                              \
+    case 9: CALL9; break;                                      \
+    case 25: CALL25; break;                                    \
+    case 27: CALL27; break;                                    \
+    case 49: CALL49; break;                                    \
+    default: break;                                            \
   }
 
 template <typename T, typename Vin, typename Vout>
@@ -413,7 +414,8 @@ void launch_apply(const StencilView<T>& A, VecSel<const Vin> x, VecSel<Vout> y, 
   size_t sm = table_smem<T>(A.g, false);
   HELM_SWITCH_NOFF(A.g.noff, (k_apply<9, T, Vin, Vout><<<g, kThreads, sm, s>>>(A, x, y, ws, active)),
                    (k_apply<25, T, Vin, Vout><<<g, kThreads, sm, s>>>(A, x, y, ws, active)),
-                   (k_apply<27, T, Vin, Vout><<<g, kThreads, sm, s>>>(A, x, y, ws, active)));
+                   (k_apply<27, T, Vin, Vout><<<g, kThreads, sm, s>>>(A, x, y, ws, active)),
+                   (k_apply<49, T, Vin, Vout><<<g, kThreads, sm, s>>>(A, x, y, ws, active)));
 }
 
 void launch_apply_df(const StencilView<double>& A, VecSel<const float2> x, float4* ws, const int* active,
@@ -422,7 +424,8 @@ void launch_apply_df(const StencilView<double>& A, VecSel<const float2> x, float
   size_t sm = table_smem<double>(A.g, false);   // 16 bytes per coefficient either way
   HELM_SWITCH_NOFF(A.g.noff, (k_apply_df<9><<<g, kThreads, sm, s>>>(A, x, ws, active)),
                    (k_apply_df<25><<<g, kThreads, sm, s>>>(A, x, ws, active)),
-                   (k_apply_df<27><<<g, kThreads, sm, s>>>(A, x, ws, active)));
+                   (k_apply_df<27><<<g, kThreads, sm, s>>>(A, x, ws, active)),
+                   (k_apply_df<49><<<g, kThreads, sm, s>>>(A, x, ws, active)));
 }
 
 template <typename T, typename Vf, typename Vr>
@@ -432,7 +435,8 @@ void launch_residual(const StencilView<T>& A, VecSel<const Vf> f, const c2<T>* u
   size_t sm = table_smem<T>(A.g, false);
   HELM_SWITCH_NOFF(A.g.noff, (k_residual<9, T, Vf, Vr><<<g, kThreads, sm, s>>>(A, f, u, r, active)),
                    (k_residual<25, T, Vf, Vr><<<g, kThreads, sm, s>>>(A, f, u, r, active)),
-                   (k_residual<27, T, Vf, Vr><<<g, kThreads, sm, s>>>(A, f, u, r, active)));
+                   (k_residual<27, T, Vf, Vr><<<g, kThreads, sm, s>>>(A, f, u, r, active)),
+                   (k_residual<49, T, Vf, Vr><<<g, kThreads, sm, s>>>(A, f, u, r, active)));
 }
 
 template <typename T, typename Vf>
@@ -443,7 +447,8 @@ void launch_jacobi_from_zero(const StencilView<T>& A, VecSel<const Vf> f, c2<T>*
   int two = two_steps ? 1 : 0;
   HELM_SWITCH_NOFF(A.g.noff, (k_jacobi0<9, T, Vf><<<g, kThreads, sm, s>>>(A, f, u_out, fcopy, two, active)),
                    (k_jacobi0<25, T, Vf><<<g, kThreads, sm, s>>>(A, f, u_out, fcopy, two, active)),
-                   (k_jacobi0<27, T, Vf><<<g, kThreads, sm, s>>>(A, f, u_out, fcopy, two, active)));
+                   (k_jacobi0<27, T, Vf><<<g, kThreads, sm, s>>>(A, f, u_out, fcopy, two, active)),
+                   (k_jacobi0<49, T, Vf><<<g, kThreads, sm, s>>>(A, f, u_out, fcopy, two, active)));
 }
 
 template <typename T, typename Vf, typename Vout>
@@ -453,7 +458,8 @@ void launch_jacobi(const StencilView<T>& A, VecSel<const Vf> f, const c2<T>* u, 
   size_t sm = table_smem<T>(A.g, true);
   HELM_SWITCH_NOFF(A.g.noff, (k_jacobi<9, T, Vf, Vout><<<g, kThreads, sm, s>>>(A, f, u, out, active)),
                    (k_jacobi<25, T, Vf, Vout><<<g, kThreads, sm, s>>>(A, f, u, out, active)),
-                   (k_jacobi<27, T, Vf, Vout><<<g, kThreads, sm, s>>>(A, f, u, out, active)));
+                   (k_jacobi<27, T, Vf, Vout><<<g, kThreads, sm, s>>>(A, f, u, out, active)),
+                   (k_jacobi<49, T, Vf, Vout><<<g, kThreads, sm, s>>>(A, f, u, out, active)));
 }
 
 template <typename T>
@@ -477,6 +483,25 @@ template <typename Vin, typename Vout>
 void launch_coarse_unpack(const GridDesc& gc, const CoarseLayout& L, const Vin* pad, Vout* nat,
                           cudaStream_t s) {
   k_coarse_unpack<Vin, Vout><<<grid_for(gc.N), kThreads, 0, s>>>(gc, L, pad, nat);
+}
+
+// The 49-point (Q3) class tables exceed the default 48 KB of dynamic shared memory in
+// complex128 (81 classes x 49 offsets x 16 B): raise the limit once, at setup (outside
+// stream capture), for every instantiation that stages them.
+void stencil_prepare() {
+  const int lim = 100 * 1024;
+  cudaFuncSetAttribute(k_apply<49, float, float2, float2>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
+  cudaFuncSetAttribute(k_apply<49, double, double2, double2>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
+  cudaFuncSetAttribute(k_apply_df<49>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
+  cudaFuncSetAttribute(k_residual<49, float, float2, float2>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
+  cudaFuncSetAttribute(k_residual<49, double, double2, double2>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
+  cudaFuncSetAttribute(k_jacobi0<49, float, double2>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
+  cudaFuncSetAttribute(k_jacobi0<49, float, float4>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
+  cudaFuncSetAttribute(k_jacobi0<49, double, double2>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
+  cudaFuncSetAttribute(k_jacobi<49, float, float2, float2>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
+  cudaFuncSetAttribute(k_jacobi<49, float, float2, double2>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
+  cudaFuncSetAttribute(k_jacobi<49, double, double2, double2>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
+  cudaGetLastError();
 }
 
 // ---- explicit instantiations -------------------------------------------------

@@ -829,6 +829,13 @@ int host_prolongation_row(const HostTables& t, int64_t fine_dof, int64_t* cols, 
   return HELM_OK;
 }
 
+// Coordinate of lattice index a along an axis: element a / order, local point a % order at the
+// element's interpolation node (equispaced for P_p and Q1, Q2; Gauss-Lobatto for Q3).
+static double lattice_coord(int a, int order, double h, int elements) {
+  if (elements == HELM_TENSOR && order == 3) return (a / 3 + gll01(3, a % 3)) * h;
+  return (double)a * h / order;
+}
+
 void rhs_planewave(int d, int order, int n, double k, double theta, double2* F, int elements) {
   SMesh m{d, order, n, order * n + 1, 1.0 / n, elements};
   int64_t N = 1;
@@ -840,8 +847,8 @@ void rhs_planewave(int d, int order, int n, double k, double theta, double2* F, 
     int nb = (int)loc.size();
     double dn = dir[0] * nrm[0] + dir[1] * nrm[1] + dir[2] * nrm[2];
     for (int j = 0; j < nb; ++j) {
-      double ph = 0;   // lattice points are equispaced for the orders the load builders take (<= 2)
-      for (int ax = 0; ax < d; ++ax) ph += dir[ax] * loc[j][ax] * m.h / order;
+      double ph = 0;
+      for (int ax = 0; ax < d; ++ax) ph += dir[ax] * lattice_coord(loc[j][ax], order, m.h, elements);
       // g = i k (d.n - 1) exp(i k d.x)
       double gr = -k * (dn - 1.0) * std::sin(k * ph), gi = k * (dn - 1.0) * std::cos(k * ph);
       for (int i = 0; i < nb; ++i) {
@@ -858,14 +865,14 @@ void rhs_gaussian(int d, int order, int n, double sigma, const double* c, double
   std::vector<double> Ks, Ms, Bs;
   int ncls;
   level_stencils(d, order, n, g, Ks, Ms, Bs, ncls, elements);
-  double h = 1.0 / n / order;
+  const double he = 1.0 / n;
   int W = g.W, side = 2 * g.R + 1;
   std::vector<double> f(g.N);
   for (int64_t p = 0; p < g.N; ++p) {
     int64_t t = p;
     double r2 = 0;
     for (int ax = 0; ax < d; ++ax) {
-      double x = (double)(t % W) * h - c[ax];
+      double x = lattice_coord((int)(t % W), order, he, elements) - c[ax];
       t /= W;
       r2 += x * x;
     }

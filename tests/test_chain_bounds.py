@@ -177,7 +177,8 @@ def check_grid_chain(nb, B, ldb, elem):
 
 LAYOUTS = [(2, 1, n) for n in (8, 10, 16, 30, 36, 64, 128, 256, 512, 1024)] + \
           [(2, 2, n) for n in (8, 12, 22, 64, 128, 256, 512, 1024)] + \
-          [(3, 1, n) for n in (8, 12, 16, 32, 48, 96)]
+          [(3, 1, n) for n in (8, 12, 16, 32, 48, 96)] + \
+          [(2, 3, n) for n in (8, 16, 18, 32, 64, 128)]   # Q3: blocks of three lattice lines
 
 
 @pytest.mark.parametrize("dim,order,n", LAYOUTS, ids=lambda v: str(v))

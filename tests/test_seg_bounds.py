@@ -200,7 +200,8 @@ def check_fixup_middle_products(nb, B, ldb, m, pp):
 
 LAYOUTS = [(2, 1, n) for n in (30, 32, 36, 48, 64, 100, 128, 256, 512, 1024, 2046)] + \
           [(2, 2, n) for n in (32, 44, 64, 128, 256, 512)] + \
-          [(3, 1, n) for n in (30, 32, 40, 48, 60, 62)]
+          [(3, 1, n) for n in (30, 32, 40, 48, 60, 62)] + \
+          [(2, 3, n) for n in (32, 34, 64, 128)]   # Q3: blocks of three lattice lines
 
 
 @pytest.mark.parametrize("dim,order,n", LAYOUTS, ids=lambda v: str(v))

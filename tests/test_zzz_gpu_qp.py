@@ -1,11 +1,13 @@
 """GPU parity of the tensor-product Q_p path (helm_setup_q; Sec. 2's Q_p elements) against the
 FP64 CPU oracle oracle/qfem.py, through the C ABI.
 
-The kernels are the ones of the simplex path (9/25/27-point class stencils, the same lattice,
-block layout and transfers); only the host tables differ, and those are pinned row by row on
-the CPU (test_host_tables). Tolerances as in test_gpu_parity, for the same arithmetic:
-operator applies <= 1e-12, FP64 coarse solve / V-cycle <= 1e-9, complex64 <= 2e-5, solves to
-relres 1e-8 with iterations within +-1 (FP64) / +-3 (complex64 preconditioner).
+The kernels are the ones of the simplex path (9/25/27-point class stencils, and 49-point ones
+for Q3, the same lattice, block layout and transfers); only the host tables differ, and those
+are pinned row by row on the CPU (test_host_tables). Q1-Q3 also run with the paper's own
+smoother setting, V(3,3) with omega = 2/3 (Sec. 4, Sec. 7). Tolerances as in test_gpu_parity,
+for the same arithmetic: operator applies <= 1e-12, FP64 coarse solve / V-cycle <= 1e-9,
+complex64 <= 2e-5, solves to relres 1e-8 with iterations within +-1 (FP64) / +-3 (complex64
+preconditioner), all also entry by entry per DoF class.
 """
 import numpy as np
 import pytest
@@ -29,6 +31,16 @@ CASES = [
     hi.Workload("q2_n8", 2, 2, 8, 6.0, 18.0, "random", seed=23),
     hi.Workload("q2_n22_ragged", 2, 2, 22, 10.0, 50.0, "random", seed=24),
     hi.Workload("q1_3d_n6", 3, 1, 6, 4.0, 8.0, "random", seed=25),
+    # Q3 at the Gauss-Lobatto points (49-point stencils, 81 classes, blocks of three lattice lines)
+    hi.Workload("q3_n8", 2, 3, 8, 6.0, 18.0, "random", seed=26),
+    hi.Workload("q3_n18_ragged", 2, 3, 18, 12.0, 72.0, "random", seed=27),
+    hi.Workload("q3_n16", 2, 3, 16, 20.0, 200.0, "planewave"),
+]
+# The paper's own smoother setting, V(3,3) with omega = 2/3 (Sec. 4, Sec. 7), on Q1, Q2, Q3
+V33 = [
+    hi.Workload("q1_n64_v33", 2, 1, 64, 20.0, 20.0 ** 1.5, "planewave", omega=2.0 / 3.0, nu=3),
+    hi.Workload("q2_n32_v33", 2, 2, 32, 20.0, 20.0 ** 1.5, "planewave", omega=2.0 / 3.0, nu=3),
+    hi.Workload("q3_n16_v33", 2, 3, 16, 20.0, 20.0 ** 1.5, "planewave", omega=2.0 / 3.0, nu=3),
 ]
 _PB = {}
 
@@ -53,7 +65,8 @@ def dev(a):
 
 
 def solver_q(wl, **kw):
-    return pkg.Solver(wl.k, wl.n, wl.order, wl.shift, dim=wl.dim, elements=pkg.HELM_TENSOR, **kw)
+    return pkg.Solver(wl.k, wl.n, wl.order, wl.shift, dim=wl.dim, elements=pkg.HELM_TENSOR, omega=wl.omega,
+                      nu=wl.nu, **kw)
 
 
 @pytest.mark.parametrize("wl", CASES, ids=lambda w: w.name)
@@ -70,7 +83,7 @@ def test_apply_q(wl):
 
 
 @pytest.mark.parametrize("prec,tol", [(pkg.HELM_FP64, 1e-9), (pkg.HELM_MIXED, 2e-5)])
-@pytest.mark.parametrize("wl", CASES, ids=lambda w: w.name)
+@pytest.mark.parametrize("wl", CASES + V33, ids=lambda w: w.name)
 def test_coarse_solve_and_vcycle_q(wl, prec, tol):
     pb = problem(wl)
     s = solver_q(wl, precision=prec)
@@ -86,7 +99,8 @@ def test_coarse_solve_and_vcycle_q(wl, prec, tol):
 
 
 @pytest.mark.parametrize("prec", [pkg.HELM_FP64, pkg.HELM_MIXED])
-@pytest.mark.parametrize("wl", [CASES[1], CASES[2], CASES[4], CASES[5]], ids=lambda w: w.name)
+@pytest.mark.parametrize("wl", [CASES[1], CASES[2], CASES[4], CASES[5], CASES[7], CASES[8]] + V33,
+                         ids=lambda w: w.name)
 def test_solve_parity_q(wl, prec):
     pb = problem(wl)
     ref = pb.solve()
@@ -103,8 +117,9 @@ def test_solve_parity_q(wl, prec):
     s.close()
 
 
-def test_rhs_planewave_q():
-    wl = CASES[2]
+@pytest.mark.parametrize("wl", [CASES[2], CASES[8]], ids=lambda w: w.name)
+def test_rhs_planewave_q(wl):
+    """The plane-wave load at the lattice's interpolation nodes (Gauss-Lobatto for Q3)."""
     pb = problem(wl)
     s = solver_q(wl)
     F = s.rhs_planewave(wl.theta).numpy()
