@@ -458,6 +458,9 @@ def run_ours(args):
             legs["serve"] = serve_leg(pkg, args.requests, args.rate, tuple(int(g) for g in args.grids.split(",")),
                                       args.max_active)
         legs["serve"]["clocks"] = ck.summary()
+        with ClockSampler(local) as ck:
+            legs["qp_wedge"] = qp_leg(pkg)
+        legs["qp_wedge"]["clocks"] = ck.summary()
 
     lat = sorted(t * 1e3 for t in t_mixed)
     p99 = lat[min(len(lat) - 1, math.ceil(0.99 * len(lat)) - 1)]
@@ -559,6 +562,52 @@ def sweep_leg(pkg, n_pairs, max_n, fp64_samples, max_active):
                            "batched_mixed_speedup": v / v64},
         "best_shift_fit": {"params": [float(x) for x in params], "loss": loss, "points": len(best)},
     }
+
+
+def wedge_k(k_max, n, dim=2):
+    """k = k_max mu(x) of the wedge profile at the element centres of an n^dim tensor mesh, in
+    the element order helm_setup_het takes (cells lexicographic, x fastest)."""
+    import numpy as np
+    c = (np.arange(n) + 0.5) / n
+    xs = np.stack(np.meshgrid(*([c] * dim), indexing="ij")[::-1], axis=-1).reshape(-1, dim)
+    return k_max * hi.wedge_profile(xs)
+
+
+def qp_leg(pkg, k_max=100.0, steps=2):
+    """The paper's own elements and smoother on its wedge-type problem (Sec. 6, Sec. 7): Q_p,
+    p = 1, 2, 3 (helm_setup_het, HELM_TENSOR) with about 263k DoFs each, k(x) = k_max mu(x) on
+    the synthetic wedge, V(3,3) with omega = 2/3, the shift eps = k_max^sigma from the paper's
+    fitted map (Table tab:optweights at k_max and l = log2 n), the point source of Sec. 6,
+    FGMRES(50) to relres 1e-8. setup + solve per step, mixed and FP64."""
+    import math as _m
+    import torch
+    from paper_2104_01439_gb300 import sweep
+    out = {"workload": f"2D Q_p wedge, k_max={k_max:g}, V(3,3) omega=2/3, eps from the fitted map, point "
+                       f"source, FGMRES(50), relres 1e-8; setup + solve per step"}
+    for p, n in ((1, 512), (2, 256), (3, 170)):
+        eps = sweep.shift_of(sweep.PAPER_SHIFT_WEIGHTS[p], k_max, n)
+        kf, kc = wedge_k(k_max, n), wedge_k(k_max, n // 2)
+        row = {"n": n, "dofs": (p * n + 1) ** 2, "eps": eps}
+        for prec, name in ((pkg.HELM_MIXED, "mixed"), (pkg.HELM_FP64, "fp64")):
+            def step():
+                s = pkg.Solver(k_max, n, p, eps, elements=pkg.HELM_TENSOR, k_fine=kf, k_coarse=kc, omega=2.0 / 3.0,
+                               nu=3, restart=50, maxit=500, tol=1e-8, precision=prec)
+                F = s.rhs_source().cuda()
+                _, r = s.solve(F)
+                setup = s.setup_ms
+                s.close()
+                return r, setup
+            step()                                 # warm-up
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            for _ in range(steps):
+                r, setup = step()
+            torch.cuda.synchronize()
+            dt = (time.perf_counter() - t0) / steps
+            row[name] = {"solves_per_s": 1.0 / dt, "iters": r.iters, "relres_true": r.relres_true,
+                         "status": r.status, "setup_ms": setup}
+        out[f"q{p}"] = row
+    return out
 
 
 def run_sweep_bench(args):
@@ -686,8 +735,9 @@ def main():
     ap.add_argument("--kernel", choices=["coarse", "vcycle", "apply", "stencil", "solve"],
                     help="only launch one hot-path step --steps times (profiling aid)")
     ap.add_argument("--fp64", action="store_true", help="with --kernel: the all-FP64 form")
-    ap.add_argument("--workload", default="solve", choices=["solve", "sweep", "serve"],
-                    help="solve: the headline step (default); sweep: batched shift sweep; serve: serving trace")
+    ap.add_argument("--workload", default="solve", choices=["solve", "sweep", "serve", "qp"],
+                    help="solve: the headline step (default); sweep: batched shift sweep; serve: serving trace; "
+                         "qp: Q1-Q3 on the heterogeneous wedge")
     ap.add_argument("--pairs", type=int, default=8, help="sweep: (k, kh) pairs (x 16 shifts)")
     ap.add_argument("--max-n", type=int, default=256, help="sweep: keep pairs whose mesh has n <= this")
     ap.add_argument("--fp64-samples", type=int, default=32, help="sweep: samples of the FP64 per-solve form")
@@ -702,6 +752,11 @@ def main():
         run_sweep_bench(args)
     elif args.workload == "serve":
         run_serve_bench(args)
+    elif args.workload == "qp":
+        import __graft_entry__
+        __graft_entry__.build()
+        import paper_2104_01439_gb300 as pkg
+        print(json.dumps({"metric": METRIC, "qp_wedge": qp_leg(pkg)}), flush=True)
     elif args.impl == "reference":
         run_reference(args)
     else:
