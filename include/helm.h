@@ -163,8 +163,9 @@ int helm_setup_info(helm_t h, float* ms, int* kernels);
  * by every iteration) as block elimination along two chains of coarse blocks. The interior
  * blocks of the coarse operator are all alike, so each chain's Schur complement follows one
  * recurrence; where it has converged (the relative change of the block inverse stays below
- * 1e-9 for the complex64 form's double-float factor, 1e-11 for the FP64 form, two steps in a
- * row) the remaining blocks of that chain take the converged inverse instead of being
+ * 1e-7 for the complex64 form's double-float factor, which the solve rounds to complex64, and
+ * 1e-11 for the FP64 form, two steps in a row) the remaining blocks of that chain take the
+ * converged inverse instead of being
  * factored. This happens for large shifts (e.g. eps = k^2 / 2) and not for small ones.
  * Reports how many of the nb coarse blocks were factored and how many reused (either
  * pointer may be NULL). HELM_EINVAL for an operator-only handle.
