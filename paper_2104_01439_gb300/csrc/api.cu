@@ -548,7 +548,8 @@ size_t estimate_bytes(int dim, int order, int n, int precision, int restart) {
   const int64_t blk = B * ldb;
   const int64_t v = precision == HELM_MIXED ? 8 : 16;
   const int64_t m = restart, ldN = (N + 31) & ~int64_t(31), nblk = std::max<int64_t>(1, (N + 255) / 256);
-  const int64_t prec = v * (4 * N + 2 * nb * ldb) + 64 + 3 * 4 * nb;   // (+ the coarse block maps)
+  // (+ the coarse block maps and the group lists of the grouped block products)
+  const int64_t prec = v * (4 * N + 2 * nb * ldb) + 64 + 3 * 4 * nb + 3 * 4 * kGroupInts * nb;
   // Dinv, Lm, Up; the mixed form's segmented solve adds two product sets and one vector
   const int64_t factor = v * 3 * blk * nb + (precision == HELM_MIXED ? 8 * (2 * blk * nb + nb * ldb) : 0);
   // basis (double-float), w split, Z (complex64 in the mixed form), W (FP64 form), residual
@@ -806,6 +807,22 @@ static int setup_impl(helm_ctx* h) {
       if (!rc) rc = put(pmapf, &L.pmapf);
       if (!rc) rc = put(pmapb, &L.pmapb);
       if (h->reused_blocks == 0) cmap.clear();
+      // grouped block products: every use of one (mapped) block in one group of up to gcap
+      std::vector<int> gg, gf, gb;
+      L.gcap = coarse_group_lists(L, plan, o.precision == HELM_MIXED ? sizeof(float2) : sizeof(double2), cmap,
+                                  pmapf, pmapb, &gg, &gf, &gb);
+      auto put_groups = [&](const std::vector<int>& v, const int** dst, int* n) -> int {
+        *n = (int)(v.size() / kGroupInts);
+        if (v.empty()) return HELM_OK;
+        int* d = nullptr;
+        CK(h->alloc(&d, sizeof(int) * v.size()));
+        CK(cudaMemcpyAsync(d, v.data(), sizeof(int) * v.size(), cudaMemcpyHostToDevice, s));
+        *dst = d;
+        return HELM_OK;
+      };
+      if (!rc) rc = put_groups(gg, &L.ggemv, &L.ngemv);
+      if (!rc) rc = put_groups(gf, &L.gfixf, &L.nfixf);
+      if (!rc) rc = put_groups(gb, &L.gfixb, &L.nfixb);
     }
   }
   // couplings folded into the inverses: Lm[J] = Dinv[J] A_J,J-1, Up[J] = Dinv[J] A_J,J+1

@@ -1328,71 +1328,152 @@ __global__ void __launch_bounds__(256) k_seg_middle(const c2<T>* __restrict__ Lm
   if (lane == 0) y[(size_t)m * ldb + a] = csub(p[(size_t)m * ldb + a], v);
 }
 
-// Rows of one dense B x ldb block times a vector staged in shared memory: each warp takes
-// kRowsWarp rows at a time (16-byte loads, several per row in flight per lane), 16 warps per CTA.
-// out[a] = sub ? out[a] - M[a] x : M[a] x.
+// ---------------------------------------------------------------------------
+// Grouped block products. A group names one dense B x ldb matrix block and g <= 4 vector
+// blocks (sources X[src_v], destinations Y[dst_v]); the CTA stages the g vectors in shared
+// memory and each row chunk it reads from global memory is applied to all of them, so a block
+// that repeats (a converged chain, CoarseLayout's maps) is read once per group instead of once
+// per use. Grid: (groups, row slabs of kRowsSlab rows); each warp takes GroupRows<T>::R rows at
+// a time and lane l walks the 16-byte chunks l, l + 32, ... of them.
+// Y[dst_v][a] = M[a] x_v, or Y[dst_v][a] -= M[a] x_v (sub). X and Y may be the same array:
+// the sources of a launch are never among its destinations.
+// ---------------------------------------------------------------------------
 constexpr int kRowsThreads = 512;
-constexpr int kRowsSlab = 64;   // rows per CTA (one pass of 16 warps x 4 rows)
-constexpr int kRowsWarp = 4;    // rows in flight per warp (8 measured slower)
-template <typename T>
-__device__ __forceinline__ void block_rows(const c2<T>* __restrict__ M, const c2<T>* xs, c2<T>* out, int B, int ldb,
-                                           bool sub) {
+constexpr int kRowsSlab = 64;   // rows per CTA
+template <typename T> struct GroupRows;
+template <> struct GroupRows<float> {
+  static constexpr int R = 4;           // rows per warp
+  using C = float4;                     // 16-byte chunk: two complex64 values
+  static constexpr int per = 2;
+};
+template <> struct GroupRows<double> {
+  static constexpr int R = 2;
+  using C = double2;                    // one complex128 value
+  static constexpr int per = 1;
+};
+__device__ __forceinline__ float2 chunk_fma(float4 p, float4 q, float2 s) {
+  return cfma(make_float2(p.z, p.w), make_float2(q.z, q.w), cfma(make_float2(p.x, p.y), make_float2(q.x, q.y), s));
+}
+__device__ __forceinline__ double2 chunk_fma(double2 p, double2 q, double2 s) { return cfma(p, q, s); }
+
+// Reduce-scatter across the warp of N per-lane partial sums (N a power of two, 2..32): on
+// return lane l holds the warp's total of value l / (32 / N). N - 1 shuffles instead of 5 N.
+template <int N, typename S>
+__device__ __forceinline__ S warp_reduce_scatter(S (&v)[N], int lane) {
+#pragma unroll
+  for (int n = N, o = 16; n > 1; n >>= 1, o >>= 1) {
+    const bool up = lane & o;            // this lane keeps the upper half of the live values
+#pragma unroll
+    for (int j = 0; j < n / 2; ++j) {
+      const S send = up ? v[j] : v[j + n / 2];
+      const S keep = up ? v[j + n / 2] : v[j];
+      v[j] = keep + __shfl_xor_sync(0xffffffffu, send, o);
+    }
+  }
+  S r = v[0];
+#pragma unroll
+  for (int o = 16 / N; o > 0; o >>= 1) r += __shfl_xor_sync(0xffffffffu, r, o);
+  return r;
+}
+
+template <typename T, int G>
+__device__ __forceinline__ void group_rows(const c2<T>* __restrict__ M, const c2<T>* xs, c2<T>* Y, const int* dst,
+                                           int B, int ldb, bool sub) {
   using V = c2<T>;
+  using C = typename GroupRows<T>::C;
+  constexpr int R = GroupRows<T>::R, N = 2 * R * G, step = 32 / N;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
   const int abeg = blockIdx.y * kRowsSlab, aend = min(B, abeg + kRowsSlab);
-  for (int a0 = abeg + warp * kRowsWarp; a0 < aend; a0 += nw * kRowsWarp) {
-    V s[kRowsWarp];
+  const int nc = ldb / GroupRows<T>::per;
+  const C* x4 = reinterpret_cast<const C*>(xs);
+  for (int a0 = abeg + warp * R; a0 < aend; a0 += nw * R) {
+    const C* rows[R];
 #pragma unroll
-    for (int r = 0; r < kRowsWarp; ++r) {
-      const int a = min(a0 + r, aend - 1);
-      s[r] = row_dot(M + (size_t)a * ldb, xs, ldb, lane);
+    for (int r = 0; r < R; ++r) rows[r] = reinterpret_cast<const C*>(M + (size_t)min(a0 + r, aend - 1) * ldb);
+    V s[R][G];
+#pragma unroll
+    for (int r = 0; r < R; ++r)
+#pragma unroll
+      for (int v = 0; v < G; ++v) s[r][v] = mk(T(0), T(0));
+#pragma unroll 1
+    for (int i = lane; i < nc; i += 32) {
+      C p[R];
+#pragma unroll
+      for (int r = 0; r < R; ++r) p[r] = __ldg(rows[r] + i);
+#pragma unroll
+      for (int v = 0; v < G; ++v) {
+        const C q = x4[v * nc + i];
+#pragma unroll
+        for (int r = 0; r < R; ++r) s[r][v] = chunk_fma(p[r], q, s[r][v]);
+      }
     }
+    T f[N];   // value (r G + v) 2 + component
 #pragma unroll
-    for (int r = 0; r < kRowsWarp; ++r) {
-      const V v = warp_sum(s[r]);
-      if (lane == 0 && a0 + r < aend) out[a0 + r] = sub ? csub(out[a0 + r], v) : v;
+    for (int r = 0; r < R; ++r)
+#pragma unroll
+      for (int v = 0; v < G; ++v) {
+        f[(r * G + v) * 2] = s[r][v].x;
+        f[(r * G + v) * 2 + 1] = s[r][v].y;
+      }
+    const T t = warp_reduce_scatter<N>(f, lane);
+    const T ty = __shfl_down_sync(0xffffffffu, t, step);   // imaginary part from the next value's lanes
+    if (lane % (2 * step) == 0) {
+      const int c = lane / (2 * step), r = c / G, v = c % G;
+      if (a0 + r < aend) {
+        V* o = Y + (size_t)dst[v] * ldb + a0 + r;
+        const V val = mk(t, ty);
+        *o = sub ? csub(*o, val) : val;
+      }
     }
   }
 }
 
-// Block-diagonal pre-pass with the block's vector staged in shared memory (one CTA per block).
+// Group descriptor: matrix block, g, sources[kGroup], destinations[kGroup].
 template <typename T>
-__global__ void __launch_bounds__(kRowsThreads) k_block_gemv(const c2<T>* __restrict__ Dinv,
-                                                             const c2<T>* __restrict__ rc, c2<T>* __restrict__ out,
-                                                             CoarseLayout L, const int* active) {
+__device__ __forceinline__ void group_products(const c2<T>* __restrict__ M, const c2<T>* X, c2<T>* Y,
+                                               const int* __restrict__ groups, int B, int ldb, bool sub) {
   using V = c2<T>;
-  if (active && *active == 0) return;
   extern __shared__ __align__(16) unsigned char smv[];
   V* xs = reinterpret_cast<V*>(smv);
-  const int B = L.B, ldb = L.ldb, J = blockIdx.x;
-  for (int i = threadIdx.x; i < ldb; i += blockDim.x) xs[i] = cvt_ldcg(rc + (size_t)J * ldb + i);
+  __shared__ int gd[kGroupInts];
+  if (threadIdx.x < kGroupInts) gd[threadIdx.x] = __ldg(groups + (size_t)blockIdx.x * kGroupInts + threadIdx.x);
   __syncthreads();
-  block_rows<T>(Dinv + (size_t)map_block(L.cmap, J) * B * ldb, xs, out + (size_t)J * ldb, B, ldb, false);
+  const int g = gd[1], gpad = g == 3 ? 4 : g;   // three vectors run as four, the fourth zero
+  const V zero = mk(T(0), T(0));
+  for (int e = threadIdx.x; e < gpad * ldb; e += blockDim.x) {
+    const int v = e / ldb, i = e - v * ldb;
+    xs[e] = i < B && v < g ? cvt_ldcg(X + (size_t)gd[2 + v] * ldb + i) : zero;
+  }
+  __syncthreads();
+  const V* Mb = M + (size_t)gd[0] * B * ldb;
+  const int* dst = gd + 2 + kGroup;
+  if (g == 1)
+    group_rows<T, 1>(Mb, xs, Y, dst, B, ldb, sub);
+  else if (g == 2)
+    group_rows<T, 2>(Mb, xs, Y, dst, B, ldb, sub);
+  else
+    group_rows<T, 4>(Mb, xs, Y, dst, B, ldb, sub);
+}
+
+// Block-diagonal pre-pass: p_J = Dinv[cmap J] r_J, grouped by inverse (L.ggemv).
+template <typename T>
+__global__ void __launch_bounds__(kRowsThreads, 2) k_block_gemv(const c2<T>* __restrict__ Dinv,
+                                                                const c2<T>* __restrict__ rc, c2<T>* __restrict__ out,
+                                                                CoarseLayout L, const int* active) {
+  if (active && *active == 0) return;
+  if ((int)blockIdx.x >= L.ngemv) return;
+  group_products<T>(Dinv, rc, out, L.ggemv, L.B, L.ldb, false);
 }
 
 // Phase C: z_q -= P[J(q)] z_e(k-1) for every position q of segments k >= 1 except their
-// ends, on both paths of a sweep. One CTA per position; the history vector is staged once.
+// ends, on both paths of a sweep, grouped by segment product (L.gfixf / L.gfixb).
 template <typename T>
-__global__ void __launch_bounds__(kRowsThreads) k_seg_fixup(const c2<T>* __restrict__ P, c2<T>* __restrict__ Z,
-                                                            CoarseLayout L, SegPath p0, SegPath p1,
-                                                            const int* pmap, const int* active) {
-  using V = c2<T>;
+__global__ void __launch_bounds__(kRowsThreads, 2) k_seg_fixup(const c2<T>* __restrict__ P, c2<T>* Z,
+                                                               CoarseLayout L, const int* groups, int ngroups,
+                                                               const int* active) {
   if (active && *active == 0) return;
-  __shared__ __align__(16) V xs[kSegMaxLdb];
-  const int B = L.B, ldb = L.ldb;
-  const int n0 = max(0, p0.n - p0.Ls);
-  const int g = blockIdx.x;
-  const bool second = g >= n0;
-  const SegPath& pp = second ? p1 : p0;
-  const int q = pp.Ls + (second ? g - n0 : g);
-  if (q >= pp.n) return;
-  const int k = q / pp.Ls;
-  if (q == seg_end(k, pp.Ls, pp.n)) return;   // done by phase B
-  const V* src = Z + (size_t)path_block(pp, k * pp.Ls - 1) * ldb;
-  for (int i = threadIdx.x; i < ldb; i += blockDim.x) xs[i] = i < B ? cvt_ldcg(src + i) : mk(T(0), T(0));
-  __syncthreads();
-  const int J = path_block(pp, q);
-  block_rows<T>(P + (size_t)map_block(pmap, J) * B * ldb, xs, Z + (size_t)J * ldb, B, ldb, true);
+  if ((int)blockIdx.x >= ngroups) return;
+  group_products<T>(P, Z, Z, groups, L.B, L.ldb, true);
 }
 
 // Segment products, step i of every segment k >= 1 of one path (one z-slice per segment):
@@ -1666,9 +1747,10 @@ void launch_coarse_solve(const CoarsePlan& plan, const c2<T>* Dinv, const c2<T>*
                          const CoarseLayout& L, const c2<T>* rc, c2<T>* uc, unsigned* bar, int* err,
                          const int* active, int nsm, cudaStream_t s, const SegBufs<T>* seg) {
   // p = blockdiag(Dinv) r for all blocks at once, into uc
-  if (sizeof(c2<T>) * L.ldb <= 48 * 1024)
-    k_block_gemv<T><<<dim3(L.nb, (L.B + kRowsSlab - 1) / kRowsSlab), kRowsThreads, sizeof(c2<T>) * L.ldb, s>>>(
-        Dinv, rc, uc, L, active);
+  const int slabs = (L.B + kRowsSlab - 1) / kRowsSlab;
+  const size_t gsmem = sizeof(c2<T>) * L.ldb * L.gcap;
+  if (L.gcap > 0 && gsmem <= 48 * 1024)
+    k_block_gemv<T><<<dim3(std::max(1, L.ngemv), slabs), kRowsThreads, gsmem, s>>>(Dinv, rc, uc, L, active);
   else
     k_block_gemv_wide<T><<<nsm * 8, 256, 0, s>>>(Dinv, rc, uc, L, active);
   if (plan.seg && seg) {
@@ -1700,15 +1782,14 @@ void launch_coarse_solve(const CoarsePlan& plan, const c2<T>* Dinv, const c2<T>*
     // forward sweeps: uc (p) -> yb (y); middle block x_m -> yb[mid]
     chain(SegArgs<T>{uc, seg->yb, {Lm, Up}, seg->Pf, L.pmapf, {f[0], f[1]}, 0}, f[0].K + f[1].K);
     chain(SegArgs<T>{seg->yb, seg->yb, {Lm, Up}, seg->Pf, L.pmapf, {f[0], f[1]}, 1}, 2);
-    const int slabs = (L.B + kRowsSlab - 1) / kRowsSlab;
-    k_seg_fixup<T><<<dim3(std::max(1, f[0].n - f[0].Ls + f[1].n - f[1].Ls), slabs), kRowsThreads, 0, s>>>(
-        seg->Pf, seg->yb, L, f[0], f[1], L.pmapf, active);
+    k_seg_fixup<T><<<dim3(std::max(1, L.nfixf), slabs), kRowsThreads, gsmem, s>>>(seg->Pf, seg->yb, L, L.gfixf,
+                                                                                  L.nfixf, active);
     k_seg_middle<T><<<(L.B * 32 + 255) / 256, 256, 0, s>>>(Lm, Up, uc, seg->yb, L, active);
     // backward sweeps: yb (y, x_m) -> uc (x)
     chain(SegArgs<T>{seg->yb, uc, {Up, Lm}, seg->Pb, L.pmapb, {b[0], b[1]}, 0}, b[0].K + b[1].K);
     chain(SegArgs<T>{uc, uc, {Up, Lm}, seg->Pb, L.pmapb, {b[0], b[1]}, 1}, 2);
-    k_seg_fixup<T><<<dim3(std::max(1, b[0].n - b[0].Ls + b[1].n - b[1].Ls), slabs), kRowsThreads, 0, s>>>(
-        seg->Pb, uc, L, b[0], b[1], L.pmapb, active);
+    k_seg_fixup<T><<<dim3(std::max(1, L.nfixb), slabs), kRowsThreads, gsmem, s>>>(seg->Pb, uc, L, L.gfixb, L.nfixb,
+                                                                                  active);
     return;
   }
   if (plan.grid) {
@@ -1907,6 +1988,71 @@ void coarse_block_maps(const CoarseLayout& L, const CoarsePlan* plan, const int*
           pm[path_block(p, q)] = path_block(p, ks * p.Ls + (q - k * p.Ls));
     }
   }
+}
+
+namespace {
+// Items (matrix block, source, destination) sharing a matrix block, packed as groups of at most
+// cap items in the order of each block's first use.
+void pack_groups(const std::vector<int3>& items, int cap, std::vector<int>* out) {
+  std::vector<int> order;                       // matrix blocks in order of first use
+  std::vector<std::vector<int>> uses;           // item indices per matrix block
+  std::vector<int> slot;
+  for (size_t i = 0; i < items.size(); ++i) {
+    const int mb = items[i].x;
+    if (mb >= (int)slot.size()) slot.resize(mb + 1, -1);
+    if (slot[mb] < 0) {
+      slot[mb] = (int)uses.size();
+      uses.emplace_back();
+      order.push_back(mb);
+    }
+    uses[slot[mb]].push_back((int)i);
+  }
+  out->clear();
+  for (size_t u = 0; u < uses.size(); ++u)
+    for (size_t b = 0; b < uses[u].size(); b += cap) {
+      const int g = (int)std::min<size_t>(cap, uses[u].size() - b);
+      const size_t o = out->size();
+      out->resize(o + kGroupInts);
+      int* d = out->data() + o;
+      d[0] = order[u];
+      d[1] = g;
+      for (int v = 0; v < kGroup; ++v) {
+        const int3& it = items[uses[u][b + std::min(v, g - 1)]];   // unused slots repeat the last
+        d[2 + v] = it.y;
+        d[2 + kGroup + v] = it.z;
+      }
+    }
+}
+}  // namespace
+
+int coarse_group_lists(const CoarseLayout& L, const CoarsePlan* plan, size_t elem, const std::vector<int>& cmap,
+                       const std::vector<int>& pmapf, const std::vector<int>& pmapb, std::vector<int>* gemv,
+                       std::vector<int>* fixf, std::vector<int>* fixb) {
+  gemv->clear();
+  fixf->clear();
+  fixb->clear();
+  const size_t row = elem * (size_t)L.ldb;
+  const int cap = row * 4 <= 48 * 1024 ? 4 : row * 2 <= 48 * 1024 ? 2 : row <= 48 * 1024 ? 1 : 0;
+  if (cap == 0) return 0;
+  std::vector<int3> items;
+  for (int J = 0; J < L.nb; ++J) items.push_back(make_int3(cmap.empty() ? J : cmap[J], J, J));
+  pack_groups(items, cap, gemv);
+  if (!plan || !plan->seg) return cap;
+  SegPath f[2], b[2];
+  seg_paths(L, *plan, f, b);
+  for (int sweep = 0; sweep < 2; ++sweep) {
+    const std::vector<int>& pm = sweep == 0 ? pmapf : pmapb;
+    items.clear();
+    for (const SegPath& p : sweep == 0 ? f : b)
+      for (int q = p.Ls; q < p.n; ++q) {
+        const int k = q / p.Ls;
+        if (q == seg_end(k, p.Ls, p.n)) continue;   // a segment's end: solved by phase B
+        const int J = path_block(p, q);
+        items.push_back(make_int3(pm.empty() ? J : pm[J], path_block(p, k * p.Ls - 1), J));
+      }
+    pack_groups(items, cap, sweep == 0 ? fixf : fixb);
+  }
+  return cap;
 }
 
 void coarse_seg_products(const float2* Lm, const float2* Up, float2* Pf, float2* Pb, const CoarseLayout& L,

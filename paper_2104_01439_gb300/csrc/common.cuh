@@ -142,7 +142,19 @@ struct CoarseLayout {
   const int* cmap = nullptr;
   const int* pmapf = nullptr;
   const int* pmapb = nullptr;
+  // Grouped block products (device arrays of kGroupInts ints per group: matrix block, count g,
+  // kGroup source blocks, kGroup destination blocks). Vectors that use the same matrix block
+  // (under the maps above) share a group of at most gcap, so the block is read once for all
+  // of them. ggemv: the pre-pass p_J = Dinv[J] r_J; gfixf / gfixb: the fix-up products of the
+  // forward / backward segmented sweeps. gcap = 0: no groups (blocks too wide to stage).
+  const int* ggemv = nullptr;
+  const int* gfixf = nullptr;
+  const int* gfixb = nullptr;
+  int ngemv = 0, nfixf = 0, nfixb = 0;
+  int gcap = 0;
 };
+constexpr int kGroup = 4;
+constexpr int kGroupInts = 2 + 2 * kGroup;
 __host__ __device__ inline int map_block(const int* map, int J) {
 #if defined(__CUDA_ARCH__)
   return map ? __ldg(map + J) : J;

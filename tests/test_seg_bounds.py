@@ -1,8 +1,8 @@
 """Index bounds of the segmented coarse-solve kernels, emulated on the CPU.
 
 The index arithmetic of the complex64 segmented solve (k_seg_chain's producer bulk copies,
-consumer reads and writes, shared-memory ring and receive buffers; k_seg_fixup; k_seg_middle;
-k_seg_products) is restated here from the kernels and every access is checked against its
+consumer reads and writes, shared-memory ring and receive buffers; the grouped fix-up
+products of k_seg_fixup and the host's group lists; k_seg_middle; k_seg_products) is restated here from the kernels and every access is checked against its
 allocation:
   coupling matrices Lm, Up and the segment products Pf, Pb: nb x B x ldb complex64;
   coarse vectors (p, y, x): nb x ldb;
@@ -156,29 +156,68 @@ def check_disjoint(writes, allowed):
             seen[J] = cid
 
 
-def check_fixup_middle_products(nb, B, ldb, m, pp):
+GROUP = 4                             # vectors per group of the grouped block products
+GROUP_SMEM = 48 * 1024
+
+
+def group_cap(ldb, elem):
+    row = elem * ldb
+    return 4 if 4 * row <= GROUP_SMEM else 2 if 2 * row <= GROUP_SMEM else 1 if row <= GROUP_SMEM else 0
+
+
+def pack_groups(items, cap):
+    """(matrix block, source, destination) items packed as groups of at most cap items sharing a
+    matrix block, in the order of each block's first use; unused slots repeat the last item."""
+    uses = {}
+    for it in items:
+        uses.setdefault(it[0], []).append(it)
+    groups = []
+    for mb, lst in uses.items():
+        for b in range(0, len(lst), cap):
+            chunk = lst[b:b + cap]
+            pad = chunk + [chunk[-1]] * (GROUP - len(chunk))
+            groups.append((mb, len(chunk), [it[1] for it in pad], [it[2] for it in pad]))
+    return groups
+
+
+def check_group_launch(groups, nb, B, ldb, cap, elem, sub):
+    """k_block_gemv / k_seg_fixup over a group list: staged vectors, matrix rows, outputs."""
     mat_size, vec_size = nb * B * ldb, nb * ldb
-    assert ldb <= SEG_MAX_LDB
-    n0 = max(0, pp[0]["n"] - pp[0]["Ls"])
-    grid = max(1, n0 + pp[1]["n"] - pp[1]["Ls"])
-    fixed = set()
-    for g in range(grid):                             # k_seg_fixup, x dimension
-        second = g >= n0
-        p = pp[1] if second else pp[0]
-        q = p["Ls"] + (g - n0 if second else g)
-        if q >= p["n"]:
-            continue
-        k = q // p["Ls"]
-        if q == seg_end(k, p["Ls"], p["n"]):
-            continue
-        J, src = blk(p, q), blk(p, k * p["Ls"] - 1)
-        assert 0 <= J < nb and 0 <= src < nb and src != J
-        assert src * ldb + B <= vec_size and J * ldb + B <= vec_size
+    assert cap in (1, 2, 4) and cap * ldb * elem <= GROUP_SMEM and ldb % 2 == 0
+    srcs, dsts = set(), set()
+    for mb, g, src, dst in groups:
+        assert 1 <= g <= cap and 0 <= mb < nb
+        gpad = 4 if g == 3 else g                     # three vectors run as four (a zero fourth)
+        assert gpad <= cap                            # shared memory holds gpad staged vectors
+        G = 1 if g == 1 else 2 if g == 2 else 4       # the group_rows instance
+        assert g <= G <= cap
+        for v in range(g):
+            assert 0 <= src[v] < nb and 0 <= dst[v] < nb
+            assert src[v] * ldb + B <= vec_size and dst[v] * ldb + B <= vec_size
+            assert dst[v] not in dsts                 # each destination written by one CTA column
+            dsts.add(dst[v])
+            srcs.add(src[v])
         for slab in range((B + ROWS_SLAB - 1) // ROWS_SLAB):
             aend = min(B, slab * ROWS_SLAB + ROWS_SLAB)
-            assert (J * B + aend - 1) * ldb + ldb <= mat_size
-        assert J not in fixed
-        fixed.add(J)
+            assert (mb * B + aend - 1) * ldb + ldb <= mat_size
+    if sub:
+        assert not srcs & dsts                        # sources are read while destinations change
+    return dsts
+
+
+def check_fixup_middle_products(nb, B, ldb, m, pp, pmap=None):
+    mat_size, vec_size = nb * B * ldb, nb * ldb
+    assert ldb <= SEG_MAX_LDB
+    cap = group_cap(ldb, ELEM)
+    items = []
+    for p in pp:                                      # the host's group list of the fix-ups
+        for q in range(p["Ls"], p["n"]):
+            k = q // p["Ls"]
+            if q == seg_end(k, p["Ls"], p["n"]):
+                continue                              # a segment's end: phase B
+            J = blk(p, q)
+            items.append((pmap[J] if pmap else J, blk(p, k * p["Ls"] - 1), J))
+    fixed = check_group_launch(pack_groups(items, cap), nb, B, ldb, cap, ELEM, True)
     for p in pp:
         for q in range(p["Ls"], p["n"]):              # every non-end position of k >= 1 fixed
             k = q // p["Ls"]
@@ -222,5 +261,73 @@ def test_segment_kernels_stay_in_bounds(dim, order, n):
                 for GB in GBs:
                     check_disjoint(check_chain(nb, B, ldb, GB, pp, 1), set())
                 check_fixup_middle_products(nb, B, ldb, m, pp)
+                for ctop, cbot in converged_points(nb, m):
+                    cmap = block_map(nb, m, ctop, cbot)
+                    check_fixup_middle_products(nb, B, ldb, m, pp, product_map(nb, pp, cmap))
             checked += 1
     assert checked > 0
+
+
+def converged_points(nb, m):
+    """Blocks at which the top and bottom chains' Schur inverses are taken as converged."""
+    return [(c, nb - 1 - c) for c in (1, 2, 5, m // 2) if 1 <= c < m and m < nb - 1 - c <= nb - 2]
+
+
+def block_map(nb, m, ctop, cbot):
+    """Host cmap: later blocks of a converged chain use the converged block."""
+    cmap = list(range(nb))
+    for J in range(ctop + 1, m):
+        cmap[J] = ctop
+    for J in range(m + 1, cbot):
+        cmap[J] = cbot
+    return cmap
+
+
+def product_map(nb, pp, cmap):
+    """Host pmap of one sweep: the run of segments k >= 1 whose blocks all repeat a converged
+    block; its first segment is computed and the rest repeat it position by position."""
+    pm = list(range(nb))
+    for p in pp:
+        kstar, lo, hi = -1, 1, 0
+        for k in range(1, p["K"]):
+            rep = all(cmap[blk(p, q)] != blk(p, q) for q in range(k * p["Ls"], seg_end(k, p["Ls"], p["n"]) + 1))
+            if rep and kstar < 0:
+                kstar = k
+            elif rep:
+                lo = k if lo > hi else lo
+                hi = k
+            elif kstar >= 0:
+                break
+        for k in range(lo, hi + 1):
+            for q in range(k * p["Ls"], seg_end(k, p["Ls"], p["n"]) + 1):
+                pm[blk(p, q)] = blk(p, kstar * p["Ls"] + (q - k * p["Ls"]))
+    return pm
+
+
+GEMV_LAYOUTS = [(2, 1, n) for n in (8, 30, 64, 512, 1024, 2046)] + [(2, 2, n) for n in (8, 64, 512, 1024)] + \
+               [(3, 1, n) for n in (8, 32, 62, 96)] + [(2, 3, n) for n in (16, 128)]
+
+
+@pytest.mark.parametrize("dim,order,n", GEMV_LAYOUTS, ids=lambda v: str(v))
+@pytest.mark.parametrize("elem", [8, 16], ids=["complex64", "complex128"])
+def test_grouped_prepass_stays_in_bounds(dim, order, n, elem):
+    """k_block_gemv's groups p_J = Dinv[cmap J] r_J cover every block once, with and without
+    converged chains (blocks wider than 48 KB of shared memory take the wide kernel instead)."""
+    nb, B, ldb = coarse_layout(dim, order, n)
+    cap = group_cap(ldb, elem)
+    if cap == 0:
+        assert elem * ldb > GROUP_SMEM
+        return
+    m = nb // 2 if nb >= 4 else nb - 1
+    maps = [list(range(nb))] + [block_map(nb, m, c, b) for c, b in converged_points(nb, m)]
+    for cmap in maps:
+        groups = pack_groups([(cmap[J], J, J) for J in range(nb)], cap)
+        assert check_group_launch(groups, nb, B, ldb, cap, elem, False) == set(range(nb))
+        assert len(groups) <= nb and all(g[2] == g[3] for g in groups)
+
+
+def test_pack_groups_shares_repeated_blocks():
+    items = [(7, J, J) for J in range(10)] + [(3, 10, 10)]
+    groups = pack_groups(items, 4)
+    assert [(g[0], g[1]) for g in groups] == [(7, 4), (7, 4), (7, 2), (3, 1)]
+    assert groups[2][2] == [8, 9, 9, 9] and groups[3][3] == [10, 10, 10, 10]
