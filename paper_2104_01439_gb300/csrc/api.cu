@@ -885,11 +885,12 @@ static int setup_impl(helm_ctx* h) {
   const int m = o.restart;
   kb.N = h->gf.N;
   kb.ldN = (kb.N + 31) & ~int64_t(31);
-  // element-wise Krylov kernels: one entry per thread; inner products: <= 8 per thread
+  // element-wise Krylov kernels: one entry per thread
   kb.nblk = (int)std::max<int64_t>(1, (kb.N + 255) / 256);
-  kb.nblk_dots = (int)std::max<int64_t>(1, (kb.N + 2047) / 2048);   // 8 entries per thread
+  kb.exact_gs = o.precision == HELM_MIXED ? 0 : 1;
+  kb.nblk_dots = dots_blocks(kb.N, h->nsm, kb.exact_gs);
   kb.m = m;
-  kb.nblk_upd = (int)std::max<int64_t>(1, (kb.N + 255) / 256);
+  kb.nblk_upd = update_blocks(kb.N, h->nsm, kb.exact_gs, sizeof(float4) * 2 * m);
   kb.pstride = std::max(kb.nblk, std::max(kb.nblk_upd, kb.nblk_dots));
   CK(h->alloc(&kb.Vs, sizeof(float4) * kb.ldN * (m + 1)));
   CK(h->alloc(&kb.Ws, sizeof(float4) * kb.ldN));

@@ -201,10 +201,12 @@ struct KrylovBufs {
   double2* tp;     // m+1 : t_i = <v_i, w>
   double2* part;   // pstride x kb_rows(m) partial sums (inner products: double-float as float4)
   int nblk;        // blocks of the element-wise Krylov kernels (256 threads, one entry per thread)
-  int nblk_dots;   // blocks of the inner-product kernel (256 threads, <= 8 entries per thread)
+  int nblk_dots;   // blocks of the inner-product kernel (dots_blocks(N, SMs))
   int m;           // restart length (host copy of KState::m, sizes launches)
-  int nblk_upd;    // blocks of the update kernel (32 entries per warp)
+  int nblk_upd;    // blocks of the update kernel (update_blocks)
   int pstride;     // row stride of the partials buffer: max over the kernels that write it
+  int exact_gs;    // 1: both Gram-Schmidt passes in double-float (FP64 form); 0: the first
+                   // pass's projections and the second pass's small correction sum in float
   KState* st;
 };
 
@@ -212,6 +214,10 @@ struct KrylovBufs {
 // its Givens step), the joint correction sweep and u_{j+1} = w / ||w||. `mid` (may be null)
 // is recorded between the coefficient kernel and the correction sweep.
 void launch_arnoldi(const KrylovBufs& kb, cudaStream_t s, cudaEvent_t mid);
+// blocks of the inner-product kernel for N entries: one wave on nsm SMs (exact: FP64 form)
+int dots_blocks(int64_t N, int nsm, bool exact);
+// blocks of the correction sweep (smem: its dynamic shared memory, 2 m float4)
+int update_blocks(int64_t N, int nsm, bool exact, size_t smem);
 void launch_cycle_start(const KrylovBufs& kb, const double2* r, cudaStream_t s);   // V0 = r / ||r||
 void launch_backsolve(const KrylovBufs& kb, cudaStream_t s);
 void launch_update_x(const KrylovBufs& kb, double2* x, cudaStream_t s);

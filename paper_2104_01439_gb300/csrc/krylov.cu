@@ -54,87 +54,211 @@ __device__ __forceinline__ DF df_wsum(DF v) {
   return v;
 }
 
-constexpr int kE = 8;    // basis entries per thread in the inner-product kernel
-constexpr int kGD = 2;   // basis vectors per sweep of the inner-product kernel
+constexpr int kDT = 128;      // threads of the inner-product kernel
+constexpr int kDS = 3;        // cp.async stages per thread of the inner-product kernel
+constexpr int kDPerSM = 6;    // its resident blocks per SM aimed at (register bound)
+// basis vectors per group of the inner-product kernel: 4 with float first-pass sums, 2 when
+// both passes are double-float (register budget)
+template <bool kExact> constexpr int kGDOf = kExact ? 2 : 4;
+
+__device__ __forceinline__ void cp_async16(void* smem, const void* gmem) {
+  const unsigned d = (unsigned)__cvta_generic_to_shared(smem);
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(d), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() {
+  asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory");
+}
+
+// The inner-product kernel's work split: the (group, entry) space of ngr groups x N entries,
+// flattened group-major, is cut into G equal contiguous ranges, one per block; block b holds
+// [b T / G, (b + 1) T / G) with T = ngr N. dots_block_of(f) is the block whose range holds f.
+__host__ __device__ inline int64_t dots_range_begin(int64_t b, int64_t T, int64_t G) { return b * T / G; }
+__host__ __device__ inline int64_t dots_block_of(int64_t f, int64_t T, int64_t G) { return ((f + 1) * G - 1) / T; }
+
+// Reduce-scatter across the warp of NV per-lane values (NV a power of two, 2..32): on return
+// lane l holds the warp's total of value l / (32 / NV). NV - 1 exchanges (plus log2(32 / NV)
+// full ones) instead of 5 NV.
+template <int NV>
+__device__ __forceinline__ DF df_reduce_scatter(DF (&v)[NV], int lane) {
+#pragma unroll
+  for (int n = NV, o = 16; n > 1; n >>= 1, o >>= 1) {
+    const bool up = lane & o;   // this lane keeps the upper half of the live values
+#pragma unroll
+    for (int q = 0; q < n / 2; ++q) {
+      const DF send = up ? v[q] : v[q + n / 2];
+      const DF keep = up ? v[q + n / 2] : v[q];
+      v[q] = df_add(keep, DF{__shfl_xor_sync(0xffffffffu, send.h, o), __shfl_xor_sync(0xffffffffu, send.l, o)});
+    }
+  }
+  DF r = v[0];
+#pragma unroll
+  for (int o = 16 / NV; o > 0; o >>= 1)
+    r = df_add(r, DF{__shfl_xor_sync(0xffffffffu, r.h, o), __shfl_xor_sync(0xffffffffu, r.l, o)});
+  return r;
+}
+template <int NV>
+__device__ __forceinline__ float f_reduce_scatter(float (&v)[NV], int lane) {
+#pragma unroll
+  for (int n = NV, o = 16; n > 1; n >>= 1, o >>= 1) {
+    const bool up = lane & o;
+#pragma unroll
+    for (int q = 0; q < n / 2; ++q) {
+      const float send = up ? v[q] : v[q + n / 2];
+      v[q] = (up ? v[q + n / 2] : v[q]) + __shfl_xor_sync(0xffffffffu, send, o);
+    }
+  }
+  float r = v[0];
+#pragma unroll
+  for (int o = 16 / NV; o > 0; o >>= 1) r += __shfl_xor_sync(0xffffffffu, r, o);
+  return r;
+}
+
+// Accumulators of the first-pass products t_i = <v_i, w>: double-float (kExact) or float.
+template <bool kExact> struct TAcc;
+template <> struct TAcc<true> {
+  DF r, i;
+  __device__ __forceinline__ void mac(float4 v, float4 x) {
+    df_mac(v.x, v.z, x.x, x.z, r);
+    df_mac(v.y, v.w, x.y, x.w, r);
+    df_mac(v.x, v.z, x.y, x.w, i);
+    df_mac(-v.y, -v.w, x.x, x.z, i);
+  }
+};
+template <> struct TAcc<false> {
+  float r, i;
+  __device__ __forceinline__ void mac(float4 v, float4 x) {   // the high parts of x only
+    r = fmaf(v.x, x.x, fmaf(v.y, x.y, r));
+    i = fmaf(v.x, x.y, fmaf(-v.y, x.x, i));
+  }
+};
 
 // Inner products of the basis slots 0..j against two vectors in one sweep over V:
 //   s_i = <v_i, u_j>  (u_j = the once-orthogonalised vector in slot j; s_j = ||u_j||^2)
 //   t_i = <v_i, w>    (w = A0 z_j; only when this step applies the preconditioner)
-// Grid: x over chunks of the vectors (kE entries per thread), y over groups of kGD basis
-// slots, so every (chunk, group) pair is its own block. Block partials stay double-float.
-__global__ void __launch_bounds__(kT, 5) k_dots2(KrylovBufs kb) {
+// The slots are taken in groups of kGD (u_j and w are read once per group). A persistent
+// grid of G blocks splits the (group, entry) space evenly (dots_range_begin), whatever j is;
+// each block accumulates every group its range touches and writes one partial per row and
+// block. Each thread streams its entries through shared memory with cp.async, kDS - 1
+// entries ahead of the arithmetic.
+// The s_i, the second pass that makes the basis orthogonal, are double-float (exact
+// products, TwoSum accumulation). The t_i only choose the first correction, which the exact
+// double-float update applies as given and the next step's second pass completes, so the
+// complex64 form (kExact = false) forms them from the high parts in float (absolute error
+// ~1e-7 |v_i| |w|, removed with the rest by that pass); the FP64 form keeps them double-float.
+// Block partials are double-float.
+template <bool kExact>
+__global__ void __launch_bounds__(kDT, kDPerSM) k_dots2(KrylovBufs kb) {
+  constexpr int kGD = kGDOf<kExact>, kQ = 2 + kGD;   // staged per entry: u_j, w, the group's slots
+  constexpr int NV = 2 * kGD;                          // re, im of each slot
+  __shared__ __align__(16) float4 stg[kDS][kQ][kDT];
+  __shared__ float4 red[kDT / 32][2 * NV];            // [warp][value]: s as (h, l, 0, 0), then t
   KState* st = kb.st;
   if (!st->active) return;
   const int j = st->j, m = st->m;
   const bool pre = st->pre != 0;
-  const int i0 = blockIdx.y * kGD;
-  if (i0 > j) return;
-  const int ng = min(kGD, j + 1 - i0);
   const int64_t N = kb.N, ld = kb.ldN;
-  __shared__ float4 red[kT / 32][2 * kGD];
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  const int64_t PS = kb.pstride;
-  const int64_t stride = (int64_t)gridDim.x * blockDim.x, base = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  float4* part4 = reinterpret_cast<float4*>(kb.part);
-  const float4* uj = kb.Vs + (int64_t)j * ld;
-  DF sr[kGD], si[kGD], tr[kGD], ti[kGD];
+  const int64_t T = (int64_t)((j + kGD) / kGD) * N, G = gridDim.x;
+  const int64_t fe = dots_range_begin(blockIdx.x + 1, T, G);
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  for (int64_t f = dots_range_begin(blockIdx.x, T, G); f < fe;) {
+    const int g = (int)(f / N);
+    const int64_t nbeg = f - (int64_t)g * N, nend = min(N, fe - (int64_t)g * N);
+    f = (int64_t)g * N + nend;
+    const int i0 = g * kGD, ng = min(kGD, j + 1 - i0);
+    const float4* uj = kb.Vs + (int64_t)j * ld;
+    const float4* vb = kb.Vs + (int64_t)i0 * ld;
+    int vo[kGD];   // entry offsets of the slots; slots past ng repeat the last one (not written)
 #pragma unroll
-  for (int t = 0; t < kGD; ++t) sr[t] = si[t] = tr[t] = ti[t] = DF{0.f, 0.f};
-  // entries base + k * stride, k < kE, in batches of two: the next batch's loads are issued
-  // before the current batch's arithmetic. Out-of-range entries load entry 0 and are weighted 0.
-  float4 u[2], w[2], v[2][kGD];
-  auto load = [&](int k, int b) {
-    const int64_t n = base + k * stride;
-    const int64_t nn = n < N ? n : 0;
-    const float4 z = dfc_zero();
-    u[b] = n < N ? uj[nn] : z;
-    w[b] = (pre && n < N) ? kb.Ws[nn] : z;
-#pragma unroll
-    for (int t = 0; t < kGD; ++t) v[b][t] = t < ng ? kb.Vs[(int64_t)(i0 + t) * ld + nn] : z;
-  };
-  load(0, 0);
-#pragma unroll
-  for (int k = 0; k < kE; ++k) {
-    const int b = k & 1;
-    if (k + 1 < kE) load(k + 1, b ^ 1);
+    for (int t = 0; t < kGD; ++t) vo[t] = min(t, ng - 1) * (int)ld;
+    DF sr[kGD], si[kGD];
+    TAcc<kExact> ta[kGD];
 #pragma unroll
     for (int t = 0; t < kGD; ++t) {
-      const float4 vv = v[b][t], uu = u[b], ww = w[b];
-      // conj(v) x = (vr xr + vi xi) + i (vr xi - vi xr)
-      df_mac(vv.x, vv.z, uu.x, uu.z, sr[t]);
-      df_mac(vv.y, vv.w, uu.y, uu.w, sr[t]);
-      df_mac(vv.x, vv.z, uu.y, uu.w, si[t]);
-      df_mac(-vv.y, -vv.w, uu.x, uu.z, si[t]);
-      if (pre) {
-        df_mac(vv.x, vv.z, ww.x, ww.z, tr[t]);
-        df_mac(vv.y, vv.w, ww.y, ww.w, tr[t]);
-        df_mac(vv.x, vv.z, ww.y, ww.w, ti[t]);
-        df_mac(-vv.y, -vv.w, ww.x, ww.z, ti[t]);
+      sr[t] = si[t] = DF{0.f, 0.f};
+      ta[t] = TAcc<kExact>{};
+    }
+    // entry n of this thread's sequence nbeg + tid + k kDT into stage slot (empty groups past the end)
+    auto issue = [&](int64_t n, int slot) {
+      if (n < nend) {
+        cp_async16(&stg[slot][0][tid], uj + n);
+        if (pre) cp_async16(&stg[slot][1][tid], kb.Ws + n);
+#pragma unroll
+        for (int t = 0; t < kGD; ++t) cp_async16(&stg[slot][2 + t][tid], vb + vo[t] + n);
+      }
+      cp_async_commit();
+    };
+    int64_t n = nbeg + tid;
+#pragma unroll
+    for (int p = 0; p < kDS - 1; ++p) issue(n + (int64_t)p * kDT, p);
+    for (int k = 0; n < nend; ++k, n += kDT) {
+      issue(n + (int64_t)(kDS - 1) * kDT, (k + kDS - 1) % kDS);
+      cp_async_wait<kDS - 1>();   // this entry's copies (issued by this thread) have landed
+      const int slot = k % kDS;
+      const float4 uu = stg[slot][0][tid];
+      const float4 ww = stg[slot][1][tid];
+#pragma unroll
+      for (int t = 0; t < kGD; ++t) {
+        const float4 vv = stg[slot][2 + t][tid];
+        // conj(v) x = (vr xr + vi xi) + i (vr xi - vi xr)
+        df_mac(vv.x, vv.z, uu.x, uu.z, sr[t]);
+        df_mac(vv.y, vv.w, uu.y, uu.w, sr[t]);
+        df_mac(vv.x, vv.z, uu.y, uu.w, si[t]);
+        df_mac(-vv.y, -vv.w, uu.x, uu.z, si[t]);
+        if (pre) ta[t].mac(vv, ww);
       }
     }
-  }
+    cp_async_wait<0>();
+    // warp sums: value 2t + 0/1 = re/im of slot i0 + t; lane l ends with value l / (32 / NV)
+    DF sv[NV];
 #pragma unroll
-  for (int t = 0; t < kGD; ++t) {
-    DF r = df_wsum(sr[t]), q = df_wsum(si[t]);
-    if (lane == 0) red[warp][t] = make_float4(r.h, r.l, q.h, q.l);
+    for (int t = 0; t < kGD; ++t) {
+      sv[2 * t] = sr[t];
+      sv[2 * t + 1] = si[t];
+    }
+    const DF s_out = df_reduce_scatter<NV>(sv, lane);
+    DF t_out{0.f, 0.f};
     if (pre) {
-      r = df_wsum(tr[t]);
-      q = df_wsum(ti[t]);
-      if (lane == 0) red[warp][kGD + t] = make_float4(r.h, r.l, q.h, q.l);
+      if constexpr (kExact) {
+        DF tv[NV];
+#pragma unroll
+        for (int t = 0; t < kGD; ++t) {
+          tv[2 * t] = ta[t].r;
+          tv[2 * t + 1] = ta[t].i;
+        }
+        t_out = df_reduce_scatter<NV>(tv, lane);
+      } else {
+        float tv[NV];
+#pragma unroll
+        for (int t = 0; t < kGD; ++t) {
+          tv[2 * t] = ta[t].r;
+          tv[2 * t + 1] = ta[t].i;
+        }
+        t_out = DF{f_reduce_scatter<NV>(tv, lane), 0.f};
+      }
     }
-  }
-  __syncthreads();
-  const int nout = pre ? 2 * kGD : kGD;
-  if (threadIdx.x < nout && (threadIdx.x % kGD) < ng) {
-    DF r{0.f, 0.f}, q{0.f, 0.f};
-    for (int wi2 = 0; wi2 < kT / 32; ++wi2) {
-      const float4 x = red[wi2][threadIdx.x];
-      r = df_add(r, DF{x.x, x.y});
-      q = df_add(q, DF{x.z, x.w});
+    if ((lane & (32 / NV - 1)) == 0) {
+      const int q = lane / (32 / NV);
+      red[warp][q] = make_float4(s_out.h, s_out.l, 0.f, 0.f);
+      red[warp][NV + q] = make_float4(t_out.h, t_out.l, 0.f, 0.f);
     }
-    const int t = threadIdx.x % kGD;
-    const int64_t row = threadIdx.x < kGD ? kb_row_s(i0 + t) : kb_row_t(m, i0 + t);
-    part4[row * PS + blockIdx.x] = make_float4(r.h, r.l, q.h, q.l);
+    __syncthreads();
+    // thread c < 2 kGD: slot i0 + c % kGD of s (c < kGD) or t (c >= kGD), re and im over the warps
+    const int c = tid;
+    if (c < (pre ? 2 * kGD : kGD) && c % kGD < ng) {
+      const int t = c % kGD, base = (c < kGD ? 0 : NV) + 2 * t;
+      DF r{0.f, 0.f}, q{0.f, 0.f};
+#pragma unroll
+      for (int wi2 = 0; wi2 < kDT / 32; ++wi2) {
+        const float4 x = red[wi2][base], y = red[wi2][base + 1];
+        r = df_add(r, DF{x.x, x.y});
+        q = df_add(q, DF{y.x, y.y});
+      }
+      const int64_t row = c < kGD ? kb_row_s(i0 + t) : kb_row_t(m, i0 + t);
+      reinterpret_cast<float4*>(kb.part)[row * kb.pstride + blockIdx.x] = make_float4(r.h, r.l, q.h, q.l);
+    }
+    __syncthreads();   // red is reused by the next group of the range
   }
 }
 
@@ -147,7 +271,8 @@ __device__ __forceinline__ double2 sum_partials(const KrylovBufs& kb, int64_t r,
   return wsum(s);
 }
 
-// s_i, t_i = sums of the double-float block partials (reduced in double-float, converted once).
+// s_i, t_i = sums of the double-float block partials (reduced in double-float, converted once)
+// over the inner-product blocks whose ranges touched the slot's group.
 // One warp per row; rows 0..j are s, then (when the step applied the preconditioner) t.
 __global__ void __launch_bounds__(kT) k_reduce2(KrylovBufs kb) {
   KState* st = kb.st;
@@ -161,7 +286,12 @@ __global__ void __launch_bounds__(kT) k_reduce2(KrylovBufs kb) {
     const int i = is_t ? q - (j + 1) : q;
     DF r{0.f, 0.f}, c{0.f, 0.f};
     const float4* row = p4 + (is_t ? kb_row_t(m, i) : kb_row_s(i)) * kb.pstride;
-    for (int b = lane; b < kb.nblk_dots; b += 32) {
+    // the blocks whose ranges touched slot i's group (dots_range_begin)
+    const int gd = kb.exact_gs ? kGDOf<true> : kGDOf<false>, g = i / gd;
+    const int64_t T = (int64_t)((j + gd) / gd) * kb.N, G = kb.nblk_dots;
+    const int blo = (int)dots_block_of((int64_t)g * kb.N, T, G);
+    const int bhi = (int)dots_block_of((int64_t)(g + 1) * kb.N - 1, T, G);
+    for (int b = blo + lane; b <= bhi; b += 32) {
       const float4 x = row[b];
       r = df_add(r, DF{x.x, x.y});
       c = df_add(c, DF{x.z, x.w});
@@ -347,14 +477,51 @@ __global__ void __launch_bounds__(32) k_coef(KrylovBufs kb) {
   }
 }
 
-// One sweep over V[0..j-1] for both corrections of the step, all in double-float:
+// One sweep over V[0..j-1] for both corrections of the step:
 //   v_j = (u_j - sum s_i v_i) / rho          (written into slot j)
 //   w  <- w / rho - sum t'_i v_i - h_jj v_j   (t'_i = t_i / rho)
 // and w, unnormalised, becomes u_{j+1}: slot j+1 of the basis, the next step's
 // preconditioner input (the FP64 form also gets it in complex128, W). Normalisation is
-// lagged into rho.
-// A warp takes 32 entries: its two half-warps sum over the two halves of the basis for two
-// entries per lane, meet with one shuffle, and then every lane finishes one entry.
+// lagged into rho. The w correction is double-float throughout. The s_i are the second
+// pass's coefficients, small against |w| (first-pass error, about 1e-7 |w| with float t_i),
+// so in the complex64 form (kExact = false) sum s_i v_i is formed in float from the high
+// parts (error ~1e-7 of that sum, ~1e-13 |w|) and subtracted from u_j in double-float;
+// the FP64 form forms it in double-float.
+// A warp takes 16 entries at a time: its two half-warps sum over the two halves of the basis,
+// one entry per lane, and meet with one shuffle; the grid is one wave of resident blocks
+// striding over the entries.
+template <bool kExact> struct UAcc;
+template <> struct UAcc<true> {
+  DFC_ACC a;
+  __device__ __forceinline__ void mac(float4 hs, float4 v) {   // hs: (re.h, re.l, im.h, im.l)
+    df_mac(hs.x, hs.y, v.x, v.z, a.re);
+    df_mac(-hs.z, -hs.w, v.y, v.w, a.re);
+    df_mac(hs.x, hs.y, v.y, v.w, a.im);
+    df_mac(hs.z, hs.w, v.x, v.z, a.im);
+  }
+  __device__ __forceinline__ void xsum() {
+    auto x = [](DF v) {
+      return df_add(v, DF{__shfl_xor_sync(0xffffffffu, v.h, 16), __shfl_xor_sync(0xffffffffu, v.l, 16)});
+    };
+    a.re = x(a.re);
+    a.im = x(a.im);
+  }
+  __device__ __forceinline__ float4 fin() const { return dfc_fin(a); }
+};
+template <> struct UAcc<false> {
+  float re, im;
+  __device__ __forceinline__ void mac(float4 hs, float4 v) {
+    re = fmaf(hs.x, v.x, fmaf(-hs.z, v.y, re));
+    im = fmaf(hs.x, v.y, fmaf(hs.z, v.x, im));
+  }
+  __device__ __forceinline__ void xsum() {
+    re += __shfl_xor_sync(0xffffffffu, re, 16);
+    im += __shfl_xor_sync(0xffffffffu, im, 16);
+  }
+  __device__ __forceinline__ float4 fin() const { return make_float4(re, im, 0.f, 0.f); }
+};
+
+template <bool kExact>
 __global__ void __launch_bounds__(kT, 5) k_update2(KrylovBufs kb) {
   KState* st = kb.st;
   if (!st->active) return;
@@ -372,46 +539,34 @@ __global__ void __launch_bounds__(kT, 5) k_update2(KrylovBufs kb) {
   const int split = (j + 1) / 2;   // slots [0, split) and [split, j)
   const int ib = half ? split : 0, ie = half ? j : split;
   const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
-  for (int64_t wg = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5; wg * 32 < N; wg += nw) {
-    const int64_t na = wg * 32 + (lane & 15), nb2 = na + 16;
-    const bool va = na < N, vb = nb2 < N;
-    const float4* pa = kb.Vs + (va ? na : 0);
-    const float4* pb = kb.Vs + (vb ? nb2 : 0);
-    DFC_ACC ua{}, ub{}, wa{}, wb{};
-#pragma unroll 2
+  for (int64_t wg = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5; wg * 16 < N; wg += nw) {
+    const int64_t n = wg * 16 + (lane & 15);
+    const bool valid = n < N;
+    const float4* pv = kb.Vs + (valid ? n : 0);
+    UAcc<kExact> ua{};
+    DFC_ACC wa{};
+#pragma unroll 4
     for (int i = ib; i < ie; ++i) {
       const float4 hs = hs4[i], ht = hs4[j + i];   // (re.h, re.l, im.h, im.l)
-      const float4 v = pa[(int64_t)i * ld], u = pb[(int64_t)i * ld];
+      const float4 v = pv[(int64_t)i * ld];
       // c x = (cr xr - ci xi) + i (cr xi + ci xr), x in (hr, hi, lr, li) layout
-      df_mac(hs.x, hs.y, v.x, v.z, ua.re);
-      df_mac(-hs.z, -hs.w, v.y, v.w, ua.re);
-      df_mac(hs.x, hs.y, v.y, v.w, ua.im);
-      df_mac(hs.z, hs.w, v.x, v.z, ua.im);
-      df_mac(hs.x, hs.y, u.x, u.z, ub.re);
-      df_mac(-hs.z, -hs.w, u.y, u.w, ub.re);
-      df_mac(hs.x, hs.y, u.y, u.w, ub.im);
-      df_mac(hs.z, hs.w, u.x, u.z, ub.im);
+      ua.mac(hs, v);
       df_mac(ht.x, ht.y, v.x, v.z, wa.re);
       df_mac(-ht.z, -ht.w, v.y, v.w, wa.re);
       df_mac(ht.x, ht.y, v.y, v.w, wa.im);
       df_mac(ht.z, ht.w, v.x, v.z, wa.im);
-      df_mac(ht.x, ht.y, u.x, u.z, wb.re);
-      df_mac(-ht.z, -ht.w, u.y, u.w, wb.re);
-      df_mac(ht.x, ht.y, u.y, u.w, wb.im);
-      df_mac(ht.z, ht.w, u.x, u.z, wb.im);
     }
+    ua.xsum();
     auto xsum = [](DF v) {
       return df_add(v, DF{__shfl_xor_sync(0xffffffffu, v.h, 16), __shfl_xor_sync(0xffffffffu, v.l, 16)});
     };
-    ua.re = xsum(ua.re); ua.im = xsum(ua.im); ub.re = xsum(ub.re); ub.im = xsum(ub.im);
-    wa.re = xsum(wa.re); wa.im = xsum(wa.im); wb.re = xsum(wb.re); wb.im = xsum(wb.im);
-    // lanes 0-15 finish entry na, lanes 16-31 entry nb2 (= wg * 32 + lane in both cases)
-    const int64_t n = wg * 32 + lane;
-    if (n < N) {
-      const DFC_ACC cu = half ? ub : ua;
-      DFC_ACC cw = half ? wb : wa;
+    wa.re = xsum(wa.re);
+    wa.im = xsum(wa.im);
+    // lanes 0-15 finish the warp's 16 entries
+    if (half == 0 && valid) {
+      DFC_ACC cw = wa;
       float4* slot = kb.Vs + (int64_t)j * ld + n;
-      const float4 d = dfc_sub(*slot, dfc_fin(cu));
+      const float4 d = dfc_sub(*slot, ua.fin());
       const float4 v = dfc_make(df_mul(dfc_re(d), irho), df_mul(dfc_im(d), irho));
       *slot = v;
       dfc_mac(hjj, v, cw);
@@ -423,6 +578,22 @@ __global__ void __launch_bounds__(kT, 5) k_update2(KrylovBufs kb) {
     }
   }
 }
+
+}  // namespace
+
+// Blocks of the correction sweep: one wave of resident blocks (at most one per 16 entries).
+int update_blocks(int64_t N, int nsm, bool exact, size_t smem) {
+  int per_sm = 0;
+  const cudaError_t e = exact ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_update2<true>, kT, smem)
+                              : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_update2<false>, kT, smem);
+  if (e != cudaSuccess || per_sm < 1) {
+    cudaGetLastError();
+    per_sm = 1;
+  }
+  return (int)std::max<int64_t>(1, std::min<int64_t>((int64_t)nsm * per_sm, (N + kT / 2 - 1) / (kT / 2)));
+}
+
+namespace {
 
 // ||v||^2 partials / final
 __global__ void __launch_bounds__(kT) k_norm_part(KrylovBufs kb, const double2* v) {
@@ -543,11 +714,29 @@ __global__ void __launch_bounds__(kT) k_update_x(KrylovBufs kb, double2* x) {
 }  // namespace
 
 void launch_arnoldi(const KrylovBufs& kb, cudaStream_t s, cudaEvent_t mid) {
-  k_dots2<<<dim3(kb.nblk_dots, (kb.m + 1 + kGD - 1) / kGD), kT, 0, s>>>(kb);
+  if (kb.exact_gs)
+    k_dots2<true><<<kb.nblk_dots, kDT, 0, s>>>(kb);
+  else
+    k_dots2<false><<<kb.nblk_dots, kDT, 0, s>>>(kb);
   k_reduce2<<<(2 * (kb.m + 1) + kT / 32 - 1) / (kT / 32), kT, 0, s>>>(kb);
   k_coef<<<1, 32, 0, s>>>(kb);
   if (mid) cudaEventRecord(mid, s);
-  k_update2<<<kb.nblk_upd, kT, sizeof(float4) * 2 * kb.m, s>>>(kb);
+  if (kb.exact_gs)
+    k_update2<true><<<kb.nblk_upd, kT, sizeof(float4) * 2 * kb.m, s>>>(kb);
+  else
+    k_update2<false><<<kb.nblk_upd, kT, sizeof(float4) * 2 * kb.m, s>>>(kb);
+}
+
+// One wave of resident blocks, and at least 64 entries per block (every range non-empty).
+int dots_blocks(int64_t N, int nsm, bool exact) {
+  int per_sm = 0;
+  const cudaError_t e = exact ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_dots2<true>, kDT, 0)
+                              : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_dots2<false>, kDT, 0);
+  if (e != cudaSuccess || per_sm < 1) {
+    cudaGetLastError();
+    per_sm = 1;
+  }
+  return (int)std::max<int64_t>(1, std::min<int64_t>((int64_t)nsm * per_sm, N / 64));
 }
 
 void launch_cycle_start(const KrylovBufs& kb, const double2* r, cudaStream_t s) {
