@@ -810,7 +810,7 @@ static int setup_impl(helm_ctx* h) {
       // grouped block products: every use of one (mapped) block in one group of up to gcap
       std::vector<int> gg, gf, gb;
       L.gcap = coarse_group_lists(L, plan, o.precision == HELM_MIXED ? sizeof(float2) : sizeof(double2), cmap,
-                                  pmapf, pmapb, &gg, &gf, &gb);
+                                  pmapf, pmapb, &gg, &gf, &gb, &L.grows);
       auto put_groups = [&](const std::vector<int>& v, const int** dst, int* n) -> int {
         *n = (int)(v.size() / kGroupInts);
         if (v.empty()) return HELM_OK;

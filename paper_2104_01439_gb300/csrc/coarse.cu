@@ -1331,15 +1331,20 @@ __global__ void __launch_bounds__(256) k_seg_middle(const c2<T>* __restrict__ Lm
 // ---------------------------------------------------------------------------
 // Grouped block products. A group names one dense B x ldb matrix block and g <= 4 vector
 // blocks (sources X[src_v], destinations Y[dst_v]); the CTA stages the g vectors in shared
-// memory and each row chunk it reads from global memory is applied to all of them, so a block
-// that repeats (a converged chain, CoarseLayout's maps) is read once per group instead of once
-// per use. Grid: (groups, row slabs of kRowsSlab rows); each warp takes GroupRows<T>::R rows at
-// a time and lane l walks the 16-byte chunks l, l + 32, ... of them.
+// memory and applies each matrix row to all of them, so a block that repeats (a converged
+// chain, CoarseLayout's maps) is read once per group instead of once per use.
+// Grid: (groups, row slabs of L.grows rows). The kernels are short and bound by memory
+// latency, so each CTA requests its whole slab at once: one thread issues kSlabChunks bulk
+// copies (cp.async.bulk, completing on one mbarrier each) while the others stage the vectors;
+// each warp then waits (bounded) for the chunks holding its rows and works from shared memory.
+// Every chunk barrier is waited on before the CTA exits, so no copy outlives it.
 // Y[dst_v][a] = M[a] x_v, or Y[dst_v][a] -= M[a] x_v (sub). X and Y may be the same array:
 // the sources of a launch are never among its destinations.
 // ---------------------------------------------------------------------------
-constexpr int kRowsThreads = 512;
-constexpr int kRowsSlab = 64;   // rows per CTA
+constexpr int kRowsThreads = 256;
+constexpr int kSlabChunks = 4;         // bulk copies (and barriers) per slab
+constexpr int kSlabMaxRows = 32;
+constexpr size_t kSlabBytes = 64 * 1024;   // slab size aimed at (or one row, if wider)
 template <typename T> struct GroupRows;
 template <> struct GroupRows<float> {
   static constexpr int R = 4;           // rows per warp
@@ -1347,7 +1352,7 @@ template <> struct GroupRows<float> {
   static constexpr int per = 2;
 };
 template <> struct GroupRows<double> {
-  static constexpr int R = 2;
+  static constexpr int R = 4;
   using C = double2;                    // one complex128 value
   static constexpr int per = 1;
 };
@@ -1376,68 +1381,101 @@ __device__ __forceinline__ S warp_reduce_scatter(S (&v)[N], int lane) {
   return r;
 }
 
+// Rows a0 + lr (lr = the warp's R consecutive slab rows, lr < nr) of the staged slab times the
+// G staged vectors; lane l walks the 16-byte chunks l, l + 32, ... of each row.
 template <typename T, int G>
-__device__ __forceinline__ void group_rows(const c2<T>* __restrict__ M, const c2<T>* xs, c2<T>* Y, const int* dst,
-                                           int B, int ldb, bool sub) {
+__device__ __forceinline__ void group_rows(const c2<T>* slab, const c2<T>* xs, c2<T>* Y, const int* dst, int a0,
+                                           int nr, int ldb, bool sub, int lr0) {
   using V = c2<T>;
   using C = typename GroupRows<T>::C;
   constexpr int R = GroupRows<T>::R, N = 2 * R * G, step = 32 / N;
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
-  const int abeg = blockIdx.y * kRowsSlab, aend = min(B, abeg + kRowsSlab);
+  const int lane = threadIdx.x & 31;
   const int nc = ldb / GroupRows<T>::per;
   const C* x4 = reinterpret_cast<const C*>(xs);
-  for (int a0 = abeg + warp * R; a0 < aend; a0 += nw * R) {
-    const C* rows[R];
+  const C* rows[R];
 #pragma unroll
-    for (int r = 0; r < R; ++r) rows[r] = reinterpret_cast<const C*>(M + (size_t)min(a0 + r, aend - 1) * ldb);
-    V s[R][G];
+  for (int r = 0; r < R; ++r) rows[r] = reinterpret_cast<const C*>(slab + (size_t)min(lr0 + r, nr - 1) * ldb);
+  V s[R][G];
 #pragma unroll
-    for (int r = 0; r < R; ++r)
+  for (int r = 0; r < R; ++r)
 #pragma unroll
-      for (int v = 0; v < G; ++v) s[r][v] = mk(T(0), T(0));
-#pragma unroll 1
-    for (int i = lane; i < nc; i += 32) {
-      C p[R];
+    for (int v = 0; v < G; ++v) s[r][v] = mk(T(0), T(0));
+  for (int i = lane; i < nc; i += 32) {
+    C p[R];
 #pragma unroll
-      for (int r = 0; r < R; ++r) p[r] = __ldg(rows[r] + i);
+    for (int r = 0; r < R; ++r) p[r] = rows[r][i];
 #pragma unroll
-      for (int v = 0; v < G; ++v) {
-        const C q = x4[v * nc + i];
+    for (int v = 0; v < G; ++v) {
+      const C q = x4[v * nc + i];
 #pragma unroll
-        for (int r = 0; r < R; ++r) s[r][v] = chunk_fma(p[r], q, s[r][v]);
-      }
-    }
-    T f[N];   // value (r G + v) 2 + component
-#pragma unroll
-    for (int r = 0; r < R; ++r)
-#pragma unroll
-      for (int v = 0; v < G; ++v) {
-        f[(r * G + v) * 2] = s[r][v].x;
-        f[(r * G + v) * 2 + 1] = s[r][v].y;
-      }
-    const T t = warp_reduce_scatter<N>(f, lane);
-    const T ty = __shfl_down_sync(0xffffffffu, t, step);   // imaginary part from the next value's lanes
-    if (lane % (2 * step) == 0) {
-      const int c = lane / (2 * step), r = c / G, v = c % G;
-      if (a0 + r < aend) {
-        V* o = Y + (size_t)dst[v] * ldb + a0 + r;
-        const V val = mk(t, ty);
-        *o = sub ? csub(*o, val) : val;
-      }
+      for (int r = 0; r < R; ++r) s[r][v] = chunk_fma(p[r], q, s[r][v]);
     }
   }
+  T f[N];   // value (r G + v) 2 + component
+#pragma unroll
+  for (int r = 0; r < R; ++r)
+#pragma unroll
+    for (int v = 0; v < G; ++v) {
+      f[(r * G + v) * 2] = s[r][v].x;
+      f[(r * G + v) * 2 + 1] = s[r][v].y;
+    }
+  const T t = warp_reduce_scatter<N>(f, lane);
+  const T ty = __shfl_down_sync(0xffffffffu, t, step);   // imaginary part from the next value's lanes
+  if (lane % (2 * step) == 0) {
+    const int c = lane / (2 * step), r = c / G, v = c % G;
+    if (lr0 + r < nr) {
+      V* o = Y + (size_t)dst[v] * ldb + a0 + lr0 + r;
+      const V val = mk(t, ty);
+      *o = sub ? csub(*o, val) : val;
+    }
+  }
+}
+
+// Dynamic shared memory of a grouped-product CTA: chunk barriers and the error word, the
+// staged vectors (gcap of them), the slab.
+__host__ __device__ inline size_t group_xs_offset() { return 128; }
+template <typename V>
+__host__ __device__ inline size_t group_slab_offset(const CoarseLayout& L) {
+  return group_xs_offset() + ((sizeof(V) * (size_t)L.gcap * L.ldb + 127) & ~size_t(127));
+}
+template <typename V>
+__host__ __device__ inline size_t group_smem(const CoarseLayout& L) {
+  return group_slab_offset<V>(L) + sizeof(V) * (size_t)L.grows * L.ldb;
 }
 
 // Group descriptor: matrix block, g, sources[kGroup], destinations[kGroup].
 template <typename T>
 __device__ __forceinline__ void group_products(const c2<T>* __restrict__ M, const c2<T>* X, c2<T>* Y,
-                                               const int* __restrict__ groups, int B, int ldb, bool sub) {
+                                               const int* __restrict__ groups, const CoarseLayout& L, bool sub,
+                                               int* err) {
   using V = c2<T>;
-  extern __shared__ __align__(16) unsigned char smv[];
-  V* xs = reinterpret_cast<V*>(smv);
+  constexpr int R = GroupRows<T>::R;
+  extern __shared__ __align__(128) unsigned char smv[];
+  uint64_t* bars = reinterpret_cast<uint64_t*>(smv);
+  int* s_err = reinterpret_cast<int*>(smv + 8 * kSlabChunks);
+  V* xs = reinterpret_cast<V*>(smv + group_xs_offset());
+  V* slab = reinterpret_cast<V*>(smv + group_slab_offset<V>(L));
   __shared__ int gd[kGroupInts];
+  const int B = L.B, ldb = L.ldb;
+  const int a0 = blockIdx.y * L.grows, nr = min(B, a0 + L.grows) - a0;   // nr >= 1 (host grid)
+  const int rpc = (nr + kSlabChunks - 1) / kSlabChunks;                    // rows per chunk
   if (threadIdx.x < kGroupInts) gd[threadIdx.x] = __ldg(groups + (size_t)blockIdx.x * kGroupInts + threadIdx.x);
+  if (threadIdx.x == 0) {
+    for (int c = 0; c < kSlabChunks; ++c) mbar_init(&bars[c], 1);
+    *s_err = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
   __syncthreads();
+  if (threadIdx.x == 0) {
+    const V* src = M + ((size_t)gd[0] * B + a0) * ldb;
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    for (int c = 0; c < kSlabChunks; ++c) {
+      const int r0 = min(nr, c * rpc), r1 = min(nr, r0 + rpc);
+      const unsigned bytes = (unsigned)(sizeof(V) * (size_t)(r1 - r0) * ldb);
+      mbar_expect_tx(&bars[c], bytes);   // the arrival (count 1) and the chunk's bytes
+      if (bytes) bulk_g2s(slab + (size_t)r0 * ldb, src + (size_t)r0 * ldb, bytes, &bars[c]);
+    }
+  }
   const int g = gd[1], gpad = g == 3 ? 4 : g;   // three vectors run as four, the fourth zero
   const V zero = mk(T(0), T(0));
   for (int e = threadIdx.x; e < gpad * ldb; e += blockDim.x) {
@@ -1445,35 +1483,44 @@ __device__ __forceinline__ void group_products(const c2<T>* __restrict__ M, cons
     xs[e] = i < B && v < g ? cvt_ldcg(X + (size_t)gd[2 + v] * ldb + i) : zero;
   }
   __syncthreads();
-  const V* Mb = M + (size_t)gd[0] * B * ldb;
   const int* dst = gd + 2 + kGroup;
-  if (g == 1)
-    group_rows<T, 1>(Mb, xs, Y, dst, B, ldb, sub);
-  else if (g == 2)
-    group_rows<T, 2>(Mb, xs, Y, dst, B, ldb, sub);
-  else
-    group_rows<T, 4>(Mb, xs, Y, dst, B, ldb, sub);
+  const int warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  for (int lr0 = warp * R; lr0 < nr; lr0 += nw * R) {
+    bool ok = true;
+    for (int c = lr0 / rpc; c <= min(nr - 1, lr0 + R - 1) / rpc; ++c) ok &= mbar_wait(&bars[c], 0u, s_err, err);
+    if (__all_sync(0xffffffffu, ok)) {
+      if (g == 1)
+        group_rows<T, 1>(slab, xs, Y, dst, a0, nr, ldb, sub, lr0);
+      else if (g == 2)
+        group_rows<T, 2>(slab, xs, Y, dst, a0, nr, ldb, sub, lr0);
+      else
+        group_rows<T, 4>(slab, xs, Y, dst, a0, nr, ldb, sub, lr0);
+    }
+  }
+  __syncthreads();
+  if (threadIdx.x == 0)   // no copy outlives the CTA (returns at once when all have landed)
+    for (int c = 0; c < kSlabChunks; ++c) mbar_wait(&bars[c], 0u, s_err, err, kDrainPolls);
 }
 
 // Block-diagonal pre-pass: p_J = Dinv[cmap J] r_J, grouped by inverse (L.ggemv).
 template <typename T>
-__global__ void __launch_bounds__(kRowsThreads, 2) k_block_gemv(const c2<T>* __restrict__ Dinv,
-                                                                const c2<T>* __restrict__ rc, c2<T>* __restrict__ out,
-                                                                CoarseLayout L, const int* active) {
+__global__ void __launch_bounds__(kRowsThreads) k_block_gemv(const c2<T>* __restrict__ Dinv,
+                                                             const c2<T>* __restrict__ rc, c2<T>* __restrict__ out,
+                                                             CoarseLayout L, int* err, const int* active) {
   if (active && *active == 0) return;
   if ((int)blockIdx.x >= L.ngemv) return;
-  group_products<T>(Dinv, rc, out, L.ggemv, L.B, L.ldb, false);
+  group_products<T>(Dinv, rc, out, L.ggemv, L, false, err);
 }
 
 // Phase C: z_q -= P[J(q)] z_e(k-1) for every position q of segments k >= 1 except their
 // ends, on both paths of a sweep, grouped by segment product (L.gfixf / L.gfixb).
 template <typename T>
-__global__ void __launch_bounds__(kRowsThreads, 2) k_seg_fixup(const c2<T>* __restrict__ P, c2<T>* Z,
-                                                               CoarseLayout L, const int* groups, int ngroups,
-                                                               const int* active) {
+__global__ void __launch_bounds__(kRowsThreads) k_seg_fixup(const c2<T>* __restrict__ P, c2<T>* Z, CoarseLayout L,
+                                                            const int* groups, int ngroups, int* err,
+                                                            const int* active) {
   if (active && *active == 0) return;
   if ((int)blockIdx.x >= ngroups) return;
-  group_products<T>(P, Z, Z, groups, L.B, L.ldb, true);
+  group_products<T>(P, Z, Z, groups, L, true, err);
 }
 
 // Segment products, step i of every segment k >= 1 of one path (one z-slice per segment):
@@ -1595,6 +1642,9 @@ int plan_coarse_solve(const CoarseLayout& L, CoarsePlan* plan) {
   cudaFuncSetAttribute(k_seg_chain<T, 1>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
   cudaFuncSetAttribute(k_seg_chain<T, kRPW>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
   cudaFuncSetAttribute(k_seg_chain<T, 1, kSegWideWarps>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+  // the grouped products stage up to gcap blocks of vectors and one slab (group_smem)
+  cudaFuncSetAttribute(k_block_gemv<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)budget);
+  cudaFuncSetAttribute(k_seg_fixup<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)budget);
   // complex64 solves of long chains: segmented recurrences on the four half-sweeps of the
   // twisted form, one co-resident cluster per segment in phase A. Eight-CTA clusters give
   // twice as many concurrent segments as sixteen-CTA ones for a slower step.
@@ -1747,10 +1797,10 @@ void launch_coarse_solve(const CoarsePlan& plan, const c2<T>* Dinv, const c2<T>*
                          const CoarseLayout& L, const c2<T>* rc, c2<T>* uc, unsigned* bar, int* err,
                          const int* active, int nsm, cudaStream_t s, const SegBufs<T>* seg) {
   // p = blockdiag(Dinv) r for all blocks at once, into uc
-  const int slabs = (L.B + kRowsSlab - 1) / kRowsSlab;
-  const size_t gsmem = sizeof(c2<T>) * L.ldb * L.gcap;
-  if (L.gcap > 0 && gsmem <= 48 * 1024)
-    k_block_gemv<T><<<dim3(std::max(1, L.ngemv), slabs), kRowsThreads, gsmem, s>>>(Dinv, rc, uc, L, active);
+  const int slabs = L.grows > 0 ? (L.B + L.grows - 1) / L.grows : 0;
+  const size_t gsmem = group_smem<c2<T>>(L);
+  if (L.gcap > 0)
+    k_block_gemv<T><<<dim3(std::max(1, L.ngemv), slabs), kRowsThreads, gsmem, s>>>(Dinv, rc, uc, L, err, active);
   else
     k_block_gemv_wide<T><<<nsm * 8, 256, 0, s>>>(Dinv, rc, uc, L, active);
   if (plan.seg && seg) {
@@ -1783,13 +1833,13 @@ void launch_coarse_solve(const CoarsePlan& plan, const c2<T>* Dinv, const c2<T>*
     chain(SegArgs<T>{uc, seg->yb, {Lm, Up}, seg->Pf, L.pmapf, {f[0], f[1]}, 0}, f[0].K + f[1].K);
     chain(SegArgs<T>{seg->yb, seg->yb, {Lm, Up}, seg->Pf, L.pmapf, {f[0], f[1]}, 1}, 2);
     k_seg_fixup<T><<<dim3(std::max(1, L.nfixf), slabs), kRowsThreads, gsmem, s>>>(seg->Pf, seg->yb, L, L.gfixf,
-                                                                                  L.nfixf, active);
+                                                                                  L.nfixf, err, active);
     k_seg_middle<T><<<(L.B * 32 + 255) / 256, 256, 0, s>>>(Lm, Up, uc, seg->yb, L, active);
     // backward sweeps: yb (y, x_m) -> uc (x)
     chain(SegArgs<T>{seg->yb, uc, {Up, Lm}, seg->Pb, L.pmapb, {b[0], b[1]}, 0}, b[0].K + b[1].K);
     chain(SegArgs<T>{uc, uc, {Up, Lm}, seg->Pb, L.pmapb, {b[0], b[1]}, 1}, 2);
     k_seg_fixup<T><<<dim3(std::max(1, L.nfixb), slabs), kRowsThreads, gsmem, s>>>(seg->Pb, uc, L, L.gfixb, L.nfixb,
-                                                                                  active);
+                                                                                  err, active);
     return;
   }
   if (plan.grid) {
@@ -2027,13 +2077,18 @@ void pack_groups(const std::vector<int3>& items, int cap, std::vector<int>* out)
 
 int coarse_group_lists(const CoarseLayout& L, const CoarsePlan* plan, size_t elem, const std::vector<int>& cmap,
                        const std::vector<int>& pmapf, const std::vector<int>& pmapb, std::vector<int>* gemv,
-                       std::vector<int>* fixf, std::vector<int>* fixb) {
+                       std::vector<int>* fixf, std::vector<int>* fixb, int* grows) {
+  *grows = 0;
   gemv->clear();
   fixf->clear();
   fixb->clear();
   const size_t row = elem * (size_t)L.ldb;
   const int cap = row * 4 <= 48 * 1024 ? 4 : row * 2 <= 48 * 1024 ? 2 : row <= 48 * 1024 ? 1 : 0;
   if (cap == 0) return 0;
+  // rows per slab: at most kSlabMaxRows and about kSlabBytes, spread evenly over the slabs
+  const int smax = (int)std::max<size_t>(1, std::min<size_t>(kSlabMaxRows, kSlabBytes / row));
+  const int nslab = (L.B + smax - 1) / smax;
+  *grows = (L.B + nslab - 1) / nslab;
   std::vector<int3> items;
   for (int J = 0; J < L.nb; ++J) items.push_back(make_int3(cmap.empty() ? J : cmap[J], J, J));
   pack_groups(items, cap, gemv);

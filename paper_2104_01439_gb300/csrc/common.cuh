@@ -152,6 +152,7 @@ struct CoarseLayout {
   const int* gfixb = nullptr;
   int ngemv = 0, nfixf = 0, nfixb = 0;
   int gcap = 0;
+  int grows = 0;   // matrix rows per CTA (slab) of the grouped products
 };
 constexpr int kGroup = 4;
 constexpr int kGroupInts = 2 + 2 * kGroup;

@@ -118,11 +118,12 @@ void coarse_block_maps(const CoarseLayout& L, const CoarsePlan* plan, const int*
                        std::vector<int>* pmapf, std::vector<int>* pmapb);
 // Host group lists of the grouped block products (see CoarseLayout) from the block maps (empty
 // map = identity): gemv for the pre-pass, fixf / fixb for the segmented sweeps' fix-ups (left
-// empty without plan.seg). Returns the group capacity (1, 2 or 4 vectors: as many blocks of
-// elem-byte values as 48 KB of shared memory holds; 0 = none fits, lists left empty).
+// empty without plan.seg), and the rows per slab (grows). Returns the group capacity (1, 2 or 4
+// vectors: as many blocks of elem-byte values as 48 KB of shared memory holds; 0 = none fits,
+// lists left empty).
 int coarse_group_lists(const CoarseLayout& L, const CoarsePlan* plan, size_t elem, const std::vector<int>& cmap,
                        const std::vector<int>& pmapf, const std::vector<int>& pmapb, std::vector<int>* gemv,
-                       std::vector<int>* fixf, std::vector<int>* fixb);
+                       std::vector<int>* fixf, std::vector<int>* fixb, int* grows);
 int coarse_seg_launches(const CoarseLayout& L, const CoarsePlan& plan);
 // Block-Thomas factorisation: Dinv[J] = (A_JJ - A_J,J-1 Dinv[J-1] A_J-1,J)^{-1} (two chains
 // meeting at L.mid), in complex128 (8-pivot Gauss-Jordan panels) or in complex double-float

@@ -2,7 +2,7 @@
 
 The index arithmetic of the complex64 segmented solve (k_seg_chain's producer bulk copies,
 consumer reads and writes, shared-memory ring and receive buffers; the grouped fix-up
-products of k_seg_fixup and the host's group lists; k_seg_middle; k_seg_products) is restated here from the kernels and every access is checked against its
+products of k_seg_fixup (slab bulk copies) and the host's group lists; k_seg_middle; k_seg_products) is restated here from the kernels and every access is checked against its
 allocation:
   coupling matrices Lm, Up and the segment products Pf, Pb: nb x B x ldb complex64;
   coarse vectors (p, y, x): nb x ldb;
@@ -19,7 +19,6 @@ import pytest
 ELEM = 8                              # complex64
 SMEM_BUDGET = 227 * 1024 - 1024      # opt-in shared memory per CTA minus the plan's reserve
 SOLVE_MAX_WARPS, SEG_WIDE_WARPS, RPW_MAX, SEG_MAX_LDB = 18, 32, 4, 1040
-ROWS_SLAB = 64
 
 
 def coarse_layout(dim, order, n):
@@ -180,10 +179,29 @@ def pack_groups(items, cap):
     return groups
 
 
+SLAB_CHUNKS, SLAB_MAX_ROWS, SLAB_BYTES = 4, 32, 64 * 1024
+
+
+def slab_rows(B, ldb, elem):
+    """Rows per CTA of the grouped products (the host's grows)."""
+    smax = max(1, min(SLAB_MAX_ROWS, SLAB_BYTES // (ldb * elem)))
+    nslab = -(-B // smax)
+    return -(-B // nslab)
+
+
+def group_smem(cap, ldb, elem, rows):
+    return 128 + ((elem * cap * ldb + 127) & ~127) + elem * rows * ldb
+
+
 def check_group_launch(groups, nb, B, ldb, cap, elem, sub):
-    """k_block_gemv / k_seg_fixup over a group list: staged vectors, matrix rows, outputs."""
+    """k_block_gemv / k_seg_fixup over a group list: staged vectors, the slab's bulk copies,
+    matrix rows, outputs."""
     mat_size, vec_size = nb * B * ldb, nb * ldb
     assert cap in (1, 2, 4) and cap * ldb * elem <= GROUP_SMEM and ldb % 2 == 0
+    rows = slab_rows(B, ldb, elem)
+    assert group_smem(cap, ldb, elem, rows) <= SMEM_BUDGET
+    slabs = [(a0, min(B, a0 + rows)) for a0 in range(0, B, rows)]
+    assert all(a1 > a0 for a0, a1 in slabs)                # no empty slab (every CTA has rows)
     srcs, dsts = set(), set()
     for mb, g, src, dst in groups:
         assert 1 <= g <= cap and 0 <= mb < nb
@@ -197,9 +215,21 @@ def check_group_launch(groups, nb, B, ldb, cap, elem, sub):
             assert dst[v] not in dsts                 # each destination written by one CTA column
             dsts.add(dst[v])
             srcs.add(src[v])
-        for slab in range((B + ROWS_SLAB - 1) // ROWS_SLAB):
-            aend = min(B, slab * ROWS_SLAB + ROWS_SLAB)
-            assert (mb * B + aend - 1) * ldb + ldb <= mat_size
+    mbs = [gr[0] for gr in groups]
+    for mb in {min(mbs), max(mbs)} if mbs else ():    # copies are affine in mb: check the extremes
+        for a0, a1 in slabs:                           # the slab's bulk copies, chunk by chunk
+            nr = a1 - a0
+            rpc = -(-nr // SLAB_CHUNKS)
+            covered = 0
+            for c in range(SLAB_CHUNKS):
+                r0 = min(nr, c * rpc)
+                r1 = min(nr, r0 + rpc)
+                nbytes = elem * (r1 - r0) * ldb
+                src = ((mb * B + a0) + r0) * ldb
+                assert nbytes % 16 == 0 and (src * elem) % 16 == 0 and nbytes < (1 << 20)
+                assert src + (r1 - r0) * ldb <= mat_size and r1 * ldb <= rows * ldb
+                covered += r1 - r0
+            assert covered == nr
     if sub:
         assert not srcs & dsts                        # sources are read while destinations change
     return dsts
