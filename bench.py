@@ -52,7 +52,7 @@ def workload_config(prec_name):
 
 # ---------------------------------------------------------------------------- helpers
 
-COARSE_TRAFFIC_BYTES = 296.5e6   # ncu DRAM bytes of one coarse solve (profiles/coarse_solve_p1_n512.md)
+COARSE_TRAFFIC_BYTES = 235.9e6   # ncu DRAM bytes of one coarse solve (the coarse-solve summary under profiles/)
 
 # stencil kernels at a size above L2: 2D P1, h = 1/4096 (16.8 M DoFs; one complex128
 # vector is 268 MB, twice the 129 MB L2), same kh and shift exponent as the solve workload
