@@ -1334,9 +1334,10 @@ __global__ void __launch_bounds__(256) k_seg_middle(const c2<T>* __restrict__ Lm
 // memory and applies each matrix row to all of them, so a block that repeats (a converged
 // chain, CoarseLayout's maps) is read once per group instead of once per use.
 // Grid: (groups, row slabs of L.grows rows). The kernels are short and bound by memory
-// latency, so each CTA requests its whole slab at once: one thread issues kSlabChunks bulk
-// copies (cp.async.bulk, completing on one mbarrier each) while the others stage the vectors;
-// each warp then waits (bounded) for the chunks holding its rows and works from shared memory.
+// latency, so each CTA requests everything at once: one thread issues a bulk copy
+// (cp.async.bulk) per vector, completing on one mbarrier, and kSlabChunks copies of the slab,
+// on one mbarrier each; the warps wait (bounded) for the vectors, then for the chunks holding
+// their rows, and work from shared memory.
 // Every chunk barrier is waited on before the CTA exits, so no copy outlives it.
 // Y[dst_v][a] = M[a] x_v, or Y[dst_v][a] -= M[a] x_v (sub). X and Y may be the same array:
 // the sources of a launch are never among its destinations.
@@ -1451,8 +1452,8 @@ __device__ __forceinline__ void group_products(const c2<T>* __restrict__ M, cons
   using V = c2<T>;
   constexpr int R = GroupRows<T>::R;
   extern __shared__ __align__(128) unsigned char smv[];
-  uint64_t* bars = reinterpret_cast<uint64_t*>(smv);
-  int* s_err = reinterpret_cast<int*>(smv + 8 * kSlabChunks);
+  uint64_t* bars = reinterpret_cast<uint64_t*>(smv);   // kSlabChunks slab chunks, then the vectors
+  int* s_err = reinterpret_cast<int*>(smv + 8 * (kSlabChunks + 1));
   V* xs = reinterpret_cast<V*>(smv + group_xs_offset());
   V* slab = reinterpret_cast<V*>(smv + group_slab_offset<V>(L));
   __shared__ int gd[kGroupInts];
@@ -1461,14 +1462,19 @@ __device__ __forceinline__ void group_products(const c2<T>* __restrict__ M, cons
   const int rpc = (nr + kSlabChunks - 1) / kSlabChunks;                    // rows per chunk
   if (threadIdx.x < kGroupInts) gd[threadIdx.x] = __ldg(groups + (size_t)blockIdx.x * kGroupInts + threadIdx.x);
   if (threadIdx.x == 0) {
-    for (int c = 0; c < kSlabChunks; ++c) mbar_init(&bars[c], 1);
+    for (int c = 0; c <= kSlabChunks; ++c) mbar_init(&bars[c], 1);
     *s_err = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
   __syncthreads();
+  const int g = gd[1], gpad = g == 3 ? 4 : g;   // three vectors run as four, the fourth zero
   if (threadIdx.x == 0) {
-    const V* src = M + ((size_t)gd[0] * B + a0) * ldb;
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    // the vectors first (every warp waits for them), then the slab chunk by chunk
+    const unsigned vbytes = (unsigned)(sizeof(V) * (size_t)ldb);
+    mbar_expect_tx(&bars[kSlabChunks], vbytes * g);
+    for (int v = 0; v < g; ++v) bulk_g2s(xs + (size_t)v * ldb, X + (size_t)gd[2 + v] * ldb, vbytes, &bars[kSlabChunks]);
+    const V* src = M + ((size_t)gd[0] * B + a0) * ldb;
     for (int c = 0; c < kSlabChunks; ++c) {
       const int r0 = min(nr, c * rpc), r1 = min(nr, r0 + rpc);
       const unsigned bytes = (unsigned)(sizeof(V) * (size_t)(r1 - r0) * ldb);
@@ -1476,11 +1482,12 @@ __device__ __forceinline__ void group_products(const c2<T>* __restrict__ M, cons
       if (bytes) bulk_g2s(slab + (size_t)r0 * ldb, src + (size_t)r0 * ldb, bytes, &bars[c]);
     }
   }
-  const int g = gd[1], gpad = g == 3 ? 4 : g;   // three vectors run as four, the fourth zero
   const V zero = mk(T(0), T(0));
+  const bool xs_ok = mbar_wait(&bars[kSlabChunks], 0u, s_err, err);
+  // the vectors' padding entries (i >= B) and a fourth vector of three are zero
   for (int e = threadIdx.x; e < gpad * ldb; e += blockDim.x) {
     const int v = e / ldb, i = e - v * ldb;
-    xs[e] = i < B && v < g ? cvt_ldcg(X + (size_t)gd[2 + v] * ldb + i) : zero;
+    if (i >= B || v >= g || !xs_ok) xs[e] = zero;
   }
   __syncthreads();
   const int* dst = gd + 2 + kGroup;
@@ -1499,7 +1506,7 @@ __device__ __forceinline__ void group_products(const c2<T>* __restrict__ M, cons
   }
   __syncthreads();
   if (threadIdx.x == 0)   // no copy outlives the CTA (returns at once when all have landed)
-    for (int c = 0; c < kSlabChunks; ++c) mbar_wait(&bars[c], 0u, s_err, err, kDrainPolls);
+    for (int c = 0; c <= kSlabChunks; ++c) mbar_wait(&bars[c], 0u, s_err, err, kDrainPolls);
 }
 
 // Block-diagonal pre-pass: p_J = Dinv[cmap J] r_J, grouped by inverse (L.ggemv).

@@ -194,7 +194,7 @@ def group_smem(cap, ldb, elem, rows):
 
 
 def check_group_launch(groups, nb, B, ldb, cap, elem, sub):
-    """k_block_gemv / k_seg_fixup over a group list: staged vectors, the slab's bulk copies,
+    """k_block_gemv / k_seg_fixup over a group list: the vectors' and the slab's bulk copies,
     matrix rows, outputs."""
     mat_size, vec_size = nb * B * ldb, nb * ldb
     assert cap in (1, 2, 4) and cap * ldb * elem <= GROUP_SMEM and ldb % 2 == 0
@@ -212,9 +212,12 @@ def check_group_launch(groups, nb, B, ldb, cap, elem, sub):
         for v in range(g):
             assert 0 <= src[v] < nb and 0 <= dst[v] < nb
             assert src[v] * ldb + B <= vec_size and dst[v] * ldb + B <= vec_size
+            # the vector's bulk copy: ldb entries from src[v] ldb into staged slot v
+            assert src[v] * ldb + ldb <= vec_size and (src[v] * ldb * elem) % 16 == 0 and (ldb * elem) % 16 == 0
             assert dst[v] not in dsts                 # each destination written by one CTA column
             dsts.add(dst[v])
             srcs.add(src[v])
+        assert g * ldb * elem < (1 << 20)             # the vectors' barrier transaction count
     mbs = [gr[0] for gr in groups]
     for mb in {min(mbs), max(mbs)} if mbs else ():    # copies are affine in mb: check the extremes
         for a0, a1 in slabs:                           # the slab's bulk copies, chunk by chunk
