@@ -4,8 +4,9 @@ room for the synchronisation a cudaMalloc may cause). It must give what
 helm_coarse_solve gives, call after call, using only the library's fixed 4 MiB
 scratch array, and refuse problems that do not fit. Both are also held, entry by
 entry, to the oracle's sparse direct solve of its own assembled coarse matrix
-(independent of the library's factor). Collected after the main parity tests (only
-the Q_p parity tests of test_zzz_gpu_qp come later).
+(independent of the library's factor). The file's name sorts after every other test
+file, so pytest collects it last: a run that stops at the first failure has already run
+everything else when it gets here.
 """
 import ctypes
 
