@@ -58,12 +58,15 @@ extern "C" {
 #define HELM_SIMPLICES 0
 #define HELM_TENSOR 1
 
-#define HELM_FP64 0          /* everything in complex128 */
+#define HELM_FP64 0          /* everything in complex128 (Gram-Schmidt arithmetic in
+                                double-float pairs) */
 #define HELM_MIXED 1         /* V-cycle (smoother, transfers, coarse triangular
                                 solves) in complex64; outer apply, Arnoldi basis
                                 and coarse factorisation in double-float pairs
-                                (~48 significant bits); Hessenberg, Givens and the
-                                true residual in complex128 */
+                                (~48 significant bits), the orthogonalising second
+                                Gram-Schmidt pass too (the first pass's projections
+                                in float); Hessenberg, Givens and the true residual
+                                in complex128 */
 
 typedef struct helm_ctx* helm_t;
 
