@@ -490,8 +490,9 @@ def run_ours(args):
                  "relres_true": r64.relres_true, "setup_ms": setup_ms_fp64, "solve_ms": r64.solve_ms,
                  "mixed_speedup": value / (world * len(t_fp64) / fp64_total)},
         "accuracy": {"mixed": accuracy(x_mixed, r), "fp64": accuracy(x_fp64, r64),
-                     "note": "complex64 V-cycle with double-float (~48-bit) Arnoldi basis and coarse factor "
-                             "(mixed); complex128 throughout except the double-float Gram-Schmidt (fp64)"},
+                     "note": "complex64 V-cycle with double-float (~48-bit) Arnoldi basis, second Gram-Schmidt "
+                             "pass and coarse factor, first-pass projections in float (mixed); complex128 "
+                             "throughout except the double-float Gram-Schmidt (fp64)"},
         "coarse_factor": {"mixed": {"factored_blocks": reuse_mixed[0], "reused_blocks": reuse_mixed[1]},
                           "fp64": {"factored_blocks": reuse_fp64[0], "reused_blocks": reuse_fp64[1]}},
         "phase_ms_per_iteration": phase_ms,
