@@ -148,7 +148,15 @@ def _fgmres_mgs(A, M, F, m, tol, maxit):
         x = x + np.array(Z).T @ y
 
 
-def _fgmres_lagged(A, M, F, m, tol, maxit):
+def _fgmres_lagged(A, M, F, m, tol, maxit, float_first=False, float_second=False, orth=None):
+    """The lagged one-sweep CGS2 FGMRES of krylov.cu. float_first: the first pass's projections
+    t_i and the second pass's correction sum sum s_i v_i in complex64 arithmetic (the complex64
+    form); float_second: the second pass's projections s_i in complex64 too (a negative control).
+    orth collects max |V^H V - I| over each cycle's finished basis."""
+    c64 = np.complex64
+
+    def dot(a, b, low):
+        return complex(np.vdot(a.astype(c64), b.astype(c64))) if low else np.vdot(a, b)
     n = len(F)
     x = np.zeros(n, complex)
     nF, total, hist = np.linalg.norm(F), 0, []
@@ -170,8 +178,8 @@ def _fgmres_lagged(A, M, F, m, tol, maxit):
             if pre:                                      # preconditioner and A0 on slot j
                 Z[j] = M @ Vs[j]
                 W = A @ Z[j]
-            s = np.array([np.vdot(Vs[i], Vs[j]) for i in range(j + 1)])        # k_dots2
-            t = np.array([np.vdot(Vs[i], W) for i in range(j + 1)]) if pre else None
+            s = np.array([dot(Vs[i], Vs[j], float_second and i < j) for i in range(j + 1)])   # k_dots2
+            t = np.array([dot(Vs[i], W, float_first) for i in range(j + 1)]) if pre else None
             rho2 = s[j].real - np.sum(np.abs(s[:j]) ** 2)                      # k_coef
             rho = np.sqrt(rho2) if rho2 > 0 else 0.0
             stop = False
@@ -202,12 +210,16 @@ def _fgmres_lagged(A, M, F, m, tol, maxit):
             d = np.sum(np.conj(s[:j]) * t[:j])
             hjj = (t[j] - d) / rho / rho                 # the step uses z_j / rho
             hcol[:j], hcol[j], zs[j] = t[:j] / rho, hjj, 1.0 / rho
-            v = (Vs[j] - s[:j] @ Vs[:j]) / rho           # k_update2
+            corr = (s[:j].astype(c64) @ Vs[:j].astype(c64)).astype(complex) if float_first else s[:j] @ Vs[:j]
+            v = (Vs[j] - corr) / rho                     # k_update2
             Vs[j] = v
             W = W / rho - hcol[:j] @ Vs[:j] - hjj * v
             pre = j + 1 < m and total + 2 <= maxit
             j += 1
             Vs[j] = W                                    # unnormalised u_{j+1}
+        if orth is not None and j > 0:
+            Q = Vs[:j]
+            orth.append(np.abs(Q.conj() @ Q.T - np.eye(j)).max())
         y = np.linalg.solve(np.triu(H[:j, :j]), g[:j]) * zs[:j] if j > 0 else np.zeros(0)
         x = x + Z[:j].T @ y
 
@@ -227,6 +239,31 @@ def test_lagged_cgs2_fgmres_matches_mgs_fgmres(m, maxit):
     r1 = np.linalg.norm(F - A @ x1)
     r2 = np.linalg.norm(F - A @ x2)
     assert abs(r1 - r2) <= 1e-6 * np.linalg.norm(F) + 1e-3 * r1
+
+
+@pytest.mark.parametrize("m", [20, 7])
+def test_float_first_pass_keeps_the_basis_orthogonal(m):
+    """The complex64 form's Gram-Schmidt: first-pass projections and the second pass's
+    correction sum in float, second-pass projections in full precision. The second pass
+    removes what the float first pass leaves, so the basis stays orthogonal to ~1e-13, the
+    iterations match MGS FGMRES and the Givens estimate equals the true residual. The control
+    with the second pass in float too loses orthogonality at the float level."""
+    rng = np.random.default_rng(3)
+    n = 120
+    A = np.eye(n) * 4 + 0.3 * (rng.standard_normal((n, n)) + 1j * rng.standard_normal((n, n)))
+    M = np.linalg.inv(A + 0.05 * rng.standard_normal((n, n)))
+    F = rng.standard_normal(n) + 1j * rng.standard_normal(n)
+    x1, it1, _ = _fgmres_mgs(A, M, F, m, 1e-10, 500)
+    orth = []
+    x2, it2, h2 = _fgmres_lagged(A, M, F, m, 1e-10, 500, float_first=True, orth=orth)
+    assert abs(it1 - it2) <= 1
+    assert max(orth) <= 1e-12
+    r2 = np.linalg.norm(F - A @ x2) / np.linalg.norm(F)
+    assert r2 <= 1e-10 * 1.01 and abs(h2[-1] - r2) <= 1e-14   # (relative to |F|: the rounding floor)
+    assert np.linalg.norm(x2 - x1) <= 1e-8 * np.linalg.norm(x1)
+    orth_low = []
+    _fgmres_lagged(A, M, F, m, 1e-10, 500, float_first=True, float_second=True, orth=orth_low)
+    assert max(orth_low) > 1e-9
 
 
 def test_segment_products_bounded_on_helmholtz_coarse_operator():
