@@ -17,6 +17,9 @@
 // Knuth's TwoSum; warp reductions stay in double-float and only the per-block
 // partials are converted to double. Inner products carry ~48 significant bits
 // (relative error ~1e-15 of sum |a_i b_i|), the vector w itself stays complex128.
+// In the complex64 form the first pass's projections, and the second pass's small
+// correction sum, are formed in float (k_dots2, k_update2): the second pass, which
+// stays double-float, completes them.
 // Complex Givens rotations (c real, s complex), the residual estimate
 // |g_{j+1}| and the convergence test run on the device in one warp, so a
 // captured iteration never returns to the host. All kernels read the Arnoldi
